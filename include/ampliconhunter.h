@@ -1,0 +1,251 @@
+/*
+ * ampliconhunter.h -- C ABI of the GB300 (sm_103a) in-silico PCR hot path.
+ *
+ * The operations are those of AmpliconHunter (Howard-Stone & Mandoiu,
+ * arXiv 2509.13300): find the binding sites of a degenerate primer pair on
+ * both strands of every genome with at most k mismatches (Sec. 2.1, Primer
+ * matching), score each site's nearest-neighbour melting temperature as the
+ * maximum over the primer's oligonucleotides (Sec. 2.1, Melting temperature
+ * filtering), pair sites on opposite strands into amplicons inside the
+ * length window (Sec. 2.1, Amplicon calling) with FR/RF/FF/RR labels (Sec.
+ * 2.1, Amplicon analysis, item 1) and return the amplicon sequences (Sec.
+ * 2.1, Visualization).  The inputs follow the paper's (Sec. 1): genome
+ * sequences with contigs, degenerate primers, annealing temperature,
+ * mismatch limit, amplicon length bounds, and the concentration and salt
+ * parameters of the NN model.
+ *
+ * Conventions for every call:
+ *  - Coordinates are 0-based, half-open and relative to the contig.
+ *  - Bulk arrays marked "host or device" may be host memory (pageable or
+ *    pinned) or device memory of the context's GPU; the library detects which.
+ *    Arrays marked "host" must be host memory.  The caller owns every array
+ *    it passes; the library owns the packed genome sets (until
+ *    ah_unload_genomes or ah_destroy) and its own scratch memory.
+ *  - `stream` is a cudaStream_t (NULL: the context's own stream).  Work is
+ *    ordered after earlier work on that stream.  Every call returns only
+ *    when its outputs are written (host outputs included).
+ *  - Outputs with a capacity: if `cap` is smaller than the number of records
+ *    needed, nothing is written, `*n_out` receives the needed count and the
+ *    call returns AH_ERR_OVERFLOW.  cap = 0 is therefore a size query.
+ *  - Canonical order (results are deterministic and bit-exact across runs):
+ *    sites by (pair, contig, pos, primer, strand); amplicons by
+ *    (pair, contig, start, end, orient).  "contig" is the index of the contig
+ *    in the order the genome set was loaded.
+ *  - A context is thread-compatible, not thread-safe: calls on one context
+ *    must not overlap.  Different contexts are independent.
+ *  - On any error the call returns a non-zero status; ah_last_error() gives a
+ *    one-line message.  No call aborts the process.
+ */
+#ifndef AMPLICONHUNTER_H
+#define AMPLICONHUNTER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ah_status;
+#define AH_OK 0
+#define AH_ERR_ARG 1          /* invalid argument: null pointer, bad size, unknown id, bad parameter */
+#define AH_ERR_PRIMER 2       /* primer rejected: non-IUPAC letter, length < 5 or > 32, degeneracy > 10000, k > 10 */
+#define AH_ERR_OOM 3          /* device memory allocation failed */
+#define AH_ERR_BUDGET 4       /* the request would exceed the context's device-memory budget */
+#define AH_ERR_OVERFLOW 5     /* output capacity too small; *n_out holds the needed count */
+#define AH_ERR_CUDA 6         /* CUDA runtime error (message in ah_last_error) */
+#define AH_ERR_TIMEOUT 7      /* a bounded device-side wait ran out; the context stays usable */
+#define AH_ERR_JIT 8          /* run-time compilation of a specialised kernel failed */
+#define AH_ERR_DEVICE_CHECK 9 /* a device-side consistency check failed */
+
+/* Server limits of Sec. 2.2 (the paper's web server), enforced by ah_set_primers. */
+#define AH_MAX_DEGENERACY 10000
+#define AH_MAX_MISMATCHES 10
+#define AH_MIN_PRIMER_LEN 5
+/* Kernel limit of this library: a primer holds at most 32 positions. */
+#define AH_MAX_PRIMER_LEN 32
+/* Most primer pairs one ah_scan call fuses into one pass over the genomes. */
+#define AH_MAX_PAIRS_PER_SCAN 16
+
+typedef struct ah_ctx ah_ctx;
+
+/* PCR parameters of one primer pair (Sec. 1 and Sec. 2.1).
+ * k         mismatches allowed per primer site, 0..10 (Sec. 2.2 limit)
+ * clamp     3' clamp length: no mismatch in the clamp 3'-most primer bases (0 = off)
+ * min_len, max_len
+ *           amplicon length window, inclusive; the length is the outer length
+ *           end - start, both primer sites included
+ * tm_min    minimum melting temperature in deg C; a site passes when the max
+ *           Tm over its primer's oligos is >= tm_min (ah_tm pass flags)
+ * dnac1_nM  primer concentration; dnac2_nM template concentration (nM);
+ *           the NN model uses x = (dnac1 - dnac2/2) * 1e-9, which must be > 0
+ * Na_mM, K_mM, Tris_mM, Mg_mM, dNTPs_mM
+ *           ion concentrations (mM); [Na_eq] = Na + K + Tris/2
+ *           + 120 sqrt(Mg - dNTPs) when Mg > dNTPs (von Ahsen 2001)
+ * saltcorr  0 none; 1 Tm += 16.6 log10[Na_eq]; 2 Tm += 16.6 log10([Na_eq]/(1 +
+ *           0.7 [Na_eq])) + 3.85; 3 Tm += 12.5 log10[Na_eq]; 4 Tm += 11.7
+ *           log10[Na_eq]; 5 dS += 0.368 (L - 1) ln[Na_eq] ([Na_eq] in mol/L) */
+typedef struct ah_pcr_params {
+    int32_t k;
+    int32_t clamp;
+    int32_t min_len;
+    int32_t max_len;
+    double tm_min;
+    double dnac1_nM;
+    double dnac2_nM;
+    double Na_mM;
+    double K_mM;
+    double Tris_mM;
+    double Mg_mM;
+    double dNTPs_mM;
+    int32_t saltcorr;
+    int32_t reserved;
+} ah_pcr_params;
+
+/* One primer binding site (Sec. 2.1 Primer matching).
+ * strand 0 ('+'): the primer matches the + strand at [pos, pos + L);
+ * strand 1 ('-'): the primer's reverse complement matches the + strand at
+ * [pos, pos + L).  mm = mismatches (<= k).  pair = index into the pair_ids
+ * array of the ah_scan call that produced it. */
+typedef struct ah_site {
+    uint32_t genome;
+    uint32_t contig;
+    uint32_t pos;
+    uint8_t primer; /* 0 forward, 1 reverse */
+    uint8_t strand; /* 0 '+', 1 '-' */
+    uint8_t mm;
+    uint8_t pair;
+} ah_site;
+
+/* One amplicon (Sec. 2.1 Amplicon calling): a '+' site at `start` (index
+ * `left` in the site array) and a '-' site ending at `end` (index `right`) in
+ * the same contig.  orient: 0 FR, 1 RF, 2 FF, 3 RR = (primer of the left
+ * site, primer of the right site) (Sec. 2.1 Amplicon analysis, item 1). */
+typedef struct ah_amplicon {
+    uint32_t genome;
+    uint32_t contig;
+    uint32_t start;
+    uint32_t end;
+    uint32_t left;
+    uint32_t right;
+    uint8_t orient;
+    uint8_t pair;
+    uint8_t pad0;
+    uint8_t pad1;
+} ah_amplicon;
+
+/* Nearest-neighbour parameter table (Sec. 2.1: the NN model of DNA duplex
+ * stability).  Base index A=0 C=1 G=2 T=3.
+ * stack_dH/dS[((t0*4 + t1)*4 + b0)*4 + b1]: stack of top 5'-t0 t1-3' over the
+ *   template bases b0 (opposite t0) and b1 (opposite t1); kcal/mol, cal/(K mol).
+ * term_dH/dS[p*4 + t]: initiation term of a duplex end whose primer base is p
+ *   and template base is t.
+ * The default table (used when none is set) holds the SantaLucia (1998)
+ * unified Watson-Crick stacks and terminal initiation terms; a stack holding
+ * a mismatched pair contributes (0, 0) and a mismatched end takes the
+ * initiation term of the primer base's class (A/T or G/C). */
+typedef struct ah_nn_table {
+    double stack_dH[256];
+    double stack_dS[256];
+    double term_dH[16];
+    double term_dS[16];
+} ah_nn_table;
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes caps the device
+ * memory the context may hold (packed genomes + scratch); 0 = no cap.
+ * Returns AH_ERR_ARG for a bad device or null out, AH_ERR_CUDA on a CUDA
+ * failure. */
+ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out);
+
+/* Destroy a context and free everything it owns.  Null is a no-op. */
+void ah_destroy(ah_ctx *ctx);
+
+/* Message of the last error on this context (library-owned, valid until the
+ * next call on the context).  Null ctx: the last ah_create error. */
+const char *ah_last_error(const ah_ctx *ctx);
+
+/* Device bytes the context holds now (pool + scratch). */
+size_t ah_device_bytes(const ah_ctx *ctx);
+
+/* Load a genome collection (Sec. 1: genome sequences in FASTA form, here
+ * already parsed).  seq (host or device): n_bases ASCII letters, all contigs
+ * concatenated; any case; letters other than A/C/G/T (N, IUPAC codes, gaps)
+ * are kept as "no base", which mismatches every primer position.
+ * contig_off (host): n_contigs + 1 non-decreasing offsets into seq, first 0,
+ * last n_bases.  contig_genome (host): genome id of each contig.
+ * The library packs the sequence on the device into its own layout (4 one-hot
+ * bitplanes A/C/G/T) and returns an id in *set_id_out.  The caller's arrays
+ * are not referenced after the call.
+ * Errors: AH_ERR_ARG (null pointers, non-monotone offsets, n_contigs = 0),
+ * AH_ERR_BUDGET, AH_ERR_OOM, AH_ERR_CUDA. */
+ah_status ah_load_genomes(ah_ctx *ctx, const uint8_t *seq, uint64_t n_bases, const uint64_t *contig_off,
+                          uint32_t n_contigs, const uint32_t *contig_genome, uint32_t *set_id_out, void *stream);
+
+/* Free a loaded genome set.  AH_ERR_ARG for an unknown id. */
+ah_status ah_unload_genomes(ah_ctx *ctx, uint32_t set_id);
+
+/* Register a degenerate primer pair with its PCR parameters (Sec. 1, Sec.
+ * 2.1).  fwd, rev: NUL-terminated IUPAC strings (A C G T R Y S W K M B D H V N,
+ * any case), 5'->3'.  Validation follows the limits of Sec. 2.2: each primer
+ * at least 5 letters and degeneracy at most 10000, k at most 10; this library
+ * also requires at most 32 letters.  Errors: AH_ERR_PRIMER for a primer or k
+ * outside the limits, AH_ERR_ARG for other bad parameters (clamp < 0,
+ * min_len > max_len, x <= 0, salt method outside 0..5, [Na_eq] <= 0 with a
+ * salt method). */
+ah_status ah_set_primers(ah_ctx *ctx, const char *fwd, const char *rev, const ah_pcr_params *params,
+                         uint32_t *pair_id_out);
+
+/* Replace the NN parameter table of a registered pair (host struct, copied).
+ * Null restores the default table.  AH_ERR_ARG for an unknown pair or a
+ * non-finite entry. */
+ah_status ah_set_nn_table(ah_ctx *ctx, uint32_t pair_id, const ah_nn_table *table);
+
+/* Primer matching (Sec. 2.1): every site of every listed pair on both strands
+ * of every contig of the set with <= k mismatches (and the 3' clamp when
+ * set), in canonical order.  A mismatch is a genome position whose base is not
+ * in the primer position's IUPAC set; a non-ACGT genome letter mismatches
+ * every position.  Windows never cross a contig end.  All listed pairs share
+ * one pass over the packed genomes.  pair_ids (host): n_pairs ids, 1..16.
+ * out (host or device): cap records.  *n_out (host): number of sites.
+ * Errors: AH_ERR_ARG, AH_ERR_OVERFLOW, AH_ERR_JIT, AH_ERR_TIMEOUT, AH_ERR_CUDA. */
+ah_status ah_scan(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, ah_site *out,
+                  uint64_t cap, uint64_t *n_out, void *stream);
+
+/* Melting temperature (Sec. 2.1): for each site, the maximum over every
+ * oligonucleotide of its primer of the NN Tm (deg C) of that oligo against the
+ * template at the site, computed in fp32 (NaN when the template window holds a
+ * non-ACGT letter).  sites (host or device) as returned by ah_scan with the
+ * same pair_ids.  tm_out (host or device, n floats).  pass_out (host or
+ * device, n bytes, may be null): 1 when the site's max Tm >= its pair's
+ * tm_min; the decision is taken in fp64 whenever the fp32 value lies within
+ * 0.05 deg C of tm_min, so it equals the fp64 decision.
+ * Errors: AH_ERR_ARG, AH_ERR_CUDA. */
+ah_status ah_tm(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, const ah_site *sites,
+                uint64_t n, float *tm_out, uint8_t *pass_out, void *stream);
+
+/* Amplicon calling (Sec. 2.1): every '+' site at s paired with every '-' site
+ * at t >= s of the same pair and contig whose amplicon [s, t + L_right) has
+ * length in [min_len, max_len]; when `pass` (host or device, n bytes) is
+ * given, both sites must have pass = 1 (the Tm filter).  sites (host or
+ * device) must be in canonical order (as ah_scan returns them).  out (host or
+ * device, cap records) in canonical order; *n_out (host).
+ * Errors: AH_ERR_ARG, AH_ERR_OVERFLOW, AH_ERR_CUDA. */
+ah_status ah_pair(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, const ah_site *sites,
+                  const uint8_t *pass, uint64_t n, ah_amplicon *out, uint64_t cap, uint64_t *n_out, void *stream);
+
+/* Amplicon sequences (Sec. 2.1: the main output is a FASTA of amplicon
+ * sequences with coordinates and orientations).  For each amplicon the bases
+ * [start, end) of its contig, upper case, every non-ACGT letter as 'N'; an RF
+ * amplicon is reverse-complemented so it reads from the forward primer.
+ * seq_out (host or device, cap bytes, no separators); offsets_out (host or
+ * device, n + 1 entries): amplicon i is seq_out[offsets[i], offsets[i+1]).
+ * On AH_ERR_OVERFLOW offsets_out is written and offsets_out[n] is the size
+ * needed.  Errors: AH_ERR_ARG, AH_ERR_OVERFLOW, AH_ERR_CUDA. */
+ah_status ah_fetch(ah_ctx *ctx, uint32_t set_id, const ah_amplicon *amplicons, uint64_t n, char *seq_out,
+                   uint64_t cap, uint64_t *offsets_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMPLICONHUNTER_H */

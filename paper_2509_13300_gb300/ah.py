@@ -1,0 +1,270 @@
+"""Python binding of the C ABI in include/ampliconhunter.h (ctypes).
+
+Argument marshalling only: every step of the hot path runs in the native
+library's CUDA kernels.  Arrays may be numpy arrays (host) or torch tensors
+(host or CUDA); the library detects device pointers itself.  The library is
+loaded on first use; if it has not been built this raises, there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+AH_OK, AH_ERR_ARG, AH_ERR_PRIMER, AH_ERR_OOM, AH_ERR_BUDGET, AH_ERR_OVERFLOW, AH_ERR_CUDA, AH_ERR_TIMEOUT, \
+    AH_ERR_JIT, AH_ERR_DEVICE_CHECK = range(10)
+STATUS_NAMES = {0: "AH_OK", 1: "AH_ERR_ARG", 2: "AH_ERR_PRIMER", 3: "AH_ERR_OOM", 4: "AH_ERR_BUDGET",
+                5: "AH_ERR_OVERFLOW", 6: "AH_ERR_CUDA", 7: "AH_ERR_TIMEOUT", 8: "AH_ERR_JIT",
+                9: "AH_ERR_DEVICE_CHECK"}
+
+SITE_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("pos", "<u4"), ("primer", "u1"),
+                       ("strand", "u1"), ("mm", "u1"), ("pair", "u1")])
+AMPLICON_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("start", "<u4"), ("end", "<u4"),
+                           ("left", "<u4"), ("right", "<u4"), ("orient", "u1"), ("pair", "u1"),
+                           ("pad0", "u1"), ("pad1", "u1")])
+
+# Every symbol include/ampliconhunter.h declares.
+EXPORTS = ["ah_create", "ah_destroy", "ah_last_error", "ah_device_bytes", "ah_load_genomes", "ah_unload_genomes",
+           "ah_set_primers", "ah_set_nn_table", "ah_scan", "ah_tm", "ah_pair", "ah_fetch"]
+
+
+class AHError(RuntimeError):
+    """A non-zero ah_status.  For AH_ERR_OVERFLOW, `needed` is the count the
+    call reported in its n_out argument."""
+
+    def __init__(self, status: int, msg: str, needed: int | None = None):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+        self.needed = needed
+
+
+class PcrParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("clamp", ctypes.c_int32), ("min_len", ctypes.c_int32),
+                ("max_len", ctypes.c_int32), ("tm_min", ctypes.c_double), ("dnac1_nM", ctypes.c_double),
+                ("dnac2_nM", ctypes.c_double), ("Na_mM", ctypes.c_double), ("K_mM", ctypes.c_double),
+                ("Tris_mM", ctypes.c_double), ("Mg_mM", ctypes.c_double), ("dNTPs_mM", ctypes.c_double),
+                ("saltcorr", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class NNTable(ctypes.Structure):
+    _fields_ = [("stack_dH", ctypes.c_double * 256), ("stack_dS", ctypes.c_double * 256),
+                ("term_dH", ctypes.c_double * 16), ("term_dS", ctypes.c_double * 16)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded native library (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"native library missing: {path}; build it with "
+                               "paper_2509_13300_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        P, U32, U64, I32, S = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_size_t
+        sig = {
+            "ah_create": (I32, [ctypes.c_int, S, ctypes.POINTER(P)]),
+            "ah_destroy": (None, [P]),
+            "ah_last_error": (ctypes.c_char_p, [P]),
+            "ah_device_bytes": (S, [P]),
+            "ah_load_genomes": (I32, [P, P, U64, P, U32, P, ctypes.POINTER(U32), P]),
+            "ah_unload_genomes": (I32, [P, U32]),
+            "ah_set_primers": (I32, [P, ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(PcrParams),
+                                     ctypes.POINTER(U32)]),
+            "ah_set_nn_table": (I32, [P, U32, P]),
+            "ah_scan": (I32, [P, U32, P, U32, P, U64, ctypes.POINTER(U64), P]),
+            "ah_tm": (I32, [P, U32, P, U32, P, U64, P, P, P]),
+            "ah_pair": (I32, [P, U32, P, U32, P, P, U64, P, U64, ctypes.POINTER(U64), P]),
+            "ah_fetch": (I32, [P, U32, P, U64, P, U64, P, P]),
+            "ah_debug_compile_scan": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(s.cuda_stream)
+    return ctypes.c_void_p(int(s))
+
+
+def pcr_params(d: dict) -> PcrParams:
+    return PcrParams(int(d["k"]), int(d.get("clamp", 0)), int(d["min_len"]), int(d["max_len"]),
+                     float(d.get("tm_min", float("-inf"))), float(d.get("dnac1_nM", 250.0)),
+                     float(d.get("dnac2_nM", 25.0)), float(d.get("Na_mM", 50.0)), float(d.get("K_mM", 0.0)),
+                     float(d.get("Tris_mM", 0.0)), float(d.get("Mg_mM", 0.0)), float(d.get("dNTPs_mM", 0.0)),
+                     int(d.get("saltcorr", 5)), 0)
+
+
+# ---------------------------------------------------------------- ABI calls
+class Context:
+    """One ah_ctx.  Methods carry the ABI's names and arguments."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        self._lib = lib()
+        h = ctypes.c_void_p()
+        st = self._lib.ah_create(device, mem_budget_bytes, ctypes.byref(h))
+        if st != AH_OK:
+            raise AHError(st, self._lib.ah_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.ah_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st: int, needed: int | None = None):
+        if st != AH_OK:
+            raise AHError(st, self._lib.ah_last_error(self.h).decode(), needed)
+
+    def last_error(self) -> str:
+        return self._lib.ah_last_error(self.h).decode()
+
+    def device_bytes(self) -> int:
+        return int(self._lib.ah_device_bytes(self.h))
+
+    def ah_load_genomes(self, seq, n_bases: int, contig_off: np.ndarray, contig_genome: np.ndarray,
+                        stream=None) -> int:
+        contig_off = np.ascontiguousarray(contig_off, dtype=np.uint64)
+        contig_genome = np.ascontiguousarray(contig_genome, dtype=np.uint32)
+        sid = ctypes.c_uint32()
+        self._check(self._lib.ah_load_genomes(self.h, _ptr(seq), n_bases, _ptr(contig_off), len(contig_off) - 1,
+                                              _ptr(contig_genome), ctypes.byref(sid), _stream(stream)))
+        return sid.value
+
+    def ah_unload_genomes(self, set_id: int):
+        self._check(self._lib.ah_unload_genomes(self.h, set_id))
+
+    def ah_set_primers(self, fwd: str, rev: str, params: dict) -> int:
+        pid = ctypes.c_uint32()
+        p = pcr_params(params)
+        self._check(self._lib.ah_set_primers(self.h, fwd.encode(), rev.encode(), ctypes.byref(p), ctypes.byref(pid)))
+        return pid.value
+
+    def ah_set_nn_table(self, pair_id: int, table: NNTable | None):
+        self._check(self._lib.ah_set_nn_table(self.h, pair_id, ctypes.byref(table) if table is not None else None))
+
+    def ah_scan(self, set_id: int, pair_ids, out, cap: int, stream=None) -> int:
+        ids = np.ascontiguousarray(pair_ids, dtype=np.uint32)
+        n = ctypes.c_uint64()
+        st = self._lib.ah_scan(self.h, set_id, _ptr(ids), len(ids), _ptr(out), cap, ctypes.byref(n), _stream(stream))
+        self._check(st, n.value)
+        return n.value
+
+    def ah_tm(self, set_id: int, pair_ids, sites, n: int, tm_out, pass_out=None, stream=None):
+        ids = np.ascontiguousarray(pair_ids, dtype=np.uint32)
+        self._check(self._lib.ah_tm(self.h, set_id, _ptr(ids), len(ids), _ptr(sites), n, _ptr(tm_out),
+                                    _ptr(pass_out), _stream(stream)))
+
+    def ah_pair(self, set_id: int, pair_ids, sites, passed, n: int, out, cap: int, stream=None) -> int:
+        ids = np.ascontiguousarray(pair_ids, dtype=np.uint32)
+        m = ctypes.c_uint64()
+        st = self._lib.ah_pair(self.h, set_id, _ptr(ids), len(ids), _ptr(sites), _ptr(passed), n, _ptr(out), cap,
+                               ctypes.byref(m), _stream(stream))
+        self._check(st, m.value)
+        return m.value
+
+    def ah_fetch(self, set_id: int, amplicons, n: int, seq_out, cap: int, offsets_out, stream=None):
+        self._check(self._lib.ah_fetch(self.h, set_id, _ptr(amplicons), n, _ptr(seq_out), cap, _ptr(offsets_out),
+                                       _stream(stream)))
+
+    # ------------------------------------------------ numpy conveniences (host buffers)
+    def load(self, seq: np.ndarray, contig_off, contig_genome, stream=None) -> int:
+        n = int(contig_off[-1])
+        return self.ah_load_genomes(seq, n, contig_off, contig_genome, stream)
+
+    def scan(self, set_id: int, pair_ids) -> np.ndarray:
+        """Sites as a numpy structured array (size query, then the call)."""
+        try:
+            n = self.ah_scan(set_id, pair_ids, None, 0)
+        except AHError as e:
+            if e.status != AH_ERR_OVERFLOW:
+                raise
+            n = e.needed
+        out = np.zeros(n, dtype=SITE_DTYPE)
+        if n:
+            m = self.ah_scan(set_id, pair_ids, out, n)
+            assert m == n
+        return out
+
+    def tm(self, set_id: int, pair_ids, sites: np.ndarray):
+        tm = np.zeros(len(sites), dtype=np.float32)
+        ps = np.zeros(len(sites), dtype=np.uint8)
+        self.ah_tm(set_id, pair_ids, np.ascontiguousarray(sites), len(sites), tm, ps)
+        return tm, ps
+
+    def pair(self, set_id: int, pair_ids, sites: np.ndarray, passed: np.ndarray | None = None) -> np.ndarray:
+        sites = np.ascontiguousarray(sites)
+        ids = np.ascontiguousarray(pair_ids, dtype=np.uint32)
+        m = ctypes.c_uint64()
+        st = self._lib.ah_pair(self.h, set_id, _ptr(ids), len(ids), _ptr(sites), _ptr(passed), len(sites), None, 0,
+                               ctypes.byref(m), None)
+        if st not in (AH_OK, AH_ERR_OVERFLOW):
+            self._check(st)
+        out = np.zeros(m.value, dtype=AMPLICON_DTYPE)
+        if m.value:
+            k = self.ah_pair(set_id, pair_ids, sites, passed, len(sites), out, m.value)
+            assert k == m.value
+        return out
+
+    def fetch(self, set_id: int, amplicons: np.ndarray):
+        amplicons = np.ascontiguousarray(amplicons)
+        offs = np.zeros(len(amplicons) + 1, dtype=np.uint64)
+        st = self._lib.ah_fetch(self.h, set_id, _ptr(amplicons), len(amplicons), None, 0, _ptr(offs), None)
+        if st not in (AH_OK, AH_ERR_OVERFLOW):
+            self._check(st)
+        total = int(offs[-1])
+        out = np.zeros(max(total, 1), dtype=np.uint8)
+        self.ah_fetch(set_id, amplicons, len(amplicons), out, total, offs)
+        return out[:total].tobytes(), offs
+
+
+def debug_compile_scan(fwd: str, rev: str, k: int, R: int = 4, arith_pct: int = 0, order: int = 0):
+    """Generate and NVRTC-compile the scan kernel of one pair (no GPU needed).
+    Returns (ok, log) where the log holds the ptxas register report."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    rc = lib().ah_debug_compile_scan(fwd.encode(), rev.encode(), k, R, arith_pct, order, buf, len(buf))
+    return rc == 0, buf.value.decode(errors="replace")

@@ -1,0 +1,704 @@
+// C ABI of the in-silico PCR hot path: context, genome pool, primer
+// registry, pointer staging and the call sequences of ah_scan / ah_tm /
+// ah_pair / ah_fetch.  All arithmetic runs in the kernels of this library.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "ah_internal.h"
+
+using namespace ah;
+
+struct ah_ctx {
+    int device = 0;
+    int sms = 0;
+    size_t budget = 0; // 0 = unlimited
+    size_t used = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::map<uint32_t, std::unique_ptr<GenomeSet>> sets;
+    uint32_t next_set = 1;
+    std::map<uint32_t, PrimerPair> pairs;
+    uint32_t next_pair = 1;
+    std::map<std::string, Scratch> scratch;
+    int *d_err = nullptr;
+    uint64_t *d_counter = nullptr;
+    ScanTuning tuning;
+    uint64_t key_cap = 1 << 20;
+};
+
+namespace {
+
+std::mutex g_create_mu;
+std::string g_create_err;
+
+template <class F> ah_status guarded(ah_ctx *ctx, F &&f)
+{
+    try {
+        if (ctx)
+            AH_CUDA(cudaSetDevice(ctx->device));
+        f();
+        return AH_OK;
+    } catch (const Error &e) {
+        if (ctx)
+            ctx->err = e.msg;
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        if (ctx)
+            ctx->err = "host allocation failed";
+        return AH_ERR_OOM;
+    } catch (const std::exception &e) {
+        if (ctx)
+            ctx->err = e.what();
+        return AH_ERR_ARG;
+    }
+}
+
+void require(bool cond, ah_status st, const std::string &msg)
+{
+    if (!cond)
+        throw Error(st, msg);
+}
+
+void *dev_alloc(ah_ctx *c, size_t bytes)
+{
+    if (bytes == 0)
+        bytes = 16;
+    if (c->budget && c->used + bytes > c->budget)
+        throw Error(AH_ERR_BUDGET, "device-memory budget exceeded: need " + std::to_string(bytes) + " more bytes, " +
+                                       std::to_string(c->budget - c->used) + " left");
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(AH_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    c->used += bytes;
+    return p;
+}
+
+void dev_free(ah_ctx *c, void *p, size_t bytes)
+{
+    if (!p)
+        return;
+    cudaFree(p);
+    if (bytes == 0)
+        bytes = 16;
+    c->used -= std::min(c->used, bytes);
+}
+
+void *scratch(ah_ctx *c, const std::string &name, size_t bytes)
+{
+    Scratch &s = c->scratch[name];
+    if (s.bytes >= bytes && s.p)
+        return s.p;
+    if (s.p) {
+        AH_CUDA(cudaStreamSynchronize(c->stream));
+        dev_free(c, s.p, s.bytes);
+        s.p = nullptr;
+        s.bytes = 0;
+    }
+    size_t want = std::max<size_t>(bytes + bytes / 4, 4096);
+    s.p = dev_alloc(c, want);
+    s.bytes = want;
+    return s.p;
+}
+
+bool is_device_ptr(ah_ctx *c, const void *p)
+{
+    if (!p)
+        return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        if (a.type == cudaMemoryTypeDevice && a.device != c->device)
+            throw Error(AH_ERR_ARG, "device pointer belongs to another GPU");
+        return true;
+    }
+    return false;
+}
+
+cudaStream_t stream_of(ah_ctx *c, void *s) { return s ? (cudaStream_t)s : c->stream; }
+
+template <class T> const T *stage_in(ah_ctx *c, const char *name, const T *p, uint64_t count, cudaStream_t st)
+{
+    if (is_device_ptr(c, p) || count == 0)
+        return p;
+    T *d = (T *)scratch(c, name, count * sizeof(T));
+    AH_CUDA(cudaMemcpyAsync(d, p, count * sizeof(T), cudaMemcpyHostToDevice, st));
+    return d;
+}
+
+template <class T> T *out_buf(ah_ctx *c, const char *name, T *p, uint64_t count)
+{
+    if (count == 0 || is_device_ptr(c, p))
+        return p;
+    return (T *)scratch(c, name, count * sizeof(T));
+}
+
+template <class T> void out_finish(T *user, T *dev, uint64_t count, cudaStream_t st)
+{
+    if (count && user != dev)
+        AH_CUDA(cudaMemcpyAsync(user, dev, count * sizeof(T), cudaMemcpyDeviceToHost, st));
+}
+
+void reset_flags(ah_ctx *c, cudaStream_t st)
+{
+    AH_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    AH_CUDA(cudaMemsetAsync(c->d_counter, 0, sizeof(uint64_t), st));
+}
+
+void check_flags(ah_ctx *c, cudaStream_t st)
+{
+    int e = 0;
+    AH_CUDA(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    AH_CUDA(cudaStreamSynchronize(st));
+    if (e == kDevTimeout)
+        throw Error(AH_ERR_TIMEOUT, "a device-side wait ran out of iterations");
+    if (e == kDevBounds)
+        throw Error(AH_ERR_ARG, "input record out of range (pair, contig or position)");
+    if (e != 0)
+        throw Error(AH_ERR_DEVICE_CHECK, "device consistency check failed (code " + std::to_string(e) + ")");
+}
+
+GenomeSet &get_set(ah_ctx *c, uint32_t id)
+{
+    auto it = c->sets.find(id);
+    require(it != c->sets.end(), AH_ERR_ARG, "unknown genome set id " + std::to_string(id));
+    return *it->second;
+}
+
+PrimerPair &get_pair(ah_ctx *c, uint32_t id)
+{
+    auto it = c->pairs.find(id);
+    require(it != c->pairs.end(), AH_ERR_ARG, "unknown primer pair id " + std::to_string(id));
+    return it->second;
+}
+
+} // namespace
+
+// IUPAC letter -> 4-bit base set (A=1 C=2 G=4 T=8); 0 for anything else.
+int ah::iupac_mask(char ch)
+{
+    switch (ch >= 'a' && ch <= 'z' ? ch - 32 : ch) {
+    case 'A': return 1;
+    case 'C': return 2;
+    case 'G': return 4;
+    case 'T': return 8;
+    case 'R': return 1 | 4;
+    case 'Y': return 2 | 8;
+    case 'S': return 2 | 4;
+    case 'W': return 1 | 8;
+    case 'K': return 4 | 8;
+    case 'M': return 1 | 2;
+    case 'B': return 2 | 4 | 8;
+    case 'D': return 1 | 4 | 8;
+    case 'H': return 1 | 2 | 8;
+    case 'V': return 1 | 2 | 4;
+    case 'N': return 15;
+    default: return 0;
+    }
+}
+
+// complement of a base set: A<->T, C<->G
+int ah::comp_mask(int m) { return ((m & 1) << 3) | ((m & 8) >> 3) | ((m & 2) << 1) | ((m & 4) >> 1); }
+
+namespace {
+
+// Default NN table: SantaLucia (1998) unified Watson-Crick parameters, here
+// indexed by the top-strand dinucleotide (each has exactly one Watson-Crick
+// stack), and terminal initiation by the class of the primer base.
+void default_table(ah_nn_table *t)
+{
+    static const double dH[4][4] = {{-7.9, -8.4, -7.8, -7.2},
+                                    {-8.5, -8.0, -10.6, -7.8},
+                                    {-8.2, -9.8, -8.0, -8.4},
+                                    {-7.2, -8.2, -8.5, -7.9}};
+    static const double dS[4][4] = {{-22.2, -22.4, -21.0, -20.4},
+                                    {-22.7, -19.9, -27.2, -21.0},
+                                    {-22.2, -24.4, -19.9, -22.4},
+                                    {-21.3, -22.2, -22.7, -22.2}};
+    memset(t, 0, sizeof(*t));
+    for (int x = 0; x < 4; ++x)
+        for (int y = 0; y < 4; ++y) {
+            const int idx = ((x * 4 + y) * 4 + (3 - x)) * 4 + (3 - y);
+            t->stack_dH[idx] = dH[x][y];
+            t->stack_dS[idx] = dS[x][y];
+        }
+    for (int p = 0; p < 4; ++p)
+        for (int q = 0; q < 4; ++q) {
+            const bool gc = (p == 1 || p == 2);
+            t->term_dH[p * 4 + q] = gc ? 0.1 : 2.3;
+            t->term_dS[p * 4 + q] = gc ? -2.8 : 4.1;
+        }
+}
+
+double na_eq_mM(const ah_pcr_params &p)
+{
+    double mon = p.Na_mM + p.K_mM + p.Tris_mM / 2.0;
+    if (p.Mg_mM > p.dNTPs_mM)
+        mon += 120.0 * std::sqrt(p.Mg_mM - p.dNTPs_mM);
+    return mon;
+}
+
+PairDev make_pair_dev(const PrimerPair &pp)
+{
+    PairDev d;
+    memset(&d, 0, sizeof(d));
+    d.L[0] = pp.L[0];
+    d.L[1] = pp.L[1];
+    d.min_len = pp.params.min_len;
+    d.max_len = pp.params.max_len;
+    memcpy(d.mask, pp.mask, sizeof(d.mask));
+    d.tm_min = pp.params.tm_min;
+    d.tm_min_f = (float)pp.params.tm_min;
+    const double x = (pp.params.dnac1_nM - pp.params.dnac2_nM / 2.0) * 1e-9;
+    d.sconst = 1.987 * std::log(x);
+    const double na = na_eq_mM(pp.params) / 1000.0;
+    d.salt_dS_per_stack = 0.0;
+    d.tm_shift = 0.0;
+    switch (pp.params.saltcorr) {
+    case 1: d.tm_shift = 16.6 * std::log10(na); break;
+    case 2: d.tm_shift = 16.6 * std::log10(na / (1.0 + 0.7 * na)) + 3.85; break;
+    case 3: d.tm_shift = 12.5 * std::log10(na); break;
+    case 4: d.tm_shift = 11.7 * std::log10(na); break;
+    case 5: d.salt_dS_per_stack = 0.368 * std::log(na); break;
+    default: break;
+    }
+    for (int i = 0; i < 256; ++i) {
+        d.stack_dH[i] = (float)pp.table.stack_dH[i];
+        d.stack_dS[i] = (float)pp.table.stack_dS[i];
+        d.stack_dH_d[i] = pp.table.stack_dH[i];
+        d.stack_dS_d[i] = pp.table.stack_dS[i];
+    }
+    for (int i = 0; i < 16; ++i) {
+        d.term_dH[i] = (float)pp.table.term_dH[i];
+        d.term_dS[i] = (float)pp.table.term_dS[i];
+        d.term_dH_d[i] = pp.table.term_dH[i];
+        d.term_dS_d[i] = pp.table.term_dS[i];
+    }
+    return d;
+}
+
+const PairDev *upload_pairs(ah_ctx *c, const uint32_t *pair_ids, uint32_t n_pairs, cudaStream_t st)
+{
+    require(pair_ids != nullptr, AH_ERR_ARG, "pair_ids is null");
+    require(n_pairs >= 1 && n_pairs <= AH_MAX_PAIRS_PER_SCAN, AH_ERR_ARG, "n_pairs must be 1..16");
+    std::vector<PairDev> h(n_pairs);
+    for (uint32_t j = 0; j < n_pairs; ++j)
+        h[j] = make_pair_dev(get_pair(c, pair_ids[j]));
+    PairDev *d = (PairDev *)scratch(c, "pairdev", n_pairs * sizeof(PairDev));
+    AH_CUDA(cudaMemcpyAsync(d, h.data(), n_pairs * sizeof(PairDev), cudaMemcpyHostToDevice, st));
+    // the host copy must outlive the async copy
+    AH_CUDA(cudaStreamSynchronize(st));
+    return d;
+}
+
+int bit_length(uint64_t v)
+{
+    int b = 0;
+    while (v) {
+        ++b;
+        v >>= 1;
+    }
+    return b;
+}
+
+std::vector<ScanPattern> patterns_of(ah_ctx *c, const uint32_t *pair_ids, uint32_t n_pairs)
+{
+    std::vector<ScanPattern> pats;
+    for (uint32_t j = 0; j < n_pairs; ++j) {
+        const PrimerPair &pp = get_pair(c, pair_ids[j]);
+        for (int primer = 0; primer < 2; ++primer)
+            for (int strand = 0; strand < 2; ++strand) {
+                ScanPattern p;
+                p.L = pp.L[primer];
+                p.k = pp.params.k;
+                p.clamp = std::min(pp.params.clamp, p.L);
+                p.pair = (int)j;
+                p.primer = primer;
+                p.strand = strand;
+                for (int i = 0; i < p.L; ++i)
+                    p.mask[i] = strand == 0 ? pp.mask[primer][i] : (uint8_t)comp_mask(pp.mask[primer][p.L - 1 - i]);
+                pats.push_back(p);
+            }
+    }
+    return pats;
+}
+
+} // namespace
+
+// ===========================================================================
+extern "C" {
+
+ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
+{
+    std::lock_guard<std::mutex> lock(g_create_mu);
+    if (!out) {
+        g_create_err = "ah_create: out is null";
+        return AH_ERR_ARG;
+    }
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        g_create_err = "ah_create: no such CUDA device";
+        return AH_ERR_ARG;
+    }
+    ah_ctx *c = new (std::nothrow) ah_ctx;
+    if (!c) {
+        g_create_err = "ah_create: host allocation failed";
+        return AH_ERR_OOM;
+    }
+    c->device = device;
+    c->budget = mem_budget_bytes;
+    ah_status st = guarded(c, [&] {
+        AH_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device));
+        AH_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->d_err = (int *)dev_alloc(c, sizeof(int));
+        c->d_counter = (uint64_t *)dev_alloc(c, sizeof(uint64_t));
+    });
+    if (st != AH_OK) {
+        g_create_err = c->err;
+        ah_destroy(c);
+        return st;
+    }
+    *out = c;
+    return AH_OK;
+}
+
+void ah_destroy(ah_ctx *c)
+{
+    if (!c)
+        return;
+    cudaSetDevice(c->device);
+    if (c->stream)
+        cudaStreamSynchronize(c->stream);
+    for (auto &kv : c->sets) {
+        cudaFree(kv.second->planes);
+        cudaFree(kv.second->contig_off);
+        cudaFree(kv.second->contig_genome);
+    }
+    for (auto &kv : c->scratch)
+        cudaFree(kv.second.p);
+    cudaFree(c->d_err);
+    cudaFree(c->d_counter);
+    if (c->stream)
+        cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char *ah_last_error(const ah_ctx *c)
+{
+    if (!c)
+        return g_create_err.c_str();
+    return c->err.c_str();
+}
+
+size_t ah_device_bytes(const ah_ctx *c) { return c ? c->used : 0; }
+
+ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const uint64_t *contig_off,
+                          uint32_t n_contigs, const uint32_t *contig_genome, uint32_t *set_id_out, void *stream)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require(set_id_out && contig_off && contig_genome && n_contigs >= 1, AH_ERR_ARG,
+                "ah_load_genomes: null argument or no contigs");
+        require(n_bases == 0 || seq, AH_ERR_ARG, "ah_load_genomes: seq is null");
+        require(n_bases < (1ull << 44), AH_ERR_ARG, "ah_load_genomes: more than 2^44 bases in one set");
+        require(contig_off[0] == 0 && contig_off[n_contigs] == n_bases, AH_ERR_ARG,
+                "ah_load_genomes: contig_off must start at 0 and end at n_bases");
+        for (uint32_t i = 0; i < n_contigs; ++i)
+            require(contig_off[i] <= contig_off[i + 1], AH_ERR_ARG, "ah_load_genomes: contig_off not monotone");
+        for (uint32_t i = 0; i < n_contigs; ++i)
+            require(contig_off[i + 1] - contig_off[i] < (1ull << 32), AH_ERR_ARG,
+                    "ah_load_genomes: contig longer than 2^32 - 1");
+        cudaStream_t st = stream_of(c, stream);
+        auto gs = std::make_unique<GenomeSet>();
+        gs->n_bases = n_bases;
+        gs->n_contigs = n_contigs;
+        gs->n_tiles = (n_bases + kTileBases - 1) / kTileBases;
+        gs->contig_off_h.assign(contig_off, contig_off + n_contigs + 1);
+        gs->contig_genome_h.assign(contig_genome, contig_genome + n_contigs);
+        const size_t plane_bytes = gs->n_tiles * kTileBytes;
+        try {
+            gs->planes = (uint32_t *)dev_alloc(c, plane_bytes);
+            gs->contig_off = (uint64_t *)dev_alloc(c, (n_contigs + 1) * sizeof(uint64_t));
+            gs->contig_genome = (uint32_t *)dev_alloc(c, n_contigs * sizeof(uint32_t));
+        } catch (...) {
+            dev_free(c, gs->planes, plane_bytes);
+            dev_free(c, gs->contig_off, (n_contigs + 1) * sizeof(uint64_t));
+            dev_free(c, gs->contig_genome, n_contigs * sizeof(uint32_t));
+            throw;
+        }
+        gs->bytes = plane_bytes + (n_contigs + 1) * sizeof(uint64_t) + n_contigs * sizeof(uint32_t);
+        AH_CUDA(cudaMemcpyAsync(gs->contig_off, gs->contig_off_h.data(), (n_contigs + 1) * sizeof(uint64_t),
+                                cudaMemcpyHostToDevice, st));
+        AH_CUDA(cudaMemcpyAsync(gs->contig_genome, gs->contig_genome_h.data(), n_contigs * sizeof(uint32_t),
+                                cudaMemcpyHostToDevice, st));
+        if (gs->n_tiles) {
+            if (is_device_ptr(c, seq)) {
+                launch_pack(seq, 0, n_bases, n_bases, gs->planes, 0, gs->n_tiles, st);
+            } else {
+                // host sequence: stream it through a staging buffer in tile-aligned chunks;
+                // each chunk also carries the first bytes of the next tile (extension words)
+                const uint64_t chunk_tiles = 4096; // 128 Mbp
+                const uint64_t stage_bytes = chunk_tiles * kTileBases + kTileBases;
+                uint8_t *stage = (uint8_t *)scratch(c, "load_stage", stage_bytes);
+                for (uint64_t t0 = 0; t0 < gs->n_tiles; t0 += chunk_tiles) {
+                    const uint64_t t1 = std::min(gs->n_tiles, t0 + chunk_tiles);
+                    const uint64_t b0 = t0 * kTileBases;
+                    const uint64_t b1 = std::min(n_bases, t1 * kTileBases + kTileBases);
+                    AH_CUDA(cudaMemcpyAsync(stage, seq + b0, b1 - b0, cudaMemcpyHostToDevice, st));
+                    launch_pack(stage, b0, b1 - b0, n_bases, gs->planes, t0, t1, st);
+                    AH_CUDA(cudaStreamSynchronize(st));
+                }
+            }
+        }
+        AH_CUDA(cudaStreamSynchronize(st));
+        uint32_t id = c->next_set++;
+        c->sets[id] = std::move(gs);
+        *set_id_out = id;
+    });
+}
+
+ah_status ah_unload_genomes(ah_ctx *c, uint32_t set_id)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        GenomeSet &gs = get_set(c, set_id);
+        AH_CUDA(cudaStreamSynchronize(c->stream));
+        dev_free(c, gs.planes, gs.n_tiles * kTileBytes);
+        dev_free(c, gs.contig_off, (gs.n_contigs + 1) * sizeof(uint64_t));
+        dev_free(c, gs.contig_genome, gs.n_contigs * sizeof(uint32_t));
+        c->sets.erase(set_id);
+    });
+}
+
+ah_status ah_set_primers(ah_ctx *c, const char *fwd, const char *rev, const ah_pcr_params *p, uint32_t *pair_id_out)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require(fwd && rev && p && pair_id_out, AH_ERR_ARG, "ah_set_primers: null argument");
+        PrimerPair pp;
+        const char *pr[2] = {fwd, rev};
+        for (int x = 0; x < 2; ++x) {
+            const size_t L = strlen(pr[x]);
+            require(L >= AH_MIN_PRIMER_LEN, AH_ERR_PRIMER, "primer shorter than 5 letters");
+            require(L <= AH_MAX_PRIMER_LEN, AH_ERR_PRIMER, "primer longer than 32 letters");
+            double deg = 1.0;
+            for (size_t i = 0; i < L; ++i) {
+                const int m = iupac_mask(pr[x][i]);
+                require(m != 0, AH_ERR_PRIMER, std::string("non-IUPAC letter in primer: '") + pr[x][i] + "'");
+                pp.mask[x][i] = (uint8_t)m;
+                deg *= (double)__builtin_popcount(m);
+            }
+            require(deg <= AH_MAX_DEGENERACY, AH_ERR_PRIMER, "primer degeneracy above 10000");
+            pp.L[x] = (int)L;
+        }
+        pp.fwd = fwd;
+        pp.rev = rev;
+        require(p->k >= 0 && p->k <= AH_MAX_MISMATCHES, AH_ERR_PRIMER, "k must be 0..10");
+        require(p->clamp >= 0, AH_ERR_ARG, "clamp must be >= 0");
+        require(p->min_len >= 0 && p->min_len <= p->max_len, AH_ERR_ARG, "need 0 <= min_len <= max_len");
+        require(p->saltcorr >= 0 && p->saltcorr <= 5, AH_ERR_ARG, "saltcorr must be 0..5");
+        require(!std::isnan(p->tm_min) && p->tm_min < INFINITY, AH_ERR_ARG, "tm_min must be a number or -inf");
+        const double vals[] = {p->dnac1_nM, p->dnac2_nM, p->Na_mM, p->K_mM, p->Tris_mM, p->Mg_mM, p->dNTPs_mM};
+        for (double v : vals)
+            require(std::isfinite(v) && v >= 0, AH_ERR_ARG, "concentrations must be finite and >= 0");
+        require(p->dnac1_nM - p->dnac2_nM / 2.0 > 0, AH_ERR_ARG, "need dnac1 > dnac2 / 2");
+        require(p->saltcorr == 0 || na_eq_mM(*p) > 0, AH_ERR_ARG, "salt correction needs [Na_eq] > 0");
+        pp.params = *p;
+        default_table(&pp.table);
+        uint32_t id = c->next_pair++;
+        c->pairs[id] = pp;
+        *pair_id_out = id;
+    });
+}
+
+ah_status ah_set_nn_table(ah_ctx *c, uint32_t pair_id, const ah_nn_table *t)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        PrimerPair &pp = get_pair(c, pair_id);
+        if (!t) {
+            default_table(&pp.table);
+            return;
+        }
+        for (int i = 0; i < 256; ++i)
+            require(std::isfinite(t->stack_dH[i]) && std::isfinite(t->stack_dS[i]), AH_ERR_ARG, "non-finite entry");
+        for (int i = 0; i < 16; ++i)
+            require(std::isfinite(t->term_dH[i]) && std::isfinite(t->term_dS[i]), AH_ERR_ARG, "non-finite entry");
+        pp.table = *t;
+    });
+}
+
+ah_status ah_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, ah_site *out,
+                  uint64_t cap, uint64_t *n_out, void *stream)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require(n_out != nullptr && (cap == 0 || out != nullptr), AH_ERR_ARG, "ah_scan: null output");
+        require(pair_ids && n_pairs >= 1 && n_pairs <= AH_MAX_PAIRS_PER_SCAN, AH_ERR_ARG, "n_pairs must be 1..16");
+        *n_out = 0;
+        GenomeSet &gs = get_set(c, set_id);
+        cudaStream_t st = stream_of(c, stream);
+        std::vector<ScanPattern> pats = patterns_of(c, pair_ids, n_pairs);
+        const int pbits = std::max(1, bit_length(gs.n_bases));
+        uint64_t count = 0;
+        uint64_t *keys = nullptr;
+        if (gs.n_tiles) {
+            ScanKernel *k = scan_kernel(pats, c->tuning, c->device);
+            for (int attempt = 0; attempt < 2; ++attempt) {
+                keys = (uint64_t *)scratch(c, "scan_keys", c->key_cap * sizeof(uint64_t));
+                reset_flags(c, st);
+                const uint64_t grid = std::min<uint64_t>(gs.n_tiles, (uint64_t)c->sms * k->blocks_per_sm);
+                const uint32_t *planes = gs.planes;
+                uint64_t n_tiles = gs.n_tiles;
+                const uint64_t *coff = gs.contig_off;
+                uint32_t nc = gs.n_contigs;
+                uint64_t kc = c->key_cap;
+                int pb = pbits;
+                void *args[] = {&planes, &n_tiles, &coff, &nc, &keys, &kc, &c->d_counter, &pb, &c->d_err};
+                AH_CUDA(cudaLaunchKernel((const void *)k->fn, dim3((unsigned)grid), dim3(k->threads), args, k->smem, st));
+                AH_CUDA(cudaMemcpyAsync(&count, c->d_counter, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+                check_flags(c, st);
+                if (count <= c->key_cap)
+                    break;
+                c->key_cap = count;
+            }
+        }
+        *n_out = count;
+        if (count > cap)
+            throw Error(AH_ERR_OVERFLOW, "ah_scan: " + std::to_string(count) + " sites, capacity " +
+                                             std::to_string(cap));
+        if (count == 0)
+            return;
+        const int end_bit = 10 + pbits + bit_length(n_pairs - 1);
+        size_t tb = sort_keys_temp_bytes(count, end_bit);
+        void *temp = scratch(c, "sort_temp", tb);
+        uint64_t *sorted = (uint64_t *)scratch(c, "scan_keys_sorted", count * sizeof(uint64_t));
+        sort_keys(temp, tb, keys, sorted, count, 8, end_bit, st);
+        ah_site *dst = out_buf(c, "sites_out", out, count);
+        launch_decode_keys(sorted, count, pbits, gs.contig_off, gs.n_contigs, gs.contig_genome, dst, st);
+        out_finish(out, dst, count, st);
+        AH_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, const ah_site *sites,
+                uint64_t n, float *tm_out, uint8_t *pass_out, void *stream)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require(n == 0 || (sites && tm_out), AH_ERR_ARG, "ah_tm: null argument");
+        GenomeSet &gs = get_set(c, set_id);
+        cudaStream_t st = stream_of(c, stream);
+        const PairDev *pd = upload_pairs(c, pair_ids, n_pairs, st);
+        if (n == 0)
+            return;
+        reset_flags(c, st);
+        const ah_site *s = stage_in(c, "tm_sites_in", sites, n, st);
+        launch_validate_sites(s, n, pd, (int)n_pairs, gs.contig_off, gs.n_contigs, c->d_err, st);
+        check_flags(c, st);
+        float *tm = out_buf(c, "tm_out", tm_out, n);
+        uint8_t *ps = pass_out ? out_buf(c, "pass_out", pass_out, n) : nullptr;
+        launch_tm(s, n, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, ps, c->d_err, st);
+        out_finish(tm_out, tm, n, st);
+        if (pass_out)
+            out_finish(pass_out, ps, n, st);
+        check_flags(c, st);
+    });
+}
+
+ah_status ah_pair(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, const ah_site *sites,
+                  const uint8_t *pass, uint64_t n, ah_amplicon *out, uint64_t cap, uint64_t *n_out, void *stream)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require(n_out && (cap == 0 || out) && (n == 0 || sites), AH_ERR_ARG, "ah_pair: null argument");
+        *n_out = 0;
+        GenomeSet &gs = get_set(c, set_id);
+        cudaStream_t st = stream_of(c, stream);
+        const PairDev *pd = upload_pairs(c, pair_ids, n_pairs, st);
+        if (n == 0)
+            return;
+        reset_flags(c, st);
+        const ah_site *s = stage_in(c, "pair_sites_in", sites, n, st);
+        const uint8_t *ps = pass ? stage_in(c, "pair_pass_in", pass, n, st) : nullptr;
+        launch_validate_sites(s, n, pd, (int)n_pairs, gs.contig_off, gs.n_contigs, c->d_err, st);
+        check_flags(c, st);
+        uint64_t *counts = (uint64_t *)scratch(c, "pair_counts", n * sizeof(uint64_t));
+        uint64_t *offs = (uint64_t *)scratch(c, "pair_offsets", n * sizeof(uint64_t));
+        launch_pair_count(s, n, ps, pd, counts, st);
+        size_t tb = scan_u64_temp_bytes(n);
+        void *temp = scratch(c, "scan_temp", tb);
+        exclusive_scan_u64(temp, tb, counts, offs, n, st);
+        uint64_t last[2] = {0, 0};
+        AH_CUDA(cudaMemcpyAsync(&last[0], offs + n - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        AH_CUDA(cudaMemcpyAsync(&last[1], counts + n - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        AH_CUDA(cudaStreamSynchronize(st));
+        const uint64_t total = last[0] + last[1];
+        *n_out = total;
+        if (total > cap)
+            throw Error(AH_ERR_OVERFLOW, "ah_pair: " + std::to_string(total) + " amplicons, capacity " +
+                                             std::to_string(cap));
+        if (total == 0)
+            return;
+        ah_amplicon *dst = out_buf(c, "amp_out", out, total);
+        launch_pair_write(s, n, ps, pd, offs, dst, total, st);
+        out_finish(out, dst, total, st);
+        AH_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+ah_status ah_fetch(ah_ctx *c, uint32_t set_id, const ah_amplicon *amplicons, uint64_t n, char *seq_out,
+                   uint64_t cap, uint64_t *offsets_out, void *stream)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require(offsets_out && (n == 0 || amplicons) && (cap == 0 || seq_out), AH_ERR_ARG, "ah_fetch: null argument");
+        GenomeSet &gs = get_set(c, set_id);
+        cudaStream_t st = stream_of(c, stream);
+        reset_flags(c, st);
+        const ah_amplicon *a = stage_in(c, "fetch_in", amplicons, n, st);
+        uint64_t *len = (uint64_t *)scratch(c, "fetch_len", (n + 1) * sizeof(uint64_t));
+        uint64_t *offs = out_buf(c, "fetch_offsets", offsets_out, n + 1);
+        AH_CUDA(cudaMemsetAsync(len + n, 0, sizeof(uint64_t), st));
+        launch_fetch_lengths(a, n, gs.contig_off, gs.n_contigs, len, c->d_err, st);
+        check_flags(c, st);
+        size_t tb = scan_u64_temp_bytes(n + 1);
+        void *temp = scratch(c, "scan_temp", tb);
+        exclusive_scan_u64(temp, tb, len, offs, n + 1, st);
+        uint64_t total = 0;
+        AH_CUDA(cudaMemcpyAsync(&total, offs + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        out_finish(offsets_out, offs, n + 1, st);
+        AH_CUDA(cudaStreamSynchronize(st));
+        if (total > cap)
+            throw Error(AH_ERR_OVERFLOW, "ah_fetch: " + std::to_string(total) + " bytes needed, capacity " +
+                                             std::to_string(cap));
+        if (total == 0)
+            return;
+        char *dst = out_buf(c, "fetch_out", seq_out, total);
+        launch_fetch(a, n, offs, gs.planes, gs.contig_off, dst, st);
+        out_finish(seq_out, dst, total, st);
+        AH_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+} // extern "C"

@@ -1,0 +1,187 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/ampliconhunter.h"
+
+namespace ah {
+
+// ---------------------------------------------------------------------------
+// Packed genome layout in HBM ("tile-strided one-hot bitplanes").
+//
+// The flat position space is the concatenation of all contigs of a set.  It
+// is cut into tiles of kTileBases = 32 * kTileW positions.  Tile t stores, for
+// each base plane x in {A, C, G, T}, kTileWX 32-bit words; bit b of word j of
+// plane x is 1 iff the base at flat position
+//     t * kTileBases + b * kTileW + j
+// is x (upper or lower case).  For j >= kTileW the formula reaches into the
+// next tile: these kTileExt "extension" words let a thread read the window
+// of positions p .. p + L - 1 for every start p of its own words as plain
+// word offsets j .. j + L - 1, with no funnel shifts (L <= 32).  A non-ACGT
+// letter, and every position at or past the end of the set, has all four
+// planes 0.  Layout: planes[(t * 4 + x) * kTileWX + j], 0.516 bytes per base.
+// ---------------------------------------------------------------------------
+constexpr int kTileW = 1024;
+constexpr int kTileExt = 32;
+constexpr int kTileWX = kTileW + kTileExt;
+constexpr uint64_t kTileBases = 32ull * kTileW;
+constexpr size_t kTileBytes = 4ull * kTileWX * sizeof(uint32_t);
+
+struct GenomeSet {
+    uint64_t n_bases = 0;
+    uint32_t n_contigs = 0;
+    uint64_t n_tiles = 0;
+    uint32_t *planes = nullptr;        // device, n_tiles * kTileBytes
+    uint64_t *contig_off = nullptr;    // device, n_contigs + 1
+    uint32_t *contig_genome = nullptr; // device, n_contigs
+    std::vector<uint64_t> contig_off_h;
+    std::vector<uint32_t> contig_genome_h;
+    size_t bytes = 0;
+};
+
+// One registered primer pair.  mask[i] is the 4-bit IUPAC set of primer
+// position i (A=1 C=2 G=4 T=8), 5'->3'.
+struct PrimerPair {
+    std::string fwd, rev;
+    int L[2] = {0, 0};
+    uint8_t mask[2][AH_MAX_PRIMER_LEN] = {};
+    ah_pcr_params params{};
+    ah_nn_table table{};
+};
+
+// One scan pattern: the primer (strand '+') or its reverse complement
+// (strand '-') as matched against the + strand.
+struct ScanPattern {
+    int L = 0;
+    int k = 0;
+    int clamp = 0;
+    int pair = 0;   // index in the ah_scan call's pair list
+    int primer = 0; // 0 forward, 1 reverse
+    int strand = 0; // 0 '+', 1 '-'
+    uint8_t mask[AH_MAX_PRIMER_LEN] = {};
+};
+
+// Tunables of the generated scan kernel (autotuned per pattern set).
+struct ScanTuning {
+    int R = 4;            // words per thread (4 or 8); threads per block = kTileW / R
+    int arith_pct = 0;    // share of full adders that form the sum with integer adds
+    int min_blocks = 1;   // __launch_bounds__ minimum blocks per SM
+    int order = 0;        // 0: word-major, 1: pattern-major code order
+    bool operator<(const ScanTuning &o) const
+    {
+        if (R != o.R) return R < o.R;
+        if (arith_pct != o.arith_pct) return arith_pct < o.arith_pct;
+        if (min_blocks != o.min_blocks) return min_blocks < o.min_blocks;
+        return order < o.order;
+    }
+};
+
+struct ScanKernel {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t fn = nullptr;
+    int threads = 0;
+    int blocks_per_sm = 0;
+    size_t smem = 0;
+    int regs = -1;
+    std::string log;
+};
+
+class Error : public std::exception {
+  public:
+    Error(ah_status s, std::string m) : status(s), msg(std::move(m)) {}
+    const char *what() const noexcept override { return msg.c_str(); }
+    ah_status status;
+    std::string msg;
+};
+
+#define AH_CUDA(call)                                                                                    \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess)                                                                           \
+            throw ::ah::Error(AH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));          \
+    } while (0)
+
+// Scratch buffer that grows on demand inside the context's budget.
+struct Scratch {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Device error word layout (written by kernels, read by the host).
+enum DeviceErr : int { kDevOk = 0, kDevTimeout = 1, kDevBounds = 2, kDevCheck = 3 };
+
+// IUPAC letter -> 4-bit base set (A=1 C=2 G=4 T=8), 0 if not a code; and the
+// complement of a base set (A<->T, C<->G).  Defined in ah_api.cu.
+int iupac_mask(char ch);
+int comp_mask(int m);
+
+// ---- generated scan kernel (scan_jit.cu) ----
+// Compile (no load) the scan kernel of one pair; for CPU-side checks of the
+// generator.  Returns the NVRTC log (ptxas register report included).
+std::string scan_compile_only(const std::vector<ScanPattern> &pats, const ScanTuning &t, bool *ok);
+std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &t);
+ScanKernel *scan_kernel(const std::vector<ScanPattern> &pats, const ScanTuning &t, int device);
+
+// ---- kernel launchers ----
+// pack.cu: pack tiles [t0, t1) from seq, which holds flat positions
+// [seq_base, seq_base + seq_len) of a set of n_bases bases.
+void launch_pack(const uint8_t *seq, uint64_t seq_base, uint64_t seq_len, uint64_t n_bases, uint32_t *planes,
+                 uint64_t t0, uint64_t t1, cudaStream_t s);
+void launch_unpack_check(const uint32_t *planes, uint64_t n_tiles, uint8_t *codes, uint64_t n_bases,
+                         cudaStream_t s);
+
+// sites.cu
+size_t sort_keys_temp_bytes(uint64_t n, int end_bit);
+void sort_keys(void *temp, size_t temp_bytes, const uint64_t *in, uint64_t *out, uint64_t n, int begin_bit,
+               int end_bit, cudaStream_t s);
+void launch_decode_keys(const uint64_t *keys, uint64_t n, int pbits, const uint64_t *contig_off, uint32_t n_contigs,
+                        const uint32_t *contig_genome, ah_site *out, cudaStream_t s);
+
+struct PairDev;
+// Check user-supplied sites before any kernel indexes memory with them:
+// pair < n_pairs, primer and strand in {0, 1}, contig < n_contigs, and the
+// window inside its contig.  Sets *err = kDevBounds on a bad record.
+void launch_validate_sites(const ah_site *sites, uint64_t n, const PairDev *pairs_d, int n_pairs,
+                           const uint64_t *contig_off, uint32_t n_contigs, int *err, cudaStream_t s);
+
+// Per-pair constants for the Tm and pair kernels.
+struct PairDev {
+    int L[2];
+    int min_len, max_len;
+    uint8_t mask[2][AH_MAX_PRIMER_LEN];
+    float tm_min_f;
+    double tm_min;
+    double sconst;      // R ln(x) [+ salt entropy slope handled per L]
+    double salt_dS_per_stack; // 0.368 ln[Na_eq] for method 5, else 0
+    double tm_shift;    // methods 1-4
+    float stack_dH[256], stack_dS[256], term_dH[16], term_dS[16];
+    double stack_dH_d[256], stack_dS_d[256], term_dH_d[16], term_dS_d[16];
+};
+
+// tm.cu
+void launch_tm(const ah_site *sites, uint64_t n, const PairDev *pairs_d, int n_pairs, const uint32_t *planes,
+               const uint64_t *contig_off, float *tm_out, uint8_t *pass_out, int *err, cudaStream_t s);
+
+// pair.cu
+void launch_pair_count(const ah_site *sites, uint64_t n, const uint8_t *pass, const PairDev *pairs_d,
+                       uint64_t *counts, cudaStream_t s);
+size_t scan_u64_temp_bytes(uint64_t n);
+void exclusive_scan_u64(void *temp, size_t temp_bytes, const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s);
+void launch_pair_write(const ah_site *sites, uint64_t n, const uint8_t *pass, const PairDev *pairs_d,
+                       const uint64_t *offsets, ah_amplicon *out, uint64_t cap, cudaStream_t s);
+
+// fetch.cu
+// lengths of the amplicons; a record outside its contig sets *err = kDevBounds (length 0)
+void launch_fetch_lengths(const ah_amplicon *a, uint64_t n, const uint64_t *contig_off, uint32_t n_contigs,
+                          uint64_t *len, int *err, cudaStream_t s);
+void launch_fetch(const ah_amplicon *a, uint64_t n, const uint64_t *offsets, const uint32_t *planes,
+                  const uint64_t *contig_off, char *out, cudaStream_t s);
+
+} // namespace ah

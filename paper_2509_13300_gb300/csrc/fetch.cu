@@ -1,0 +1,81 @@
+// Amplicon sequences (Sec. 2.1, Visualization: the main output is a FASTA of
+// amplicon sequences).  Decoded from the packed planes: upper case, 'N' for
+// any position with no base plane set; RF amplicons reverse-complemented so
+// they read from the forward primer.  One warp per amplicon.
+#include "ah_internal.h"
+
+namespace ah {
+namespace {
+
+__global__ void fetch_len_kernel(const ah_amplicon *__restrict__ a, uint64_t n, const uint64_t *__restrict__ contig_off,
+                                 uint32_t n_contigs, uint64_t *__restrict__ len, int *__restrict__ err)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const ah_amplicon am = a[i];
+        bool ok = am.contig < n_contigs && am.start <= am.end;
+        if (ok)
+            ok = (uint64_t)am.end <= contig_off[am.contig + 1] - contig_off[am.contig];
+        if (!ok)
+            atomicExch(err, kDevBounds);
+        len[i] = ok ? (uint64_t)(am.end - am.start) : 0;
+    }
+}
+
+__global__ void fetch_kernel(const ah_amplicon *__restrict__ a, uint64_t n, const uint64_t *__restrict__ offsets,
+                             const uint32_t *__restrict__ planes, const uint64_t *__restrict__ contig_off,
+                             char *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const ah_amplicon am = a[i];
+        const uint64_t len = offsets[i + 1] - offsets[i];
+        if (len == 0)
+            continue;
+        const uint64_t base = contig_off[am.contig] + am.start;
+        const bool rc = am.orient == 1;
+        char *o = out + offsets[i];
+        for (uint64_t q = lane; q < len; q += 32) {
+            const uint64_t P = base + (rc ? len - 1 - q : q);
+            const uint64_t t = P / kTileBases, r = P % kTileBases;
+            const int b = (int)(r / kTileW), j = (int)(r % kTileW);
+            const uint32_t *w = planes + t * 4 * kTileWX + j;
+            int code = -1;
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+                if ((__ldg(w + x * kTileWX) >> b) & 1u)
+                    code = x;
+            if (code >= 0 && rc)
+                code = 3 - code;
+            o[q] = code < 0 ? 'N' : "ACGT"[code];
+        }
+    }
+}
+
+} // namespace
+
+void launch_fetch_lengths(const ah_amplicon *a, uint64_t n, const uint64_t *contig_off, uint32_t n_contigs,
+                          uint64_t *len, int *err, cudaStream_t s)
+{
+    if (!n)
+        return;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > 8192)
+        blocks = 8192;
+    fetch_len_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, n, contig_off, n_contigs, len, err);
+    AH_CUDA(cudaGetLastError());
+}
+
+void launch_fetch(const ah_amplicon *a, uint64_t n, const uint64_t *offsets, const uint32_t *planes,
+                  const uint64_t *contig_off, char *out, cudaStream_t s)
+{
+    if (!n)
+        return;
+    uint64_t blocks = (n + 7) / 8;
+    if (blocks > 16384)
+        blocks = 16384;
+    fetch_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, n, offsets, planes, contig_off, out);
+    AH_CUDA(cudaGetLastError());
+}
+
+} // namespace ah

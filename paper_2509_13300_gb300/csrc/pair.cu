@@ -1,0 +1,234 @@
+// Amplicon calling (Sec. 2.1): pair '+' sites with '-' sites of the same pair
+// and contig inside the length window, labelled FR/RF/FF/RR (Sec. 2.1,
+// Amplicon analysis, item 1).
+//
+// Sites arrive in canonical order, so all sites at one (pair, contig, pos)
+// are adjacent (at most F+, F-, R+, R-).  One thread owns each "start group"
+// -- the '+' sites at one position (F+ and/or R+) -- and walks the sorted
+// sites after it whose position can close an amplicon: right sites t with
+// t >= s and t + L_Y - s in [min_len, max_len].  A count pass, an exclusive
+// scan and a write pass place every group's amplicons at fixed offsets; the
+// write pass merges the up-to-four (left primer, right primer) streams of its
+// group by (end, orient), each of which is already sorted by end, so the
+// output comes out in canonical order with no global sort.
+#include <cub/device/device_scan.cuh>
+
+#include "ah_internal.h"
+
+namespace ah {
+namespace {
+
+__device__ __forceinline__ bool same_group(const ah_site &a, const ah_site &b)
+{
+    return a.pair == b.pair && a.contig == b.contig && a.pos == b.pos;
+}
+
+// first index in [lo, n) whose (pair, contig, pos) >= (pair, contig, t)
+__device__ uint64_t lower_bound_pos(const ah_site *__restrict__ s, uint64_t lo, uint64_t n, uint32_t pair,
+                                    uint32_t contig, uint64_t t)
+{
+    uint64_t hi = n;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        const ah_site m = s[mid];
+        const bool less = (m.pair < pair) || (m.pair == pair && (m.contig < contig || (m.contig == contig && m.pos < t)));
+        if (less)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+struct Group {
+    int nl;          // number of passing left sites (0..2)
+    uint64_t li[2];  // their indices
+    int lx[2];       // their primers
+    uint64_t first;  // first candidate index
+    uint64_t tmax;   // last candidate position
+    bool valid;
+};
+
+__device__ Group make_group(const ah_site *__restrict__ s, uint64_t n, const uint8_t *__restrict__ pass,
+                            const PairDev *__restrict__ pairs, uint64_t a)
+{
+    Group g;
+    g.valid = false;
+    g.nl = 0;
+    const ah_site sa = s[a];
+    if (sa.strand != 0)
+        return g;
+    uint64_t g0 = a; // first site of this (pair, contig, pos) group
+    for (int d = 1; d <= 3 && (uint64_t)d <= a; ++d) {
+        const ah_site p = s[a - d];
+        if (!same_group(p, sa))
+            break;
+        if (p.strand == 0)
+            return g; // an earlier '+' site leads this group
+        g0 = a - d;
+    }
+    for (uint64_t b = a; b < n && b < a + 4 && same_group(s[b], sa); ++b) {
+        if (s[b].strand == 0 && (!pass || pass[b])) {
+            g.li[g.nl] = b;
+            g.lx[g.nl] = s[b].primer;
+            ++g.nl;
+        }
+    }
+    if (g.nl == 0)
+        return g;
+    const PairDev &pd = pairs[sa.pair];
+    const int Lmin = min(pd.L[0], pd.L[1]), Lmax = max(pd.L[0], pd.L[1]);
+    const int64_t lo = max((int64_t)0, (int64_t)pd.min_len - Lmax);
+    const int64_t hi = (int64_t)pd.max_len - Lmin;
+    if (hi < lo)
+        return g;
+    g.first = lower_bound_pos(s, g0, n, sa.pair, sa.contig, (uint64_t)sa.pos + (uint64_t)lo);
+    g.tmax = (uint64_t)sa.pos + (uint64_t)hi;
+    g.valid = true;
+    return g;
+}
+
+__device__ __forceinline__ bool in_window(const PairDev &pd, uint32_t s_pos, const ah_site &r, uint32_t *end)
+{
+    const int64_t e = (int64_t)r.pos + pd.L[r.primer];
+    const int64_t len = e - (int64_t)s_pos;
+    *end = (uint32_t)e;
+    return r.pos >= s_pos && len >= pd.min_len && len <= pd.max_len;
+}
+
+__global__ void pair_count_kernel(const ah_site *__restrict__ s, uint64_t n, const uint8_t *__restrict__ pass,
+                                  const PairDev *__restrict__ pairs, uint64_t *__restrict__ counts)
+{
+    for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t cnt = 0;
+        const Group g = make_group(s, n, pass, pairs, a);
+        if (g.valid) {
+            const ah_site sa = s[a];
+            const PairDev &pd = pairs[sa.pair];
+            for (uint64_t b = g.first; b < n; ++b) {
+                const ah_site r = s[b];
+                if (r.pair != sa.pair || r.contig != sa.contig || r.pos > g.tmax)
+                    break;
+                if (r.strand != 1 || (pass && !pass[b]))
+                    continue;
+                uint32_t end;
+                if (in_window(pd, sa.pos, r, &end))
+                    cnt += g.nl;
+            }
+        }
+        counts[a] = cnt;
+    }
+}
+
+__device__ __forceinline__ int orient_of(int x, int y) { return (x == 0 && y == 1) ? 0 : (x == 1 && y == 0) ? 1 : (x == 0 ? 2 : 3); }
+
+__global__ void pair_write_kernel(const ah_site *__restrict__ s, uint64_t n, const uint8_t *__restrict__ pass,
+                                  const PairDev *__restrict__ pairs, const uint64_t *__restrict__ offsets,
+                                  ah_amplicon *__restrict__ out, uint64_t cap)
+{
+    for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (uint64_t)gridDim.x * blockDim.x) {
+        const Group g = make_group(s, n, pass, pairs, a);
+        if (!g.valid)
+            continue;
+        const ah_site sa = s[a];
+        const PairDev &pd = pairs[sa.pair];
+        // streams: (left index li, right primer y); cursor = next candidate index
+        uint64_t cur[4];
+        const int ns = g.nl * 2;
+        auto advance = [&](int st, uint64_t from) -> uint64_t {
+            const int y = st & 1;
+            for (uint64_t b = from; b < n; ++b) {
+                const ah_site r = s[b];
+                if (r.pair != sa.pair || r.contig != sa.contig || r.pos > g.tmax)
+                    return n;
+                if (r.strand != 1 || r.primer != y || (pass && !pass[b]))
+                    continue;
+                uint32_t end;
+                if (in_window(pd, sa.pos, r, &end))
+                    return b;
+            }
+            return n;
+        };
+        for (int st = 0; st < ns; ++st)
+            cur[st] = advance(st, g.first);
+        uint64_t o = offsets[a];
+        for (;;) {
+            int best = -1;
+            uint32_t bend = 0;
+            int bor = 0;
+            for (int st = 0; st < ns; ++st) {
+                if (cur[st] >= n)
+                    continue;
+                const ah_site r = s[cur[st]];
+                const uint32_t end = r.pos + pd.L[r.primer];
+                const int orr = orient_of(g.lx[st >> 1], r.primer);
+                if (best < 0 || end < bend || (end == bend && orr < bor)) {
+                    best = st;
+                    bend = end;
+                    bor = orr;
+                }
+            }
+            if (best < 0)
+                break;
+            if (o < cap) {
+                ah_amplicon am;
+                am.genome = sa.genome;
+                am.contig = sa.contig;
+                am.start = sa.pos;
+                am.end = bend;
+                am.left = (uint32_t)g.li[best >> 1];
+                am.right = (uint32_t)cur[best];
+                am.orient = (uint8_t)bor;
+                am.pair = sa.pair;
+                am.pad0 = am.pad1 = 0;
+                out[o] = am;
+            }
+            ++o;
+            cur[best] = advance(best, cur[best] + 1);
+        }
+    }
+}
+
+unsigned grid_for(uint64_t n, int threads)
+{
+    uint64_t b = (n + threads - 1) / threads;
+    if (b > 16384)
+        b = 16384;
+    if (b == 0)
+        b = 1;
+    return (unsigned)b;
+}
+
+} // namespace
+
+void launch_pair_count(const ah_site *sites, uint64_t n, const uint8_t *pass, const PairDev *pairs_d,
+                       uint64_t *counts, cudaStream_t s)
+{
+    if (!n)
+        return;
+    pair_count_kernel<<<grid_for(n, 128), 128, 0, s>>>(sites, n, pass, pairs_d, counts);
+    AH_CUDA(cudaGetLastError());
+}
+
+size_t scan_u64_temp_bytes(uint64_t n)
+{
+    size_t bytes = 0;
+    AH_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, bytes, (const uint64_t *)nullptr, (uint64_t *)nullptr, (int64_t)n));
+    return bytes;
+}
+
+void exclusive_scan_u64(void *temp, size_t temp_bytes, const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s)
+{
+    AH_CUDA(cub::DeviceScan::ExclusiveSum(temp, temp_bytes, in, out, (int64_t)n, s));
+}
+
+void launch_pair_write(const ah_site *sites, uint64_t n, const uint8_t *pass, const PairDev *pairs_d,
+                       const uint64_t *offsets, ah_amplicon *out, uint64_t cap, cudaStream_t s)
+{
+    if (!n)
+        return;
+    pair_write_kernel<<<grid_for(n, 128), 128, 0, s>>>(sites, n, pass, pairs_d, offsets, out, cap);
+    AH_CUDA(cudaGetLastError());
+}
+
+} // namespace ah

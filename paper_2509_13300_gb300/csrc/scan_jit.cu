@@ -1,0 +1,473 @@
+// Scan kernel generator (primer matching, Sec. 2.1) and its run-time compiler.
+//
+// Why generate: the mismatch count of a window against a degenerate primer is
+// a sum of L one-bit terms, and on this GPU its cost is set by integer issue
+// slots.  With the primer's IUPAC codes known when the kernel is compiled,
+// the match word of a single-base position is a plane word itself (0 ops), a
+// two- or three-base position is a sum of disjoint plane words (integer adds,
+// which do not use the logic pipe), and the count runs through a carry-save
+// network whose shape depends on L and k.  So each set of patterns gets its
+// own straight-line kernel, built here as CUDA source and compiled with NVRTC
+// for sm_103a; compiled kernels are cached per process.
+//
+// Bit-sliced counting.  A thread owns R consecutive words of a tile; word j
+// holds starts p = b * W + j for b = 0..31 (tile-strided layout), so the
+// window base at offset i of all 32 starts is word j + i.  For each pattern
+// and word the kernel forms the L match words M_i (bit b = 1 when the base at
+// p_b + i is in the pattern's set) and reduces them column by column with
+// full adders.  It works in the "match" domain: a full adder on match words
+// yields the complements of the sum and carry of the mismatch bits, so no
+// inversion is ever needed, and padding uses all-ones words (a match).  With
+// K2 the smallest power of two above k, columns of weight < K2 are reduced
+// to one bit each; a mismatch count >= K2 shows as a zero bit in any carry
+// word of weight K2, so those are AND-ed; the low bits are compared with k by
+// one or two LOP3s.  Full adders are either two LOP3s (xor3, majority) or one
+// majority LOP3 plus integer adds for the sum (s = a + b + c - 2 maj), a mix
+// chosen by the tuner to balance the logic and integer pipes.
+//
+// Hits are rare; a warp that has any runs a slow path that rechecks each hit
+// bit against the contig table (windows never cross a contig end), recounts
+// its mismatches exactly from shared memory (a device check that the network
+// agrees), applies the 3' clamp, and appends 64-bit keys with one atomic per
+// warp.  Key = ((pair << pbits | flat position) << 10) | primer << 9 |
+// strand << 8 | mm, so sorting keys gives the canonical site order.
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <sstream>
+
+#include "ah_internal.h"
+
+namespace ah {
+namespace {
+
+const char *kPrelude = R"CUDA(
+typedef unsigned int u32;
+typedef unsigned long long u64;
+typedef unsigned char u8;
+template <int IMM> __device__ __forceinline__ u32 lop3(u32 a, u32 b, u32 c)
+{
+    u32 d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(IMM));
+    return d;
+}
+)CUDA";
+
+// Body of the kernel after the generated hit words.  Uses: h[NPAT*R] (hit
+// words), any, sm (tile planes), tile, j0, and the pattern tables.
+const char *kEmit = R"CUDA(
+    if (__any_sync(0xffffffffu, any != 0u)) {
+        const int lane = threadIdx.x & 31;
+        u32 hl[NPAT * R];
+#pragma unroll
+        for (int i = 0; i < NPAT * R; ++i) hl[i] = h[i];
+        u32 nv = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            u64 idx = 0;
+            if (pass == 1) {
+                u32 incl = nv;
+                for (int d = 1; d < 32; d <<= 1) {
+                    u32 y = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl += y;
+                }
+                u32 total = __shfl_sync(0xffffffffu, incl, 31);
+                u64 base = 0;
+                if (lane == 31 && total) base = atomicAdd(counter, (u64)total);
+                base = __shfl_sync(0xffffffffu, base, 31);
+                idx = base + incl - nv;
+            }
+            for (int qr = 0; qr < NPAT * R; ++qr) {
+                u32 m = hl[qr];
+                const int q = qr / R, r = qr % R;
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int jr = j0 + r;
+                    const u64 P = tile * TB + (u64)b * W + jr;
+                    const int L = c_L[q];
+                    u32 lo = 0, hi = n_contigs;
+                    while (hi - lo > 1) {
+                        u32 mid = (lo + hi) >> 1;
+                        if (contig_off[mid] <= P) lo = mid; else hi = mid;
+                    }
+                    if (P + L > contig_off[lo + 1]) continue;
+                    int mm = 0, clamp_bad = 0;
+                    const int c = c_clamp[q];
+                    for (int i = 0; i < L; ++i) {
+                        const int wj = jr + i;
+                        const u32 code = ((sm[wj] >> b) & 1u) | (((sm[WX + wj] >> b) & 1u) << 1) |
+                                         (((sm[2 * WX + wj] >> b) & 1u) << 2) | (((sm[3 * WX + wj] >> b) & 1u) << 3);
+                        const int mis = (code & c_mask[q][i]) == 0u;
+                        mm += mis;
+                        const int in_clamp = c_strand[q] == 0 ? (i >= L - c) : (i < c);
+                        clamp_bad |= mis & in_clamp;
+                    }
+                    if (mm > c_k[q]) { atomicExch(err, 3); continue; } // network disagrees with the recount
+                    if (clamp_bad) continue;
+                    if (pass == 0) { ++nv; continue; }
+                    if (idx < cap)
+                        keys[idx] = ((((u64)c_pair[q] << pbits) | P) << 10) | ((u64)c_primer[q] << 9) |
+                                    ((u64)c_strand[q] << 8) | (u64)mm;
+                    ++idx;
+                }
+            }
+        }
+    }
+)CUDA";
+
+struct Gen {
+    std::ostringstream os;
+    int n = 0;
+    int fa_total = 0, fa_arith = 0;
+    int arith_pct = 0;
+
+    std::string tmp() { return "v" + std::to_string(n++); }
+    std::string lop(const std::string &a, const std::string &b, const std::string &c, int imm)
+    {
+        std::string v = tmp();
+        os << "    const u32 " << v << " = lop3<0x" << std::hex << imm << std::dec << ">(" << a << ", " << b << ", "
+           << c << ");\n";
+        return v;
+    }
+    // full adder on match-domain words -> (sum, carry)
+    void fa(const std::string &a, const std::string &b, const std::string &c, std::string &s, std::string &cy)
+    {
+        ++fa_total;
+        cy = lop(a, b, c, 0xE8);
+        // Bresenham-style spread of the arithmetic full adders
+        bool arith = (fa_arith * 100 < arith_pct * fa_total);
+        if (arith) {
+            ++fa_arith;
+            s = tmp();
+            os << "    const u32 " << s << " = " << a << " + " << b << " + " << c << " - " << cy << " - " << cy
+               << ";\n";
+        } else {
+            s = lop(a, b, c, 0x96);
+        }
+    }
+};
+
+int popc4(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1) + ((m >> 3) & 1); }
+
+// match word of an IUPAC mask at window index w
+std::string match_word(Gen &g, int mask, int w, std::map<std::pair<int, int>, std::string> &cache)
+{
+    auto key = std::make_pair(mask, w);
+    auto it = cache.find(key);
+    if (it != cache.end())
+        return it->second;
+    static const char *P[4] = {"pA", "pC", "pG", "pT"};
+    std::string r;
+    int n = popc4(mask);
+    if (n == 4) {
+        r = "pV[" + std::to_string(w) + "]";
+    } else if (n == 1) {
+        for (int x = 0; x < 4; ++x)
+            if (mask & (1 << x))
+                r = std::string(P[x]) + "[" + std::to_string(w) + "]";
+    } else {
+        r = g.tmp();
+        g.os << "    const u32 " << r << " = ";
+        bool first = true;
+        for (int x = 0; x < 4; ++x)
+            if (mask & (1 << x)) {
+                g.os << (first ? "" : " + ") << P[x] << "[" << w << "]";
+                first = false;
+            }
+        g.os << ";\n";
+    }
+    cache[key] = r;
+    return r;
+}
+
+// LOP3 immediate of f over (a, b, c): bit index (a << 2) | (b << 1) | c.
+template <class F> int lut3(F f)
+{
+    int imm = 0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c)
+                if (f(a, b, c))
+                    imm |= 1 << ((a << 2) | (b << 1) | c);
+    return imm;
+}
+
+std::string and_reduce(Gen &g, std::deque<std::string> v)
+{
+    if (v.empty())
+        return "0xffffffffu";
+    while (v.size() > 1) {
+        std::string a = v.front();
+        v.pop_front();
+        std::string b = v.front();
+        v.pop_front();
+        std::string c = "0xffffffffu";
+        if (!v.empty()) {
+            c = v.front();
+            v.pop_front();
+        }
+        v.push_back(g.lop(a, b, c, 0x80));
+    }
+    return v.front();
+}
+
+// Hit word of pattern p for the thread's word r: bit b set iff the window at
+// start p_b has <= k mismatches.
+std::string gen_hit(Gen &g, const ScanPattern &p, int r, std::map<std::pair<int, int>, std::string> &cache)
+{
+    if (p.k >= p.L)
+        return "0xffffffffu";
+    int klog = 0;
+    while ((1 << klog) <= p.k)
+        ++klog; // K2 = 2^klog > k
+    std::deque<std::string> col[6];
+    for (int i = 0; i < p.L; ++i)
+        col[0].push_back(match_word(g, p.mask[i], r + i, cache));
+    for (int w = 0; w < klog; ++w) {
+        while (col[w].size() > 1) {
+            std::string a = col[w].front();
+            col[w].pop_front();
+            std::string b = col[w].front();
+            col[w].pop_front();
+            std::string c = "0xffffffffu";
+            if (!col[w].empty()) {
+                c = col[w].front();
+                col[w].pop_front();
+            }
+            std::string s, cy;
+            g.fa(a, b, c, s, cy);
+            col[w].push_back(s);
+            col[w + 1].push_back(cy);
+        }
+    }
+    std::string hi = and_reduce(g, col[klog]);
+    if (p.k == (1 << klog) - 1)
+        return hi;
+    // low part: match-domain bits s_w (mismatch bit = ~s_w), value v = sum 2^w (1 - s_w) <= k
+    std::string s[4];
+    for (int w = 0; w < klog; ++w)
+        s[w] = col[w].empty() ? std::string("0xffffffffu") : col[w].front();
+    const int k = p.k;
+    if (klog == 2) { // k == 2 (k == 3 handled above)
+        int imm = lut3([&](int a, int b, int c) { return a && ((1 - b) + 2 * (1 - c) <= k); });
+        return g.lop(hi, s[0], s[1], imm);
+    }
+    if (klog == 3) { // k in 4..6
+        int imm = lut3([&](int a, int b, int c) { return ((1 - a) + 2 * (1 - b) + 4 * (1 - c)) <= k; });
+        std::string lo = g.lop(s[0], s[1], s[2], imm);
+        return g.lop(hi, lo, "0xffffffffu", 0x80);
+    }
+    // klog == 4, k in 8..10: v = low3 + 8 (1 - s3); low3 <= 7 <= k, so v <= k iff s3 or low3 <= k - 8
+    int imm = lut3([&](int a, int b, int c) { return ((1 - a) + 2 * (1 - b) + 4 * (1 - c)) <= k - 8; });
+    std::string lo = g.lop(s[0], s[1], s[2], imm);
+    int imm2 = lut3([](int a, int b, int c) { return a && (b || c); });
+    return g.lop(hi, s[3], lo, imm2);
+}
+
+} // namespace
+
+std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &t)
+{
+    const int npat = (int)pats.size();
+    int Lmax = 1;
+    for (auto &p : pats)
+        Lmax = std::max(Lmax, p.L);
+    const int R = t.R;
+    const int nwin = 4 * ((R + Lmax - 1 + 3) / 4);
+    const int NT = kTileW / R;
+    Gen g;
+    g.arith_pct = t.arith_pct;
+    std::ostringstream &os = g.os;
+    os << kPrelude;
+    os << "#define W " << kTileW << "\n#define WX " << kTileWX << "\n#define TB " << kTileBases << "ull\n";
+    os << "#define R " << R << "\n#define NPAT " << npat << "\n#define NWIN " << nwin << "\n#define NT " << NT
+       << "\n";
+    auto table = [&](const char *name, auto get) {
+        os << "__device__ const u8 " << name << "[" << npat << "] = {";
+        for (int q = 0; q < npat; ++q)
+            os << (q ? ", " : "") << get(pats[q]);
+        os << "};\n";
+    };
+    table("c_L", [](const ScanPattern &p) { return p.L; });
+    table("c_k", [](const ScanPattern &p) { return p.k; });
+    table("c_clamp", [](const ScanPattern &p) { return p.clamp; });
+    table("c_pair", [](const ScanPattern &p) { return p.pair; });
+    table("c_primer", [](const ScanPattern &p) { return p.primer; });
+    table("c_strand", [](const ScanPattern &p) { return p.strand; });
+    os << "__device__ const u8 c_mask[" << npat << "][32] = {";
+    for (int q = 0; q < npat; ++q) {
+        os << (q ? ", " : "") << "{";
+        for (int i = 0; i < 32; ++i)
+            os << (i ? "," : "") << (i < pats[q].L ? (int)pats[q].mask[i] : 15);
+        os << "}";
+    }
+    os << "};\n";
+    os << "extern \"C\" __global__ void __launch_bounds__(NT, " << t.min_blocks << ")\n"
+       << "ah_scan_kernel(const u32 *__restrict__ planes, u64 n_tiles, const u64 *__restrict__ contig_off,\n"
+       << "               u32 n_contigs, u64 *__restrict__ keys, u64 cap, u64 *__restrict__ counter, int pbits,\n"
+       << "               int *__restrict__ err)\n{\n"
+       << "  extern __shared__ __align__(16) u32 sm[];\n"
+       << "  for (u64 tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {\n"
+       << "    {\n"
+       << "      const uint4 *src = reinterpret_cast<const uint4 *>(planes + tile * 4 * WX);\n"
+       << "      uint4 *dst = reinterpret_cast<uint4 *>(sm);\n"
+       << "      for (int i = threadIdx.x; i < WX; i += NT) dst[i] = __ldg(src + i);\n"
+       << "    }\n"
+       << "    __syncthreads();\n"
+       << "    const int j0 = threadIdx.x * R;\n"
+       << "    u32 pA[NWIN], pC[NWIN], pG[NWIN], pT[NWIN], pV[NWIN];\n"
+       << "#pragma unroll\n"
+       << "    for (int c = 0; c < NWIN / 4; ++c) {\n"
+       << "      uint4 a = reinterpret_cast<const uint4 *>(sm + 0 * WX + j0)[c];\n"
+       << "      uint4 cc = reinterpret_cast<const uint4 *>(sm + 1 * WX + j0)[c];\n"
+       << "      uint4 gg = reinterpret_cast<const uint4 *>(sm + 2 * WX + j0)[c];\n"
+       << "      uint4 tt = reinterpret_cast<const uint4 *>(sm + 3 * WX + j0)[c];\n"
+       << "      pA[4*c] = a.x; pA[4*c+1] = a.y; pA[4*c+2] = a.z; pA[4*c+3] = a.w;\n"
+       << "      pC[4*c] = cc.x; pC[4*c+1] = cc.y; pC[4*c+2] = cc.z; pC[4*c+3] = cc.w;\n"
+       << "      pG[4*c] = gg.x; pG[4*c+1] = gg.y; pG[4*c+2] = gg.z; pG[4*c+3] = gg.w;\n"
+       << "      pT[4*c] = tt.x; pT[4*c+1] = tt.y; pT[4*c+2] = tt.z; pT[4*c+3] = tt.w;\n"
+       << "    }\n"
+       << "#pragma unroll\n"
+       << "    for (int w = 0; w < NWIN; ++w) pV[w] = pA[w] + pC[w] + pG[w] + pT[w];\n"
+       << "    u32 h[NPAT * R];\n"
+       << "    u32 any = 0;\n";
+    std::map<std::pair<int, int>, std::string> cache;
+    auto one = [&](int q, int r) {
+        os << "    // pattern " << q << ", word " << r << "\n";
+        std::string hw = gen_hit(g, pats[q], r, cache);
+        os << "    h[" << q * R + r << "] = " << hw << ";\n    any |= h[" << q * R + r << "];\n";
+    };
+    if (t.order == 0) {
+        for (int r = 0; r < R; ++r)
+            for (int q = 0; q < npat; ++q)
+                one(q, r);
+    } else {
+        for (int q = 0; q < npat; ++q)
+            for (int r = 0; r < R; ++r)
+                one(q, r);
+    }
+    os << kEmit;
+    os << "    __syncthreads();\n  }\n}\n";
+    return os.str();
+}
+
+namespace {
+std::mutex g_mu;
+std::map<std::string, std::unique_ptr<ScanKernel>> g_cache; // key: device + source
+
+std::string nvrtc_err(nvrtcResult r) { return nvrtcGetErrorString(r); }
+} // namespace
+
+namespace {
+std::string compile_cubin(const std::string &src, std::vector<char> *cubin, bool *ok)
+{
+    nvrtcProgram prog;
+    nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "ah_scan_generated.cu", 0, nullptr, nullptr);
+    if (r != NVRTC_SUCCESS)
+        throw Error(AH_ERR_JIT, "nvrtcCreateProgram: " + nvrtc_err(r));
+    const char *opts[] = {"-arch=sm_103a", "-std=c++17", "-lineinfo", "--ptxas-options=-v", "-DNDEBUG"};
+    r = nvrtcCompileProgram(prog, 5, opts);
+    size_t log_size = 0;
+    nvrtcGetProgramLogSize(prog, &log_size);
+    std::string log(log_size, '\0');
+    if (log_size)
+        nvrtcGetProgramLog(prog, &log[0]);
+    *ok = (r == NVRTC_SUCCESS);
+    if (*ok && cubin) {
+        size_t cubin_size = 0;
+        nvrtcGetCUBINSize(prog, &cubin_size);
+        cubin->resize(cubin_size);
+        nvrtcGetCUBIN(prog, cubin->data());
+    }
+    nvrtcDestroyProgram(&prog);
+    return log;
+}
+} // namespace
+
+std::string scan_compile_only(const std::vector<ScanPattern> &pats, const ScanTuning &t, bool *ok)
+{
+    return compile_cubin(scan_source(pats, t), nullptr, ok);
+}
+
+ScanKernel *scan_kernel(const std::vector<ScanPattern> &pats, const ScanTuning &t, int device)
+{
+    std::string src = scan_source(pats, t);
+    std::string key = std::to_string(device) + "\n" + src;
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end())
+        return it->second.get();
+
+    bool ok = false;
+    std::vector<char> cubin;
+    std::string log = compile_cubin(src, &cubin, &ok);
+    if (!ok)
+        throw Error(AH_ERR_JIT, "scan kernel compilation failed: " + log.substr(0, 2000));
+
+    auto k = std::make_unique<ScanKernel>();
+    k->log = log;
+    AH_CUDA(cudaLibraryLoadData(&k->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
+    AH_CUDA(cudaLibraryGetKernel(&k->fn, k->lib, "ah_scan_kernel"));
+    k->threads = kTileW / t.R;
+    k->smem = kTileBytes;
+    auto pos = log.find("Used ");
+    if (pos != std::string::npos)
+        k->regs = atoi(log.c_str() + pos + 5);
+    int bps = 0;
+    AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void *)k->fn, k->threads, k->smem));
+    k->blocks_per_sm = std::max(1, bps);
+    ScanKernel *raw = k.get();
+    g_cache[key] = std::move(k);
+    return raw;
+}
+
+} // namespace ah
+
+// Generate and compile (no GPU needed) the scan kernel of one primer pair;
+// writes the NVRTC/ptxas log (register use) into log[0..log_cap).  Returns 0
+// on success.  A development aid; not part of the public header.
+extern "C" int ah_debug_compile_scan(const char *fwd, const char *rev, int k, int R, int arith_pct, int order,
+                                     char *log, size_t log_cap)
+{
+    try {
+        std::vector<ah::ScanPattern> pats;
+        const char *pr[2] = {fwd, rev};
+        for (int primer = 0; primer < 2; ++primer)
+            for (int strand = 0; strand < 2; ++strand) {
+                ah::ScanPattern p;
+                p.L = (int)strlen(pr[primer]);
+                if (p.L < 1 || p.L > AH_MAX_PRIMER_LEN)
+                    return 2;
+                p.k = k;
+                p.primer = primer;
+                p.strand = strand;
+                for (int i = 0; i < p.L; ++i) {
+                    int m = strand == 0 ? ah::iupac_mask(pr[primer][i]) : ah::comp_mask(ah::iupac_mask(pr[primer][p.L - 1 - i]));
+                    if (!m)
+                        return 2;
+                    p.mask[i] = (uint8_t)m;
+                }
+                pats.push_back(p);
+            }
+        ah::ScanTuning t;
+        t.R = R;
+        t.arith_pct = arith_pct;
+        t.order = order;
+        bool ok = false;
+        std::string l = ah::scan_compile_only(pats, t, &ok);
+        if (log && log_cap) {
+            size_t n = std::min(log_cap - 1, l.size());
+            memcpy(log, l.data(), n);
+            log[n] = 0;
+        }
+        return ok ? 0 : 1;
+    } catch (const std::exception &e) {
+        if (log && log_cap)
+            snprintf(log, log_cap, "%s", e.what());
+        return 3;
+    }
+}

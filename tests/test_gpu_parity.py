@@ -1,0 +1,273 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer results -- sites, mismatch counts, amplicons, pass flags, sequences
+-- must be identical; the fp32 Tm must be within 0.01 deg C of the oracle's
+fp64 value (NaN where the oracle has NaN).  Inputs are seeded synthetic
+workloads; nothing here is produced by the CUDA path and then trusted.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_13300_gb300 import ah, build, synth
+
+pytestmark = pytest.mark.gpu
+TM_TOL = 0.01  # deg C
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    build.build()
+    c = ah.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_run(ctx, w, table=None):
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    try:
+        pids = [ctx.ah_set_primers(p["fwd"], p["rev"], p) for p in w.pairs]
+        if table is not None:
+            for p in pids:
+                ctx.ah_set_nn_table(p, table)
+        sites = ctx.scan(sid, pids)
+        tm, ps = ctx.tm(sid, pids, sites)
+        amps = ctx.pair(sid, pids, sites)
+        amps_tm = ctx.pair(sid, pids, sites, ps)
+        seqs, offs = ctx.fetch(sid, amps)
+    finally:
+        ctx.ah_unload_genomes(sid)
+    return dict(sites=sites, tm=tm, pass_=ps, amps=amps, amps_tm=amps_tm, seqs=seqs, offs=offs)
+
+
+def oracle_run(w, table=None):
+    sites = oracle.scan(w.seq, w.contig_off, w.contig_genome, w.pairs)
+    tm, ps = oracle.tm(w.seq, w.contig_off, sites, w.pairs, table)
+    amps = oracle.pair(sites, w.pairs)
+    amps_tm = oracle.pair(sites, w.pairs, ps)
+    seqs, offs = oracle.fetch(w.seq, w.contig_off, amps)
+    return dict(sites=sites, tm=tm, pass_=ps, amps=amps, amps_tm=amps_tm, seqs=seqs, offs=offs)
+
+
+def assert_parity(g, o, min_sites=1):
+    assert len(g["sites"]) == len(o["sites"]), (len(g["sites"]), len(o["sites"]))
+    assert len(o["sites"]) >= min_sites
+    assert g["sites"].tobytes() == o["sites"].tobytes()
+    tg, to = g["tm"].astype(np.float64), o["tm"]
+    nan_g, nan_o = np.isnan(tg), np.isnan(to)
+    assert np.array_equal(nan_g, nan_o)
+    if (~nan_o).any():
+        err = np.abs(tg[~nan_o] - to[~nan_o]).max()
+        assert err <= TM_TOL, err
+    assert np.array_equal(g["pass_"], o["pass_"])
+    assert g["amps"].tobytes() == o["amps"].tobytes()
+    assert g["amps_tm"].tobytes() == o["amps_tm"].tobytes()
+    assert np.array_equal(g["offs"], o["offs"])
+    assert g["seqs"] == o["seqs"]
+
+
+def test_tiny_workload(ctx):
+    """Plain method, tiny: 200 kbp, 3 contigs, 10 planted amplicons, k = 2."""
+    w = synth.tiny(0)
+    o = oracle_run(w)
+    assert_parity(gpu_run(ctx, w), o, min_sites=10)
+    # the same with the paper's default 50 deg C threshold (Sec. 3.2)
+    w.pairs = [dict(w.pairs[0], tm_min=50.0)]
+    o2 = oracle_run(w)
+    assert 0 < o2["pass_"].sum() < len(o2["pass_"]) or len(o2["pass_"]) == 0
+    assert_parity(gpu_run(ctx, w), o2)
+
+
+@pytest.mark.parametrize("seed,k,clamp", [(1, 0, 0), (2, 1, 0), (3, 2, 1), (4, 3, 0), (5, 4, 2), (6, 5, 0),
+                                          (7, 7, 0), (8, 9, 3), (9, 10, 0)])
+def test_random_small_with_edge_letters(ctx, seed, k, clamp):
+    """Short primers so hits are frequent; lower case, IUPAC letters and gaps in
+    the genome; several contigs including tiny ones; k from 0 to 10."""
+    max_len = 900 if k < 4 else 200 if k < 7 else 80
+    w = synth.random_small(seed, n_bases=60_000 // (1 + k // 3) + 777 * seed, n_contigs=7, L_f=7 + k + seed % 3,
+                           L_r=6 + k + seed % 2, k=k, codes_f="RNY"[: 1 + seed % 3], codes_r="SBD"[: 1 + seed % 3],
+                           lower_frac=0.05, iupac_frac=0.003, min_len=30, max_len=max_len)
+    w.pairs = [dict(w.pairs[0], clamp=clamp, tm_min=float(seed * 3))]
+    assert_parity(gpu_run(ctx, w), oracle_run(w))
+
+
+def test_k_at_least_length_reports_every_window(ctx):
+    w = synth.random_small(21, n_bases=5000, n_contigs=3, L_f=6, L_r=5, k=6, min_len=5, max_len=40)
+    assert_parity(gpu_run(ctx, w), oracle_run(w), min_sites=19000)
+
+
+def test_several_pairs_in_one_pass(ctx):
+    rng = np.random.default_rng(5)
+    w = synth.random_small(33, n_bases=120_000, n_contigs=5, L_f=12, L_r=10, k=2, min_len=40, max_len=2000)
+    pairs = [w.pairs[0]]
+    for j in range(4):
+        f = synth.random_primer(rng, 10 + j, "RY")
+        r = synth.random_primer(rng, 11 + j, "N")
+        pairs.append(synth.pcr_params(f, r, k=j % 4, min_len=20 + j, max_len=1500, tm_min=20.0))
+    w.pairs = pairs
+    assert_parity(gpu_run(ctx, w), oracle_run(w))
+
+
+def test_collection_spanning_many_tiles(ctx):
+    """Genome-collection generator at reduced size: ~5 Mbp, 6 genomes, many
+    contigs, N runs, planted operons with 0-4 substitutions, the 960-oligo pair."""
+    w = synth.collection(seed=1, n_genomes=6, len_lo=4e5, len_hi=1.5e6, max_subs=4)
+    o = oracle_run(w)
+    assert len(o["amps"]) >= 3
+    assert_parity(gpu_run(ctx, w), o)
+
+
+def test_paper_primer_pairs(ctx):
+    """The four benchmark pairs printed in the paper (Sec. 2.3) on one collection."""
+    pairs = [synth.pcr_params(f, r, k=2, min_len=100, max_len=3000, tm_min=50.0)
+             for f, r in synth.PAPER_PAIRS.values()]
+    w = synth.collection(seed=4, n_genomes=3, len_lo=3e5, len_hi=8e5, pairs=pairs, plant_max=4, max_subs=2)
+    assert_parity(gpu_run(ctx, w), oracle_run(w))
+
+
+@pytest.mark.parametrize("salt", [0, 1, 2, 3, 4, 5])
+def test_salt_methods_and_ions(ctx, salt):
+    w = synth.tiny(0)
+    w.pairs = [dict(w.pairs[0], saltcorr=salt, K_mM=10.0, Tris_mM=20.0, Mg_mM=1.5, dNTPs_mM=0.2,
+                    dnac1_nM=400.0, dnac2_nM=100.0, tm_min=45.0)]
+    assert_parity(gpu_run(ctx, w), oracle_run(w))
+
+
+def test_custom_nn_table_with_mismatch_terms(ctx):
+    """A table with non-zero mismatch stacks and mismatch-specific terminal
+    terms, passed to both sides; includes entries that make some duplex
+    entropies positive, which forces the enumeration path on the GPU."""
+    rng = np.random.default_rng(12)
+    t = oracle.default_table()
+    ta = ah.NNTable()
+    H = np.array(t.stack_dH)
+    S = np.array(t.stack_dS)
+    zero = (H == 0)
+    H[zero] = np.round(rng.uniform(-3, 4, zero.sum()), 1)
+    S[zero] = np.round(rng.uniform(-12, 12, zero.sum()), 1)
+    TH = np.round(rng.uniform(-1, 3, 16), 1)
+    TS = np.round(rng.uniform(-4, 6, 16), 1)
+    for tt in (t, ta):
+        tt.stack_dH[:] = list(H)
+        tt.stack_dS[:] = list(S)
+        tt.term_dH[:] = list(TH)
+        tt.term_dS[:] = list(TS)
+    w = synth.tiny(0)
+    w.pairs = [dict(w.pairs[0], tm_min=30.0)]
+    g = gpu_run(ctx, w, table=ta)
+    o = oracle_run(w, table=t)
+    assert_parity(g, o)
+
+
+def test_threshold_decisions_at_the_boundary(ctx):
+    """tm_min set at (and a hair either side of) oracle Tm values: the pass
+    flags must still equal the fp64 decisions."""
+    w = synth.tiny(0)
+    o = oracle_run(w)
+    vals = o["tm"][~np.isnan(o["tm"])]
+    assert len(vals) > 3
+    for v in (vals[0], vals[len(vals) // 2] + 1e-9, vals[-1] - 1e-9):
+        w.pairs = [dict(w.pairs[0], tm_min=float(v))]
+        assert_parity(gpu_run(ctx, w), oracle_run(w))
+
+
+def test_device_resident_buffers(ctx):
+    """Inputs and outputs in device memory (torch CUDA tensors) give the same
+    records as host buffers."""
+    import torch
+    w = synth.tiny(0)
+    o = oracle_run(w)
+    seq_d = torch.from_numpy(w.seq).cuda()
+    sid = ctx.ah_load_genomes(seq_d, len(w.seq), w.contig_off, w.contig_genome)
+    pid = ctx.ah_set_primers(w.pairs[0]["fwd"], w.pairs[0]["rev"], w.pairs[0])
+    n = len(o["sites"])
+    sites_d = torch.zeros(n * 16, dtype=torch.uint8, device="cuda")
+    assert ctx.ah_scan(sid, [pid], sites_d, n) == n
+    assert sites_d.cpu().numpy().tobytes() == o["sites"].tobytes()
+    tm_d = torch.zeros(n, dtype=torch.float32, device="cuda")
+    ps_d = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    ctx.ah_tm(sid, [pid], sites_d, n, tm_d, ps_d)
+    assert np.nanmax(np.abs(tm_d.cpu().numpy() - o["tm"])) <= TM_TOL
+    m = len(o["amps"])
+    amps_d = torch.zeros(m * 28, dtype=torch.uint8, device="cuda")
+    assert ctx.ah_pair(sid, [pid], sites_d, None, n, amps_d, m) == m
+    assert amps_d.cpu().numpy().tobytes() == o["amps"].tobytes()
+    total = int(o["offs"][-1])
+    seq_out = torch.zeros(total, dtype=torch.uint8, device="cuda")
+    offs_d = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
+    ctx.ah_fetch(sid, amps_d, m, seq_out, total, offs_d)
+    assert seq_out.cpu().numpy().tobytes() == o["seqs"]
+    assert np.array_equal(offs_d.cpu().numpy().astype(np.uint64), o["offs"])
+    ctx.ah_unload_genomes(sid)
+
+
+def test_errors_are_reported_not_raised_on_device(ctx):
+    w = synth.tiny(0)
+    p = dict(w.pairs[0])
+    with pytest.raises(ah.AHError) as e:
+        ctx.ah_set_primers("ACGX", p["rev"], p)
+    assert e.value.status == ah.AH_ERR_PRIMER
+    with pytest.raises(ah.AHError) as e:
+        ctx.ah_set_primers("ACGT", p["rev"], p)  # shorter than 5
+    assert e.value.status == ah.AH_ERR_PRIMER
+    with pytest.raises(ah.AHError) as e:
+        ctx.ah_set_primers("NNNNNNNNNNNN", p["rev"], p)  # degeneracy 4^12 > 10000
+    assert e.value.status == ah.AH_ERR_PRIMER
+    with pytest.raises(ah.AHError) as e:
+        ctx.ah_set_primers(p["fwd"], p["rev"], dict(p, k=11))
+    assert e.value.status == ah.AH_ERR_PRIMER
+    with pytest.raises(ah.AHError) as e:
+        ctx.ah_set_primers(p["fwd"], p["rev"], dict(p, min_len=10, max_len=5))
+    assert e.value.status == ah.AH_ERR_ARG
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    pid = ctx.ah_set_primers(p["fwd"], p["rev"], p)
+    with pytest.raises(ah.AHError) as e:  # size query: cap = 0 reports the count with AH_ERR_OVERFLOW
+        ctx.ah_scan(sid, [pid], None, 0)
+    assert e.value.status == ah.AH_ERR_OVERFLOW
+    n = e.value.needed
+    assert n > 2
+    small = np.zeros(n - 1, dtype=ah.SITE_DTYPE)
+    with pytest.raises(ah.AHError) as e:
+        ctx.ah_scan(sid, [pid], small, n - 1)
+    assert e.value.status == ah.AH_ERR_OVERFLOW and e.value.needed == n
+    assert not small.any()
+    with pytest.raises(ah.AHError) as e:
+        ctx.ah_scan(sid + 100, [pid], None, 0)
+    assert e.value.status == ah.AH_ERR_ARG
+    # a site record outside its contig is rejected before any kernel uses it
+    bad = np.zeros(1, dtype=ah.SITE_DTYPE)
+    bad["contig"] = 2
+    bad["pos"] = 10 ** 9
+    with pytest.raises(ah.AHError) as e:
+        ctx.tm(sid, [pid], bad)
+    assert e.value.status == ah.AH_ERR_ARG
+    ctx.ah_unload_genomes(sid)
+    # the context is still usable afterwards
+    assert_parity(gpu_run(ctx, w), oracle_run(w))
+
+
+def test_memory_budget_is_enforced():
+    build.build()
+    w = synth.tiny(0)
+    with ah.Context(0, mem_budget_bytes=1 << 16) as c:
+        with pytest.raises(ah.AHError) as e:
+            c.load(w.seq, w.contig_off, w.contig_genome)
+        assert e.value.status == ah.AH_ERR_BUDGET
+        assert c.device_bytes() < (1 << 16)
+
+
+def test_empty_and_degenerate_sets(ctx):
+    p = synth.tiny(0).pairs[0]
+    pid = ctx.ah_set_primers(p["fwd"], p["rev"], p)
+    # no bases at all, one empty contig
+    sid = ctx.ah_load_genomes(np.zeros(1, np.uint8), 0, np.array([0, 0], np.uint64), np.array([0], np.uint32))
+    assert ctx.ah_scan(sid, [pid], None, 0) == 0  # zero sites fit in capacity 0
+    ctx.ah_unload_genomes(sid)
+    # contigs shorter than the primers, empty contigs in between, all-N contig
+    seq = np.frombuffer(b"ACGTACG" + b"N" * 50 + b"ACGT", np.uint8).copy()
+    off = np.array([0, 7, 7, 57, 61], np.uint64)
+    sid = ctx.ah_load_genomes(seq, len(seq), off, np.array([0, 0, 1, 1], np.uint32))
+    assert ctx.ah_scan(sid, [pid], None, 0) == 0
+    ctx.ah_unload_genomes(sid)
