@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark of the in-silico PCR hot path on one GB300 (or N, one process per GPU).
+
+Workload (N = 1): the genome-collection configuration -- 100 synthetic
+genomes, lengths log-uniform in 2-7 Mbp (~0.4 Gbp), 1-200 contigs each, GC
+U(0.3, 0.7), 0.1% N runs, planted operon-like regions; one degenerate pair of
+20 and 22 nt with 960 oligos in total; k = 3; window 100-2500 bp; Tm with
+50 mM Na+, 0.25 uM primer, threshold 50 C.
+
+One step = the whole hot path on that batch through the C ABI: load/pack the
+resident ASCII genomes, scan both strands, Tm of every site, pair, fetch the
+amplicon sequences.  `value` is Gbp scanned per primer pair per second with
+the inputs already in HBM; `e2e` is the same with host (pinned) input and
+output buffers, the copies inside the timed region.  Under torchrun every
+rank scans its own seeded collection (weak scaling, no data-path collective);
+value = all ranks' bases / max rank time.
+
+--impl reference times the CPU oracle on a bounded sample of the same
+workload (the reference arm of this benchmark).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gbp/s scanned per primer pair (both strands, k mm)"
+WORKLOAD = "collection-100genomes-0.4Gbp-pair960-k3"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# logic-pipe issue roof of a GB300: 152 SMs x 64 lane-ops/clk (LOP3 is half rate) x clock
+SMS, LOP_LANES_PER_CLK = 152, 64
+
+
+def workload(seed: int):
+    from paper_2509_13300_gb300 import synth
+    w = synth.collection(seed=seed, n_genomes=100, len_lo=2e6, len_hi=7e6, k=3, min_len=100, max_len=2500)
+    w.pairs = [dict(w.pairs[0], tm_min=50.0, dnac1_nM=250.0, Na_mM=50.0)]
+    return w
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_baseline(w, target_s: float = 15.0):
+    """The oracle as it stands, on a bounded sample (leading genomes) of the
+    workload, on all host cores: scan + Tm + pair + fetch."""
+    import oracle
+    cores = os.cpu_count() or 1
+    goff = w.genome_off
+    # ~1.5 Mbp/s per 8 Neoverse/Xeon cores measured for the oracle scan; size the sample for ~target_s
+    want = max(2e6, 0.2e6 * cores * target_s)
+    g = 1
+    while g < len(goff) - 1 and goff[g] < want:
+        g += 1
+    nb = int(goff[g])
+    nc = int(np.searchsorted(w.contig_off, nb))
+    seq = w.seq[:nb]
+    off = w.contig_off[:nc + 1]
+    cg = w.contig_genome[:nc]
+    t0 = time.perf_counter()
+    s = oracle.scan(seq, off, cg, w.pairs, n_threads=cores)
+    tm, ps = oracle.tm(seq, off, s, w.pairs, n_threads=cores)
+    a = oracle.pair(s, w.pairs, ps)
+    oracle.fetch(seq, off, a)
+    dt = time.perf_counter() - t0
+    return {"value": nb / dt / 1e9, "unit": "Gbp/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {g} of 100 genomes ({nb / 1e6:.1f} Mbp, {nc} contigs), scan+Tm+pair+fetch, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            return
+    w = workload(1)
+    steps = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(w, target_s=args.ref_seconds)
+        if i >= args.warmup:
+            steps.append(r)
+    v = float(np.mean([r["value"] for r in steps]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gbp/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": steps[0]["sample"]},
+            "cpu_baseline": {"value": v, "unit": "Gbp/s", "cores": steps[0]["cores"], "kind": "oracle",
+                             "sample": steps[0]["sample"]},
+            "e2e": {"value": v, "unit": "Gbp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def load_peaks():
+    try:
+        p = json.load(open(PEAKS_FILE))
+        return float(p["hbm_gbs"]), "measured", p
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback", {}
+
+
+def traffic_record(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if it still matches this build."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    from paper_2509_13300_gb300 import build
+    if rec.get("source_digest") != build.source_digest():
+        return None
+    return rec
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank, world, local = dist_info()
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_2509_13300_gb300 import ah, build
+    build.build()
+
+    w = workload(1 + rank)
+    p = w.pairs[0]
+    n_bases = w.n_bases
+    stream = torch.cuda.current_stream()
+    seq_d = torch.from_numpy(w.seq).to("cuda")
+    ctx = ah.Context(local)
+    pid = ctx.ah_set_primers(p["fwd"], p["rev"], p)
+
+    # capacities from one warm-up pass (also compiles the generated scan kernel)
+    sid = ctx.ah_load_genomes(seq_d, n_bases, w.contig_off, w.contig_genome, stream)
+    sites = ctx.scan(sid, [pid])
+    tm, ps = ctx.tm(sid, [pid], sites)
+    amps = ctx.pair(sid, [pid], sites, ps)
+    seqs, offs = ctx.fetch(sid, amps)
+    ctx.ah_unload_genomes(sid)
+    cap_s, cap_a, cap_q = len(sites) + 1, len(amps) + 1, len(seqs) + 1
+    sites_d = torch.empty(cap_s * 16, dtype=torch.uint8, device="cuda")
+    tm_d = torch.empty(cap_s, dtype=torch.float32, device="cuda")
+    ps_d = torch.empty(cap_s, dtype=torch.uint8, device="cuda")
+    amps_d = torch.empty(cap_a * 28, dtype=torch.uint8, device="cuda")
+    seq_out_d = torch.empty(cap_q, dtype=torch.uint8, device="cuda")
+    offs_d = torch.empty(cap_a + 1, dtype=torch.int64, device="cuda")
+
+    def step_device():
+        sid = ctx.ah_load_genomes(seq_d, n_bases, w.contig_off, w.contig_genome, stream)
+        n = ctx.ah_scan(sid, [pid], sites_d, cap_s, stream)
+        ctx.ah_tm(sid, [pid], sites_d, n, tm_d, ps_d, stream)
+        m = ctx.ah_pair(sid, [pid], sites_d, ps_d, n, amps_d, cap_a, stream)
+        ctx.ah_fetch(sid, amps_d, m, seq_out_d, cap_q, offs_d, stream)
+        ctx.ah_unload_genomes(sid)
+        return n, m
+
+    for _ in range(args.warmup):
+        step_device()
+    ctx.ah_set_profiling(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for i in range(args.steps):
+            n, m = step_device()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    t_ms = ev[0].elapsed_time(ev[-1])
+    t_max = max_over_ranks(t_ms, world)
+    bases_all = sum_over_ranks(float(n_bases), world)
+    value = bases_all * args.steps / (t_max / 1e3) / 1e9  # Gbp/s, one pair
+
+    stages = {}
+    for st in ("pack", "scan", "sort", "decode", "validate", "tm", "pair", "fetch"):
+        ms, launches, calls = ctx.ah_get_profile(st)
+        stages[st] = {"ms_per_step": ms / args.steps, "launches_per_step": launches / args.steps,
+                      "avg_launch_us": (ms / calls * 1e3) if calls else None}
+    _, total_launches, _ = ctx.ah_get_profile(None)
+    ctx.ah_set_profiling(False)
+
+    # ---- roofline of the dominant kernel (live CUDA-event durations) ----
+    hbm_peak, peak_kind, peaks = load_peaks()
+    clocks = clk.summary()
+    scan_us = stages["scan"]["avg_launch_us"]
+    pack_us = stages["pack"]["avg_launch_us"]
+    dominant = "scan" if stages["scan"]["ms_per_step"] >= stages["pack"]["ms_per_step"] else "pack"
+    scan_hbm = 0.5 * n_bases / (scan_us * 1e-6) / 1e9  # 4 planes x 1 bit per base
+    pack_hbm = 1.5 * n_bases / (pack_us * 1e-6) / 1e9  # 1 B/base read + 0.5 B/base written
+    # logic-pipe ops of the generated scan kernel per launch (static count of its LOP3s per word)
+    lop_per_word = ctx_scan_lop_count(p)
+    words = n_bases / 32.0
+    scan_tops = lop_per_word * words / (scan_us * 1e-6) / 1e12
+    clk_mhz = clocks["sm_mhz"] or 2070.0
+    alu_peak = SMS * LOP_LANES_PER_CLK * clk_mhz * 1e6 / 1e12
+    if dominant == "scan":
+        tr = traffic_record("ah_scan_kernel")
+        roof = {"bound": "alu", "achieved": scan_tops, "peak": alu_peak, "unit": "Tops/s",
+                "frac": scan_tops / alu_peak, "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "kernel": "ah_scan_kernel",
+                "peak_note": f"logic pipe: {SMS} SMs x {LOP_LANES_PER_CLK} LOP3 lanes/clk x {clk_mhz:.0f} MHz "
+                             f"(median SM clock under load)",
+                "algorithmic": f"{lop_per_word} LOP3 per 32 starts per pass over the planes",
+                "hbm_achieved_gbs": scan_hbm, "hbm_peak_gbs": hbm_peak,
+                "hbm_frac": scan_hbm / hbm_peak, "hbm_peak_kind": peak_kind,
+                "hbm_algorithmic": "0.5 B/base (4 one-hot planes x 1 bit)"}
+    else:
+        tr = traffic_record("pack_kernel")
+        roof = {"bound": "hbm", "achieved": pack_hbm, "peak": hbm_peak, "unit": "GB/s",
+                "frac": pack_hbm / hbm_peak, "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "kernel": "pack_kernel", "peak_kind": peak_kind,
+                "algorithmic": "1.5 B/base (1 B ASCII read + 0.5 B planes written)"}
+
+    # ---- end to end through the public API with host (pinned) buffers ----
+    seq_h = torch.from_numpy(w.seq).pin_memory()
+    sites_h = torch.empty(cap_s * 16, dtype=torch.uint8).pin_memory()
+    tm_h = torch.empty(cap_s, dtype=torch.float32).pin_memory()
+    ps_h = torch.empty(cap_s, dtype=torch.uint8).pin_memory()
+    amps_h = torch.empty(cap_a * 28, dtype=torch.uint8).pin_memory()
+    seq_out_h = torch.empty(cap_q, dtype=torch.uint8).pin_memory()
+    offs_h = torch.empty(cap_a + 1, dtype=torch.int64).pin_memory()
+
+    def step_host():
+        sid = ctx.ah_load_genomes(seq_h, n_bases, w.contig_off, w.contig_genome, stream)
+        n = ctx.ah_scan(sid, [pid], sites_h, cap_s, stream)
+        ctx.ah_tm(sid, [pid], sites_h, n, tm_h, ps_h, stream)
+        m = ctx.ah_pair(sid, [pid], sites_h, ps_h, n, amps_h, cap_a, stream)
+        ctx.ah_fetch(sid, amps_h, m, seq_out_h, cap_q, offs_h, stream)
+        ctx.ah_unload_genomes(sid)
+        q = int(offs_h[m].item())
+        h2d = n_bases + w.contig_off.nbytes + w.contig_genome.nbytes + 2 * 16 * n + n + 28 * m
+        d2h = 16 * n + 5 * n + 28 * m + q + 8 * (m + 1)
+        return h2d, d2h
+
+    step_host()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        h2d, d2h = step_host()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e = {"value": bases_all * args.e2e_steps / (e2e_ms / 1e3) / 1e9, "unit": "Gbp/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps}
+
+    if rank != 0:
+        ctx.close()
+        return
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(w)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gbp/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_bases_per_gpu": n_bases, "n_contigs": w.n_contigs, "pairs": 1,
+                   "oligos": 960, "k": 3, "window": [100, 2500], "tm_min_C": 50.0, "tm_dtype": "f32",
+                   "sites": int(n), "amplicons": int(m), "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (0.4 GB ASCII + 0.2 GB planes per step)"},
+        "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99))},
+        "stages": stages, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": int(total_launches), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def ctx_scan_lop_count(pair: dict) -> int:
+    """LOP3 instructions the generated scan kernel issues per word (32 starts)
+    for this pair: counted from the generated source."""
+    from paper_2509_13300_gb300 import ah
+    return ah.scan_lop3_per_word(pair["fwd"], pair["rev"], int(pair["k"]))
+
+
+if __name__ == "__main__":
+    main()

@@ -244,6 +244,18 @@ ah_status ah_pair(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32
 ah_status ah_fetch(ah_ctx *ctx, uint32_t set_id, const ah_amplicon *amplicons, uint64_t n, char *seq_out,
                    uint64_t cap, uint64_t *offsets_out, void *stream);
 
+/* Measurement: per-stage device time and kernel launches.  ah_set_profiling
+ * (enable != 0) clears the counters and, from then on, brackets each stage
+ * of each call with CUDA events on the stream the stage runs on.  Stages:
+ * "pack" (ah_load_genomes), "scan", "sort", "decode" (ah_scan), "validate"
+ * (record checks of ah_tm / ah_pair), "tm", "pair", "fetch".  ah_get_profile
+ * returns, for one stage, the summed milliseconds, the kernels launched and
+ * the number of bracketed calls; stage = NULL gives the sums over stages and
+ * the count of every kernel the library launched since the last clear
+ * (counted whether or not profiling is on).  Output pointers may be null. */
+ah_status ah_set_profiling(ah_ctx *ctx, int enable);
+ah_status ah_get_profile(const ah_ctx *ctx, const char *stage, double *ms, uint64_t *launches, uint64_t *calls);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,8 @@ AMPLICON_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("start", "<u4"
 
 # Every symbol include/ampliconhunter.h declares.
 EXPORTS = ["ah_create", "ah_destroy", "ah_last_error", "ah_device_bytes", "ah_load_genomes", "ah_unload_genomes",
-           "ah_set_primers", "ah_set_nn_table", "ah_scan", "ah_tm", "ah_pair", "ah_fetch"]
+           "ah_set_primers", "ah_set_nn_table", "ah_scan", "ah_tm", "ah_pair", "ah_fetch", "ah_set_profiling",
+           "ah_get_profile"]
 
 
 class AHError(RuntimeError):
@@ -86,7 +87,11 @@ def lib():
             "ah_tm": (I32, [P, U32, P, U32, P, U64, P, P, P]),
             "ah_pair": (I32, [P, U32, P, U32, P, P, U64, P, U64, ctypes.POINTER(U64), P]),
             "ah_fetch": (I32, [P, U32, P, U64, P, U64, P, P]),
+            "ah_set_profiling": (I32, [P, I32]),
+            "ah_get_profile": (I32, [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(U64),
+                                     ctypes.POINTER(U64)]),
             "ah_debug_compile_scan": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
+            "ah_debug_scan_source": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -165,6 +170,16 @@ class Context:
 
     def device_bytes(self) -> int:
         return int(self._lib.ah_device_bytes(self.h))
+
+    def ah_set_profiling(self, enable: bool):
+        self._check(self._lib.ah_set_profiling(self.h, 1 if enable else 0))
+
+    def ah_get_profile(self, stage: str | None):
+        """(milliseconds, kernel launches, calls) of one stage, or totals for None."""
+        ms, l, k = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self._lib.ah_get_profile(self.h, stage.encode() if stage else None, ctypes.byref(ms),
+                                             ctypes.byref(l), ctypes.byref(k)))
+        return ms.value, l.value, k.value
 
     def ah_load_genomes(self, seq, n_bases: int, contig_off: np.ndarray, contig_genome: np.ndarray,
                         stream=None) -> int:
@@ -268,3 +283,20 @@ def debug_compile_scan(fwd: str, rev: str, k: int, R: int = 4, arith_pct: int = 
     buf = ctypes.create_string_buffer(1 << 16)
     rc = lib().ah_debug_compile_scan(fwd.encode(), rev.encode(), k, R, arith_pct, order, buf, len(buf))
     return rc == 0, buf.value.decode(errors="replace")
+
+
+def debug_scan_source(fwd: str, rev: str, k: int, R: int = 4, arith_pct: int = 0, order: int = 0) -> str:
+    """The generated CUDA source of one pair's scan kernel."""
+    buf = ctypes.create_string_buffer(1 << 22)
+    rc = lib().ah_debug_scan_source(fwd.encode(), rev.encode(), k, R, arith_pct, order, buf, len(buf))
+    if rc != 0:
+        raise RuntimeError(f"scan source generation failed ({rc})")
+    return buf.value.decode()
+
+
+def scan_lop3_per_word(fwd: str, rev: str, k: int, R: int = 4, arith_pct: int = 0) -> int:
+    """Logic-pipe (LOP3) operations the generated hot loop issues per 32-start
+    word for one pair, counted in its generated source."""
+    src = debug_scan_source(fwd, rev, k, R, arith_pct)
+    hot = src[src.index("u32 h[NPAT * R];"):src.index("__any_sync")]
+    return round(hot.count("lop3<") / R)

@@ -40,6 +40,16 @@ def _compile(src: str, obj: str, extra: list[str]) -> str:
     return r.stderr
 
 
+def source_digest() -> str:
+    """Hash of the library sources (kernels, generator, headers): identifies a build."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INCLUDE, "*.h"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     """Compile what changed and link the library; returns its path."""
     extra = extra or []

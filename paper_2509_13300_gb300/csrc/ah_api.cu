@@ -28,6 +28,24 @@ struct ah_ctx {
     uint64_t *d_counter = nullptr;
     ScanTuning tuning;
     uint64_t key_cap = 1 << 20;
+    // caching allocator: large blocks released by the library are kept for reuse
+    std::map<void *, size_t> live;             // block -> bytes
+    std::multimap<size_t, void *> cached;      // bytes -> block
+    // per-stage profiling (CUDA events on the launching stream)
+    struct Prof {
+        double ms = 0;
+        uint64_t launches = 0, calls = 0;
+    };
+    struct Pending {
+        std::string stage;
+        cudaEvent_t a, b;
+        int launches;
+    };
+    bool profiling = false;
+    std::map<std::string, Prof> prof;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> events;
+    uint64_t launches_total = 0;
 };
 
 namespace {
@@ -35,16 +53,23 @@ namespace {
 std::mutex g_create_mu;
 std::string g_create_err;
 
+void prof_flush(ah_ctx *c);
+
 template <class F> ah_status guarded(ah_ctx *ctx, F &&f)
 {
     try {
         if (ctx)
             AH_CUDA(cudaSetDevice(ctx->device));
         f();
+        if (ctx && !ctx->pending.empty())
+            prof_flush(ctx);
         return AH_OK;
     } catch (const Error &e) {
-        if (ctx)
+        if (ctx) {
             ctx->err = e.msg;
+            if (!ctx->pending.empty())
+                prof_flush(ctx);
+        }
         return e.status;
     } catch (const std::bad_alloc &) {
         if (ctx)
@@ -63,10 +88,34 @@ void require(bool cond, ah_status st, const std::string &msg)
         throw Error(st, msg);
 }
 
+constexpr size_t kCacheMin = 1 << 20; // blocks at least this large are cached on release
+
+void release_cached(ah_ctx *c, size_t need)
+{
+    // free cached blocks (largest first) until `need` more bytes fit the budget
+    while (!c->cached.empty() && (need == SIZE_MAX || (c->budget && c->used + need > c->budget))) {
+        auto it = std::prev(c->cached.end());
+        cudaFree(it->second);
+        c->used -= std::min(c->used, it->first);
+        c->live.erase(it->second);
+        c->cached.erase(it);
+    }
+}
+
 void *dev_alloc(ah_ctx *c, size_t bytes)
 {
     if (bytes == 0)
         bytes = 16;
+    if (bytes >= kCacheMin) { // reuse a cached block of at most twice the size
+        auto it = c->cached.lower_bound(bytes);
+        if (it != c->cached.end() && it->first <= 2 * bytes) {
+            void *p = it->second;
+            c->cached.erase(it);
+            return p;
+        }
+    }
+    if (c->budget && c->used + bytes > c->budget)
+        release_cached(c, bytes);
     if (c->budget && c->used + bytes > c->budget)
         throw Error(AH_ERR_BUDGET, "device-memory budget exceeded: need " + std::to_string(bytes) + " more bytes, " +
                                        std::to_string(c->budget - c->used) + " left");
@@ -74,20 +123,93 @@ void *dev_alloc(ah_ctx *c, size_t bytes)
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        throw Error(AH_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+        release_cached(c, SIZE_MAX);
+        e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error(AH_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+        }
     }
     c->used += bytes;
+    c->live[p] = bytes;
     return p;
 }
 
-void dev_free(ah_ctx *c, void *p, size_t bytes)
+void dev_free(ah_ctx *c, void *p, size_t)
 {
     if (!p)
         return;
+    auto it = c->live.find(p);
+    if (it == c->live.end())
+        return;
+    if (it->second >= kCacheMin) {
+        c->cached.emplace(it->second, p);
+        return;
+    }
     cudaFree(p);
-    if (bytes == 0)
-        bytes = 16;
-    c->used -= std::min(c->used, bytes);
+    c->used -= std::min(c->used, it->second);
+    c->live.erase(it);
+}
+
+cudaEvent_t get_event(ah_ctx *c)
+{
+    if (!c->events.empty()) {
+        cudaEvent_t e = c->events.back();
+        c->events.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    AH_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+// Scope of one pipeline stage: counts its kernel launches and, when
+// profiling, brackets it with events on the launching stream.
+struct Stage {
+    ah_ctx *c;
+    const char *name;
+    cudaStream_t st;
+    int launches;
+    cudaEvent_t a = nullptr;
+    Stage(ah_ctx *c_, const char *n, cudaStream_t s, int l) : c(c_), name(n), st(s), launches(l)
+    {
+        c->launches_total += (uint64_t)l;
+        if (c->profiling) {
+            a = get_event(c);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~Stage()
+    {
+        if (a) {
+            cudaEvent_t b = get_event(c);
+            cudaEventRecord(b, st);
+            c->pending.push_back({name, a, b, launches});
+        }
+    }
+};
+
+// Kernels CUB launches for our calls (sm_100-class tuning): a one-sweep
+// radix sort runs one histogram kernel plus one pass per 8 key bits; a
+// device-wide scan runs an init kernel and a scan kernel.
+int cub_sort_launches(uint64_t n, int bits) { return n <= 1 ? 0 : 1 + (bits + 7) / 8; }
+int cub_scan_launches(uint64_t n) { return n == 0 ? 0 : 2; }
+
+void prof_flush(ah_ctx *c)
+{
+    for (auto &p : c->pending) {
+        float ms = 0;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            auto &q = c->prof[p.stage];
+            q.ms += ms;
+            q.launches += (uint64_t)p.launches;
+            q.calls += 1;
+        }
+        cudaGetLastError();
+        c->events.push_back(p.a);
+        c->events.push_back(p.b);
+    }
+    c->pending.clear();
 }
 
 void *scratch(ah_ctx *c, const std::string &name, size_t bytes)
@@ -381,18 +503,59 @@ void ah_destroy(ah_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream)
         cudaStreamSynchronize(c->stream);
-    for (auto &kv : c->sets) {
-        cudaFree(kv.second->planes);
-        cudaFree(kv.second->contig_off);
-        cudaFree(kv.second->contig_genome);
+    for (auto &kv : c->live)
+        cudaFree(kv.first);
+    for (auto &p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
     }
-    for (auto &kv : c->scratch)
-        cudaFree(kv.second.p);
-    cudaFree(c->d_err);
-    cudaFree(c->d_counter);
+    for (auto e : c->events)
+        cudaEventDestroy(e);
     if (c->stream)
         cudaStreamDestroy(c->stream);
     delete c;
+}
+
+ah_status ah_set_profiling(ah_ctx *c, int enable)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        AH_CUDA(cudaStreamSynchronize(c->stream));
+        prof_flush(c);
+        c->prof.clear();
+        c->launches_total = 0;
+        c->profiling = enable != 0;
+    });
+}
+
+ah_status ah_get_profile(const ah_ctx *c, const char *stage, double *ms, uint64_t *launches, uint64_t *calls)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    double m = 0;
+    uint64_t l = 0, k = 0;
+    if (!stage) {
+        for (auto &kv : c->prof) {
+            m += kv.second.ms;
+            k += kv.second.calls;
+        }
+        l = c->launches_total;
+    } else {
+        auto it = c->prof.find(stage);
+        if (it != c->prof.end()) {
+            m = it->second.ms;
+            l = it->second.launches;
+            k = it->second.calls;
+        }
+    }
+    if (ms)
+        *ms = m;
+    if (launches)
+        *launches = l;
+    if (calls)
+        *calls = k;
+    return AH_OK;
 }
 
 const char *ah_last_error(const ah_ctx *c)
@@ -446,6 +609,7 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
                                 cudaMemcpyHostToDevice, st));
         if (gs->n_tiles) {
             if (is_device_ptr(c, seq)) {
+                Stage sg(c, "pack", st, 1);
                 launch_pack(seq, 0, n_bases, n_bases, gs->planes, 0, gs->n_tiles, st);
             } else {
                 // host sequence: stream it through a staging buffer in tile-aligned chunks;
@@ -458,7 +622,10 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
                     const uint64_t b0 = t0 * kTileBases;
                     const uint64_t b1 = std::min(n_bases, t1 * kTileBases + kTileBases);
                     AH_CUDA(cudaMemcpyAsync(stage, seq + b0, b1 - b0, cudaMemcpyHostToDevice, st));
-                    launch_pack(stage, b0, b1 - b0, n_bases, gs->planes, t0, t1, st);
+                    {
+                        Stage sg(c, "pack", st, 1);
+                        launch_pack(stage, b0, b1 - b0, n_bases, gs->planes, t0, t1, st);
+                    }
                     AH_CUDA(cudaStreamSynchronize(st));
                 }
             }
@@ -572,7 +739,11 @@ ah_status ah_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
                 uint64_t kc = c->key_cap;
                 int pb = pbits;
                 void *args[] = {&planes, &n_tiles, &coff, &nc, &keys, &kc, &c->d_counter, &pb, &c->d_err};
-                AH_CUDA(cudaLaunchKernel((const void *)k->fn, dim3((unsigned)grid), dim3(k->threads), args, k->smem, st));
+                {
+                    Stage sg(c, "scan", st, 1);
+                    AH_CUDA(cudaLaunchKernel((const void *)k->fn, dim3((unsigned)grid), dim3(k->threads), args,
+                                             k->smem, st));
+                }
                 AH_CUDA(cudaMemcpyAsync(&count, c->d_counter, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
                 check_flags(c, st);
                 if (count <= c->key_cap)
@@ -590,9 +761,15 @@ ah_status ah_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
         size_t tb = sort_keys_temp_bytes(count, end_bit);
         void *temp = scratch(c, "sort_temp", tb);
         uint64_t *sorted = (uint64_t *)scratch(c, "scan_keys_sorted", count * sizeof(uint64_t));
-        sort_keys(temp, tb, keys, sorted, count, 8, end_bit, st);
+        {
+            Stage sg(c, "sort", st, cub_sort_launches(count, end_bit - 8));
+            sort_keys(temp, tb, keys, sorted, count, 8, end_bit, st);
+        }
         ah_site *dst = out_buf(c, "sites_out", out, count);
-        launch_decode_keys(sorted, count, pbits, gs.contig_off, gs.n_contigs, gs.contig_genome, dst, st);
+        {
+            Stage sg(c, "decode", st, 1);
+            launch_decode_keys(sorted, count, pbits, gs.contig_off, gs.n_contigs, gs.contig_genome, dst, st);
+        }
         out_finish(out, dst, count, st);
         AH_CUDA(cudaStreamSynchronize(st));
     });
@@ -612,11 +789,17 @@ ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n
             return;
         reset_flags(c, st);
         const ah_site *s = stage_in(c, "tm_sites_in", sites, n, st);
-        launch_validate_sites(s, n, pd, (int)n_pairs, gs.contig_off, gs.n_contigs, c->d_err, st);
+        {
+            Stage sg(c, "validate", st, 1);
+            launch_validate_sites(s, n, pd, (int)n_pairs, gs.contig_off, gs.n_contigs, c->d_err, st);
+        }
         check_flags(c, st);
         float *tm = out_buf(c, "tm_out", tm_out, n);
         uint8_t *ps = pass_out ? out_buf(c, "pass_out", pass_out, n) : nullptr;
-        launch_tm(s, n, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, ps, c->d_err, st);
+        {
+            Stage sg(c, "tm", st, 1);
+            launch_tm(s, n, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, ps, c->d_err, st);
+        }
         out_finish(tm_out, tm, n, st);
         if (pass_out)
             out_finish(pass_out, ps, n, st);
@@ -640,14 +823,20 @@ ah_status ah_pair(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
         reset_flags(c, st);
         const ah_site *s = stage_in(c, "pair_sites_in", sites, n, st);
         const uint8_t *ps = pass ? stage_in(c, "pair_pass_in", pass, n, st) : nullptr;
-        launch_validate_sites(s, n, pd, (int)n_pairs, gs.contig_off, gs.n_contigs, c->d_err, st);
+        {
+            Stage sg(c, "validate", st, 1);
+            launch_validate_sites(s, n, pd, (int)n_pairs, gs.contig_off, gs.n_contigs, c->d_err, st);
+        }
         check_flags(c, st);
         uint64_t *counts = (uint64_t *)scratch(c, "pair_counts", n * sizeof(uint64_t));
         uint64_t *offs = (uint64_t *)scratch(c, "pair_offsets", n * sizeof(uint64_t));
-        launch_pair_count(s, n, ps, pd, counts, st);
         size_t tb = scan_u64_temp_bytes(n);
         void *temp = scratch(c, "scan_temp", tb);
-        exclusive_scan_u64(temp, tb, counts, offs, n, st);
+        {
+            Stage sg(c, "pair", st, 1 + cub_scan_launches(n));
+            launch_pair_count(s, n, ps, pd, counts, st);
+            exclusive_scan_u64(temp, tb, counts, offs, n, st);
+        }
         uint64_t last[2] = {0, 0};
         AH_CUDA(cudaMemcpyAsync(&last[0], offs + n - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         AH_CUDA(cudaMemcpyAsync(&last[1], counts + n - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
@@ -660,7 +849,10 @@ ah_status ah_pair(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
         if (total == 0)
             return;
         ah_amplicon *dst = out_buf(c, "amp_out", out, total);
-        launch_pair_write(s, n, ps, pd, offs, dst, total, st);
+        {
+            Stage sg(c, "pair", st, 1);
+            launch_pair_write(s, n, ps, pd, offs, dst, total, st);
+        }
         out_finish(out, dst, total, st);
         AH_CUDA(cudaStreamSynchronize(st));
     });
@@ -680,11 +872,14 @@ ah_status ah_fetch(ah_ctx *c, uint32_t set_id, const ah_amplicon *amplicons, uin
         uint64_t *len = (uint64_t *)scratch(c, "fetch_len", (n + 1) * sizeof(uint64_t));
         uint64_t *offs = out_buf(c, "fetch_offsets", offsets_out, n + 1);
         AH_CUDA(cudaMemsetAsync(len + n, 0, sizeof(uint64_t), st));
-        launch_fetch_lengths(a, n, gs.contig_off, gs.n_contigs, len, c->d_err, st);
-        check_flags(c, st);
         size_t tb = scan_u64_temp_bytes(n + 1);
         void *temp = scratch(c, "scan_temp", tb);
-        exclusive_scan_u64(temp, tb, len, offs, n + 1, st);
+        {
+            Stage sg(c, "fetch", st, (n ? 1 : 0) + cub_scan_launches(n + 1));
+            launch_fetch_lengths(a, n, gs.contig_off, gs.n_contigs, len, c->d_err, st);
+            exclusive_scan_u64(temp, tb, len, offs, n + 1, st);
+        }
+        check_flags(c, st);
         uint64_t total = 0;
         AH_CUDA(cudaMemcpyAsync(&total, offs + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         out_finish(offsets_out, offs, n + 1, st);
@@ -695,7 +890,10 @@ ah_status ah_fetch(ah_ctx *c, uint32_t set_id, const ah_amplicon *amplicons, uin
         if (total == 0)
             return;
         char *dst = out_buf(c, "fetch_out", seq_out, total);
-        launch_fetch(a, n, offs, gs.planes, gs.contig_off, dst, st);
+        {
+            Stage sg(c, "fetch", st, 1);
+            launch_fetch(a, n, offs, gs.planes, gs.contig_off, dst, st);
+        }
         out_finish(seq_out, dst, total, st);
         AH_CUDA(cudaStreamSynchronize(st));
     });

@@ -430,8 +430,8 @@ ScanKernel *scan_kernel(const std::vector<ScanPattern> &pats, const ScanTuning &
 // Generate and compile (no GPU needed) the scan kernel of one primer pair;
 // writes the NVRTC/ptxas log (register use) into log[0..log_cap).  Returns 0
 // on success.  A development aid; not part of the public header.
-extern "C" int ah_debug_compile_scan(const char *fwd, const char *rev, int k, int R, int arith_pct, int order,
-                                     char *log, size_t log_cap)
+static int debug_scan(const char *fwd, const char *rev, int k, int R, int arith_pct, int order, char *log,
+                      size_t log_cap, bool compile)
 {
     try {
         std::vector<ah::ScanPattern> pats;
@@ -458,7 +458,9 @@ extern "C" int ah_debug_compile_scan(const char *fwd, const char *rev, int k, in
         t.arith_pct = arith_pct;
         t.order = order;
         bool ok = false;
-        std::string l = ah::scan_compile_only(pats, t, &ok);
+        std::string l = compile ? ah::scan_compile_only(pats, t, &ok) : ah::scan_source(pats, t);
+        if (!compile)
+            ok = true;
         if (log && log_cap) {
             size_t n = std::min(log_cap - 1, l.size());
             memcpy(log, l.data(), n);
@@ -470,4 +472,17 @@ extern "C" int ah_debug_compile_scan(const char *fwd, const char *rev, int k, in
             snprintf(log, log_cap, "%s", e.what());
         return 3;
     }
+}
+
+extern "C" int ah_debug_compile_scan(const char *fwd, const char *rev, int k, int R, int arith_pct, int order,
+                                     char *log, size_t log_cap)
+{
+    return debug_scan(fwd, rev, k, R, arith_pct, order, log, log_cap, true);
+}
+
+// The generated source of one pair's scan kernel (development aid).
+extern "C" int ah_debug_scan_source(const char *fwd, const char *rev, int k, int R, int arith_pct, int order,
+                                    char *out, size_t cap)
+{
+    return debug_scan(fwd, rev, k, R, arith_pct, order, out, cap, false);
 }
