@@ -232,7 +232,7 @@ def test_errors_are_reported_not_raised_on_device(ctx):
     with pytest.raises(ah.AHError) as e:
         ctx.ah_scan(sid, [pid], small, n - 1)
     assert e.value.status == ah.AH_ERR_OVERFLOW and e.value.needed == n
-    assert not small.any()
+    assert not small.view(np.uint8).any()
     with pytest.raises(ah.AHError) as e:
         ctx.ah_scan(sid + 100, [pid], None, 0)
     assert e.value.status == ah.AH_ERR_ARG
