@@ -211,6 +211,27 @@ ah_status ah_set_nn_table(ah_ctx *ctx, uint32_t pair_id, const ah_nn_table *tabl
 ah_status ah_scan(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, ah_site *out,
                   uint64_t cap, uint64_t *n_out, void *stream);
 
+/* Variant of the generated scan kernel picked by ah_tune_scan. */
+typedef struct ah_tune_result {
+    int32_t R;          /* 32-start words per thread (threads per block = 1024 / R) */
+    int32_t arith_pct;  /* share of full adders whose sum uses integer adds instead of a LOP3 */
+    int32_t min_blocks; /* occupancy hint given to the compiler */
+    int32_t order;      /* 0 word-major, 1 pattern-major code order */
+    int32_t regs;       /* registers per thread of the chosen variant */
+    int32_t reserved;
+    double us_per_tile; /* measured time per 32768-base tile */
+    uint64_t tiles;     /* tiles in the timed sample */
+} ah_tune_result;
+
+/* Autotuner of the scan (a performance aid; it does not change results):
+ * compiles the candidate variants of the scan kernel specialised to these
+ * pairs, times each on the first sample_tiles tiles of the set (0 = 4096),
+ * and keeps the fastest for every later ah_scan of the same pattern set on
+ * this context.  best_out (host, may be null) receives the choice.
+ * Errors: AH_ERR_ARG, AH_ERR_JIT, AH_ERR_CUDA. */
+ah_status ah_tune_scan(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs,
+                       uint64_t sample_tiles, ah_tune_result *best_out, void *stream);
+
 /* Melting temperature (Sec. 2.1): for each site, the maximum over every
  * oligonucleotide of its primer of the NN Tm (deg C) of that oligo against the
  * template at the site, computed in fp32 (NaN when the template window holds a

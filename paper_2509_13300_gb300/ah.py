@@ -30,7 +30,7 @@ AMPLICON_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("start", "<u4"
 # Every symbol include/ampliconhunter.h declares.
 EXPORTS = ["ah_create", "ah_destroy", "ah_last_error", "ah_device_bytes", "ah_load_genomes", "ah_unload_genomes",
            "ah_set_primers", "ah_set_nn_table", "ah_scan", "ah_tm", "ah_pair", "ah_fetch", "ah_set_profiling",
-           "ah_get_profile", "ah_pair_noalloc"]
+           "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan"]
 
 
 class AHError(RuntimeError):
@@ -49,6 +49,12 @@ class PcrParams(ctypes.Structure):
                 ("dnac2_nM", ctypes.c_double), ("Na_mM", ctypes.c_double), ("K_mM", ctypes.c_double),
                 ("Tris_mM", ctypes.c_double), ("Mg_mM", ctypes.c_double), ("dNTPs_mM", ctypes.c_double),
                 ("saltcorr", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_int32), ("arith_pct", ctypes.c_int32), ("min_blocks", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("regs", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("us_per_tile", ctypes.c_double), ("tiles", ctypes.c_uint64)]
 
 
 class NNTable(ctypes.Structure):
@@ -90,6 +96,7 @@ def lib():
             "ah_set_profiling": (I32, [P, I32]),
             "ah_get_profile": (I32, [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(U64),
                                      ctypes.POINTER(U64)]),
+            "ah_tune_scan": (I32, [P, U32, P, U32, U64, ctypes.POINTER(TuneResult), P]),
             "ah_pair_noalloc": (I32, [P, U32, P, P, U64, P, U64, ctypes.POINTER(U64), P]),
             "ah_debug_compile_scan": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
             "ah_debug_scan_source": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
@@ -209,6 +216,13 @@ class Context:
         st = self._lib.ah_scan(self.h, set_id, _ptr(ids), len(ids), _ptr(out), cap, ctypes.byref(n), _stream(stream))
         self._check(st, n.value)
         return n.value
+
+    def ah_tune_scan(self, set_id: int, pair_ids, sample_tiles: int = 0, stream=None) -> dict:
+        ids = np.ascontiguousarray(pair_ids, dtype=np.uint32)
+        r = TuneResult()
+        self._check(self._lib.ah_tune_scan(self.h, set_id, _ptr(ids), len(ids), sample_tiles, ctypes.byref(r),
+                                           _stream(stream)))
+        return {f: getattr(r, f) for f, _ in TuneResult._fields_ if f != "reserved"}
 
     def ah_tm(self, set_id: int, pair_ids, sites, n: int, tm_out, pass_out=None, stream=None):
         ids = np.ascontiguousarray(pair_ids, dtype=np.uint32)

@@ -26,7 +26,8 @@ struct ah_ctx {
     std::map<std::string, Scratch> scratch;
     int *d_err = nullptr;
     uint64_t *d_counter = nullptr;
-    ScanTuning tuning;
+    ScanTuning tuning;                          // default tuning
+    std::map<std::string, ScanTuning> tuned;    // autotuned, per pattern-set signature
     uint64_t key_cap = 1 << 20;
     // caching allocator: large blocks released by the library are kept for reuse
     std::map<void *, size_t> live;             // block -> bytes
@@ -189,10 +190,11 @@ struct Stage {
     }
 };
 
-// Kernels CUB launches for our calls (sm_100-class tuning): a one-sweep
-// radix sort runs one histogram kernel plus one pass per 8 key bits; a
-// device-wide scan runs an init kernel and a scan kernel.
-int cub_sort_launches(uint64_t n, int bits) { return n <= 1 ? 0 : 1 + (bits + 7) / 8; }
+// Kernels CUB launches for our calls (counted in an ncu launch list on a
+// GB300): a one-sweep radix sort runs a histogram kernel, an exclusive-sum
+// kernel and one pass per 8 key bits; a device-wide scan runs an init kernel
+// and a scan kernel.
+int cub_sort_launches(uint64_t n, int bits) { return n <= 1 ? 0 : 2 + (bits + 7) / 8; }
 int cub_scan_launches(uint64_t n) { return n == 0 ? 0 : 2; }
 
 void prof_flush(ah_ctx *c)
@@ -433,6 +435,36 @@ int bit_length(uint64_t v)
     return b;
 }
 
+std::string signature(const std::vector<ScanPattern> &pats)
+{
+    std::string k;
+    for (auto &p : pats) {
+        k += std::to_string(p.L) + "," + std::to_string(p.k) + "," + std::to_string(p.clamp) + ",";
+        for (int i = 0; i < p.L; ++i)
+            k += (char)('a' + p.mask[i]);
+        k += ";";
+    }
+    return k;
+}
+
+const ScanTuning &tuning_for(ah_ctx *c, const std::vector<ScanPattern> &pats)
+{
+    auto it = c->tuned.find(signature(pats));
+    return it != c->tuned.end() ? it->second : c->tuning;
+}
+
+// Launch the generated scan kernel over tiles [0, n_tiles) of a set.
+void launch_scan(ah_ctx *c, ScanKernel *k, const GenomeSet &gs, uint64_t n_tiles, uint64_t *keys, uint64_t cap,
+                 int pbits, cudaStream_t st)
+{
+    const uint64_t grid = std::min<uint64_t>(n_tiles, (uint64_t)c->sms * k->blocks_per_sm);
+    const uint32_t *planes = gs.planes;
+    const uint64_t *coff = gs.contig_off;
+    uint32_t nc = gs.n_contigs;
+    void *args[] = {&planes, &n_tiles, &coff, &nc, &keys, &cap, &c->d_counter, &pbits, &c->d_err};
+    AH_CUDA(cudaLaunchKernel((const void *)k->fn, dim3((unsigned)grid), dim3(k->threads), args, k->smem, st));
+}
+
 std::vector<ScanPattern> patterns_of(ah_ctx *c, const uint32_t *pair_ids, uint32_t n_pairs)
 {
     std::vector<ScanPattern> pats;
@@ -607,10 +639,11 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
                                 cudaMemcpyHostToDevice, st));
         AH_CUDA(cudaMemcpyAsync(gs->contig_genome, gs->contig_genome_h.data(), n_contigs * sizeof(uint32_t),
                                 cudaMemcpyHostToDevice, st));
+        reset_flags(c, st);
         if (gs->n_tiles) {
             if (is_device_ptr(c, seq)) {
                 Stage sg(c, "pack", st, 1);
-                launch_pack(seq, 0, n_bases, n_bases, gs->planes, 0, gs->n_tiles, st);
+                launch_pack(seq, 0, n_bases, n_bases, gs->planes, 0, gs->n_tiles, c->d_err, st);
             } else {
                 // host sequence: stream it through a staging buffer in tile-aligned chunks;
                 // each chunk also carries the first bytes of the next tile (extension words)
@@ -624,13 +657,13 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
                     AH_CUDA(cudaMemcpyAsync(stage, seq + b0, b1 - b0, cudaMemcpyHostToDevice, st));
                     {
                         Stage sg(c, "pack", st, 1);
-                        launch_pack(stage, b0, b1 - b0, n_bases, gs->planes, t0, t1, st);
+                        launch_pack(stage, b0, b1 - b0, n_bases, gs->planes, t0, t1, c->d_err, st);
                     }
                     AH_CUDA(cudaStreamSynchronize(st));
                 }
             }
         }
-        AH_CUDA(cudaStreamSynchronize(st));
+        check_flags(c, st);
         uint32_t id = c->next_set++;
         c->sets[id] = std::move(gs);
         *set_id_out = id;
@@ -727,22 +760,13 @@ ah_status ah_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
         uint64_t count = 0;
         uint64_t *keys = nullptr;
         if (gs.n_tiles) {
-            ScanKernel *k = scan_kernel(pats, c->tuning, c->device);
+            ScanKernel *k = scan_kernel(pats, tuning_for(c, pats), c->device);
             for (int attempt = 0; attempt < 2; ++attempt) {
                 keys = (uint64_t *)scratch(c, "scan_keys", c->key_cap * sizeof(uint64_t));
                 reset_flags(c, st);
-                const uint64_t grid = std::min<uint64_t>(gs.n_tiles, (uint64_t)c->sms * k->blocks_per_sm);
-                const uint32_t *planes = gs.planes;
-                uint64_t n_tiles = gs.n_tiles;
-                const uint64_t *coff = gs.contig_off;
-                uint32_t nc = gs.n_contigs;
-                uint64_t kc = c->key_cap;
-                int pb = pbits;
-                void *args[] = {&planes, &n_tiles, &coff, &nc, &keys, &kc, &c->d_counter, &pb, &c->d_err};
                 {
                     Stage sg(c, "scan", st, 1);
-                    AH_CUDA(cudaLaunchKernel((const void *)k->fn, dim3((unsigned)grid), dim3(k->threads), args,
-                                             k->smem, st));
+                    launch_scan(c, k, gs, gs.n_tiles, keys, c->key_cap, pbits, st);
                 }
                 AH_CUDA(cudaMemcpyAsync(&count, c->d_counter, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
                 check_flags(c, st);
@@ -772,6 +796,78 @@ ah_status ah_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
         }
         out_finish(out, dst, count, st);
         AH_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+ah_status ah_tune_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, uint64_t sample_tiles,
+                       ah_tune_result *best_out, void *stream)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require(pair_ids && n_pairs >= 1 && n_pairs <= AH_MAX_PAIRS_PER_SCAN, AH_ERR_ARG, "n_pairs must be 1..16");
+        GenomeSet &gs = get_set(c, set_id);
+        cudaStream_t st = stream_of(c, stream);
+        std::vector<ScanPattern> pats = patterns_of(c, pair_ids, n_pairs);
+        const int pbits = std::max(1, bit_length(gs.n_bases));
+        uint64_t tiles = std::min<uint64_t>(gs.n_tiles, sample_tiles ? sample_tiles : 4096);
+        require(tiles > 0, AH_ERR_ARG, "ah_tune_scan: empty genome set");
+        // the sample must cover whole waves of the persistent grid to time it fairly
+        std::vector<ScanTuning> cand;
+        for (int R : {4, 8})
+            for (int ap : {0, 25, 50})
+                for (int order : {0, 1}) {
+                    ScanTuning t;
+                    t.R = R;
+                    t.arith_pct = ap;
+                    t.order = order;
+                    t.min_blocks = 1;
+                    cand.push_back(t);
+                }
+        cudaEvent_t e0 = get_event(c), e1 = get_event(c);
+        double best_us = 1e30;
+        ScanTuning best = c->tuning;
+        int best_regs = -1;
+        for (const ScanTuning &t : cand) {
+            ScanKernel *k = nullptr;
+            try {
+                k = scan_kernel(pats, t, c->device);
+            } catch (const Error &) {
+                continue; // a variant that does not compile is skipped
+            }
+            uint64_t *keys = (uint64_t *)scratch(c, "scan_keys", c->key_cap * sizeof(uint64_t));
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 4; ++rep) {
+                reset_flags(c, st);
+                AH_CUDA(cudaEventRecord(e0, st));
+                launch_scan(c, k, gs, tiles, keys, c->key_cap, pbits, st);
+                AH_CUDA(cudaEventRecord(e1, st));
+                AH_CUDA(cudaEventSynchronize(e1));
+                float ms = 0;
+                AH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep > 0)
+                    ms_min = std::min(ms_min, ms);
+            }
+            check_flags(c, st);
+            const double us = ms_min * 1e3 / (double)tiles;
+            if (us < best_us) {
+                best_us = us;
+                best = t;
+                best_regs = k->regs;
+            }
+        }
+        c->events.push_back(e0);
+        c->events.push_back(e1);
+        c->tuned[signature(pats)] = best;
+        if (best_out) {
+            best_out->R = best.R;
+            best_out->arith_pct = best.arith_pct;
+            best_out->min_blocks = best.min_blocks;
+            best_out->order = best.order;
+            best_out->regs = best_regs;
+            best_out->us_per_tile = best_us;
+            best_out->tiles = tiles;
+        }
     });
 }
 

@@ -133,7 +133,7 @@ ScanKernel *scan_kernel(const std::vector<ScanPattern> &pats, const ScanTuning &
 // pack.cu: pack tiles [t0, t1) from seq, which holds flat positions
 // [seq_base, seq_base + seq_len) of a set of n_bases bases.
 void launch_pack(const uint8_t *seq, uint64_t seq_base, uint64_t seq_len, uint64_t n_bases, uint32_t *planes,
-                 uint64_t t0, uint64_t t1, cudaStream_t s);
+                 uint64_t t0, uint64_t t1, int *err, cudaStream_t s);
 void launch_unpack_check(const uint32_t *planes, uint64_t n_tiles, uint8_t *codes, uint64_t n_bases,
                          cudaStream_t s);
 

@@ -55,6 +55,45 @@ template <int IMM> __device__ __forceinline__ u32 lop3(u32 a, u32 b, u32 c)
     asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(IMM));
     return d;
 }
+__device__ __forceinline__ u32 smem_addr(const void *p) { return (u32)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(u64 *bar, u32 count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// one thread: expect `bytes` on the barrier, then start the bulk copy that delivers them
+__device__ __forceinline__ void tma_load(void *dst, const void *src, u32 bytes, u64 *bar)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(u64 *bar, u32 parity)
+{
+    u32 ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ u64 global_ns()
+{
+    u64 t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait for a barrier phase: gives up after ~2 s instead of hanging
+__device__ __forceinline__ bool mbar_wait(u64 *bar, u32 parity)
+{
+    if (mbar_try(bar, parity))
+        return true;
+    const u64 t0 = global_ns();
+    while (!mbar_try(bar, parity))
+        if (global_ns() - t0 > 2000000000ull)
+            return false;
+    return true;
+}
 )CUDA";
 
 // Body of the kernel after the generated hit words.  Uses: h[NPAT*R] (hit
@@ -310,14 +349,34 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "ah_scan_kernel(const u32 *__restrict__ planes, u64 n_tiles, const u64 *__restrict__ contig_off,\n"
        << "               u32 n_contigs, u64 *__restrict__ keys, u64 cap, u64 *__restrict__ counter, int pbits,\n"
        << "               int *__restrict__ err)\n{\n"
-       << "  extern __shared__ __align__(16) u32 sm[];\n"
-       << "  for (u64 tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {\n"
-       << "    {\n"
-       << "      const uint4 *src = reinterpret_cast<const uint4 *>(planes + tile * 4 * WX);\n"
-       << "      uint4 *dst = reinterpret_cast<uint4 *>(sm);\n"
-       << "      for (int i = threadIdx.x; i < WX; i += NT) dst[i] = __ldg(src + i);\n"
+       << "  // two tile buffers filled by bulk async copies (TMA), one mbarrier each\n"
+       << "  extern __shared__ __align__(128) u32 smbuf[];\n"
+       << "  __shared__ __align__(8) u64 bar[2];\n"
+       << "  const u32 TILE_BYTES = 4u * WX * 4u;\n"
+       << "  if (threadIdx.x == 0) {\n"
+       << "    mbar_init(&bar[0], 1);\n"
+       << "    mbar_init(&bar[1], 1);\n"
+       << "    asm volatile(\"fence.mbarrier_init.release.cluster;\" ::: \"memory\");\n"
+       << "  }\n"
+       << "  __syncthreads();\n"
+       << "  if (threadIdx.x == 0 && (u64)blockIdx.x < n_tiles)\n"
+       << "    tma_load(smbuf, planes + (u64)blockIdx.x * 4 * WX, TILE_BYTES, &bar[0]);\n"
+       << "  int it = 0;\n"
+       << "  for (u64 tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {\n"
+       << "    const int sb = it & 1;\n"
+       << "    const u64 next = tile + gridDim.x;\n"
+       << "    if (threadIdx.x == 0 && next < n_tiles)\n"
+       << "      tma_load(smbuf + (sb ^ 1) * 4 * WX, planes + next * 4 * WX, TILE_BYTES, &bar[sb ^ 1]);\n"
+       << "    const bool ok = mbar_wait(&bar[sb], (u32)((it >> 1) & 1));\n"
+       << "    if (!__syncthreads_and(ok)) {\n"
+       << "      // the copy never landed: report, wait (bounded) for the copy still in flight, leave\n"
+       << "      if (threadIdx.x == 0) {\n"
+       << "        atomicExch(err, 1);\n"
+       << "        if (next < n_tiles) mbar_wait(&bar[sb ^ 1], (u32)(((it + 1) >> 1) & 1));\n"
+       << "      }\n"
+       << "      break;\n"
        << "    }\n"
-       << "    __syncthreads();\n"
+       << "    const u32 *sm = smbuf + sb * 4 * WX;\n"
        << "    const int j0 = threadIdx.x * R;\n"
        << "    u32 pA[NWIN], pC[NWIN], pG[NWIN], pT[NWIN], pV[NWIN];\n"
        << "#pragma unroll\n"
@@ -413,7 +472,7 @@ ScanKernel *scan_kernel(const std::vector<ScanPattern> &pats, const ScanTuning &
     AH_CUDA(cudaLibraryLoadData(&k->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
     AH_CUDA(cudaLibraryGetKernel(&k->fn, k->lib, "ah_scan_kernel"));
     k->threads = kTileW / t.R;
-    k->smem = kTileBytes;
+    k->smem = 2 * kTileBytes; // double-buffered tiles
     auto pos = log.find("Used ");
     if (pos != std::string::npos)
         k->regs = atoi(log.c_str() + pos + 5);

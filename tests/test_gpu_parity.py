@@ -271,3 +271,20 @@ def test_empty_and_degenerate_sets(ctx):
     sid = ctx.ah_load_genomes(seq, len(seq), off, np.array([0, 0, 1, 1], np.uint32))
     assert ctx.ah_scan(sid, [pid], None, 0) == 0
     ctx.ah_unload_genomes(sid)
+
+
+def test_pack_classifies_every_byte_value(ctx):
+    """All 256 byte values, at every offset within a 4-byte word and across
+    tile boundaries: exactly A/C/G/T in either case are bases, all else N."""
+    rng = np.random.default_rng(3)
+    vals = np.tile(np.arange(256, dtype=np.uint8), 600)
+    seq = np.concatenate([vals, rng.permutation(vals), np.frombuffer(b"ACGTacgtN" * 5000, np.uint8)])
+    off = np.array([0, 70_001, len(seq)], np.uint64)  # a contig boundary inside a word
+    sid = ctx.ah_load_genomes(seq, len(seq), off, np.array([0, 1], np.uint32))
+    amps = np.zeros(2, dtype=ah.AMPLICON_DTYPE)
+    amps["contig"] = [0, 1]
+    amps["end"] = [70_001, len(seq) - 70_001]
+    got, goff = ctx.fetch(sid, amps)
+    want, woff = oracle.fetch(seq, off, amps)
+    ctx.ah_unload_genomes(sid)
+    assert np.array_equal(goff, woff) and got == want
