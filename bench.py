@@ -242,8 +242,9 @@ def main():
     ctx = ah.Context(local)
     pid = ctx.ah_set_primers(p["fwd"], p["rev"], p)
 
-    # capacities from one warm-up pass (also compiles the generated scan kernel)
+    # capacities from one warm-up pass (also compiles and tunes the generated scan kernel)
     sid = ctx.ah_load_genomes(seq_d, n_bases, w.contig_off, w.contig_genome, stream)
+    tune = ctx.ah_tune_scan(sid, [pid], 0, stream)
     sites = ctx.scan(sid, [pid])
     tm, ps = ctx.tm(sid, [pid], sites)
     amps = ctx.pair(sid, [pid], sites, ps)
@@ -302,7 +303,7 @@ def main():
     scan_hbm = 0.5 * n_bases / (scan_us * 1e-6) / 1e9  # 4 planes x 1 bit per base
     pack_hbm = 1.5 * n_bases / (pack_us * 1e-6) / 1e9  # 1 B/base read + 0.5 B/base written
     # logic-pipe ops of the generated scan kernel per launch (static count of its LOP3s per word)
-    lop_per_word = ctx_scan_lop_count(p)
+    lop_per_word = ctx_scan_lop_count(p, tune)
     words = n_bases / 32.0
     scan_tops = lop_per_word * words / (scan_us * 1e-6) / 1e12
     clk_mhz = clocks["sm_mhz"] or 2070.0
@@ -370,6 +371,7 @@ def main():
         "config": {"workload": WORKLOAD, "n_bases_per_gpu": n_bases, "n_contigs": w.n_contigs, "pairs": 1,
                    "oligos": 960, "k": 3, "window": [100, 2500], "tm_min_C": 50.0, "tm_dtype": "f32",
                    "sites": int(n), "amplicons": int(m), "parallelism": f"replicas x{world}",
+                   "scan_tuning": tune,
                    "l2": "inputs larger than L2 (0.4 GB ASCII + 0.2 GB planes per step)"},
         "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99))},
         "stages": stages, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
@@ -379,11 +381,11 @@ def main():
     ctx.close()
 
 
-def ctx_scan_lop_count(pair: dict) -> int:
-    """LOP3 instructions the generated scan kernel issues per word (32 starts)
-    for this pair: counted from the generated source."""
+def ctx_scan_lop_count(pair: dict, tune: dict) -> int:
+    """LOP3 instructions the generated scan kernel (the tuned variant) issues
+    per word of 32 starts for this pair: counted in its generated source."""
     from paper_2509_13300_gb300 import ah
-    return ah.scan_lop3_per_word(pair["fwd"], pair["rev"], int(pair["k"]))
+    return ah.scan_lop3_per_word(pair["fwd"], pair["rev"], int(pair["k"]), tune["R"], tune["arith_pct"])
 
 
 if __name__ == "__main__":
