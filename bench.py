@@ -245,27 +245,27 @@ def main():
     # capacities from one warm-up pass (also compiles and tunes the generated scan kernel)
     sid = ctx.ah_load_genomes(seq_d, n_bases, w.contig_off, w.contig_genome, stream)
     tune = ctx.ah_tune_scan(sid, [pid], 0, stream)
-    sites = ctx.scan(sid, [pid])
-    tm, ps = ctx.tm(sid, [pid], sites)
-    amps = ctx.pair(sid, [pid], sites, ps)
-    seqs, offs = ctx.fetch(sid, amps)
+    r = ctx.run(sid, [pid], tm_filter=True)
     ctx.ah_unload_genomes(sid)
-    cap_s, cap_a, cap_q = len(sites) + 1, len(amps) + 1, len(seqs) + 1
-    sites_d = torch.empty(cap_s * 16, dtype=torch.uint8, device="cuda")
-    tm_d = torch.empty(cap_s, dtype=torch.float32, device="cuda")
-    ps_d = torch.empty(cap_s, dtype=torch.uint8, device="cuda")
-    amps_d = torch.empty(cap_a * 28, dtype=torch.uint8, device="cuda")
-    seq_out_d = torch.empty(cap_q, dtype=torch.uint8, device="cuda")
-    offs_d = torch.empty(cap_a + 1, dtype=torch.int64, device="cuda")
+    cap_s, cap_a, cap_q = len(r["sites"]) + 1, len(r["amps"]) + 1, len(r["seqs"]) + 1
+
+    def run_out(dev: str, pinned: bool):
+        def buf(n, dt):
+            t = torch.empty(n, dtype=dt, device=dev)
+            return t.pin_memory() if pinned else t
+        b = dict(sites=buf(cap_s * 16, torch.uint8), tm=buf(cap_s, torch.float32), ps=buf(cap_s, torch.uint8),
+                 amps=buf(cap_a * 28, torch.uint8), seq=buf(cap_q, torch.uint8), offs=buf(cap_a + 1, torch.int64))
+        o = ah.RunOut(b["sites"].data_ptr(), cap_s, 0, b["tm"].data_ptr(), b["ps"].data_ptr(), b["amps"].data_ptr(),
+                      cap_a, 0, b["seq"].data_ptr(), cap_q, 0, b["offs"].data_ptr(), 1, 0)
+        return o, b
+
+    out_d, bufs_d = run_out("cuda", False)
 
     def step_device():
         sid = ctx.ah_load_genomes(seq_d, n_bases, w.contig_off, w.contig_genome, stream)
-        n = ctx.ah_scan(sid, [pid], sites_d, cap_s, stream)
-        ctx.ah_tm(sid, [pid], sites_d, n, tm_d, ps_d, stream)
-        m = ctx.ah_pair(sid, [pid], sites_d, ps_d, n, amps_d, cap_a, stream)
-        ctx.ah_fetch(sid, amps_d, m, seq_out_d, cap_q, offs_d, stream)
+        ctx.ah_run(sid, [pid], out_d, stream)
         ctx.ah_unload_genomes(sid)
-        return n, m
+        return out_d.n_sites, out_d.n_amplicons
 
     for _ in range(args.warmup):
         step_device()
@@ -328,23 +328,15 @@ def main():
 
     # ---- end to end through the public API with host (pinned) buffers ----
     seq_h = torch.from_numpy(w.seq).pin_memory()
-    sites_h = torch.empty(cap_s * 16, dtype=torch.uint8).pin_memory()
-    tm_h = torch.empty(cap_s, dtype=torch.float32).pin_memory()
-    ps_h = torch.empty(cap_s, dtype=torch.uint8).pin_memory()
-    amps_h = torch.empty(cap_a * 28, dtype=torch.uint8).pin_memory()
-    seq_out_h = torch.empty(cap_q, dtype=torch.uint8).pin_memory()
-    offs_h = torch.empty(cap_a + 1, dtype=torch.int64).pin_memory()
+    out_h, bufs_h = run_out("cpu", True)
 
     def step_host():
         sid = ctx.ah_load_genomes(seq_h, n_bases, w.contig_off, w.contig_genome, stream)
-        n = ctx.ah_scan(sid, [pid], sites_h, cap_s, stream)
-        ctx.ah_tm(sid, [pid], sites_h, n, tm_h, ps_h, stream)
-        m = ctx.ah_pair(sid, [pid], sites_h, ps_h, n, amps_h, cap_a, stream)
-        ctx.ah_fetch(sid, amps_h, m, seq_out_h, cap_q, offs_h, stream)
+        ctx.ah_run(sid, [pid], out_h, stream)
         ctx.ah_unload_genomes(sid)
-        q = int(offs_h[m].item())
-        h2d = n_bases + w.contig_off.nbytes + w.contig_genome.nbytes + 2 * 16 * n + n + 28 * m
-        d2h = 16 * n + 5 * n + 28 * m + q + 8 * (m + 1)
+        n, m, q = out_h.n_sites, out_h.n_amplicons, out_h.n_seq
+        h2d = n_bases + w.contig_off.nbytes + w.contig_genome.nbytes
+        d2h = 16 * n + 4 * n + n + 28 * m + q + 8 * (m + 1)
         return h2d, d2h
 
     step_host()

@@ -265,6 +265,39 @@ ah_status ah_pair(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32
 ah_status ah_fetch(ah_ctx *ctx, uint32_t set_id, const ah_amplicon *amplicons, uint64_t n, char *seq_out,
                    uint64_t cap, uint64_t *offsets_out, void *stream);
 
+/* Outputs of ah_run.  The caller sets the buffers and capacities (host or
+ * device memory, any may be null with capacity 0); ah_run fills the counts.
+ * tm and pass hold n_sites entries (capacity sites_cap); seq_offsets holds
+ * n_amplicons + 1 entries (capacity amplicons_cap + 1). */
+typedef struct ah_run_out {
+    ah_site *sites;
+    uint64_t sites_cap;
+    uint64_t n_sites;
+    float *tm;
+    uint8_t *pass;
+    ah_amplicon *amplicons;
+    uint64_t amplicons_cap;
+    uint64_t n_amplicons;
+    char *seq;
+    uint64_t seq_cap;
+    uint64_t n_seq;
+    uint64_t *seq_offsets;
+    int32_t tm_filter; /* 1: amplicons only from sites whose Tm passes (Sec. 2.1: filter, then pair) */
+    int32_t reserved;
+} ah_run_out;
+
+/* The whole hot path of Sec. 2.1 in one call: primer matching (as ah_scan),
+ * the Tm of every site with pass flags (as ah_tm), amplicon calling on the
+ * sites (as ah_pair; with tm_filter only sites that pass) and the amplicon
+ * sequences (as ah_fetch), for the listed pairs on one loaded set.  The
+ * results are identical to that sequence of calls; only the number of host
+ * synchronisations differs (four).  An output whose capacity is too small is
+ * not written, its count is still reported, the others are written, and the
+ * call returns AH_ERR_OVERFLOW.
+ * Errors: AH_ERR_ARG, AH_ERR_OVERFLOW, AH_ERR_JIT, AH_ERR_TIMEOUT, AH_ERR_CUDA. */
+ah_status ah_run(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, ah_run_out *out,
+                 void *stream);
+
 /* Measurement: per-stage device time and kernel launches.  ah_set_profiling
  * (enable != 0) clears the counters and, from then on, brackets each stage
  * of each call with CUDA events on the stream the stage runs on.  Stages:

@@ -30,7 +30,7 @@ AMPLICON_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("start", "<u4"
 # Every symbol include/ampliconhunter.h declares.
 EXPORTS = ["ah_create", "ah_destroy", "ah_last_error", "ah_device_bytes", "ah_load_genomes", "ah_unload_genomes",
            "ah_set_primers", "ah_set_nn_table", "ah_scan", "ah_tm", "ah_pair", "ah_fetch", "ah_set_profiling",
-           "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan"]
+           "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan", "ah_run"]
 
 
 class AHError(RuntimeError):
@@ -55,6 +55,15 @@ class TuneResult(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int32), ("arith_pct", ctypes.c_int32), ("min_blocks", ctypes.c_int32),
                 ("order", ctypes.c_int32), ("regs", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("us_per_tile", ctypes.c_double), ("tiles", ctypes.c_uint64)]
+
+
+class RunOut(ctypes.Structure):
+    """ah_run_out: caller-set buffers/capacities; the call fills the n_* counts."""
+    _fields_ = [("sites", ctypes.c_void_p), ("sites_cap", ctypes.c_uint64), ("n_sites", ctypes.c_uint64),
+                ("tm", ctypes.c_void_p), ("pass_", ctypes.c_void_p),
+                ("amplicons", ctypes.c_void_p), ("amplicons_cap", ctypes.c_uint64), ("n_amplicons", ctypes.c_uint64),
+                ("seq", ctypes.c_void_p), ("seq_cap", ctypes.c_uint64), ("n_seq", ctypes.c_uint64),
+                ("seq_offsets", ctypes.c_void_p), ("tm_filter", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class NNTable(ctypes.Structure):
@@ -96,6 +105,7 @@ def lib():
             "ah_set_profiling": (I32, [P, I32]),
             "ah_get_profile": (I32, [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(U64),
                                      ctypes.POINTER(U64)]),
+            "ah_run": (I32, [P, U32, P, U32, ctypes.POINTER(RunOut), P]),
             "ah_tune_scan": (I32, [P, U32, P, U32, U64, ctypes.POINTER(TuneResult), P]),
             "ah_pair_noalloc": (I32, [P, U32, P, P, U64, P, U64, ctypes.POINTER(U64), P]),
             "ah_debug_compile_scan": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
@@ -216,6 +226,36 @@ class Context:
         st = self._lib.ah_scan(self.h, set_id, _ptr(ids), len(ids), _ptr(out), cap, ctypes.byref(n), _stream(stream))
         self._check(st, n.value)
         return n.value
+
+    def ah_run(self, set_id: int, pair_ids, out: RunOut, stream=None) -> RunOut:
+        ids = np.ascontiguousarray(pair_ids, dtype=np.uint32)
+        st = self._lib.ah_run(self.h, set_id, _ptr(ids), len(ids), ctypes.byref(out), _stream(stream))
+        self._check(st, out.n_sites)
+        return out
+
+    def run(self, set_id: int, pair_ids, tm_filter: bool = True, caps=(0, 0, 0)) -> dict:
+        """The whole path into numpy arrays (host buffers).  caps are capacity
+        hints (sites, amplicons, sequence bytes); when too small the call is
+        repeated with the reported counts."""
+        for _ in range(2):
+            sites = np.zeros(max(caps[0], 1), dtype=SITE_DTYPE)
+            tm = np.zeros(max(caps[0], 1), dtype=np.float32)
+            ps = np.zeros(max(caps[0], 1), dtype=np.uint8)
+            amps = np.zeros(max(caps[1], 1), dtype=AMPLICON_DTYPE)
+            seq = np.zeros(max(caps[2], 1), dtype=np.uint8)
+            offs = np.zeros(max(caps[1], 1) + 1, dtype=np.uint64)
+            o = RunOut(sites.ctypes.data, caps[0], 0, tm.ctypes.data, ps.ctypes.data, amps.ctypes.data, caps[1], 0,
+                       seq.ctypes.data, caps[2], 0, offs.ctypes.data, 1 if tm_filter else 0, 0)
+            ids = np.ascontiguousarray(pair_ids, dtype=np.uint32)
+            st = self._lib.ah_run(self.h, set_id, _ptr(ids), len(ids), ctypes.byref(o), None)
+            if st == AH_OK:
+                n, m, q = o.n_sites, o.n_amplicons, o.n_seq
+                return dict(sites=sites[:n], tm=tm[:n], pass_=ps[:n], amps=amps[:m], seqs=seq[:q].tobytes(),
+                            offs=offs[:m + 1])
+            if st != AH_ERR_OVERFLOW:
+                self._check(st)
+            caps = (o.n_sites, o.n_amplicons, o.n_seq)
+        raise AHError(AH_ERR_OVERFLOW, "ah_run: counts changed between calls")
 
     def ah_tune_scan(self, set_id: int, pair_ids, sample_tiles: int = 0, stream=None) -> dict:
         ids = np.ascontiguousarray(pair_ids, dtype=np.uint32)

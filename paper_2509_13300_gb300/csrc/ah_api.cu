@@ -24,8 +24,13 @@ struct ah_ctx {
     std::map<uint32_t, PrimerPair> pairs;
     uint32_t next_pair = 1;
     std::map<std::string, Scratch> scratch;
-    int *d_err = nullptr;
+    // device flag block: [0] hit counter, [1] auxiliary total, [2] error word
+    uint64_t *d_flags = nullptr;
     uint64_t *d_counter = nullptr;
+    uint64_t *d_aux = nullptr;
+    int *d_err = nullptr;
+    uint64_t *h_flags = nullptr;     // pinned host mirror of the flag block
+    std::vector<PairDev> pairdev_h;  // host source of the last per-pair upload
     ScanTuning tuning;                          // default tuning
     std::map<std::string, ScanTuning> tuned;    // autotuned, per pattern-set signature
     uint64_t key_cap = 1 << 20;
@@ -275,15 +280,16 @@ template <class T> void out_finish(T *user, T *dev, uint64_t count, cudaStream_t
 
 void reset_flags(ah_ctx *c, cudaStream_t st)
 {
-    AH_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
-    AH_CUDA(cudaMemsetAsync(c->d_counter, 0, sizeof(uint64_t), st));
+    AH_CUDA(cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(uint64_t), st));
 }
 
+// One device->host copy of the flag block and one synchronisation; raises on
+// a device-reported error.  h_flags[0] = counter, h_flags[1] = aux total.
 void check_flags(ah_ctx *c, cudaStream_t st)
 {
-    int e = 0;
-    AH_CUDA(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    AH_CUDA(cudaMemcpyAsync(c->h_flags, c->d_flags, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     AH_CUDA(cudaStreamSynchronize(st));
+    const int e = (int)(c->h_flags[2] & 0xffffffffu);
     if (e == kDevTimeout)
         throw Error(AH_ERR_TIMEOUT, "a device-side wait ran out of iterations");
     if (e == kDevBounds)
@@ -415,13 +421,12 @@ const PairDev *upload_pairs(ah_ctx *c, const uint32_t *pair_ids, uint32_t n_pair
 {
     require(pair_ids != nullptr, AH_ERR_ARG, "pair_ids is null");
     require(n_pairs >= 1 && n_pairs <= AH_MAX_PAIRS_PER_SCAN, AH_ERR_ARG, "n_pairs must be 1..16");
-    std::vector<PairDev> h(n_pairs);
+    c->pairdev_h.resize(n_pairs);
     for (uint32_t j = 0; j < n_pairs; ++j)
-        h[j] = make_pair_dev(get_pair(c, pair_ids[j]));
+        c->pairdev_h[j] = make_pair_dev(get_pair(c, pair_ids[j]));
     PairDev *d = (PairDev *)scratch(c, "pairdev", n_pairs * sizeof(PairDev));
-    AH_CUDA(cudaMemcpyAsync(d, h.data(), n_pairs * sizeof(PairDev), cudaMemcpyHostToDevice, st));
-    // the host copy must outlive the async copy
-    AH_CUDA(cudaStreamSynchronize(st));
+    // the source stays alive in the context: every call synchronises before it returns
+    AH_CUDA(cudaMemcpyAsync(d, c->pairdev_h.data(), n_pairs * sizeof(PairDev), cudaMemcpyHostToDevice, st));
     return d;
 }
 
@@ -489,6 +494,79 @@ std::vector<ScanPattern> patterns_of(ah_ctx *c, const uint32_t *pair_ids, uint32
 
 } // namespace
 
+namespace {
+
+// ---- stages shared by ah_scan and ah_run ----
+
+// Scan kernel over the whole set; keys land in the "scan_keys" scratch.
+// Returns the number of sites (one synchronisation; rerun once with a
+// larger key buffer if it overflowed).
+uint64_t scan_keys(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPattern> &pats, uint64_t **keys_out,
+                   cudaStream_t st)
+{
+    const int pbits = std::max(1, bit_length(gs.n_bases));
+    uint64_t count = 0;
+    *keys_out = nullptr;
+    if (!gs.n_tiles)
+        return 0;
+    ScanKernel *k = scan_kernel(pats, tuning_for(c, pats), c->device);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        uint64_t *keys = (uint64_t *)scratch(c, "scan_keys", c->key_cap * sizeof(uint64_t));
+        reset_flags(c, st);
+        {
+            Stage sg(c, "scan", st, 1);
+            launch_scan(c, k, gs, gs.n_tiles, keys, c->key_cap, pbits, st);
+        }
+        check_flags(c, st);
+        count = c->h_flags[0];
+        *keys_out = keys;
+        if (count <= c->key_cap)
+            break;
+        c->key_cap = count;
+    }
+    return count;
+}
+
+// Sort keys into canonical order and decode them into site records.
+void sort_decode(ah_ctx *c, const GenomeSet &gs, uint32_t n_pairs, const uint64_t *keys, uint64_t count, ah_site *dst,
+                 cudaStream_t st)
+{
+    const int pbits = std::max(1, bit_length(gs.n_bases));
+    const int end_bit = 10 + pbits + bit_length(n_pairs - 1);
+    size_t tb = sort_keys_temp_bytes(count, end_bit);
+    void *temp = scratch(c, "sort_temp", tb);
+    uint64_t *sorted = (uint64_t *)scratch(c, "scan_keys_sorted", count * sizeof(uint64_t));
+    {
+        Stage sg(c, "sort", st, cub_sort_launches(count, end_bit - 8));
+        sort_keys(temp, tb, keys, sorted, count, 8, end_bit, st);
+    }
+    {
+        Stage sg(c, "decode", st, 1);
+        launch_decode_keys(sorted, count, pbits, gs.contig_off, gs.n_contigs, gs.contig_genome, dst, st);
+    }
+}
+
+// Buffer for an output of `count` records: the caller's own device buffer
+// when it is on this device and large enough, else a scratch buffer.
+template <class T> T *direct_or_scratch(ah_ctx *c, const char *name, T *user, uint64_t cap, uint64_t count)
+{
+    if (user && count <= cap && is_device_ptr(c, user))
+        return user;
+    return (T *)scratch(c, name, std::max<uint64_t>(count, 1) * sizeof(T));
+}
+
+// Copy a finished output to the caller's buffer when it was not written in place.
+template <class T> bool deliver(T *user, uint64_t cap, const T *dev, uint64_t count, cudaStream_t st)
+{
+    if (count > cap)
+        return false; // overflow: nothing written
+    if (user && count && user != dev)
+        AH_CUDA(cudaMemcpyAsync(user, dev, count * sizeof(T), cudaMemcpyDefault, st));
+    return true;
+}
+
+} // namespace
+
 // ===========================================================================
 extern "C" {
 
@@ -516,8 +594,11 @@ ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
     ah_status st = guarded(c, [&] {
         AH_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device));
         AH_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-        c->d_err = (int *)dev_alloc(c, sizeof(int));
-        c->d_counter = (uint64_t *)dev_alloc(c, sizeof(uint64_t));
+        c->d_flags = (uint64_t *)dev_alloc(c, 4 * sizeof(uint64_t));
+        c->d_counter = c->d_flags;
+        c->d_aux = c->d_flags + 1;
+        c->d_err = (int *)(c->d_flags + 2);
+        AH_CUDA(cudaMallocHost(&c->h_flags, 4 * sizeof(uint64_t)));
     });
     if (st != AH_OK) {
         g_create_err = c->err;
@@ -543,6 +624,8 @@ void ah_destroy(ah_ctx *c)
     }
     for (auto e : c->events)
         cudaEventDestroy(e);
+    if (c->h_flags)
+        cudaFreeHost(c->h_flags);
     if (c->stream)
         cudaStreamDestroy(c->stream);
     delete c;
@@ -756,44 +839,16 @@ ah_status ah_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
         GenomeSet &gs = get_set(c, set_id);
         cudaStream_t st = stream_of(c, stream);
         std::vector<ScanPattern> pats = patterns_of(c, pair_ids, n_pairs);
-        const int pbits = std::max(1, bit_length(gs.n_bases));
-        uint64_t count = 0;
         uint64_t *keys = nullptr;
-        if (gs.n_tiles) {
-            ScanKernel *k = scan_kernel(pats, tuning_for(c, pats), c->device);
-            for (int attempt = 0; attempt < 2; ++attempt) {
-                keys = (uint64_t *)scratch(c, "scan_keys", c->key_cap * sizeof(uint64_t));
-                reset_flags(c, st);
-                {
-                    Stage sg(c, "scan", st, 1);
-                    launch_scan(c, k, gs, gs.n_tiles, keys, c->key_cap, pbits, st);
-                }
-                AH_CUDA(cudaMemcpyAsync(&count, c->d_counter, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-                check_flags(c, st);
-                if (count <= c->key_cap)
-                    break;
-                c->key_cap = count;
-            }
-        }
+        const uint64_t count = scan_keys(c, gs, pats, &keys, st);
         *n_out = count;
         if (count > cap)
             throw Error(AH_ERR_OVERFLOW, "ah_scan: " + std::to_string(count) + " sites, capacity " +
                                              std::to_string(cap));
         if (count == 0)
             return;
-        const int end_bit = 10 + pbits + bit_length(n_pairs - 1);
-        size_t tb = sort_keys_temp_bytes(count, end_bit);
-        void *temp = scratch(c, "sort_temp", tb);
-        uint64_t *sorted = (uint64_t *)scratch(c, "scan_keys_sorted", count * sizeof(uint64_t));
-        {
-            Stage sg(c, "sort", st, cub_sort_launches(count, end_bit - 8));
-            sort_keys(temp, tb, keys, sorted, count, 8, end_bit, st);
-        }
         ah_site *dst = out_buf(c, "sites_out", out, count);
-        {
-            Stage sg(c, "decode", st, 1);
-            launch_decode_keys(sorted, count, pbits, gs.contig_off, gs.n_contigs, gs.contig_genome, dst, st);
-        }
+        sort_decode(c, gs, n_pairs, keys, count, dst, st);
         out_finish(out, dst, count, st);
         AH_CUDA(cudaStreamSynchronize(st));
     });
@@ -869,6 +924,101 @@ ah_status ah_tune_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
             best_out->tiles = tiles;
         }
     });
+}
+
+ah_status ah_run(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, ah_run_out *o, void *stream)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    bool overflow = false;
+    ah_status st_ = guarded(c, [&] {
+        require(o != nullptr, AH_ERR_ARG, "ah_run: out is null");
+        require(pair_ids && n_pairs >= 1 && n_pairs <= AH_MAX_PAIRS_PER_SCAN, AH_ERR_ARG, "n_pairs must be 1..16");
+        require((o->sites_cap == 0 || o->sites) && (o->amplicons_cap == 0 || o->amplicons) &&
+                    (o->seq_cap == 0 || o->seq),
+                AH_ERR_ARG, "ah_run: null buffer with non-zero capacity");
+        o->n_sites = o->n_amplicons = o->n_seq = 0;
+        GenomeSet &gs = get_set(c, set_id);
+        cudaStream_t st = stream_of(c, stream);
+        std::vector<ScanPattern> pats = patterns_of(c, pair_ids, n_pairs);
+        const PairDev *pd = upload_pairs(c, pair_ids, n_pairs, st);
+        // 1. primer matching (synchronisation 1: the site count)
+        uint64_t *keys = nullptr;
+        const uint64_t ns = scan_keys(c, gs, pats, &keys, st);
+        o->n_sites = ns;
+        ah_site *sites = direct_or_scratch(c, "run_sites", o->sites, o->sites_cap, ns);
+        float *tm = direct_or_scratch(c, "run_tm", o->tm, o->tm ? o->sites_cap : 0, ns);
+        uint8_t *pass = direct_or_scratch(c, "run_pass", o->pass, o->pass ? o->sites_cap : 0, ns);
+        uint64_t na = 0, nq = 0;
+        ah_amplicon *amps = nullptr;
+        uint64_t *qoff = nullptr;
+        char *seq = nullptr;
+        if (ns) {
+            // 2. canonical sites, Tm, pair counts (synchronisation 2: the amplicon count)
+            sort_decode(c, gs, n_pairs, keys, ns, sites, st);
+            {
+                Stage sg(c, "tm", st, 1);
+                launch_tm(sites, ns, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, pass, c->d_err, st);
+            }
+            const uint8_t *filt = o->tm_filter ? pass : nullptr;
+            uint64_t *counts = (uint64_t *)scratch(c, "pair_counts", ns * sizeof(uint64_t));
+            uint64_t *offs = (uint64_t *)scratch(c, "pair_offsets", ns * sizeof(uint64_t));
+            size_t tb = scan_u64_temp_bytes(ns);
+            void *temp = scratch(c, "scan_temp", tb);
+            {
+                Stage sg(c, "pair", st, 2 + cub_scan_launches(ns));
+                launch_pair_count(sites, ns, filt, pd, counts, st);
+                exclusive_scan_u64(temp, tb, counts, offs, ns, st);
+                launch_total(offs, counts, ns, c->d_aux, st);
+            }
+            check_flags(c, st);
+            na = c->h_flags[1];
+            o->n_amplicons = na;
+            // 3. amplicons and sequence offsets (synchronisation 3: the sequence bytes)
+            amps = direct_or_scratch(c, "run_amps", o->amplicons, o->amplicons_cap, na);
+            qoff = direct_or_scratch(c, "run_qoff", o->seq_offsets, o->seq_offsets ? o->amplicons_cap + 1 : 0, na + 1);
+            if (na) {
+                Stage sg(c, "pair", st, 1);
+                launch_pair_write(sites, ns, filt, pd, offs, amps, na, st);
+            }
+            uint64_t *len = (uint64_t *)scratch(c, "fetch_len", (na + 1) * sizeof(uint64_t));
+            size_t tb2 = scan_u64_temp_bytes(na + 1);
+            void *temp2 = scratch(c, "scan_temp", tb2);
+            {
+                Stage sg(c, "fetch", st, (na ? 1 : 0) + cub_scan_launches(na + 1));
+                AH_CUDA(cudaMemsetAsync(len + na, 0, sizeof(uint64_t), st));
+                launch_fetch_lengths(amps, na, gs.contig_off, gs.n_contigs, len, c->d_err, st);
+                exclusive_scan_u64(temp2, tb2, len, qoff, na + 1, st);
+                AH_CUDA(cudaMemcpyAsync(c->d_aux, qoff + na, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+            }
+            check_flags(c, st);
+            nq = c->h_flags[1];
+            o->n_seq = nq;
+            // 4. sequences, then every output that was not written in place (synchronisation 4)
+            seq = direct_or_scratch(c, "run_seq", o->seq, o->seq_cap, nq);
+            if (na && nq) {
+                Stage sg(c, "fetch", st, 1);
+                launch_fetch(amps, na, qoff, gs.planes, gs.contig_off, seq, st);
+            }
+        }
+        overflow |= !deliver(o->sites, o->sites_cap, sites, ns, st);
+        if (o->tm)
+            overflow |= !deliver(o->tm, o->sites_cap, tm, ns, st);
+        if (o->pass)
+            overflow |= !deliver(o->pass, o->sites_cap, pass, ns, st);
+        overflow |= !deliver(o->amplicons, o->amplicons_cap, amps, na, st);
+        if (o->seq_offsets) {
+            if (ns)
+                overflow |= !deliver(o->seq_offsets, o->amplicons_cap + 1, qoff, na + 1, st);
+            else
+                AH_CUDA(cudaMemsetAsync(o->seq_offsets, 0, sizeof(uint64_t), st));
+        }
+        overflow |= !deliver(o->seq, o->seq_cap, seq, nq, st);
+        check_flags(c, st);
+        if (overflow)
+            throw Error(AH_ERR_OVERFLOW, "ah_run: an output buffer is too small (counts are in the out struct)");
+    });
+    return st_;
 }
 
 ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, const ah_site *sites,

@@ -172,6 +172,8 @@ void launch_tm(const ah_site *sites, uint64_t n, const PairDev *pairs_d, int n_p
 // pair.cu
 void launch_pair_count(const ah_site *sites, uint64_t n, const uint8_t *pass, const PairDev *pairs_d,
                        uint64_t *counts, cudaStream_t s);
+// *out = offs[n-1] + counts[n-1] (the total of an exclusive scan), on the device
+void launch_total(const uint64_t *offs, const uint64_t *counts, uint64_t n, uint64_t *out, cudaStream_t s);
 size_t scan_u64_temp_bytes(uint64_t n);
 void exclusive_scan_u64(void *temp, size_t temp_bytes, const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s);
 void launch_pair_write(const ah_site *sites, uint64_t n, const uint8_t *pass, const PairDev *pairs_d,

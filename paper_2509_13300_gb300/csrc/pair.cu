@@ -189,6 +189,12 @@ __global__ void pair_write_kernel(const ah_site *__restrict__ s, uint64_t n, con
     }
 }
 
+__global__ void total_kernel(const uint64_t *__restrict__ offs, const uint64_t *__restrict__ counts, uint64_t n,
+                             uint64_t *__restrict__ out)
+{
+    *out = n ? offs[n - 1] + counts[n - 1] : 0;
+}
+
 unsigned grid_for(uint64_t n, int threads)
 {
     uint64_t b = (n + threads - 1) / threads;
@@ -207,6 +213,12 @@ void launch_pair_count(const ah_site *sites, uint64_t n, const uint8_t *pass, co
     if (!n)
         return;
     pair_count_kernel<<<grid_for(n, 128), 128, 0, s>>>(sites, n, pass, pairs_d, counts);
+    AH_CUDA(cudaGetLastError());
+}
+
+void launch_total(const uint64_t *offs, const uint64_t *counts, uint64_t n, uint64_t *out, cudaStream_t s)
+{
+    total_kernel<<<1, 1, 0, s>>>(offs, counts, n, out);
     AH_CUDA(cudaGetLastError());
 }
 

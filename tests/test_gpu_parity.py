@@ -288,3 +288,35 @@ def test_pack_classifies_every_byte_value(ctx):
     want, woff = oracle.fetch(seq, off, amps)
     ctx.ah_unload_genomes(sid)
     assert np.array_equal(goff, woff) and got == want
+
+
+@pytest.mark.parametrize("tm_filter", [True, False])
+def test_run_equals_separate_calls_and_oracle(ctx, tm_filter):
+    """ah_run (the fused path) gives the records of ah_scan/ah_tm/ah_pair/ah_fetch
+    and of the oracle; too-small outputs are reported, not written."""
+    w = synth.collection(seed=2, n_genomes=4, len_lo=3e5, len_hi=9e5)
+    w.pairs = [dict(w.pairs[0], tm_min=50.0)]
+    o = oracle_run(w)
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    pid = ctx.ah_set_primers(w.pairs[0]["fwd"], w.pairs[0]["rev"], w.pairs[0])
+    r = ctx.run(sid, [pid], tm_filter=tm_filter)
+    amps = o["amps_tm"] if tm_filter else o["amps"]
+    seqs, offs = oracle.fetch(w.seq, w.contig_off, amps)
+    assert r["sites"].tobytes() == o["sites"].tobytes()
+    assert np.array_equal(r["pass_"], o["pass_"])
+    ok = ~np.isnan(o["tm"])
+    assert np.array_equal(np.isnan(r["tm"]), ~ok) and np.abs(r["tm"][ok] - o["tm"][ok]).max() <= TM_TOL
+    assert r["amps"].tobytes() == amps.tobytes() and len(amps) > 0
+    assert r["seqs"] == seqs and np.array_equal(r["offs"], offs)
+    # capacity one short on the amplicons: counts reported, sites still written
+    n, m = len(r["sites"]), len(r["amps"])
+    sites = np.zeros(n, dtype=ah.SITE_DTYPE)
+    small = np.zeros(m, dtype=ah.AMPLICON_DTYPE)
+    out = ah.RunOut(sites.ctypes.data, n, 0, None, None, small.ctypes.data, m - 1, 0, None, 0, 0, None,
+                    1 if tm_filter else 0, 0)
+    with pytest.raises(ah.AHError) as e:
+        ctx.ah_run(sid, [pid], out)
+    assert e.value.status == ah.AH_ERR_OVERFLOW
+    assert out.n_sites == n and out.n_amplicons == m and out.n_seq == len(seqs)
+    assert sites.tobytes() == o["sites"].tobytes() and not small.view(np.uint8).any()
+    ctx.ah_unload_genomes(sid)
