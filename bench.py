@@ -41,9 +41,9 @@ FALLBACK_HBM_GBS = 6800.0
 SMS, LOP_LANES_PER_CLK = 152, 64
 
 
-def workload(seed: int):
+def workload(seed: int, n_genomes: int = 100):
     from paper_2509_13300_gb300 import synth
-    w = synth.collection(seed=seed, n_genomes=100, len_lo=2e6, len_hi=7e6, k=3, min_len=100, max_len=2500)
+    w = synth.collection(seed=seed, n_genomes=n_genomes, len_lo=2e6, len_hi=7e6, k=3, min_len=100, max_len=2500)
     w.pairs = [dict(w.pairs[0], tm_min=50.0, dnac1_nM=250.0, Na_mM=50.0)]
     return w
 
@@ -221,6 +221,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default (or AH_SCAN_TUNING) scan variant")
+    ap.add_argument("--n-genomes", type=int, default=100, help="smaller collections for profiling runs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -234,7 +236,7 @@ def main():
     from paper_2509_13300_gb300 import ah, build
     build.build()
 
-    w = workload(1 + rank)
+    w = workload(1 + rank, args.n_genomes)
     p = w.pairs[0]
     n_bases = w.n_bases
     stream = torch.cuda.current_stream()
@@ -244,7 +246,7 @@ def main():
 
     # capacities from one warm-up pass (also compiles and tunes the generated scan kernel)
     sid = ctx.ah_load_genomes(seq_d, n_bases, w.contig_off, w.contig_genome, stream)
-    tune = ctx.ah_tune_scan(sid, [pid], 0, stream)
+    tune = None if args.no_tune else ctx.ah_tune_scan(sid, [pid], 0, stream)
     r = ctx.run(sid, [pid], tm_filter=True)
     ctx.ah_unload_genomes(sid)
     cap_s, cap_a, cap_q = len(r["sites"]) + 1, len(r["amps"]) + 1, len(r["seqs"]) + 1
@@ -269,6 +271,7 @@ def main():
 
     for _ in range(args.warmup):
         step_device()
+    n, m = out_d.n_sites, out_d.n_amplicons
     ctx.ah_set_profiling(True)
     barrier(world)
     torch.cuda.synchronize()
@@ -303,7 +306,7 @@ def main():
     scan_hbm = 0.5 * n_bases / (scan_us * 1e-6) / 1e9  # 4 planes x 1 bit per base
     pack_hbm = 1.5 * n_bases / (pack_us * 1e-6) / 1e9  # 1 B/base read + 0.5 B/base written
     # logic-pipe ops of the generated scan kernel per launch (static count of its LOP3s per word)
-    lop_per_word = ctx_scan_lop_count(p, tune)
+    lop_per_word = ctx_scan_lop_count(p, tune or {"R": 4, "arith_pct": 0})
     words = n_bases / 32.0
     scan_tops = lop_per_word * words / (scan_us * 1e-6) / 1e12
     clk_mhz = clocks["sm_mhz"] or 2070.0
@@ -339,18 +342,20 @@ def main():
         d2h = 16 * n + 4 * n + n + 28 * m + q + 8 * (m + 1)
         return h2d, d2h
 
-    step_host()
-    barrier(world)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.e2e_steps):
-        h2d, d2h = step_host()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
-    e2e = {"value": bases_all * args.e2e_steps / (e2e_ms / 1e3) / 1e9, "unit": "Gbp/s",
-           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps}
+    e2e = None
+    if args.e2e_steps > 0:
+        step_host()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            h2d, d2h = step_host()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+        e2e = {"value": bases_all * args.e2e_steps / (e2e_ms / 1e3) / 1e9, "unit": "Gbp/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps}
 
     if rank != 0:
         ctx.close()

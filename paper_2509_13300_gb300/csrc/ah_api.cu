@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -593,6 +594,17 @@ ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
     c->budget = mem_budget_bytes;
     ah_status st = guarded(c, [&] {
         AH_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device));
+        // default scan variant; AH_SCAN_TUNING="R,arith_pct,order,min_blocks" overrides it (profiling aid)
+        if (const char *e = getenv("AH_SCAN_TUNING")) {
+            int R = 4, ap = 0, order = 0, mb = 1;
+            if (sscanf(e, "%d,%d,%d,%d", &R, &ap, &order, &mb) >= 1 && (R == 4 || R == 8) && ap >= 0 && ap <= 100 &&
+                (order == 0 || order == 1) && mb >= 1 && mb <= 4) {
+                c->tuning.R = R;
+                c->tuning.arith_pct = ap;
+                c->tuning.order = order;
+                c->tuning.min_blocks = mb;
+            }
+        }
         AH_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         c->d_flags = (uint64_t *)dev_alloc(c, 4 * sizeof(uint64_t));
         c->d_counter = c->d_flags;
@@ -905,6 +917,9 @@ ah_status ah_tune_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
             }
             check_flags(c, st);
             const double us = ms_min * 1e3 / (double)tiles;
+            if (getenv("AH_TUNE_VERBOSE"))
+                fprintf(stderr, "ah_tune_scan: R=%d arith=%d order=%d regs=%d bps=%d  %.4f us/tile\n", t.R,
+                        t.arith_pct, t.order, k->regs, k->blocks_per_sm, us);
             if (us < best_us) {
                 best_us = us;
                 best = t;
