@@ -213,14 +213,16 @@ ah_status ah_scan(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32
 
 /* Variant of the generated scan kernel picked by ah_tune_scan. */
 typedef struct ah_tune_result {
-    int32_t R;          /* 32-start words per thread (threads per block = 1024 / R) */
-    int32_t arith_pct;  /* share of full adders whose sum uses integer adds instead of a LOP3 */
-    int32_t min_blocks; /* occupancy hint given to the compiler */
-    int32_t order;      /* 0 word-major, 1 pattern-major code order */
-    int32_t regs;       /* registers per thread of the chosen variant */
+    int32_t R;             /* 32-start words per thread */
+    int32_t arith_pct;     /* share of full adders whose sum uses integer adds instead of a LOP3 */
+    int32_t min_blocks;    /* occupancy hint given to the compiler */
+    int32_t order;         /* 0 word-major, 1 pattern-major code order */
+    int32_t stages;        /* bulk-copy stages per warp */
+    int32_t warps_per_cta; /* warps per thread block */
+    int32_t regs;          /* registers per thread of the chosen variant */
     int32_t reserved;
-    double us_per_tile; /* measured time per 32768-base tile */
-    uint64_t tiles;     /* tiles in the timed sample */
+    double us_per_tile;    /* measured time per 32768-base tile */
+    uint64_t tiles;        /* tiles in the timed sample */
 } ah_tune_result;
 
 /* Autotuner of the scan (a performance aid; it does not change results):

@@ -53,8 +53,9 @@ class PcrParams(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int32), ("arith_pct", ctypes.c_int32), ("min_blocks", ctypes.c_int32),
-                ("order", ctypes.c_int32), ("regs", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("us_per_tile", ctypes.c_double), ("tiles", ctypes.c_uint64)]
+                ("order", ctypes.c_int32), ("stages", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("regs", ctypes.c_int32), ("reserved", ctypes.c_int32), ("us_per_tile", ctypes.c_double),
+                ("tiles", ctypes.c_uint64)]
 
 
 class RunOut(ctypes.Structure):

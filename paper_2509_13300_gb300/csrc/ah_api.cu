@@ -95,7 +95,6 @@ void require(bool cond, ah_status st, const std::string &msg)
         throw Error(st, msg);
 }
 
-constexpr size_t kCacheMin = 1 << 20; // blocks at least this large are cached on release
 
 void release_cached(ah_ctx *c, size_t need)
 {
@@ -113,7 +112,7 @@ void *dev_alloc(ah_ctx *c, size_t bytes)
 {
     if (bytes == 0)
         bytes = 16;
-    if (bytes >= kCacheMin) { // reuse a cached block of at most twice the size
+    { // reuse a cached block of at most twice the size (cudaFree would synchronise the device)
         auto it = c->cached.lower_bound(bytes);
         if (it != c->cached.end() && it->first <= 2 * bytes) {
             void *p = it->second;
@@ -149,13 +148,7 @@ void dev_free(ah_ctx *c, void *p, size_t)
     auto it = c->live.find(p);
     if (it == c->live.end())
         return;
-    if (it->second >= kCacheMin) {
-        c->cached.emplace(it->second, p);
-        return;
-    }
-    cudaFree(p);
-    c->used -= std::min(c->used, it->second);
-    c->live.erase(it);
+    c->cached.emplace(it->second, p); // kept for reuse; released under budget pressure or at ah_destroy
 }
 
 cudaEvent_t get_event(ah_ctx *c)
@@ -594,15 +587,16 @@ ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
     c->budget = mem_budget_bytes;
     ah_status st = guarded(c, [&] {
         AH_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device));
-        // default scan variant; AH_SCAN_TUNING="R,arith_pct,order,min_blocks" overrides it (profiling aid)
+        // default scan variant; AH_SCAN_TUNING="R,arith_pct,order,stages,warps" overrides it (profiling aid)
         if (const char *e = getenv("AH_SCAN_TUNING")) {
-            int R = 4, ap = 0, order = 0, mb = 1;
-            if (sscanf(e, "%d,%d,%d,%d", &R, &ap, &order, &mb) >= 1 && (R == 4 || R == 8) && ap >= 0 && ap <= 100 &&
-                (order == 0 || order == 1) && mb >= 1 && mb <= 4) {
+            int R = 8, ap = 0, order = 1, S = 3, wpc = 4;
+            if (sscanf(e, "%d,%d,%d,%d,%d", &R, &ap, &order, &S, &wpc) >= 1 && (R == 4 || R == 8) && ap >= 0 &&
+                ap <= 100 && (order == 0 || order == 1) && S >= 2 && S <= 4 && wpc >= 1 && wpc <= 8) {
                 c->tuning.R = R;
                 c->tuning.arith_pct = ap;
                 c->tuning.order = order;
-                c->tuning.min_blocks = mb;
+                c->tuning.stages = S;
+                c->tuning.warps = wpc;
             }
         }
         AH_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
@@ -882,15 +876,16 @@ ah_status ah_tune_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
         // the sample must cover whole waves of the persistent grid to time it fairly
         std::vector<ScanTuning> cand;
         for (int R : {4, 8})
-            for (int ap : {0, 25, 50})
-                for (int order : {0, 1}) {
-                    ScanTuning t;
-                    t.R = R;
-                    t.arith_pct = ap;
-                    t.order = order;
-                    t.min_blocks = 1;
-                    cand.push_back(t);
-                }
+            for (int order : {0, 1})
+                for (int S : {2, 4})
+                    for (int wpc : {2, 4}) {
+                        ScanTuning t;
+                        t.R = R;
+                        t.order = order;
+                        t.stages = S;
+                        t.warps = wpc;
+                        cand.push_back(t);
+                    }
         cudaEvent_t e0 = get_event(c), e1 = get_event(c);
         double best_us = 1e30;
         ScanTuning best = c->tuning;
@@ -918,8 +913,8 @@ ah_status ah_tune_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
             check_flags(c, st);
             const double us = ms_min * 1e3 / (double)tiles;
             if (getenv("AH_TUNE_VERBOSE"))
-                fprintf(stderr, "ah_tune_scan: R=%d arith=%d order=%d regs=%d bps=%d  %.4f us/tile\n", t.R,
-                        t.arith_pct, t.order, k->regs, k->blocks_per_sm, us);
+                fprintf(stderr, "ah_tune_scan: R=%d arith=%d order=%d stages=%d warps=%d regs=%d bps=%d  %.4f us/tile\n",
+                        t.R, t.arith_pct, t.order, t.stages, t.warps, k->regs, k->blocks_per_sm, us);
             if (us < best_us) {
                 best_us = us;
                 best = t;
@@ -934,6 +929,8 @@ ah_status ah_tune_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
             best_out->arith_pct = best.arith_pct;
             best_out->min_blocks = best.min_blocks;
             best_out->order = best.order;
+            best_out->stages = best.stages;
+            best_out->warps_per_cta = best.warps;
             best_out->regs = best_regs;
             best_out->us_per_tile = best_us;
             best_out->tiles = tiles;

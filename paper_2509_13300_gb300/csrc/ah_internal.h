@@ -70,17 +70,12 @@ struct ScanPattern {
 
 // Tunables of the generated scan kernel (autotuned per pattern set).
 struct ScanTuning {
-    int R = 4;            // words per thread (4 or 8); threads per block = kTileW / R
+    int R = 8;            // 32-start words per thread (4 or 8)
     int arith_pct = 0;    // share of full adders that form the sum with integer adds
     int min_blocks = 1;   // __launch_bounds__ minimum blocks per SM
-    int order = 0;        // 0: word-major, 1: pattern-major code order
-    bool operator<(const ScanTuning &o) const
-    {
-        if (R != o.R) return R < o.R;
-        if (arith_pct != o.arith_pct) return arith_pct < o.arith_pct;
-        if (min_blocks != o.min_blocks) return min_blocks < o.min_blocks;
-        return order < o.order;
-    }
+    int order = 1;        // 0: word-major, 1: pattern-major code order
+    int stages = 3;       // TMA stages per warp (2..4)
+    int warps = 4;        // warps per CTA (1..8)
 };
 
 struct ScanKernel {

@@ -60,12 +60,11 @@ __device__ __forceinline__ void mbar_init(u64 *bar, u32 count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
-// one thread: expect `bytes` on the barrier, then start the bulk copy that delivers them
-__device__ __forceinline__ void tma_load(void *dst, const void *src, u32 bytes, u64 *bar)
+// one thread: start a bulk copy (TMA) whose bytes complete on `bar`; the
+// generic-proxy reads of the buffer are ordered before the async write
+__device__ __forceinline__ void tma_copy(void *dst, const void *src, u32 bytes, u64 *bar)
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
                  : "memory");
@@ -97,10 +96,11 @@ __device__ __forceinline__ bool mbar_wait(u64 *bar, u32 parity)
 )CUDA";
 
 // Body of the kernel after the generated hit words.  Uses: h[NPAT*R] (hit
-// words), any, sm (tile planes), tile, j0, and the pattern tables.
+// words), any, lane, sm (the warp's slice planes, stride SLW), tile, wbase
+// (first tile word of the slice), j0 (the thread's first slice word) and the
+// pattern tables.
 const char *kEmit = R"CUDA(
     if (__any_sync(0xffffffffu, any != 0u)) {
-        const int lane = threadIdx.x & 31;
         u32 hl[NPAT * R];
 #pragma unroll
         for (int i = 0; i < NPAT * R; ++i) hl[i] = h[i];
@@ -126,7 +126,7 @@ const char *kEmit = R"CUDA(
                     const int b = __ffs(m) - 1;
                     m &= m - 1;
                     const int jr = j0 + r;
-                    const u64 P = tile * TB + (u64)b * W + jr;
+                    const u64 P = tile * TB + (u64)b * W + wbase + jr;
                     const int L = c_L[q];
                     u32 lo = 0, hi = n_contigs;
                     while (hi - lo > 1) {
@@ -138,8 +138,8 @@ const char *kEmit = R"CUDA(
                     const int c = c_clamp[q];
                     for (int i = 0; i < L; ++i) {
                         const int wj = jr + i;
-                        const u32 code = ((sm[wj] >> b) & 1u) | (((sm[WX + wj] >> b) & 1u) << 1) |
-                                         (((sm[2 * WX + wj] >> b) & 1u) << 2) | (((sm[3 * WX + wj] >> b) & 1u) << 3);
+                        const u32 code = ((sm[wj] >> b) & 1u) | (((sm[SLW + wj] >> b) & 1u) << 1) |
+                                         (((sm[2 * SLW + wj] >> b) & 1u) << 2) | (((sm[3 * SLW + wj] >> b) & 1u) << 3);
                         const int mis = (code & c_mask[q][i]) == 0u;
                         mm += mis;
                         const int in_clamp = c_strand[q] == 0 ? (i >= L - c) : (i < c);
@@ -317,7 +317,7 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
         Lmax = std::max(Lmax, p.L);
     const int R = t.R;
     const int nwin = 4 * ((R + Lmax - 1 + 3) / 4);
-    const int NT = kTileW / R;
+    const int NT = 32 * t.warps;
     Gen g;
     g.arith_pct = t.arith_pct;
     std::ostringstream &os = g.os;
@@ -345,46 +345,62 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
         os << "}";
     }
     os << "};\n";
+    os << "#define S " << t.stages << "\n#define WPC " << t.warps << "\n#define SLICES (W / (32 * R))\n"
+       << "#define SLW (32 * R + 32)\n";
     os << "extern \"C\" __global__ void __launch_bounds__(NT, " << t.min_blocks << ")\n"
        << "ah_scan_kernel(const u32 *__restrict__ planes, u64 n_tiles, const u64 *__restrict__ contig_off,\n"
        << "               u32 n_contigs, u64 *__restrict__ keys, u64 cap, u64 *__restrict__ counter, int pbits,\n"
        << "               int *__restrict__ err)\n{\n"
-       << "  // two tile buffers filled by bulk async copies (TMA), one mbarrier each\n"
+       << "  // Every warp owns slices of tiles (32*R words of each plane plus a 32-word\n"
+       << "  // overhang) and runs its own S-stage pipeline: lane 0 starts bulk async\n"
+       << "  // copies (TMA) into the warp's buffers, one mbarrier per stage; no CTA-wide\n"
+       << "  // barrier is ever taken.\n"
        << "  extern __shared__ __align__(128) u32 smbuf[];\n"
-       << "  __shared__ __align__(8) u64 bar[2];\n"
-       << "  const u32 TILE_BYTES = 4u * WX * 4u;\n"
-       << "  if (threadIdx.x == 0) {\n"
-       << "    mbar_init(&bar[0], 1);\n"
-       << "    mbar_init(&bar[1], 1);\n"
+       << "  __shared__ __align__(8) u64 bars[WPC * S];\n"
+       << "  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n"
+       << "  u32 *wbuf = smbuf + warp * (S * 4 * SLW);\n"
+       << "  u64 *wbar = bars + warp * S;\n"
+       << "  const u64 n_items = n_tiles * SLICES;\n"
+       << "  const u64 gw = (u64)blockIdx.x * WPC + warp, tw = (u64)gridDim.x * WPC;\n"
+       << "  if (lane == 0) {\n"
+       << "    for (int q = 0; q < S; ++q) mbar_init(&wbar[q], 1);\n"
        << "    asm volatile(\"fence.mbarrier_init.release.cluster;\" ::: \"memory\");\n"
        << "  }\n"
-       << "  __syncthreads();\n"
-       << "  if (threadIdx.x == 0 && (u64)blockIdx.x < n_tiles)\n"
-       << "    tma_load(smbuf, planes + (u64)blockIdx.x * 4 * WX, TILE_BYTES, &bar[0]);\n"
-       << "  int it = 0;\n"
-       << "  for (u64 tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {\n"
-       << "    const int sb = it & 1;\n"
-       << "    const u64 next = tile + gridDim.x;\n"
-       << "    if (threadIdx.x == 0 && next < n_tiles)\n"
-       << "      tma_load(smbuf + (sb ^ 1) * 4 * WX, planes + next * 4 * WX, TILE_BYTES, &bar[sb ^ 1]);\n"
-       << "    const bool ok = mbar_wait(&bar[sb], (u32)((it >> 1) & 1));\n"
-       << "    if (!__syncthreads_and(ok)) {\n"
-       << "      // the copy never landed: report, wait (bounded) for the copy still in flight, leave\n"
-       << "      if (threadIdx.x == 0) {\n"
+       << "  __syncwarp();\n"
+       << "  auto issue = [&](u64 wi, int stg) {\n"
+       << "    const u64 tl = wi / SLICES;\n"
+       << "    const int sl = (int)(wi % SLICES);\n"
+       << "    asm volatile(\"mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\" ::\"r\"(smem_addr(&wbar[stg])),\n"
+       << "                 \"r\"((u32)(4 * SLW * 4)) : \"memory\");\n"
+       << "    for (int x = 0; x < 4; ++x)\n"
+       << "      tma_copy(wbuf + (stg * 4 + x) * SLW, planes + (tl * 4 + x) * WX + sl * 32 * R, SLW * 4, &wbar[stg]);\n"
+       << "  };\n"
+       << "  if (lane == 0)\n"
+       << "    for (int q = 0; q < S; ++q) if (gw + q * tw < n_items) issue(gw + q * tw, q);\n"
+       << "  int k = 0;\n"
+       << "  for (u64 wi = gw; wi < n_items; wi += tw, ++k) {\n"
+       << "    const int stg = k % S;\n"
+       << "    const bool ok = mbar_wait(&wbar[stg], (u32)((k / S) & 1));\n"
+       << "    if (!__all_sync(0xffffffffu, ok)) {\n"
+       << "      // a copy never landed: report, wait (bounded) for the copies still in flight, leave\n"
+       << "      if (lane == 0) {\n"
        << "        atomicExch(err, 1);\n"
-       << "        if (next < n_tiles) mbar_wait(&bar[sb ^ 1], (u32)(((it + 1) >> 1) & 1));\n"
+       << "        for (int d = 1; d < S; ++d)\n"
+       << "          if (wi + d * tw < n_items) mbar_wait(&wbar[(k + d) % S], (u32)(((k + d) / S) & 1));\n"
        << "      }\n"
        << "      break;\n"
        << "    }\n"
-       << "    const u32 *sm = smbuf + sb * 4 * WX;\n"
-       << "    const int j0 = threadIdx.x * R;\n"
+       << "    const u64 tile = wi / SLICES;\n"
+       << "    const int wbase = (int)(wi % SLICES) * 32 * R;\n"
+       << "    const u32 *sm = wbuf + stg * 4 * SLW;\n"
+       << "    const int j0 = lane * R;\n"
        << "    u32 pA[NWIN], pC[NWIN], pG[NWIN], pT[NWIN], pV[NWIN];\n"
        << "#pragma unroll\n"
        << "    for (int c = 0; c < NWIN / 4; ++c) {\n"
-       << "      uint4 a = reinterpret_cast<const uint4 *>(sm + 0 * WX + j0)[c];\n"
-       << "      uint4 cc = reinterpret_cast<const uint4 *>(sm + 1 * WX + j0)[c];\n"
-       << "      uint4 gg = reinterpret_cast<const uint4 *>(sm + 2 * WX + j0)[c];\n"
-       << "      uint4 tt = reinterpret_cast<const uint4 *>(sm + 3 * WX + j0)[c];\n"
+       << "      uint4 a = reinterpret_cast<const uint4 *>(sm + 0 * SLW + j0)[c];\n"
+       << "      uint4 cc = reinterpret_cast<const uint4 *>(sm + 1 * SLW + j0)[c];\n"
+       << "      uint4 gg = reinterpret_cast<const uint4 *>(sm + 2 * SLW + j0)[c];\n"
+       << "      uint4 tt = reinterpret_cast<const uint4 *>(sm + 3 * SLW + j0)[c];\n"
        << "      pA[4*c] = a.x; pA[4*c+1] = a.y; pA[4*c+2] = a.z; pA[4*c+3] = a.w;\n"
        << "      pC[4*c] = cc.x; pC[4*c+1] = cc.y; pC[4*c+2] = cc.z; pC[4*c+3] = cc.w;\n"
        << "      pG[4*c] = gg.x; pG[4*c+1] = gg.y; pG[4*c+2] = gg.z; pG[4*c+3] = gg.w;\n"
@@ -410,7 +426,9 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
                 one(q, r);
     }
     os << kEmit;
-    os << "    __syncthreads();\n  }\n}\n";
+    os << "    __syncwarp();\n"
+       << "    if (lane == 0 && wi + S * tw < n_items) issue(wi + S * tw, stg);\n"
+       << "  }\n}\n";
     return os.str();
 }
 
@@ -471,8 +489,11 @@ ScanKernel *scan_kernel(const std::vector<ScanPattern> &pats, const ScanTuning &
     k->log = log;
     AH_CUDA(cudaLibraryLoadData(&k->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
     AH_CUDA(cudaLibraryGetKernel(&k->fn, k->lib, "ah_scan_kernel"));
-    k->threads = kTileW / t.R;
-    k->smem = 2 * kTileBytes; // double-buffered tiles
+    k->threads = 32 * t.warps;
+    k->smem = (size_t)t.warps * t.stages * 4 * (32 * t.R + 32) * sizeof(uint32_t); // per-warp stage buffers
+    if (k->smem > 48 * 1024)
+        AH_CUDA(cudaKernelSetAttributeForDevice(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k->smem,
+                                                device));
     auto pos = log.find("Used ");
     if (pos != std::string::npos)
         k->regs = atoi(log.c_str() + pos + 5);

@@ -11,17 +11,15 @@
 // primer (choice = base at each position, restricted to its IUPAC set), and
 // Dinkelbach's iteration lam <- ratio(argmin F) climbs to the maximum ratio in
 // a few rounds, provided dS(o) + C < 0 for every oligo (checked first with a
-// max-path pass; otherwise the kernel enumerates the oligos).  One thread per
-// site, fp32; when a pass flag is requested and the fp32 Tm is within 0.05 deg C
-// of tm_min the site is recomputed in fp64 so the decision equals the fp64 one.
+// max-path pass; otherwise the oligos are enumerated).  Four lanes per site,
+// fp32; when a pass flag is requested and the fp32 Tm is within 0.05 deg C of
+// tm_min the site is recomputed in fp64 so the decision equals the fp64 one.
 #include <cmath>
 
 #include "ah_internal.h"
 
 namespace ah {
 namespace {
-
-constexpr double kR = 1.987; // cal / (K mol)
 
 template <class T> struct Tab {
     const T *sdH, *sdS, *tdH, *tdS;
@@ -175,52 +173,166 @@ __device__ __forceinline__ int base_at(const uint32_t *__restrict__ planes, uint
     return code;
 }
 
-__global__ void __launch_bounds__(128) tm_kernel(const ah_site *__restrict__ sites, uint64_t n,
-                                                 const PairDev *__restrict__ pairs, int n_pairs,
-                                                 const uint32_t *__restrict__ planes,
-                                                 const uint64_t *__restrict__ contig_off, float *__restrict__ tm_out,
-                                                 uint8_t *__restrict__ pass_out, int *__restrict__ err)
+// Four lanes per site: lane y of a group holds the DP state "oligo base at
+// the current position = y".  Each step takes the four predecessor costs by
+// shuffles, keeps the best predecessor (2 bits per position, so the argmin
+// oligo is recovered by a backtrack across the group's lanes) and the
+// oligo's dH, dS are then summed by the four lanes together.  Eight sites per
+// warp; the rare enumeration fallback and the fp64 recompute near tm_min run
+// on lane 0 of the group with the single-thread routine above.
+constexpr int kTmWarps = 4;
+
+template <class F> __device__ __forceinline__ float group_reduce(float v, F op)
 {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const ah_site s = sites[i];
-        if (s.pair >= n_pairs || s.primer > 1 || s.strand > 1) {
+    v = op(v, __shfl_xor_sync(0xffffffffu, v, 1));
+    v = op(v, __shfl_xor_sync(0xffffffffu, v, 2));
+    return v;
+}
+
+__global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__restrict__ sites, uint64_t n,
+                                                           const PairDev *__restrict__ pairs, int n_pairs,
+                                                           const uint32_t *__restrict__ planes,
+                                                           const uint64_t *__restrict__ contig_off,
+                                                           float *__restrict__ tm_out, uint8_t *__restrict__ pass_out,
+                                                           int *__restrict__ err)
+{
+    __shared__ int8_t bts[kTmWarps][8][AH_MAX_PRIMER_LEN];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, y = lane & 3, g0 = lane & ~3;
+    int8_t *bt = bts[warp][g];
+    const float INF = INFINITY;
+    const uint64_t groups = (uint64_t)gridDim.x * kTmWarps * 8;
+    for (uint64_t base = ((uint64_t)blockIdx.x * kTmWarps + warp) * 8; base < n; base += groups) {
+        const uint64_t i = base + g;
+        const bool live = i < n;
+        ah_site s{};
+        if (live)
+            s = sites[i];
+        bool bad_rec = live && (s.pair >= n_pairs || s.primer > 1 || s.strand > 1);
+        if (bad_rec && y == 0)
             atomicExch(err, kDevBounds);
+        const bool act = live && !bad_rec;
+        const PairDev &pd = pairs[act ? s.pair : 0];
+        const int L = act ? pd.L[s.primer] : 2;
+        const uint8_t *mask = pd.mask[act ? s.primer : 0];
+        // template base opposite each primer position (-1: not a base)
+        // every entry the DP reads is written (0..3), also for groups without a live site
+        bool bad = false;
+        if (act) {
+            const uint64_t P = contig_off[s.contig] + s.pos;
+            for (int q = y; q < L; q += 4) {
+                const int c = base_at(planes, P + (s.strand == 0 ? q : L - 1 - q));
+                bad |= c < 0;
+                bt[q] = (int8_t)(c < 0 ? 0 : (s.strand == 0 ? 3 - c : c));
+            }
+        } else {
+            for (int q = y; q < L; q += 4)
+                bt[q] = 0;
+        }
+        __syncwarp();
+        bad = __shfl_sync(0xffffffffu, (int)bad, g0) | __shfl_sync(0xffffffffu, (int)bad, g0 + 1) |
+              __shfl_sync(0xffffffffu, (int)bad, g0 + 2) | __shfl_sync(0xffffffffu, (int)bad, g0 + 3);
+        const bool run = act && !bad;
+        const float cst = act ? (float)(pd.sconst + pd.salt_dS_per_stack * (L - 1)) : -1.f;
+        // largest denominator over oligos (max-path of dS); all groups take part in the shuffles
+        float sm = (run && (mask[0] >> y & 1)) ? pd.term_dS[y * 4 + bt[0]] : -INF;
+        for (int q = 1; q < L; ++q) {
+            float best = -INF;
+            for (int x = 0; x < 4; ++x) {
+                const float cx = __shfl_sync(0xffffffffu, sm, g0 + x);
+                const float v = cx + pd.stack_dS[((x * 4 + y) * 4 + bt[q - 1]) * 4 + bt[q]];
+                best = v > best ? v : best;
+            }
+            sm = (mask[q] >> y & 1) ? best : -INF;
+        }
+        float dm = sm + ((mask[L - 1] >> y & 1) ? pd.term_dS[y * 4 + bt[L - 1]] : 0.f);
+        dm = group_reduce(dm, [](float a, float b) { return a > b ? a : b; });
+        const bool dink = run && dm + cst < 0.f;
+        float lam = 0.f;
+        for (int it = 0; it < 64; ++it) {
+            // min over oligos of 1000 dH - lam dS, with the best predecessor of every position
+            float c = (dink && (mask[0] >> y & 1)) ? 1000.f * pd.term_dH[y * 4 + bt[0]] - lam * pd.term_dS[y * 4 + bt[0]]
+                                                    : INF;
+            uint64_t pred = 0;
+            for (int q = 1; q < L; ++q) {
+                float best = INF;
+                int arg = 0;
+                for (int x = 0; x < 4; ++x) {
+                    const float cx = __shfl_sync(0xffffffffu, c, g0 + x);
+                    const int idx = ((x * 4 + y) * 4 + bt[q - 1]) * 4 + bt[q];
+                    const float v = cx + 1000.f * pd.stack_dH[idx] - lam * pd.stack_dS[idx];
+                    if (v < best) {
+                        best = v;
+                        arg = x;
+                    }
+                }
+                c = (mask[q] >> y & 1) ? best : INF;
+                pred |= (uint64_t)arg << (2 * q);
+            }
+            float fin = c + 1000.f * pd.term_dH[y * 4 + bt[L - 1]] - lam * pd.term_dS[y * 4 + bt[L - 1]];
+            if (!(c < INF))
+                fin = INF;
+            // argmin over the group's four end states (ties: lowest base)
+            float fmin = group_reduce(fin, [](float a, float b) { return a < b ? a : b; });
+            const unsigned hit = __ballot_sync(0xffffffffu, fin == fmin) >> g0 & 0xFu;
+            int cur = hit ? __ffs(hit) - 1 : 0;
+            // backtrack the oligo: o[L-1] = cur, o[q-1] = pred of lane o[q] at position q
+            uint64_t olig = (uint64_t)cur << (2 * (L - 1));
+            for (int q = L - 1; q >= 1; --q) {
+                const uint64_t pp = __shfl_sync(0xffffffffu, pred, g0 + cur);
+                cur = (int)(pp >> (2 * q) & 3u);
+                olig |= (uint64_t)cur << (2 * (q - 1));
+            }
+            // its dH and dS, split over the four lanes
+            float H = 0.f, S = 0.f;
+            for (int q = 1 + y; q < L; q += 4) {
+                const int a = (int)(olig >> (2 * (q - 1)) & 3u), b2 = (int)(olig >> (2 * q) & 3u);
+                const int idx = ((a * 4 + b2) * 4 + bt[q - 1]) * 4 + bt[q];
+                H += pd.stack_dH[idx];
+                S += pd.stack_dS[idx];
+            }
+            H = group_reduce(H, [](float a, float b) { return a + b; });
+            S = group_reduce(S, [](float a, float b) { return a + b; });
+            const int o0 = (int)(olig & 3u), oL = (int)(olig >> (2 * (L - 1)) & 3u);
+            H += pd.term_dH[o0 * 4 + bt[0]] + pd.term_dH[oL * 4 + bt[L - 1]];
+            S += pd.term_dS[o0 * 4 + bt[0]] + pd.term_dS[oL * 4 + bt[L - 1]];
+            const float r = 1000.f * H / (S + cst);
+            // warp-uniform loop: stop when no group still improves
+            const bool more = dink && (it == 0 || r > lam);
+            if (more)
+                lam = r;
+            if (!__any_sync(0xffffffffu, more))
+                break;
+        }
+        if (y == 0 && act) {
+            float tm = NAN;
+            uint8_t pass = 0;
+            if (!bad) {
+                int bti[AH_MAX_PRIMER_LEN];
+                for (int q = 0; q < L; ++q)
+                    bti[q] = bt[q];
+                int used_enum = 0;
+                const float ratio = dink ? lam : max_ratio<float>(pd, mask, bti, L, cst, &used_enum);
+                tm = ratio - 273.15f + (float)pd.tm_shift;
+                if (pass_out) {
+                    if (fabsf(tm - pd.tm_min_f) < 0.05f) {
+                        const double cst_d = pd.sconst + pd.salt_dS_per_stack * (L - 1);
+                        const double tm_d = max_ratio<double>(pd, mask, bti, L, cst_d, &used_enum) - 273.15 + pd.tm_shift;
+                        pass = tm_d >= pd.tm_min;
+                    } else {
+                        pass = tm >= pd.tm_min_f;
+                    }
+                }
+            }
+            tm_out[i] = tm;
+            if (pass_out)
+                pass_out[i] = pass;
+        } else if (y == 0 && bad_rec) {
             tm_out[i] = NAN;
             if (pass_out)
                 pass_out[i] = 0;
-            continue;
         }
-        const PairDev &pd = pairs[s.pair];
-        const int L = pd.L[s.primer];
-        const uint8_t *mask = pd.mask[s.primer];
-        const uint64_t P = contig_off[s.contig] + s.pos;
-        int bt[AH_MAX_PRIMER_LEN];
-        bool bad = false;
-        for (int q = 0; q < L; ++q) {
-            const int c = base_at(planes, P + (s.strand == 0 ? q : L - 1 - q));
-            if (c < 0)
-                bad = true;
-            bt[q] = (s.strand == 0) ? 3 - c : c; // template base opposite primer position q
-        }
-        float tm = NAN;
-        uint8_t pass = 0;
-        if (!bad) {
-            int used_enum = 0;
-            const float cst = (float)(pd.sconst + pd.salt_dS_per_stack * (L - 1));
-            tm = max_ratio<float>(pd, mask, bt, L, cst, &used_enum) - 273.15f + (float)pd.tm_shift;
-            if (pass_out) {
-                if (fabsf(tm - pd.tm_min_f) < 0.05f) {
-                    const double cst_d = pd.sconst + pd.salt_dS_per_stack * (L - 1);
-                    const double tm_d = max_ratio<double>(pd, mask, bt, L, cst_d, &used_enum) - 273.15 + pd.tm_shift;
-                    pass = tm_d >= pd.tm_min;
-                } else {
-                    pass = tm >= pd.tm_min_f;
-                }
-            }
-        }
-        tm_out[i] = tm;
-        if (pass_out)
-            pass_out[i] = pass;
+        __syncwarp();
     }
 }
 
@@ -231,10 +343,12 @@ void launch_tm(const ah_site *sites, uint64_t n, const PairDev *pairs_d, int n_p
 {
     if (!n)
         return;
-    uint64_t blocks = (n + 127) / 128;
+    const uint64_t per_block = 8ull * kTmWarps; // sites per block per pass
+    uint64_t blocks = (n + per_block - 1) / per_block;
     if (blocks > 65535)
         blocks = 65535;
-    tm_kernel<<<(unsigned)blocks, 128, 0, s>>>(sites, n, pairs_d, n_pairs, planes, contig_off, tm_out, pass_out, err);
+    tm_kernel<<<(unsigned)blocks, 32 * kTmWarps, 0, s>>>(sites, n, pairs_d, n_pairs, planes, contig_off, tm_out,
+                                                         pass_out, err);
     AH_CUDA(cudaGetLastError());
 }
 
