@@ -234,16 +234,26 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
               __shfl_sync(0xffffffffu, (int)bad, g0 + 2) | __shfl_sync(0xffffffffu, (int)bad, g0 + 3);
         const bool run = act && !bad;
         const float cst = act ? (float)(pd.sconst + pd.salt_dS_per_stack * (L - 1)) : -1.f;
-        // largest denominator over oligos (max-path of dS); all groups take part in the shuffles
+        // Shuffles need all 32 lanes, but the groups' primer lengths differ: every
+        // position loop runs to the warp's longest primer Lw and each group only
+        // reads tables and updates its state while q < L (bt[q] is written for q < L).
+        int Lw = L;
+        for (int d = 16; d >= 1; d >>= 1)
+            Lw = max(Lw, __shfl_xor_sync(0xffffffffu, Lw, d));
+        // largest denominator over oligos (max-path of dS)
         float sm = (run && (mask[0] >> y & 1)) ? pd.term_dS[y * 4 + bt[0]] : -INF;
-        for (int q = 1; q < L; ++q) {
+        for (int q = 1; q < Lw; ++q) {
+            const bool in = q < L;
             float best = -INF;
             for (int x = 0; x < 4; ++x) {
                 const float cx = __shfl_sync(0xffffffffu, sm, g0 + x);
-                const float v = cx + pd.stack_dS[((x * 4 + y) * 4 + bt[q - 1]) * 4 + bt[q]];
-                best = v > best ? v : best;
+                if (in) {
+                    const float v = cx + pd.stack_dS[((x * 4 + y) * 4 + bt[q - 1]) * 4 + bt[q]];
+                    best = v > best ? v : best;
+                }
             }
-            sm = (mask[q] >> y & 1) ? best : -INF;
+            if (in)
+                sm = (mask[q] >> y & 1) ? best : -INF;
         }
         float dm = sm + ((mask[L - 1] >> y & 1) ? pd.term_dS[y * 4 + bt[L - 1]] : 0.f);
         dm = group_reduce(dm, [](float a, float b) { return a > b ? a : b; });
@@ -254,20 +264,25 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
             float c = (dink && (mask[0] >> y & 1)) ? 1000.f * pd.term_dH[y * 4 + bt[0]] - lam * pd.term_dS[y * 4 + bt[0]]
                                                     : INF;
             uint64_t pred = 0;
-            for (int q = 1; q < L; ++q) {
+            for (int q = 1; q < Lw; ++q) {
+                const bool in = q < L;
                 float best = INF;
                 int arg = 0;
                 for (int x = 0; x < 4; ++x) {
                     const float cx = __shfl_sync(0xffffffffu, c, g0 + x);
-                    const int idx = ((x * 4 + y) * 4 + bt[q - 1]) * 4 + bt[q];
-                    const float v = cx + 1000.f * pd.stack_dH[idx] - lam * pd.stack_dS[idx];
-                    if (v < best) {
-                        best = v;
-                        arg = x;
+                    if (in) {
+                        const int idx = ((x * 4 + y) * 4 + bt[q - 1]) * 4 + bt[q];
+                        const float v = cx + 1000.f * pd.stack_dH[idx] - lam * pd.stack_dS[idx];
+                        if (v < best) {
+                            best = v;
+                            arg = x;
+                        }
                     }
                 }
-                c = (mask[q] >> y & 1) ? best : INF;
-                pred |= (uint64_t)arg << (2 * q);
+                if (in) {
+                    c = (mask[q] >> y & 1) ? best : INF;
+                    pred |= (uint64_t)arg << (2 * q);
+                }
             }
             float fin = c + 1000.f * pd.term_dH[y * 4 + bt[L - 1]] - lam * pd.term_dS[y * 4 + bt[L - 1]];
             if (!(c < INF))
@@ -278,10 +293,12 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
             int cur = hit ? __ffs(hit) - 1 : 0;
             // backtrack the oligo: o[L-1] = cur, o[q-1] = pred of lane o[q] at position q
             uint64_t olig = (uint64_t)cur << (2 * (L - 1));
-            for (int q = L - 1; q >= 1; --q) {
+            for (int q = Lw - 1; q >= 1; --q) {
                 const uint64_t pp = __shfl_sync(0xffffffffu, pred, g0 + cur);
-                cur = (int)(pp >> (2 * q) & 3u);
-                olig |= (uint64_t)cur << (2 * (q - 1));
+                if (q < L) {
+                    cur = (int)(pp >> (2 * q) & 3u);
+                    olig |= (uint64_t)cur << (2 * (q - 1));
+                }
             }
             // its dH and dS, split over the four lanes
             float H = 0.f, S = 0.f;
