@@ -2,21 +2,24 @@
 //
 // One CTA packs one tile at a time.  The tile's 32 KB of ASCII are 32 rows of
 // kTileW bytes (row b = flat positions t*kTileBases + b*kTileW + [0, kTileW)),
-// plus the next tile's first 32 bytes ("row 32") for the extension words; a
-// bulk async copy (TMA) brings them into shared memory.  Word j of plane x
-// takes bit b from row b, column j, so thread i builds the four words of
-// columns 4i .. 4i+3 alone, with no cross-lane traffic:
+// plus the next tile's first 32 bytes ("row 32") for the extension words; bulk
+// async copies (TMA) bring them into shared memory, two tiles staged per CTA
+// so the next copy overlaps the current packing.  Word j of plane x takes bit
+// b from row b, column j, so thread i builds the four words of columns
+// 4i .. 4i+3 alone, with no cross-lane traffic:
 //   - per block of 4 rows it reads 4 row words (4 columns each) and
 //     transposes the 4x4 bytes with PRMT, giving one register per column;
-//   - base letters are told apart by bits 1 and 2 of the upper-cased byte
-//     (A 00, C 01, T 10, G 11); those bits of 4 bytes are gathered into 4 bits
-//     by one multiply whose partial products never overlap (no carries);
-//   - a byte is a base only if it equals the letter its two bits name: the
-//     expected letter comes from a 4-entry PRMT table, and an exact per-byte
-//     zero test of the difference marks non-ACGT bytes (N, IUPAC, gaps, ...).
-// Plane words then follow from (h, l, valid) with one LOP3 each.  About 0.2
-// warp instructions per base, so the kernel is bound by HBM: 1 byte read and
-// 0.516 bytes written per base.
+//   - a letter's base is read from bits 1 and 2 of its byte (A 00, C 01,
+//     T 10, G 11); those bits of 4 bytes are gathered into 4 bits by one
+//     multiply whose partial products never overlap (no carries);
+//   - a byte is a base only if it is exactly A/C/G/T in either case: its low
+//     nibble (1, 3, 7, 4) indexes an 8-entry PRMT table holding that letter
+//     (other entries 0xFF; nibbles >= 8 select a sign byte, 0x00 or 0xFF),
+//     and an exact per-byte zero test compares the two.
+// Plane words then follow from (h, l, valid) with one LOP3 each.  The work is
+// split between the logic and the multiply pipes (right shifts and nibble
+// placement are multiplies by run-time powers of two) so that the kernel is
+// bound by HBM: 1 byte read and 0.516 bytes written per base.
 #include "ah_internal.h"
 
 namespace ah {
@@ -24,6 +27,8 @@ namespace {
 
 constexpr int kRowWords = kTileW / 4; // u32 words per ASCII row in shared memory
 constexpr int kPackThreads = kTileW / 4;
+constexpr int kRows = 33;                    // 32 rows + the next tile's head
+constexpr int kBufWords = kRows * kRowWords; // one staged tile
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -64,46 +69,50 @@ __device__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     return true;
 }
 
-// bits 1 and 2 of the 4 bytes of u -> (l, h) as 4-bit masks; valid = byte is exactly A/C/G/T
-__device__ __forceinline__ void classify4(uint32_t u, uint32_t &l4, uint32_t &h4, uint32_t &v4)
+// Classify 4 bytes (one column, 4 rows) and add their bits at the nibble
+// given by pw (a run-time power of two) of the column's L (bit 1 of the
+// letter), H (bit 2) and V (exactly one of A C G T, either case) words.
+__device__ __forceinline__ void classify4(uint32_t raw, uint32_t pw, uint32_t sixteen, uint32_t top4, uint32_t &L,
+                                          uint32_t &H, uint32_t &V)
 {
-    const uint32_t t = (u >> 1) & 0x03030303u;                  // 2h + l per byte
-    l4 = ((t & 0x01010101u) * 0x10204080u) >> 28;               // byte k bit 0 -> bit k
-    h4 = (((t >> 1) & 0x01010101u) * 0x10204080u) >> 28;        // byte k bit 1 -> bit k
-    const uint32_t x = t | (t >> 4);                            // nibbles t0 t1 in byte 0, t2 t3 in byte 2
-    const uint32_t sel = __byte_perm(x, 0, 0x4420);             // 4 selector nibbles
-    const uint32_t expect = __byte_perm(0x47544341u, 0, sel);   // "ACTG"[2h + l] per byte
-    const uint32_t z = u ^ expect;
-    const uint32_t nz = (((z & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | z) & 0x80808080u; // MSB set iff byte != 0
-    v4 = ((nz ^ 0x80808080u) * 0x00204081u) >> 28;              // byte k MSB -> bit k
+    const uint32_t l4 = __umulhi((raw & 0x02020202u) * 0x08102040u, sixteen); // byte k bit 1 -> bit k
+    const uint32_t h4 = __umulhi((raw & 0x04040404u) * 0x04081020u, sixteen); // byte k bit 2 -> bit k
+    const uint32_t n = raw & 0x0F0F0F0Fu;
+    const uint32_t x = n + __umulhi(n, top4);                           // nibbles n0 n1 | n2 n3 (n | n >> 4)
+    const uint32_t sel = __byte_perm(x, 0, 0x4420);                     // 4 selector nibbles
+    const uint32_t expect = __byte_perm(0x43FF41FFu, 0x47FFFF54u, sel); // letter the nibble names
+    const uint32_t z = (raw & 0xDFDFDFDFu) ^ expect;                    // upper-cased letter vs expected
+    const uint32_t s = (z & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;                 // byte MSB: low 7 bits non-zero
+    const uint32_t valid = ~(s | z) & 0x80808080u;                      // byte MSB: z byte == 0
+    const uint32_t v4 = __umulhi(valid * 0x00204081u, sixteen);         // byte k MSB -> bit k
+    L = l4 * pw + L; // the nibbles are disjoint: add = or
+    H = h4 * pw + H;
+    V = v4 * pw + V;
 }
 
 // Build plane words for columns 4*ci .. 4*ci+3 from rows r0 .. r0+31 of the
 // staged tile and store them as words j0 .. j0+3 of the tile's planes.
-__device__ __forceinline__ void pack_columns(const uint32_t *__restrict__ rows, int r0, int ci, uint32_t *__restrict__ dst,
-                                             int j0)
+__device__ __forceinline__ void pack_columns(const uint32_t *__restrict__ rows, int r0, int ci,
+                                             uint32_t *__restrict__ dst, int j0, uint32_t one)
 {
+    const uint32_t sixteen = one << 4, top4 = one << 28;
     uint32_t L[4] = {0, 0, 0, 0}, H[4] = {0, 0, 0, 0}, V[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int rb = 0; rb < 8; ++rb) {
         const int r = r0 + 4 * rb;
-        const uint32_t a = rows[(r + 0) * kRowWords + ci] & 0xDFDFDFDFu; // upper case
-        const uint32_t b = rows[(r + 1) * kRowWords + ci] & 0xDFDFDFDFu;
-        const uint32_t c = rows[(r + 2) * kRowWords + ci] & 0xDFDFDFDFu;
-        const uint32_t d = rows[(r + 3) * kRowWords + ci] & 0xDFDFDFDFu;
+        const uint32_t a = rows[(r + 0) * kRowWords + ci];
+        const uint32_t b = rows[(r + 1) * kRowWords + ci];
+        const uint32_t c = rows[(r + 2) * kRowWords + ci];
+        const uint32_t d = rows[(r + 3) * kRowWords + ci];
         // 4x4 byte transpose: col k = bytes k of a, b, c, d
         const uint32_t t0 = __byte_perm(a, b, 0x5140), t1 = __byte_perm(a, b, 0x7362);
         const uint32_t t2 = __byte_perm(c, d, 0x5140), t3 = __byte_perm(c, d, 0x7362);
         const uint32_t col[4] = {__byte_perm(t0, t2, 0x5410), __byte_perm(t0, t2, 0x7632), __byte_perm(t1, t3, 0x5410),
                                  __byte_perm(t1, t3, 0x7632)};
+        const uint32_t pw = one << (4 * rb);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            uint32_t l4, h4, v4;
-            classify4(col[k], l4, h4, v4);
-            L[k] |= l4 << (4 * rb);
-            H[k] |= h4 << (4 * rb);
-            V[k] |= v4 << (4 * rb);
-        }
+        for (int k = 0; k < 4; ++k)
+            classify4(col[k], pw, sixteen, top4, L[k], H[k], V[k]);
     }
     uint4 pa, pc, pg, pt;
     uint32_t *A = &pa.x, *C = &pc.x, *G = &pg.x, *T = &pt.x;
@@ -123,39 +132,62 @@ __device__ __forceinline__ void pack_columns(const uint32_t *__restrict__ rows, 
 __global__ void __launch_bounds__(kPackThreads) pack_kernel(const uint8_t *__restrict__ seq, uint64_t seq_base,
                                                             uint64_t seq_len, uint64_t n_bases,
                                                             uint32_t *__restrict__ planes, uint64_t t0, uint64_t t1,
-                                                            int tma_ok, int *__restrict__ err)
+                                                            int tma_ok, uint32_t one, int *__restrict__ err)
 {
-    extern __shared__ __align__(128) uint32_t rows[]; // 33 rows of kTileW bytes
-    __shared__ __align__(8) uint64_t bar;
+    extern __shared__ __align__(128) uint32_t smem[]; // two staged tiles
+    __shared__ __align__(8) uint64_t bar[2];
     const uint64_t lim = n_bases < seq_base + seq_len ? n_bases : seq_base + seq_len;
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar[1])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    uint32_t phase = 0;
-    for (uint64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
-        const uint64_t p0 = t * kTileBases; // flat position of row 0, column 0
-        const bool full = tma_ok && p0 >= seq_base && p0 + kTileBases + 32 <= lim;
-        if (full) {
-            if (threadIdx.x == 0) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar)),
-                             "r"((uint32_t)(kTileBases + 32))
-                             : "memory");
-                tma_load(rows, seq + (p0 - seq_base), (uint32_t)kTileBases, &bar);
-                tma_load(rows + 32 * kRowWords, seq + (p0 + kTileBases - seq_base), 32u, &bar);
-            }
-            const bool ok = mbar_wait(&bar, phase);
-            phase ^= 1;
+    // a tile goes through TMA when all of its bytes (and the next tile's head) are present and aligned
+    auto full = [&](uint64_t t) {
+        const uint64_t p0 = t * kTileBases;
+        return tma_ok && p0 >= seq_base && p0 + kTileBases + 32 <= lim;
+    };
+    auto issue = [&](uint64_t t, int sb) {
+        const uint64_t p0 = t * kTileBases;
+        uint32_t *rows = smem + sb * kBufWords;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&bar[sb])),
+                     "r"((uint32_t)(kTileBases + 32))
+                     : "memory");
+        tma_load(rows, seq + (p0 - seq_base), (uint32_t)kTileBases, &bar[sb]);
+        tma_load(rows + 32 * kRowWords, seq + (p0 + kTileBases - seq_base), 32u, &bar[sb]);
+    };
+    uint32_t phase0 = 0, phase1 = 0;
+    const uint64_t first = t0 + blockIdx.x;
+    if (threadIdx.x == 0 && first < t1 && full(first))
+        issue(first, 0);
+    int it = 0;
+    for (uint64_t t = first; t < t1; t += gridDim.x, ++it) {
+        const int sb = it & 1;
+        uint32_t *rows = smem + sb * kBufWords;
+        const uint64_t next = t + gridDim.x;
+        // the other buffer was released by the barrier that ended the previous tile
+        if (threadIdx.x == 0 && next < t1 && full(next))
+            issue(next, sb ^ 1);
+        const uint64_t p0 = t * kTileBases;
+        if (full(t)) {
+            const bool ok = mbar_wait(&bar[sb], sb ? phase1 : phase0);
+            if (sb)
+                phase1 ^= 1;
+            else
+                phase0 ^= 1;
             if (!__syncthreads_and(ok)) {
-                if (threadIdx.x == 0)
+                if (threadIdx.x == 0) {
                     atomicExch(err, kDevTimeout);
-                return; // the copy never landed; nothing else is in flight
+                    if (next < t1 && full(next)) // bounded wait for the copy still in flight
+                        mbar_wait(&bar[sb ^ 1], sb ? phase0 : phase1);
+                }
+                return;
             }
         } else {
             // tail or unaligned tile: byte loads with bounds, zero past the end
-            for (int w = threadIdx.x; w < 33 * kRowWords; w += blockDim.x) {
+            for (int w = threadIdx.x; w < kBufWords; w += blockDim.x) {
                 const int r = w / kRowWords, cw = w % kRowWords;
                 uint32_t v = 0;
                 if (r < 32 || cw < 8) {
@@ -169,10 +201,10 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const uint8_t *__res
             __syncthreads();
         }
         uint32_t *dst = planes + t * 4 * kTileWX;
-        pack_columns(rows, 0, threadIdx.x, dst, 4 * threadIdx.x);
+        pack_columns(rows, 0, threadIdx.x, dst, 4 * threadIdx.x, one);
         if (threadIdx.x < kTileExt / 4) // extension words W .. W+31: rows 1 .. 32, columns 0 .. 31
-            pack_columns(rows, 1, threadIdx.x, dst, kTileW + 4 * threadIdx.x);
-        __syncthreads(); // the rows buffer is reused by the next tile
+            pack_columns(rows, 1, threadIdx.x, dst, kTileW + 4 * threadIdx.x, one);
+        __syncthreads(); // this buffer is refilled two tiles from now
     }
 }
 
@@ -203,17 +235,23 @@ void launch_pack(const uint8_t *seq, uint64_t seq_base, uint64_t seq_len, uint64
     if (t1 <= t0)
         return;
     static_assert(kTileW % 128 == 0 && kTileExt == 32, "pack layout");
-    const size_t smem = 33ull * kTileW; // 32 rows + the next tile's head (33 KB, under the 48 KB default)
-    int dev = 0, sms = 148, per_sm = 1;
+    const size_t smem = 2ull * kBufWords * sizeof(uint32_t); // two staged tiles (67.6 KB)
+    // grid size and the shared-memory opt-in, once per device
+    static int cached_dev = -1, sms = 148, per_sm = 1;
+    int dev = 0;
     AH_CUDA(cudaGetDevice(&dev));
-    AH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_kernel, kPackThreads, smem));
+    if (dev != cached_dev) {
+        AH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        AH_CUDA(cudaFuncSetAttribute(pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_kernel, kPackThreads, smem));
+        cached_dev = dev;
+    }
     uint64_t blocks = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
     if (blocks > t1 - t0)
         blocks = t1 - t0;
     const int tma_ok = ((reinterpret_cast<uintptr_t>(seq) - seq_base) % 16 == 0) ? 1 : 0;
     pack_kernel<<<(unsigned)blocks, kPackThreads, smem, s>>>(seq, seq_base, seq_len, n_bases, planes, t0, t1, tma_ok,
-                                                             err);
+                                                             1u, err);
     AH_CUDA(cudaGetLastError());
 }
 

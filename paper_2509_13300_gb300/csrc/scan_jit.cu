@@ -472,13 +472,22 @@ std::string scan_compile_only(const std::vector<ScanPattern> &pats, const ScanTu
 
 ScanKernel *scan_kernel(const std::vector<ScanPattern> &pats, const ScanTuning &t, int device)
 {
-    std::string src = scan_source(pats, t);
-    std::string key = std::to_string(device) + "\n" + src;
+    // cache key: device, tuning and the patterns (cheap; the source is only generated on a miss)
+    std::string key = std::to_string(device) + "|" + std::to_string(t.R) + "," + std::to_string(t.arith_pct) + "," +
+                      std::to_string(t.min_blocks) + "," + std::to_string(t.order) + "," + std::to_string(t.stages) +
+                      "," + std::to_string(t.warps) + "|";
+    for (auto &p : pats) {
+        key += std::to_string(p.L) + "," + std::to_string(p.k) + "," + std::to_string(p.clamp) + "," +
+               std::to_string(p.pair) + "," + std::to_string(p.primer) + "," + std::to_string(p.strand) + ":";
+        for (int i = 0; i < p.L; ++i)
+            key += (char)('a' + p.mask[i]);
+        key += ";";
+    }
     std::lock_guard<std::mutex> lock(g_mu);
     auto it = g_cache.find(key);
     if (it != g_cache.end())
         return it->second.get();
-
+    const std::string src = scan_source(pats, t);
     bool ok = false;
     std::vector<char> cubin;
     std::string log = compile_cubin(src, &cubin, &ok);

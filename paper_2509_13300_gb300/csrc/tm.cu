@@ -12,8 +12,9 @@
 // Dinkelbach's iteration lam <- ratio(argmin F) climbs to the maximum ratio in
 // a few rounds, provided dS(o) + C < 0 for every oligo (checked first with a
 // max-path pass; otherwise the oligos are enumerated).  Four lanes per site,
-// fp32; when a pass flag is requested and the fp32 Tm is within 0.05 deg C of
-// tm_min the site is recomputed in fp64 so the decision equals the fp64 one.
+// fp32; when a pass flag is requested and the fp32 Tm is within 0.01 deg C of
+// tm_min, the decision is taken in fp64 (one DP at the threshold), so it
+// equals the fp64 decision.
 #include <cmath>
 
 #include "ah_internal.h"
@@ -321,23 +322,63 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
             if (!__any_sync(0xffffffffu, more))
                 break;
         }
+        // Pass flags: the fp32 maximum decides unless it lies within 0.01 deg C of
+        // tm_min (fp32 error here is ~1e-4 deg C).  Those sites are decided in
+        // fp64 by one DP at lam = T = tm_min + 273.15 - shift: max Tm >= tm_min
+        // iff the minimum over oligos of 1000 dH - T (dS + C) is <= 0.
+        const float tm32 = lam - 273.15f + (act ? (float)pd.tm_shift : 0.f);
+        const bool need = pass_out && dink && fabsf(tm32 - pd.tm_min_f) < 0.01f;
+        bool pass64 = false;
+        if (__any_sync(0xffffffffu, need)) {
+            const double T = act ? pd.tm_min + 273.15 - pd.tm_shift : 0.0;
+            const double DINF = INFINITY;
+            double cd = (need && (mask[0] >> y & 1)) ? 1000.0 * pd.term_dH_d[y * 4 + bt[0]] - T * pd.term_dS_d[y * 4 + bt[0]]
+                                                      : DINF;
+            for (int q = 1; q < Lw; ++q) {
+                const bool in = q < L;
+                double best = DINF;
+                for (int x = 0; x < 4; ++x) {
+                    const double cx = __shfl_sync(0xffffffffu, cd, g0 + x);
+                    if (in) {
+                        const int idx = ((x * 4 + y) * 4 + bt[q - 1]) * 4 + bt[q];
+                        const double v = cx + 1000.0 * pd.stack_dH_d[idx] - T * pd.stack_dS_d[idx];
+                        best = v < best ? v : best;
+                    }
+                }
+                if (in)
+                    cd = (mask[q] >> y & 1) ? best : DINF;
+            }
+            double fin = cd + 1000.0 * pd.term_dH_d[y * 4 + bt[L - 1]] - T * pd.term_dS_d[y * 4 + bt[L - 1]];
+            if (!(cd < DINF))
+                fin = DINF;
+            fin = fmin(fin, __shfl_xor_sync(0xffffffffu, fin, 1));
+            fin = fmin(fin, __shfl_xor_sync(0xffffffffu, fin, 2));
+            const double cst_d = act ? pd.sconst + pd.salt_dS_per_stack * (L - 1) : 0.0;
+            pass64 = fin - T * cst_d <= 0.0;
+        }
         if (y == 0 && act) {
             float tm = NAN;
             uint8_t pass = 0;
             if (!bad) {
-                int bti[AH_MAX_PRIMER_LEN];
-                for (int q = 0; q < L; ++q)
-                    bti[q] = bt[q];
-                int used_enum = 0;
-                const float ratio = dink ? lam : max_ratio<float>(pd, mask, bti, L, cst, &used_enum);
-                tm = ratio - 273.15f + (float)pd.tm_shift;
-                if (pass_out) {
-                    if (fabsf(tm - pd.tm_min_f) < 0.05f) {
-                        const double cst_d = pd.sconst + pd.salt_dS_per_stack * (L - 1);
-                        const double tm_d = max_ratio<double>(pd, mask, bti, L, cst_d, &used_enum) - 273.15 + pd.tm_shift;
-                        pass = tm_d >= pd.tm_min;
-                    } else {
-                        pass = tm >= pd.tm_min_f;
+                if (dink) {
+                    tm = tm32;
+                    pass = need ? (uint8_t)pass64 : (uint8_t)(tm >= pd.tm_min_f);
+                } else {
+                    // tables under which some duplex entropy is >= -C: enumerate the oligos
+                    int bti[AH_MAX_PRIMER_LEN];
+                    for (int q = 0; q < L; ++q)
+                        bti[q] = bt[q];
+                    int used_enum = 0;
+                    tm = max_ratio<float>(pd, mask, bti, L, cst, &used_enum) - 273.15f + (float)pd.tm_shift;
+                    if (pass_out) {
+                        if (fabsf(tm - pd.tm_min_f) < 0.01f) {
+                            const double cst_d = pd.sconst + pd.salt_dS_per_stack * (L - 1);
+                            const double tm_d =
+                                max_ratio<double>(pd, mask, bti, L, cst_d, &used_enum) - 273.15 + pd.tm_shift;
+                            pass = tm_d >= pd.tm_min;
+                        } else {
+                            pass = tm >= pd.tm_min_f;
+                        }
                     }
                 }
             }
