@@ -415,8 +415,10 @@ static void duplex_terms(const char *o, const char *b, int L, const or_nn_table 
     if (tab) {
         int e0 = base_index(o[0]) * 4 + base_index(b[0]);
         int e1 = base_index(o[L - 1]) * 4 + base_index(b[L - 1]);
-        H += tab->term_dH[e0] + tab->term_dH[e1];
-        S += tab->term_dS[e0] + tab->term_dS[e1];
+        H += tab->term_dH[e0];
+        S += tab->term_dS[e0];
+        H += tab->term_dH[e1];
+        S += tab->term_dS[e1];
     } else {
         default_terminal(o[0], b[0], &h, &s);
         H += h;
