@@ -386,14 +386,14 @@ PairDev make_pair_dev(const PrimerPair &pp)
     const double x = (pp.params.dnac1_nM - pp.params.dnac2_nM / 2.0) * 1e-9;
     d.sconst = 1.987 * std::log(x);
     const double na = na_eq_mM(pp.params) / 1000.0;
-    d.salt_dS_per_stack = 0.0;
+    d.saltcorr = pp.params.saltcorr;
+    d.log_na = pp.params.saltcorr == 5 ? std::log(na) : 0.0;
     d.tm_shift = 0.0;
     switch (pp.params.saltcorr) {
     case 1: d.tm_shift = 16.6 * std::log10(na); break;
     case 2: d.tm_shift = 16.6 * std::log10(na / (1.0 + 0.7 * na)) + 3.85; break;
     case 3: d.tm_shift = 12.5 * std::log10(na); break;
     case 4: d.tm_shift = 11.7 * std::log10(na); break;
-    case 5: d.salt_dS_per_stack = 0.368 * std::log(na); break;
     default: break;
     }
     for (int i = 0; i < 256; ++i) {

@@ -146,16 +146,19 @@ struct PairDev;
 void launch_validate_sites(const ah_site *sites, uint64_t n, const PairDev *pairs_d, int n_pairs,
                            const uint64_t *contig_off, uint32_t n_contigs, int *err, cudaStream_t s);
 
-// Per-pair constants for the Tm and pair kernels.
+// Per-pair constants for the Tm and pair kernels.  The fp64 fields are the
+// exact host values of the model's constants (same expressions as the
+// reference definition), so device fp64 Tm values can be bit-identical.
 struct PairDev {
     int L[2];
     int min_len, max_len;
     uint8_t mask[2][AH_MAX_PRIMER_LEN];
     float tm_min_f;
+    int saltcorr;
     double tm_min;
-    double sconst;      // R ln(x) [+ salt entropy slope handled per L]
-    double salt_dS_per_stack; // 0.368 ln[Na_eq] for method 5, else 0
-    double tm_shift;    // methods 1-4
+    double sconst;   // R ln(x), x = (dnac1 - dnac2/2) 1e-9
+    double log_na;   // ln([Na_eq] in mol/L); salt method 5 adds 0.368 (L-1) log_na to dS
+    double tm_shift; // salt methods 1-4
     float stack_dH[256], stack_dS[256], term_dH[16], term_dS[16];
     double stack_dH_d[256], stack_dS_d[256], term_dH_d[16], term_dS_d[16];
 };

@@ -2,164 +2,29 @@
 // the maximum over every oligonucleotide of the degenerate primer of the
 // two-state nearest-neighbour Tm against the template at the site,
 //     Tm(o) = 1000 dH(o) / (dS(o) + C) - 273.15 (+ shift for salt methods 1-4),
-// C = R ln(x) (+ 0.368 (L - 1) ln[Na_eq] for salt method 5).
+// C = R ln(x), and salt method 5 adds 0.368 (L - 1) ln[Na_eq] to dS.
 //
 // The paper evaluates every oligo separately.  Here the maximum is found
-// exactly without enumeration: dH and dS are sums over adjacent primer
-// positions, so for a trial value lam the minimum over oligos of
-// F(o) = 1000 dH(o) - lam (dS(o) + C) is a 4-state shortest path along the
-// primer (choice = base at each position, restricted to its IUPAC set), and
+// without enumeration: dH and dS are sums over adjacent primer positions, so
+// for a trial value lam the minimum over oligos of F(o) = 1000 dH(o) -
+// lam (dS(o) + C) is a 4-state shortest path along the primer (the state is
+// the oligo's base at a position, restricted to its IUPAC set), and
 // Dinkelbach's iteration lam <- ratio(argmin F) climbs to the maximum ratio in
 // a few rounds, provided dS(o) + C < 0 for every oligo (checked first with a
-// max-path pass; otherwise the oligos are enumerated).  Four lanes per site,
-// fp32; when a pass flag is requested and the fp32 Tm is within 0.01 deg C of
-// tm_min, the decision is taken in fp64 (one DP at the threshold), so it
-// equals the fp64 decision.
+// max-path pass).  Four lanes per site (one DP state each), fp32.
+//
+// Sites whose fp32 maximum lies within 0.01 deg C of tm_min (fp32 error here
+// is ~1e-4 deg C), and sites under a table where some duplex entropy reaches
+// -C, are evaluated the reference way instead: every oligo, in fp64, with the
+// same operation order as the definition and no fused multiply-adds, the
+// warp's 32 lanes sharing the oligos.  Their pass flag is therefore the exact
+// fp64 decision.
 #include <cmath>
 
 #include "ah_internal.h"
 
 namespace ah {
 namespace {
-
-template <class T> struct Tab {
-    const T *sdH, *sdS, *tdH, *tdS;
-};
-
-__device__ __forceinline__ Tab<float> tab_of(const PairDev &p, float)
-{
-    return {p.stack_dH, p.stack_dS, p.term_dH, p.term_dS};
-}
-__device__ __forceinline__ Tab<double> tab_of(const PairDev &p, double)
-{
-    return {p.stack_dH_d, p.stack_dS_d, p.term_dH_d, p.term_dS_d};
-}
-
-// Max Tm ratio (Kelvin) over oligos with o_i in mask[i], template bases bt[i]
-// opposite o_i.  Returns NaN if it cannot decide (never with sane tables).
-template <class T>
-__device__ T max_ratio(const PairDev &pd, const uint8_t *mask, const int *bt, int L, T cst, int *used_enum)
-{
-    const Tab<T> tb = tab_of(pd, T(0));
-    const T INF = (T)INFINITY;
-    // 1. the largest denominator over oligos: max path of dS
-    T smax[4];
-    for (int x = 0; x < 4; ++x)
-        smax[x] = (mask[0] >> x & 1) ? tb.tdS[x * 4 + bt[0]] : -INF;
-    for (int i = 1; i < L; ++i) {
-        T nx[4];
-        for (int y = 0; y < 4; ++y) {
-            nx[y] = -INF;
-            if (!(mask[i] >> y & 1))
-                continue;
-            for (int x = 0; x < 4; ++x) {
-                T v = smax[x] + tb.sdS[((x * 4 + y) * 4 + bt[i - 1]) * 4 + bt[i]];
-                nx[y] = v > nx[y] ? v : nx[y];
-            }
-        }
-        for (int y = 0; y < 4; ++y)
-            smax[y] = nx[y];
-    }
-    T dmax = -INF;
-    for (int x = 0; x < 4; ++x) {
-        T v = smax[x] + tb.tdS[x * 4 + bt[L - 1]];
-        dmax = v > dmax ? v : dmax;
-    }
-    if (dmax + cst < (T)0) {
-        // 2. Dinkelbach iteration on lam
-        T lam = 0;
-        for (int it = 0; it < 64; ++it) {
-            T c[4], h[4], s[4];
-            for (int x = 0; x < 4; ++x) {
-                if (mask[0] >> x & 1) {
-                    h[x] = tb.tdH[x * 4 + bt[0]];
-                    s[x] = tb.tdS[x * 4 + bt[0]];
-                    c[x] = (T)1000 * h[x] - lam * s[x];
-                } else {
-                    c[x] = INF;
-                    h[x] = s[x] = 0;
-                }
-            }
-            for (int i = 1; i < L; ++i) {
-                T nc[4], nh[4], ns[4];
-                for (int y = 0; y < 4; ++y) {
-                    nc[y] = INF;
-                    nh[y] = ns[y] = 0;
-                    if (!(mask[i] >> y & 1))
-                        continue;
-                    for (int x = 0; x < 4; ++x) {
-                        if (!(c[x] < INF))
-                            continue;
-                        const int idx = ((x * 4 + y) * 4 + bt[i - 1]) * 4 + bt[i];
-                        const T dh = tb.sdH[idx], ds = tb.sdS[idx];
-                        const T v = c[x] + (T)1000 * dh - lam * ds;
-                        if (v < nc[y]) {
-                            nc[y] = v;
-                            nh[y] = h[x] + dh;
-                            ns[y] = s[x] + ds;
-                        }
-                    }
-                }
-                for (int y = 0; y < 4; ++y) {
-                    c[y] = nc[y];
-                    h[y] = nh[y];
-                    s[y] = ns[y];
-                }
-            }
-            T best = INF, bh = 0, bs = 0;
-            for (int x = 0; x < 4; ++x) {
-                if (!(c[x] < INF))
-                    continue;
-                const T th = tb.tdH[x * 4 + bt[L - 1]], ts = tb.tdS[x * 4 + bt[L - 1]];
-                const T v = c[x] + (T)1000 * th - lam * ts;
-                if (v < best) {
-                    best = v;
-                    bh = h[x] + th;
-                    bs = s[x] + ts;
-                }
-            }
-            const T r = (T)1000 * bh / (bs + cst);
-            if (it > 0 && !(r > lam))
-                return lam;
-            lam = r;
-        }
-        return lam;
-    }
-    // 3. fallback: enumerate every oligo
-    *used_enum = 1;
-    int dig[AH_MAX_PRIMER_LEN];
-    for (int i = 0; i < L; ++i) {
-        dig[i] = 0;
-        while (!(mask[i] >> dig[i] & 1))
-            ++dig[i];
-    }
-    T best = -INF;
-    for (int guard = 0; guard < 20000; ++guard) {
-        T H = tb.tdH[dig[0] * 4 + bt[0]] + tb.tdH[dig[L - 1] * 4 + bt[L - 1]];
-        T S = tb.tdS[dig[0] * 4 + bt[0]] + tb.tdS[dig[L - 1] * 4 + bt[L - 1]];
-        for (int i = 1; i < L; ++i) {
-            const int idx = ((dig[i - 1] * 4 + dig[i]) * 4 + bt[i - 1]) * 4 + bt[i];
-            H += tb.sdH[idx];
-            S += tb.sdS[idx];
-        }
-        const T r = (T)1000 * H / (S + cst);
-        best = r > best ? r : best;
-        int i = L - 1;
-        for (; i >= 0; --i) {
-            do {
-                ++dig[i];
-            } while (dig[i] < 4 && !(mask[i] >> dig[i] & 1));
-            if (dig[i] < 4)
-                break;
-            dig[i] = 0;
-            while (!(mask[i] >> dig[i] & 1))
-                ++dig[i];
-        }
-        if (i < 0)
-            break;
-    }
-    return best;
-}
 
 __device__ __forceinline__ int base_at(const uint32_t *__restrict__ planes, uint64_t P)
 {
@@ -174,13 +39,6 @@ __device__ __forceinline__ int base_at(const uint32_t *__restrict__ planes, uint
     return code;
 }
 
-// Four lanes per site: lane y of a group holds the DP state "oligo base at
-// the current position = y".  Each step takes the four predecessor costs by
-// shuffles, keeps the best predecessor (2 bits per position, so the argmin
-// oligo is recovered by a backtrack across the group's lanes) and the
-// oligo's dH, dS are then summed by the four lanes together.  Eight sites per
-// warp; the rare enumeration fallback and the fp64 recompute near tm_min run
-// on lane 0 of the group with the single-thread routine above.
 constexpr int kTmWarps = 4;
 
 template <class F> __device__ __forceinline__ float group_reduce(float v, F op)
@@ -190,6 +48,37 @@ template <class F> __device__ __forceinline__ float group_reduce(float v, F op)
     return v;
 }
 
+// fp64 Tm of oligo `olig` (2-bit codes) against template bases bt, in the
+// operation order of the definition: stacks 0..L-2, then the 5' and the 3'
+// initiation terms, then the salt entropy, then the ratio; _rn intrinsics so
+// nothing is contracted.
+__device__ double exact_tm(const PairDev &pd, const int8_t *bt, int L, uint64_t olig)
+{
+    double H = 0.0, S = 0.0;
+    for (int q = 0; q + 1 < L; ++q) {
+        const int a = (int)(olig >> (2 * q) & 3u), b = (int)(olig >> (2 * (q + 1)) & 3u);
+        const int idx = ((a * 4 + b) * 4 + bt[q]) * 4 + bt[q + 1];
+        H = __dadd_rn(H, pd.stack_dH_d[idx]);
+        S = __dadd_rn(S, pd.stack_dS_d[idx]);
+    }
+    const int o0 = (int)(olig & 3u), oL = (int)(olig >> (2 * (L - 1)) & 3u);
+    H = __dadd_rn(H, pd.term_dH_d[o0 * 4 + bt[0]]);
+    S = __dadd_rn(S, pd.term_dS_d[o0 * 4 + bt[0]]);
+    H = __dadd_rn(H, pd.term_dH_d[oL * 4 + bt[L - 1]]);
+    S = __dadd_rn(S, pd.term_dS_d[oL * 4 + bt[L - 1]]);
+    if (pd.saltcorr == 5)
+        S = __dadd_rn(S, __dmul_rn(__dmul_rn(0.368, (double)(L - 1)), pd.log_na));
+    double tm = __dsub_rn(__ddiv_rn(__dmul_rn(1000.0, H), __dadd_rn(S, pd.sconst)), 273.15);
+    if (pd.saltcorr >= 1 && pd.saltcorr <= 4)
+        tm = __dadd_rn(tm, pd.tm_shift);
+    return tm;
+}
+
+// Four lanes per site: lane y of a group holds the DP state "oligo base at
+// the current position = y".  Each step takes the four predecessor costs by
+// shuffles and keeps the best predecessor (2 bits per position), so the
+// argmin oligo is recovered by a backtrack across the group's lanes; its dH,
+// dS are then summed by the four lanes together.  Eight sites per warp.
 __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__restrict__ sites, uint64_t n,
                                                            const PairDev *__restrict__ pairs, int n_pairs,
                                                            const uint32_t *__restrict__ planes,
@@ -209,15 +98,15 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
         ah_site s{};
         if (live)
             s = sites[i];
-        bool bad_rec = live && (s.pair >= n_pairs || s.primer > 1 || s.strand > 1);
+        const bool bad_rec = live && (s.pair >= n_pairs || s.primer > 1 || s.strand > 1);
         if (bad_rec && y == 0)
             atomicExch(err, kDevBounds);
         const bool act = live && !bad_rec;
         const PairDev &pd = pairs[act ? s.pair : 0];
         const int L = act ? pd.L[s.primer] : 2;
         const uint8_t *mask = pd.mask[act ? s.primer : 0];
-        // template base opposite each primer position (-1: not a base)
-        // every entry the DP reads is written (0..3), also for groups without a live site
+        // template base opposite each primer position; every entry the DP reads
+        // is written (0..3), also for groups without a live site
         bool bad = false;
         if (act) {
             const uint64_t P = contig_off[s.contig] + s.pos;
@@ -234,7 +123,8 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
         bad = __shfl_sync(0xffffffffu, (int)bad, g0) | __shfl_sync(0xffffffffu, (int)bad, g0 + 1) |
               __shfl_sync(0xffffffffu, (int)bad, g0 + 2) | __shfl_sync(0xffffffffu, (int)bad, g0 + 3);
         const bool run = act && !bad;
-        const float cst = act ? (float)(pd.sconst + pd.salt_dS_per_stack * (L - 1)) : -1.f;
+        const float cst =
+            act ? (float)(pd.sconst + (pd.saltcorr == 5 ? 0.368 * (double)(L - 1) * pd.log_na : 0.0)) : -1.f;
         // Shuffles need all 32 lanes, but the groups' primer lengths differ: every
         // position loop runs to the warp's longest primer Lw and each group only
         // reads tables and updates its state while q < L (bt[q] is written for q < L).
@@ -289,10 +179,10 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
             if (!(c < INF))
                 fin = INF;
             // argmin over the group's four end states (ties: lowest base)
-            float fmin = group_reduce(fin, [](float a, float b) { return a < b ? a : b; });
+            const float fmin = group_reduce(fin, [](float a, float b) { return a < b ? a : b; });
             const unsigned hit = __ballot_sync(0xffffffffu, fin == fmin) >> g0 & 0xFu;
             int cur = hit ? __ffs(hit) - 1 : 0;
-            // backtrack the oligo: o[L-1] = cur, o[q-1] = pred of lane o[q] at position q
+            // backtrack the oligo: o[L-1] = cur, o[q-1] = predecessor kept by lane o[q] at q
             uint64_t olig = (uint64_t)cur << (2 * (L - 1));
             for (int q = Lw - 1; q >= 1; --q) {
                 const uint64_t pp = __shfl_sync(0xffffffffu, pred, g0 + cur);
@@ -322,64 +212,63 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
             if (!__any_sync(0xffffffffu, more))
                 break;
         }
-        // Pass flags: the fp32 maximum decides unless it lies within 0.01 deg C of
-        // tm_min (fp32 error here is ~1e-4 deg C).  Those sites are decided in
-        // fp64 by one DP at lam = T = tm_min + 273.15 - shift: max Tm >= tm_min
-        // iff the minimum over oligos of 1000 dH - T (dS + C) is <= 0.
         const float tm32 = lam - 273.15f + (act ? (float)pd.tm_shift : 0.f);
-        const bool need = pass_out && dink && fabsf(tm32 - pd.tm_min_f) < 0.01f;
-        bool pass64 = false;
-        if (__any_sync(0xffffffffu, need)) {
-            const double T = act ? pd.tm_min + 273.15 - pd.tm_shift : 0.0;
-            const double DINF = INFINITY;
-            double cd = (need && (mask[0] >> y & 1)) ? 1000.0 * pd.term_dH_d[y * 4 + bt[0]] - T * pd.term_dS_d[y * 4 + bt[0]]
-                                                      : DINF;
-            for (int q = 1; q < Lw; ++q) {
-                const bool in = q < L;
-                double best = DINF;
-                for (int x = 0; x < 4; ++x) {
-                    const double cx = __shfl_sync(0xffffffffu, cd, g0 + x);
-                    if (in) {
-                        const int idx = ((x * 4 + y) * 4 + bt[q - 1]) * 4 + bt[q];
-                        const double v = cx + 1000.0 * pd.stack_dH_d[idx] - T * pd.stack_dS_d[idx];
-                        best = v < best ? v : best;
-                    }
+        // sites decided the reference way (see the file comment), one at a time with all 32 lanes
+        const bool exact = run && (!dink || (pass_out && fabsf(tm32 - pd.tm_min_f) < 0.01f));
+        unsigned todo = __ballot_sync(0xffffffffu, exact && y == 0);
+        double tm_exact = 0.0;
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int sp = __shfl_sync(0xffffffffu, act ? (int)s.pair : 0, src);
+            const int spr = __shfl_sync(0xffffffffu, act ? (int)s.primer : 0, src);
+            const int sL = __shfl_sync(0xffffffffu, L, src);
+            const PairDev &qd = pairs[sp];
+            const uint8_t *qm = qd.mask[spr];
+            const int8_t *qb = bts[warp][src >> 2];
+            int deg = 1;
+            for (int q = 0; q < sL; ++q)
+                deg *= __popc(qm[q]);
+            double best = -INFINITY;
+            for (int o = lane; o < deg; o += 32) {
+                // oligo number o -> bases (mixed radix over the positions' sets)
+                uint64_t olig = 0;
+                int rem = o;
+                for (int q = sL - 1; q >= 0; --q) {
+                    const int nq = __popc(qm[q]);
+                    int d = rem % nq;
+                    rem /= nq;
+                    int base_q = 0;
+                    for (int x = 0; x < 4; ++x)
+                        if (qm[q] >> x & 1) {
+                            if (d == 0) {
+                                base_q = x;
+                                break;
+                            }
+                            --d;
+                        }
+                    olig |= (uint64_t)base_q << (2 * q);
                 }
-                if (in)
-                    cd = (mask[q] >> y & 1) ? best : DINF;
+                const double t = exact_tm(qd, qb, sL, olig);
+                best = t > best ? t : best;
             }
-            double fin = cd + 1000.0 * pd.term_dH_d[y * 4 + bt[L - 1]] - T * pd.term_dS_d[y * 4 + bt[L - 1]];
-            if (!(cd < DINF))
-                fin = DINF;
-            fin = fmin(fin, __shfl_xor_sync(0xffffffffu, fin, 1));
-            fin = fmin(fin, __shfl_xor_sync(0xffffffffu, fin, 2));
-            const double cst_d = act ? pd.sconst + pd.salt_dS_per_stack * (L - 1) : 0.0;
-            pass64 = fin - T * cst_d <= 0.0;
+            for (int d = 16; d >= 1; d >>= 1) {
+                const double o2 = __shfl_xor_sync(0xffffffffu, best, d);
+                best = o2 > best ? o2 : best;
+            }
+            if (lane == src)
+                tm_exact = best;
         }
         if (y == 0 && act) {
             float tm = NAN;
             uint8_t pass = 0;
             if (!bad) {
-                if (dink) {
-                    tm = tm32;
-                    pass = need ? (uint8_t)pass64 : (uint8_t)(tm >= pd.tm_min_f);
+                if (exact) {
+                    tm = (float)tm_exact;
+                    pass = tm_exact >= pd.tm_min;
                 } else {
-                    // tables under which some duplex entropy is >= -C: enumerate the oligos
-                    int bti[AH_MAX_PRIMER_LEN];
-                    for (int q = 0; q < L; ++q)
-                        bti[q] = bt[q];
-                    int used_enum = 0;
-                    tm = max_ratio<float>(pd, mask, bti, L, cst, &used_enum) - 273.15f + (float)pd.tm_shift;
-                    if (pass_out) {
-                        if (fabsf(tm - pd.tm_min_f) < 0.01f) {
-                            const double cst_d = pd.sconst + pd.salt_dS_per_stack * (L - 1);
-                            const double tm_d =
-                                max_ratio<double>(pd, mask, bti, L, cst_d, &used_enum) - 273.15 + pd.tm_shift;
-                            pass = tm_d >= pd.tm_min;
-                        } else {
-                            pass = tm >= pd.tm_min_f;
-                        }
-                    }
+                    tm = tm32;
+                    pass = tm32 >= pd.tm_min_f;
                 }
             }
             tm_out[i] = tm;
