@@ -205,8 +205,11 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
             H += pd.term_dH[o0 * 4 + bt[0]] + pd.term_dH[oL * 4 + bt[L - 1]];
             S += pd.term_dS[o0 * 4 + bt[0]] + pd.term_dS[oL * 4 + bt[L - 1]];
             const float r = 1000.f * H / (S + cst);
-            // warp-uniform loop: stop when no group still improves
-            const bool more = dink && (it == 0 || r > lam);
+            // Warp-uniform loop: stop when no group still improves by more than
+            // 1e-4 K.  In fp32 two oligos of nearly equal ratio could otherwise
+            // trade places by one ulp for many rounds; 1e-4 K is far below the
+            // 0.01 deg C tolerance, and sites near tm_min are decided exactly below.
+            const bool more = dink && (it == 0 || r > lam + 1e-4f);
             if (more)
                 lam = r;
             if (!__any_sync(0xffffffffu, more))
@@ -236,8 +239,20 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                 int rem = o;
                 for (int q = sL - 1; q >= 0; --q) {
                     const int nq = __popc(qm[q]);
-                    int d = rem % nq;
-                    rem /= nq;
+                    int d; // rem % nq, rem /= nq for nq in 1..4 (rem < 10000)
+                    if (nq == 1) {
+                        d = 0;
+                    } else if (nq == 2) {
+                        d = rem & 1;
+                        rem >>= 1;
+                    } else if (nq == 4) {
+                        d = rem & 3;
+                        rem >>= 2;
+                    } else {
+                        const int q3 = (rem * 43691) >> 17; // rem / 3, exact for rem < 2^16
+                        d = rem - 3 * q3;
+                        rem = q3;
+                    }
                     int base_q = 0;
                     for (int x = 0; x < 4; ++x)
                         if (qm[q] >> x & 1) {
