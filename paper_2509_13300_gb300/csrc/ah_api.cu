@@ -194,7 +194,6 @@ struct Stage {
 // kernel and one pass per 8 key bits; a device-wide scan runs an init kernel
 // and a scan kernel.
 int cub_sort_launches(uint64_t n, int bits) { return n <= 1 ? 0 : 2 + (bits + 7) / 8; }
-int cub_scan_launches(uint64_t n) { return n == 0 ? 0 : 2; }
 
 void prof_flush(ah_ctx *c)
 {
@@ -526,6 +525,11 @@ void sort_decode(ah_ctx *c, const GenomeSet &gs, uint32_t n_pairs, const uint64_
                  cudaStream_t st)
 {
     const int pbits = std::max(1, bit_length(gs.n_bases));
+    if (count <= kSmallSort) { // one block: sort in shared memory and decode
+        Stage sg(c, "sort", st, 1);
+        launch_sort_decode_small(keys, count, pbits, gs.contig_off, gs.n_contigs, gs.contig_genome, dst, st);
+        return;
+    }
     const int end_bit = 10 + pbits + bit_length(n_pairs - 1);
     size_t tb = sort_keys_temp_bytes(count, end_bit);
     void *temp = scratch(c, "sort_temp", tb);
@@ -978,7 +982,7 @@ ah_status ah_run(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t 
             size_t tb = scan_u64_temp_bytes(ns);
             void *temp = scratch(c, "scan_temp", tb);
             {
-                Stage sg(c, "pair", st, 2 + cub_scan_launches(ns));
+                Stage sg(c, "pair", st, 2 + scan_u64_launches(ns));
                 launch_pair_count(sites, ns, filt, pd, counts, st);
                 exclusive_scan_u64(temp, tb, counts, offs, ns, st);
                 launch_total(offs, counts, ns, c->d_aux, st);
@@ -997,7 +1001,7 @@ ah_status ah_run(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t 
             size_t tb2 = scan_u64_temp_bytes(na + 1);
             void *temp2 = scratch(c, "scan_temp", tb2);
             {
-                Stage sg(c, "fetch", st, (na ? 1 : 0) + cub_scan_launches(na + 1));
+                Stage sg(c, "fetch", st, (na ? 1 : 0) + scan_u64_launches(na + 1));
                 AH_CUDA(cudaMemsetAsync(len + na, 0, sizeof(uint64_t), st));
                 launch_fetch_lengths(amps, na, gs.contig_off, gs.n_contigs, len, c->d_err, st);
                 exclusive_scan_u64(temp2, tb2, len, qoff, na + 1, st);
@@ -1091,7 +1095,7 @@ ah_status ah_pair(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
         size_t tb = scan_u64_temp_bytes(n);
         void *temp = scratch(c, "scan_temp", tb);
         {
-            Stage sg(c, "pair", st, 1 + cub_scan_launches(n));
+            Stage sg(c, "pair", st, 1 + scan_u64_launches(n));
             launch_pair_count(s, n, ps, pd, counts, st);
             exclusive_scan_u64(temp, tb, counts, offs, n, st);
         }
@@ -1133,7 +1137,7 @@ ah_status ah_fetch(ah_ctx *c, uint32_t set_id, const ah_amplicon *amplicons, uin
         size_t tb = scan_u64_temp_bytes(n + 1);
         void *temp = scratch(c, "scan_temp", tb);
         {
-            Stage sg(c, "fetch", st, (n ? 1 : 0) + cub_scan_launches(n + 1));
+            Stage sg(c, "fetch", st, (n ? 1 : 0) + scan_u64_launches(n + 1));
             launch_fetch_lengths(a, n, gs.contig_off, gs.n_contigs, len, c->d_err, st);
             exclusive_scan_u64(temp, tb, len, offs, n + 1, st);
         }

@@ -138,6 +138,10 @@ void sort_keys(void *temp, size_t temp_bytes, const uint64_t *in, uint64_t *out,
                int end_bit, cudaStream_t s);
 void launch_decode_keys(const uint64_t *keys, uint64_t n, int pbits, const uint64_t *contig_off, uint32_t n_contigs,
                         const uint32_t *contig_genome, ah_site *out, cudaStream_t s);
+// One-block sort + decode for up to kSmallSort keys; false (nothing launched) above that.
+constexpr uint64_t kSmallSort = 16384;
+bool launch_sort_decode_small(const uint64_t *keys, uint64_t n, int pbits, const uint64_t *contig_off,
+                              uint32_t n_contigs, const uint32_t *contig_genome, ah_site *out, cudaStream_t s);
 
 struct PairDev;
 // Check user-supplied sites before any kernel indexes memory with them:
@@ -173,6 +177,10 @@ void launch_pair_count(const ah_site *sites, uint64_t n, const uint8_t *pass, co
 // *out = offs[n-1] + counts[n-1] (the total of an exclusive scan), on the device
 void launch_total(const uint64_t *offs, const uint64_t *counts, uint64_t n, uint64_t *out, cudaStream_t s);
 size_t scan_u64_temp_bytes(uint64_t n);
+// Exclusive scan of n u64 values; one block (no temporary) for n <= kSmallScan, CUB above.
+constexpr uint64_t kSmallScan = 65536;
+// number of kernels exclusive_scan_u64 launches for n values
+int scan_u64_launches(uint64_t n);
 void exclusive_scan_u64(void *temp, size_t temp_bytes, const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s);
 void launch_pair_write(const ah_site *sites, uint64_t n, const uint8_t *pass, const PairDev *pairs_d,
                        const uint64_t *offsets, ah_amplicon *out, uint64_t cap, cudaStream_t s);

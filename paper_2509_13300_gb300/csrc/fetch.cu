@@ -1,7 +1,7 @@
 // Amplicon sequences (Sec. 2.1, Visualization: the main output is a FASTA of
 // amplicon sequences).  Decoded from the packed planes: upper case, 'N' for
 // any position with no base plane set; RF amplicons reverse-complemented so
-// they read from the forward primer.  One warp per amplicon.
+// they read from the forward primer.  One block per amplicon.
 #include "ah_internal.h"
 
 namespace ah {
@@ -21,21 +21,22 @@ __global__ void fetch_len_kernel(const ah_amplicon *__restrict__ a, uint64_t n, 
     }
 }
 
-__global__ void fetch_kernel(const ah_amplicon *__restrict__ a, uint64_t n, const uint64_t *__restrict__ offsets,
-                             const uint32_t *__restrict__ planes, const uint64_t *__restrict__ contig_off,
-                             char *__restrict__ out)
+// One block per amplicon: consecutive threads decode consecutive positions,
+// which sit in consecutive words of a plane row, so the loads coalesce.
+__global__ void __launch_bounds__(256) fetch_kernel(const ah_amplicon *__restrict__ a, uint64_t n,
+                                                    const uint64_t *__restrict__ offsets,
+                                                    const uint32_t *__restrict__ planes,
+                                                    const uint64_t *__restrict__ contig_off, char *__restrict__ out)
 {
-    const int lane = threadIdx.x & 31;
-    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
-        const ah_amplicon am = a[i];
+    for (uint64_t i = blockIdx.x; i < n; i += gridDim.x) {
         const uint64_t len = offsets[i + 1] - offsets[i];
         if (len == 0)
             continue;
+        const ah_amplicon am = a[i];
         const uint64_t base = contig_off[am.contig] + am.start;
         const bool rc = am.orient == 1;
         char *o = out + offsets[i];
-        for (uint64_t q = lane; q < len; q += 32) {
+        for (uint64_t q = threadIdx.x; q < len; q += blockDim.x) {
             const uint64_t P = base + (rc ? len - 1 - q : q);
             const uint64_t t = P / kTileBases, r = P % kTileBases;
             const int b = (int)(r / kTileW), j = (int)(r % kTileW);
@@ -71,9 +72,7 @@ void launch_fetch(const ah_amplicon *a, uint64_t n, const uint64_t *offsets, con
 {
     if (!n)
         return;
-    uint64_t blocks = (n + 7) / 8;
-    if (blocks > 16384)
-        blocks = 16384;
+    const uint64_t blocks = n < 8192 ? n : 8192;
     fetch_kernel<<<(unsigned)blocks, 256, 0, s>>>(a, n, offsets, planes, contig_off, out);
     AH_CUDA(cudaGetLastError());
 }

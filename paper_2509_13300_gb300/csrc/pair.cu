@@ -195,6 +195,33 @@ __global__ void total_kernel(const uint64_t *__restrict__ offs, const uint64_t *
     *out = n ? offs[n - 1] + counts[n - 1] : 0;
 }
 
+// One-block exclusive scan: each thread sums a contiguous chunk, the block
+// scans the chunk totals, each thread writes its chunk's prefixes.
+__global__ void __launch_bounds__(1024) scan_small_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
+                                                          uint32_t n)
+{
+    __shared__ uint64_t part[1024];
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    const uint32_t lo = min(n, threadIdx.x * per), hi = min(n, lo + per);
+    uint64_t sum = 0;
+    for (uint32_t i = lo; i < hi; ++i)
+        sum += in[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (uint32_t d = 1; d < blockDim.x; d <<= 1) { // Hillis-Steele inclusive scan of the chunk totals
+        const uint64_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint64_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (uint32_t i = lo; i < hi; ++i) {
+        const uint64_t v = in[i];
+        out[i] = run;
+        run += v;
+    }
+}
+
 unsigned grid_for(uint64_t n, int threads)
 {
     uint64_t b = (n + threads - 1) / threads;
@@ -231,8 +258,17 @@ size_t scan_u64_temp_bytes(uint64_t n)
 
 void exclusive_scan_u64(void *temp, size_t temp_bytes, const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s)
 {
+    if (n == 0)
+        return;
+    if (n <= kSmallScan) {
+        scan_small_kernel<<<1, 1024, 0, s>>>(in, out, (uint32_t)n);
+        AH_CUDA(cudaGetLastError());
+        return;
+    }
     AH_CUDA(cub::DeviceScan::ExclusiveSum(temp, temp_bytes, in, out, (int64_t)n, s));
 }
+
+int scan_u64_launches(uint64_t n) { return n == 0 ? 0 : n <= kSmallScan ? 1 : 2; }
 
 void launch_pair_write(const ah_site *sites, uint64_t n, const uint8_t *pass, const PairDev *pairs_d,
                        const uint64_t *offsets, ah_amplicon *out, uint64_t cap, cudaStream_t s)
