@@ -320,3 +320,12 @@ def test_run_equals_separate_calls_and_oracle(ctx, tm_filter):
     assert out.n_sites == n and out.n_amplicons == m and out.n_seq == len(seqs)
     assert sites.tobytes() == o["sites"].tobytes() and not small.view(np.uint8).any()
     ctx.ah_unload_genomes(sid)
+
+
+def test_many_sites_take_the_device_wide_paths(ctx):
+    """More than 16384 sites (device-wide sort instead of the one-block sort)
+    and more than 65536 values in the pairing prefix sum (device-wide scan)."""
+    w = synth.random_small(41, n_bases=20_000, n_contigs=8, L_f=6, L_r=5, k=6, min_len=12, max_len=12)
+    o = oracle_run(w)
+    assert len(o["sites"]) > 65536
+    assert_parity(gpu_run(ctx, w), o)
