@@ -525,12 +525,12 @@ void sort_decode(ah_ctx *c, const GenomeSet &gs, uint32_t n_pairs, const uint64_
                  cudaStream_t st)
 {
     const int pbits = std::max(1, bit_length(gs.n_bases));
-    if (count <= kSmallSort) { // one block: sort in shared memory and decode
+    const int end_bit = 10 + pbits + bit_length(n_pairs - 1);
+    if (count <= kSmallSort) { // one block: sort in registers and decode
         Stage sg(c, "sort", st, 1);
-        launch_sort_decode_small(keys, count, pbits, gs.contig_off, gs.n_contigs, gs.contig_genome, dst, st);
+        launch_sort_decode_small(keys, count, end_bit, pbits, gs.contig_off, gs.n_contigs, gs.contig_genome, dst, st);
         return;
     }
-    const int end_bit = 10 + pbits + bit_length(n_pairs - 1);
     size_t tb = sort_keys_temp_bytes(count, end_bit);
     void *temp = scratch(c, "sort_temp", tb);
     uint64_t *sorted = (uint64_t *)scratch(c, "scan_keys_sorted", count * sizeof(uint64_t));

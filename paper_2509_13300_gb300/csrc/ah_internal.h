@@ -140,7 +140,7 @@ void launch_decode_keys(const uint64_t *keys, uint64_t n, int pbits, const uint6
                         const uint32_t *contig_genome, ah_site *out, cudaStream_t s);
 // One-block sort + decode for up to kSmallSort keys; false (nothing launched) above that.
 constexpr uint64_t kSmallSort = 16384;
-bool launch_sort_decode_small(const uint64_t *keys, uint64_t n, int pbits, const uint64_t *contig_off,
+bool launch_sort_decode_small(const uint64_t *keys, uint64_t n, int end_bit, int pbits, const uint64_t *contig_off,
                               uint32_t n_contigs, const uint32_t *contig_genome, ah_site *out, cudaStream_t s);
 
 struct PairDev;

@@ -100,42 +100,42 @@ void launch_decode_keys(const uint64_t *keys, uint64_t n, int pbits, const uint6
 } // namespace ah
 
 // ---------------------------------------------------------------------------
-// Small-count fast path: one block sorts up to kSmallSort keys in shared
-// memory (bitonic network; keys are unique, so stability does not matter) and
-// writes the decoded site records directly.  A handful of launches of CUB's
-// device-wide sort cost more than the whole job at these sizes.
+// Small-count fast path: one block of 1024 threads sorts up to kSmallSort
+// keys held in registers (16 per thread) with a block-wide radix sort over the
+// key bits in use, then writes the decoded site records directly.  A series
+// of device-wide sort launches costs more than the whole job at these sizes.
 // ---------------------------------------------------------------------------
+#include <cub/block/block_radix_sort.cuh>
+
 namespace ah {
 namespace {
 
-__global__ void __launch_bounds__(1024) sort_decode_small_kernel(const uint64_t *__restrict__ keys, uint32_t n,
-                                                                 uint32_t npow2, int pbits,
-                                                                 const uint64_t *__restrict__ contig_off,
-                                                                 uint32_t n_contigs,
-                                                                 const uint32_t *__restrict__ contig_genome,
-                                                                 ah_site *__restrict__ out)
+constexpr int kSortThreads = 1024, kSortItems = 16;
+static_assert(kSortThreads * kSortItems == (int)kSmallSort, "one block holds the small sort");
+
+__global__ void __launch_bounds__(kSortThreads) sort_decode_small_kernel(const uint64_t *__restrict__ keys,
+                                                                         uint32_t n, int end_bit, int pbits,
+                                                                         const uint64_t *__restrict__ contig_off,
+                                                                         uint32_t n_contigs,
+                                                                         const uint32_t *__restrict__ contig_genome,
+                                                                         ah_site *__restrict__ out)
 {
-    extern __shared__ uint64_t sk[];
-    for (uint32_t i = threadIdx.x; i < npow2; i += blockDim.x)
-        sk[i] = i < n ? keys[i] : ~0ull;
-    __syncthreads();
-    for (uint32_t size = 2; size <= npow2; size <<= 1) {
-        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (uint32_t t = threadIdx.x; t < npow2 / 2; t += blockDim.x) {
-                const uint32_t lo = 2 * stride * (t / stride) + (t % stride);
-                const uint32_t hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const uint64_t a = sk[lo], b = sk[hi];
-                if ((a > b) == up) {
-                    sk[lo] = b;
-                    sk[hi] = a;
-                }
-            }
-            __syncthreads();
-        }
+    using Sort = cub::BlockRadixSort<uint64_t, kSortThreads, kSortItems>;
+    extern __shared__ __align__(16) unsigned char sort_smem[]; // Sort::TempStorage (> 48 KB: dynamic)
+    typename Sort::TempStorage &tmp = *reinterpret_cast<typename Sort::TempStorage *>(sort_smem);
+    uint64_t k[kSortItems];
+#pragma unroll
+    for (int q = 0; q < kSortItems; ++q) { // blocked arrangement: thread t holds keys t*16 .. t*16+15
+        const uint32_t i = threadIdx.x * kSortItems + q;
+        k[q] = i < n ? keys[i] : ~0ull; // padding sorts last
     }
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const uint64_t key = sk[i];
+    Sort(tmp).Sort(k, 8, end_bit > 8 ? end_bit : 9);
+#pragma unroll
+    for (int q = 0; q < kSortItems; ++q) {
+        const uint32_t i = threadIdx.x * kSortItems + q;
+        if (i >= n)
+            continue;
+        const uint64_t key = k[q];
         const uint64_t pp = key >> 10;
         const uint64_t P = pp & ((1ull << pbits) - 1);
         uint32_t lo = 0, hi = n_contigs;
@@ -160,25 +160,22 @@ __global__ void __launch_bounds__(1024) sort_decode_small_kernel(const uint64_t 
 
 } // namespace
 
-bool launch_sort_decode_small(const uint64_t *keys, uint64_t n, int pbits, const uint64_t *contig_off,
+bool launch_sort_decode_small(const uint64_t *keys, uint64_t n, int end_bit, int pbits, const uint64_t *contig_off,
                               uint32_t n_contigs, const uint32_t *contig_genome, ah_site *out, cudaStream_t s)
 {
     if (n == 0 || n > kSmallSort)
         return false;
-    uint32_t npow2 = 1;
-    while (npow2 < n)
-        npow2 <<= 1;
-    const size_t smem = (size_t)npow2 * sizeof(uint64_t);
+    using Sort = cub::BlockRadixSort<uint64_t, kSortThreads, kSortItems>;
+    const size_t smem = sizeof(typename Sort::TempStorage);
     static int attr_dev = -1;
     int dev = 0;
     AH_CUDA(cudaGetDevice(&dev));
     if (dev != attr_dev) {
-        AH_CUDA(cudaFuncSetAttribute(sort_decode_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(kSmallSort * sizeof(uint64_t))));
+        AH_CUDA(cudaFuncSetAttribute(sort_decode_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_dev = dev;
     }
-    sort_decode_small_kernel<<<1, 1024, smem, s>>>(keys, (uint32_t)n, npow2, pbits, contig_off, n_contigs,
-                                                   contig_genome, out);
+    sort_decode_small_kernel<<<1, kSortThreads, smem, s>>>(keys, (uint32_t)n, end_bit, pbits, contig_off, n_contigs,
+                                                           contig_genome, out);
     AH_CUDA(cudaGetLastError());
     return true;
 }
