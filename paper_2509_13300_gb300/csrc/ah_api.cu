@@ -25,7 +25,7 @@ struct ah_ctx {
     std::map<uint32_t, PrimerPair> pairs;
     uint32_t next_pair = 1;
     std::map<std::string, Scratch> scratch;
-    // device flag block: [0] hit counter, [1] auxiliary total, [2] error word
+    // device flag block: [0] hit counter, [1] auxiliary total, [2] error word, [3] Tm queue length
     uint64_t *d_flags = nullptr;
     uint64_t *d_counter = nullptr;
     uint64_t *d_aux = nullptr;
@@ -973,8 +973,10 @@ ah_status ah_run(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t 
             // 2. canonical sites, Tm, pair counts (synchronisation 2: the amplicon count)
             sort_decode(c, gs, n_pairs, keys, ns, sites, st);
             {
-                Stage sg(c, "tm", st, 1);
-                launch_tm(sites, ns, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, pass, c->d_err, st);
+                Stage sg(c, "tm", st, 2);
+                uint32_t *q = (uint32_t *)scratch(c, "tm_queue", ns * sizeof(uint32_t));
+                launch_tm(sites, ns, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, pass, q,
+                          (uint32_t *)(c->d_flags + 3), c->d_err, st);
             }
             const uint8_t *filt = o->tm_filter ? pass : nullptr;
             uint64_t *counts = (uint64_t *)scratch(c, "pair_counts", ns * sizeof(uint64_t));
@@ -1059,8 +1061,10 @@ ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n
         float *tm = out_buf(c, "tm_out", tm_out, n);
         uint8_t *ps = pass_out ? out_buf(c, "pass_out", pass_out, n) : nullptr;
         {
-            Stage sg(c, "tm", st, 1);
-            launch_tm(s, n, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, ps, c->d_err, st);
+            Stage sg(c, "tm", st, 2);
+            uint32_t *q = (uint32_t *)scratch(c, "tm_queue", n * sizeof(uint32_t));
+            launch_tm(s, n, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, ps, q, (uint32_t *)(c->d_flags + 3),
+                      c->d_err, st);
         }
         out_finish(tm_out, tm, n, st);
         if (pass_out)

@@ -168,8 +168,11 @@ struct PairDev {
 };
 
 // tm.cu
+// queue: n entries of scratch for the sites decided by exhaustive fp64
+// enumeration; queue_n: one device word (zeroed here).  Two kernels.
 void launch_tm(const ah_site *sites, uint64_t n, const PairDev *pairs_d, int n_pairs, const uint32_t *planes,
-               const uint64_t *contig_off, float *tm_out, uint8_t *pass_out, int *err, cudaStream_t s);
+               const uint64_t *contig_off, float *tm_out, uint8_t *pass_out, uint32_t *queue, uint32_t *queue_n,
+               int *err, cudaStream_t s);
 
 // pair.cu
 void launch_pair_count(const ah_site *sites, uint64_t n, const uint8_t *pass, const PairDev *pairs_d,

@@ -110,17 +110,19 @@ void launch_decode_keys(const uint64_t *keys, uint64_t n, int pbits, const uint6
 namespace ah {
 namespace {
 
-constexpr int kSortThreads = 1024, kSortItems = 16;
-static_assert(kSortThreads * kSortItems == (int)kSmallSort, "one block holds the small sort");
+constexpr int kSortItems = 16;
 
-__global__ void __launch_bounds__(kSortThreads) sort_decode_small_kernel(const uint64_t *__restrict__ keys,
-                                                                         uint32_t n, int end_bit, int pbits,
-                                                                         const uint64_t *__restrict__ contig_off,
-                                                                         uint32_t n_contigs,
-                                                                         const uint32_t *__restrict__ contig_genome,
-                                                                         ah_site *__restrict__ out)
+// One block of THREADS threads sorts up to THREADS * 16 keys (RADIX bits per
+// pass over the key bits in use) and decodes them.
+template <int THREADS, int RADIX>
+__global__ void __launch_bounds__(THREADS) sort_decode_small_kernel(const uint64_t *__restrict__ keys, uint32_t n,
+                                                                    int end_bit, int pbits,
+                                                                    const uint64_t *__restrict__ contig_off,
+                                                                    uint32_t n_contigs,
+                                                                    const uint32_t *__restrict__ contig_genome,
+                                                                    ah_site *__restrict__ out)
 {
-    using Sort = cub::BlockRadixSort<uint64_t, kSortThreads, kSortItems>;
+    using Sort = cub::BlockRadixSort<uint64_t, THREADS, kSortItems, cub::NullType, RADIX>;
     extern __shared__ __align__(16) unsigned char sort_smem[]; // Sort::TempStorage (> 48 KB: dynamic)
     typename Sort::TempStorage &tmp = *reinterpret_cast<typename Sort::TempStorage *>(sort_smem);
     uint64_t k[kSortItems];
@@ -158,6 +160,25 @@ __global__ void __launch_bounds__(kSortThreads) sort_decode_small_kernel(const u
     }
 }
 
+template <int THREADS, int RADIX>
+void run_small_sort(const uint64_t *keys, uint64_t n, int end_bit, int pbits, const uint64_t *contig_off,
+                    uint32_t n_contigs, const uint32_t *contig_genome, ah_site *out, cudaStream_t s)
+{
+    using Sort = cub::BlockRadixSort<uint64_t, THREADS, kSortItems, cub::NullType, RADIX>;
+    const size_t smem = sizeof(typename Sort::TempStorage);
+    static int attr_dev = -1; // one instance per template: opt in to its shared memory once per device
+    int dev = 0;
+    AH_CUDA(cudaGetDevice(&dev));
+    if (dev != attr_dev) {
+        AH_CUDA(cudaFuncSetAttribute(sort_decode_small_kernel<THREADS, RADIX>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_dev = dev;
+    }
+    sort_decode_small_kernel<THREADS, RADIX><<<1, THREADS, smem, s>>>(keys, (uint32_t)n, end_bit, pbits, contig_off,
+                                                                      n_contigs, contig_genome, out);
+    AH_CUDA(cudaGetLastError());
+}
+
 } // namespace
 
 bool launch_sort_decode_small(const uint64_t *keys, uint64_t n, int end_bit, int pbits, const uint64_t *contig_off,
@@ -165,18 +186,15 @@ bool launch_sort_decode_small(const uint64_t *keys, uint64_t n, int end_bit, int
 {
     if (n == 0 || n > kSmallSort)
         return false;
-    using Sort = cub::BlockRadixSort<uint64_t, kSortThreads, kSortItems>;
-    const size_t smem = sizeof(typename Sort::TempStorage);
-    static int attr_dev = -1;
-    int dev = 0;
-    AH_CUDA(cudaGetDevice(&dev));
-    if (dev != attr_dev) {
-        AH_CUDA(cudaFuncSetAttribute(sort_decode_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_dev = dev;
-    }
-    sort_decode_small_kernel<<<1, kSortThreads, smem, s>>>(keys, (uint32_t)n, end_bit, pbits, contig_off, n_contigs,
-                                                           contig_genome, out);
-    AH_CUDA(cudaGetLastError());
+    static_assert(1024 * kSortItems == (int)kSmallSort, "the largest instance holds the small sort");
+    if (n <= 2048)
+        run_small_sort<128, 8>(keys, n, end_bit, pbits, contig_off, n_contigs, contig_genome, out, s);
+    else if (n <= 4096)
+        run_small_sort<256, 8>(keys, n, end_bit, pbits, contig_off, n_contigs, contig_genome, out, s);
+    else if (n <= 8192)
+        run_small_sort<512, 6>(keys, n, end_bit, pbits, contig_off, n_contigs, contig_genome, out, s);
+    else
+        run_small_sort<1024, 6>(keys, n, end_bit, pbits, contig_off, n_contigs, contig_genome, out, s);
     return true;
 }
 

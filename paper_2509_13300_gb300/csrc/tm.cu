@@ -16,9 +16,9 @@
 // Sites whose fp32 maximum lies within 0.01 deg C of tm_min (fp32 error here
 // is ~1e-4 deg C), and sites under a table where some duplex entropy reaches
 // -C, are evaluated the reference way instead: every oligo, in fp64, with the
-// same operation order as the definition and no fused multiply-adds, the
-// warp's 32 lanes sharing the oligos.  Their pass flag is therefore the exact
-// fp64 decision.
+// same operation order as the definition and no fused multiply-adds, a whole
+// block sharing one site's oligos (tm_exact_kernel).  Their pass flag is
+// therefore the exact fp64 decision.
 #include <cmath>
 
 #include "ah_internal.h"
@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                                                            const uint32_t *__restrict__ planes,
                                                            const uint64_t *__restrict__ contig_off,
                                                            float *__restrict__ tm_out, uint8_t *__restrict__ pass_out,
+                                                           uint32_t *__restrict__ queue, uint32_t *__restrict__ queue_n,
                                                            int *__restrict__ err)
 {
     __shared__ int8_t bts[kTmWarps][8][AH_MAX_PRIMER_LEN];
@@ -216,75 +217,17 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                 break;
         }
         const float tm32 = lam - 273.15f + (act ? (float)pd.tm_shift : 0.f);
-        // sites decided the reference way (see the file comment), one at a time with all 32 lanes
+        // sites decided the reference way (see the file comment) go to a queue that
+        // tm_exact_kernel works off with a whole block per site
         const bool exact = run && (!dink || (pass_out && fabsf(tm32 - pd.tm_min_f) < 0.01f));
-        unsigned todo = __ballot_sync(0xffffffffu, exact && y == 0);
-        double tm_exact = 0.0;
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int sp = __shfl_sync(0xffffffffu, act ? (int)s.pair : 0, src);
-            const int spr = __shfl_sync(0xffffffffu, act ? (int)s.primer : 0, src);
-            const int sL = __shfl_sync(0xffffffffu, L, src);
-            const PairDev &qd = pairs[sp];
-            const uint8_t *qm = qd.mask[spr];
-            const int8_t *qb = bts[warp][src >> 2];
-            int deg = 1;
-            for (int q = 0; q < sL; ++q)
-                deg *= __popc(qm[q]);
-            double best = -INFINITY;
-            for (int o = lane; o < deg; o += 32) {
-                // oligo number o -> bases (mixed radix over the positions' sets)
-                uint64_t olig = 0;
-                int rem = o;
-                for (int q = sL - 1; q >= 0; --q) {
-                    const int nq = __popc(qm[q]);
-                    int d; // rem % nq, rem /= nq for nq in 1..4 (rem < 10000)
-                    if (nq == 1) {
-                        d = 0;
-                    } else if (nq == 2) {
-                        d = rem & 1;
-                        rem >>= 1;
-                    } else if (nq == 4) {
-                        d = rem & 3;
-                        rem >>= 2;
-                    } else {
-                        const int q3 = (rem * 43691) >> 17; // rem / 3, exact for rem < 2^16
-                        d = rem - 3 * q3;
-                        rem = q3;
-                    }
-                    int base_q = 0;
-                    for (int x = 0; x < 4; ++x)
-                        if (qm[q] >> x & 1) {
-                            if (d == 0) {
-                                base_q = x;
-                                break;
-                            }
-                            --d;
-                        }
-                    olig |= (uint64_t)base_q << (2 * q);
-                }
-                const double t = exact_tm(qd, qb, sL, olig);
-                best = t > best ? t : best;
-            }
-            for (int d = 16; d >= 1; d >>= 1) {
-                const double o2 = __shfl_xor_sync(0xffffffffu, best, d);
-                best = o2 > best ? o2 : best;
-            }
-            if (lane == src)
-                tm_exact = best;
-        }
+        if (exact && y == 0)
+            queue[atomicAdd(queue_n, 1u)] = (uint32_t)i;
         if (y == 0 && act) {
             float tm = NAN;
             uint8_t pass = 0;
             if (!bad) {
-                if (exact) {
-                    tm = (float)tm_exact;
-                    pass = tm_exact >= pd.tm_min;
-                } else {
-                    tm = tm32;
-                    pass = tm32 >= pd.tm_min_f;
-                }
+                tm = tm32; // replaced by tm_exact_kernel for queued sites
+                pass = tm32 >= pd.tm_min_f;
             }
             tm_out[i] = tm;
             if (pass_out)
@@ -298,19 +241,117 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
     }
 }
 
+// Queued sites, one block (128 lanes) per site: every oligo in fp64 with the
+// definition's operation order (exact_tm), block-wide maximum, then the Tm
+// and the pass flag.  The queue length is read on the device.
+constexpr int kExactThreads = 128;
+
+__global__ void __launch_bounds__(kExactThreads) tm_exact_kernel(const ah_site *__restrict__ sites,
+                                                                 const PairDev *__restrict__ pairs,
+                                                                 const uint32_t *__restrict__ planes,
+                                                                 const uint64_t *__restrict__ contig_off,
+                                                                 const uint32_t *__restrict__ queue,
+                                                                 const uint32_t *__restrict__ queue_n,
+                                                                 float *__restrict__ tm_out,
+                                                                 uint8_t *__restrict__ pass_out)
+{
+    __shared__ int8_t bt[AH_MAX_PRIMER_LEN];
+    __shared__ double wmax[kExactThreads / 32];
+    const uint32_t nq = *queue_n;
+    for (uint32_t e = blockIdx.x; e < nq; e += gridDim.x) {
+        const uint32_t i = queue[e];
+        const ah_site s = sites[i];
+        const PairDev &pd = pairs[s.pair];
+        const int L = pd.L[s.primer];
+        const uint8_t *qm = pd.mask[s.primer];
+        const uint64_t P = contig_off[s.contig] + s.pos;
+        for (int q = threadIdx.x; q < L; q += blockDim.x) {
+            const int c = base_at(planes, P + (s.strand == 0 ? q : L - 1 - q));
+            bt[q] = (int8_t)(s.strand == 0 ? 3 - c : c); // queued sites have only A/C/G/T
+        }
+        __syncthreads();
+        int deg = 1;
+        for (int q = 0; q < L; ++q)
+            deg *= __popc(qm[q]);
+        double best = -INFINITY;
+        for (int o = threadIdx.x; o < deg; o += blockDim.x) {
+            // oligo number o -> bases (mixed radix over the positions' sets)
+            uint64_t olig = 0;
+            int rem = o;
+            for (int q = L - 1; q >= 0; --q) {
+                const int nqb = __popc(qm[q]);
+                int d; // rem % nqb, rem /= nqb for nqb in 1..4 (rem < 10000)
+                if (nqb == 1) {
+                    d = 0;
+                } else if (nqb == 2) {
+                    d = rem & 1;
+                    rem >>= 1;
+                } else if (nqb == 4) {
+                    d = rem & 3;
+                    rem >>= 2;
+                } else {
+                    const int q3 = (rem * 43691) >> 17; // rem / 3, exact for rem < 2^16
+                    d = rem - 3 * q3;
+                    rem = q3;
+                }
+                int base_q = 0;
+                for (int x = 0; x < 4; ++x)
+                    if (qm[q] >> x & 1) {
+                        if (d == 0) {
+                            base_q = x;
+                            break;
+                        }
+                        --d;
+                    }
+                olig |= (uint64_t)base_q << (2 * q);
+            }
+            const double t = exact_tm(pd, bt, L, olig);
+            best = t > best ? t : best;
+        }
+        for (int d = 16; d >= 1; d >>= 1) {
+            const double o2 = __shfl_xor_sync(0xffffffffu, best, d);
+            best = o2 > best ? o2 : best;
+        }
+        if ((threadIdx.x & 31) == 0)
+            wmax[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = wmax[0];
+            for (int w = 1; w < kExactThreads / 32; ++w)
+                m = wmax[w] > m ? wmax[w] : m;
+            tm_out[i] = (float)m;
+            if (pass_out)
+                pass_out[i] = m >= pd.tm_min;
+        }
+        __syncthreads(); // bt and wmax are reused by the next queued site
+    }
+}
+
 } // namespace
 
 void launch_tm(const ah_site *sites, uint64_t n, const PairDev *pairs_d, int n_pairs, const uint32_t *planes,
-               const uint64_t *contig_off, float *tm_out, uint8_t *pass_out, int *err, cudaStream_t s)
+               const uint64_t *contig_off, float *tm_out, uint8_t *pass_out, uint32_t *queue, uint32_t *queue_n,
+               int *err, cudaStream_t s)
 {
     if (!n)
         return;
+    AH_CUDA(cudaMemsetAsync(queue_n, 0, sizeof(uint32_t), s));
     const uint64_t per_block = 8ull * kTmWarps; // sites per block per pass
     uint64_t blocks = (n + per_block - 1) / per_block;
     if (blocks > 65535)
         blocks = 65535;
     tm_kernel<<<(unsigned)blocks, 32 * kTmWarps, 0, s>>>(sites, n, pairs_d, n_pairs, planes, contig_off, tm_out,
-                                                         pass_out, err);
+                                                         pass_out, queue, queue_n, err);
+    AH_CUDA(cudaGetLastError());
+    static int cached_dev = -1, sms = 148;
+    int dev = 0;
+    AH_CUDA(cudaGetDevice(&dev));
+    if (dev != cached_dev) {
+        AH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        cached_dev = dev;
+    }
+    tm_exact_kernel<<<(unsigned)sms, kExactThreads, 0, s>>>(sites, pairs_d, planes, contig_off, queue, queue_n,
+                                                              tm_out, pass_out);
     AH_CUDA(cudaGetLastError());
 }
 
