@@ -30,6 +30,8 @@ struct ah_ctx {
     uint64_t *d_counter = nullptr;
     uint64_t *d_aux = nullptr;
     int *d_err = nullptr;
+    cudaStream_t copy_stream = nullptr; // host->device copies that overlap packing
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_packed[2] = {nullptr, nullptr};
     uint64_t *h_flags = nullptr;     // pinned host mirror of the flag block
     std::vector<PairDev> pairdev_h;  // host source of the last per-pair upload
     ScanTuning tuning;                          // default tuning
@@ -609,6 +611,11 @@ ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
         c->d_aux = c->d_flags + 1;
         c->d_err = (int *)(c->d_flags + 2);
         AH_CUDA(cudaMallocHost(&c->h_flags, 4 * sizeof(uint64_t)));
+        AH_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            AH_CUDA(cudaEventCreateWithFlags(&c->ev_copied[b], cudaEventDisableTiming));
+            AH_CUDA(cudaEventCreateWithFlags(&c->ev_packed[b], cudaEventDisableTiming));
+        }
     });
     if (st != AH_OK) {
         g_create_err = c->err;
@@ -636,6 +643,16 @@ void ah_destroy(ah_ctx *c)
         cudaEventDestroy(e);
     if (c->h_flags)
         cudaFreeHost(c->h_flags);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (c->ev_copied[b])
+            cudaEventDestroy(c->ev_copied[b]);
+        if (c->ev_packed[b])
+            cudaEventDestroy(c->ev_packed[b]);
+    }
     if (c->stream)
         cudaStreamDestroy(c->stream);
     delete c;
@@ -738,21 +755,32 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
                 Stage sg(c, "pack", st, 1);
                 launch_pack(seq, 0, n_bases, n_bases, gs->planes, 0, gs->n_tiles, c->d_err, st);
             } else {
-                // host sequence: stream it through a staging buffer in tile-aligned chunks;
-                // each chunk also carries the first bytes of the next tile (extension words)
-                const uint64_t chunk_tiles = 4096; // 128 Mbp
+                // host sequence: tile-aligned chunks through two staging buffers; the
+                // copies run on a second stream so chunk i+1 crosses the link while chunk
+                // i is packed.  Each chunk also carries the next tile (extension words).
+                const uint64_t chunk_tiles = 1024; // 32 Mbp
                 const uint64_t stage_bytes = chunk_tiles * kTileBases + kTileBases;
-                uint8_t *stage = (uint8_t *)scratch(c, "load_stage", stage_bytes);
-                for (uint64_t t0 = 0; t0 < gs->n_tiles; t0 += chunk_tiles) {
+                uint8_t *stage[2] = {(uint8_t *)scratch(c, "load_stage0", stage_bytes),
+                                     (uint8_t *)scratch(c, "load_stage1", stage_bytes)};
+                // the copy stream starts after everything queued so far on st
+                AH_CUDA(cudaEventRecord(c->ev_packed[0], st));
+                AH_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[0], 0));
+                uint64_t i = 0;
+                for (uint64_t t0 = 0; t0 < gs->n_tiles; t0 += chunk_tiles, ++i) {
+                    const int b = (int)(i & 1);
                     const uint64_t t1 = std::min(gs->n_tiles, t0 + chunk_tiles);
                     const uint64_t b0 = t0 * kTileBases;
                     const uint64_t b1 = std::min(n_bases, t1 * kTileBases + kTileBases);
-                    AH_CUDA(cudaMemcpyAsync(stage, seq + b0, b1 - b0, cudaMemcpyHostToDevice, st));
+                    if (i >= 2) // staging buffer b is free once the chunk packed from it two rounds ago is done
+                        AH_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[b], 0));
+                    AH_CUDA(cudaMemcpyAsync(stage[b], seq + b0, b1 - b0, cudaMemcpyHostToDevice, c->copy_stream));
+                    AH_CUDA(cudaEventRecord(c->ev_copied[b], c->copy_stream));
+                    AH_CUDA(cudaStreamWaitEvent(st, c->ev_copied[b], 0));
                     {
                         Stage sg(c, "pack", st, 1);
-                        launch_pack(stage, b0, b1 - b0, n_bases, gs->planes, t0, t1, c->d_err, st);
+                        launch_pack(stage[b], b0, b1 - b0, n_bases, gs->planes, t0, t1, c->d_err, st);
                     }
-                    AH_CUDA(cudaStreamSynchronize(st));
+                    AH_CUDA(cudaEventRecord(c->ev_packed[b], st));
                 }
             }
         }
