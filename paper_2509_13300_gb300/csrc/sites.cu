@@ -132,6 +132,10 @@ __global__ void __launch_bounds__(THREADS) sort_decode_small_kernel(const uint64
         k[q] = i < n ? keys[i] : ~0ull; // padding sorts last
     }
     Sort(tmp).Sort(k, 8, end_bit > 8 ? end_bit : 9);
+    // a thread's 16 keys are consecutive in sorted order: one binary search for
+    // the first, then walk forward (positions only grow within a pair)
+    uint32_t lo = 0;
+    uint64_t prev_pp = ~0ull;
 #pragma unroll
     for (int q = 0; q < kSortItems; ++q) {
         const uint32_t i = threadIdx.x * kSortItems + q;
@@ -140,14 +144,21 @@ __global__ void __launch_bounds__(THREADS) sort_decode_small_kernel(const uint64
         const uint64_t key = k[q];
         const uint64_t pp = key >> 10;
         const uint64_t P = pp & ((1ull << pbits) - 1);
-        uint32_t lo = 0, hi = n_contigs;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (contig_off[mid] <= P)
-                lo = mid;
-            else
-                hi = mid;
+        if (prev_pp == ~0ull || (pp >> pbits) != (prev_pp >> pbits)) {
+            lo = 0;
+            uint32_t hi = n_contigs;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (__ldg(contig_off + mid) <= P)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+        } else {
+            while (lo + 1 < n_contigs && __ldg(contig_off + lo + 1) <= P)
+                ++lo;
         }
+        prev_pp = pp;
         ah_site s;
         s.genome = contig_genome[lo];
         s.contig = lo;

@@ -241,10 +241,10 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
     }
 }
 
-// Queued sites, one block (128 lanes) per site: every oligo in fp64 with the
+// Queued sites, one block (1024 lanes) per site: every oligo in fp64 with the
 // definition's operation order (exact_tm), block-wide maximum, then the Tm
 // and the pass flag.  The queue length is read on the device.
-constexpr int kExactThreads = 128;
+constexpr int kExactThreads = 1024; // a site's oligos (at most 10000) in about one pass
 
 __global__ void __launch_bounds__(kExactThreads) tm_exact_kernel(const ah_site *__restrict__ sites,
                                                                  const PairDev *__restrict__ pairs,
