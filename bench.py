@@ -49,7 +49,7 @@ def workload(seed: int, n_genomes: int = 100):
 
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (every 50 ms), kept only when taken inside the timed region."""
 
     def __init__(self, index: int):
         self.index = index
@@ -62,7 +62,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -72,7 +72,19 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def wait_first(self, timeout: float = 10.0):
+        """Block until nvidia-smi has printed its first sample (it starts slowly)."""
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+
+    def mark(self, start: bool):
+        if start:
+            self.t_start = time.perf_counter()
+        else:
+            self.t_end = time.perf_counter()
 
     def __exit__(self, *a):
         if self.proc:
@@ -85,7 +97,9 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0, t1 = getattr(self, "t_start", float("-inf")), getattr(self, "t_end", float("inf"))
+        inside = [ln for t, ln in self.lines if t0 <= t <= t1 + 0.06]
+        for ln in inside:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 8:
                 continue
@@ -215,7 +229,7 @@ def traffic_record(kernel: str):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -277,11 +291,14 @@ def main():
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with ClockSampler(local) as clk:
+        clk.wait_first()
+        clk.mark(True)
         ev[0].record(stream)
         for i in range(args.steps):
             n, m = step_device()
             ev[i + 1].record(stream)
         torch.cuda.synchronize()
+        clk.mark(False)
     barrier(world)
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     t_ms = ev[0].elapsed_time(ev[-1])

@@ -25,7 +25,7 @@ struct ah_ctx {
     std::map<uint32_t, PrimerPair> pairs;
     uint32_t next_pair = 1;
     std::map<std::string, Scratch> scratch;
-    // device flag block: [0] hit counter, [1] auxiliary total, [2] error word, [3] Tm queue length
+    // device flag block (FlagWord layout)
     uint64_t *d_flags = nullptr;
     uint64_t *d_counter = nullptr;
     uint64_t *d_aux = nullptr;
@@ -34,9 +34,17 @@ struct ah_ctx {
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_packed[2] = {nullptr, nullptr};
     uint64_t *h_flags = nullptr;     // pinned host mirror of the flag block
     std::vector<PairDev> pairdev_h;  // host source of the last per-pair upload
+    std::vector<uint32_t> pairdev_ids; // pair ids of that upload
+    uint64_t pairdev_version = 0;      // pairs_version at that upload
+    const PairDev *pairdev_d = nullptr;
+    uint64_t pairs_version = 1;        // bumped whenever a registered pair changes
     ScanTuning tuning;                          // default tuning
     std::map<std::string, ScanTuning> tuned;    // autotuned, per pattern-set signature
     uint64_t key_cap = 1 << 20;
+    // one-synchronisation run: sizes of its scratch outputs, grown from the
+    // counts of runs that needed more; the last run's site count
+    uint64_t fast_amps = 16384, fast_seq = 4u << 20;
+    uint64_t last_sites = 0;
     // caching allocator: large blocks released by the library are kept for reuse
     std::map<void *, size_t> live;             // block -> bytes
     std::multimap<size_t, void *> cached;      // bytes -> block
@@ -273,18 +281,26 @@ template <class T> void out_finish(T *user, T *dev, uint64_t count, cudaStream_t
         AH_CUDA(cudaMemcpyAsync(user, dev, count * sizeof(T), cudaMemcpyDeviceToHost, st));
 }
 
+// Zero every flag word but the error word.
 void reset_flags(ah_ctx *c, cudaStream_t st)
 {
-    AH_CUDA(cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(uint64_t), st));
+    AH_CUDA(cudaMemsetAsync(c->d_flags, 0, kFlagErr * sizeof(uint64_t), st));
 }
 
-// One device->host copy of the flag block and one synchronisation; raises on
-// a device-reported error.  h_flags[0] = counter, h_flags[1] = aux total.
-void check_flags(ah_ctx *c, cudaStream_t st)
+// One device->host copy of the flag block and one synchronisation; returns
+// the device error word and clears it on the device when it is set.
+int read_flags(ah_ctx *c, cudaStream_t st)
 {
-    AH_CUDA(cudaMemcpyAsync(c->h_flags, c->d_flags, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    AH_CUDA(cudaMemcpyAsync(c->h_flags, c->d_flags, kFlagWords * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     AH_CUDA(cudaStreamSynchronize(st));
-    const int e = (int)(c->h_flags[2] & 0xffffffffu);
+    const int e = (int)(c->h_flags[kFlagErr] & 0xffffffffu);
+    if (e != 0)
+        AH_CUDA(cudaMemsetAsync(c->d_flags + kFlagErr, 0, sizeof(uint64_t), st));
+    return e;
+}
+
+void raise_device_error(int e)
+{
     if (e == kDevTimeout)
         throw Error(AH_ERR_TIMEOUT, "a device-side wait ran out of iterations");
     if (e == kDevBounds)
@@ -292,6 +308,10 @@ void check_flags(ah_ctx *c, cudaStream_t st)
     if (e != 0)
         throw Error(AH_ERR_DEVICE_CHECK, "device consistency check failed (code " + std::to_string(e) + ")");
 }
+
+// read_flags, then raise on a device-reported error.  h_flags[kFlagCounter]
+// = scan hits, h_flags[kFlagAux] = a device total.
+void check_flags(ah_ctx *c, cudaStream_t st) { raise_device_error(read_flags(c, st)); }
 
 GenomeSet &get_set(ah_ctx *c, uint32_t id)
 {
@@ -416,12 +436,21 @@ const PairDev *upload_pairs(ah_ctx *c, const uint32_t *pair_ids, uint32_t n_pair
 {
     require(pair_ids != nullptr, AH_ERR_ARG, "pair_ids is null");
     require(n_pairs >= 1 && n_pairs <= AH_MAX_PAIRS_PER_SCAN, AH_ERR_ARG, "n_pairs must be 1..16");
+    // the same pairs, unchanged since the last upload: the device copy is current
+    if (c->pairdev_d && c->pairdev_version == c->pairs_version && c->pairdev_ids.size() == n_pairs &&
+        std::equal(pair_ids, pair_ids + n_pairs, c->pairdev_ids.begin()))
+        return c->pairdev_d;
     c->pairdev_h.resize(n_pairs);
     for (uint32_t j = 0; j < n_pairs; ++j)
         c->pairdev_h[j] = make_pair_dev(get_pair(c, pair_ids[j]));
+    c->pairdev_d = nullptr;
     PairDev *d = (PairDev *)scratch(c, "pairdev", n_pairs * sizeof(PairDev));
-    // the source stays alive in the context: every call synchronises before it returns
+    // the source stays alive in the context until the next upload, which
+    // follows a synchronisation (every call that uploads synchronises before it returns)
     AH_CUDA(cudaMemcpyAsync(d, c->pairdev_h.data(), n_pairs * sizeof(PairDev), cudaMemcpyHostToDevice, st));
+    c->pairdev_ids.assign(pair_ids, pair_ids + n_pairs);
+    c->pairdev_version = c->pairs_version;
+    c->pairdev_d = d;
     return d;
 }
 
@@ -528,9 +557,10 @@ void sort_decode(ah_ctx *c, const GenomeSet &gs, uint32_t n_pairs, const uint64_
 {
     const int pbits = std::max(1, bit_length(gs.n_bases));
     const int end_bit = 10 + pbits + bit_length(n_pairs - 1);
-    if (count <= kSmallSort) { // one block: sort in registers and decode
+    if (count <= kSmallSort) { // one launch: rank sort and decode
         Stage sg(c, "sort", st, 1);
-        launch_sort_decode_small(keys, count, end_bit, pbits, gs.contig_off, gs.n_contigs, gs.contig_genome, dst, st);
+        launch_rank_sort_decode(keys, count, nullptr, end_bit - 8 <= 32, pbits, gs.contig_off, gs.n_contigs,
+                                gs.contig_genome, dst, nullptr, nullptr, st);
         return;
     }
     size_t tb = sort_keys_temp_bytes(count, end_bit);
@@ -563,6 +593,199 @@ template <class T> bool deliver(T *user, uint64_t cap, const T *dev, uint64_t co
     if (user && count && user != dev)
         AH_CUDA(cudaMemcpyAsync(user, dev, count * sizeof(T), cudaMemcpyDefault, st));
     return true;
+}
+
+
+// ---------------------------------------------------------------------------
+// ah_run in two forms.
+//
+// One synchronisation (run_fast): every count stays on the device and every
+// launch is sized for the largest count it accepts -- sites: kSmallSort, the
+// key buffer and the caller's capacity; amplicons and sequence bytes: the
+// caller's device buffers, else scratch sized from earlier runs.  A count above
+// its launch size sets a kRedo* bit and the later kernels see zero records; the
+// host then finishes with the step-by-step form (run_steps), which reuses the
+// scan's keys when they all fit.  Step by step (run_steps): one
+// synchronisation per data-dependent size, any size.
+// ---------------------------------------------------------------------------
+enum FastResult { kFastDone, kFastKeys, kFastRescan };
+
+FastResult run_fast(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPattern> &pats, const PairDev *pd,
+                    uint32_t n_pairs, ah_run_out *o, cudaStream_t st, uint64_t **keys_out, uint64_t *ns_out)
+{
+    uint64_t *F = c->d_flags;
+    const int pbits = std::max(1, bit_length(gs.n_bases));
+    const int end_bit = 10 + pbits + bit_length(n_pairs - 1);
+    // where each output is written: the caller's device buffer, else scratch
+    const bool sites_direct = o->sites_cap && is_device_ptr(c, o->sites) && (!o->tm || is_device_ptr(c, o->tm)) &&
+                              (!o->pass || is_device_ptr(c, o->pass));
+    uint64_t ns_max = std::min<uint64_t>(kSmallSort, c->key_cap);
+    if (sites_direct)
+        ns_max = std::min<uint64_t>(ns_max, o->sites_cap);
+    const bool amps_direct = o->amplicons_cap && is_device_ptr(c, o->amplicons) &&
+                             (!o->seq_offsets || is_device_ptr(c, o->seq_offsets));
+    const uint64_t na_max = std::min<uint64_t>(amps_direct ? o->amplicons_cap : c->fast_amps, kSmallScan - 1);
+    const bool seq_direct = o->seq_cap && is_device_ptr(c, o->seq);
+    const uint64_t nq_max = seq_direct ? o->seq_cap : c->fast_seq;
+
+    uint64_t *keys = (uint64_t *)scratch(c, "scan_keys", c->key_cap * sizeof(uint64_t));
+    ah_site *sites = sites_direct ? o->sites : (ah_site *)scratch(c, "run_sites", ns_max * sizeof(ah_site));
+    float *tm = sites_direct && o->tm ? o->tm : (float *)scratch(c, "run_tm", ns_max * sizeof(float));
+    uint8_t *pass = sites_direct && o->pass ? o->pass : (uint8_t *)scratch(c, "run_pass", ns_max);
+    uint32_t *queue = (uint32_t *)scratch(c, "tm_queue", ns_max * sizeof(uint32_t));
+    uint64_t *counts = (uint64_t *)scratch(c, "pair_counts", ns_max * sizeof(uint64_t));
+    uint64_t *offs = (uint64_t *)scratch(c, "pair_offsets", ns_max * sizeof(uint64_t));
+    ah_amplicon *amps = amps_direct ? o->amplicons : (ah_amplicon *)scratch(c, "run_amps", na_max * sizeof(ah_amplicon));
+    uint64_t *qoff = amps_direct && o->seq_offsets ? o->seq_offsets
+                                                   : (uint64_t *)scratch(c, "run_qoff", (na_max + 1) * sizeof(uint64_t));
+    uint64_t *len = (uint64_t *)scratch(c, "fetch_len", (na_max + 1) * sizeof(uint64_t));
+    char *seq = seq_direct ? o->seq : (char *)scratch(c, "run_seq", nq_max);
+    const uint8_t *filt = o->tm_filter ? pass : nullptr;
+
+    ScanKernel *k = scan_kernel(pats, tuning_for(c, pats), c->device);
+    reset_flags(c, st);
+    {
+        Stage sg(c, "scan", st, 1);
+        launch_scan(c, k, gs, gs.n_tiles, keys, c->key_cap, pbits, st);
+    }
+    {
+        Stage sg(c, "sort", st, 1);
+        launch_rank_sort_decode(keys, ns_max, F + kFlagCounter, end_bit - 8 <= 32, pbits, gs.contig_off,
+                                gs.n_contigs, gs.contig_genome, sites, F + kFlagSites, F + kFlagRedo, st);
+    }
+    {
+        Stage sg(c, "tm", st, 2);
+        launch_tm(sites, ns_max, F + kFlagSites, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, pass, queue,
+                  (uint32_t *)(F + kFlagTmQueue), c->d_err, st);
+    }
+    {
+        Stage sg(c, "pair", st, 4);
+        launch_pair_count(sites, ns_max, F + kFlagSites, filt, pd, counts, st);
+        exclusive_scan_u64_dev(counts, offs, ns_max, F + kFlagSites, 0, st);
+        launch_total(offs, counts, ns_max, F + kFlagSites, 0, F + kFlagAux, na_max, F + kFlagAmps, F + kFlagRedo,
+                     kRedoAmps, st);
+        launch_pair_write(sites, ns_max, F + kFlagSites, filt, pd, offs, amps, na_max, F + kFlagRedo, kRedoAmps, st);
+    }
+    {
+        Stage sg(c, "fetch", st, 4);
+        launch_fetch_lengths(amps, na_max, F + kFlagAmps, gs.contig_off, gs.n_contigs, len, c->d_err, st);
+        exclusive_scan_u64_dev(len, qoff, na_max + 1, F + kFlagAmps, 1, st);
+        launch_total(qoff, len, na_max + 1, F + kFlagAmps, 1, F + kFlagAux, nq_max, F + kFlagSeq, F + kFlagRedo,
+                     kRedoSeq, st);
+        launch_fetch(amps, na_max, F + kFlagAmps, qoff, gs.planes, gs.contig_off, seq, F + kFlagRedo, kRedoSeq, st);
+    }
+    check_flags(c, st); // the one synchronisation
+    const uint64_t *H = c->h_flags;
+    const uint64_t ns = H[kFlagCounter];
+    *keys_out = keys;
+    *ns_out = ns;
+    c->last_sites = ns;
+    if (H[kFlagRedo])
+        return ns <= c->key_cap ? kFastKeys : kFastRescan;
+    const uint64_t na = H[kFlagAmps], nq = H[kFlagSeq];
+    o->n_sites = ns;
+    o->n_amplicons = na;
+    o->n_seq = nq;
+    bool overflow = !deliver(o->sites, o->sites_cap, sites, ns, st);
+    if (o->tm)
+        overflow |= !deliver(o->tm, o->sites_cap, tm, ns, st);
+    if (o->pass)
+        overflow |= !deliver(o->pass, o->sites_cap, pass, ns, st);
+    overflow |= !deliver(o->amplicons, o->amplicons_cap, amps, na, st);
+    if (o->seq_offsets)
+        overflow |= !deliver(o->seq_offsets, o->amplicons_cap + 1, qoff, na + 1, st);
+    overflow |= !deliver(o->seq, o->seq_cap, seq, nq, st);
+    if (!(sites_direct && amps_direct && seq_direct)) // copies to host memory land before the call returns
+        AH_CUDA(cudaStreamSynchronize(st));
+    if (overflow)
+        throw Error(AH_ERR_OVERFLOW, "ah_run: an output buffer is too small (counts are in the out struct)");
+    return kFastDone;
+}
+
+void run_steps(ah_ctx *c, const GenomeSet &gs, const PairDev *pd, uint32_t n_pairs, uint64_t *keys, uint64_t ns,
+               ah_run_out *o, cudaStream_t st)
+{
+    bool overflow = false;
+    o->n_sites = ns;
+    c->last_sites = ns;
+    ah_site *sites = direct_or_scratch(c, "run_sites", o->sites, o->sites_cap, ns);
+    float *tm = direct_or_scratch(c, "run_tm", o->tm, o->tm ? o->sites_cap : 0, ns);
+    uint8_t *pass = direct_or_scratch(c, "run_pass", o->pass, o->pass ? o->sites_cap : 0, ns);
+    uint64_t na = 0, nq = 0;
+    ah_amplicon *amps = nullptr;
+    uint64_t *qoff = nullptr;
+    char *seq = nullptr;
+    if (ns) {
+        // canonical sites, Tm, pair counts (synchronisation: the amplicon count)
+        sort_decode(c, gs, n_pairs, keys, ns, sites, st);
+        {
+            Stage sg(c, "tm", st, 2);
+            uint32_t *q = (uint32_t *)scratch(c, "tm_queue", ns * sizeof(uint32_t));
+            launch_tm(sites, ns, nullptr, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, pass, q,
+                      (uint32_t *)(c->d_flags + kFlagTmQueue), c->d_err, st);
+        }
+        const uint8_t *filt = o->tm_filter ? pass : nullptr;
+        uint64_t *counts = (uint64_t *)scratch(c, "pair_counts", ns * sizeof(uint64_t));
+        uint64_t *offs = (uint64_t *)scratch(c, "pair_offsets", ns * sizeof(uint64_t));
+        size_t tb = scan_u64_temp_bytes(ns);
+        void *temp = scratch(c, "scan_temp", tb);
+        {
+            Stage sg(c, "pair", st, 2 + scan_u64_launches(ns));
+            launch_pair_count(sites, ns, nullptr, filt, pd, counts, st);
+            exclusive_scan_u64(temp, tb, counts, offs, ns, st);
+            launch_total(offs, counts, ns, nullptr, 0, c->d_aux, 0, nullptr, nullptr, 0, st);
+        }
+        check_flags(c, st);
+        na = c->h_flags[kFlagAux];
+        o->n_amplicons = na;
+        // amplicons and sequence offsets (synchronisation: the sequence bytes)
+        amps = direct_or_scratch(c, "run_amps", o->amplicons, o->amplicons_cap, na);
+        qoff = direct_or_scratch(c, "run_qoff", o->seq_offsets, o->seq_offsets ? o->amplicons_cap + 1 : 0, na + 1);
+        if (na) {
+            Stage sg(c, "pair", st, 1);
+            launch_pair_write(sites, ns, nullptr, filt, pd, offs, amps, na, nullptr, 0, st);
+        }
+        uint64_t *len = (uint64_t *)scratch(c, "fetch_len", (na + 1) * sizeof(uint64_t));
+        size_t tb2 = scan_u64_temp_bytes(na + 1);
+        void *temp2 = scratch(c, "scan_temp", tb2);
+        {
+            Stage sg(c, "fetch", st, (na ? 1 : 0) + scan_u64_launches(na + 1));
+            AH_CUDA(cudaMemsetAsync(len + na, 0, sizeof(uint64_t), st));
+            launch_fetch_lengths(amps, na, nullptr, gs.contig_off, gs.n_contigs, len, c->d_err, st);
+            exclusive_scan_u64(temp2, tb2, len, qoff, na + 1, st);
+            AH_CUDA(cudaMemcpyAsync(c->d_aux, qoff + na, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+        }
+        check_flags(c, st);
+        nq = c->h_flags[kFlagAux];
+        o->n_seq = nq;
+        // sequences, then every output that was not written in place
+        seq = direct_or_scratch(c, "run_seq", o->seq, o->seq_cap, nq);
+        if (na && nq) {
+            Stage sg(c, "fetch", st, 1);
+            launch_fetch(amps, na, nullptr, qoff, gs.planes, gs.contig_off, seq, nullptr, 0, st);
+        }
+    }
+    // later one-synchronisation runs size their scratch for counts like these
+    c->fast_amps = std::min<uint64_t>(kSmallScan - 1, std::max<uint64_t>(c->fast_amps, na + na / 4 + 16));
+    c->fast_seq = std::min<uint64_t>(1ull << 30, std::max<uint64_t>(c->fast_seq, nq + nq / 4 + 4096));
+    overflow |= !deliver(o->sites, o->sites_cap, sites, ns, st);
+    if (o->tm)
+        overflow |= !deliver(o->tm, o->sites_cap, tm, ns, st);
+    if (o->pass)
+        overflow |= !deliver(o->pass, o->sites_cap, pass, ns, st);
+    overflow |= !deliver(o->amplicons, o->amplicons_cap, amps, na, st);
+    if (o->seq_offsets) {
+        if (ns)
+            overflow |= !deliver(o->seq_offsets, o->amplicons_cap + 1, qoff, na + 1, st);
+        else if (is_device_ptr(c, o->seq_offsets))
+            AH_CUDA(cudaMemsetAsync(o->seq_offsets, 0, sizeof(uint64_t), st));
+        else
+            o->seq_offsets[0] = 0;
+    }
+    overflow |= !deliver(o->seq, o->seq_cap, seq, nq, st);
+    check_flags(c, st);
+    if (overflow)
+        throw Error(AH_ERR_OVERFLOW, "ah_run: an output buffer is too small (counts are in the out struct)");
 }
 
 } // namespace
@@ -606,11 +829,13 @@ ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
             }
         }
         AH_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
-        c->d_flags = (uint64_t *)dev_alloc(c, 4 * sizeof(uint64_t));
-        c->d_counter = c->d_flags;
-        c->d_aux = c->d_flags + 1;
-        c->d_err = (int *)(c->d_flags + 2);
-        AH_CUDA(cudaMallocHost(&c->h_flags, 4 * sizeof(uint64_t)));
+        c->d_flags = (uint64_t *)dev_alloc(c, kFlagWords * sizeof(uint64_t));
+        c->d_counter = c->d_flags + kFlagCounter;
+        c->d_aux = c->d_flags + kFlagAux;
+        c->d_err = (int *)(c->d_flags + kFlagErr);
+        AH_CUDA(cudaMemsetAsync(c->d_flags, 0, kFlagWords * sizeof(uint64_t), c->stream));
+        AH_CUDA(cudaStreamSynchronize(c->stream));
+        AH_CUDA(cudaMallocHost(&c->h_flags, kFlagWords * sizeof(uint64_t)));
         AH_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
         for (int b = 0; b < 2; ++b) {
             AH_CUDA(cudaEventCreateWithFlags(&c->ev_copied[b], cudaEventDisableTiming));
@@ -749,9 +974,12 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
                                 cudaMemcpyHostToDevice, st));
         AH_CUDA(cudaMemcpyAsync(gs->contig_genome, gs->contig_genome_h.data(), n_contigs * sizeof(uint32_t),
                                 cudaMemcpyHostToDevice, st));
-        reset_flags(c, st);
+        const bool dev_seq = n_bases && is_device_ptr(c, seq);
         if (gs->n_tiles) {
-            if (is_device_ptr(c, seq)) {
+            if (dev_seq) {
+                // stream-ordered: the pack runs after the caller's earlier work on
+                // the stream; a device-side failure reaches the next call that
+                // synchronises (the error word is kept until the host reads it)
                 Stage sg(c, "pack", st, 1);
                 launch_pack(seq, 0, n_bases, n_bases, gs->planes, 0, gs->n_tiles, c->d_err, st);
             } else {
@@ -784,7 +1012,8 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
                 }
             }
         }
-        check_flags(c, st);
+        if (!dev_seq) // the caller's host buffer may be reused once this call returns
+            check_flags(c, st);
         uint32_t id = c->next_set++;
         c->sets[id] = std::move(gs);
         *set_id_out = id;
@@ -797,11 +1026,12 @@ ah_status ah_unload_genomes(ah_ctx *c, uint32_t set_id)
         return AH_ERR_ARG;
     return guarded(c, [&] {
         GenomeSet &gs = get_set(c, set_id);
-        AH_CUDA(cudaStreamSynchronize(c->stream));
+        const int e = read_flags(c, c->stream); // also reports a failure of a pack nothing else synchronised on
         dev_free(c, gs.planes, gs.n_tiles * kTileBytes);
         dev_free(c, gs.contig_off, (gs.n_contigs + 1) * sizeof(uint64_t));
         dev_free(c, gs.contig_genome, gs.n_contigs * sizeof(uint32_t));
         c->sets.erase(set_id);
+        raise_device_error(e);
     });
 }
 
@@ -843,6 +1073,7 @@ ah_status ah_set_primers(ah_ctx *c, const char *fwd, const char *rev, const ah_p
         default_table(&pp.table);
         uint32_t id = c->next_pair++;
         c->pairs[id] = pp;
+        ++c->pairs_version;
         *pair_id_out = id;
     });
 }
@@ -853,6 +1084,7 @@ ah_status ah_set_nn_table(ah_ctx *c, uint32_t pair_id, const ah_nn_table *t)
         return AH_ERR_ARG;
     return guarded(c, [&] {
         PrimerPair &pp = get_pair(c, pair_id);
+        ++c->pairs_version;
         if (!t) {
             default_table(&pp.table);
             return;
@@ -862,6 +1094,7 @@ ah_status ah_set_nn_table(ah_ctx *c, uint32_t pair_id, const ah_nn_table *t)
         for (int i = 0; i < 16; ++i)
             require(std::isfinite(t->term_dH[i]) && std::isfinite(t->term_dS[i]), AH_ERR_ARG, "non-finite entry");
         pp.table = *t;
+        ++c->pairs_version;
     });
 }
 
@@ -974,8 +1207,7 @@ ah_status ah_run(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t 
 {
     if (!c)
         return AH_ERR_ARG;
-    bool overflow = false;
-    ah_status st_ = guarded(c, [&] {
+    return guarded(c, [&] {
         require(o != nullptr, AH_ERR_ARG, "ah_run: out is null");
         require(pair_ids && n_pairs >= 1 && n_pairs <= AH_MAX_PAIRS_PER_SCAN, AH_ERR_ARG, "n_pairs must be 1..16");
         require((o->sites_cap == 0 || o->sites) && (o->amplicons_cap == 0 || o->amplicons) &&
@@ -986,85 +1218,17 @@ ah_status ah_run(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t 
         cudaStream_t st = stream_of(c, stream);
         std::vector<ScanPattern> pats = patterns_of(c, pair_ids, n_pairs);
         const PairDev *pd = upload_pairs(c, pair_ids, n_pairs, st);
-        // 1. primer matching (synchronisation 1: the site count)
         uint64_t *keys = nullptr;
-        const uint64_t ns = scan_keys(c, gs, pats, &keys, st);
-        o->n_sites = ns;
-        ah_site *sites = direct_or_scratch(c, "run_sites", o->sites, o->sites_cap, ns);
-        float *tm = direct_or_scratch(c, "run_tm", o->tm, o->tm ? o->sites_cap : 0, ns);
-        uint8_t *pass = direct_or_scratch(c, "run_pass", o->pass, o->pass ? o->sites_cap : 0, ns);
-        uint64_t na = 0, nq = 0;
-        ah_amplicon *amps = nullptr;
-        uint64_t *qoff = nullptr;
-        char *seq = nullptr;
-        if (ns) {
-            // 2. canonical sites, Tm, pair counts (synchronisation 2: the amplicon count)
-            sort_decode(c, gs, n_pairs, keys, ns, sites, st);
-            {
-                Stage sg(c, "tm", st, 2);
-                uint32_t *q = (uint32_t *)scratch(c, "tm_queue", ns * sizeof(uint32_t));
-                launch_tm(sites, ns, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, pass, q,
-                          (uint32_t *)(c->d_flags + 3), c->d_err, st);
-            }
-            const uint8_t *filt = o->tm_filter ? pass : nullptr;
-            uint64_t *counts = (uint64_t *)scratch(c, "pair_counts", ns * sizeof(uint64_t));
-            uint64_t *offs = (uint64_t *)scratch(c, "pair_offsets", ns * sizeof(uint64_t));
-            size_t tb = scan_u64_temp_bytes(ns);
-            void *temp = scratch(c, "scan_temp", tb);
-            {
-                Stage sg(c, "pair", st, 2 + scan_u64_launches(ns));
-                launch_pair_count(sites, ns, filt, pd, counts, st);
-                exclusive_scan_u64(temp, tb, counts, offs, ns, st);
-                launch_total(offs, counts, ns, c->d_aux, st);
-            }
-            check_flags(c, st);
-            na = c->h_flags[1];
-            o->n_amplicons = na;
-            // 3. amplicons and sequence offsets (synchronisation 3: the sequence bytes)
-            amps = direct_or_scratch(c, "run_amps", o->amplicons, o->amplicons_cap, na);
-            qoff = direct_or_scratch(c, "run_qoff", o->seq_offsets, o->seq_offsets ? o->amplicons_cap + 1 : 0, na + 1);
-            if (na) {
-                Stage sg(c, "pair", st, 1);
-                launch_pair_write(sites, ns, filt, pd, offs, amps, na, st);
-            }
-            uint64_t *len = (uint64_t *)scratch(c, "fetch_len", (na + 1) * sizeof(uint64_t));
-            size_t tb2 = scan_u64_temp_bytes(na + 1);
-            void *temp2 = scratch(c, "scan_temp", tb2);
-            {
-                Stage sg(c, "fetch", st, (na ? 1 : 0) + scan_u64_launches(na + 1));
-                AH_CUDA(cudaMemsetAsync(len + na, 0, sizeof(uint64_t), st));
-                launch_fetch_lengths(amps, na, gs.contig_off, gs.n_contigs, len, c->d_err, st);
-                exclusive_scan_u64(temp2, tb2, len, qoff, na + 1, st);
-                AH_CUDA(cudaMemcpyAsync(c->d_aux, qoff + na, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
-            }
-            check_flags(c, st);
-            nq = c->h_flags[1];
-            o->n_seq = nq;
-            // 4. sequences, then every output that was not written in place (synchronisation 4)
-            seq = direct_or_scratch(c, "run_seq", o->seq, o->seq_cap, nq);
-            if (na && nq) {
-                Stage sg(c, "fetch", st, 1);
-                launch_fetch(amps, na, qoff, gs.planes, gs.contig_off, seq, st);
-            }
-        }
-        overflow |= !deliver(o->sites, o->sites_cap, sites, ns, st);
-        if (o->tm)
-            overflow |= !deliver(o->tm, o->sites_cap, tm, ns, st);
-        if (o->pass)
-            overflow |= !deliver(o->pass, o->sites_cap, pass, ns, st);
-        overflow |= !deliver(o->amplicons, o->amplicons_cap, amps, na, st);
-        if (o->seq_offsets) {
-            if (ns)
-                overflow |= !deliver(o->seq_offsets, o->amplicons_cap + 1, qoff, na + 1, st);
-            else
-                AH_CUDA(cudaMemsetAsync(o->seq_offsets, 0, sizeof(uint64_t), st));
-        }
-        overflow |= !deliver(o->seq, o->seq_cap, seq, nq, st);
-        check_flags(c, st);
-        if (overflow)
-            throw Error(AH_ERR_OVERFLOW, "ah_run: an output buffer is too small (counts are in the out struct)");
+        uint64_t ns = 0;
+        FastResult r = kFastRescan;
+        if (gs.n_tiles && c->last_sites <= kSmallSort)
+            r = run_fast(c, gs, pats, pd, n_pairs, o, st, &keys, &ns);
+        if (r == kFastDone)
+            return;
+        if (r == kFastRescan)
+            ns = scan_keys(c, gs, pats, &keys, st);
+        run_steps(c, gs, pd, n_pairs, keys, ns, o, st);
     });
-    return st_;
 }
 
 ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, const ah_site *sites,
@@ -1091,7 +1255,8 @@ ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n
         {
             Stage sg(c, "tm", st, 2);
             uint32_t *q = (uint32_t *)scratch(c, "tm_queue", n * sizeof(uint32_t));
-            launch_tm(s, n, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, ps, q, (uint32_t *)(c->d_flags + 3),
+            launch_tm(s, n, nullptr, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, ps, q,
+                      (uint32_t *)(c->d_flags + kFlagTmQueue),
                       c->d_err, st);
         }
         out_finish(tm_out, tm, n, st);
@@ -1128,7 +1293,7 @@ ah_status ah_pair(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
         void *temp = scratch(c, "scan_temp", tb);
         {
             Stage sg(c, "pair", st, 1 + scan_u64_launches(n));
-            launch_pair_count(s, n, ps, pd, counts, st);
+            launch_pair_count(s, n, nullptr, ps, pd, counts, st);
             exclusive_scan_u64(temp, tb, counts, offs, n, st);
         }
         uint64_t last[2] = {0, 0};
@@ -1145,7 +1310,7 @@ ah_status ah_pair(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
         ah_amplicon *dst = out_buf(c, "amp_out", out, total);
         {
             Stage sg(c, "pair", st, 1);
-            launch_pair_write(s, n, ps, pd, offs, dst, total, st);
+            launch_pair_write(s, n, nullptr, ps, pd, offs, dst, total, nullptr, 0, st);
         }
         out_finish(out, dst, total, st);
         AH_CUDA(cudaStreamSynchronize(st));
@@ -1170,7 +1335,7 @@ ah_status ah_fetch(ah_ctx *c, uint32_t set_id, const ah_amplicon *amplicons, uin
         void *temp = scratch(c, "scan_temp", tb);
         {
             Stage sg(c, "fetch", st, (n ? 1 : 0) + scan_u64_launches(n + 1));
-            launch_fetch_lengths(a, n, gs.contig_off, gs.n_contigs, len, c->d_err, st);
+            launch_fetch_lengths(a, n, nullptr, gs.contig_off, gs.n_contigs, len, c->d_err, st);
             exclusive_scan_u64(temp, tb, len, offs, n + 1, st);
         }
         check_flags(c, st);
@@ -1186,7 +1351,7 @@ ah_status ah_fetch(ah_ctx *c, uint32_t set_id, const ah_amplicon *amplicons, uin
         char *dst = out_buf(c, "fetch_out", seq_out, total);
         {
             Stage sg(c, "fetch", st, 1);
-            launch_fetch(a, n, offs, gs.planes, gs.contig_off, dst, st);
+            launch_fetch(a, n, nullptr, offs, gs.planes, gs.contig_off, dst, nullptr, 0, st);
         }
         out_finish(seq_out, dst, total, st);
         AH_CUDA(cudaStreamSynchronize(st));

@@ -138,10 +138,39 @@ void sort_keys(void *temp, size_t temp_bytes, const uint64_t *in, uint64_t *out,
                int end_bit, cudaStream_t s);
 void launch_decode_keys(const uint64_t *keys, uint64_t n, int pbits, const uint64_t *contig_off, uint32_t n_contigs,
                         const uint32_t *contig_genome, ah_site *out, cudaStream_t s);
-// One-block sort + decode for up to kSmallSort keys; false (nothing launched) above that.
+// Rank sort + decode (canonical order) for up to kSmallSort keys in one
+// launch.  Host-count form: n_dev = nullptr, n = the count.  Device-count form
+// (one-synchronisation path): the count is *n_dev and n is the largest count
+// the launch was sized for; above it the kernel writes *n_out = 0, sets
+// kRedoSites in *redo and sorts nothing.  Otherwise *n_out = the count.
+// key32: the sort bits [8, end_bit) fit in 32 bits.
 constexpr uint64_t kSmallSort = 16384;
-bool launch_sort_decode_small(const uint64_t *keys, uint64_t n, int end_bit, int pbits, const uint64_t *contig_off,
-                              uint32_t n_contigs, const uint32_t *contig_genome, ah_site *out, cudaStream_t s);
+void launch_rank_sort_decode(const uint64_t *keys, uint64_t n, const uint64_t *n_dev, bool key32, int pbits,
+                             const uint64_t *contig_off, uint32_t n_contigs, const uint32_t *contig_genome,
+                             ah_site *out, uint64_t *n_out, uint64_t *redo, cudaStream_t s);
+
+// Device flag block of a context (u64 words, read by the host with one copy).
+// The error word is last so that one memset clears every other word; it is
+// cleared only after the host has read a non-zero value, so an error raised
+// by a call that returns without synchronising reaches the next call that does.
+enum FlagWord : int {
+    kFlagCounter = 0, // scan hits appended
+    kFlagAux = 1,     // a total computed on the device
+    kFlagTmQueue = 2, // sites queued for the exhaustive fp64 Tm
+    kFlagSites = 3,   // one-synchronisation path: sites sorted
+    kFlagAmps = 4,    // ... amplicons
+    kFlagSeq = 5,     // ... sequence bytes
+    kFlagRedo = 6,    // ... kRedo* bits: a count above what the launches were sized for
+    kFlagErr = 7,     // DeviceErr (low 32 bits)
+    kFlagWords = 8
+};
+constexpr uint64_t kRedoSites = 1, kRedoAmps = 2, kRedoSeq = 4;
+
+// Count of a kernel that may read it on the device: min(*n_dev, n), or n.
+__device__ __forceinline__ uint64_t dev_count(uint64_t n, const uint64_t *n_dev)
+{
+    return n_dev ? (*n_dev < n ? *n_dev : n) : n;
+}
 
 struct PairDev;
 // Check user-supplied sites before any kernel indexes memory with them:
@@ -170,29 +199,41 @@ struct PairDev {
 // tm.cu
 // queue: n entries of scratch for the sites decided by exhaustive fp64
 // enumeration; queue_n: one device word (zeroed here).  Two kernels.
-void launch_tm(const ah_site *sites, uint64_t n, const PairDev *pairs_d, int n_pairs, const uint32_t *planes,
+// n_dev: optional device count (min(*n_dev, n) sites).
+void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const PairDev *pairs_d, int n_pairs, const uint32_t *planes,
                const uint64_t *contig_off, float *tm_out, uint8_t *pass_out, uint32_t *queue, uint32_t *queue_n,
                int *err, cudaStream_t s);
 
 // pair.cu
-void launch_pair_count(const ah_site *sites, uint64_t n, const uint8_t *pass, const PairDev *pairs_d,
-                       uint64_t *counts, cudaStream_t s);
-// *out = offs[n-1] + counts[n-1] (the total of an exclusive scan), on the device
-void launch_total(const uint64_t *offs, const uint64_t *counts, uint64_t n, uint64_t *out, cudaStream_t s);
+// n_dev (here and below): optional device count, min(*n_dev, n) records.
+void launch_pair_count(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const uint8_t *pass,
+                       const PairDev *pairs_d, uint64_t *counts, cudaStream_t s);
+// *out = offs[m-1] + counts[m-1] (the total of an exclusive scan over m values,
+// m = n or min(*n_dev + add, n)).  With eff != nullptr also *eff = the total if it
+// is at most cap, else 0 with redo_bit set in *redo.
+void launch_total(const uint64_t *offs, const uint64_t *counts, uint64_t n, const uint64_t *n_dev, uint64_t add,
+                  uint64_t *out, uint64_t cap, uint64_t *eff, uint64_t *redo, uint64_t redo_bit, cudaStream_t s);
 size_t scan_u64_temp_bytes(uint64_t n);
 // Exclusive scan of n u64 values; one block (no temporary) for n <= kSmallScan, CUB above.
 constexpr uint64_t kSmallScan = 65536;
 // number of kernels exclusive_scan_u64 launches for n values
 int scan_u64_launches(uint64_t n);
 void exclusive_scan_u64(void *temp, size_t temp_bytes, const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s);
-void launch_pair_write(const ah_site *sites, uint64_t n, const uint8_t *pass, const PairDev *pairs_d,
-                       const uint64_t *offsets, ah_amplicon *out, uint64_t cap, cudaStream_t s);
+// One-block exclusive scan of min(*n_dev + add, n) values (n <= kSmallScan).
+void exclusive_scan_u64_dev(const uint64_t *in, uint64_t *out, uint64_t n, const uint64_t *n_dev, uint64_t add,
+                            cudaStream_t s);
+// skip: optional device word; the kernel writes nothing when (*skip & skip_bit) != 0.
+void launch_pair_write(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const uint8_t *pass,
+                       const PairDev *pairs_d, const uint64_t *offsets, ah_amplicon *out, uint64_t cap,
+                       const uint64_t *skip, uint64_t skip_bit, cudaStream_t s);
 
 // fetch.cu
 // lengths of the amplicons; a record outside its contig sets *err = kDevBounds (length 0)
-void launch_fetch_lengths(const ah_amplicon *a, uint64_t n, const uint64_t *contig_off, uint32_t n_contigs,
-                          uint64_t *len, int *err, cudaStream_t s);
-void launch_fetch(const ah_amplicon *a, uint64_t n, const uint64_t *offsets, const uint32_t *planes,
-                  const uint64_t *contig_off, char *out, cudaStream_t s);
+// With n_dev the kernel also writes len[count] = 0 (the scan's closing entry).
+void launch_fetch_lengths(const ah_amplicon *a, uint64_t n, const uint64_t *n_dev, const uint64_t *contig_off,
+                          uint32_t n_contigs, uint64_t *len, int *err, cudaStream_t s);
+void launch_fetch(const ah_amplicon *a, uint64_t n, const uint64_t *n_dev, const uint64_t *offsets,
+                  const uint32_t *planes, const uint64_t *contig_off, char *out, const uint64_t *skip,
+                  uint64_t skip_bit, cudaStream_t s);
 
 } // namespace ah

@@ -139,7 +139,7 @@ extern "C" ah_status ah_pair_noalloc(const int32_t *pair_windows, uint32_t n_pai
         AH_CUDA(cudaStreamSynchronize(st));
         if (bad)
             return AH_ERR_ARG;
-        ah::launch_pair_count(sites, n, pass, pd, counts, st);
+        ah::launch_pair_count(sites, n, nullptr, pass, pd, counts, st);
         ah::exclusive_scan_u64(cub_temp, cub_bytes, counts, offs, n, st);
         AH_CUDA(cudaMemcpyAsync(&last[0], offs + n - 1, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
         AH_CUDA(cudaMemcpyAsync(&last[1], counts + n - 1, sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
@@ -151,7 +151,7 @@ extern "C" ah_status ah_pair_noalloc(const int32_t *pair_windows, uint32_t n_pai
         if (total > cap)
             return AH_ERR_OVERFLOW;
         if (total) {
-            ah::launch_pair_write(sites, n, pass, pd, offs, out, total, st);
+            ah::launch_pair_write(sites, n, nullptr, pass, pd, offs, out, total, nullptr, 0, st);
             AH_CUDA(cudaStreamSynchronize(st));
         }
     } catch (const ah::Error &e) {

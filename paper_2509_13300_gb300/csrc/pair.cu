@@ -96,9 +96,11 @@ __device__ __forceinline__ bool in_window(const PairDev &pd, uint32_t s_pos, con
     return r.pos >= s_pos && len >= pd.min_len && len <= pd.max_len;
 }
 
-__global__ void pair_count_kernel(const ah_site *__restrict__ s, uint64_t n, const uint8_t *__restrict__ pass,
-                                  const PairDev *__restrict__ pairs, uint64_t *__restrict__ counts)
+__global__ void pair_count_kernel(const ah_site *__restrict__ s, uint64_t n_arg, const uint64_t *__restrict__ n_dev,
+                                  const uint8_t *__restrict__ pass, const PairDev *__restrict__ pairs,
+                                  uint64_t *__restrict__ counts)
 {
+    const uint64_t n = dev_count(n_arg, n_dev);
     for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t cnt = 0;
         const Group g = make_group(s, n, pass, pairs, a);
@@ -122,10 +124,14 @@ __global__ void pair_count_kernel(const ah_site *__restrict__ s, uint64_t n, con
 
 __device__ __forceinline__ int orient_of(int x, int y) { return (x == 0 && y == 1) ? 0 : (x == 1 && y == 0) ? 1 : (x == 0 ? 2 : 3); }
 
-__global__ void pair_write_kernel(const ah_site *__restrict__ s, uint64_t n, const uint8_t *__restrict__ pass,
-                                  const PairDev *__restrict__ pairs, const uint64_t *__restrict__ offsets,
-                                  ah_amplicon *__restrict__ out, uint64_t cap)
+__global__ void pair_write_kernel(const ah_site *__restrict__ s, uint64_t n_arg, const uint64_t *__restrict__ n_dev,
+                                  const uint8_t *__restrict__ pass, const PairDev *__restrict__ pairs,
+                                  const uint64_t *__restrict__ offsets, ah_amplicon *__restrict__ out, uint64_t cap,
+                                  const uint64_t *__restrict__ skip, uint64_t skip_bit)
 {
+    if (skip && (*skip & skip_bit))
+        return;
+    const uint64_t n = dev_count(n_arg, n_dev);
     for (uint64_t a = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (uint64_t)gridDim.x * blockDim.x) {
         const Group g = make_group(s, n, pass, pairs, a);
         if (!g.valid)
@@ -189,18 +195,28 @@ __global__ void pair_write_kernel(const ah_site *__restrict__ s, uint64_t n, con
     }
 }
 
-__global__ void total_kernel(const uint64_t *__restrict__ offs, const uint64_t *__restrict__ counts, uint64_t n,
-                             uint64_t *__restrict__ out)
+__global__ void total_kernel(const uint64_t *__restrict__ offs, const uint64_t *__restrict__ counts, uint64_t n_arg,
+                             const uint64_t *__restrict__ n_dev, uint64_t add, uint64_t *__restrict__ out,
+                             uint64_t cap, uint64_t *__restrict__ eff, uint64_t *__restrict__ redo, uint64_t redo_bit)
 {
-    *out = n ? offs[n - 1] + counts[n - 1] : 0;
+    const uint64_t n = n_dev ? min(*n_dev + add, n_arg) : n_arg;
+    const uint64_t t = n ? offs[n - 1] + counts[n - 1] : 0;
+    *out = t;
+    if (eff) {
+        *eff = t <= cap ? t : 0;
+        if (t > cap)
+            atomicOr((unsigned long long *)redo, (unsigned long long)redo_bit);
+    }
 }
 
 // One-block exclusive scan: each thread sums a contiguous chunk, the block
 // scans the chunk totals, each thread writes its chunk's prefixes.
 __global__ void __launch_bounds__(1024) scan_small_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
-                                                          uint32_t n)
+                                                          uint32_t n_arg, const uint64_t *__restrict__ n_dev,
+                                                          uint64_t add)
 {
     __shared__ uint64_t part[1024];
+    const uint32_t n = n_dev ? (uint32_t)min(*n_dev + add, (uint64_t)n_arg) : n_arg;
     const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
     const uint32_t lo = min(n, threadIdx.x * per), hi = min(n, lo + per);
     uint64_t sum = 0;
@@ -234,18 +250,19 @@ unsigned grid_for(uint64_t n, int threads)
 
 } // namespace
 
-void launch_pair_count(const ah_site *sites, uint64_t n, const uint8_t *pass, const PairDev *pairs_d,
-                       uint64_t *counts, cudaStream_t s)
+void launch_pair_count(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const uint8_t *pass,
+                       const PairDev *pairs_d, uint64_t *counts, cudaStream_t s)
 {
     if (!n)
         return;
-    pair_count_kernel<<<grid_for(n, 128), 128, 0, s>>>(sites, n, pass, pairs_d, counts);
+    pair_count_kernel<<<grid_for(n, 128), 128, 0, s>>>(sites, n, n_dev, pass, pairs_d, counts);
     AH_CUDA(cudaGetLastError());
 }
 
-void launch_total(const uint64_t *offs, const uint64_t *counts, uint64_t n, uint64_t *out, cudaStream_t s)
+void launch_total(const uint64_t *offs, const uint64_t *counts, uint64_t n, const uint64_t *n_dev, uint64_t add,
+                  uint64_t *out, uint64_t cap, uint64_t *eff, uint64_t *redo, uint64_t redo_bit, cudaStream_t s)
 {
-    total_kernel<<<1, 1, 0, s>>>(offs, counts, n, out);
+    total_kernel<<<1, 1, 0, s>>>(offs, counts, n, n_dev, add, out, cap, eff, redo, redo_bit);
     AH_CUDA(cudaGetLastError());
 }
 
@@ -261,21 +278,32 @@ void exclusive_scan_u64(void *temp, size_t temp_bytes, const uint64_t *in, uint6
     if (n == 0)
         return;
     if (n <= kSmallScan) {
-        scan_small_kernel<<<1, 1024, 0, s>>>(in, out, (uint32_t)n);
+        scan_small_kernel<<<1, 1024, 0, s>>>(in, out, (uint32_t)n, nullptr, 0);
         AH_CUDA(cudaGetLastError());
         return;
     }
     AH_CUDA(cub::DeviceScan::ExclusiveSum(temp, temp_bytes, in, out, (int64_t)n, s));
 }
 
+void exclusive_scan_u64_dev(const uint64_t *in, uint64_t *out, uint64_t n, const uint64_t *n_dev, uint64_t add,
+                            cudaStream_t s)
+{
+    if (n == 0 || n > kSmallScan)
+        throw Error(AH_ERR_ARG, "device-count scan: size outside 1..65536");
+    scan_small_kernel<<<1, 1024, 0, s>>>(in, out, (uint32_t)n, n_dev, add);
+    AH_CUDA(cudaGetLastError());
+}
+
 int scan_u64_launches(uint64_t n) { return n == 0 ? 0 : n <= kSmallScan ? 1 : 2; }
 
-void launch_pair_write(const ah_site *sites, uint64_t n, const uint8_t *pass, const PairDev *pairs_d,
-                       const uint64_t *offsets, ah_amplicon *out, uint64_t cap, cudaStream_t s)
+void launch_pair_write(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const uint8_t *pass,
+                       const PairDev *pairs_d, const uint64_t *offsets, ah_amplicon *out, uint64_t cap,
+                       const uint64_t *skip, uint64_t skip_bit, cudaStream_t s)
 {
     if (!n)
         return;
-    pair_write_kernel<<<grid_for(n, 128), 128, 0, s>>>(sites, n, pass, pairs_d, offsets, out, cap);
+    pair_write_kernel<<<grid_for(n, 128), 128, 0, s>>>(sites, n, n_dev, pass, pairs_d, offsets, out, cap, skip,
+                                                       skip_bit);
     AH_CUDA(cudaGetLastError());
 }
 

@@ -100,113 +100,168 @@ void launch_decode_keys(const uint64_t *keys, uint64_t n, int pbits, const uint6
 } // namespace ah
 
 // ---------------------------------------------------------------------------
-// Small-count fast path: one block of 1024 threads sorts up to kSmallSort
-// keys held in registers (16 per thread) with a block-wide radix sort over the
-// key bits in use, then writes the decoded site records directly.  A series
-// of device-wide sort launches costs more than the whole job at these sizes.
+// Small-count path: rank sort.  Site keys are distinct in their bits
+// [8, end_bit) -- (pair, flat position, primer, strand) names one site -- so
+// a key's place in canonical order is the number of keys below it.  A block
+// of kRankWarps warps takes 32 * kRankQ keys ("queries", kRankQ per lane);
+// each of its warps counts, for every query, the smaller keys in one
+// kRankWarps-th of the whole key array staged in shared memory; warp 0 adds
+// the partial counts, decodes its keys and writes each record at its rank.
+// n^2 compares spread over the whole GPU in one launch: a few microseconds
+// for thousands of sites, where a one-block radix sort or a series of
+// device-wide sort launches takes tens.
 // ---------------------------------------------------------------------------
-#include <cub/block/block_radix_sort.cuh>
-
 namespace ah {
 namespace {
 
-constexpr int kSortItems = 16;
+constexpr int kRankWarps = 8;
+constexpr int kRankQ = 2;
+constexpr uint32_t kRankStageContigs = 4096; // contig tables up to this size are staged in shared memory
 
-// One block of THREADS threads sorts up to THREADS * 16 keys (RADIX bits per
-// pass over the key bits in use) and decodes them.
-template <int THREADS, int RADIX>
-__global__ void __launch_bounds__(THREADS) sort_decode_small_kernel(const uint64_t *__restrict__ keys, uint32_t n,
-                                                                    int end_bit, int pbits,
-                                                                    const uint64_t *__restrict__ contig_off,
-                                                                    uint32_t n_contigs,
-                                                                    const uint32_t *__restrict__ contig_genome,
-                                                                    ah_site *__restrict__ out)
+template <typename K> struct Vec16;
+template <> struct Vec16<uint32_t> {
+    using T = uint4;
+    static constexpr int V = 4;
+    __device__ static void get(const T &x, uint32_t (&e)[4]) { e[0] = x.x; e[1] = x.y; e[2] = x.z; e[3] = x.w; }
+};
+template <> struct Vec16<uint64_t> {
+    using T = ulonglong2;
+    static constexpr int V = 2;
+    __device__ static void get(const T &x, uint64_t (&e)[2]) { e[0] = x.x; e[1] = x.y; }
+};
+
+// K: uint32_t when the sort bits [8, end_bit) fit in 32 bits, else uint64_t.
+// Shared memory: the keys (rounded up to 16 bytes), the partial counts, and
+// the contig offsets when stage_contigs.
+template <typename K>
+__global__ void __launch_bounds__(32 * kRankWarps)
+    rank_sort_decode_kernel(const uint64_t *__restrict__ keys, uint64_t n_arg, const uint64_t *__restrict__ n_dev,
+                            int pbits, const uint64_t *__restrict__ contig_off, uint32_t n_contigs,
+                            bool stage_contigs, const uint32_t *__restrict__ contig_genome, ah_site *__restrict__ out,
+                            uint64_t *__restrict__ n_out, uint64_t *__restrict__ redo)
 {
-    using Sort = cub::BlockRadixSort<uint64_t, THREADS, kSortItems, cub::NullType, RADIX>;
-    extern __shared__ __align__(16) unsigned char sort_smem[]; // Sort::TempStorage (> 48 KB: dynamic)
-    typename Sort::TempStorage &tmp = *reinterpret_cast<typename Sort::TempStorage *>(sort_smem);
-    uint64_t k[kSortItems];
-#pragma unroll
-    for (int q = 0; q < kSortItems; ++q) { // blocked arrangement: thread t holds keys t*16 .. t*16+15
-        const uint32_t i = threadIdx.x * kSortItems + q;
-        k[q] = i < n ? keys[i] : ~0ull; // padding sorts last
+    using VT = Vec16<K>;
+    constexpr int V = VT::V;
+    const uint64_t n64 = n_dev ? *n_dev : n_arg;
+    if (n64 > n_arg) { // device count above the launch's size: the host redoes this step
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *n_out = 0;
+            atomicOr((unsigned long long *)redo, (unsigned long long)kRedoSites);
+        }
+        return;
     }
-    Sort(tmp).Sort(k, 8, end_bit > 8 ? end_bit : 9);
-    // a thread's 16 keys are consecutive in sorted order: one binary search for
-    // the first, then walk forward (positions only grow within a pair)
-    uint32_t lo = 0;
-    uint64_t prev_pp = ~0ull;
+    const uint32_t n = (uint32_t)n64;
+    if (n_out && blockIdx.x == 0 && threadIdx.x == 0)
+        *n_out = n;
+    const uint32_t q0 = blockIdx.x * 32u * kRankQ;
+    if (q0 >= n)
+        return;
+    extern __shared__ __align__(16) unsigned char rank_smem[];
+    const uint32_t nv = (n + V - 1) / V;
+    K *cand = reinterpret_cast<K *>(rank_smem);
+    uint32_t *part = reinterpret_cast<uint32_t *>(rank_smem + (size_t)nv * 16);
+    uint64_t *coff = reinterpret_cast<uint64_t *>(rank_smem + (size_t)nv * 16 + kRankWarps * 32 * kRankQ * 4);
+    for (uint32_t i = threadIdx.x; i < nv * V; i += blockDim.x)
+        cand[i] = i < n ? (K)(keys[i] >> 8) : (K)~(K)0; // padding is never below a key
+    if (stage_contigs)
+        for (uint32_t i = threadIdx.x; i <= n_contigs; i += blockDim.x)
+            coff[i] = contig_off[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    K q[kRankQ];
+    uint32_t r[kRankQ];
 #pragma unroll
-    for (int q = 0; q < kSortItems; ++q) {
-        const uint32_t i = threadIdx.x * kSortItems + q;
+    for (int j = 0; j < kRankQ; ++j) {
+        const uint32_t i = q0 + lane + 32u * j;
+        q[j] = i < n ? cand[i] : (K)0;
+        r[j] = 0;
+    }
+    const uint32_t v0 = (uint32_t)((uint64_t)nv * w / kRankWarps);
+    const uint32_t v1 = (uint32_t)((uint64_t)nv * (w + 1) / kRankWarps);
+    const typename VT::T *cv = reinterpret_cast<const typename VT::T *>(cand);
+#pragma unroll 4
+    for (uint32_t v = v0; v < v1; ++v) {
+        K e[V];
+        VT::get(cv[v], e);
+#pragma unroll
+        for (int t = 0; t < V; ++t)
+#pragma unroll
+            for (int j = 0; j < kRankQ; ++j)
+                r[j] += e[t] < q[j] ? 1u : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kRankQ; ++j)
+        part[w * 32 * kRankQ + lane + 32 * j] = r[j];
+    __syncthreads();
+    if (w != 0)
+        return;
+    const uint64_t *co = stage_contigs ? coff : contig_off;
+    for (int j = 0; j < kRankQ; ++j) {
+        const uint32_t i = q0 + lane + 32u * j;
         if (i >= n)
-            continue;
-        const uint64_t key = k[q];
+            break;
+        uint32_t rank = 0;
+#pragma unroll
+        for (int ww = 0; ww < kRankWarps; ++ww)
+            rank += part[ww * 32 * kRankQ + lane + 32 * j];
+        const uint64_t key = keys[i];
         const uint64_t pp = key >> 10;
         const uint64_t P = pp & ((1ull << pbits) - 1);
-        if (prev_pp == ~0ull || (pp >> pbits) != (prev_pp >> pbits)) {
-            lo = 0;
-            uint32_t hi = n_contigs;
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (__ldg(contig_off + mid) <= P)
-                    lo = mid;
-                else
-                    hi = mid;
-            }
-        } else {
-            while (lo + 1 < n_contigs && __ldg(contig_off + lo + 1) <= P)
-                ++lo;
+        uint32_t lo = 0, hi = n_contigs;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (co[mid] <= P)
+                lo = mid;
+            else
+                hi = mid;
         }
-        prev_pp = pp;
         ah_site s;
         s.genome = contig_genome[lo];
         s.contig = lo;
-        s.pos = (uint32_t)(P - contig_off[lo]);
+        s.pos = (uint32_t)(P - co[lo]);
         s.primer = (uint8_t)((key >> 9) & 1);
         s.strand = (uint8_t)((key >> 8) & 1);
         s.mm = (uint8_t)(key & 0xff);
         s.pair = (uint8_t)(pp >> pbits);
-        out[i] = s;
+        out[rank] = s;
     }
 }
 
-template <int THREADS, int RADIX>
-void run_small_sort(const uint64_t *keys, uint64_t n, int end_bit, int pbits, const uint64_t *contig_off,
-                    uint32_t n_contigs, const uint32_t *contig_genome, ah_site *out, cudaStream_t s)
+template <typename K>
+void run_rank_sort(const uint64_t *keys, uint64_t n, const uint64_t *n_dev, int pbits, const uint64_t *contig_off,
+                   uint32_t n_contigs, const uint32_t *contig_genome, ah_site *out, uint64_t *n_out, uint64_t *redo,
+                   cudaStream_t s)
 {
-    using Sort = cub::BlockRadixSort<uint64_t, THREADS, kSortItems, cub::NullType, RADIX>;
-    const size_t smem = sizeof(typename Sort::TempStorage);
-    static int attr_dev = -1; // one instance per template: opt in to its shared memory once per device
+    const bool stage = n_contigs + 1 <= kRankStageContigs;
+    const size_t smem = (size_t)((n + Vec16<K>::V - 1) / Vec16<K>::V) * 16 + kRankWarps * 32 * kRankQ * 4 +
+                        (stage ? (size_t)(n_contigs + 1) * 8 : 0);
+    static int attr_dev = -1; // one instance per key type: opt in to the largest size once per device
     int dev = 0;
     AH_CUDA(cudaGetDevice(&dev));
     if (dev != attr_dev) {
-        AH_CUDA(cudaFuncSetAttribute(sort_decode_small_kernel<THREADS, RADIX>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const size_t most = kSmallSort * sizeof(K) + kRankWarps * 32 * kRankQ * 4 + kRankStageContigs * 8;
+        AH_CUDA(cudaFuncSetAttribute(rank_sort_decode_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)most));
         attr_dev = dev;
     }
-    sort_decode_small_kernel<THREADS, RADIX><<<1, THREADS, smem, s>>>(keys, (uint32_t)n, end_bit, pbits, contig_off,
-                                                                      n_contigs, contig_genome, out);
+    const unsigned blocks = (unsigned)((n + 32 * kRankQ - 1) / (32 * kRankQ));
+    rank_sort_decode_kernel<K><<<blocks, 32 * kRankWarps, smem, s>>>(keys, n, n_dev, pbits, contig_off, n_contigs,
+                                                                      stage, contig_genome, out, n_out, redo);
     AH_CUDA(cudaGetLastError());
 }
 
 } // namespace
 
-bool launch_sort_decode_small(const uint64_t *keys, uint64_t n, int end_bit, int pbits, const uint64_t *contig_off,
-                              uint32_t n_contigs, const uint32_t *contig_genome, ah_site *out, cudaStream_t s)
+void launch_rank_sort_decode(const uint64_t *keys, uint64_t n, const uint64_t *n_dev, bool key32, int pbits,
+                             const uint64_t *contig_off, uint32_t n_contigs, const uint32_t *contig_genome,
+                             ah_site *out, uint64_t *n_out, uint64_t *redo, cudaStream_t s)
 {
     if (n == 0 || n > kSmallSort)
-        return false;
-    static_assert(1024 * kSortItems == (int)kSmallSort, "the largest instance holds the small sort");
-    if (n <= 2048)
-        run_small_sort<128, 8>(keys, n, end_bit, pbits, contig_off, n_contigs, contig_genome, out, s);
-    else if (n <= 4096)
-        run_small_sort<256, 8>(keys, n, end_bit, pbits, contig_off, n_contigs, contig_genome, out, s);
-    else if (n <= 8192)
-        run_small_sort<512, 6>(keys, n, end_bit, pbits, contig_off, n_contigs, contig_genome, out, s);
+        throw Error(AH_ERR_ARG, "rank sort: count outside 1..16384");
+    if (key32)
+        run_rank_sort<uint32_t>(keys, n, n_dev, pbits, contig_off, n_contigs, contig_genome, out, n_out, redo, s);
     else
-        run_small_sort<1024, 6>(keys, n, end_bit, pbits, contig_off, n_contigs, contig_genome, out, s);
-    return true;
+        run_rank_sort<uint64_t>(keys, n, n_dev, pbits, contig_off, n_contigs, contig_genome, out, n_out, redo, s);
 }
 
 } // namespace ah

@@ -79,7 +79,8 @@ __device__ double exact_tm(const PairDev &pd, const int8_t *bt, int L, uint64_t 
 // shuffles and keeps the best predecessor (2 bits per position), so the
 // argmin oligo is recovered by a backtrack across the group's lanes; its dH,
 // dS are then summed by the four lanes together.  Eight sites per warp.
-__global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__restrict__ sites, uint64_t n,
+__global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__restrict__ sites, uint64_t n_arg,
+                                                           const uint64_t *__restrict__ n_dev,
                                                            const PairDev *__restrict__ pairs, int n_pairs,
                                                            const uint32_t *__restrict__ planes,
                                                            const uint64_t *__restrict__ contig_off,
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                                                            int *__restrict__ err)
 {
     __shared__ int8_t bts[kTmWarps][8][AH_MAX_PRIMER_LEN];
+    const uint64_t n = dev_count(n_arg, n_dev);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, y = lane & 3, g0 = lane & ~3;
     int8_t *bt = bts[warp][g];
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(kExactThreads) tm_exact_kernel(const ah_site *
 
 } // namespace
 
-void launch_tm(const ah_site *sites, uint64_t n, const PairDev *pairs_d, int n_pairs, const uint32_t *planes,
+void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const PairDev *pairs_d, int n_pairs, const uint32_t *planes,
                const uint64_t *contig_off, float *tm_out, uint8_t *pass_out, uint32_t *queue, uint32_t *queue_n,
                int *err, cudaStream_t s)
 {
@@ -340,7 +342,7 @@ void launch_tm(const ah_site *sites, uint64_t n, const PairDev *pairs_d, int n_p
     uint64_t blocks = (n + per_block - 1) / per_block;
     if (blocks > 65535)
         blocks = 65535;
-    tm_kernel<<<(unsigned)blocks, 32 * kTmWarps, 0, s>>>(sites, n, pairs_d, n_pairs, planes, contig_off, tm_out,
+    tm_kernel<<<(unsigned)blocks, 32 * kTmWarps, 0, s>>>(sites, n, n_dev, pairs_d, n_pairs, planes, contig_off, tm_out,
                                                          pass_out, queue, queue_n, err);
     AH_CUDA(cudaGetLastError());
     static int cached_dev = -1, sms = 148;

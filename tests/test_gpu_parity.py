@@ -329,3 +329,96 @@ def test_many_sites_take_the_device_wide_paths(ctx):
     o = oracle_run(w)
     assert len(o["sites"]) > 65536
     assert_parity(gpu_run(ctx, w), o)
+
+
+def _run_into_device(ctx, sid, pid, caps, tm_filter=True):
+    """ah_run into device buffers (torch) with the given capacities (sites,
+    amplicons, sequence bytes); returns (status, out struct, host copies)."""
+    import torch
+    ns, na, nq = caps
+    u8 = dict(dtype=torch.uint8, device="cuda")
+    b = dict(sites=torch.zeros(max(ns, 1) * 16, **u8), tm=torch.zeros(max(ns, 1), dtype=torch.float32, device="cuda"),
+             ps=torch.zeros(max(ns, 1), **u8), amps=torch.zeros(max(na, 1) * 28, **u8),
+             seq=torch.zeros(max(nq, 1), **u8), offs=torch.zeros(max(na, 1) + 1, dtype=torch.int64, device="cuda"))
+    out = ah.RunOut(b["sites"].data_ptr(), ns, 0, b["tm"].data_ptr(), b["ps"].data_ptr(), b["amps"].data_ptr(), na, 0,
+                    b["seq"].data_ptr(), nq, 0, b["offs"].data_ptr(), 1 if tm_filter else 0, 0)
+    status = ah.AH_OK
+    try:
+        ctx.ah_run(sid, [pid], out)
+    except ah.AHError as e:
+        status = e.status
+    torch.cuda.synchronize()
+    return status, out, {k: v.cpu().numpy() for k, v in b.items()}
+
+
+def test_run_into_device_buffers_and_every_fallback(ctx):
+    """ah_run with device outputs: generous and exact capacities take the
+    one-synchronisation path; a capacity one short on any output is reported
+    with the true counts (the step-by-step path), and the next call with room
+    is exact again."""
+    w = synth.collection(seed=3, n_genomes=3, len_lo=3e5, len_hi=9e5)
+    w.pairs = [dict(w.pairs[0], tm_min=50.0)]
+    o = oracle_run(w)
+    n, m = len(o["sites"]), len(o["amps_tm"])
+    seqs, offs = oracle.fetch(w.seq, w.contig_off, o["amps_tm"])
+    q = len(seqs)
+    assert n > 0 and m > 0
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    pid = ctx.ah_set_primers(w.pairs[0]["fwd"], w.pairs[0]["rev"], w.pairs[0])
+
+    def check_all(b):
+        assert b["sites"][:16 * n].tobytes() == o["sites"].tobytes()
+        assert np.array_equal(b["ps"][:n], o["pass_"])
+        assert b["amps"][:28 * m].tobytes() == o["amps_tm"].tobytes()
+        assert b["seq"][:q].tobytes() == seqs
+        assert np.array_equal(b["offs"][:m + 1].astype(np.uint64), offs)
+
+    for caps in [(n + 100, m + 100, q + 100), (n, m, q), (20000, 60000, 1 << 22)]:
+        st, out, b = _run_into_device(ctx, sid, pid, caps)
+        assert st == ah.AH_OK and (out.n_sites, out.n_amplicons, out.n_seq) == (n, m, q)
+        check_all(b)
+    for short in range(3):
+        caps = [n, m, q]
+        caps[short] -= 1
+        st, out, b = _run_into_device(ctx, sid, pid, tuple(caps))
+        assert st == ah.AH_ERR_OVERFLOW and (out.n_sites, out.n_amplicons, out.n_seq) == (n, m, q)
+        if short != 0:
+            assert b["sites"][:16 * n].tobytes() == o["sites"].tobytes()
+    st, out, b = _run_into_device(ctx, sid, pid, (n, m, q))
+    assert st == ah.AH_OK
+    check_all(b)
+    ctx.ah_unload_genomes(sid)
+
+
+@pytest.mark.parametrize("case", ["sites_above_16384", "amplicons_above_16384", "amplicons_above_65535"])
+def test_run_past_the_one_synchronisation_sizes(ctx, case):
+    """Counts above what the one-synchronisation launches are sized for
+    (sites, amplicons, sequence bytes) finish on the step-by-step path with
+    the oracle's records, on the first call and on repeated calls; a small
+    workload afterwards is exact again."""
+    if case == "sites_above_16384":
+        w = synth.random_small(41, n_bases=20_000, n_contigs=8, L_f=6, L_r=5, k=6, min_len=12, max_len=12)
+    elif case == "amplicons_above_16384":
+        w = synth.random_small(7, n_bases=120_000, n_contigs=1, L_f=5, L_r=5, k=1, codes_f="R", codes_r="Y",
+                               min_len=12, max_len=100)
+    else:
+        w = synth.random_small(9, n_bases=100_000, n_contigs=1, L_f=5, L_r=5, k=1, codes_f="R", codes_r="Y",
+                               min_len=10, max_len=250)
+    o = oracle_run(w)
+    seqs, offs = oracle.fetch(w.seq, w.contig_off, o["amps_tm"])
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    pid = ctx.ah_set_primers(w.pairs[0]["fwd"], w.pairs[0]["rev"], w.pairs[0])
+    for _ in range(2):
+        r = ctx.run(sid, [pid], tm_filter=True)
+        assert r["sites"].tobytes() == o["sites"].tobytes()
+        assert np.array_equal(r["pass_"], o["pass_"])
+        assert r["amps"].tobytes() == o["amps_tm"].tobytes()
+        assert r["seqs"] == seqs and np.array_equal(r["offs"], offs)
+    ctx.ah_unload_genomes(sid)
+    t = synth.tiny(0)
+    ot = oracle_run(t)
+    sid = ctx.load(t.seq, t.contig_off, t.contig_genome)
+    pid = ctx.ah_set_primers(t.pairs[0]["fwd"], t.pairs[0]["rev"], t.pairs[0])
+    r = ctx.run(sid, [pid], tm_filter=False)
+    assert r["sites"].tobytes() == ot["sites"].tobytes() and r["amps"].tobytes() == ot["amps"].tobytes()
+    ctx.ah_unload_genomes(sid)
