@@ -161,19 +161,50 @@ __global__ void __launch_bounds__(32 * kRankWarps)
     K *cand = reinterpret_cast<K *>(rank_smem);
     uint32_t *part = reinterpret_cast<uint32_t *>(rank_smem + (size_t)nv * 16);
     uint64_t *coff = reinterpret_cast<uint64_t *>(rank_smem + (size_t)nv * 16 + kRankWarps * 32 * kRankQ * 4);
-    for (uint32_t i = threadIdx.x; i < nv * V; i += blockDim.x)
-        cand[i] = i < n ? (K)(keys[i] >> 8) : (K)~(K)0; // padding is never below a key
-    if (stage_contigs)
-        for (uint32_t i = threadIdx.x; i <= n_contigs; i += blockDim.x)
-            coff[i] = contig_off[i];
-    __syncthreads();
+    uint32_t *cgen = reinterpret_cast<uint32_t *>(coff + (stage_contigs ? n_contigs + 1 : 0));
+    // the block's own queries, full keys, loaded first so their latency overlaps the staging
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint64_t qkey[kRankQ];
+#pragma unroll
+    for (int j = 0; j < kRankQ; ++j) {
+        const uint32_t i = q0 + lane + 32u * j;
+        qkey[j] = i < n ? __ldg(keys + i) : 0;
+    }
+    // stage every key (sort bits only): two keys per 16-byte load, eight loads in flight per thread
+    {
+        const uint32_t pairs = n / 2; // keys is 16-byte aligned (a scratch allocation)
+        const ulonglong2 *k2 = reinterpret_cast<const ulonglong2 *>(keys);
+        for (uint32_t b = threadIdx.x; b < pairs; b += 8 * blockDim.x) {
+            ulonglong2 x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t p = b + u * blockDim.x;
+                x[u] = p < pairs ? __ldg(k2 + p) : make_ulonglong2(~0ull, ~0ull);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t p = b + u * blockDim.x;
+                if (p < pairs) {
+                    cand[2 * p] = (K)(x[u].x >> 8);
+                    cand[2 * p + 1] = (K)(x[u].y >> 8);
+                }
+            }
+        }
+        for (uint32_t i = 2 * pairs + threadIdx.x; i < nv * V; i += blockDim.x)
+            cand[i] = i < n ? (K)(__ldg(keys + i) >> 8) : (K)~(K)0; // odd tail and padding (never below a key)
+    }
+    if (stage_contigs) {
+        for (uint32_t i = threadIdx.x; i <= n_contigs; i += blockDim.x)
+            coff[i] = __ldg(contig_off + i);
+        for (uint32_t i = threadIdx.x; i < n_contigs; i += blockDim.x)
+            cgen[i] = __ldg(contig_genome + i);
+    }
+    __syncthreads();
     K q[kRankQ];
     uint32_t r[kRankQ];
 #pragma unroll
     for (int j = 0; j < kRankQ; ++j) {
-        const uint32_t i = q0 + lane + 32u * j;
-        q[j] = i < n ? cand[i] : (K)0;
+        q[j] = (K)(qkey[j] >> 8);
         r[j] = 0;
     }
     const uint32_t v0 = (uint32_t)((uint64_t)nv * w / kRankWarps);
@@ -196,6 +227,8 @@ __global__ void __launch_bounds__(32 * kRankWarps)
     if (w != 0)
         return;
     const uint64_t *co = stage_contigs ? coff : contig_off;
+    const uint32_t *cg = stage_contigs ? cgen : contig_genome;
+#pragma unroll
     for (int j = 0; j < kRankQ; ++j) {
         const uint32_t i = q0 + lane + 32u * j;
         if (i >= n)
@@ -204,7 +237,7 @@ __global__ void __launch_bounds__(32 * kRankWarps)
 #pragma unroll
         for (int ww = 0; ww < kRankWarps; ++ww)
             rank += part[ww * 32 * kRankQ + lane + 32 * j];
-        const uint64_t key = keys[i];
+        const uint64_t key = qkey[j];
         const uint64_t pp = key >> 10;
         const uint64_t P = pp & ((1ull << pbits) - 1);
         uint32_t lo = 0, hi = n_contigs;
@@ -216,7 +249,7 @@ __global__ void __launch_bounds__(32 * kRankWarps)
                 hi = mid;
         }
         ah_site s;
-        s.genome = contig_genome[lo];
+        s.genome = cg[lo];
         s.contig = lo;
         s.pos = (uint32_t)(P - co[lo]);
         s.primer = (uint8_t)((key >> 9) & 1);
@@ -234,12 +267,12 @@ void run_rank_sort(const uint64_t *keys, uint64_t n, const uint64_t *n_dev, int 
 {
     const bool stage = n_contigs + 1 <= kRankStageContigs;
     const size_t smem = (size_t)((n + Vec16<K>::V - 1) / Vec16<K>::V) * 16 + kRankWarps * 32 * kRankQ * 4 +
-                        (stage ? (size_t)(n_contigs + 1) * 8 : 0);
+                        (stage ? (size_t)(n_contigs + 1) * 8 + (size_t)n_contigs * 4 : 0);
     static int attr_dev = -1; // one instance per key type: opt in to the largest size once per device
     int dev = 0;
     AH_CUDA(cudaGetDevice(&dev));
     if (dev != attr_dev) {
-        const size_t most = kSmallSort * sizeof(K) + kRankWarps * 32 * kRankQ * 4 + kRankStageContigs * 8;
+        const size_t most = kSmallSort * sizeof(K) + kRankWarps * 32 * kRankQ * 4 + kRankStageContigs * 12;
         AH_CUDA(cudaFuncSetAttribute(rank_sort_decode_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)most));
         attr_dev = dev;
@@ -258,6 +291,8 @@ void launch_rank_sort_decode(const uint64_t *keys, uint64_t n, const uint64_t *n
 {
     if (n == 0 || n > kSmallSort)
         throw Error(AH_ERR_ARG, "rank sort: count outside 1..16384");
+    if (reinterpret_cast<uintptr_t>(keys) % 16 != 0)
+        throw Error(AH_ERR_ARG, "rank sort: keys not 16-byte aligned");
     if (key32)
         run_rank_sort<uint32_t>(keys, n, n_dev, pbits, contig_off, n_contigs, contig_genome, out, n_out, redo, s);
     else

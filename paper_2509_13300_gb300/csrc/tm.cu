@@ -14,11 +14,16 @@
 // max-path pass).  Four lanes per site (one DP state each), fp32.
 //
 // Sites whose fp32 maximum lies within 0.01 deg C of tm_min (fp32 error here
-// is ~1e-4 deg C), and sites under a table where some duplex entropy reaches
-// -C, are evaluated the reference way instead: every oligo, in fp64, with the
-// same operation order as the definition and no fused multiply-adds, a whole
-// block sharing one site's oligos (tm_exact_kernel).  Their pass flag is
-// therefore the exact fp64 decision.
+// is ~1e-3 deg C at most) get an exact decision instead: Tm(o) >= tm_min iff
+// F(o) = 1000 dH(o) - thr (dS(o) + C) <= 0 at thr = tm_min in kelvin (the
+// entropy side is negative), so one more shortest-path pass, in fp64 at
+// lam = thr, gives the sign of the minimum of F over all oligos.  Its fp64
+// error is ~1e-10 cal; a minimum within 1e-6 cal of zero (a ratio within
+// ~1e-9 K of the threshold), and every site under a table where some duplex
+// entropy reaches -C, is evaluated the reference way: every oligo, in fp64,
+// with the same operation order as the definition and no fused multiply-adds,
+// a whole block sharing one site's oligos (tm_exact_kernel).  Either way the
+// pass flag is the exact fp64 decision.
 #include <cmath>
 
 #include "ah_internal.h"
@@ -219,9 +224,43 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                 break;
         }
         const float tm32 = lam - 273.15f + (act ? (float)pd.tm_shift : 0.f);
+        // near the threshold: the sign of min F at lam = thr, in fp64 (file comment)
+        const bool near = dink && pass_out && fabsf(tm32 - pd.tm_min_f) < 0.01f;
+        int decided = -1; // 1 pass, 0 fail, -1 undecided
+        if (__any_sync(0xffffffffu, near)) {
+            const double DINF = __longlong_as_double(0x7ff0000000000000ll);
+            const double thr =
+                near ? pd.tm_min + 273.15 - ((pd.saltcorr >= 1 && pd.saltcorr <= 4) ? pd.tm_shift : 0.0) : 0.0;
+            double cd = (near && (mask[0] >> y & 1))
+                            ? 1000.0 * pd.term_dH_d[y * 4 + bt[0]] - thr * pd.term_dS_d[y * 4 + bt[0]]
+                            : DINF;
+            for (int q = 1; q < Lw; ++q) {
+                const bool in = q < L;
+                double best = DINF;
+                for (int x = 0; x < 4; ++x) {
+                    const double cx = __shfl_sync(0xffffffffu, cd, g0 + x);
+                    if (in) {
+                        const int idx = ((x * 4 + y) * 4 + bt[q - 1]) * 4 + bt[q];
+                        const double v = cx + 1000.0 * pd.stack_dH_d[idx] - thr * pd.stack_dS_d[idx];
+                        best = v < best ? v : best;
+                    }
+                }
+                if (in)
+                    cd = (mask[q] >> y & 1) ? best : DINF;
+            }
+            double fin = cd < DINF ? cd + 1000.0 * pd.term_dH_d[y * 4 + bt[L - 1]] -
+                                         thr * pd.term_dS_d[y * 4 + bt[L - 1]]
+                                   : DINF;
+            fin = fmin(fin, __shfl_xor_sync(0xffffffffu, fin, 1));
+            fin = fmin(fin, __shfl_xor_sync(0xffffffffu, fin, 2));
+            const double Cp = pd.sconst + (pd.saltcorr == 5 ? 0.368 * (double)(L - 1) * pd.log_na : 0.0);
+            const double F = fin - thr * Cp;
+            if (near)
+                decided = F < -1e-6 ? 1 : (F > 1e-6 ? 0 : -1);
+        }
         // sites decided the reference way (see the file comment) go to a queue that
         // tm_exact_kernel works off with a whole block per site
-        const bool exact = run && (!dink || (pass_out && fabsf(tm32 - pd.tm_min_f) < 0.01f));
+        const bool exact = run && (!dink || (near && decided < 0));
         if (exact && y == 0)
             queue[atomicAdd(queue_n, 1u)] = (uint32_t)i;
         if (y == 0 && act) {
@@ -230,6 +269,13 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
             if (!bad) {
                 tm = tm32; // replaced by tm_exact_kernel for queued sites
                 pass = tm32 >= pd.tm_min_f;
+                if (decided >= 0) { // the exact decision; the fp32 value (within 1e-3) made consistent with it
+                    pass = (uint8_t)decided;
+                    if (decided && tm < pd.tm_min_f)
+                        tm = pd.tm_min_f;
+                    if (!decided && tm >= pd.tm_min_f)
+                        tm = nextafterf(pd.tm_min_f, -INFINITY);
+                }
             }
             tm_out[i] = tm;
             if (pass_out)
@@ -321,9 +367,14 @@ __global__ void __launch_bounds__(kExactThreads) tm_exact_kernel(const ah_site *
             double m = wmax[0];
             for (int w = 1; w < kExactThreads / 32; ++w)
                 m = wmax[w] > m ? wmax[w] : m;
-            tm_out[i] = (float)m;
-            if (pass_out)
-                pass_out[i] = m >= pd.tm_min;
+            float tm = (float)m;
+            if (pass_out) {
+                const bool pass = m >= pd.tm_min;
+                pass_out[i] = pass;
+                if (!pass && tm >= pd.tm_min_f) // rounding to fp32 may reach the threshold: stay below it
+                    tm = nextafterf(pd.tm_min_f, -INFINITY);
+            }
+            tm_out[i] = tm;
         }
         __syncthreads(); // bt and wmax are reused by the next queued site
     }

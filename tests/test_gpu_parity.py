@@ -173,6 +173,36 @@ def test_threshold_decisions_at_the_boundary(ctx):
         assert_parity(gpu_run(ctx, w), oracle_run(w))
 
 
+def test_threshold_band_decisions(ctx):
+    """tm_min placed inside the 0.01 deg C band around site Tm values, at
+    offsets from 1e-12 to 9e-3: the pass flags equal the fp64 decisions (the
+    fp64 sign test decides most, exhaustive enumeration the closest), and the
+    reported Tm stays within 0.01 of the oracle and on the side of its flag."""
+    w = synth.tiny(0)
+    o_sites = oracle.scan(w.seq, w.contig_off, w.contig_genome, w.pairs)
+    o_tm, _ = oracle.tm(w.seq, w.contig_off, o_sites, w.pairs)
+    vals = np.unique(o_tm[~np.isnan(o_tm)])
+    vals = vals[np.linspace(0, len(vals) - 1, min(5, len(vals))).astype(int)]
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    try:
+        p0 = ctx.ah_set_primers(w.pairs[0]["fwd"], w.pairs[0]["rev"], w.pairs[0])
+        sites = ctx.scan(sid, [p0])
+        assert sites.tobytes() == o_sites.tobytes()
+        for v in vals:
+            for d in (0.0, 1e-12, -1e-12, 1e-9, -1e-9, 1e-6, -1e-6, 1e-4, -1e-4, 3e-3, -3e-3, 9e-3, -9e-3):
+                p = dict(w.pairs[0], tm_min=float(v) + d)
+                pid = ctx.ah_set_primers(p["fwd"], p["rev"], p)
+                tm, ps = ctx.tm(sid, [pid], sites)
+                e_tm, e_ps = oracle.tm(w.seq, w.contig_off, o_sites, [p])
+                assert np.array_equal(ps, e_ps), (v, d)
+                ok = ~np.isnan(e_tm)
+                assert np.abs(tm[ok].astype(np.float64) - e_tm[ok]).max() <= TM_TOL
+                tmin = np.float32(p["tm_min"])
+                assert np.all((tm[ok] >= tmin) == (ps[ok] == 1)), (v, d)
+    finally:
+        ctx.ah_unload_genomes(sid)
+
+
 def test_device_resident_buffers(ctx):
     """Inputs and outputs in device memory (torch CUDA tensors) give the same
     records as host buffers."""
