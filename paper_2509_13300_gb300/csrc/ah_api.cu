@@ -659,19 +659,17 @@ FastResult run_fast(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPatter
                   (uint32_t *)(F + kFlagTmQueue), c->d_err, st);
     }
     {
-        Stage sg(c, "pair", st, 4);
+        Stage sg(c, "pair", st, 3);
         launch_pair_count(sites, ns_max, F + kFlagSites, filt, pd, counts, st);
-        exclusive_scan_u64_dev(counts, offs, ns_max, F + kFlagSites, 0, st);
-        launch_total(offs, counts, ns_max, F + kFlagSites, 0, F + kFlagAux, na_max, F + kFlagAmps, F + kFlagRedo,
-                     kRedoAmps, st);
+        exclusive_scan_u64_dev(counts, offs, ns_max, F + kFlagSites, 0, F + kFlagAux, na_max, F + kFlagAmps,
+                               F + kFlagRedo, kRedoAmps, st);
         launch_pair_write(sites, ns_max, F + kFlagSites, filt, pd, offs, amps, na_max, F + kFlagRedo, kRedoAmps, st);
     }
     {
-        Stage sg(c, "fetch", st, 4);
+        Stage sg(c, "fetch", st, 3);
         launch_fetch_lengths(amps, na_max, F + kFlagAmps, gs.contig_off, gs.n_contigs, len, c->d_err, st);
-        exclusive_scan_u64_dev(len, qoff, na_max + 1, F + kFlagAmps, 1, st);
-        launch_total(qoff, len, na_max + 1, F + kFlagAmps, 1, F + kFlagAux, nq_max, F + kFlagSeq, F + kFlagRedo,
-                     kRedoSeq, st);
+        exclusive_scan_u64_dev(len, qoff, na_max + 1, F + kFlagAmps, 1, F + kFlagAux, nq_max, F + kFlagSeq,
+                               F + kFlagRedo, kRedoSeq, st);
         launch_fetch(amps, na_max, F + kFlagAmps, qoff, gs.planes, gs.contig_off, seq, F + kFlagRedo, kRedoSeq, st);
     }
     check_flags(c, st); // the one synchronisation

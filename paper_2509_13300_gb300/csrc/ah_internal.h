@@ -219,8 +219,10 @@ constexpr uint64_t kSmallScan = 65536;
 // number of kernels exclusive_scan_u64 launches for n values
 int scan_u64_launches(uint64_t n);
 void exclusive_scan_u64(void *temp, size_t temp_bytes, const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s);
-// One-block exclusive scan of min(*n_dev + add, n) values (n <= kSmallScan).
+// One-block exclusive scan of min(*n_dev + add, n) values (n <= kSmallScan);
+// with tot also their sum, and with eff the capacity check of launch_total.
 void exclusive_scan_u64_dev(const uint64_t *in, uint64_t *out, uint64_t n, const uint64_t *n_dev, uint64_t add,
+                            uint64_t *tot, uint64_t cap, uint64_t *eff, uint64_t *redo, uint64_t redo_bit,
                             cudaStream_t s);
 // skip: optional device word; the kernel writes nothing when (*skip & skip_bit) != 0.
 void launch_pair_write(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const uint8_t *pass,

@@ -23,16 +23,30 @@ __device__ __forceinline__ bool same_group(const ah_site &a, const ah_site &b)
     return a.pair == b.pair && a.contig == b.contig && a.pos == b.pos;
 }
 
-// first index in [lo, n) whose (pair, contig, pos) >= (pair, contig, t)
+__device__ __forceinline__ bool site_less(const ah_site &m, uint32_t pair, uint32_t contig, uint64_t t)
+{
+    return (m.pair < pair) || (m.pair == pair && (m.contig < contig || (m.contig == contig && m.pos < t)));
+}
+
+// First index in [lo, n) whose (pair, contig, pos) >= (pair, contig, t), by
+// galloping from lo: probes lo, lo+1, lo+3, lo+7, ... then a binary search in
+// the last gap.  Candidates usually sit right after the group, so this takes
+// one or two dependent loads where a plain binary search over all sites takes
+// log2(n).
 __device__ uint64_t lower_bound_pos(const ah_site *__restrict__ s, uint64_t lo, uint64_t n, uint32_t pair,
                                     uint32_t contig, uint64_t t)
 {
-    uint64_t hi = n;
-    while (lo < hi) {
+    uint64_t step = 1, hi = lo;
+    while (hi < n && site_less(s[hi], pair, contig, t)) {
+        lo = hi + 1;
+        hi = lo + step - 1;
+        step <<= 1;
+    }
+    if (hi > n)
+        hi = n;
+    while (lo < hi) { // s[lo-1] is less (or lo is the start), s[hi] is not (or hi == n)
         const uint64_t mid = (lo + hi) >> 1;
-        const ah_site m = s[mid];
-        const bool less = (m.pair < pair) || (m.pair == pair && (m.contig < contig || (m.contig == contig && m.pos < t)));
-        if (less)
+        if (site_less(s[mid], pair, contig, t))
             lo = mid + 1;
         else
             hi = mid;
@@ -55,22 +69,37 @@ __device__ Group make_group(const ah_site *__restrict__ s, uint64_t n, const uin
     Group g;
     g.valid = false;
     g.nl = 0;
-    const ah_site sa = s[a];
+    // the site and its three neighbours either side, as one batch of independent loads
+    ah_site nb[7];
+#pragma unroll
+    for (int d = -3; d <= 3; ++d) {
+        const int64_t idx = (int64_t)a + d;
+        if (idx >= 0 && (uint64_t)idx < n)
+            nb[d + 3] = s[idx];
+        else
+            nb[d + 3].pair = 0xff; // no site: never in a group
+    }
+    const ah_site sa = nb[3];
     if (sa.strand != 0)
         return g;
     uint64_t g0 = a; // first site of this (pair, contig, pos) group
-    for (int d = 1; d <= 3 && (uint64_t)d <= a; ++d) {
-        const ah_site p = s[a - d];
-        if (!same_group(p, sa))
+#pragma unroll
+    for (int d = 1; d <= 3; ++d) {
+        const ah_site &p = nb[3 - d];
+        if (p.pair == 0xff || !same_group(p, sa))
             break;
         if (p.strand == 0)
             return g; // an earlier '+' site leads this group
         g0 = a - d;
     }
-    for (uint64_t b = a; b < n && b < a + 4 && same_group(s[b], sa); ++b) {
-        if (s[b].strand == 0 && (!pass || pass[b])) {
-            g.li[g.nl] = b;
-            g.lx[g.nl] = s[b].primer;
+#pragma unroll
+    for (int d = 0; d <= 3; ++d) {
+        const ah_site &q = nb[3 + d];
+        if (q.pair == 0xff || !same_group(q, sa))
+            break;
+        if (q.strand == 0 && (!pass || pass[a + d])) {
+            g.li[g.nl] = a + d;
+            g.lx[g.nl] = q.primer;
             ++g.nl;
         }
     }
@@ -209,32 +238,80 @@ __global__ void total_kernel(const uint64_t *__restrict__ offs, const uint64_t *
     }
 }
 
-// One-block exclusive scan: each thread sums a contiguous chunk, the block
-// scans the chunk totals, each thread writes its chunk's prefixes.
+// One-block exclusive scan of m u64 values (m = n, or min(*n_dev + add, n)),
+// 4096 at a time: coalesced loads (four per thread in flight) staged through
+// shared memory, each thread scans four consecutive values, warp shuffles and
+// one shared pass scan the 1024 thread sums, and the results leave through
+// shared memory as coalesced stores.  With tot it also writes the sum of all
+// m values; with eff, *eff = that sum if it is at most cap, else 0 with
+// redo_bit set in *redo.
 __global__ void __launch_bounds__(1024) scan_small_kernel(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
                                                           uint32_t n_arg, const uint64_t *__restrict__ n_dev,
-                                                          uint64_t add)
+                                                          uint64_t add, uint64_t *__restrict__ tot, uint64_t cap,
+                                                          uint64_t *__restrict__ eff, uint64_t *__restrict__ redo,
+                                                          uint64_t redo_bit)
 {
-    __shared__ uint64_t part[1024];
+    __shared__ uint64_t buf[4096];
+    __shared__ uint64_t wsum[32];
     const uint32_t n = n_dev ? (uint32_t)min(*n_dev + add, (uint64_t)n_arg) : n_arg;
-    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
-    const uint32_t lo = min(n, threadIdx.x * per), hi = min(n, lo + per);
-    uint64_t sum = 0;
-    for (uint32_t i = lo; i < hi; ++i)
-        sum += in[i];
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    for (uint32_t d = 1; d < blockDim.x; d <<= 1) { // Hillis-Steele inclusive scan of the chunk totals
-        const uint64_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint64_t carry = 0;
+    for (uint32_t base = 0; base < n; base += 4096) {
+        uint64_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t i = base + tid + 1024u * u;
+            v[u] = i < n ? in[i] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            buf[tid + 1024 * u] = v[u];
         __syncthreads();
-        part[threadIdx.x] += v;
+        const uint64_t x0 = buf[4 * tid], x1 = buf[4 * tid + 1], x2 = buf[4 * tid + 2], x3 = buf[4 * tid + 3];
+        const uint64_t sum = x0 + x1 + x2 + x3;
+        uint64_t incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d)
+                incl += y;
+        }
+        if (lane == 31)
+            wsum[warp] = incl;
         __syncthreads();
+        if (warp == 0) {
+            uint64_t w = wsum[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d)
+                    w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const uint64_t ex = carry + (warp ? wsum[warp - 1] : 0) + incl - sum;
+        buf[4 * tid] = ex;
+        buf[4 * tid + 1] = ex + x0;
+        buf[4 * tid + 2] = ex + x0 + x1;
+        buf[4 * tid + 3] = ex + x0 + x1 + x2;
+        carry += wsum[31];
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t i = base + tid + 1024u * u;
+            if (i < n)
+                out[i] = buf[tid + 1024 * u];
+        }
+        __syncthreads(); // buf and wsum are rewritten by the next chunk
     }
-    uint64_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
-    for (uint32_t i = lo; i < hi; ++i) {
-        const uint64_t v = in[i];
-        out[i] = run;
-        run += v;
+    if (tid == 0 && tot) {
+        *tot = carry;
+        if (eff) {
+            *eff = carry <= cap ? carry : 0;
+            if (carry > cap)
+                atomicOr((unsigned long long *)redo, (unsigned long long)redo_bit);
+        }
     }
 }
 
@@ -278,7 +355,7 @@ void exclusive_scan_u64(void *temp, size_t temp_bytes, const uint64_t *in, uint6
     if (n == 0)
         return;
     if (n <= kSmallScan) {
-        scan_small_kernel<<<1, 1024, 0, s>>>(in, out, (uint32_t)n, nullptr, 0);
+        scan_small_kernel<<<1, 1024, 0, s>>>(in, out, (uint32_t)n, nullptr, 0, nullptr, 0, nullptr, nullptr, 0);
         AH_CUDA(cudaGetLastError());
         return;
     }
@@ -286,11 +363,12 @@ void exclusive_scan_u64(void *temp, size_t temp_bytes, const uint64_t *in, uint6
 }
 
 void exclusive_scan_u64_dev(const uint64_t *in, uint64_t *out, uint64_t n, const uint64_t *n_dev, uint64_t add,
+                            uint64_t *tot, uint64_t cap, uint64_t *eff, uint64_t *redo, uint64_t redo_bit,
                             cudaStream_t s)
 {
     if (n == 0 || n > kSmallScan)
         throw Error(AH_ERR_ARG, "device-count scan: size outside 1..65536");
-    scan_small_kernel<<<1, 1024, 0, s>>>(in, out, (uint32_t)n, n_dev, add);
+    scan_small_kernel<<<1, 1024, 0, s>>>(in, out, (uint32_t)n, n_dev, add, tot, cap, eff, redo, redo_bit);
     AH_CUDA(cudaGetLastError());
 }
 
