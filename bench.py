@@ -253,8 +253,10 @@ def main():
     w = workload(1 + rank, args.n_genomes)
     p = w.pairs[0]
     n_bases = w.n_bases
-    stream = torch.cuda.current_stream()
+    # one stream carries the library's work and the timing events
+    stream = torch.cuda.Stream()
     seq_d = torch.from_numpy(w.seq).to("cuda")
+    torch.cuda.synchronize()
     ctx = ah.Context(local)
     pid = ctx.ah_set_primers(p["fwd"], p["rev"], p)
 

@@ -33,6 +33,11 @@ struct ah_ctx {
     cudaStream_t copy_stream = nullptr; // host->device copies that overlap packing
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_packed[2] = {nullptr, nullptr};
     uint64_t *h_flags = nullptr;     // pinned host mirror of the flag block
+    bool flags_dirty = false;        // work was queued that may set the error word, not read since
+    std::vector<cudaEvent_t> set_events; // free "ready" events of genome sets
+    uint8_t *pin = nullptr;          // pinned staging of small host->device copies (contig tables)
+    size_t pin_bytes = 0;
+    cudaEvent_t pin_ev = nullptr;    // recorded after the last copy out of pin
     std::vector<PairDev> pairdev_h;  // host source of the last per-pair upload
     std::vector<uint32_t> pairdev_ids; // pair ids of that upload
     uint64_t pairdev_version = 0;      // pairs_version at that upload
@@ -293,6 +298,7 @@ int read_flags(ah_ctx *c, cudaStream_t st)
 {
     AH_CUDA(cudaMemcpyAsync(c->h_flags, c->d_flags, kFlagWords * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     AH_CUDA(cudaStreamSynchronize(st));
+    c->flags_dirty = false;
     const int e = (int)(c->h_flags[kFlagErr] & 0xffffffffu);
     if (e != 0)
         AH_CUDA(cudaMemsetAsync(c->d_flags + kFlagErr, 0, sizeof(uint64_t), st));
@@ -318,6 +324,14 @@ GenomeSet &get_set(ah_ctx *c, uint32_t id)
     auto it = c->sets.find(id);
     require(it != c->sets.end(), AH_ERR_ARG, "unknown genome set id " + std::to_string(id));
     return *it->second;
+}
+
+// Order the caller's stream after the work that filled the set (which may
+// have been queued on another stream without a synchronisation).
+void wait_ready(const GenomeSet &gs, cudaStream_t st)
+{
+    if (gs.ready)
+        AH_CUDA(cudaStreamWaitEvent(st, gs.ready, 0));
 }
 
 PrimerPair &get_pair(ah_ctx *c, uint32_t id)
@@ -835,6 +849,7 @@ ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
         AH_CUDA(cudaStreamSynchronize(c->stream));
         AH_CUDA(cudaMallocHost(&c->h_flags, kFlagWords * sizeof(uint64_t)));
         AH_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        AH_CUDA(cudaEventCreateWithFlags(&c->pin_ev, cudaEventDisableTiming));
         for (int b = 0; b < 2; ++b) {
             AH_CUDA(cudaEventCreateWithFlags(&c->ev_copied[b], cudaEventDisableTiming));
             AH_CUDA(cudaEventCreateWithFlags(&c->ev_packed[b], cudaEventDisableTiming));
@@ -866,6 +881,15 @@ void ah_destroy(ah_ctx *c)
         cudaEventDestroy(e);
     if (c->h_flags)
         cudaFreeHost(c->h_flags);
+    if (c->pin)
+        cudaFreeHost(c->pin);
+    if (c->pin_ev)
+        cudaEventDestroy(c->pin_ev);
+    for (auto &kv : c->sets)
+        if (kv.second->ready)
+            cudaEventDestroy(kv.second->ready);
+    for (auto e : c->set_events)
+        cudaEventDestroy(e);
     if (c->copy_stream) {
         cudaStreamSynchronize(c->copy_stream);
         cudaStreamDestroy(c->copy_stream);
@@ -954,8 +978,6 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
         gs->n_bases = n_bases;
         gs->n_contigs = n_contigs;
         gs->n_tiles = (n_bases + kTileBases - 1) / kTileBases;
-        gs->contig_off_h.assign(contig_off, contig_off + n_contigs + 1);
-        gs->contig_genome_h.assign(contig_genome, contig_genome + n_contigs);
         const size_t plane_bytes = gs->n_tiles * kTileBytes;
         try {
             gs->planes = (uint32_t *)dev_alloc(c, plane_bytes);
@@ -968,10 +990,26 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
             throw;
         }
         gs->bytes = plane_bytes + (n_contigs + 1) * sizeof(uint64_t) + n_contigs * sizeof(uint32_t);
-        AH_CUDA(cudaMemcpyAsync(gs->contig_off, gs->contig_off_h.data(), (n_contigs + 1) * sizeof(uint64_t),
-                                cudaMemcpyHostToDevice, st));
-        AH_CUDA(cudaMemcpyAsync(gs->contig_genome, gs->contig_genome_h.data(), n_contigs * sizeof(uint32_t),
-                                cudaMemcpyHostToDevice, st));
+        {
+            // contig tables through pinned staging: asynchronous copies (a pageable
+            // source would make the driver stage and wait)
+            const size_t ob = (n_contigs + 1) * sizeof(uint64_t), gb = n_contigs * sizeof(uint32_t);
+            AH_CUDA(cudaEventSynchronize(c->pin_ev)); // the last copies out of the staging buffer are done
+            if (c->pin_bytes < ob + gb) {
+                if (c->pin)
+                    AH_CUDA(cudaFreeHost(c->pin));
+                c->pin = nullptr;
+                c->pin_bytes = 0;
+                const size_t want = std::max<size_t>(ob + gb + (ob + gb) / 4, 1 << 16);
+                AH_CUDA(cudaMallocHost(&c->pin, want));
+                c->pin_bytes = want;
+            }
+            memcpy(c->pin, contig_off, ob);
+            memcpy(c->pin + ob, contig_genome, gb);
+            AH_CUDA(cudaMemcpyAsync(gs->contig_off, c->pin, ob, cudaMemcpyHostToDevice, st));
+            AH_CUDA(cudaMemcpyAsync(gs->contig_genome, c->pin + ob, gb, cudaMemcpyHostToDevice, st));
+            AH_CUDA(cudaEventRecord(c->pin_ev, st));
+        }
         const bool dev_seq = n_bases && is_device_ptr(c, seq);
         if (gs->n_tiles) {
             if (dev_seq) {
@@ -1010,8 +1048,18 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
                 }
             }
         }
+        if (c->set_events.empty()) {
+            cudaEvent_t e;
+            AH_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            c->set_events.push_back(e);
+        }
+        gs->ready = c->set_events.back();
+        c->set_events.pop_back();
+        AH_CUDA(cudaEventRecord(gs->ready, st));
         if (!dev_seq) // the caller's host buffer may be reused once this call returns
             check_flags(c, st);
+        else
+            c->flags_dirty = true;
         uint32_t id = c->next_set++;
         c->sets[id] = std::move(gs);
         *set_id_out = id;
@@ -1024,10 +1072,16 @@ ah_status ah_unload_genomes(ah_ctx *c, uint32_t set_id)
         return AH_ERR_ARG;
     return guarded(c, [&] {
         GenomeSet &gs = get_set(c, set_id);
-        const int e = read_flags(c, c->stream); // also reports a failure of a pack nothing else synchronised on
+        // the calls that read a set synchronise before they return; its packing may not have
+        if (gs.ready)
+            AH_CUDA(cudaEventSynchronize(gs.ready));
+        // a failure of a packing nothing else synchronised on is reported here
+        const int e = c->flags_dirty ? read_flags(c, c->stream) : 0;
         dev_free(c, gs.planes, gs.n_tiles * kTileBytes);
         dev_free(c, gs.contig_off, (gs.n_contigs + 1) * sizeof(uint64_t));
         dev_free(c, gs.contig_genome, gs.n_contigs * sizeof(uint32_t));
+        if (gs.ready)
+            c->set_events.push_back(gs.ready);
         c->sets.erase(set_id);
         raise_device_error(e);
     });
@@ -1107,6 +1161,7 @@ ah_status ah_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
         *n_out = 0;
         GenomeSet &gs = get_set(c, set_id);
         cudaStream_t st = stream_of(c, stream);
+        wait_ready(gs, st);
         std::vector<ScanPattern> pats = patterns_of(c, pair_ids, n_pairs);
         uint64_t *keys = nullptr;
         const uint64_t count = scan_keys(c, gs, pats, &keys, st);
@@ -1132,6 +1187,7 @@ ah_status ah_tune_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
         require(pair_ids && n_pairs >= 1 && n_pairs <= AH_MAX_PAIRS_PER_SCAN, AH_ERR_ARG, "n_pairs must be 1..16");
         GenomeSet &gs = get_set(c, set_id);
         cudaStream_t st = stream_of(c, stream);
+        wait_ready(gs, st);
         std::vector<ScanPattern> pats = patterns_of(c, pair_ids, n_pairs);
         const int pbits = std::max(1, bit_length(gs.n_bases));
         uint64_t tiles = std::min<uint64_t>(gs.n_tiles, sample_tiles ? sample_tiles : 4096);
@@ -1214,6 +1270,7 @@ ah_status ah_run(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t 
         o->n_sites = o->n_amplicons = o->n_seq = 0;
         GenomeSet &gs = get_set(c, set_id);
         cudaStream_t st = stream_of(c, stream);
+        wait_ready(gs, st);
         std::vector<ScanPattern> pats = patterns_of(c, pair_ids, n_pairs);
         const PairDev *pd = upload_pairs(c, pair_ids, n_pairs, st);
         uint64_t *keys = nullptr;
@@ -1238,6 +1295,7 @@ ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n
         require(n == 0 || (sites && tm_out), AH_ERR_ARG, "ah_tm: null argument");
         GenomeSet &gs = get_set(c, set_id);
         cudaStream_t st = stream_of(c, stream);
+        wait_ready(gs, st);
         const PairDev *pd = upload_pairs(c, pair_ids, n_pairs, st);
         if (n == 0)
             return;
@@ -1274,6 +1332,7 @@ ah_status ah_pair(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
         *n_out = 0;
         GenomeSet &gs = get_set(c, set_id);
         cudaStream_t st = stream_of(c, stream);
+        wait_ready(gs, st);
         const PairDev *pd = upload_pairs(c, pair_ids, n_pairs, st);
         if (n == 0)
             return;
@@ -1324,6 +1383,7 @@ ah_status ah_fetch(ah_ctx *c, uint32_t set_id, const ah_amplicon *amplicons, uin
         require(offsets_out && (n == 0 || amplicons) && (cap == 0 || seq_out), AH_ERR_ARG, "ah_fetch: null argument");
         GenomeSet &gs = get_set(c, set_id);
         cudaStream_t st = stream_of(c, stream);
+        wait_ready(gs, st);
         reset_flags(c, st);
         const ah_amplicon *a = stage_in(c, "fetch_in", amplicons, n, st);
         uint64_t *len = (uint64_t *)scratch(c, "fetch_len", (n + 1) * sizeof(uint64_t));

@@ -41,9 +41,10 @@ struct GenomeSet {
     uint32_t *planes = nullptr;        // device, n_tiles * kTileBytes
     uint64_t *contig_off = nullptr;    // device, n_contigs + 1
     uint32_t *contig_genome = nullptr; // device, n_contigs
-    std::vector<uint64_t> contig_off_h;
-    std::vector<uint32_t> contig_genome_h;
     size_t bytes = 0;
+    // recorded after the work that fills the set (the packing); every call that
+    // reads the set waits for it on its own stream, and unloading waits for it
+    cudaEvent_t ready = nullptr;
 };
 
 // One registered primer pair.  mask[i] is the 4-bit IUPAC set of primer
