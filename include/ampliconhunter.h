@@ -174,14 +174,21 @@ size_t ah_device_bytes(const ah_ctx *ctx);
  * contig_off (host): n_contigs + 1 non-decreasing offsets into seq, first 0,
  * last n_bases.  contig_genome (host): genome id of each contig.
  * The library packs the sequence on the device into its own layout (4 one-hot
- * bitplanes A/C/G/T) and returns an id in *set_id_out.  The caller's arrays
- * are not referenced after the call.
+ * bitplanes A/C/G/T) and returns an id in *set_id_out.  Host arrays are not
+ * referenced after the call.  A device seq is read by work queued on
+ * `stream` (stream-ordered, like any CUDA call): it must stay valid until
+ * that work has run; the call returns without waiting for it.  Every later
+ * call that reads the set orders itself after the packing, whatever stream
+ * it is given.  A device-side failure of the packing is reported by the next
+ * call on the context that synchronises (ah_unload_genomes at the latest).
  * Errors: AH_ERR_ARG (null pointers, non-monotone offsets, n_contigs = 0),
- * AH_ERR_BUDGET, AH_ERR_OOM, AH_ERR_CUDA. */
+ * AH_ERR_BUDGET, AH_ERR_OOM, AH_ERR_TIMEOUT, AH_ERR_CUDA. */
 ah_status ah_load_genomes(ah_ctx *ctx, const uint8_t *seq, uint64_t n_bases, const uint64_t *contig_off,
                           uint32_t n_contigs, const uint32_t *contig_genome, uint32_t *set_id_out, void *stream);
 
-/* Free a loaded genome set.  AH_ERR_ARG for an unknown id. */
+/* Free a loaded genome set (after its packing has run).  AH_ERR_ARG for an
+ * unknown id; AH_ERR_TIMEOUT for a packing that failed on the device and was
+ * not reported before (the set is freed either way). */
 ah_status ah_unload_genomes(ah_ctx *ctx, uint32_t set_id);
 
 /* Register a degenerate primer pair with its PCR parameters (Sec. 1, Sec.
@@ -293,22 +300,33 @@ typedef struct ah_run_out {
  * sites (as ah_pair; with tm_filter only sites that pass) and the amplicon
  * sequences (as ah_fetch), for the listed pairs on one loaded set.  The
  * results are identical to that sequence of calls; only the number of host
- * synchronisations differs (four).  An output whose capacity is too small is
- * not written, its count is still reported, the others are written, and the
- * call returns AH_ERR_OVERFLOW.
+ * synchronisations differs: one when every count fits the sizes the call's
+ * launches are sized for (at most 16384 sites and the sites capacity when the
+ * site outputs are device memory; the amplicon and sequence capacities when
+ * those outputs are device memory, else sizes the context grows from earlier
+ * calls; fewer than 65536 amplicons), else the call continues step by step
+ * with up to three more.  Device outputs are complete when the call returns
+ * (copies to host outputs too).  An output whose capacity is too small is not
+ * written, its count is still reported, the others are written, and the call
+ * returns AH_ERR_OVERFLOW.
  * Errors: AH_ERR_ARG, AH_ERR_OVERFLOW, AH_ERR_JIT, AH_ERR_TIMEOUT, AH_ERR_CUDA. */
 ah_status ah_run(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, ah_run_out *out,
                  void *stream);
 
-/* Measurement: per-stage device time and kernel launches.  ah_set_profiling
- * (enable != 0) clears the counters and, from then on, brackets each stage
- * of each call with CUDA events on the stream the stage runs on.  Stages:
- * "pack" (ah_load_genomes), "scan", "sort", "decode" (ah_scan), "validate"
- * (record checks of ah_tm / ah_pair), "tm", "pair", "fetch".  ah_get_profile
- * returns, for one stage, the summed milliseconds, the kernels launched and
- * the number of bracketed calls; stage = NULL gives the sums over stages and
- * the count of every kernel the library launched since the last clear
- * (counted whether or not profiling is on).  Output pointers may be null. */
+/* Measurement: per-stage device time, host time and kernel launches.
+ * ah_set_profiling clears the counters; enable = 1 then brackets each stage
+ * of each call with CUDA events on the stream the stage runs on and times
+ * host sections, enable = 2 times host sections only, 0 stops.  Device
+ * stages: "pack" (ah_load_genomes), "scan", "sort", "decode" (ah_scan),
+ * "validate" (record checks of ah_tm / ah_pair), "tm", "pair", "fetch".  Host
+ * sections (wall time inside the library): "host.load", "host.load.alloc",
+ * "host.load.tables", "host.load.pack", "host.run", "host.run.prep",
+ * "host.run.launch", "host.run.wait", "host.unload".  ah_get_profile returns,
+ * for one stage or section, the summed milliseconds, the kernels launched
+ * and the number of bracketed calls; stage = NULL gives the sums over device
+ * stages and the count of every kernel the library launched since the last
+ * clear (counted whether or not profiling is on).  Event timings are read
+ * lazily (at ah_get_profile at the latest).  Output pointers may be null. */
 ah_status ah_set_profiling(ah_ctx *ctx, int enable);
 ah_status ah_get_profile(const ah_ctx *ctx, const char *stage, double *ms, uint64_t *launches, uint64_t *calls);
 

@@ -190,8 +190,9 @@ class Context:
     def device_bytes(self) -> int:
         return int(self._lib.ah_device_bytes(self.h))
 
-    def ah_set_profiling(self, enable: bool):
-        self._check(self._lib.ah_set_profiling(self.h, 1 if enable else 0))
+    def ah_set_profiling(self, enable):
+        """0/False off, 1/True stage events and host sections, 2 host sections only."""
+        self._check(self._lib.ah_set_profiling(self.h, int(enable)))
 
     def ah_get_profile(self, stage: str | None):
         """(milliseconds, kernel launches, calls) of one stage, or totals for None."""

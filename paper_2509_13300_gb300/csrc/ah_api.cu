@@ -2,6 +2,7 @@
 // registry, pointer staging and the call sequences of ah_scan / ah_tm /
 // ah_pair / ah_fetch.  All arithmetic runs in the kernels of this library.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -63,7 +64,8 @@ struct ah_ctx {
         cudaEvent_t a, b;
         int launches;
     };
-    bool profiling = false;
+    bool profiling = false;  // stage events
+    bool host_timing = false; // host sections
     std::map<std::string, Prof> prof;
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> events;
@@ -83,15 +85,12 @@ template <class F> ah_status guarded(ah_ctx *ctx, F &&f)
         if (ctx)
             AH_CUDA(cudaSetDevice(ctx->device));
         f();
-        if (ctx && !ctx->pending.empty())
+        if (ctx && ctx->pending.size() >= 4096) // event timings are read lazily
             prof_flush(ctx);
         return AH_OK;
     } catch (const Error &e) {
-        if (ctx) {
+        if (ctx)
             ctx->err = e.msg;
-            if (!ctx->pending.empty())
-                prof_flush(ctx);
-        }
         return e.status;
     } catch (const std::bad_alloc &) {
         if (ctx)
@@ -102,6 +101,13 @@ template <class F> ah_status guarded(ah_ctx *ctx, F &&f)
             ctx->err = e.what();
         return AH_ERR_ARG;
     }
+}
+
+// (a literal message builds no string unless the check fails: these run in per-contig loops)
+void require(bool cond, ah_status st, const char *msg)
+{
+    if (!cond)
+        throw Error(st, msg);
 }
 
 void require(bool cond, ah_status st, const std::string &msg)
@@ -200,6 +206,26 @@ struct Stage {
             cudaEvent_t b = get_event(c);
             cudaEventRecord(b, st);
             c->pending.push_back({name, a, b, launches});
+        }
+    }
+};
+
+// Host wall time of one section of a call, when host timing is on.
+struct HostSpan {
+    ah_ctx *c;
+    const char *name;
+    std::chrono::steady_clock::time_point t0;
+    HostSpan(ah_ctx *c_, const char *n) : c(c_), name(n)
+    {
+        if (c->host_timing)
+            t0 = std::chrono::steady_clock::now();
+    }
+    ~HostSpan()
+    {
+        if (c->host_timing) {
+            auto &q = c->prof[name];
+            q.ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            q.calls += 1;
         }
     }
 };
@@ -627,6 +653,7 @@ enum FastResult { kFastDone, kFastKeys, kFastRescan };
 FastResult run_fast(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPattern> &pats, const PairDev *pd,
                     uint32_t n_pairs, ah_run_out *o, cudaStream_t st, uint64_t **keys_out, uint64_t *ns_out)
 {
+    std::unique_ptr<HostSpan> span(new HostSpan(c, "host.run.prep"));
     uint64_t *F = c->d_flags;
     const int pbits = std::max(1, bit_length(gs.n_bases));
     const int end_bit = 10 + pbits + bit_length(n_pairs - 1);
@@ -657,6 +684,7 @@ FastResult run_fast(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPatter
     const uint8_t *filt = o->tm_filter ? pass : nullptr;
 
     ScanKernel *k = scan_kernel(pats, tuning_for(c, pats), c->device);
+    span.reset(new HostSpan(c, "host.run.launch"));
     reset_flags(c, st);
     {
         Stage sg(c, "scan", st, 1);
@@ -686,7 +714,9 @@ FastResult run_fast(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPatter
                                F + kFlagRedo, kRedoSeq, st);
         launch_fetch(amps, na_max, F + kFlagAmps, qoff, gs.planes, gs.contig_off, seq, F + kFlagRedo, kRedoSeq, st);
     }
+    span.reset(new HostSpan(c, "host.run.wait"));
     check_flags(c, st); // the one synchronisation
+    span.reset();
     const uint64_t *H = c->h_flags;
     const uint64_t ns = H[kFlagCounter];
     *keys_out = keys;
@@ -914,7 +944,8 @@ ah_status ah_set_profiling(ah_ctx *c, int enable)
         prof_flush(c);
         c->prof.clear();
         c->launches_total = 0;
-        c->profiling = enable != 0;
+        c->profiling = enable == 1;
+        c->host_timing = enable == 1 || enable == 2;
     });
 }
 
@@ -922,10 +953,19 @@ ah_status ah_get_profile(const ah_ctx *c, const char *stage, double *ms, uint64_
 {
     if (!c)
         return AH_ERR_ARG;
+    if (!c->pending.empty()) { // read the event timings still pending
+        try {
+            cudaSetDevice(c->device);
+            prof_flush(const_cast<ah_ctx *>(c));
+        } catch (...) {
+        }
+    }
     double m = 0;
     uint64_t l = 0, k = 0;
     if (!stage) {
         for (auto &kv : c->prof) {
+            if (kv.first.compare(0, 5, "host.") == 0)
+                continue;
             m += kv.second.ms;
             k += kv.second.calls;
         }
@@ -962,6 +1002,7 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
     if (!c)
         return AH_ERR_ARG;
     return guarded(c, [&] {
+        HostSpan hs(c, "host.load");
         require(set_id_out && contig_off && contig_genome && n_contigs >= 1, AH_ERR_ARG,
                 "ah_load_genomes: null argument or no contigs");
         require(n_bases == 0 || seq, AH_ERR_ARG, "ah_load_genomes: seq is null");
@@ -979,6 +1020,7 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
         gs->n_contigs = n_contigs;
         gs->n_tiles = (n_bases + kTileBases - 1) / kTileBases;
         const size_t plane_bytes = gs->n_tiles * kTileBytes;
+        HostSpan hs_alloc(c, "host.load.alloc");
         try {
             gs->planes = (uint32_t *)dev_alloc(c, plane_bytes);
             gs->contig_off = (uint64_t *)dev_alloc(c, (n_contigs + 1) * sizeof(uint64_t));
@@ -990,28 +1032,10 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
             throw;
         }
         gs->bytes = plane_bytes + (n_contigs + 1) * sizeof(uint64_t) + n_contigs * sizeof(uint32_t);
-        {
-            // contig tables through pinned staging: asynchronous copies (a pageable
-            // source would make the driver stage and wait)
-            const size_t ob = (n_contigs + 1) * sizeof(uint64_t), gb = n_contigs * sizeof(uint32_t);
-            AH_CUDA(cudaEventSynchronize(c->pin_ev)); // the last copies out of the staging buffer are done
-            if (c->pin_bytes < ob + gb) {
-                if (c->pin)
-                    AH_CUDA(cudaFreeHost(c->pin));
-                c->pin = nullptr;
-                c->pin_bytes = 0;
-                const size_t want = std::max<size_t>(ob + gb + (ob + gb) / 4, 1 << 16);
-                AH_CUDA(cudaMallocHost(&c->pin, want));
-                c->pin_bytes = want;
-            }
-            memcpy(c->pin, contig_off, ob);
-            memcpy(c->pin + ob, contig_genome, gb);
-            AH_CUDA(cudaMemcpyAsync(gs->contig_off, c->pin, ob, cudaMemcpyHostToDevice, st));
-            AH_CUDA(cudaMemcpyAsync(gs->contig_genome, c->pin + ob, gb, cudaMemcpyHostToDevice, st));
-            AH_CUDA(cudaEventRecord(c->pin_ev, st));
-        }
         const bool dev_seq = n_bases && is_device_ptr(c, seq);
+        // the packing first (it reads no contig table), then the tables' copies
         if (gs->n_tiles) {
+            HostSpan hs_pack(c, "host.load.pack");
             if (dev_seq) {
                 // stream-ordered: the pack runs after the caller's earlier work on
                 // the stream; a device-side failure reaches the next call that
@@ -1048,6 +1072,27 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
                 }
             }
         }
+        {
+            HostSpan hs_tables(c, "host.load.tables");
+            // contig tables through pinned staging: asynchronous copies (a pageable
+            // source would make the driver stage and wait)
+            const size_t ob = (n_contigs + 1) * sizeof(uint64_t), gb = n_contigs * sizeof(uint32_t);
+            AH_CUDA(cudaEventSynchronize(c->pin_ev)); // the last copies out of the staging buffer are done
+            if (c->pin_bytes < ob + gb) {
+                if (c->pin)
+                    AH_CUDA(cudaFreeHost(c->pin));
+                c->pin = nullptr;
+                c->pin_bytes = 0;
+                const size_t want = std::max<size_t>(ob + gb + (ob + gb) / 4, 1 << 16);
+                AH_CUDA(cudaMallocHost(&c->pin, want));
+                c->pin_bytes = want;
+            }
+            memcpy(c->pin, contig_off, ob);
+            memcpy(c->pin + ob, contig_genome, gb);
+            AH_CUDA(cudaMemcpyAsync(gs->contig_off, c->pin, ob, cudaMemcpyHostToDevice, st));
+            AH_CUDA(cudaMemcpyAsync(gs->contig_genome, c->pin + ob, gb, cudaMemcpyHostToDevice, st));
+            AH_CUDA(cudaEventRecord(c->pin_ev, st));
+        }
         if (c->set_events.empty()) {
             cudaEvent_t e;
             AH_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -1071,6 +1116,7 @@ ah_status ah_unload_genomes(ah_ctx *c, uint32_t set_id)
     if (!c)
         return AH_ERR_ARG;
     return guarded(c, [&] {
+        HostSpan hs(c, "host.unload");
         GenomeSet &gs = get_set(c, set_id);
         // the calls that read a set synchronise before they return; its packing may not have
         if (gs.ready)
@@ -1268,6 +1314,7 @@ ah_status ah_run(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t 
                     (o->seq_cap == 0 || o->seq),
                 AH_ERR_ARG, "ah_run: null buffer with non-zero capacity");
         o->n_sites = o->n_amplicons = o->n_seq = 0;
+        HostSpan hs(c, "host.run");
         GenomeSet &gs = get_set(c, set_id);
         cudaStream_t st = stream_of(c, stream);
         wait_ready(gs, st);
