@@ -116,7 +116,7 @@ namespace {
 
 constexpr int kRankWarps = 8;
 constexpr int kRankQ = 2;
-constexpr uint32_t kRankStageContigs = 4096; // contig tables up to this size are staged in shared memory
+constexpr uint32_t kRankStageContigs = 4096; // contig offset tables up to this size are staged in shared memory
 
 template <typename K> struct Vec16;
 template <> struct Vec16<uint32_t> {
@@ -161,7 +161,6 @@ __global__ void __launch_bounds__(32 * kRankWarps)
     K *cand = reinterpret_cast<K *>(rank_smem);
     uint32_t *part = reinterpret_cast<uint32_t *>(rank_smem + (size_t)nv * 16);
     uint64_t *coff = reinterpret_cast<uint64_t *>(rank_smem + (size_t)nv * 16 + kRankWarps * 32 * kRankQ * 4);
-    uint32_t *cgen = reinterpret_cast<uint32_t *>(coff + (stage_contigs ? n_contigs + 1 : 0));
     // the block's own queries, full keys, loaded first so their latency overlaps the staging
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint64_t qkey[kRankQ];
@@ -193,11 +192,26 @@ __global__ void __launch_bounds__(32 * kRankWarps)
         for (uint32_t i = 2 * pairs + threadIdx.x; i < nv * V; i += blockDim.x)
             cand[i] = i < n ? (K)(__ldg(keys + i) >> 8) : (K)~(K)0; // odd tail and padding (never below a key)
     }
-    if (stage_contigs) {
-        for (uint32_t i = threadIdx.x; i <= n_contigs; i += blockDim.x)
-            coff[i] = __ldg(contig_off + i);
-        for (uint32_t i = threadIdx.x; i < n_contigs; i += blockDim.x)
-            cgen[i] = __ldg(contig_genome + i);
+    if (stage_contigs) { // n_contigs + 1 <= kRankStageContigs: at most 8 vector loads per thread, all in flight
+        const uint32_t m = n_contigs + 1, m2 = m / 2;
+        const ulonglong2 *c2 = reinterpret_cast<const ulonglong2 *>(contig_off); // 16-byte aligned (checked on the host)
+        ulonglong2 x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t p = threadIdx.x + u * blockDim.x;
+            if (p < m2)
+                x[u] = __ldg(c2 + p);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t p = threadIdx.x + u * blockDim.x;
+            if (p < m2) {
+                coff[2 * p] = x[u].x;
+                coff[2 * p + 1] = x[u].y;
+            }
+        }
+        if ((m & 1) && threadIdx.x == 0)
+            coff[m - 1] = __ldg(contig_off + m - 1);
     }
     __syncthreads();
     K q[kRankQ];
@@ -227,7 +241,6 @@ __global__ void __launch_bounds__(32 * kRankWarps)
     if (w != 0)
         return;
     const uint64_t *co = stage_contigs ? coff : contig_off;
-    const uint32_t *cg = stage_contigs ? cgen : contig_genome;
 #pragma unroll
     for (int j = 0; j < kRankQ; ++j) {
         const uint32_t i = q0 + lane + 32u * j;
@@ -249,7 +262,7 @@ __global__ void __launch_bounds__(32 * kRankWarps)
                 hi = mid;
         }
         ah_site s;
-        s.genome = cg[lo];
+        s.genome = __ldg(contig_genome + lo);
         s.contig = lo;
         s.pos = (uint32_t)(P - co[lo]);
         s.primer = (uint8_t)((key >> 9) & 1);
@@ -265,14 +278,15 @@ void run_rank_sort(const uint64_t *keys, uint64_t n, const uint64_t *n_dev, int 
                    uint32_t n_contigs, const uint32_t *contig_genome, ah_site *out, uint64_t *n_out, uint64_t *redo,
                    cudaStream_t s)
 {
-    const bool stage = n_contigs + 1 <= kRankStageContigs;
+    // staging reads the offsets with 16-byte loads, 8 per thread of 256
+    const bool stage = n_contigs + 1 <= kRankStageContigs && reinterpret_cast<uintptr_t>(contig_off) % 16 == 0;
     const size_t smem = (size_t)((n + Vec16<K>::V - 1) / Vec16<K>::V) * 16 + kRankWarps * 32 * kRankQ * 4 +
-                        (stage ? (size_t)(n_contigs + 1) * 8 + (size_t)n_contigs * 4 : 0);
+                        (stage ? (size_t)(n_contigs + 1) * 8 : 0);
     static int attr_dev = -1; // one instance per key type: opt in to the largest size once per device
     int dev = 0;
     AH_CUDA(cudaGetDevice(&dev));
     if (dev != attr_dev) {
-        const size_t most = kSmallSort * sizeof(K) + kRankWarps * 32 * kRankQ * 4 + kRankStageContigs * 12;
+        const size_t most = kSmallSort * sizeof(K) + kRankWarps * 32 * kRankQ * 4 + kRankStageContigs * 8;
         AH_CUDA(cudaFuncSetAttribute(rank_sort_decode_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)most));
         attr_dev = dev;
