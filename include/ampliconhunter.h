@@ -316,7 +316,9 @@ ah_status ah_run(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32_
 /* Measurement: per-stage device time, host time and kernel launches.
  * ah_set_profiling clears the counters; enable = 1 then brackets each stage
  * of each call with CUDA events on the stream the stage runs on and times
- * host sections, enable = 2 times host sections only, 0 stops.  Device
+ * host sections, enable = 2 times host sections only, enable = 3 brackets
+ * only the "pack" and "scan" stages (the streaming kernels; fewer events in
+ * the stream) and times host sections, 0 stops.  Device
  * stages: "pack" (ah_load_genomes), "scan", "sort", "decode" (ah_scan),
  * "validate" (record checks of ah_tm / ah_pair), "tm", "pair", "fetch".  Host
  * sections (wall time inside the library): "host.load", "host.load.alloc",

@@ -191,7 +191,8 @@ class Context:
         return int(self._lib.ah_device_bytes(self.h))
 
     def ah_set_profiling(self, enable):
-        """0/False off, 1/True stage events and host sections, 2 host sections only."""
+        """0/False off, 1/True stage events and host sections, 2 host sections only,
+        3 events on the pack and scan stages only, and host sections."""
         self._check(self._lib.ah_set_profiling(self.h, int(enable)))
 
     def ah_get_profile(self, stage: str | None):

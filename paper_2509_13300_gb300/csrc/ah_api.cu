@@ -65,6 +65,7 @@ struct ah_ctx {
         int launches;
     };
     bool profiling = false;  // stage events
+    bool prof_streaming_only = false; // events on the "pack" and "scan" stages only
     bool host_timing = false; // host sections
     std::map<std::string, Prof> prof;
     std::vector<Pending> pending;
@@ -195,7 +196,7 @@ struct Stage {
     Stage(ah_ctx *c_, const char *n, cudaStream_t s, int l) : c(c_), name(n), st(s), launches(l)
     {
         c->launches_total += (uint64_t)l;
-        if (c->profiling) {
+        if (c->profiling && (!c->prof_streaming_only || !strcmp(n, "pack") || !strcmp(n, "scan"))) {
             a = get_event(c);
             cudaEventRecord(a, st);
         }
@@ -944,8 +945,9 @@ ah_status ah_set_profiling(ah_ctx *c, int enable)
         prof_flush(c);
         c->prof.clear();
         c->launches_total = 0;
-        c->profiling = enable == 1;
-        c->host_timing = enable == 1 || enable == 2;
+        c->profiling = enable == 1 || enable == 3;
+        c->prof_streaming_only = enable == 3;
+        c->host_timing = enable >= 1 && enable <= 3;
     });
 }
 
