@@ -443,6 +443,13 @@ PairDev make_pair_dev(const PrimerPair &pp)
     d.min_len = pp.params.min_len;
     d.max_len = pp.params.max_len;
     memcpy(d.mask, pp.mask, sizeof(d.mask));
+    for (int x = 0; x < 2; ++x) { // Tm shortest-path keys: both ends and every degenerate position
+        int nk = 0;
+        for (int q = 0; q < pp.L[x]; ++q)
+            if (q == 0 || q == pp.L[x] - 1 || __builtin_popcount(pp.mask[x][q]) > 1)
+                d.key[x][nk++] = (uint8_t)q;
+        d.nkey[x] = nk;
+    }
     d.tm_min = pp.params.tm_min;
     d.tm_min_f = (float)pp.params.tm_min;
     const double x = (pp.params.dnac1_nM - pp.params.dnac2_nM / 2.0) * 1e-9;
@@ -493,6 +500,15 @@ const PairDev *upload_pairs(ah_ctx *c, const uint32_t *pair_ids, uint32_t n_pair
     c->pairdev_version = c->pairs_version;
     c->pairdev_d = d;
     return d;
+}
+
+// Largest Tm segment count (keys - 1) over the primers of the last upload.
+int tm_seg_max(const ah_ctx *c)
+{
+    int m = 1;
+    for (const PairDev &d : c->pairdev_h)
+        m = std::max(m, std::max(d.nkey[0], d.nkey[1]) - 1);
+    return m;
 }
 
 int bit_length(uint64_t v)
@@ -699,7 +715,7 @@ FastResult run_fast(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPatter
     {
         Stage sg(c, "tm", st, 2);
         launch_tm(sites, ns_max, F + kFlagSites, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, pass, queue,
-                  (uint32_t *)(F + kFlagTmQueue), c->d_err, st);
+                  (uint32_t *)(F + kFlagTmQueue), tm_seg_max(c), c->d_err, st);
     }
     {
         Stage sg(c, "pair", st, 3);
@@ -765,7 +781,7 @@ void run_steps(ah_ctx *c, const GenomeSet &gs, const PairDev *pd, uint32_t n_pai
             Stage sg(c, "tm", st, 2);
             uint32_t *q = (uint32_t *)scratch(c, "tm_queue", ns * sizeof(uint32_t));
             launch_tm(sites, ns, nullptr, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, pass, q,
-                      (uint32_t *)(c->d_flags + kFlagTmQueue), c->d_err, st);
+                      (uint32_t *)(c->d_flags + kFlagTmQueue), tm_seg_max(c), c->d_err, st);
         }
         const uint8_t *filt = o->tm_filter ? pass : nullptr;
         uint64_t *counts = (uint64_t *)scratch(c, "pair_counts", ns * sizeof(uint64_t));
@@ -1361,7 +1377,7 @@ ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n
             Stage sg(c, "tm", st, 2);
             uint32_t *q = (uint32_t *)scratch(c, "tm_queue", n * sizeof(uint32_t));
             launch_tm(s, n, nullptr, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, ps, q,
-                      (uint32_t *)(c->d_flags + kFlagTmQueue),
+                      (uint32_t *)(c->d_flags + kFlagTmQueue), tm_seg_max(c),
                       c->d_err, st);
         }
         out_finish(tm_out, tm, n, st);

@@ -90,11 +90,16 @@ __device__ __forceinline__ void classify4(uint32_t raw, uint32_t pw, uint32_t si
     V = v4 * pw + V;
 }
 
-// Build plane words for columns 4*ci .. 4*ci+3 from rows r0 .. r0+31 of the
-// staged tile and store them as words j0 .. j0+3 of the tile's planes.
-__device__ __forceinline__ void pack_columns(const uint32_t *__restrict__ rows, int r0, int ci,
-                                             uint32_t *__restrict__ dst, int j0, uint32_t one)
+// Build plane words for columns 4*ci .. 4*ci+3 from rows 0 .. 31 of the
+// staged tile and store them as words 4*ci .. 4*ci+3 of the tile's planes.
+// Threads of columns below kTileExt also store the extension words W + 4*ci
+// .. W + 4*ci + 3: bit b of extension word W + j is the base at row b + 1,
+// column j, i.e. the column's own word shifted right by one with bit 31 from
+// row 32 (the next tile's first row, staged with the tile).
+__device__ __forceinline__ void pack_columns(const uint32_t *__restrict__ rows, int ci, uint32_t *__restrict__ dst,
+                                             uint32_t one)
 {
+    const int r0 = 0, j0 = 4 * ci;
     const uint32_t sixteen = one << 4, top4 = one << 28;
     uint32_t L[4] = {0, 0, 0, 0}, H[4] = {0, 0, 0, 0}, V[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -127,6 +132,25 @@ __device__ __forceinline__ void pack_columns(const uint32_t *__restrict__ rows, 
     *reinterpret_cast<uint4 *>(dst + 1 * kTileWX + j0) = pc;
     *reinterpret_cast<uint4 *>(dst + 2 * kTileWX + j0) = pg;
     *reinterpret_cast<uint4 *>(dst + 3 * kTileWX + j0) = pt;
+    if (j0 < kTileExt) {
+        // row 32 of these four columns: bit k of hl / hh / hv = byte k's letter bits and validity
+        uint32_t hl = 0, hh = 0, hv = 0;
+        classify4(rows[32 * kRowWords + ci], one, one << 4, one << 28, hl, hh, hv);
+        const uint32_t ha = hv & ~hh & ~hl, hc = hv & ~hh & hl, ht = hv & hh & ~hl, hg = hv & hh & hl;
+        uint4 ea, ec, eg, et;
+        uint32_t *EA = &ea.x, *EC = &ec.x, *EG = &eg.x, *ET = &et.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            EA[k] = (A[k] >> 1) | ((ha >> k & 1u) << 31);
+            EC[k] = (C[k] >> 1) | ((hc >> k & 1u) << 31);
+            EG[k] = (G[k] >> 1) | ((hg >> k & 1u) << 31);
+            ET[k] = (T[k] >> 1) | ((ht >> k & 1u) << 31);
+        }
+        *reinterpret_cast<uint4 *>(dst + 0 * kTileWX + kTileW + j0) = ea;
+        *reinterpret_cast<uint4 *>(dst + 1 * kTileWX + kTileW + j0) = ec;
+        *reinterpret_cast<uint4 *>(dst + 2 * kTileWX + kTileW + j0) = eg;
+        *reinterpret_cast<uint4 *>(dst + 3 * kTileWX + kTileW + j0) = et;
+    }
 }
 
 __global__ void __launch_bounds__(kPackThreads) pack_kernel(const uint8_t *__restrict__ seq, uint64_t seq_base,
@@ -200,10 +224,7 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const uint8_t *__res
             }
             __syncthreads();
         }
-        uint32_t *dst = planes + t * 4 * kTileWX;
-        pack_columns(rows, 0, threadIdx.x, dst, 4 * threadIdx.x, one);
-        if (threadIdx.x < kTileExt / 4) // extension words W .. W+31: rows 1 .. 32, columns 0 .. 31
-            pack_columns(rows, 1, threadIdx.x, dst, kTileW + 4 * threadIdx.x, one);
+        pack_columns(rows, threadIdx.x, planes + t * 4 * kTileWX, one);
         __syncthreads(); // this buffer is refilled two tiles from now
     }
 }

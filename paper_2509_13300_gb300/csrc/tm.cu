@@ -8,7 +8,9 @@
 // without enumeration: dH and dS are sums over adjacent primer positions, so
 // for a trial value lam the minimum over oligos of F(o) = 1000 dH(o) -
 // lam (dS(o) + C) is a 4-state shortest path along the primer (the state is
-// the oligo's base at a position, restricted to its IUPAC set), and
+// the oligo's base at a position, restricted to its IUPAC set; only the
+// degenerate positions and the two ends need a step, the fixed stretches
+// between them being folded into per-site 4x4 tables), and
 // Dinkelbach's iteration lam <- ratio(argmin F) climbs to the maximum ratio in
 // a few rounds, provided dS(o) + C < 0 for every oligo (checked first with a
 // max-path pass).  Four lanes per site (one DP state each), fp32.
@@ -80,10 +82,10 @@ __device__ double exact_tm(const PairDev &pd, const int8_t *bt, int L, uint64_t 
 }
 
 // Four lanes per site: lane y of a group holds the DP state "oligo base at
-// the current position = y".  Each step takes the four predecessor costs by
-// shuffles and keeps the best predecessor (2 bits per position), so the
-// argmin oligo is recovered by a backtrack across the group's lanes; its dH,
-// dS are then summed by the four lanes together.  Eight sites per warp.
+// the current key position = y".  Each step takes the four predecessor costs
+// by shuffles and keeps the best predecessor (2 bits per key), so the argmin
+// oligo is recovered by a backtrack across the group's lanes; its dH, dS are
+// then summed by the four lanes together.  Eight sites per warp.
 __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__restrict__ sites, uint64_t n_arg,
                                                            const uint64_t *__restrict__ n_dev,
                                                            const PairDev *__restrict__ pairs, int n_pairs,
@@ -91,9 +93,10 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                                                            const uint64_t *__restrict__ contig_off,
                                                            float *__restrict__ tm_out, uint8_t *__restrict__ pass_out,
                                                            uint32_t *__restrict__ queue, uint32_t *__restrict__ queue_n,
-                                                           int *__restrict__ err)
+                                                           int seg_max, int *__restrict__ err)
 {
     __shared__ int8_t bts[kTmWarps][8][AH_MAX_PRIMER_LEN];
+    extern __shared__ float2 seg_smem[]; // [kTmWarps * 8 sites][seg_max][16]: segment tables
     const uint64_t n = dev_count(n_arg, n_dev);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, y = lane & 3, g0 = lane & ~3;
@@ -133,45 +136,88 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
         const bool run = act && !bad;
         const float cst =
             act ? (float)(pd.sconst + (pd.saltcorr == 5 ? 0.368 * (double)(L - 1) * pd.log_na : 0.0)) : -1.f;
-        // Shuffles need all 32 lanes, but the groups' primer lengths differ: every
-        // position loop runs to the warp's longest primer Lw and each group only
-        // reads tables and updates its state while q < L (bt[q] is written for q < L).
+        // The fp64 sign test below steps over every position; its shuffles need all
+        // 32 lanes, so its loop runs to the warp's longest primer Lw and each group
+        // only reads tables and updates its state while q < L (bt[q] is written for q < L).
         int Lw = L;
         for (int d = 16; d >= 1; d >>= 1)
             Lw = max(Lw, __shfl_xor_sync(0xffffffffu, Lw, d));
+        // Steps at key positions only (primer positions 0 and L-1 and every
+        // degenerate one): between two keys the oligo bases are fixed, so all
+        // stacks from key i to key i+1 form a 4x4 table of (dH, dS) sums
+        // indexed by the bases at the two keys, E[i][a * 4 + b].  Lane y fills
+        // column y of the site's tables once; every pass below reads them.
+        const int m = act ? pd.nkey[s.primer] - 1 : 0; // segments
+        const uint8_t *key = pd.key[act ? s.primer : 0];
+        float2 *E = seg_smem + (size_t)(warp * 8 + g) * seg_max * 16;
+        if (run) {
+            for (int si = 0; si < m; ++si) {
+                const int k0 = key[si], k1 = key[si + 1];
+                if (k1 == k0 + 1) {
+                    for (int x = 0; x < 4; ++x) {
+                        const int idx = ((x * 4 + y) * 4 + bt[k0]) * 4 + bt[k1];
+                        E[si * 16 + x * 4 + y] = make_float2(pd.stack_dH[idx], pd.stack_dS[idx]);
+                    }
+                } else {
+                    float cH = 0.f, cS = 0.f; // stacks between two fixed bases
+                    for (int q = k0 + 2; q < k1; ++q) {
+                        const int a0 = __ffs(mask[q - 1]) - 1, b0 = __ffs(mask[q]) - 1;
+                        const int idx = ((a0 * 4 + b0) * 4 + bt[q - 1]) * 4 + bt[q];
+                        cH += pd.stack_dH[idx];
+                        cS += pd.stack_dS[idx];
+                    }
+                    const int fa = __ffs(mask[k0 + 1]) - 1, fb = __ffs(mask[k1 - 1]) - 1;
+                    const int iq = ((fb * 4 + y) * 4 + bt[k1 - 1]) * 4 + bt[k1]; // into key k1, base y
+                    const float qH = pd.stack_dH[iq] + cH, qS = pd.stack_dS[iq] + cS;
+                    for (int x = 0; x < 4; ++x) {
+                        const int ip = ((x * 4 + fa) * 4 + bt[k0]) * 4 + bt[k0 + 1]; // out of key k0, base x
+                        E[si * 16 + x * 4 + y] = make_float2(pd.stack_dH[ip] + qH, pd.stack_dS[ip] + qS);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        // Shuffles need all 32 lanes, but the groups' segment counts differ: every
+        // segment loop runs to the warp's largest count mw and each group only
+        // updates its state while si < m.
+        int mw = run ? m : 0;
+        for (int d = 16; d >= 1; d >>= 1)
+            mw = max(mw, __shfl_xor_sync(0xffffffffu, mw, d));
         // largest denominator over oligos (max-path of dS)
         float sm = (run && (mask[0] >> y & 1)) ? pd.term_dS[y * 4 + bt[0]] : -INF;
-        for (int q = 1; q < Lw; ++q) {
-            const bool in = q < L;
+        for (int si = 0; si < mw; ++si) {
+            const bool in = run && si < m;
             float best = -INF;
+#pragma unroll
             for (int x = 0; x < 4; ++x) {
                 const float cx = __shfl_sync(0xffffffffu, sm, g0 + x);
                 if (in) {
-                    const float v = cx + pd.stack_dS[((x * 4 + y) * 4 + bt[q - 1]) * 4 + bt[q]];
+                    const float v = cx + E[si * 16 + x * 4 + y].y;
                     best = v > best ? v : best;
                 }
             }
             if (in)
-                sm = (mask[q] >> y & 1) ? best : -INF;
+                sm = (mask[key[si + 1]] >> y & 1) ? best : -INF;
         }
-        float dm = sm + ((mask[L - 1] >> y & 1) ? pd.term_dS[y * 4 + bt[L - 1]] : 0.f);
+        float dm = sm + ((run && (mask[L - 1] >> y & 1)) ? pd.term_dS[y * 4 + bt[L - 1]] : 0.f);
         dm = group_reduce(dm, [](float a, float b) { return a > b ? a : b; });
         const bool dink = run && dm + cst < 0.f;
         float lam = 0.f;
         for (int it = 0; it < 64; ++it) {
-            // min over oligos of 1000 dH - lam dS, with the best predecessor of every position
+            // min over oligos of 1000 dH - lam dS, with the best predecessor at every key
             float c = (dink && (mask[0] >> y & 1)) ? 1000.f * pd.term_dH[y * 4 + bt[0]] - lam * pd.term_dS[y * 4 + bt[0]]
                                                     : INF;
             uint64_t pred = 0;
-            for (int q = 1; q < Lw; ++q) {
-                const bool in = q < L;
+            for (int si = 0; si < mw; ++si) {
+                const bool in = dink && si < m;
                 float best = INF;
                 int arg = 0;
+#pragma unroll
                 for (int x = 0; x < 4; ++x) {
                     const float cx = __shfl_sync(0xffffffffu, c, g0 + x);
                     if (in) {
-                        const int idx = ((x * 4 + y) * 4 + bt[q - 1]) * 4 + bt[q];
-                        const float v = cx + 1000.f * pd.stack_dH[idx] - lam * pd.stack_dS[idx];
+                        const float2 e = E[si * 16 + x * 4 + y];
+                        const float v = cx + fmaf(-lam, e.y, 1000.f * e.x);
                         if (v < best) {
                             best = v;
                             arg = x;
@@ -179,37 +225,38 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                     }
                 }
                 if (in) {
-                    c = (mask[q] >> y & 1) ? best : INF;
-                    pred |= (uint64_t)arg << (2 * q);
+                    c = (mask[key[si + 1]] >> y & 1) ? best : INF;
+                    pred |= (uint64_t)arg << (2 * si);
                 }
             }
-            float fin = c + 1000.f * pd.term_dH[y * 4 + bt[L - 1]] - lam * pd.term_dS[y * 4 + bt[L - 1]];
+            float fin = dink ? c + 1000.f * pd.term_dH[y * 4 + bt[L - 1]] - lam * pd.term_dS[y * 4 + bt[L - 1]] : INF;
             if (!(c < INF))
                 fin = INF;
             // argmin over the group's four end states (ties: lowest base)
             const float fmin = group_reduce(fin, [](float a, float b) { return a < b ? a : b; });
             const unsigned hit = __ballot_sync(0xffffffffu, fin == fmin) >> g0 & 0xFu;
             int cur = hit ? __ffs(hit) - 1 : 0;
-            // backtrack the oligo: o[L-1] = cur, o[q-1] = predecessor kept by lane o[q] at q
-            uint64_t olig = (uint64_t)cur << (2 * (L - 1));
-            for (int q = Lw - 1; q >= 1; --q) {
+            // backtrack the bases at the keys: ks[i] = base at key i (2 bits each)
+            uint64_t ks = (uint64_t)cur << (2 * m);
+            for (int si = mw - 1; si >= 0; --si) {
                 const uint64_t pp = __shfl_sync(0xffffffffu, pred, g0 + cur);
-                if (q < L) {
-                    cur = (int)(pp >> (2 * q) & 3u);
-                    olig |= (uint64_t)cur << (2 * (q - 1));
+                if (si < m) {
+                    cur = (int)(pp >> (2 * si) & 3u);
+                    ks |= (uint64_t)cur << (2 * si);
                 }
             }
-            // its dH and dS, split over the four lanes
+            // its dH and dS: the segment tables, split over the four lanes
             float H = 0.f, S = 0.f;
-            for (int q = 1 + y; q < L; q += 4) {
-                const int a = (int)(olig >> (2 * (q - 1)) & 3u), b2 = (int)(olig >> (2 * q) & 3u);
-                const int idx = ((a * 4 + b2) * 4 + bt[q - 1]) * 4 + bt[q];
-                H += pd.stack_dH[idx];
-                S += pd.stack_dS[idx];
-            }
+            if (dink)
+                for (int si = y; si < m; si += 4) {
+                    const int a0 = (int)(ks >> (2 * si) & 3u), b0 = (int)(ks >> (2 * (si + 1)) & 3u);
+                    const float2 e = E[si * 16 + a0 * 4 + b0];
+                    H += e.x;
+                    S += e.y;
+                }
             H = group_reduce(H, [](float a, float b) { return a + b; });
             S = group_reduce(S, [](float a, float b) { return a + b; });
-            const int o0 = (int)(olig & 3u), oL = (int)(olig >> (2 * (L - 1)) & 3u);
+            const int o0 = (int)(ks & 3u), oL = (int)(ks >> (2 * m) & 3u);
             H += pd.term_dH[o0 * 4 + bt[0]] + pd.term_dH[oL * 4 + bt[L - 1]];
             S += pd.term_dS[o0 * 4 + bt[0]] + pd.term_dS[oL * 4 + bt[L - 1]];
             const float r = 1000.f * H / (S + cst);
@@ -382,27 +429,32 @@ __global__ void __launch_bounds__(kExactThreads) tm_exact_kernel(const ah_site *
 
 } // namespace
 
-void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const PairDev *pairs_d, int n_pairs, const uint32_t *planes,
-               const uint64_t *contig_off, float *tm_out, uint8_t *pass_out, uint32_t *queue, uint32_t *queue_n,
-               int *err, cudaStream_t s)
+void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const PairDev *pairs_d, int n_pairs,
+               const uint32_t *planes, const uint64_t *contig_off, float *tm_out, uint8_t *pass_out, uint32_t *queue,
+               uint32_t *queue_n, int seg_max, int *err, cudaStream_t s)
 {
     if (!n)
         return;
-    AH_CUDA(cudaMemsetAsync(queue_n, 0, sizeof(uint32_t), s));
-    const uint64_t per_block = 8ull * kTmWarps; // sites per block per pass
-    uint64_t blocks = (n + per_block - 1) / per_block;
-    if (blocks > 65535)
-        blocks = 65535;
-    tm_kernel<<<(unsigned)blocks, 32 * kTmWarps, 0, s>>>(sites, n, n_dev, pairs_d, n_pairs, planes, contig_off, tm_out,
-                                                         pass_out, queue, queue_n, err);
-    AH_CUDA(cudaGetLastError());
+    if (seg_max < 1 || seg_max > AH_MAX_PRIMER_LEN - 1)
+        throw Error(AH_ERR_ARG, "Tm: segment count outside 1..31");
     static int cached_dev = -1, sms = 148;
     int dev = 0;
     AH_CUDA(cudaGetDevice(&dev));
     if (dev != cached_dev) {
         AH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int most = kTmWarps * 8 * (AH_MAX_PRIMER_LEN - 1) * 16 * (int)sizeof(float2);
+        AH_CUDA(cudaFuncSetAttribute(tm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most));
         cached_dev = dev;
     }
+    AH_CUDA(cudaMemsetAsync(queue_n, 0, sizeof(uint32_t), s));
+    const uint64_t per_block = 8ull * kTmWarps; // sites per block per pass
+    uint64_t blocks = (n + per_block - 1) / per_block;
+    if (blocks > 65535)
+        blocks = 65535;
+    const size_t smem = (size_t)kTmWarps * 8 * seg_max * 16 * sizeof(float2);
+    tm_kernel<<<(unsigned)blocks, 32 * kTmWarps, smem, s>>>(sites, n, n_dev, pairs_d, n_pairs, planes, contig_off,
+                                                            tm_out, pass_out, queue, queue_n, seg_max, err);
+    AH_CUDA(cudaGetLastError());
     tm_exact_kernel<<<(unsigned)sms, kExactThreads, 0, s>>>(sites, pairs_d, planes, contig_off, queue, queue_n,
                                                               tm_out, pass_out);
     AH_CUDA(cudaGetLastError());
