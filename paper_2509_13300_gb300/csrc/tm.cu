@@ -81,6 +81,17 @@ __device__ double exact_tm(const PairDev &pd, const int8_t *bt, int L, uint64_t 
     return tm;
 }
 
+// Per-pair constants of the fp32 path, staged in shared memory by every
+// block (the shortest-path steps read them in dependent chains).
+struct TmPairS {
+    float2 st[256]; // (dH, dS) of each stack
+    float2 tm[16];  // (dH, dS) of each terminal pair
+    uint8_t mask[2][AH_MAX_PRIMER_LEN];
+    uint8_t key[2][AH_MAX_PRIMER_LEN];
+    int L[2], nkey[2];
+};
+static_assert(sizeof(TmPairS) % 16 == 0, "TmPairS keeps 16-byte alignment");
+
 // Four lanes per site: lane y of a group holds the DP state "oligo base at
 // the current key position = y".  Each step takes the four predecessor costs
 // by shuffles and keeps the best predecessor (2 bits per key), so the argmin
@@ -96,7 +107,26 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                                                            int seg_max, int *__restrict__ err)
 {
     __shared__ int8_t bts[kTmWarps][8][AH_MAX_PRIMER_LEN];
-    extern __shared__ float2 seg_smem[]; // [kTmWarps * 8 sites][seg_max][16]: segment tables
+    // dynamic: [n_pairs] TmPairS, then [kTmWarps * 8 sites][seg_max][16] segment tables
+    extern __shared__ __align__(16) unsigned char tm_smem[];
+    TmPairS *ps = reinterpret_cast<TmPairS *>(tm_smem);
+    float2 *seg_smem = reinterpret_cast<float2 *>(tm_smem + (size_t)n_pairs * sizeof(TmPairS));
+    for (int j = 0; j < n_pairs; ++j) {
+        const PairDev &P = pairs[j];
+        for (int t = threadIdx.x; t < 256; t += blockDim.x)
+            ps[j].st[t] = make_float2(P.stack_dH[t], P.stack_dS[t]);
+        if (threadIdx.x < 16)
+            ps[j].tm[threadIdx.x] = make_float2(P.term_dH[threadIdx.x], P.term_dS[threadIdx.x]);
+        if (threadIdx.x < 2 * AH_MAX_PRIMER_LEN) {
+            (&ps[j].mask[0][0])[threadIdx.x] = (&P.mask[0][0])[threadIdx.x];
+            (&ps[j].key[0][0])[threadIdx.x] = (&P.key[0][0])[threadIdx.x];
+        }
+        if (threadIdx.x < 2) {
+            ps[j].L[threadIdx.x] = P.L[threadIdx.x];
+            ps[j].nkey[threadIdx.x] = P.nkey[threadIdx.x];
+        }
+    }
+    __syncthreads();
     const uint64_t n = dev_count(n_arg, n_dev);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, y = lane & 3, g0 = lane & ~3;
@@ -114,17 +144,40 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
             atomicExch(err, kDevBounds);
         const bool act = live && !bad_rec;
         const PairDev &pd = pairs[act ? s.pair : 0];
-        const int L = act ? pd.L[s.primer] : 2;
-        const uint8_t *mask = pd.mask[act ? s.primer : 0];
+        const TmPairS &sp = ps[act ? s.pair : 0];
+        const int L = act ? sp.L[s.primer] : 2;
+        const uint8_t *mask = sp.mask[act ? s.primer : 0];
         // template base opposite each primer position; every entry the DP reads
-        // is written (0..3), also for groups without a live site
+        // is written (0..3), also for groups without a live site.  All of a lane's
+        // plane words are requested before any is used (one memory latency).
         bool bad = false;
         if (act) {
             const uint64_t P = contig_off[s.contig] + s.pos;
-            for (int q = y; q < L; q += 4) {
-                const int c = base_at(planes, P + (s.strand == 0 ? q : L - 1 - q));
-                bad |= c < 0;
-                bt[q] = (int8_t)(c < 0 ? 0 : (s.strand == 0 ? 3 - c : c));
+            uint32_t w[8][4];
+            int bitpos[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int q = min(y + 4 * j, L - 1); // past the primer: a repeat of its last position, unused
+                const uint64_t Pq = P + (s.strand == 0 ? q : L - 1 - q);
+                const uint64_t t = Pq / kTileBases, r = Pq % kTileBases;
+                bitpos[j] = (int)(r / kTileW);
+                const uint32_t *wp = planes + t * 4 * kTileWX + (r % kTileW);
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+                    w[j][x] = __ldg(wp + x * kTileWX);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int q = y + 4 * j;
+                if (q < L) {
+                    int c = -1;
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+                        if ((w[j][x] >> bitpos[j]) & 1u)
+                            c = x;
+                    bad |= c < 0;
+                    bt[q] = (int8_t)(c < 0 ? 0 : (s.strand == 0 ? 3 - c : c));
+                }
             }
         } else {
             for (int q = y; q < L; q += 4)
@@ -147,36 +200,44 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
         // stacks from key i to key i+1 form a 4x4 table of (dH, dS) sums
         // indexed by the bases at the two keys, E[i][a * 4 + b].  Lane y fills
         // column y of the site's tables once; every pass below reads them.
-        const int m = act ? pd.nkey[s.primer] - 1 : 0; // segments
-        const uint8_t *key = pd.key[act ? s.primer : 0];
+        const int m = act ? sp.nkey[s.primer] - 1 : 0; // segments
+        const uint8_t *key = sp.key[act ? s.primer : 0];
         float2 *E = seg_smem + (size_t)(warp * 8 + g) * seg_max * 16;
         if (run) {
             for (int si = 0; si < m; ++si) {
                 const int k0 = key[si], k1 = key[si + 1];
                 if (k1 == k0 + 1) {
                     for (int x = 0; x < 4; ++x) {
-                        const int idx = ((x * 4 + y) * 4 + bt[k0]) * 4 + bt[k1];
-                        E[si * 16 + x * 4 + y] = make_float2(pd.stack_dH[idx], pd.stack_dS[idx]);
+                        E[si * 16 + x * 4 + y] = sp.st[((x * 4 + y) * 4 + bt[k0]) * 4 + bt[k1]];
                     }
                 } else {
                     float cH = 0.f, cS = 0.f; // stacks between two fixed bases
                     for (int q = k0 + 2; q < k1; ++q) {
                         const int a0 = __ffs(mask[q - 1]) - 1, b0 = __ffs(mask[q]) - 1;
-                        const int idx = ((a0 * 4 + b0) * 4 + bt[q - 1]) * 4 + bt[q];
-                        cH += pd.stack_dH[idx];
-                        cS += pd.stack_dS[idx];
+                        const float2 e = sp.st[((a0 * 4 + b0) * 4 + bt[q - 1]) * 4 + bt[q]];
+                        cH += e.x;
+                        cS += e.y;
                     }
                     const int fa = __ffs(mask[k0 + 1]) - 1, fb = __ffs(mask[k1 - 1]) - 1;
-                    const int iq = ((fb * 4 + y) * 4 + bt[k1 - 1]) * 4 + bt[k1]; // into key k1, base y
-                    const float qH = pd.stack_dH[iq] + cH, qS = pd.stack_dS[iq] + cS;
+                    const float2 eq = sp.st[((fb * 4 + y) * 4 + bt[k1 - 1]) * 4 + bt[k1]]; // into key k1, base y
+                    const float qH = eq.x + cH, qS = eq.y + cS;
                     for (int x = 0; x < 4; ++x) {
-                        const int ip = ((x * 4 + fa) * 4 + bt[k0]) * 4 + bt[k0 + 1]; // out of key k0, base x
-                        E[si * 16 + x * 4 + y] = make_float2(pd.stack_dH[ip] + qH, pd.stack_dS[ip] + qS);
+                        const float2 ep = sp.st[((x * 4 + fa) * 4 + bt[k0]) * 4 + bt[k0 + 1]]; // out of key k0, base x
+                        E[si * 16 + x * 4 + y] = make_float2(ep.x + qH, ep.y + qS);
                     }
                 }
             }
         }
         __syncwarp();
+        // bit i: base y is allowed at key i; this lane's terminal terms at both ends
+        uint32_t amask = 0;
+        float2 t0 = make_float2(0.f, 0.f), tL = make_float2(0.f, 0.f);
+        if (run) {
+            for (int si = 0; si <= m; ++si)
+                amask |= (uint32_t)(mask[key[si]] >> y & 1) << si;
+            t0 = sp.tm[y * 4 + bt[0]];
+            tL = sp.tm[y * 4 + bt[L - 1]];
+        }
         // Shuffles need all 32 lanes, but the groups' segment counts differ: every
         // segment loop runs to the warp's largest count mw and each group only
         // updates its state while si < m.
@@ -184,7 +245,7 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
         for (int d = 16; d >= 1; d >>= 1)
             mw = max(mw, __shfl_xor_sync(0xffffffffu, mw, d));
         // largest denominator over oligos (max-path of dS)
-        float sm = (run && (mask[0] >> y & 1)) ? pd.term_dS[y * 4 + bt[0]] : -INF;
+        float sm = (amask & 1u) ? t0.y : -INF;
         for (int si = 0; si < mw; ++si) {
             const bool in = run && si < m;
             float best = -INF;
@@ -197,16 +258,15 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                 }
             }
             if (in)
-                sm = (mask[key[si + 1]] >> y & 1) ? best : -INF;
+                sm = (amask >> (si + 1) & 1u) ? best : -INF;
         }
-        float dm = sm + ((run && (mask[L - 1] >> y & 1)) ? pd.term_dS[y * 4 + bt[L - 1]] : 0.f);
+        float dm = sm + ((amask >> m & 1u) ? tL.y : 0.f);
         dm = group_reduce(dm, [](float a, float b) { return a > b ? a : b; });
         const bool dink = run && dm + cst < 0.f;
         float lam = 0.f;
         for (int it = 0; it < 64; ++it) {
             // min over oligos of 1000 dH - lam dS, with the best predecessor at every key
-            float c = (dink && (mask[0] >> y & 1)) ? 1000.f * pd.term_dH[y * 4 + bt[0]] - lam * pd.term_dS[y * 4 + bt[0]]
-                                                    : INF;
+            float c = (dink && (amask & 1u)) ? 1000.f * t0.x - lam * t0.y : INF;
             uint64_t pred = 0;
             for (int si = 0; si < mw; ++si) {
                 const bool in = dink && si < m;
@@ -225,11 +285,11 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                     }
                 }
                 if (in) {
-                    c = (mask[key[si + 1]] >> y & 1) ? best : INF;
+                    c = (amask >> (si + 1) & 1u) ? best : INF;
                     pred |= (uint64_t)arg << (2 * si);
                 }
             }
-            float fin = dink ? c + 1000.f * pd.term_dH[y * 4 + bt[L - 1]] - lam * pd.term_dS[y * 4 + bt[L - 1]] : INF;
+            float fin = dink ? c + 1000.f * tL.x - lam * tL.y : INF;
             if (!(c < INF))
                 fin = INF;
             // argmin over the group's four end states (ties: lowest base)
@@ -256,9 +316,10 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                 }
             H = group_reduce(H, [](float a, float b) { return a + b; });
             S = group_reduce(S, [](float a, float b) { return a + b; });
+            // terminal terms of the chosen end bases: held by the lanes of those bases
             const int o0 = (int)(ks & 3u), oL = (int)(ks >> (2 * m) & 3u);
-            H += pd.term_dH[o0 * 4 + bt[0]] + pd.term_dH[oL * 4 + bt[L - 1]];
-            S += pd.term_dS[o0 * 4 + bt[0]] + pd.term_dS[oL * 4 + bt[L - 1]];
+            H += __shfl_sync(0xffffffffu, t0.x, g0 + o0) + __shfl_sync(0xffffffffu, tL.x, g0 + oL);
+            S += __shfl_sync(0xffffffffu, t0.y, g0 + o0) + __shfl_sync(0xffffffffu, tL.y, g0 + oL);
             const float r = 1000.f * H / (S + cst);
             // Warp-uniform loop: stop when no group still improves by more than
             // 1e-4 K.  In fp32 two oligos of nearly equal ratio could otherwise
@@ -336,10 +397,10 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
     }
 }
 
-// Queued sites, one block (1024 lanes) per site: every oligo in fp64 with the
+// Queued sites, one block per site: every oligo in fp64 with the
 // definition's operation order (exact_tm), block-wide maximum, then the Tm
 // and the pass flag.  The queue length is read on the device.
-constexpr int kExactThreads = 1024; // a site's oligos (at most 10000) in about one pass
+constexpr int kExactThreads = 128; // fp64-bound: a block of 128 already keeps the SM's fp64 units busy
 
 __global__ void __launch_bounds__(kExactThreads) tm_exact_kernel(const ah_site *__restrict__ sites,
                                                                  const PairDev *__restrict__ pairs,
@@ -442,7 +503,8 @@ void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const Pa
     AH_CUDA(cudaGetDevice(&dev));
     if (dev != cached_dev) {
         AH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const int most = kTmWarps * 8 * (AH_MAX_PRIMER_LEN - 1) * 16 * (int)sizeof(float2);
+        const int most = AH_MAX_PAIRS_PER_SCAN * (int)sizeof(TmPairS) +
+                         kTmWarps * 8 * (AH_MAX_PRIMER_LEN - 1) * 16 * (int)sizeof(float2);
         AH_CUDA(cudaFuncSetAttribute(tm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most));
         cached_dev = dev;
     }
@@ -451,7 +513,7 @@ void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const Pa
     uint64_t blocks = (n + per_block - 1) / per_block;
     if (blocks > 65535)
         blocks = 65535;
-    const size_t smem = (size_t)kTmWarps * 8 * seg_max * 16 * sizeof(float2);
+    const size_t smem = (size_t)n_pairs * sizeof(TmPairS) + (size_t)kTmWarps * 8 * seg_max * 16 * sizeof(float2);
     tm_kernel<<<(unsigned)blocks, 32 * kTmWarps, smem, s>>>(sites, n, n_dev, pairs_d, n_pairs, planes, contig_off,
                                                             tm_out, pass_out, queue, queue_n, seg_max, err);
     AH_CUDA(cudaGetLastError());
