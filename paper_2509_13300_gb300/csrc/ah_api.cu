@@ -477,6 +477,19 @@ PairDev make_pair_dev(const PrimerPair &pp)
         d.term_dH_d[i] = pp.table.term_dH[i];
         d.term_dS_d[i] = pp.table.term_dS[i];
     }
+    // largest possible dS + C of a duplex of each primer, from the table's largest entries
+    double max_st = -INFINITY, max_tm = -INFINITY;
+    for (int i = 0; i < 256; ++i)
+        max_st = std::max(max_st, pp.table.stack_dS[i]);
+    for (int i = 0; i < 16; ++i)
+        max_tm = std::max(max_tm, pp.table.term_dS[i]);
+    d.few_exact = 1;
+    for (int x = 0; x < 2; ++x) {
+        const int L = pp.L[x];
+        const double salt = d.saltcorr == 5 ? 0.368 * (double)(L - 1) * d.log_na : 0.0;
+        if (!((L - 1) * max_st + 2 * max_tm + d.sconst + salt < -1e-3))
+            d.few_exact = 0;
+    }
     return d;
 }
 
@@ -500,6 +513,15 @@ const PairDev *upload_pairs(ah_ctx *c, const uint32_t *pair_ids, uint32_t n_pair
     c->pairdev_version = c->pairs_version;
     c->pairdev_d = d;
     return d;
+}
+
+// All pairs of the last upload have few_exact set.
+bool tm_few_exact(const ah_ctx *c)
+{
+    for (const PairDev &d : c->pairdev_h)
+        if (!d.few_exact)
+            return false;
+    return true;
 }
 
 // Largest Tm segment count (keys - 1) over the primers of the last upload.
@@ -715,7 +737,7 @@ FastResult run_fast(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPatter
     {
         Stage sg(c, "tm", st, 2);
         launch_tm(sites, ns_max, F + kFlagSites, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, pass, queue,
-                  (uint32_t *)(F + kFlagTmQueue), tm_seg_max(c), c->d_err, st);
+                  (uint32_t *)(F + kFlagTmQueue), tm_seg_max(c), tm_few_exact(c), c->d_err, st);
     }
     {
         Stage sg(c, "pair", st, 3);
@@ -781,7 +803,7 @@ void run_steps(ah_ctx *c, const GenomeSet &gs, const PairDev *pd, uint32_t n_pai
             Stage sg(c, "tm", st, 2);
             uint32_t *q = (uint32_t *)scratch(c, "tm_queue", ns * sizeof(uint32_t));
             launch_tm(sites, ns, nullptr, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, pass, q,
-                      (uint32_t *)(c->d_flags + kFlagTmQueue), tm_seg_max(c), c->d_err, st);
+                      (uint32_t *)(c->d_flags + kFlagTmQueue), tm_seg_max(c), tm_few_exact(c), c->d_err, st);
         }
         const uint8_t *filt = o->tm_filter ? pass : nullptr;
         uint64_t *counts = (uint64_t *)scratch(c, "pair_counts", ns * sizeof(uint64_t));
@@ -1378,7 +1400,7 @@ ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n
             uint32_t *q = (uint32_t *)scratch(c, "tm_queue", n * sizeof(uint32_t));
             launch_tm(s, n, nullptr, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, ps, q,
                       (uint32_t *)(c->d_flags + kFlagTmQueue), tm_seg_max(c),
-                      c->d_err, st);
+                      tm_few_exact(c), c->d_err, st);
         }
         out_finish(tm_out, tm, n, st);
         if (pass_out)

@@ -190,6 +190,9 @@ struct PairDev {
     // Tm shortest-path steps: positions 0 and L-1 and every degenerate position, ascending
     int nkey[2];
     uint8_t key[2][AH_MAX_PRIMER_LEN];
+    // 1 when every duplex of either primer has dS + C < 0 (a bound from the table's
+    // largest entries): only sites within ~1e-9 K of tm_min can need exhaustive fp64
+    int few_exact;
     float tm_min_f;
     int saltcorr;
     double tm_min;
@@ -202,12 +205,14 @@ struct PairDev {
 
 // tm.cu
 // queue: n entries of scratch for the sites decided by exhaustive fp64
-// enumeration; queue_n: one device word (zeroed here).  seg_max: the largest
-// nkey - 1 over the pairs' primers.  Two kernels.
+// enumeration; queue_n: two device words (queue length, finished blocks;
+// zeroed here).  seg_max: the largest nkey - 1 over the pairs' primers.
+// few_exact (all pairs' few_exact): the Tm kernel's last block evaluates the
+// queue; else a second kernel does, a block per site.
 // n_dev: optional device count (min(*n_dev, n) sites).
 void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const PairDev *pairs_d, int n_pairs, const uint32_t *planes,
                const uint64_t *contig_off, float *tm_out, uint8_t *pass_out, uint32_t *queue, uint32_t *queue_n,
-               int seg_max, int *err, cudaStream_t s);
+               int seg_max, bool few_exact, int *err, cudaStream_t s);
 
 // pair.cu
 // n_dev (here and below): optional device count, min(*n_dev, n) records.

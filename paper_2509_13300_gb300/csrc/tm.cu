@@ -46,7 +46,7 @@ __device__ __forceinline__ int base_at(const uint32_t *__restrict__ planes, uint
     return code;
 }
 
-constexpr int kTmWarps = 4;
+constexpr int kTmWarps = 4; // 128 threads: also the block size of exact_site
 
 template <class F> __device__ __forceinline__ float group_reduce(float v, F op)
 {
@@ -81,6 +81,104 @@ __device__ double exact_tm(const PairDev &pd, const int8_t *bt, int L, uint64_t 
     return tm;
 }
 
+// One queued site with a whole block of kExactThreads: every oligo in fp64
+// with the definition's operation order (exact_tm), block-wide maximum, then
+// the Tm and the pass flag.  bt and wmax are the block's shared scratch.
+constexpr int kExactThreads = 128; // fp64-bound: a block of 128 already keeps the SM's fp64 units busy
+
+__device__ void exact_site(const ah_site *__restrict__ sites, const PairDev *__restrict__ pairs,
+                           const uint32_t *__restrict__ planes, const uint64_t *__restrict__ contig_off, uint32_t i,
+                           float *__restrict__ tm_out, uint8_t *__restrict__ pass_out, int8_t *bt, double *wmax)
+{
+    const ah_site s = sites[i];
+    const PairDev &pd = pairs[s.pair];
+    const int L = pd.L[s.primer];
+    const uint8_t *qm = pd.mask[s.primer];
+    const uint64_t P = contig_off[s.contig] + s.pos;
+    for (int q = threadIdx.x; q < L; q += blockDim.x) {
+        const int c = base_at(planes, P + (s.strand == 0 ? q : L - 1 - q));
+        bt[q] = (int8_t)(s.strand == 0 ? 3 - c : c); // queued sites have only A/C/G/T
+    }
+    __syncthreads();
+    int deg = 1;
+    for (int q = 0; q < L; ++q)
+        deg *= __popc(qm[q]);
+    double best = -INFINITY;
+    for (int o = threadIdx.x; o < deg; o += blockDim.x) {
+        // oligo number o -> bases (mixed radix over the positions' sets)
+        uint64_t olig = 0;
+        int rem = o;
+        for (int q = L - 1; q >= 0; --q) {
+            const int nqb = __popc(qm[q]);
+            int d; // rem % nqb, rem /= nqb for nqb in 1..4 (rem < 10000)
+            if (nqb == 1) {
+                d = 0;
+            } else if (nqb == 2) {
+                d = rem & 1;
+                rem >>= 1;
+            } else if (nqb == 4) {
+                d = rem & 3;
+                rem >>= 2;
+            } else {
+                const int q3 = (rem * 43691) >> 17; // rem / 3, exact for rem < 2^16
+                d = rem - 3 * q3;
+                rem = q3;
+            }
+            int base_q = 0;
+            for (int x = 0; x < 4; ++x)
+                if (qm[q] >> x & 1) {
+                    if (d == 0) {
+                        base_q = x;
+                        break;
+                    }
+                    --d;
+                }
+            olig |= (uint64_t)base_q << (2 * q);
+        }
+        const double t = exact_tm(pd, bt, L, olig);
+        best = t > best ? t : best;
+    }
+    for (int d = 16; d >= 1; d >>= 1) {
+        const double o2 = __shfl_xor_sync(0xffffffffu, best, d);
+        best = o2 > best ? o2 : best;
+    }
+    if ((threadIdx.x & 31) == 0)
+        wmax[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = wmax[0];
+        for (int w = 1; w < kExactThreads / 32; ++w)
+            m = wmax[w] > m ? wmax[w] : m;
+        float tm = (float)m;
+        if (pass_out) {
+            const bool pass = m >= pd.tm_min;
+            pass_out[i] = pass;
+            if (!pass && tm >= pd.tm_min_f) // rounding to fp32 may reach the threshold: stay below it
+                tm = nextafterf(pd.tm_min_f, -INFINITY);
+        }
+        tm_out[i] = tm;
+    }
+    __syncthreads(); // bt and wmax are reused by the next queued site
+}
+
+// Queued sites, one block per site (tables under which many sites may queue).
+// The queue length is read on the device.
+__global__ void __launch_bounds__(kExactThreads) tm_exact_kernel(const ah_site *__restrict__ sites,
+                                                                 const PairDev *__restrict__ pairs,
+                                                                 const uint32_t *__restrict__ planes,
+                                                                 const uint64_t *__restrict__ contig_off,
+                                                                 const uint32_t *__restrict__ queue,
+                                                                 const uint32_t *__restrict__ queue_n,
+                                                                 float *__restrict__ tm_out,
+                                                                 uint8_t *__restrict__ pass_out)
+{
+    __shared__ int8_t bt[AH_MAX_PRIMER_LEN];
+    __shared__ double wmax[kExactThreads / 32];
+    const uint32_t nq = *queue_n;
+    for (uint32_t e = blockIdx.x; e < nq; e += gridDim.x)
+        exact_site(sites, pairs, planes, contig_off, queue[e], tm_out, pass_out, bt, wmax);
+}
+
 // Per-pair constants of the fp32 path, staged in shared memory by every
 // block (the shortest-path steps read them in dependent chains).
 struct TmPairS {
@@ -104,8 +202,9 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                                                            const uint64_t *__restrict__ contig_off,
                                                            float *__restrict__ tm_out, uint8_t *__restrict__ pass_out,
                                                            uint32_t *__restrict__ queue, uint32_t *__restrict__ queue_n,
-                                                           int seg_max, int *__restrict__ err)
+                                                           int seg_max, int last_block_exact, int *__restrict__ err)
 {
+    static_assert(32 * kTmWarps == kExactThreads, "the last block evaluates queued sites with exact_site");
     __shared__ int8_t bts[kTmWarps][8][AH_MAX_PRIMER_LEN];
     // dynamic: [n_pairs] TmPairS, then [kTmWarps * 8 sites][seg_max][16] segment tables
     extern __shared__ __align__(16) unsigned char tm_smem[];
@@ -189,12 +288,6 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
         const bool run = act && !bad;
         const float cst =
             act ? (float)(pd.sconst + (pd.saltcorr == 5 ? 0.368 * (double)(L - 1) * pd.log_na : 0.0)) : -1.f;
-        // The fp64 sign test below steps over every position; its shuffles need all
-        // 32 lanes, so its loop runs to the warp's longest primer Lw and each group
-        // only reads tables and updates its state while q < L (bt[q] is written for q < L).
-        int Lw = L;
-        for (int d = 16; d >= 1; d >>= 1)
-            Lw = max(Lw, __shfl_xor_sync(0xffffffffu, Lw, d));
         // Steps at key positions only (primer positions 0 and L-1 and every
         // degenerate one): between two keys the oligo bases are fixed, so all
         // stacks from key i to key i+1 form a 4x4 table of (dH, dS) sums
@@ -336,25 +429,59 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
         const bool near = dink && pass_out && fabsf(tm32 - pd.tm_min_f) < 0.01f;
         int decided = -1; // 1 pass, 0 fail, -1 undecided
         if (__any_sync(0xffffffffu, near)) {
+            // Same key segments, fp64.  First every weight W[i][x] = 1000 dH - thr dS of
+            // this lane's column (independent work, written over the fp32 tables, no
+            // longer needed), then the dependent chain over the segments.
             const double DINF = __longlong_as_double(0x7ff0000000000000ll);
             const double thr =
                 near ? pd.tm_min + 273.15 - ((pd.saltcorr >= 1 && pd.saltcorr <= 4) ? pd.tm_shift : 0.0) : 0.0;
-            double cd = (near && (mask[0] >> y & 1))
+            double *W = reinterpret_cast<double *>(E); // W[si * 16 + x * 4 + y], one double per float2 slot
+            __syncwarp();
+            if (near) {
+                for (int si = 0; si < m; ++si) {
+                    const int k0 = key[si], k1 = key[si + 1];
+                    if (k1 == k0 + 1) {
+                        for (int x = 0; x < 4; ++x) {
+                            const int idx = ((x * 4 + y) * 4 + bt[k0]) * 4 + bt[k1];
+                            W[si * 16 + x * 4 + y] = 1000.0 * pd.stack_dH_d[idx] - thr * pd.stack_dS_d[idx];
+                        }
+                    } else {
+                        double cH = 0.0, cS = 0.0;
+                        for (int q = k0 + 2; q < k1; ++q) {
+                            const int a0 = __ffs(mask[q - 1]) - 1, b0 = __ffs(mask[q]) - 1;
+                            const int idx = ((a0 * 4 + b0) * 4 + bt[q - 1]) * 4 + bt[q];
+                            cH += pd.stack_dH_d[idx];
+                            cS += pd.stack_dS_d[idx];
+                        }
+                        const int fa = __ffs(mask[k0 + 1]) - 1, fb = __ffs(mask[k1 - 1]) - 1;
+                        const int iq = ((fb * 4 + y) * 4 + bt[k1 - 1]) * 4 + bt[k1];
+                        cH += pd.stack_dH_d[iq];
+                        cS += pd.stack_dS_d[iq];
+                        for (int x = 0; x < 4; ++x) {
+                            const int ip = ((x * 4 + fa) * 4 + bt[k0]) * 4 + bt[k0 + 1];
+                            W[si * 16 + x * 4 + y] =
+                                1000.0 * (pd.stack_dH_d[ip] + cH) - thr * (pd.stack_dS_d[ip] + cS);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            double cd = (near && (amask & 1u))
                             ? 1000.0 * pd.term_dH_d[y * 4 + bt[0]] - thr * pd.term_dS_d[y * 4 + bt[0]]
                             : DINF;
-            for (int q = 1; q < Lw; ++q) {
-                const bool in = q < L;
+            for (int si = 0; si < mw; ++si) {
+                const bool in = near && si < m;
                 double best = DINF;
+#pragma unroll
                 for (int x = 0; x < 4; ++x) {
                     const double cx = __shfl_sync(0xffffffffu, cd, g0 + x);
                     if (in) {
-                        const int idx = ((x * 4 + y) * 4 + bt[q - 1]) * 4 + bt[q];
-                        const double v = cx + 1000.0 * pd.stack_dH_d[idx] - thr * pd.stack_dS_d[idx];
+                        const double v = cx + W[si * 16 + x * 4 + y];
                         best = v < best ? v : best;
                     }
                 }
                 if (in)
-                    cd = (mask[q] >> y & 1) ? best : DINF;
+                    cd = (amask >> (si + 1) & 1u) ? best : DINF;
             }
             double fin = cd < DINF ? cd + 1000.0 * pd.term_dH_d[y * 4 + bt[L - 1]] -
                                          thr * pd.term_dS_d[y * 4 + bt[L - 1]]
@@ -366,8 +493,8 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
             if (near)
                 decided = F < -1e-6 ? 1 : (F > 1e-6 ? 0 : -1);
         }
-        // sites decided the reference way (see the file comment) go to a queue that
-        // tm_exact_kernel works off with a whole block per site
+        // sites decided the reference way (see the file comment) go to a queue, worked
+        // off below by the last block or by tm_exact_kernel, a whole block per site
         const bool exact = run && (!dink || (near && decided < 0));
         if (exact && y == 0)
             queue[atomicAdd(queue_n, 1u)] = (uint32_t)i;
@@ -375,7 +502,7 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
             float tm = NAN;
             uint8_t pass = 0;
             if (!bad) {
-                tm = tm32; // replaced by tm_exact_kernel for queued sites
+                tm = tm32; // replaced by the exact evaluation for queued sites
                 pass = tm32 >= pd.tm_min_f;
                 if (decided >= 0) { // the exact decision; the fp32 value (within 1e-3) made consistent with it
                     pass = (uint8_t)decided;
@@ -395,96 +522,23 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
         }
         __syncwarp();
     }
-}
-
-// Queued sites, one block per site: every oligo in fp64 with the
-// definition's operation order (exact_tm), block-wide maximum, then the Tm
-// and the pass flag.  The queue length is read on the device.
-constexpr int kExactThreads = 128; // fp64-bound: a block of 128 already keeps the SM's fp64 units busy
-
-__global__ void __launch_bounds__(kExactThreads) tm_exact_kernel(const ah_site *__restrict__ sites,
-                                                                 const PairDev *__restrict__ pairs,
-                                                                 const uint32_t *__restrict__ planes,
-                                                                 const uint64_t *__restrict__ contig_off,
-                                                                 const uint32_t *__restrict__ queue,
-                                                                 const uint32_t *__restrict__ queue_n,
-                                                                 float *__restrict__ tm_out,
-                                                                 uint8_t *__restrict__ pass_out)
-{
-    __shared__ int8_t bt[AH_MAX_PRIMER_LEN];
-    __shared__ double wmax[kExactThreads / 32];
-    const uint32_t nq = *queue_n;
-    for (uint32_t e = blockIdx.x; e < nq; e += gridDim.x) {
-        const uint32_t i = queue[e];
-        const ah_site s = sites[i];
-        const PairDev &pd = pairs[s.pair];
-        const int L = pd.L[s.primer];
-        const uint8_t *qm = pd.mask[s.primer];
-        const uint64_t P = contig_off[s.contig] + s.pos;
-        for (int q = threadIdx.x; q < L; q += blockDim.x) {
-            const int c = base_at(planes, P + (s.strand == 0 ? q : L - 1 - q));
-            bt[q] = (int8_t)(s.strand == 0 ? 3 - c : c); // queued sites have only A/C/G/T
-        }
+    // Tables under which only the rare ambiguous sites queue: the last block to
+    // finish evaluates them (no second launch).  queue_n[1] counts finished blocks.
+    if (last_block_exact) {
+        __shared__ int is_last;
+        __threadfence(); // this block's queue entries and results before its count
         __syncthreads();
-        int deg = 1;
-        for (int q = 0; q < L; ++q)
-            deg *= __popc(qm[q]);
-        double best = -INFINITY;
-        for (int o = threadIdx.x; o < deg; o += blockDim.x) {
-            // oligo number o -> bases (mixed radix over the positions' sets)
-            uint64_t olig = 0;
-            int rem = o;
-            for (int q = L - 1; q >= 0; --q) {
-                const int nqb = __popc(qm[q]);
-                int d; // rem % nqb, rem /= nqb for nqb in 1..4 (rem < 10000)
-                if (nqb == 1) {
-                    d = 0;
-                } else if (nqb == 2) {
-                    d = rem & 1;
-                    rem >>= 1;
-                } else if (nqb == 4) {
-                    d = rem & 3;
-                    rem >>= 2;
-                } else {
-                    const int q3 = (rem * 43691) >> 17; // rem / 3, exact for rem < 2^16
-                    d = rem - 3 * q3;
-                    rem = q3;
-                }
-                int base_q = 0;
-                for (int x = 0; x < 4; ++x)
-                    if (qm[q] >> x & 1) {
-                        if (d == 0) {
-                            base_q = x;
-                            break;
-                        }
-                        --d;
-                    }
-                olig |= (uint64_t)base_q << (2 * q);
-            }
-            const double t = exact_tm(pd, bt, L, olig);
-            best = t > best ? t : best;
-        }
-        for (int d = 16; d >= 1; d >>= 1) {
-            const double o2 = __shfl_xor_sync(0xffffffffu, best, d);
-            best = o2 > best ? o2 : best;
-        }
-        if ((threadIdx.x & 31) == 0)
-            wmax[threadIdx.x >> 5] = best;
+        if (threadIdx.x == 0)
+            is_last = atomicAdd(queue_n + 1, 1u) == gridDim.x - 1;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double m = wmax[0];
-            for (int w = 1; w < kExactThreads / 32; ++w)
-                m = wmax[w] > m ? wmax[w] : m;
-            float tm = (float)m;
-            if (pass_out) {
-                const bool pass = m >= pd.tm_min;
-                pass_out[i] = pass;
-                if (!pass && tm >= pd.tm_min_f) // rounding to fp32 may reach the threshold: stay below it
-                    tm = nextafterf(pd.tm_min_f, -INFINITY);
-            }
-            tm_out[i] = tm;
+        if (is_last) {
+            __threadfence();
+            const uint32_t nq = *(volatile const uint32_t *)queue_n;
+            double *wmax = reinterpret_cast<double *>(seg_smem); // the segment tables are free now
+            int8_t *bt0 = &bts[0][0][0];
+            for (uint32_t e = 0; e < nq; ++e)
+                exact_site(sites, pairs, planes, contig_off, queue[e], tm_out, pass_out, bt0, wmax);
         }
-        __syncthreads(); // bt and wmax are reused by the next queued site
     }
 }
 
@@ -492,7 +546,7 @@ __global__ void __launch_bounds__(kExactThreads) tm_exact_kernel(const ah_site *
 
 void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const PairDev *pairs_d, int n_pairs,
                const uint32_t *planes, const uint64_t *contig_off, float *tm_out, uint8_t *pass_out, uint32_t *queue,
-               uint32_t *queue_n, int seg_max, int *err, cudaStream_t s)
+               uint32_t *queue_n, int seg_max, bool few_exact, int *err, cudaStream_t s)
 {
     if (!n)
         return;
@@ -508,15 +562,18 @@ void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const Pa
         AH_CUDA(cudaFuncSetAttribute(tm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most));
         cached_dev = dev;
     }
-    AH_CUDA(cudaMemsetAsync(queue_n, 0, sizeof(uint32_t), s));
+    AH_CUDA(cudaMemsetAsync(queue_n, 0, 2 * sizeof(uint32_t), s)); // queue length, finished blocks
     const uint64_t per_block = 8ull * kTmWarps; // sites per block per pass
     uint64_t blocks = (n + per_block - 1) / per_block;
     if (blocks > 65535)
         blocks = 65535;
     const size_t smem = (size_t)n_pairs * sizeof(TmPairS) + (size_t)kTmWarps * 8 * seg_max * 16 * sizeof(float2);
     tm_kernel<<<(unsigned)blocks, 32 * kTmWarps, smem, s>>>(sites, n, n_dev, pairs_d, n_pairs, planes, contig_off,
-                                                            tm_out, pass_out, queue, queue_n, seg_max, err);
+                                                            tm_out, pass_out, queue, queue_n, seg_max,
+                                                            few_exact ? 1 : 0, err);
     AH_CUDA(cudaGetLastError());
+    if (few_exact)
+        return;
     tm_exact_kernel<<<(unsigned)sms, kExactThreads, 0, s>>>(sites, pairs_d, planes, contig_off, queue, queue_n,
                                                               tm_out, pass_out);
     AH_CUDA(cudaGetLastError());
