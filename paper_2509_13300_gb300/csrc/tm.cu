@@ -190,6 +190,14 @@ struct TmPairS {
 };
 static_assert(sizeof(TmPairS) % 16 == 0, "TmPairS keeps 16-byte alignment");
 
+// The fp64 tables of the near-threshold sign test, staged too for up to
+// kTmStageD pairs (the test walks them in a dependent chain).
+struct TmPairD {
+    double2 st[256]; // (dH, dS)
+    double2 tm[16];
+};
+constexpr int kTmStageD = 4;
+
 // Four lanes per site: lane y of a group holds the DP state "oligo base at
 // the current key position = y".  Each step takes the four predecessor costs
 // by shuffles and keeps the best predecessor (2 bits per key), so the argmin
@@ -206,10 +214,14 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
 {
     static_assert(32 * kTmWarps == kExactThreads, "the last block evaluates queued sites with exact_site");
     __shared__ int8_t bts[kTmWarps][8][AH_MAX_PRIMER_LEN];
-    // dynamic: [n_pairs] TmPairS, then [kTmWarps * 8 sites][seg_max][16] segment tables
+    // dynamic: [n_pairs] TmPairS, [n_pairs <= kTmStageD ? n_pairs : 0] TmPairD,
+    // then [kTmWarps * 8 sites][seg_max][16] segment tables
     extern __shared__ __align__(16) unsigned char tm_smem[];
     TmPairS *ps = reinterpret_cast<TmPairS *>(tm_smem);
-    float2 *seg_smem = reinterpret_cast<float2 *>(tm_smem + (size_t)n_pairs * sizeof(TmPairS));
+    const int nd = n_pairs <= kTmStageD ? n_pairs : 0;
+    TmPairD *pdd = reinterpret_cast<TmPairD *>(tm_smem + (size_t)n_pairs * sizeof(TmPairS));
+    float2 *seg_smem =
+        reinterpret_cast<float2 *>(tm_smem + (size_t)n_pairs * sizeof(TmPairS) + (size_t)nd * sizeof(TmPairD));
     for (int j = 0; j < n_pairs; ++j) {
         const PairDev &P = pairs[j];
         for (int t = threadIdx.x; t < 256; t += blockDim.x)
@@ -223,6 +235,12 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
         if (threadIdx.x < 2) {
             ps[j].L[threadIdx.x] = P.L[threadIdx.x];
             ps[j].nkey[threadIdx.x] = P.nkey[threadIdx.x];
+        }
+        if (j < nd) {
+            for (int t = threadIdx.x; t < 256; t += blockDim.x)
+                pdd[j].st[t] = make_double2(P.stack_dH_d[t], P.stack_dS_d[t]);
+            if (threadIdx.x < 16)
+                pdd[j].tm[threadIdx.x] = make_double2(P.term_dH_d[threadIdx.x], P.term_dS_d[threadIdx.x]);
         }
     }
     __syncthreads();
@@ -436,39 +454,41 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
             const double thr =
                 near ? pd.tm_min + 273.15 - ((pd.saltcorr >= 1 && pd.saltcorr <= 4) ? pd.tm_shift : 0.0) : 0.0;
             double *W = reinterpret_cast<double *>(E); // W[si * 16 + x * 4 + y], one double per float2 slot
+            const bool staged = act && s.pair < nd;
+            const TmPairD &sd = pdd[staged ? s.pair : 0];
+            auto stD = [&](int idx) { return staged ? sd.st[idx] : make_double2(pd.stack_dH_d[idx], pd.stack_dS_d[idx]); };
+            auto tmD = [&](int idx) { return staged ? sd.tm[idx] : make_double2(pd.term_dH_d[idx], pd.term_dS_d[idx]); };
             __syncwarp();
             if (near) {
                 for (int si = 0; si < m; ++si) {
                     const int k0 = key[si], k1 = key[si + 1];
                     if (k1 == k0 + 1) {
                         for (int x = 0; x < 4; ++x) {
-                            const int idx = ((x * 4 + y) * 4 + bt[k0]) * 4 + bt[k1];
-                            W[si * 16 + x * 4 + y] = 1000.0 * pd.stack_dH_d[idx] - thr * pd.stack_dS_d[idx];
+                            const double2 v = stD(((x * 4 + y) * 4 + bt[k0]) * 4 + bt[k1]);
+                            W[si * 16 + x * 4 + y] = 1000.0 * v.x - thr * v.y;
                         }
                     } else {
                         double cH = 0.0, cS = 0.0;
                         for (int q = k0 + 2; q < k1; ++q) {
                             const int a0 = __ffs(mask[q - 1]) - 1, b0 = __ffs(mask[q]) - 1;
-                            const int idx = ((a0 * 4 + b0) * 4 + bt[q - 1]) * 4 + bt[q];
-                            cH += pd.stack_dH_d[idx];
-                            cS += pd.stack_dS_d[idx];
+                            const double2 v = stD(((a0 * 4 + b0) * 4 + bt[q - 1]) * 4 + bt[q]);
+                            cH += v.x;
+                            cS += v.y;
                         }
                         const int fa = __ffs(mask[k0 + 1]) - 1, fb = __ffs(mask[k1 - 1]) - 1;
-                        const int iq = ((fb * 4 + y) * 4 + bt[k1 - 1]) * 4 + bt[k1];
-                        cH += pd.stack_dH_d[iq];
-                        cS += pd.stack_dS_d[iq];
+                        const double2 vq = stD(((fb * 4 + y) * 4 + bt[k1 - 1]) * 4 + bt[k1]);
+                        cH += vq.x;
+                        cS += vq.y;
                         for (int x = 0; x < 4; ++x) {
-                            const int ip = ((x * 4 + fa) * 4 + bt[k0]) * 4 + bt[k0 + 1];
-                            W[si * 16 + x * 4 + y] =
-                                1000.0 * (pd.stack_dH_d[ip] + cH) - thr * (pd.stack_dS_d[ip] + cS);
+                            const double2 vp = stD(((x * 4 + fa) * 4 + bt[k0]) * 4 + bt[k0 + 1]);
+                            W[si * 16 + x * 4 + y] = 1000.0 * (vp.x + cH) - thr * (vp.y + cS);
                         }
                     }
                 }
             }
             __syncwarp();
-            double cd = (near && (amask & 1u))
-                            ? 1000.0 * pd.term_dH_d[y * 4 + bt[0]] - thr * pd.term_dS_d[y * 4 + bt[0]]
-                            : DINF;
+            const double2 d0 = tmD(y * 4 + bt[0]), dL = tmD(y * 4 + bt[L - 1]);
+            double cd = (near && (amask & 1u)) ? 1000.0 * d0.x - thr * d0.y : DINF;
             for (int si = 0; si < mw; ++si) {
                 const bool in = near && si < m;
                 double best = DINF;
@@ -483,9 +503,7 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                 if (in)
                     cd = (amask >> (si + 1) & 1u) ? best : DINF;
             }
-            double fin = cd < DINF ? cd + 1000.0 * pd.term_dH_d[y * 4 + bt[L - 1]] -
-                                         thr * pd.term_dS_d[y * 4 + bt[L - 1]]
-                                   : DINF;
+            double fin = cd < DINF ? cd + 1000.0 * dL.x - thr * dL.y : DINF;
             fin = fmin(fin, __shfl_xor_sync(0xffffffffu, fin, 1));
             fin = fmin(fin, __shfl_xor_sync(0xffffffffu, fin, 2));
             const double Cp = pd.sconst + (pd.saltcorr == 5 ? 0.368 * (double)(L - 1) * pd.log_na : 0.0);
@@ -557,7 +575,7 @@ void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const Pa
     AH_CUDA(cudaGetDevice(&dev));
     if (dev != cached_dev) {
         AH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const int most = AH_MAX_PAIRS_PER_SCAN * (int)sizeof(TmPairS) +
+        const int most = AH_MAX_PAIRS_PER_SCAN * (int)sizeof(TmPairS) + kTmStageD * (int)sizeof(TmPairD) +
                          kTmWarps * 8 * (AH_MAX_PRIMER_LEN - 1) * 16 * (int)sizeof(float2);
         AH_CUDA(cudaFuncSetAttribute(tm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most));
         cached_dev = dev;
@@ -567,7 +585,8 @@ void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const Pa
     uint64_t blocks = (n + per_block - 1) / per_block;
     if (blocks > 65535)
         blocks = 65535;
-    const size_t smem = (size_t)n_pairs * sizeof(TmPairS) + (size_t)kTmWarps * 8 * seg_max * 16 * sizeof(float2);
+    const size_t smem = (size_t)n_pairs * sizeof(TmPairS) + (size_t)(n_pairs <= kTmStageD ? n_pairs : 0) * sizeof(TmPairD) +
+                        (size_t)kTmWarps * 8 * seg_max * 16 * sizeof(float2);
     tm_kernel<<<(unsigned)blocks, 32 * kTmWarps, smem, s>>>(sites, n, n_dev, pairs_d, n_pairs, planes, contig_off,
                                                             tm_out, pass_out, queue, queue_n, seg_max,
                                                             few_exact ? 1 : 0, err);
