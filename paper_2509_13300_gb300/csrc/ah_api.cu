@@ -465,6 +465,7 @@ PairDev make_pair_dev(const PrimerPair &pp)
     case 4: d.tm_shift = 11.7 * std::log10(na); break;
     default: break;
     }
+    d.thr = d.tm_min + 273.15 - ((d.saltcorr >= 1 && d.saltcorr <= 4) ? d.tm_shift : 0.0);
     for (int i = 0; i < 256; ++i) {
         d.stack_dH[i] = (float)pp.table.stack_dH[i];
         d.stack_dS[i] = (float)pp.table.stack_dS[i];

@@ -196,6 +196,7 @@ struct PairDev {
     float tm_min_f;
     int saltcorr;
     double tm_min;
+    double thr;      // tm_min as a ratio 1000 dH / (dS + C) in kelvin: tm_min + 273.15 (- shift, methods 1-4)
     double sconst;   // R ln(x), x = (dnac1 - dnac2/2) 1e-9
     double log_na;   // ln([Na_eq] in mol/L); salt method 5 adds 0.368 (L-1) log_na to dS
     double tm_shift; // salt methods 1-4

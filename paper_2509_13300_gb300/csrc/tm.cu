@@ -190,11 +190,12 @@ struct TmPairS {
 };
 static_assert(sizeof(TmPairS) % 16 == 0, "TmPairS keeps 16-byte alignment");
 
-// The fp64 tables of the near-threshold sign test, staged too for up to
-// kTmStageD pairs (the test walks them in a dependent chain).
+// The fp64 weights 1000 dH - thr dS of every table entry at the pair's
+// threshold thr, for the near-threshold sign test; staged for up to kTmStageD
+// pairs (the test walks them in a dependent chain).
 struct TmPairD {
-    double2 st[256]; // (dH, dS)
-    double2 tm[16];
+    double st[256];
+    double tm[16];
 };
 constexpr int kTmStageD = 4;
 
@@ -238,9 +239,9 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
         }
         if (j < nd) {
             for (int t = threadIdx.x; t < 256; t += blockDim.x)
-                pdd[j].st[t] = make_double2(P.stack_dH_d[t], P.stack_dS_d[t]);
+                pdd[j].st[t] = 1000.0 * P.stack_dH_d[t] - P.thr * P.stack_dS_d[t];
             if (threadIdx.x < 16)
-                pdd[j].tm[threadIdx.x] = make_double2(P.term_dH_d[threadIdx.x], P.term_dS_d[threadIdx.x]);
+                pdd[j].tm[threadIdx.x] = 1000.0 * P.term_dH_d[threadIdx.x] - P.thr * P.term_dS_d[threadIdx.x];
         }
     }
     __syncthreads();
@@ -451,44 +452,35 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
             // this lane's column (independent work, written over the fp32 tables, no
             // longer needed), then the dependent chain over the segments.
             const double DINF = __longlong_as_double(0x7ff0000000000000ll);
-            const double thr =
-                near ? pd.tm_min + 273.15 - ((pd.saltcorr >= 1 && pd.saltcorr <= 4) ? pd.tm_shift : 0.0) : 0.0;
+            const double thr = pd.thr;
             double *W = reinterpret_cast<double *>(E); // W[si * 16 + x * 4 + y], one double per float2 slot
             const bool staged = act && s.pair < nd;
             const TmPairD &sd = pdd[staged ? s.pair : 0];
-            auto stD = [&](int idx) { return staged ? sd.st[idx] : make_double2(pd.stack_dH_d[idx], pd.stack_dS_d[idx]); };
-            auto tmD = [&](int idx) { return staged ? sd.tm[idx] : make_double2(pd.term_dH_d[idx], pd.term_dS_d[idx]); };
+            // weight 1000 dH - thr dS of one stack / terminal entry
+            auto stW = [&](int idx) { return staged ? sd.st[idx] : 1000.0 * pd.stack_dH_d[idx] - thr * pd.stack_dS_d[idx]; };
+            auto tmW = [&](int idx) { return staged ? sd.tm[idx] : 1000.0 * pd.term_dH_d[idx] - thr * pd.term_dS_d[idx]; };
             __syncwarp();
             if (near) {
                 for (int si = 0; si < m; ++si) {
                     const int k0 = key[si], k1 = key[si + 1];
                     if (k1 == k0 + 1) {
-                        for (int x = 0; x < 4; ++x) {
-                            const double2 v = stD(((x * 4 + y) * 4 + bt[k0]) * 4 + bt[k1]);
-                            W[si * 16 + x * 4 + y] = 1000.0 * v.x - thr * v.y;
-                        }
+                        for (int x = 0; x < 4; ++x)
+                            W[si * 16 + x * 4 + y] = stW(((x * 4 + y) * 4 + bt[k0]) * 4 + bt[k1]);
                     } else {
-                        double cH = 0.0, cS = 0.0;
+                        double cw = 0.0; // the fixed stretch and the step into key k1 with base y
                         for (int q = k0 + 2; q < k1; ++q) {
                             const int a0 = __ffs(mask[q - 1]) - 1, b0 = __ffs(mask[q]) - 1;
-                            const double2 v = stD(((a0 * 4 + b0) * 4 + bt[q - 1]) * 4 + bt[q]);
-                            cH += v.x;
-                            cS += v.y;
+                            cw += stW(((a0 * 4 + b0) * 4 + bt[q - 1]) * 4 + bt[q]);
                         }
                         const int fa = __ffs(mask[k0 + 1]) - 1, fb = __ffs(mask[k1 - 1]) - 1;
-                        const double2 vq = stD(((fb * 4 + y) * 4 + bt[k1 - 1]) * 4 + bt[k1]);
-                        cH += vq.x;
-                        cS += vq.y;
-                        for (int x = 0; x < 4; ++x) {
-                            const double2 vp = stD(((x * 4 + fa) * 4 + bt[k0]) * 4 + bt[k0 + 1]);
-                            W[si * 16 + x * 4 + y] = 1000.0 * (vp.x + cH) - thr * (vp.y + cS);
-                        }
+                        cw += stW(((fb * 4 + y) * 4 + bt[k1 - 1]) * 4 + bt[k1]);
+                        for (int x = 0; x < 4; ++x)
+                            W[si * 16 + x * 4 + y] = stW(((x * 4 + fa) * 4 + bt[k0]) * 4 + bt[k0 + 1]) + cw;
                     }
                 }
             }
             __syncwarp();
-            const double2 d0 = tmD(y * 4 + bt[0]), dL = tmD(y * 4 + bt[L - 1]);
-            double cd = (near && (amask & 1u)) ? 1000.0 * d0.x - thr * d0.y : DINF;
+            double cd = (near && (amask & 1u)) ? tmW(y * 4 + bt[0]) : DINF;
             for (int si = 0; si < mw; ++si) {
                 const bool in = near && si < m;
                 double best = DINF;
@@ -503,7 +495,7 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                 if (in)
                     cd = (amask >> (si + 1) & 1u) ? best : DINF;
             }
-            double fin = cd < DINF ? cd + 1000.0 * dL.x - thr * dL.y : DINF;
+            double fin = cd < DINF ? cd + tmW(y * 4 + bt[L - 1]) : DINF;
             fin = fmin(fin, __shfl_xor_sync(0xffffffffu, fin, 1));
             fin = fmin(fin, __shfl_xor_sync(0xffffffffu, fin, 2));
             const double Cp = pd.sconst + (pd.saltcorr == 5 ? 0.368 * (double)(L - 1) * pd.log_na : 0.0);
