@@ -190,13 +190,23 @@ struct TmPairS {
 };
 static_assert(sizeof(TmPairS) % 16 == 0, "TmPairS keeps 16-byte alignment");
 
-// The fp64 weights 1000 dH - thr dS of every table entry at the pair's
-// threshold thr, for the near-threshold sign test; staged for up to kTmStageD
-// pairs (the test walks them in a dependent chain).
+// The weights 1000 dH - thr dS of every table entry at the pair's threshold
+// thr, for the near-threshold sign test: computed in fp64 from the fp64
+// table, then held as fixed point (units of 2^-30 cal/mol, int64) so that
+// every path sum is exact; staged for up to kTmStageD pairs.
 struct TmPairD {
-    double st[256];
-    double tm[16];
+    long long st[256];
+    long long tm[16];
 };
+constexpr double kFix = 1073741824.0; // 2^30: fixed-point scale of the sign test
+// |each weight's rounding| <= 2^-31 cal/mol, so a path of <= 32 terms is within
+// 2e-8 of its exact value; decisions use a margin of 1e-6 cal/mol (file comment)
+constexpr long long kFixMargin = 1074; // 1e-6 * 2^30
+
+__device__ __forceinline__ long long fix_weight(double dH, double dS, double thr)
+{
+    return __double2ll_rn((1000.0 * dH - thr * dS) * kFix);
+}
 constexpr int kTmStageD = 4;
 
 // Four lanes per site: lane y of a group holds the DP state "oligo base at
@@ -239,9 +249,9 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
         }
         if (j < nd) {
             for (int t = threadIdx.x; t < 256; t += blockDim.x)
-                pdd[j].st[t] = 1000.0 * P.stack_dH_d[t] - P.thr * P.stack_dS_d[t];
+                pdd[j].st[t] = fix_weight(P.stack_dH_d[t], P.stack_dS_d[t], P.thr);
             if (threadIdx.x < 16)
-                pdd[j].tm[threadIdx.x] = 1000.0 * P.term_dH_d[threadIdx.x] - P.thr * P.term_dS_d[threadIdx.x];
+                pdd[j].tm[threadIdx.x] = fix_weight(P.term_dH_d[threadIdx.x], P.term_dS_d[threadIdx.x], P.thr);
         }
     }
     __syncthreads();
@@ -448,17 +458,19 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
         const bool near = dink && pass_out && fabsf(tm32 - pd.tm_min_f) < 0.01f;
         int decided = -1; // 1 pass, 0 fail, -1 undecided
         if (__any_sync(0xffffffffu, near)) {
-            // Same key segments, fp64.  First every weight W[i][x] = 1000 dH - thr dS of
-            // this lane's column (independent work, written over the fp32 tables, no
-            // longer needed), then the dependent chain over the segments.
-            const double DINF = __longlong_as_double(0x7ff0000000000000ll);
-            const double thr = pd.thr;
-            double *W = reinterpret_cast<double *>(E); // W[si * 16 + x * 4 + y], one double per float2 slot
+            // Same key segments, exact fixed-point weights at lam = thr.  First every
+            // weight W[i][x] of this lane's column (independent work, written over the
+            // fp32 tables, no longer needed), then the dependent chain over the segments.
+            const long long LINF = 0x2000000000000000ll; // above any path sum, no overflow when added to
+            long long *W = reinterpret_cast<long long *>(E); // W[si * 16 + x * 4 + y], 8 bytes per float2 slot
             const bool staged = act && s.pair < nd;
             const TmPairD &sd = pdd[staged ? s.pair : 0];
-            // weight 1000 dH - thr dS of one stack / terminal entry
-            auto stW = [&](int idx) { return staged ? sd.st[idx] : 1000.0 * pd.stack_dH_d[idx] - thr * pd.stack_dS_d[idx]; };
-            auto tmW = [&](int idx) { return staged ? sd.tm[idx] : 1000.0 * pd.term_dH_d[idx] - thr * pd.term_dS_d[idx]; };
+            auto stW = [&](int idx) {
+                return staged ? sd.st[idx] : fix_weight(pd.stack_dH_d[idx], pd.stack_dS_d[idx], pd.thr);
+            };
+            auto tmW = [&](int idx) {
+                return staged ? sd.tm[idx] : fix_weight(pd.term_dH_d[idx], pd.term_dS_d[idx], pd.thr);
+            };
             __syncwarp();
             if (near) {
                 for (int si = 0; si < m; ++si) {
@@ -467,7 +479,7 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                         for (int x = 0; x < 4; ++x)
                             W[si * 16 + x * 4 + y] = stW(((x * 4 + y) * 4 + bt[k0]) * 4 + bt[k1]);
                     } else {
-                        double cw = 0.0; // the fixed stretch and the step into key k1 with base y
+                        long long cw = 0; // the fixed stretch and the step into key k1 with base y
                         for (int q = k0 + 2; q < k1; ++q) {
                             const int a0 = __ffs(mask[q - 1]) - 1, b0 = __ffs(mask[q]) - 1;
                             cw += stW(((a0 * 4 + b0) * 4 + bt[q - 1]) * 4 + bt[q]);
@@ -480,28 +492,32 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                 }
             }
             __syncwarp();
-            double cd = (near && (amask & 1u)) ? tmW(y * 4 + bt[0]) : DINF;
+            long long cd = (near && (amask & 1u)) ? tmW(y * 4 + bt[0]) : LINF;
             for (int si = 0; si < mw; ++si) {
                 const bool in = near && si < m;
-                double best = DINF;
+                long long best = LINF;
 #pragma unroll
                 for (int x = 0; x < 4; ++x) {
-                    const double cx = __shfl_sync(0xffffffffu, cd, g0 + x);
+                    const long long cx = __shfl_sync(0xffffffffu, cd, g0 + x);
                     if (in) {
-                        const double v = cx + W[si * 16 + x * 4 + y];
+                        const long long v = cx + W[si * 16 + x * 4 + y];
                         best = v < best ? v : best;
                     }
                 }
                 if (in)
-                    cd = (amask >> (si + 1) & 1u) ? best : DINF;
+                    cd = (amask >> (si + 1) & 1u) ? best : LINF;
             }
-            double fin = cd < DINF ? cd + tmW(y * 4 + bt[L - 1]) : DINF;
-            fin = fmin(fin, __shfl_xor_sync(0xffffffffu, fin, 1));
-            fin = fmin(fin, __shfl_xor_sync(0xffffffffu, fin, 2));
-            const double Cp = pd.sconst + (pd.saltcorr == 5 ? 0.368 * (double)(L - 1) * pd.log_na : 0.0);
-            const double F = fin - thr * Cp;
-            if (near)
-                decided = F < -1e-6 ? 1 : (F > 1e-6 ? 0 : -1);
+            long long fin = cd < LINF ? cd + tmW(y * 4 + bt[L - 1]) : LINF;
+            long long o1 = __shfl_xor_sync(0xffffffffu, fin, 1);
+            fin = o1 < fin ? o1 : fin;
+            o1 = __shfl_xor_sync(0xffffffffu, fin, 2);
+            fin = o1 < fin ? o1 : fin;
+            if (near) {
+                // min F = min path sum - thr (C + salt entropy)
+                const double Cp = pd.sconst + (pd.saltcorr == 5 ? 0.368 * (double)(L - 1) * pd.log_na : 0.0);
+                const long long F = fin - __double2ll_rn(pd.thr * Cp * kFix);
+                decided = F < -kFixMargin ? 1 : (F > kFixMargin ? 0 : -1);
+            }
         }
         // sites decided the reference way (see the file comment) go to a queue, worked
         // off below by the last block or by tm_exact_kernel, a whole block per site
