@@ -902,8 +902,8 @@ ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
         // it (profiling aid)
         if (const char *e = getenv("AH_SCAN_TUNING")) {
             int R = 8, ap = 0, order = 1, S = 3, wpc = 4, mb = 1;
-            if (sscanf(e, "%d,%d,%d,%d,%d,%d", &R, &ap, &order, &S, &wpc, &mb) >= 1 && (R == 4 || R == 8) && ap >= 0 &&
-                ap <= 100 && (order == 0 || order == 1) && S >= 2 && S <= 4 && wpc >= 1 && wpc <= 8 && mb >= 1 &&
+            if (sscanf(e, "%d,%d,%d,%d,%d,%d", &R, &ap, &order, &S, &wpc, &mb) >= 1 && (R == 2 || R == 4 || R == 8) && ap >= 0 &&
+                ap <= 100 && (order == 0 || order == 1) && S >= 2 && S <= 4 && wpc >= 1 && wpc <= 16 && mb >= 1 &&
                 mb <= 8) {
                 c->tuning.R = R;
                 c->tuning.arith_pct = ap;
