@@ -902,7 +902,7 @@ ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
         // it (profiling aid)
         if (const char *e = getenv("AH_SCAN_TUNING")) {
             int R = 8, ap = 0, order = 1, S = 3, wpc = 4, mb = 1;
-            if (sscanf(e, "%d,%d,%d,%d,%d,%d", &R, &ap, &order, &S, &wpc, &mb) >= 1 && (R == 2 || R == 4 || R == 8) && ap >= 0 &&
+            if (sscanf(e, "%d,%d,%d,%d,%d,%d", &R, &ap, &order, &S, &wpc, &mb) >= 1 && (R == 4 || R == 8) && ap >= 0 &&
                 ap <= 100 && (order == 0 || order == 1) && S >= 2 && S <= 4 && wpc >= 1 && wpc <= 16 && mb >= 1 &&
                 mb <= 8) {
                 c->tuning.R = R;
@@ -1283,18 +1283,30 @@ ah_status ah_tune_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
         uint64_t tiles = std::min<uint64_t>(gs.n_tiles, sample_tiles ? sample_tiles : 4096);
         require(tiles > 0, AH_ERR_ARG, "ah_tune_scan: empty genome set");
         // the sample must cover whole waves of the persistent grid to time it fairly
+        // register-capped variants (more resident warps) first: measured fastest on
+        // the 960-oligo pair; R = 8 uncapped for pattern sets that spill under the cap
         std::vector<ScanTuning> cand;
-        for (int R : {4, 8})
+        const int shapes[][2] = {{8, 2}, {4, 4}, {16, 1}}; // warps per CTA, minimum CTAs per SM
+        for (const auto &sh : shapes)
             for (int order : {0, 1})
-                for (int S : {2, 4})
-                    for (int wpc : {2, 4}) {
-                        ScanTuning t;
-                        t.R = R;
-                        t.order = order;
-                        t.stages = S;
-                        t.warps = wpc;
-                        cand.push_back(t);
-                    }
+                for (int S : {3, 4}) {
+                    ScanTuning t;
+                    t.R = 4;
+                    t.order = order;
+                    t.stages = S;
+                    t.warps = sh[0];
+                    t.min_blocks = sh[1];
+                    cand.push_back(t);
+                }
+        for (int order : {0, 1}) {
+            ScanTuning t;
+            t.R = 8;
+            t.order = order;
+            t.stages = 3;
+            t.warps = 4;
+            t.min_blocks = 1;
+            cand.push_back(t);
+        }
         cudaEvent_t e0 = get_event(c), e1 = get_event(c);
         double best_us = 1e30;
         ScanTuning best = c->tuning;

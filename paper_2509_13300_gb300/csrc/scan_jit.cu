@@ -316,6 +316,8 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
     for (auto &p : pats)
         Lmax = std::max(Lmax, p.L);
     const int R = t.R;
+    if (R != 4 && R != 8) // the loader reads 16-byte vectors at word lane * R of the slice
+        throw Error(AH_ERR_ARG, "scan kernel: R must be 4 or 8");
     const int nwin = 4 * ((R + Lmax - 1 + 3) / 4);
     const int NT = 32 * t.warps;
     Gen g;
