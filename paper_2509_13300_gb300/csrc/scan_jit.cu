@@ -544,10 +544,12 @@ static int debug_scan(const char *fwd, const char *rev, int k, int R, int arith_
                 }
                 pats.push_back(p);
             }
-        ah::ScanTuning t;
+        ah::ScanTuning t; // no register cap: the log reports the generator's own register use
         t.R = R;
         t.arith_pct = arith_pct;
         t.order = order;
+        t.warps = 4;
+        t.min_blocks = 1;
         bool ok = false;
         std::string l = compile ? ah::scan_compile_only(pats, t, &ok) : ah::scan_source(pats, t);
         if (!compile)
