@@ -1286,7 +1286,7 @@ ah_status ah_tune_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
         // register-capped variants (more resident warps) first: measured fastest on
         // the 960-oligo pair; R = 8 uncapped for pattern sets that spill under the cap
         std::vector<ScanTuning> cand;
-        const int shapes[][2] = {{8, 2}, {4, 4}, {16, 1}}; // warps per CTA, minimum CTAs per SM
+        const int shapes[][2] = {{16, 1}, {8, 2}, {4, 4}}; // warps per CTA, minimum CTAs per SM
         for (const auto &sh : shapes)
             for (int order : {0, 1})
                 for (int S : {3, 4}) {

@@ -73,10 +73,10 @@ struct ScanPattern {
 struct ScanTuning {
     int R = 4;            // 32-start words per thread (4 or 8: the loader reads 16-byte vectors at lane * R)
     int arith_pct = 0;    // share of full adders that form the sum with integer adds
-    int min_blocks = 2;   // __launch_bounds__ minimum blocks per SM (with warps: a register cap)
+    int min_blocks = 1;   // __launch_bounds__ minimum blocks per SM (with warps: a register cap)
     int order = 0;        // 0: word-major, 1: pattern-major code order
-    int stages = 3;       // TMA stages per warp (2..4)
-    int warps = 8;        // warps per CTA (1..16)
+    int stages = 4;       // TMA stages per warp (2..4)
+    int warps = 16;       // warps per CTA (1..16); 16 warps = a 128-register cap
 };
 
 struct ScanKernel {
