@@ -570,7 +570,9 @@ void launch_scan(ah_ctx *c, ScanKernel *k, const GenomeSet &gs, uint64_t n_tiles
     const uint32_t *planes = gs.planes;
     const uint64_t *coff = gs.contig_off;
     uint32_t nc = gs.n_contigs;
-    void *args[] = {&planes, &n_tiles, &coff, &nc, &keys, &cap, &c->d_counter, &pbits, &c->d_err};
+    uint64_t *work = c->d_flags + kFlagWork;
+    AH_CUDA(cudaMemsetAsync(work, 0, sizeof(uint64_t), st));
+    void *args[] = {&planes, &n_tiles, &coff, &nc, &keys, &cap, &c->d_counter, &pbits, &c->d_err, &work};
     AH_CUDA(cudaLaunchKernel((const void *)k->fn, dim3((unsigned)grid), dim3(k->threads), args, k->smem, st));
 }
 

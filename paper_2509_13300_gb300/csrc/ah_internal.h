@@ -162,8 +162,9 @@ enum FlagWord : int {
     kFlagAmps = 4,    // ... amplicons
     kFlagSeq = 5,     // ... sequence bytes
     kFlagRedo = 6,    // ... kRedo* bits: a count above what the launches were sized for
-    kFlagErr = 7,     // DeviceErr (low 32 bits)
-    kFlagWords = 8
+    kFlagWork = 7,    // scan: slices claimed so far (zeroed before each scan launch)
+    kFlagErr = 15,    // DeviceErr (low 32 bits)
+    kFlagWords = 16
 };
 constexpr uint64_t kRedoSites = 1, kRedoAmps = 2, kRedoSeq = 4;
 

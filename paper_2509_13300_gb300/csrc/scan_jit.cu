@@ -352,18 +352,21 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
     os << "extern \"C\" __global__ void __launch_bounds__(NT, " << t.min_blocks << ")\n"
        << "ah_scan_kernel(const u32 *__restrict__ planes, u64 n_tiles, const u64 *__restrict__ contig_off,\n"
        << "               u32 n_contigs, u64 *__restrict__ keys, u64 cap, u64 *__restrict__ counter, int pbits,\n"
-       << "               int *__restrict__ err)\n{\n"
-       << "  // Every warp owns slices of tiles (32*R words of each plane plus a 32-word\n"
-       << "  // overhang) and runs its own S-stage pipeline: lane 0 starts bulk async\n"
-       << "  // copies (TMA) into the warp's buffers, one mbarrier per stage; no CTA-wide\n"
-       << "  // barrier is ever taken.\n"
+       << "               int *__restrict__ err, u64 *__restrict__ work)\n{\n"
+       << "  // Every warp claims slices of tiles (32*R words of each plane plus a 32-word\n"
+       << "  // overhang) from the shared counter `work` (zeroed before the launch), so SMs\n"
+       << "  // that run faster take more, and runs its own S-stage pipeline: lane 0 claims\n"
+       << "  // and starts bulk async copies (TMA) into the warp's buffers, one mbarrier\n"
+       << "  // per stage; no CTA-wide barrier is ever taken.  A warp's claims only grow,\n"
+       << "  // so the first claim past the end means that none of its stages holds work.\n"
        << "  extern __shared__ __align__(128) u32 smbuf[];\n"
        << "  __shared__ __align__(8) u64 bars[WPC * S];\n"
+       << "  __shared__ u64 claims[WPC * S];\n"
        << "  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n"
        << "  u32 *wbuf = smbuf + warp * (S * 4 * SLW);\n"
        << "  u64 *wbar = bars + warp * S;\n"
+       << "  u64 *witem = claims + warp * S;\n"
        << "  const u64 n_items = n_tiles * SLICES;\n"
-       << "  const u64 gw = (u64)blockIdx.x * WPC + warp, tw = (u64)gridDim.x * WPC;\n"
        << "  if (lane == 0) {\n"
        << "    for (int q = 0; q < S; ++q) mbar_init(&wbar[q], 1);\n"
        << "    asm volatile(\"fence.mbarrier_init.release.cluster;\" ::: \"memory\");\n"
@@ -378,17 +381,24 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "      tma_copy(wbuf + (stg * 4 + x) * SLW, planes + (tl * 4 + x) * WX + sl * 32 * R, SLW * 4, &wbar[stg]);\n"
        << "  };\n"
        << "  if (lane == 0)\n"
-       << "    for (int q = 0; q < S; ++q) if (gw + q * tw < n_items) issue(gw + q * tw, q);\n"
-       << "  int k = 0;\n"
-       << "  for (u64 wi = gw; wi < n_items; wi += tw, ++k) {\n"
+       << "    for (int q = 0; q < S; ++q) {\n"
+       << "      const u64 w = atomicAdd(work, 1ull);\n"
+       << "      witem[q] = w;\n"
+       << "      if (w < n_items) issue(w, q);\n"
+       << "    }\n"
+       << "  __syncwarp();\n"
+       << "  for (int k = 0;; ++k) {\n"
        << "    const int stg = k % S;\n"
+       << "    const u64 wi = witem[stg];\n"
+       << "    if (wi >= n_items)\n"
+       << "      break;\n"
        << "    const bool ok = mbar_wait(&wbar[stg], (u32)((k / S) & 1));\n"
        << "    if (!__all_sync(0xffffffffu, ok)) {\n"
        << "      // a copy never landed: report, wait (bounded) for the copies still in flight, leave\n"
        << "      if (lane == 0) {\n"
        << "        atomicExch(err, 1);\n"
        << "        for (int d = 1; d < S; ++d)\n"
-       << "          if (wi + d * tw < n_items) mbar_wait(&wbar[(k + d) % S], (u32)(((k + d) / S) & 1));\n"
+       << "          if (witem[(k + d) % S] < n_items) mbar_wait(&wbar[(k + d) % S], (u32)(((k + d) / S) & 1));\n"
        << "      }\n"
        << "      break;\n"
        << "    }\n"
@@ -429,7 +439,12 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
     }
     os << kEmit;
     os << "    __syncwarp();\n"
-       << "    if (lane == 0 && wi + S * tw < n_items) issue(wi + S * tw, stg);\n"
+       << "    if (lane == 0) { // refill this stage with the next claim\n"
+       << "      const u64 w = atomicAdd(work, 1ull);\n"
+       << "      witem[stg] = w;\n"
+       << "      if (w < n_items) issue(w, stg);\n"
+       << "    }\n"
+       << "    __syncwarp();\n"
        << "  }\n}\n";
     return os.str();
 }
