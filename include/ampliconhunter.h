@@ -313,6 +313,28 @@ typedef struct ah_run_out {
 ah_status ah_run(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, ah_run_out *out,
                  void *stream);
 
+/* ah_run in two halves, for pipelines over many genome sets (this library's
+ * addition; the paper processes one collection per run).  ah_run_begin
+ * checks the arguments and queues the work on `stream` (a cudaStream_t, or
+ * null for the context's stream) and returns; when scan_done (a cudaEvent_t
+ * created by the caller, or null) is given it is recorded on that stream
+ * right after the primer-matching kernel, so that work on another stream --
+ * packing the next set with ah_load_genomes, say -- can wait for the scan
+ * (cudaStreamWaitEvent) instead of competing with it, and then overlaps the
+ * rest of the run.  ah_run_end waits for the queued work and completes `out`
+ * exactly as ah_run does (same results, counts and errors, including
+ * AH_ERR_OVERFLOW).  `out` and its buffers, the set and the pairs must stay
+ * as they are until ah_run_end returns.  While a run is pending the only
+ * calls accepted on the context are ah_load_genomes with a device sequence,
+ * ah_run_end, ah_get_profile, ah_last_error, ah_device_bytes and ah_destroy;
+ * every other call returns AH_ERR_ARG.  When the last run needed the
+ * step-by-step form, ah_run_begin already does the whole run and
+ * ah_run_end returns its status.
+ * Errors (begin): AH_ERR_ARG, AH_ERR_JIT, AH_ERR_CUDA; (end): those of ah_run. */
+ah_status ah_run_begin(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, ah_run_out *out,
+                       void *stream, void *scan_done);
+ah_status ah_run_end(ah_ctx *ctx);
+
 /* Measurement: per-stage device time, host time and kernel launches.
  * ah_set_profiling clears the counters; enable = 1 then brackets each stage
  * of each call with CUDA events on the stream the stage runs on and times

@@ -30,7 +30,7 @@ AMPLICON_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("start", "<u4"
 # Every symbol include/ampliconhunter.h declares.
 EXPORTS = ["ah_create", "ah_destroy", "ah_last_error", "ah_device_bytes", "ah_load_genomes", "ah_unload_genomes",
            "ah_set_primers", "ah_set_nn_table", "ah_scan", "ah_tm", "ah_pair", "ah_fetch", "ah_set_profiling",
-           "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan", "ah_run"]
+           "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan", "ah_run", "ah_run_begin", "ah_run_end"]
 
 
 class AHError(RuntimeError):
@@ -107,6 +107,8 @@ def lib():
             "ah_get_profile": (I32, [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(U64),
                                      ctypes.POINTER(U64)]),
             "ah_run": (I32, [P, U32, P, U32, ctypes.POINTER(RunOut), P]),
+            "ah_run_begin": (I32, [P, U32, P, U32, ctypes.POINTER(RunOut), P, P]),
+            "ah_run_end": (I32, [P]),
             "ah_tune_scan": (I32, [P, U32, P, U32, U64, ctypes.POINTER(TuneResult), P]),
             "ah_pair_noalloc": (I32, [P, U32, P, P, U64, P, U64, ctypes.POINTER(U64), P]),
             "ah_debug_compile_scan": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
@@ -234,6 +236,25 @@ class Context:
         ids = np.ascontiguousarray(pair_ids, dtype=np.uint32)
         st = self._lib.ah_run(self.h, set_id, _ptr(ids), len(ids), ctypes.byref(out), _stream(stream))
         self._check(st, out.n_sites)
+        return out
+
+    def ah_run_begin(self, set_id: int, pair_ids, out: RunOut, stream=None, scan_done=None):
+        """Queue a run (see ah_run_end); scan_done: a torch.cuda.Event (or raw cudaEvent_t) recorded
+        after the scan.  `out` and its buffers must stay alive until ah_run_end."""
+        ids = np.ascontiguousarray(pair_ids, dtype=np.uint32)
+        self._pending_ids = ids  # kept alive with the queued run
+        ev = None
+        if scan_done is not None:
+            if hasattr(scan_done, "cuda_event"):
+                if not scan_done.cuda_event:  # torch creates its event on first use
+                    scan_done.record()
+                ev = ctypes.c_void_p(scan_done.cuda_event)
+            else:
+                ev = ctypes.c_void_p(int(scan_done))
+        self._check(self._lib.ah_run_begin(self.h, set_id, _ptr(ids), len(ids), ctypes.byref(out), _stream(stream), ev))
+
+    def ah_run_end(self, out: RunOut) -> RunOut:
+        self._check(self._lib.ah_run_end(self.h), out.n_sites)
         return out
 
     def run(self, set_id: int, pair_ids, tm_filter: bool = True, caps=(0, 0, 0)) -> dict:

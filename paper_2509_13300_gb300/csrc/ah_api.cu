@@ -51,6 +51,29 @@ struct ah_ctx {
     // counts of runs that needed more; the last run's site count
     uint64_t fast_amps = 16384, fast_seq = 4u << 20;
     uint64_t last_sites = 0;
+    // a run queued by ah_run_begin and not yet completed by ah_run_end
+    struct FastRun {
+        bool sites_direct = false, amps_direct = false, seq_direct = false;
+        uint64_t *keys = nullptr;
+        ah_site *sites = nullptr;
+        float *tm = nullptr;
+        uint8_t *pass = nullptr;
+        ah_amplicon *amps = nullptr;
+        uint64_t *qoff = nullptr;
+        char *seq = nullptr;
+    };
+    struct RunPending {
+        bool active = false, done = false; // done: completed already by ah_run_begin
+        ah_status status = AH_OK;
+        std::string msg;
+        uint32_t set_id = 0;
+        std::vector<uint32_t> pair_ids;
+        ah_run_out *o = nullptr;
+        cudaStream_t st = nullptr;
+        const PairDev *pd = nullptr;
+        FastRun fr;
+    } pend;
+    cudaEvent_t ev_run = nullptr; // recorded after the flag copy of a queued run
     // caching allocator: large blocks released by the library are kept for reuse
     std::map<void *, size_t> live;             // block -> bytes
     std::multimap<size_t, void *> cached;      // bytes -> block
@@ -692,8 +715,10 @@ template <class T> bool deliver(T *user, uint64_t cap, const T *dev, uint64_t co
 // ---------------------------------------------------------------------------
 enum FastResult { kFastDone, kFastKeys, kFastRescan };
 
-FastResult run_fast(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPattern> &pats, const PairDev *pd,
-                    uint32_t n_pairs, ah_run_out *o, cudaStream_t st, uint64_t **keys_out, uint64_t *ns_out)
+// Queue the one-synchronisation form; scan_done (optional) is recorded right
+// after the scan.  The flag block is copied to the host after the last kernel.
+void fast_begin(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPattern> &pats, const PairDev *pd,
+                uint32_t n_pairs, ah_run_out *o, cudaStream_t st, cudaEvent_t scan_done, ah_ctx::FastRun *fr)
 {
     std::unique_ptr<HostSpan> span(new HostSpan(c, "host.run.prep"));
     uint64_t *F = c->d_flags;
@@ -732,6 +757,8 @@ FastResult run_fast(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPatter
         Stage sg(c, "scan", st, 1);
         launch_scan(c, k, gs, gs.n_tiles, keys, c->key_cap, pbits, st);
     }
+    if (scan_done)
+        AH_CUDA(cudaEventRecord(scan_done, st));
     {
         Stage sg(c, "sort", st, 1);
         launch_rank_sort_decode(keys, ns_max, F + kFlagCounter, end_bit - 8 <= 32, pbits, gs.contig_off,
@@ -756,12 +783,29 @@ FastResult run_fast(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPatter
                                F + kFlagRedo, kRedoSeq, st);
         launch_fetch(amps, na_max, F + kFlagAmps, qoff, gs.planes, gs.contig_off, seq, F + kFlagRedo, kRedoSeq, st);
     }
-    span.reset(new HostSpan(c, "host.run.wait"));
-    check_flags(c, st); // the one synchronisation
-    span.reset();
+    AH_CUDA(cudaMemcpyAsync(c->h_flags, c->d_flags, kFlagWords * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    AH_CUDA(cudaEventRecord(c->ev_run, st));
+    *fr = {sites_direct, amps_direct, seq_direct, keys, sites, tm, pass, amps, qoff, seq};
+}
+
+// Wait for a queued one-synchronisation run and complete `o`, or report that
+// a count went above the launch sizes (kFastKeys: the keys are complete).
+FastResult fast_end(ah_ctx *c, ah_run_out *o, cudaStream_t st, const ah_ctx::FastRun &fr, uint64_t **keys_out,
+                    uint64_t *ns_out)
+{
+    {
+        HostSpan span(c, "host.run.wait");
+        AH_CUDA(cudaEventSynchronize(c->ev_run)); // the one synchronisation
+    }
+    c->flags_dirty = false;
     const uint64_t *H = c->h_flags;
+    const int e = (int)(H[kFlagErr] & 0xffffffffu);
+    if (e != 0) {
+        AH_CUDA(cudaMemsetAsync(c->d_flags + kFlagErr, 0, sizeof(uint64_t), st));
+        raise_device_error(e);
+    }
     const uint64_t ns = H[kFlagCounter];
-    *keys_out = keys;
+    *keys_out = fr.keys;
     *ns_out = ns;
     c->last_sites = ns;
     if (H[kFlagRedo])
@@ -770,20 +814,27 @@ FastResult run_fast(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPatter
     o->n_sites = ns;
     o->n_amplicons = na;
     o->n_seq = nq;
-    bool overflow = !deliver(o->sites, o->sites_cap, sites, ns, st);
+    bool overflow = !deliver(o->sites, o->sites_cap, fr.sites, ns, st);
     if (o->tm)
-        overflow |= !deliver(o->tm, o->sites_cap, tm, ns, st);
+        overflow |= !deliver(o->tm, o->sites_cap, fr.tm, ns, st);
     if (o->pass)
-        overflow |= !deliver(o->pass, o->sites_cap, pass, ns, st);
-    overflow |= !deliver(o->amplicons, o->amplicons_cap, amps, na, st);
+        overflow |= !deliver(o->pass, o->sites_cap, fr.pass, ns, st);
+    overflow |= !deliver(o->amplicons, o->amplicons_cap, fr.amps, na, st);
     if (o->seq_offsets)
-        overflow |= !deliver(o->seq_offsets, o->amplicons_cap + 1, qoff, na + 1, st);
-    overflow |= !deliver(o->seq, o->seq_cap, seq, nq, st);
-    if (!(sites_direct && amps_direct && seq_direct)) // copies to host memory land before the call returns
+        overflow |= !deliver(o->seq_offsets, o->amplicons_cap + 1, fr.qoff, na + 1, st);
+    overflow |= !deliver(o->seq, o->seq_cap, fr.seq, nq, st);
+    if (!(fr.sites_direct && fr.amps_direct && fr.seq_direct)) // copies to host memory land before the call returns
         AH_CUDA(cudaStreamSynchronize(st));
     if (overflow)
         throw Error(AH_ERR_OVERFLOW, "ah_run: an output buffer is too small (counts are in the out struct)");
     return kFastDone;
+}
+
+// Calls that touch the context's scratch, pair uploads or flag block wait for
+// no queued run: they return an error while one is pending.
+void require_idle(ah_ctx *c)
+{
+    require(!c->pend.active, AH_ERR_ARG, "a run is pending: complete it with ah_run_end first");
 }
 
 void run_steps(ah_ctx *c, const GenomeSet &gs, const PairDev *pd, uint32_t n_pairs, uint64_t *keys, uint64_t ns,
@@ -925,6 +976,7 @@ ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
         AH_CUDA(cudaMallocHost(&c->h_flags, kFlagWords * sizeof(uint64_t)));
         AH_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
         AH_CUDA(cudaEventCreateWithFlags(&c->pin_ev, cudaEventDisableTiming));
+        AH_CUDA(cudaEventCreateWithFlags(&c->ev_run, cudaEventDisableTiming));
         for (int b = 0; b < 2; ++b) {
             AH_CUDA(cudaEventCreateWithFlags(&c->ev_copied[b], cudaEventDisableTiming));
             AH_CUDA(cudaEventCreateWithFlags(&c->ev_packed[b], cudaEventDisableTiming));
@@ -944,6 +996,8 @@ void ah_destroy(ah_ctx *c)
     if (!c)
         return;
     cudaSetDevice(c->device);
+    if (c->pend.active && !c->pend.done)
+        cudaEventSynchronize(c->ev_run); // a queued run still uses the context's memory
     if (c->stream)
         cudaStreamSynchronize(c->stream);
     for (auto &kv : c->live)
@@ -960,6 +1014,8 @@ void ah_destroy(ah_ctx *c)
         cudaFreeHost(c->pin);
     if (c->pin_ev)
         cudaEventDestroy(c->pin_ev);
+    if (c->ev_run)
+        cudaEventDestroy(c->ev_run);
     for (auto &kv : c->sets)
         if (kv.second->ready)
             cudaEventDestroy(kv.second->ready);
@@ -985,6 +1041,7 @@ ah_status ah_set_profiling(ah_ctx *c, int enable)
     if (!c)
         return AH_ERR_ARG;
     return guarded(c, [&] {
+        require_idle(c);
         AH_CUDA(cudaStreamSynchronize(c->stream));
         prof_flush(c);
         c->prof.clear();
@@ -1079,6 +1136,9 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
         }
         gs->bytes = plane_bytes + (n_contigs + 1) * sizeof(uint64_t) + n_contigs * sizeof(uint32_t);
         const bool dev_seq = n_bases && is_device_ptr(c, seq);
+        // a queued run leaves the flag block and the staging scratch alone only for device input
+        require(dev_seq || !c->pend.active, AH_ERR_ARG,
+                "a run is pending: host input is loaded after ah_run_end (device input may be loaded now)");
         // the packing first (it reads no contig table), then the tables' copies
         if (gs->n_tiles) {
             HostSpan hs_pack(c, "host.load.pack");
@@ -1162,6 +1222,7 @@ ah_status ah_unload_genomes(ah_ctx *c, uint32_t set_id)
     if (!c)
         return AH_ERR_ARG;
     return guarded(c, [&] {
+        require_idle(c);
         HostSpan hs(c, "host.unload");
         GenomeSet &gs = get_set(c, set_id);
         // the calls that read a set synchronise before they return; its packing may not have
@@ -1184,6 +1245,7 @@ ah_status ah_set_primers(ah_ctx *c, const char *fwd, const char *rev, const ah_p
     if (!c)
         return AH_ERR_ARG;
     return guarded(c, [&] {
+        require_idle(c);
         require(fwd && rev && p && pair_id_out, AH_ERR_ARG, "ah_set_primers: null argument");
         PrimerPair pp;
         const char *pr[2] = {fwd, rev};
@@ -1227,6 +1289,7 @@ ah_status ah_set_nn_table(ah_ctx *c, uint32_t pair_id, const ah_nn_table *t)
     if (!c)
         return AH_ERR_ARG;
     return guarded(c, [&] {
+        require_idle(c);
         PrimerPair &pp = get_pair(c, pair_id);
         ++c->pairs_version;
         if (!t) {
@@ -1248,6 +1311,7 @@ ah_status ah_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
     if (!c)
         return AH_ERR_ARG;
     return guarded(c, [&] {
+        require_idle(c);
         require(n_out != nullptr && (cap == 0 || out != nullptr), AH_ERR_ARG, "ah_scan: null output");
         require(pair_ids && n_pairs >= 1 && n_pairs <= AH_MAX_PAIRS_PER_SCAN, AH_ERR_ARG, "n_pairs must be 1..16");
         *n_out = 0;
@@ -1276,6 +1340,7 @@ ah_status ah_tune_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
     if (!c)
         return AH_ERR_ARG;
     return guarded(c, [&] {
+        require_idle(c);
         require(pair_ids && n_pairs >= 1 && n_pairs <= AH_MAX_PAIRS_PER_SCAN, AH_ERR_ARG, "n_pairs must be 1..16");
         GenomeSet &gs = get_set(c, set_id);
         cudaStream_t st = stream_of(c, stream);
@@ -1361,11 +1426,13 @@ ah_status ah_tune_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
     });
 }
 
-ah_status ah_run(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, ah_run_out *o, void *stream)
+ah_status ah_run_begin(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, ah_run_out *o,
+                       void *stream, void *scan_done)
 {
     if (!c)
         return AH_ERR_ARG;
     return guarded(c, [&] {
+        require_idle(c);
         require(o != nullptr, AH_ERR_ARG, "ah_run: out is null");
         require(pair_ids && n_pairs >= 1 && n_pairs <= AH_MAX_PAIRS_PER_SCAN, AH_ERR_ARG, "n_pairs must be 1..16");
         require((o->sites_cap == 0 || o->sites) && (o->amplicons_cap == 0 || o->amplicons) &&
@@ -1378,17 +1445,70 @@ ah_status ah_run(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t 
         wait_ready(gs, st);
         std::vector<ScanPattern> pats = patterns_of(c, pair_ids, n_pairs);
         const PairDev *pd = upload_pairs(c, pair_ids, n_pairs, st);
+        ah_ctx::RunPending &P = c->pend;
+        P = ah_ctx::RunPending();
+        P.set_id = set_id;
+        P.pair_ids.assign(pair_ids, pair_ids + n_pairs);
+        P.o = o;
+        P.st = st;
+        P.pd = pd;
+        if (gs.n_tiles && c->last_sites <= kSmallSort) {
+            fast_begin(c, gs, pats, pd, n_pairs, o, st, (cudaEvent_t)scan_done, &P.fr);
+            P.active = true;
+            return;
+        }
+        // counts above the one-synchronisation sizes (seen in the last run): step by step, now
+        uint64_t *keys = nullptr;
+        const uint64_t ns = scan_keys(c, gs, pats, &keys, st);
+        if (scan_done)
+            AH_CUDA(cudaEventRecord((cudaEvent_t)scan_done, st));
+        try {
+            run_steps(c, gs, pd, n_pairs, keys, ns, o, st);
+        } catch (const Error &e) {
+            if (e.status != AH_ERR_OVERFLOW)
+                throw;
+            P.status = e.status; // reported by ah_run_end, like the counts
+            P.msg = e.msg;
+        }
+        P.active = P.done = true;
+    });
+}
+
+ah_status ah_run_end(ah_ctx *c)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require(c->pend.active, AH_ERR_ARG, "ah_run_end: no run is pending");
+        const ah_ctx::RunPending P = c->pend;
+        c->pend.active = false; // completed or failed, it is no longer pending
+        HostSpan hs(c, "host.run");
+        if (P.done) {
+            if (P.status != AH_OK)
+                throw Error(P.status, P.msg);
+            return;
+        }
+        GenomeSet &gs = get_set(c, P.set_id);
+        const uint32_t n_pairs = (uint32_t)P.pair_ids.size();
         uint64_t *keys = nullptr;
         uint64_t ns = 0;
-        FastResult r = kFastRescan;
-        if (gs.n_tiles && c->last_sites <= kSmallSort)
-            r = run_fast(c, gs, pats, pd, n_pairs, o, st, &keys, &ns);
+        const FastResult r = fast_end(c, P.o, P.st, P.fr, &keys, &ns);
         if (r == kFastDone)
             return;
-        if (r == kFastRescan)
-            ns = scan_keys(c, gs, pats, &keys, st);
-        run_steps(c, gs, pd, n_pairs, keys, ns, o, st);
+        if (r == kFastRescan) {
+            std::vector<ScanPattern> pats = patterns_of(c, P.pair_ids.data(), n_pairs);
+            ns = scan_keys(c, gs, pats, &keys, P.st);
+        }
+        run_steps(c, gs, P.pd, n_pairs, keys, ns, P.o, P.st);
     });
+}
+
+ah_status ah_run(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, ah_run_out *o, void *stream)
+{
+    const ah_status st = ah_run_begin(c, set_id, pair_ids, n_pairs, o, stream, nullptr);
+    if (st != AH_OK)
+        return st;
+    return ah_run_end(c);
 }
 
 ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, const ah_site *sites,
@@ -1397,6 +1517,7 @@ ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n
     if (!c)
         return AH_ERR_ARG;
     return guarded(c, [&] {
+        require_idle(c);
         require(n == 0 || (sites && tm_out), AH_ERR_ARG, "ah_tm: null argument");
         GenomeSet &gs = get_set(c, set_id);
         cudaStream_t st = stream_of(c, stream);
@@ -1433,6 +1554,7 @@ ah_status ah_pair(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t
     if (!c)
         return AH_ERR_ARG;
     return guarded(c, [&] {
+        require_idle(c);
         require(n_out && (cap == 0 || out) && (n == 0 || sites), AH_ERR_ARG, "ah_pair: null argument");
         *n_out = 0;
         GenomeSet &gs = get_set(c, set_id);
@@ -1485,6 +1607,7 @@ ah_status ah_fetch(ah_ctx *c, uint32_t set_id, const ah_amplicon *amplicons, uin
     if (!c)
         return AH_ERR_ARG;
     return guarded(c, [&] {
+        require_idle(c);
         require(offsets_out && (n == 0 || amplicons) && (cap == 0 || seq_out), AH_ERR_ARG, "ah_fetch: null argument");
         GenomeSet &gs = get_set(c, set_id);
         cudaStream_t st = stream_of(c, stream);

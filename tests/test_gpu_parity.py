@@ -452,3 +452,55 @@ def test_run_past_the_one_synchronisation_sizes(ctx, case):
     r = ctx.run(sid, [pid], tm_filter=False)
     assert r["sites"].tobytes() == ot["sites"].tobytes() and r["amps"].tobytes() == ot["amps"].tobytes()
     ctx.ah_unload_genomes(sid)
+
+
+def test_run_begin_end_pipeline(ctx):
+    """ah_run_begin / ah_run_end give ah_run's records; while a run is pending
+    other calls are refused; three sets run as a pipeline (the next set packs on
+    a second stream after the current scan) each match the oracle."""
+    import torch
+    ws = [synth.collection(seed=s, n_genomes=2, len_lo=3e5, len_hi=6e5) for s in (4, 5, 6)]
+    for w in ws:
+        w.pairs = [dict(w.pairs[0], tm_min=50.0)]
+    p = ws[0].pairs[0]
+    pid = ctx.ah_set_primers(p["fwd"], p["rev"], p)
+    want = []
+    for w in ws:
+        o = oracle_run(w)
+        seqs, offs = oracle.fetch(w.seq, w.contig_off, o["amps_tm"])
+        want.append((o, seqs, offs))
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    scan_done = torch.cuda.Event()
+    dev = [torch.from_numpy(w.seq).cuda() for w in ws]
+    torch.cuda.synchronize()
+    cap = 20000
+    u8 = dict(dtype=torch.uint8, device="cuda")
+    b = dict(sites=torch.zeros(cap * 16, **u8), tm=torch.zeros(cap, dtype=torch.float32, device="cuda"),
+             ps=torch.zeros(cap, **u8), amps=torch.zeros(cap * 28, **u8), seq=torch.zeros(1 << 22, **u8),
+             offs=torch.zeros(cap + 1, dtype=torch.int64, device="cuda"))
+    out = ah.RunOut(b["sites"].data_ptr(), cap, 0, b["tm"].data_ptr(), b["ps"].data_ptr(), b["amps"].data_ptr(), cap,
+                    0, b["seq"].data_ptr(), 1 << 22, 0, b["offs"].data_ptr(), 1, 0)
+    prev = ctx.ah_load_genomes(dev[0], len(ws[0].seq), ws[0].contig_off, ws[0].contig_genome, streams[0])
+    for i, w in enumerate(ws):
+        ctx.ah_run_begin(prev, [pid], out, streams[i % 2], scan_done)
+        with pytest.raises(ah.AHError) as e:  # refused while the run is pending
+            ctx.ah_scan(prev, [pid], None, 0)
+        assert e.value.status == ah.AH_ERR_ARG
+        nxt = None
+        if i + 1 < len(ws):
+            streams[(i + 1) % 2].wait_event(scan_done)
+            nxt = ctx.ah_load_genomes(dev[i + 1], len(ws[i + 1].seq), ws[i + 1].contig_off,
+                                      ws[i + 1].contig_genome, streams[(i + 1) % 2])
+        ctx.ah_run_end(out)
+        torch.cuda.synchronize()
+        o, seqs, offs = want[i]
+        n, m, q = out.n_sites, out.n_amplicons, out.n_seq
+        assert b["sites"][:16 * n].cpu().numpy().tobytes() == o["sites"].tobytes()
+        assert np.array_equal(b["ps"][:n].cpu().numpy(), o["pass_"])
+        assert b["amps"][:28 * m].cpu().numpy().tobytes() == o["amps_tm"].tobytes() and m > 0
+        assert b["seq"][:q].cpu().numpy().tobytes() == seqs
+        assert np.array_equal(b["offs"][:m + 1].cpu().numpy().astype(np.uint64), offs)
+        ctx.ah_unload_genomes(prev)
+        prev = nxt
+    with pytest.raises(ah.AHError):  # nothing pending
+        ctx.ah_run_end(out)
