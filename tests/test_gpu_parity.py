@@ -460,8 +460,9 @@ def test_run_begin_end_pipeline(ctx):
     a second stream after the current scan) each match the oracle."""
     import torch
     ws = [synth.collection(seed=s, n_genomes=2, len_lo=3e5, len_hi=6e5) for s in (4, 5, 6)]
+    pair = dict(ws[0].pairs[0], tm_min=50.0)  # one pair for every set (the generator draws one per seed)
     for w in ws:
-        w.pairs = [dict(w.pairs[0], tm_min=50.0)]
+        w.pairs = [pair]
     p = ws[0].pairs[0]
     pid = ctx.ah_set_primers(p["fwd"], p["rev"], p)
     want = []
