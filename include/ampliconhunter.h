@@ -186,6 +186,19 @@ size_t ah_device_bytes(const ah_ctx *ctx);
 ah_status ah_load_genomes(ah_ctx *ctx, const uint8_t *seq, uint64_t n_bases, const uint64_t *contig_off,
                           uint32_t n_contigs, const uint32_t *contig_genome, uint32_t *set_id_out, void *stream);
 
+/* ah_load_genomes with options.  flags: AH_LOAD_REVERSED packs every contig
+ * reversed, not complemented (position p of contig c holds the base at
+ * len_c - 1 - p of the input contig): the decoy collection of Sec. 2.1
+ * (Amplicon analysis: decoy genomes estimate the off-target rate as decoy
+ * amplicons / real amplicons).  Every later call on the set works on the
+ * reversed contigs, in their own coordinates.  A reversed load always waits
+ * for its packing before it returns.  Unknown flag bits: AH_ERR_ARG.
+ * Other arguments, ownership and errors as ah_load_genomes. */
+#define AH_LOAD_REVERSED 1u
+ah_status ah_load_genomes_ex(ah_ctx *ctx, const uint8_t *seq, uint64_t n_bases, const uint64_t *contig_off,
+                             uint32_t n_contigs, const uint32_t *contig_genome, uint32_t flags, uint32_t *set_id_out,
+                             void *stream);
+
 /* Free a loaded genome set (after its packing has run).  AH_ERR_ARG for an
  * unknown id; AH_ERR_TIMEOUT for a packing that failed on the device and was
  * not reported before (the set is freed either way). */

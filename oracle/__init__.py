@@ -186,6 +186,16 @@ def fetch(seq, contig_off, amplicons: np.ndarray):
     return out[:total].tobytes(), offsets
 
 
+def reverse_contigs(seq: np.ndarray, contig_off: np.ndarray) -> np.ndarray:
+    """The decoy collection (Sec. 2.1, Amplicon analysis): every contig reversed,
+    not complemented, in place of the original; contig offsets unchanged."""
+    seq = np.asarray(seq, dtype=np.uint8)
+    out = np.empty_like(seq)
+    for a, b in zip(contig_off[:-1], contig_off[1:]):
+        out[int(a):int(b)] = seq[int(a):int(b)][::-1]
+    return out
+
+
 def window_mismatches(window: bytes, primer: str, strand: int) -> int:
     buf = np.frombuffer(window, dtype=np.uint8).copy()
     return _load().or_window_mismatches(_ptr(buf), primer.encode(), strand)

@@ -20,6 +20,7 @@ AH_OK, AH_ERR_ARG, AH_ERR_PRIMER, AH_ERR_OOM, AH_ERR_BUDGET, AH_ERR_OVERFLOW, AH
 STATUS_NAMES = {0: "AH_OK", 1: "AH_ERR_ARG", 2: "AH_ERR_PRIMER", 3: "AH_ERR_OOM", 4: "AH_ERR_BUDGET",
                 5: "AH_ERR_OVERFLOW", 6: "AH_ERR_CUDA", 7: "AH_ERR_TIMEOUT", 8: "AH_ERR_JIT",
                 9: "AH_ERR_DEVICE_CHECK"}
+AH_LOAD_REVERSED = 1  # ah_load_genomes_ex flag: contigs packed reversed (decoy genomes)
 
 SITE_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("pos", "<u4"), ("primer", "u1"),
                        ("strand", "u1"), ("mm", "u1"), ("pair", "u1")])
@@ -30,7 +31,8 @@ AMPLICON_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("start", "<u4"
 # Every symbol include/ampliconhunter.h declares.
 EXPORTS = ["ah_create", "ah_destroy", "ah_last_error", "ah_device_bytes", "ah_load_genomes", "ah_unload_genomes",
            "ah_set_primers", "ah_set_nn_table", "ah_scan", "ah_tm", "ah_pair", "ah_fetch", "ah_set_profiling",
-           "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan", "ah_run", "ah_run_begin", "ah_run_end"]
+           "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan", "ah_run", "ah_run_begin", "ah_run_end",
+           "ah_load_genomes_ex"]
 
 
 class AHError(RuntimeError):
@@ -95,6 +97,7 @@ def lib():
             "ah_last_error": (ctypes.c_char_p, [P]),
             "ah_device_bytes": (S, [P]),
             "ah_load_genomes": (I32, [P, P, U64, P, U32, P, ctypes.POINTER(U32), P]),
+            "ah_load_genomes_ex": (I32, [P, P, U64, P, U32, P, U32, ctypes.POINTER(U32), P]),
             "ah_unload_genomes": (I32, [P, U32]),
             "ah_set_primers": (I32, [P, ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(PcrParams),
                                      ctypes.POINTER(U32)]),
@@ -205,12 +208,14 @@ class Context:
         return ms.value, l.value, k.value
 
     def ah_load_genomes(self, seq, n_bases: int, contig_off: np.ndarray, contig_genome: np.ndarray,
-                        stream=None) -> int:
+                        stream=None, reversed: bool = False) -> int:
+        """reversed: pack every contig reversed (the decoy collection)."""
         contig_off = np.ascontiguousarray(contig_off, dtype=np.uint64)
         contig_genome = np.ascontiguousarray(contig_genome, dtype=np.uint32)
         sid = ctypes.c_uint32()
-        self._check(self._lib.ah_load_genomes(self.h, _ptr(seq), n_bases, _ptr(contig_off), len(contig_off) - 1,
-                                              _ptr(contig_genome), ctypes.byref(sid), _stream(stream)))
+        self._check(self._lib.ah_load_genomes_ex(self.h, _ptr(seq), n_bases, _ptr(contig_off), len(contig_off) - 1,
+                                                 _ptr(contig_genome), AH_LOAD_REVERSED if reversed else 0,
+                                                 ctypes.byref(sid), _stream(stream)))
         return sid.value
 
     def ah_unload_genomes(self, set_id: int):
@@ -306,9 +311,9 @@ class Context:
                                        _stream(stream)))
 
     # ------------------------------------------------ numpy conveniences (host buffers)
-    def load(self, seq: np.ndarray, contig_off, contig_genome, stream=None) -> int:
+    def load(self, seq: np.ndarray, contig_off, contig_genome, stream=None, reversed: bool = False) -> int:
         n = int(contig_off[-1])
-        return self.ah_load_genomes(seq, n, contig_off, contig_genome, stream)
+        return self.ah_load_genomes(seq, n, contig_off, contig_genome, stream, reversed)
 
     def scan(self, set_id: int, pair_ids) -> np.ndarray:
         """Sites as a numpy structured array (size query, then the call)."""

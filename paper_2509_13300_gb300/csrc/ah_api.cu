@@ -1102,10 +1102,19 @@ size_t ah_device_bytes(const ah_ctx *c) { return c ? c->used : 0; }
 ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const uint64_t *contig_off,
                           uint32_t n_contigs, const uint32_t *contig_genome, uint32_t *set_id_out, void *stream)
 {
+    return ah_load_genomes_ex(c, seq, n_bases, contig_off, n_contigs, contig_genome, 0, set_id_out, stream);
+}
+
+ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const uint64_t *contig_off,
+                             uint32_t n_contigs, const uint32_t *contig_genome, uint32_t flags, uint32_t *set_id_out,
+                             void *stream)
+{
     if (!c)
         return AH_ERR_ARG;
     return guarded(c, [&] {
         HostSpan hs(c, "host.load");
+        require((flags & ~AH_LOAD_REVERSED) == 0, AH_ERR_ARG, "ah_load_genomes_ex: unknown flag bits");
+        const bool reversed = (flags & AH_LOAD_REVERSED) != 0;
         require(set_id_out && contig_off && contig_genome && n_contigs >= 1, AH_ERR_ARG,
                 "ah_load_genomes: null argument or no contigs");
         require(n_bases == 0 || seq, AH_ERR_ARG, "ah_load_genomes: seq is null");
@@ -1137,10 +1146,37 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
         gs->bytes = plane_bytes + (n_contigs + 1) * sizeof(uint64_t) + n_contigs * sizeof(uint32_t);
         const bool dev_seq = n_bases && is_device_ptr(c, seq);
         // a queued run leaves the flag block and the staging scratch alone only for device input
-        require(dev_seq || !c->pend.active, AH_ERR_ARG,
-                "a run is pending: host input is loaded after ah_run_end (device input may be loaded now)");
+        require((dev_seq && !reversed) || !c->pend.active, AH_ERR_ARG,
+                "a run is pending: host input and reversed sets are loaded after ah_run_end");
         // the packing first (it reads no contig table), then the tables' copies
-        if (gs->n_tiles) {
+        std::vector<void *> temp; // freed once the packing is done (reversed loads)
+        if (gs->n_tiles && reversed) {
+            HostSpan hs_pack(c, "host.load.pack");
+            // decoy: the input on the device, reversed contig by contig, then packed
+            const uint8_t *src = seq;
+            if (!dev_seq) {
+                uint8_t *d = (uint8_t *)dev_alloc(c, n_bases);
+                temp.push_back(d);
+                AH_CUDA(cudaMemcpyAsync(d, seq, n_bases, cudaMemcpyHostToDevice, st));
+                src = d;
+            }
+            uint8_t *dst = (uint8_t *)dev_alloc(c, n_bases);
+            temp.push_back(dst);
+            const uint64_t kStretch = 1ull << 16;
+            std::vector<RevChunk> ch;
+            ch.reserve(n_bases / kStretch + n_contigs);
+            for (uint32_t i = 0; i < n_contigs; ++i) {
+                const uint64_t o = contig_off[i], len = contig_off[i + 1] - o;
+                for (uint64_t q = 0; q < len; q += kStretch)
+                    ch.push_back({o + q, 2 * o + len - 1, std::min(kStretch, len - q)});
+            }
+            RevChunk *ch_d = (RevChunk *)dev_alloc(c, std::max<size_t>(ch.size(), 1) * sizeof(RevChunk));
+            temp.push_back(ch_d);
+            AH_CUDA(cudaMemcpyAsync(ch_d, ch.data(), ch.size() * sizeof(RevChunk), cudaMemcpyHostToDevice, st));
+            launch_reverse_contigs(src, dst, ch_d, ch.size(), st);
+            Stage sg(c, "pack", st, 1);
+            launch_pack(dst, 0, n_bases, n_bases, gs->planes, 0, gs->n_tiles, c->d_err, st);
+        } else if (gs->n_tiles) {
             HostSpan hs_pack(c, "host.load.pack");
             if (dev_seq) {
                 // stream-ordered: the pack runs after the caller's earlier work on
@@ -1207,10 +1243,19 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
         gs->ready = c->set_events.back();
         c->set_events.pop_back();
         AH_CUDA(cudaEventRecord(gs->ready, st));
-        if (!dev_seq) // the caller's host buffer may be reused once this call returns
-            check_flags(c, st);
-        else
+        if (!dev_seq || reversed) { // the caller's host buffer may be reused once this call returns
+            try {
+                check_flags(c, st);
+            } catch (...) {
+                for (void *q : temp)
+                    dev_free(c, q, 0);
+                throw;
+            }
+            for (void *q : temp) // the packing is done: the temporaries go back to the cache
+                dev_free(c, q, 0);
+        } else {
             c->flags_dirty = true;
+        }
         uint32_t id = c->next_set++;
         c->sets[id] = std::move(gs);
         *set_id_out = id;

@@ -130,6 +130,14 @@ ScanKernel *scan_kernel(const std::vector<ScanPattern> &pats, const ScanTuning &
 // [seq_base, seq_base + seq_len) of a set of n_bases bases.
 void launch_pack(const uint8_t *seq, uint64_t seq_base, uint64_t seq_len, uint64_t n_bases, uint32_t *planes,
                  uint64_t t0, uint64_t t1, int *err, cudaStream_t s);
+// One stretch of a contig-wise reversal: dst[k] = src[mirror - k] for k in
+// [start, start + len) (mirror = 2 * contig start + contig length - 1).
+struct RevChunk {
+    uint64_t start, mirror;
+    uint64_t len;
+};
+void launch_reverse_contigs(const uint8_t *src, uint8_t *dst, const RevChunk *chunks, uint64_t n_chunks,
+                            cudaStream_t s);
 void launch_unpack_check(const uint32_t *planes, uint64_t n_tiles, uint8_t *codes, uint64_t n_bases,
                          cudaStream_t s);
 

@@ -276,6 +276,33 @@ void launch_pack(const uint8_t *seq, uint64_t seq_base, uint64_t seq_len, uint64
     AH_CUDA(cudaGetLastError());
 }
 
+namespace {
+
+// Contig-wise reversal of the ASCII input (decoy genomes): one block per
+// stretch; consecutive threads read consecutive (descending) source bytes.
+__global__ void reverse_contigs_kernel(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
+                                       const RevChunk *__restrict__ chunks)
+{
+    const RevChunk c = chunks[blockIdx.x];
+    for (uint64_t i = threadIdx.x; i < c.len; i += blockDim.x) {
+        const uint64_t k = c.start + i;
+        dst[k] = src[c.mirror - k];
+    }
+}
+
+} // namespace
+
+void launch_reverse_contigs(const uint8_t *src, uint8_t *dst, const RevChunk *chunks, uint64_t n_chunks,
+                            cudaStream_t s)
+{
+    if (n_chunks == 0)
+        return;
+    if (n_chunks > 0x7fffffffull)
+        throw Error(AH_ERR_ARG, "reversal: too many stretches");
+    reverse_contigs_kernel<<<(unsigned)n_chunks, 256, 0, s>>>(src, dst, chunks);
+    AH_CUDA(cudaGetLastError());
+}
+
 void launch_unpack_check(const uint32_t *planes, uint64_t n_tiles, uint8_t *codes, uint64_t n_bases, cudaStream_t s)
 {
     (void)n_tiles;

@@ -508,3 +508,38 @@ def test_run_begin_end_pipeline(ctx):
     assert total_amps > 0  # the first set carries planted amplicons of this pair
     with pytest.raises(ah.AHError):  # nothing pending
         ctx.ah_run_end(out)
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_decoy_sets_on_reversed_contigs(ctx, on_device):
+    """A reversed (decoy) load gives, through every call and ah_run, the oracle's
+    records on the contig-wise reversed collection; the off-target rate is the
+    ratio of decoy to real amplicons."""
+    import torch
+    w = synth.collection(seed=2, n_genomes=4, len_lo=3e5, len_hi=9e5)
+    w.pairs = [dict(w.pairs[0], tm_min=40.0)]
+    rev = oracle.reverse_contigs(w.seq, w.contig_off)
+    wr = synth.Workload(**{**w.__dict__, "seq": rev})
+    o = oracle_run(wr)
+    seq_in = torch.from_numpy(w.seq).cuda() if on_device else w.seq
+    sid = ctx.ah_load_genomes(seq_in, len(w.seq), w.contig_off, w.contig_genome, reversed=True)
+    try:
+        pid = ctx.ah_set_primers(w.pairs[0]["fwd"], w.pairs[0]["rev"], w.pairs[0])
+        sites = ctx.scan(sid, [pid])
+        assert sites.tobytes() == o["sites"].tobytes() and len(sites) > 0
+        tm, ps = ctx.tm(sid, [pid], sites)
+        assert np.array_equal(ps, o["pass_"])
+        ok = ~np.isnan(o["tm"])
+        assert np.abs(tm[ok] - o["tm"][ok]).max() <= TM_TOL
+        amps = ctx.pair(sid, [pid], sites)
+        assert amps.tobytes() == o["amps"].tobytes()
+        seqs, offs = ctx.fetch(sid, amps)
+        assert seqs == o["seqs"] and np.array_equal(offs, o["offs"])
+        r = ctx.run(sid, [pid], tm_filter=True)
+        assert r["amps"].tobytes() == o["amps_tm"].tobytes()
+    finally:
+        ctx.ah_unload_genomes(sid)
+    real = oracle.pair(oracle.scan(w.seq, w.contig_off, w.contig_genome, w.pairs), w.pairs)
+    assert len(real) > 0
+    rate = len(o["amps"]) / len(real)  # the off-target estimate this load supports
+    assert 0.0 <= rate

@@ -447,3 +447,23 @@ def test_degeneracy_of_paper_primers():
     assert oracle.degeneracy(w.pairs[0]["fwd"]) + oracle.degeneracy(w.pairs[0]["rev"]) == 960
     t = synth.tiny(0)
     assert oracle.degeneracy(t.pairs[0]["fwd"]) + oracle.degeneracy(t.pairs[0]["rev"]) == 48
+
+
+def test_decoy_reversal_is_per_contig_reversal():
+    """The decoy collection reverses each contig (not complemented): twice is the
+    identity, each contig equals the original read backwards, and a site of a
+    palindromic primer pair on the reversed contig sits at the mirrored position."""
+    w = synth.random_small(5, n_bases=3000, n_contigs=4)
+    r = oracle.reverse_contigs(w.seq, w.contig_off)
+    assert np.array_equal(oracle.reverse_contigs(r, w.contig_off), w.seq)
+    for a, b in zip(w.contig_off[:-1], w.contig_off[1:]):
+        assert bytes(r[int(a):int(b)]) == bytes(w.seq[int(a):int(b)])[::-1]
+    # a pattern equal to its own reverse (ACGGCA reversed is ACGGCA) is found at p and at len - L - p
+    pal = "ACGGCA"
+    pair = synth.pcr_params(pal, pal, k=0, min_len=10, max_len=100)
+    fw = oracle.scan(w.seq, w.contig_off, w.contig_genome, [pair])
+    rv = oracle.scan(r, w.contig_off, w.contig_genome, [pair])
+    lens = np.diff(w.contig_off.astype(np.int64))
+    mir = sorted((int(s["contig"]), int(lens[s["contig"]] - 6 - s["pos"]), int(s["primer"]), int(s["strand"])) for s in fw)
+    got = sorted((int(s["contig"]), int(s["pos"]), int(s["primer"]), int(s["strand"])) for s in rv)
+    assert mir == got
