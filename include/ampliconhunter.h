@@ -348,6 +348,29 @@ ah_status ah_run_begin(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, u
                        void *stream, void *scan_done);
 ah_status ah_run_end(ah_ctx *ctx);
 
+/* Tm-threshold sweep (Sec. 3.3, Annealing Temperature Optimization: how the
+ * number of amplicons, the share of genomes amplified and the off-target
+ * pattern counts move with the minimum annealing temperature).  sites (host
+ * or device): n_sites records of the set and pairs, as ah_scan returns them;
+ * amplicons (host or device): the set's amplicons called on those sites
+ * without a Tm filter (ah_pair with pass = NULL), whose left/right fields
+ * index `sites`.  thresholds (host): n_thresholds (1..64) values in deg C.
+ * For threshold j, an amplicon counts when both of its sites pass, a site
+ * passing when its maximum Tm over the primer's oligos is >= thresholds[j],
+ * decided as the fp64 definition decides (as ah_tm's pass flag).  rows (host
+ * or device): per threshold, the amplicons, those with orientation FF or RR,
+ * and the genomes with at least one amplicon; *n_genomes_out: the set's
+ * distinct genomes (the denominator of the share amplified).
+ * Errors: AH_ERR_ARG (bad records or thresholds), AH_ERR_CUDA. */
+typedef struct {
+    uint64_t amplicons;
+    uint64_t ff_rr;
+    uint64_t genomes_amplified;
+} ah_sweep_row;
+ah_status ah_tm_sweep(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, const ah_site *sites,
+                      uint64_t n_sites, const ah_amplicon *amplicons, uint64_t n_amplicons, const double *thresholds,
+                      uint32_t n_thresholds, ah_sweep_row *rows, uint64_t *n_genomes_out, void *stream);
+
 /* Measurement: per-stage device time, host time and kernel launches.
  * ah_set_profiling clears the counters; enable = 1 then brackets each stage
  * of each call with CUDA events on the stream the stage runs on and times

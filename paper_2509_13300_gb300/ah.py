@@ -32,7 +32,7 @@ AMPLICON_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("start", "<u4"
 EXPORTS = ["ah_create", "ah_destroy", "ah_last_error", "ah_device_bytes", "ah_load_genomes", "ah_unload_genomes",
            "ah_set_primers", "ah_set_nn_table", "ah_scan", "ah_tm", "ah_pair", "ah_fetch", "ah_set_profiling",
            "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan", "ah_run", "ah_run_begin", "ah_run_end",
-           "ah_load_genomes_ex"]
+           "ah_load_genomes_ex", "ah_tm_sweep"]
 
 
 class AHError(RuntimeError):
@@ -111,6 +111,7 @@ def lib():
                                      ctypes.POINTER(U64)]),
             "ah_run": (I32, [P, U32, P, U32, ctypes.POINTER(RunOut), P]),
             "ah_run_begin": (I32, [P, U32, P, U32, ctypes.POINTER(RunOut), P, P]),
+            "ah_tm_sweep": (I32, [P, U32, P, U32, P, U64, P, U64, P, U32, P, ctypes.POINTER(U64), P]),
             "ah_run_end": (I32, [P]),
             "ah_tune_scan": (I32, [P, U32, P, U32, U64, ctypes.POINTER(TuneResult), P]),
             "ah_pair_noalloc": (I32, [P, U32, P, P, U64, P, U64, ctypes.POINTER(U64), P]),
@@ -257,6 +258,19 @@ class Context:
             else:
                 ev = ctypes.c_void_p(int(scan_done))
         self._check(self._lib.ah_run_begin(self.h, set_id, _ptr(ids), len(ids), ctypes.byref(out), _stream(stream), ev))
+
+    def ah_tm_sweep(self, set_id: int, pair_ids, sites, amplicons, thresholds, stream=None):
+        """Per threshold: (amplicons, FF/RR amplicons, genomes amplified), and the set's genome count."""
+        ids = np.ascontiguousarray(pair_ids, dtype=np.uint32)
+        thr = np.ascontiguousarray(thresholds, dtype=np.float64)
+        rows = np.zeros((len(thr), 3), dtype=np.uint64)
+        ng = ctypes.c_uint64()
+        n_s = len(sites) if isinstance(sites, np.ndarray) else sites.numel() // 16
+        n_a = len(amplicons) if isinstance(amplicons, np.ndarray) else amplicons.numel() // 28
+        self._check(self._lib.ah_tm_sweep(self.h, set_id, _ptr(ids), len(ids), _ptr(sites) if n_s else None, n_s,
+                                          _ptr(amplicons) if n_a else None, n_a, _ptr(thr), len(thr), _ptr(rows),
+                                          ctypes.byref(ng), _stream(stream)))
+        return rows, ng.value
 
     def ah_run_end(self, out: RunOut) -> RunOut:
         self._check(self._lib.ah_run_end(self.h), out.n_sites)

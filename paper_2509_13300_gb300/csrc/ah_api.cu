@@ -1131,6 +1131,12 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
         gs->n_bases = n_bases;
         gs->n_contigs = n_contigs;
         gs->n_tiles = (n_bases + kTileBases - 1) / kTileBases;
+        {
+            std::vector<uint32_t> ids(contig_genome, contig_genome + n_contigs);
+            std::sort(ids.begin(), ids.end());
+            gs->max_genome = ids.back();
+            gs->n_genomes = (uint64_t)(std::unique(ids.begin(), ids.end()) - ids.begin());
+        }
         const size_t plane_bytes = gs->n_tiles * kTileBytes;
         HostSpan hs_alloc(c, "host.load.alloc");
         try {
@@ -1554,6 +1560,62 @@ ah_status ah_run(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t 
     if (st != AH_OK)
         return st;
     return ah_run_end(c);
+}
+
+ah_status ah_tm_sweep(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, const ah_site *sites,
+                      uint64_t n_sites, const ah_amplicon *amplicons, uint64_t n_amplicons, const double *thresholds,
+                      uint32_t n_thresholds, ah_sweep_row *rows, uint64_t *n_genomes_out, void *stream)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require_idle(c);
+        require(thresholds && rows && n_genomes_out && (n_sites == 0 || sites) && (n_amplicons == 0 || amplicons),
+                AH_ERR_ARG, "ah_tm_sweep: null argument");
+        require(n_thresholds >= 1 && n_thresholds <= (uint32_t)kSweepThresholds, AH_ERR_ARG,
+                "ah_tm_sweep: 1..64 thresholds");
+        for (uint32_t j = 0; j < n_thresholds; ++j)
+            require(std::isfinite(thresholds[j]), AH_ERR_ARG, "ah_tm_sweep: thresholds must be finite");
+        GenomeSet &gs = get_set(c, set_id);
+        cudaStream_t st = stream_of(c, stream);
+        wait_ready(gs, st);
+        const PairDev *pd = upload_pairs(c, pair_ids, n_pairs, st);
+        *n_genomes_out = gs.n_genomes;
+        reset_flags(c, st);
+        const ah_site *s = stage_in(c, "sweep_sites_in", sites, n_sites, st);
+        const ah_amplicon *a = stage_in(c, "sweep_amps_in", amplicons, n_amplicons, st);
+        if (n_sites) {
+            Stage sg(c, "validate", st, 1);
+            launch_validate_sites(s, n_sites, pd, (int)n_pairs, gs.contig_off, gs.n_contigs, c->d_err, st);
+        }
+        check_flags(c, st);
+        float *tm = (float *)scratch(c, "sweep_tm", std::max<uint64_t>(n_sites, 1) * sizeof(float));
+        if (n_sites) {
+            Stage sg(c, "tm", st, 2);
+            uint32_t *q = (uint32_t *)scratch(c, "tm_queue", n_sites * sizeof(uint32_t));
+            launch_tm(s, n_sites, nullptr, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, nullptr, q,
+                      (uint32_t *)(c->d_flags + kFlagTmQueue), tm_seg_max(c), tm_few_exact(c), c->d_err, st);
+        }
+        double *thr_d = (double *)scratch(c, "sweep_thr", kSweepThresholds * sizeof(double));
+        AH_CUDA(cudaMemcpyAsync(thr_d, thresholds, n_thresholds * sizeof(double), cudaMemcpyHostToDevice, st));
+        long long *W = (long long *)scratch(c, "sweep_w", (size_t)n_pairs * n_thresholds * 272 * sizeof(long long));
+        uint64_t *mask = (uint64_t *)scratch(c, "sweep_mask", std::max<uint64_t>(n_sites, 1) * sizeof(uint64_t));
+        auto *gmask = (unsigned long long *)scratch(c, "sweep_gmask", ((uint64_t)gs.max_genome + 1) * 8);
+        auto *counts = (unsigned long long *)scratch(c, "sweep_counts", 3 * kSweepThresholds * 8);
+        {
+            Stage sg(c, "sweep", st, 4);
+            launch_tm_sweep(s, n_sites, a, n_amplicons, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, thr_d,
+                            (int)n_thresholds, W, tm_few_exact(c), mask, gmask, gs.max_genome, counts, c->d_err, st);
+        }
+        std::vector<unsigned long long> h(3 * kSweepThresholds);
+        AH_CUDA(cudaMemcpyAsync(h.data(), counts, h.size() * 8, cudaMemcpyDeviceToHost, st));
+        check_flags(c, st); // also waits for the copy
+        std::vector<ah_sweep_row> r(n_thresholds);
+        for (uint32_t j = 0; j < n_thresholds; ++j)
+            r[j] = {h[j], h[kSweepThresholds + j], h[2 * kSweepThresholds + j]};
+        AH_CUDA(cudaMemcpyAsync(rows, r.data(), n_thresholds * sizeof(ah_sweep_row), cudaMemcpyDefault, st));
+        AH_CUDA(cudaStreamSynchronize(st));
+    });
 }
 
 ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, const ah_site *sites,

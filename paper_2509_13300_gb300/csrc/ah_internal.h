@@ -45,6 +45,8 @@ struct GenomeSet {
     // recorded after the work that fills the set (the packing); every call that
     // reads the set waits for it on its own stream, and unloading waits for it
     cudaEvent_t ready = nullptr;
+    uint32_t max_genome = 0; // largest genome id
+    uint64_t n_genomes = 0;  // distinct genome ids
 };
 
 // One registered primer pair.  mask[i] is the 4-bit IUPAC set of primer
@@ -223,6 +225,19 @@ struct PairDev {
 void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const PairDev *pairs_d, int n_pairs, const uint32_t *planes,
                const uint64_t *contig_off, float *tm_out, uint8_t *pass_out, uint32_t *queue, uint32_t *queue_n,
                int seg_max, bool few_exact, int *err, cudaStream_t s);
+
+// Tm-threshold sweep (tm.cu): per-site pass bits for n_thr <= 64 thresholds
+// (thr_d: deg C, device), then per threshold the amplicons whose two sites
+// pass, those with orientation FF or RR, and the genomes with at least one.
+// counts: 192 device words ([0, 64) amplicons, [64, 128) FF/RR, [128, 192)
+// genomes); W: n_pairs * n_thr * 272 words; pass_mask: n_sites words; gmask:
+// max_genome + 1 words.  tm: the sites' fp32 maxima (launch_tm).
+constexpr int kSweepThresholds = 64;
+void launch_tm_sweep(const ah_site *sites, uint64_t n_sites, const ah_amplicon *amps, uint64_t n_amps,
+                     const PairDev *pairs_d, int n_pairs, const uint32_t *planes, const uint64_t *contig_off,
+                     const float *tm, const double *thr_d, int n_thr, long long *W, bool few_exact,
+                     uint64_t *pass_mask, unsigned long long *gmask, uint32_t max_genome, unsigned long long *counts,
+                     int *err, cudaStream_t s);
 
 // pair.cu
 // n_dev (here and below): optional device count, min(*n_dev, n) records.

@@ -26,6 +26,7 @@
 // with the same operation order as the definition and no fused multiply-adds,
 // a whole block sharing one site's oligos (tm_exact_kernel).  Either way the
 // pass flag is the exact fp64 decision.
+#include <algorithm>
 #include <cmath>
 
 #include "ah_internal.h"
@@ -81,6 +82,42 @@ __device__ double exact_tm(const PairDev &pd, const int8_t *bt, int L, uint64_t 
     return tm;
 }
 
+// Oligo number o (0 <= o < degeneracy <= 10000) of a primer with position sets
+// qm -> its bases, 2 bits per position (mixed radix over the positions' sets).
+__device__ uint64_t oligo_number(const uint8_t *qm, int L, int o)
+{
+    uint64_t olig = 0;
+    int rem = o;
+    for (int q = L - 1; q >= 0; --q) {
+        const int nqb = __popc(qm[q]);
+        int d; // rem % nqb, rem /= nqb for nqb in 1..4 (rem < 10000)
+        if (nqb == 1) {
+            d = 0;
+        } else if (nqb == 2) {
+            d = rem & 1;
+            rem >>= 1;
+        } else if (nqb == 4) {
+            d = rem & 3;
+            rem >>= 2;
+        } else {
+            const int q3 = (rem * 43691) >> 17; // rem / 3, exact for rem < 2^16
+            d = rem - 3 * q3;
+            rem = q3;
+        }
+        int base_q = 0;
+        for (int x = 0; x < 4; ++x)
+            if (qm[q] >> x & 1) {
+                if (d == 0) {
+                    base_q = x;
+                    break;
+                }
+                --d;
+            }
+        olig |= (uint64_t)base_q << (2 * q);
+    }
+    return olig;
+}
+
 // One queued site with a whole block of kExactThreads: every oligo in fp64
 // with the definition's operation order (exact_tm), block-wide maximum, then
 // the Tm and the pass flag.  bt and wmax are the block's shared scratch.
@@ -105,37 +142,7 @@ __device__ void exact_site(const ah_site *__restrict__ sites, const PairDev *__r
         deg *= __popc(qm[q]);
     double best = -INFINITY;
     for (int o = threadIdx.x; o < deg; o += blockDim.x) {
-        // oligo number o -> bases (mixed radix over the positions' sets)
-        uint64_t olig = 0;
-        int rem = o;
-        for (int q = L - 1; q >= 0; --q) {
-            const int nqb = __popc(qm[q]);
-            int d; // rem % nqb, rem /= nqb for nqb in 1..4 (rem < 10000)
-            if (nqb == 1) {
-                d = 0;
-            } else if (nqb == 2) {
-                d = rem & 1;
-                rem >>= 1;
-            } else if (nqb == 4) {
-                d = rem & 3;
-                rem >>= 2;
-            } else {
-                const int q3 = (rem * 43691) >> 17; // rem / 3, exact for rem < 2^16
-                d = rem - 3 * q3;
-                rem = q3;
-            }
-            int base_q = 0;
-            for (int x = 0; x < 4; ++x)
-                if (qm[q] >> x & 1) {
-                    if (d == 0) {
-                        base_q = x;
-                        break;
-                    }
-                    --d;
-                }
-            olig |= (uint64_t)base_q << (2 * q);
-        }
-        const double t = exact_tm(pd, bt, L, olig);
+        const double t = exact_tm(pd, bt, L, oligo_number(qm, L, o));
         best = t > best ? t : best;
     }
     for (int d = 16; d >= 1; d >>= 1) {
@@ -202,6 +209,7 @@ constexpr double kFix = 1073741824.0; // 2^30: fixed-point scale of the sign tes
 // |each weight's rounding| <= 2^-31 cal/mol, so a path of <= 32 terms is within
 // 2e-8 of its exact value; decisions use a margin of 1e-6 cal/mol (file comment)
 constexpr long long kFixMargin = 1074; // 1e-6 * 2^30
+constexpr int kSweepMax = 64;          // thresholds per sweep (one bit each)
 
 __device__ __forceinline__ long long fix_weight(double dH, double dS, double thr)
 {
@@ -568,6 +576,172 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tm-threshold sweep (Sec. 3.3, Annealing Temperature Optimization: amplicon
+// counts, genomes amplified and off-target patterns as the threshold moves).
+// Per site a bit per threshold (passes or not, decided as the fp64 definition
+// decides: the fp32 maximum where it is 0.01 deg C or more from the threshold,
+// else the exact fixed-point sign test of the file comment, else every oligo
+// in fp64), then per amplicon the AND of its two sites' bits.
+// ---------------------------------------------------------------------------
+
+// W[(pair * n_thr + j) * 272 + e]: fixed-point weight of table entry e (256
+// stacks, then 16 terminal pairs) at threshold j, in the pair's ratio units
+__global__ void sweep_weights_kernel(const PairDev *__restrict__ pairs, int n_pairs, const double *__restrict__ thr_c,
+                                     int n_thr, long long *__restrict__ W)
+{
+    const int total = n_pairs * n_thr * 272;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int e = i % 272, pj = i / 272, j = pj % n_thr, p = pj / n_thr;
+        const PairDev &pd = pairs[p];
+        const double thr = thr_c[j] + 273.15 - ((pd.saltcorr >= 1 && pd.saltcorr <= 4) ? pd.tm_shift : 0.0);
+        W[i] = e < 256 ? fix_weight(pd.stack_dH_d[e], pd.stack_dS_d[e], thr)
+                       : fix_weight(pd.term_dH_d[e - 256], pd.term_dS_d[e - 256], thr);
+    }
+}
+
+// One thread per site: bit j of pass_mask[i] = site i passes threshold j.
+__global__ void sweep_pass_kernel(const ah_site *__restrict__ sites, uint64_t n, const PairDev *__restrict__ pairs,
+                                  const uint32_t *__restrict__ planes, const uint64_t *__restrict__ contig_off,
+                                  const float *__restrict__ tm, const double *__restrict__ thr_c, int n_thr,
+                                  const long long *__restrict__ W, int few_exact, uint64_t *__restrict__ pass_mask)
+{
+    const long long LINF = 0x2000000000000000ll;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const ah_site s = sites[i];
+        const float t = tm[i];
+        const PairDev &pd = pairs[s.pair];
+        const int L = pd.L[s.primer];
+        const uint8_t *qm = pd.mask[s.primer];
+        int8_t bt[AH_MAX_PRIMER_LEN];
+        bool have_bt = false;
+        uint64_t m = 0;
+        for (int j = 0; j < n_thr; ++j) {
+            const double T = thr_c[j];
+            bool pass;
+            if (isnan(t)) {
+                pass = false; // a template with a non-ACGT letter fails every threshold
+            } else if (fabs((double)t - T) >= 0.01) {
+                pass = (double)t >= T;
+            } else {
+                if (!have_bt) {
+                    const uint64_t P = contig_off[s.contig] + s.pos;
+                    for (int q = 0; q < L; ++q) {
+                        const int c = base_at(planes, P + (s.strand == 0 ? q : L - 1 - q));
+                        bt[q] = (int8_t)(s.strand == 0 ? 3 - c : c); // finite Tm: only A/C/G/T
+                    }
+                    have_bt = true;
+                }
+                int dec = -1;
+                if (few_exact) { // sign of min over oligos of F at this threshold, exactly
+                    const long long *Wp = W + ((size_t)s.pair * n_thr + j) * 272;
+                    long long c[4];
+                    for (int y = 0; y < 4; ++y)
+                        c[y] = (qm[0] >> y & 1) ? Wp[256 + y * 4 + bt[0]] : LINF;
+                    for (int q = 1; q < L; ++q) {
+                        long long nc[4];
+                        for (int y = 0; y < 4; ++y) {
+                            long long best = LINF;
+                            if (qm[q] >> y & 1)
+                                for (int x = 0; x < 4; ++x)
+                                    if (c[x] < LINF) {
+                                        const long long v = c[x] + Wp[((x * 4 + y) * 4 + bt[q - 1]) * 4 + bt[q]];
+                                        best = v < best ? v : best;
+                                    }
+                            nc[y] = best;
+                        }
+                        for (int y = 0; y < 4; ++y)
+                            c[y] = nc[y];
+                    }
+                    long long fin = LINF;
+                    for (int y = 0; y < 4; ++y)
+                        if (c[y] < LINF) {
+                            const long long v = c[y] + Wp[256 + y * 4 + bt[L - 1]];
+                            fin = v < fin ? v : fin;
+                        }
+                    const double thr = T + 273.15 - ((pd.saltcorr >= 1 && pd.saltcorr <= 4) ? pd.tm_shift : 0.0);
+                    const double Cp = pd.sconst + (pd.saltcorr == 5 ? 0.368 * (double)(L - 1) * pd.log_na : 0.0);
+                    const long long F = fin - __double2ll_rn(thr * Cp * kFix);
+                    dec = F < -kFixMargin ? 1 : (F > kFixMargin ? 0 : -1);
+                }
+                if (dec < 0) { // every oligo, in the definition's fp64 order
+                    int deg = 1;
+                    for (int q = 0; q < L; ++q)
+                        deg *= __popc(qm[q]);
+                    double best = -INFINITY;
+                    for (int o = 0; o < deg; ++o) {
+                        const double v = exact_tm(pd, bt, L, oligo_number(qm, L, o));
+                        best = v > best ? v : best;
+                    }
+                    dec = best >= T ? 1 : 0;
+                }
+                pass = dec == 1;
+            }
+            if (pass)
+                m |= 1ull << j;
+        }
+        pass_mask[i] = m;
+    }
+}
+
+// Per amplicon: the thresholds both of its sites pass; counts per threshold
+// (all, FF or RR) and, per genome, the thresholds at which it is amplified.
+__global__ void sweep_count_kernel(const ah_amplicon *__restrict__ a, uint64_t na, uint64_t n_sites,
+                                   const uint64_t *__restrict__ pass_mask, uint32_t max_genome, int n_thr,
+                                   unsigned long long *__restrict__ amps, unsigned long long *__restrict__ ffrr,
+                                   unsigned long long *__restrict__ gmask, int *__restrict__ err)
+{
+    __shared__ unsigned long long sa[kSweepMax], sf[kSweepMax];
+    for (int j = threadIdx.x; j < kSweepMax; j += blockDim.x)
+        sa[j] = sf[j] = 0;
+    __syncthreads();
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < na; i += (uint64_t)gridDim.x * blockDim.x) {
+        const ah_amplicon am = a[i];
+        if (am.left >= n_sites || am.right >= n_sites || am.genome > max_genome || am.orient > 3) {
+            atomicExch(err, kDevBounds);
+            continue;
+        }
+        uint64_t m = pass_mask[am.left] & pass_mask[am.right];
+        if (m)
+            atomicOr(gmask + am.genome, (unsigned long long)m);
+        while (m) {
+            const int j = __ffsll((long long)m) - 1;
+            m &= m - 1;
+            atomicAdd(&sa[j], 1ull);
+            if (am.orient >= 2)
+                atomicAdd(&sf[j], 1ull);
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n_thr; j += blockDim.x) {
+        if (sa[j])
+            atomicAdd(amps + j, sa[j]);
+        if (sf[j])
+            atomicAdd(ffrr + j, sf[j]);
+    }
+}
+
+__global__ void sweep_genomes_kernel(const unsigned long long *__restrict__ gmask, uint64_t n_words, int n_thr,
+                                     unsigned long long *__restrict__ gcount)
+{
+    __shared__ unsigned long long sg[kSweepMax];
+    for (int j = threadIdx.x; j < kSweepMax; j += blockDim.x)
+        sg[j] = 0;
+    __syncthreads();
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_words; i += (uint64_t)gridDim.x * blockDim.x) {
+        unsigned long long m = gmask[i];
+        while (m) {
+            const int j = __ffsll((long long)m) - 1;
+            m &= m - 1;
+            atomicAdd(&sg[j], 1ull);
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n_thr; j += blockDim.x)
+        if (sg[j])
+            atomicAdd(gcount + j, sg[j]);
+}
+
 } // namespace
 
 void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const PairDev *pairs_d, int n_pairs,
@@ -603,6 +777,38 @@ void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const Pa
         return;
     tm_exact_kernel<<<(unsigned)sms, kExactThreads, 0, s>>>(sites, pairs_d, planes, contig_off, queue, queue_n,
                                                               tm_out, pass_out);
+    AH_CUDA(cudaGetLastError());
+}
+
+// Sweep: counts[0..n_thr) amplicons, [64..64+n_thr) FF/RR, [128..128+n_thr)
+// genomes; counts and gmask (max_genome + 1 words) zeroed here.
+void launch_tm_sweep(const ah_site *sites, uint64_t n_sites, const ah_amplicon *amps, uint64_t n_amps,
+                     const PairDev *pairs_d, int n_pairs, const uint32_t *planes, const uint64_t *contig_off,
+                     const float *tm, const double *thr_d, int n_thr, long long *W, bool few_exact,
+                     uint64_t *pass_mask, unsigned long long *gmask, uint32_t max_genome, unsigned long long *counts,
+                     int *err, cudaStream_t s)
+{
+    if (n_thr < 1 || n_thr > kSweepMax)
+        throw Error(AH_ERR_ARG, "sweep: 1..64 thresholds");
+    AH_CUDA(cudaMemsetAsync(counts, 0, 3 * kSweepMax * sizeof(unsigned long long), s));
+    AH_CUDA(cudaMemsetAsync(gmask, 0, ((uint64_t)max_genome + 1) * sizeof(unsigned long long), s));
+    sweep_weights_kernel<<<(n_pairs * n_thr * 272 + 255) / 256, 256, 0, s>>>(pairs_d, n_pairs, thr_d, n_thr, W);
+    AH_CUDA(cudaGetLastError());
+    if (n_sites) {
+        const uint64_t blocks = std::min<uint64_t>((n_sites + 127) / 128, 8192);
+        sweep_pass_kernel<<<(unsigned)blocks, 128, 0, s>>>(sites, n_sites, pairs_d, planes, contig_off, tm, thr_d,
+                                                           n_thr, W, few_exact ? 1 : 0, pass_mask);
+        AH_CUDA(cudaGetLastError());
+    }
+    if (n_amps) {
+        const uint64_t blocks = std::min<uint64_t>((n_amps + 255) / 256, 4096);
+        sweep_count_kernel<<<(unsigned)blocks, 256, 0, s>>>(amps, n_amps, n_sites, pass_mask, max_genome, n_thr,
+                                                            counts, counts + kSweepMax, gmask, err);
+        AH_CUDA(cudaGetLastError());
+    }
+    const uint64_t words = (uint64_t)max_genome + 1;
+    const uint64_t blocks = std::min<uint64_t>((words + 255) / 256, 1024);
+    sweep_genomes_kernel<<<(unsigned)blocks, 256, 0, s>>>(gmask, words, n_thr, counts + 2 * kSweepMax);
     AH_CUDA(cudaGetLastError());
 }
 

@@ -543,3 +543,39 @@ def test_decoy_sets_on_reversed_contigs(ctx, on_device):
     assert len(real) > 0
     rate = len(o["amps"]) / len(real)  # the off-target estimate this load supports
     assert 0.0 <= rate
+
+
+def test_tm_threshold_sweep(ctx):
+    """ah_tm_sweep: per threshold, the amplicons whose two sites pass, those that
+    are FF/RR, and the genomes amplified, equal to the oracle's fp64 decisions --
+    on a grid and at thresholds placed on (and within 1e-7 of) site Tm values."""
+    w = synth.collection(seed=2, n_genomes=6, len_lo=3e5, len_hi=9e5)
+    pair = w.pairs[0]
+    sites = oracle.scan(w.seq, w.contig_off, w.contig_genome, [pair])
+    amps = oracle.pair(sites, [pair])
+    tm64, _ = oracle.tm(w.seq, w.contig_off, sites, [pair])
+    fin = np.unique(tm64[~np.isnan(tm64)])
+    picks = fin[np.linspace(0, len(fin) - 1, 6).astype(int)]
+    thr = list(np.arange(20.0, 72.0, 2.0)) + [float(v) for v in picks]
+    thr += [float(picks[2]) + 1e-7, float(picks[3]) - 1e-7, float(picks[4]) + 1e-12]
+    assert len(thr) <= 64
+    want = []
+    for T in thr:
+        ok = tm64 >= T  # NaN compares false: fails every threshold
+        live = ok[amps["left"]] & ok[amps["right"]]
+        want.append((int(live.sum()), int((live & (amps["orient"] >= 2)).sum()),
+                     len(set(amps["genome"][live].tolist()))))
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    try:
+        pid = ctx.ah_set_primers(pair["fwd"], pair["rev"], pair)
+        g_sites = ctx.scan(sid, [pid])
+        assert g_sites.tobytes() == sites.tobytes()
+        g_amps = ctx.pair(sid, [pid], g_sites)
+        assert g_amps.tobytes() == amps.tobytes() and len(amps) > 0
+        rows, n_genomes = ctx.ah_tm_sweep(sid, [pid], g_sites, g_amps, thr)
+    finally:
+        ctx.ah_unload_genomes(sid)
+    assert n_genomes == len(set(w.contig_genome.tolist()))
+    got = [tuple(int(x) for x in r) for r in rows]
+    assert got == want
+    assert want[0][0] > want[-10][0]  # the counts do move with the threshold
