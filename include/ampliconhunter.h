@@ -371,6 +371,32 @@ ah_status ah_tm_sweep(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, ui
                       uint64_t n_sites, const ah_amplicon *amplicons, uint64_t n_amplicons, const double *thresholds,
                       uint32_t n_thresholds, ah_sweep_row *rows, uint64_t *n_genomes_out, void *stream);
 
+/* Amplicon sequence variants and amplitypes (Sec. 3.3, Amplicon Pattern
+ * Visualization: an amplitype is a genome's combination of copy numbers and
+ * sequence variants).  amplicons (host or device): n records of the set (as
+ * ah_pair returns them); the sequence of each is the one ah_fetch returns (RF
+ * reverse-complemented, N for non-ACGT), hashed on the device (two
+ * polynomial hashes modulo 2^61 - 1: 122 bits).  variant_out (host or device,
+ * may be null): per amplicon, its variant id, numbered 0, 1, ... in order of
+ * first occurrence in `amplicons`.  rows (host or device): one row per genome
+ * with at least one amplicon, in ascending genome id: the genome, its
+ * amplitype id (numbered by first occurrence in that order: genomes with the
+ * same multiset of (variant, copy number) share it), its amplicon count and
+ * its variant count; cap rows fit (cap = 0: size query; too small: nothing
+ * written, *n_rows_out set, AH_ERR_OVERFLOW).  *n_variants_out and
+ * *n_amplitypes_out: the distinct variants and amplitypes.
+ * Errors: AH_ERR_ARG (records outside the set, genome not its contig's),
+ * AH_ERR_OVERFLOW, AH_ERR_CUDA. */
+typedef struct {
+    uint32_t genome;
+    uint32_t amplitype;
+    uint32_t n_amplicons;
+    uint32_t n_variants;
+} ah_genome_amplitype;
+ah_status ah_amplitypes(ah_ctx *ctx, uint32_t set_id, const ah_amplicon *amplicons, uint64_t n, uint32_t *variant_out,
+                        ah_genome_amplitype *rows, uint64_t cap, uint64_t *n_rows_out, uint64_t *n_variants_out,
+                        uint64_t *n_amplitypes_out, void *stream);
+
 /* Measurement: per-stage device time, host time and kernel launches.
  * ah_set_profiling clears the counters; enable = 1 then brackets each stage
  * of each call with CUDA events on the stream the stage runs on and times

@@ -32,7 +32,7 @@ AMPLICON_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("start", "<u4"
 EXPORTS = ["ah_create", "ah_destroy", "ah_last_error", "ah_device_bytes", "ah_load_genomes", "ah_unload_genomes",
            "ah_set_primers", "ah_set_nn_table", "ah_scan", "ah_tm", "ah_pair", "ah_fetch", "ah_set_profiling",
            "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan", "ah_run", "ah_run_begin", "ah_run_end",
-           "ah_load_genomes_ex", "ah_tm_sweep"]
+           "ah_load_genomes_ex", "ah_tm_sweep", "ah_amplitypes"]
 
 
 class AHError(RuntimeError):
@@ -112,6 +112,7 @@ def lib():
             "ah_run": (I32, [P, U32, P, U32, ctypes.POINTER(RunOut), P]),
             "ah_run_begin": (I32, [P, U32, P, U32, ctypes.POINTER(RunOut), P, P]),
             "ah_tm_sweep": (I32, [P, U32, P, U32, P, U64, P, U64, P, U32, P, ctypes.POINTER(U64), P]),
+            "ah_amplitypes": (I32, [P, U32, P, U64, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
             "ah_run_end": (I32, [P]),
             "ah_tune_scan": (I32, [P, U32, P, U32, U64, ctypes.POINTER(TuneResult), P]),
             "ah_pair_noalloc": (I32, [P, U32, P, P, U64, P, U64, ctypes.POINTER(U64), P]),
@@ -271,6 +272,22 @@ class Context:
                                           _ptr(amplicons) if n_a else None, n_a, _ptr(thr), len(thr), _ptr(rows),
                                           ctypes.byref(ng), _stream(stream)))
         return rows, ng.value
+
+    def amplitypes(self, set_id: int, amplicons: np.ndarray, stream=None):
+        """(variant id per amplicon, rows [genome, amplitype, n_amplicons, n_variants] per genome with
+        amplicons, number of variants, number of amplitypes) -- size query, then the call."""
+        n = len(amplicons)
+        variant = np.zeros(max(n, 1), dtype=np.uint32)
+        nr, nv, nt = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        st = self._lib.ah_amplitypes(self.h, set_id, _ptr(amplicons) if n else None, n, None, None, 0,
+                                     ctypes.byref(nr), ctypes.byref(nv), ctypes.byref(nt), _stream(stream))
+        if st not in (AH_OK, AH_ERR_OVERFLOW):
+            self._check(st)
+        rows = np.zeros((max(nr.value, 1), 4), dtype=np.uint32)
+        self._check(self._lib.ah_amplitypes(self.h, set_id, _ptr(amplicons) if n else None, n, _ptr(variant),
+                                            _ptr(rows), nr.value, ctypes.byref(nr), ctypes.byref(nv),
+                                            ctypes.byref(nt), _stream(stream)))
+        return variant[:n], rows[:nr.value], nv.value, nt.value
 
     def ah_run_end(self, out: RunOut) -> RunOut:
         self._check(self._lib.ah_run_end(self.h), out.n_sites)

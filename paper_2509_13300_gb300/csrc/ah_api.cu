@@ -1618,6 +1618,96 @@ ah_status ah_tm_sweep(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint
     });
 }
 
+ah_status ah_amplitypes(ah_ctx *c, uint32_t set_id, const ah_amplicon *amplicons, uint64_t n, uint32_t *variant_out,
+                        ah_genome_amplitype *rows, uint64_t cap, uint64_t *n_rows_out, uint64_t *n_variants_out,
+                        uint64_t *n_amplitypes_out, void *stream)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require_idle(c);
+        require(n_rows_out && n_variants_out && n_amplitypes_out && (n == 0 || amplicons) && (cap == 0 || rows),
+                AH_ERR_ARG, "ah_amplitypes: null argument");
+        require(n < (1ull << 32), AH_ERR_ARG, "ah_amplitypes: at most 2^32 - 1 amplicons");
+        *n_rows_out = *n_variants_out = *n_amplitypes_out = 0;
+        GenomeSet &gs = get_set(c, set_id);
+        cudaStream_t st = stream_of(c, stream);
+        wait_ready(gs, st);
+        if (n == 0)
+            return;
+        reset_flags(c, st);
+        const ah_amplicon *a = stage_in(c, "amplitype_in", amplicons, n, st);
+        const uint64_t G = (uint64_t)gs.max_genome + 1;  // genome id range
+        const uint64_t N = std::max<uint64_t>(n, G);     // the largest count a scratch array serves
+        {   // the records lie in the set (checked before any kernel reads planes with them)
+            uint64_t *len = (uint64_t *)scratch(c, "fetch_len", (n + 1) * sizeof(uint64_t));
+            Stage sg(c, "validate", st, 1);
+            launch_fetch_lengths(a, n, nullptr, gs.contig_off, gs.n_contigs, len, c->d_err, st);
+        }
+        check_flags(c, st);
+        AmpliTypeScratch S;
+        S.idx = (uint32_t *)scratch(c, "at_idx", N * 4);
+        S.idx_b = (uint32_t *)scratch(c, "at_idx_b", N * 4);
+        S.run_pos = (uint32_t *)scratch(c, "at_run_pos", N * 4);
+        S.keys_a = (uint64_t *)scratch(c, "at_keys_a", N * 8);
+        S.keys_b = (uint64_t *)scratch(c, "at_keys_b", N * 8);
+        S.keys_s = (uint64_t *)scratch(c, "at_keys_s", N * 8);
+        S.head = (uint64_t *)scratch(c, "at_head", N * 8);
+        S.head_excl = (uint64_t *)scratch(c, "at_head_excl", N * 8);
+        S.is_first = (uint64_t *)scratch(c, "at_is_first", N * 8);
+        S.rank = (uint64_t *)scratch(c, "at_rank", N * 8);
+        S.temp_bytes = AmpliTypeScratch::cub_bytes(N);
+        S.temp = scratch(c, "at_cub", S.temp_bytes);
+        S.scan_bytes = scan_u64_temp_bytes(N);
+        S.scan_temp = scratch(c, "scan_temp", S.scan_bytes);
+        uint64_t *h1 = (uint64_t *)scratch(c, "at_h1", n * 8), *h2 = (uint64_t *)scratch(c, "at_h2", n * 8);
+        uint32_t *variant = (uint32_t *)scratch(c, "at_variant", n * 4);
+        uint64_t *counts = c->d_flags + kFlagSites; // three device words: variants, genome runs, rows
+        {
+            Stage sg(c, "amplitype", st, 1);
+            launch_amp_hash(a, n, gs.planes, gs.contig_off, h1, h2, st);
+            S.sort_by(h1, h2, n, st);
+            S.ids(n, variant, counts + 0, st); // sequence variants
+            launch_genome_key(a, variant, n, gs.contig_genome, h1, c->d_err, st); // h1 reused for the keys
+            S.sort_by(h1, nullptr, n, st);
+            S.ids(n, nullptr, counts + 1, st); // (genome, variant) runs
+            auto *g1 = (unsigned long long *)scratch(c, "at_g1", G * 8);
+            auto *g2 = (unsigned long long *)scratch(c, "at_g2", G * 8);
+            auto *gamp = (unsigned int *)scratch(c, "at_gamp", G * 4);
+            auto *gvar = (unsigned int *)scratch(c, "at_gvar", G * 4);
+            AH_CUDA(cudaMemsetAsync(g1, 0, G * 8, st));
+            AH_CUDA(cudaMemsetAsync(g2, 0, G * 8, st));
+            AH_CUDA(cudaMemsetAsync(gamp, 0, G * 4, st));
+            AH_CUDA(cudaMemsetAsync(gvar, 0, G * 4, st));
+            S.genome_sums(n, counts + 1, g1, g2, gamp, gvar, st);
+            uint32_t *gid = (uint32_t *)scratch(c, "at_gid", G * 4);
+            uint64_t *k1 = (uint64_t *)scratch(c, "at_k1", G * 8), *k2 = (uint64_t *)scratch(c, "at_k2", G * 8);
+            uint64_t *has = (uint64_t *)scratch(c, "at_has", G * 8), *pos = (uint64_t *)scratch(c, "at_pos", G * 8);
+            launch_genome_compact(gamp, G, has, pos, S.scan_temp, S.scan_bytes, g1, g2, gid, k1, k2, counts + 2, st);
+            check_flags(c, st);
+            const uint64_t m = c->h_flags[kFlagSites + 2];
+            const uint64_t nv = c->h_flags[kFlagSites + 0];
+            *n_rows_out = m;
+            *n_variants_out = nv;
+            uint32_t *type = (uint32_t *)scratch(c, "at_type", std::max<uint64_t>(m, 1) * 4);
+            S.sort_by(k1, k2, m, st);
+            S.ids(m, type, counts + 1, st); // amplitypes, first occurrence in ascending genome order
+            ah_genome_amplitype *r = out_buf(c, "at_rows", rows, m <= cap ? m : 0);
+            if (m <= cap)
+                launch_amplitype_rows(gid, type, m, gamp, gvar, r, st);
+            if (variant_out)
+                AH_CUDA(cudaMemcpyAsync(variant_out, variant, n * 4, cudaMemcpyDefault, st));
+            check_flags(c, st);
+            *n_amplitypes_out = c->h_flags[kFlagSites + 1];
+            if (m > cap)
+                throw Error(AH_ERR_OVERFLOW, "ah_amplitypes: " + std::to_string(m) + " genomes with amplicons, capacity " +
+                                                 std::to_string(cap));
+            out_finish(rows, r, m, st);
+            AH_CUDA(cudaStreamSynchronize(st));
+        }
+    });
+}
+
 ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, const ah_site *sites,
                 uint64_t n, float *tm_out, uint8_t *pass_out, void *stream)
 {

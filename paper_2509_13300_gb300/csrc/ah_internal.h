@@ -264,6 +264,38 @@ void launch_pair_write(const ah_site *sites, uint64_t n, const uint64_t *n_dev, 
                        const PairDev *pairs_d, const uint64_t *offsets, ah_amplicon *out, uint64_t cap,
                        const uint64_t *skip, uint64_t skip_bit, cudaStream_t s);
 
+// amplitype.cu: sequence variants and amplitypes.  Every array holds at
+// least the largest count it serves (amplicons, or genomes with amplicons).
+struct AmpliTypeScratch {
+    uint32_t *idx = nullptr, *idx_b = nullptr, *run_pos = nullptr;
+    uint64_t *keys_a = nullptr, *keys_b = nullptr, *keys_s = nullptr;
+    uint64_t *head = nullptr, *head_excl = nullptr, *is_first = nullptr, *rank = nullptr;
+    bool keys_b_valid = false;
+    void *temp = nullptr; // CUB sort storage
+    size_t temp_bytes = 0;
+    void *scan_temp = nullptr; // CUB scan storage (more than kSmallScan values)
+    size_t scan_bytes = 0;
+    // stable sort of the element indices by (ka, kb) (kb may be null)
+    void sort_by(const uint64_t *ka, const uint64_t *kb, uint64_t n, cudaStream_t s);
+    // runs of equal keys after sort_by; with id_out, first-occurrence ids per element
+    void ids(uint64_t n, uint32_t *id_out, uint64_t *n_runs_dev, cudaStream_t s);
+    // after sort_by + ids over (genome << 32 | variant) keys: per-genome multiset sums and counts
+    void genome_sums(uint64_t n, const uint64_t *n_runs_dev, unsigned long long *g1, unsigned long long *g2,
+                     unsigned int *gamp, unsigned int *gvar, cudaStream_t s);
+    static size_t cub_bytes(uint64_t n);
+};
+void launch_amp_hash(const ah_amplicon *a, uint64_t n, const uint32_t *planes, const uint64_t *contig_off,
+                     uint64_t *h1, uint64_t *h2, cudaStream_t s);
+// key (genome << 32 | variant) per amplicon; an amplicon whose genome differs
+// from its contig's, or with orientation > 3, sets *err = kDevBounds
+void launch_genome_key(const ah_amplicon *a, const uint32_t *variant, uint64_t n, const uint32_t *contig_genome,
+                       uint64_t *keys, int *err, cudaStream_t s);
+void launch_genome_compact(const unsigned int *gamp, uint64_t n_ids, uint64_t *has, uint64_t *pos, void *scan_temp,
+                           size_t scan_bytes, const unsigned long long *g1, const unsigned long long *g2, uint32_t *gid,
+                           uint64_t *k1, uint64_t *k2, uint64_t *n_out_dev, cudaStream_t s);
+void launch_amplitype_rows(const uint32_t *gid, const uint32_t *type, uint64_t m, const unsigned int *gamp,
+                           const unsigned int *gvar, ah_genome_amplitype *rows, cudaStream_t s);
+
 // fetch.cu
 // lengths of the amplicons; a record outside its contig sets *err = kDevBounds (length 0)
 // With n_dev the kernel also writes len[count] = 0 (the scan's closing entry).

@@ -579,3 +579,54 @@ def test_tm_threshold_sweep(ctx):
     got = [tuple(int(x) for x in r) for r in rows]
     assert got == want
     assert want[0][0] > want[-10][0]  # the counts do move with the threshold
+
+
+def _oracle_amplitypes(w, amps):
+    """Plain definition: variant = exact fetched sequence, numbered by first
+    occurrence; a genome's amplitype = its multiset of (variant, copies),
+    numbered by first occurrence over genomes in ascending id."""
+    seqs, offs = oracle.fetch(w.seq, w.contig_off, amps)
+    var = {}
+    vid = [var.setdefault(seqs[int(offs[i]):int(offs[i + 1])], len(var)) for i in range(len(amps))]
+    per = {}
+    for g, v in zip(amps["genome"].tolist(), vid):
+        per.setdefault(g, {}).setdefault(v, 0)
+        per[g][v] += 1
+    types = {}
+    rows = []
+    for g in sorted(per):
+        pattern = frozenset(per[g].items())
+        rows.append((g, types.setdefault(pattern, len(types)), sum(per[g].values()), len(per[g])))
+    return np.array(vid, dtype=np.uint32), rows, len(var), len(types)
+
+
+@pytest.mark.parametrize("case", ["collection", "repeats"])
+def test_amplicon_variants_and_amplitypes(ctx, case):
+    """ah_amplitypes: variant ids and per-genome amplitypes equal the plain
+    definition on the fetched sequences (exact sequence identity)."""
+    if case == "collection":
+        w = synth.collection(seed=8, n_genomes=12, len_lo=2e5, len_hi=6e5)
+    else:  # short primers on repeated genomes: many equal sequences and shared patterns
+        base = synth.random_small(3, n_bases=30_000, n_contigs=2, L_f=6, L_r=6, k=1, min_len=20, max_len=300)
+        reps = 5
+        seq = np.concatenate([base.seq] * reps)
+        n0 = len(base.seq)
+        off = np.concatenate([base.contig_off[:-1] + r * n0 for r in range(reps)] + [[reps * n0]]).astype(np.uint64)
+        gen = np.repeat(np.arange(reps, dtype=np.uint32), len(base.contig_off) - 1)
+        seq[n0 + 100:n0 + 110] = ord("N")  # genome 1 differs a little
+        w = synth.Workload(**{**base.__dict__, "seq": seq, "contig_off": off, "contig_genome": gen})
+    pair = w.pairs[0]
+    sites = oracle.scan(w.seq, w.contig_off, w.contig_genome, [pair])
+    amps = oracle.pair(sites, [pair])
+    assert len(amps) > 3
+    want_v, want_rows, want_nv, want_nt = _oracle_amplitypes(w, amps)
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    try:
+        variant, rows, nv, nt = ctx.amplitypes(sid, amps)
+    finally:
+        ctx.ah_unload_genomes(sid)
+    assert np.array_equal(variant, want_v)
+    assert [tuple(int(x) for x in r) for r in rows] == want_rows
+    assert (nv, nt) == (want_nv, want_nt)
+    if case == "repeats":
+        assert nt < len(want_rows)  # some genomes share an amplitype
