@@ -404,7 +404,8 @@ ah_status ah_amplitypes(ah_ctx *ctx, uint32_t set_id, const ah_amplicon *amplico
  * only the "pack" and "scan" stages (the streaming kernels; fewer events in
  * the stream) and times host sections, 0 stops.  Device
  * stages: "pack" (ah_load_genomes), "scan", "sort", "decode" (ah_scan),
- * "validate" (record checks of ah_tm / ah_pair), "tm", "pair", "fetch".  Host
+ * "validate" (record checks of ah_tm / ah_pair), "tm", "pair", "fetch",
+ * "sweep" (ah_tm_sweep), "amplitype" (ah_amplitypes).  Host
  * sections (wall time inside the library): "host.load", "host.load.alloc",
  * "host.load.tables", "host.load.pack", "host.run", "host.run.prep",
  * "host.run.launch", "host.run.wait", "host.unload".  ah_get_profile returns,
