@@ -397,6 +397,28 @@ ah_status ah_amplitypes(ah_ctx *ctx, uint32_t set_id, const ah_amplicon *amplico
                         ah_genome_amplitype *rows, uint64_t cap, uint64_t *n_rows_out, uint64_t *n_variants_out,
                         uint64_t *n_amplitypes_out, void *stream);
 
+/* Synthetic genome bases on the device from a counter-based generator
+ * (Philox4x32-10, Salmon et al., SC 2011) -- the library's input generator for
+ * collections too large to build on the host (no counterpart in the paper).
+ * Position P of the collection: the 32-bit draw u = output (P mod 4) of
+ * Philox(counter = (P div 4 low 32 bits, high 32 bits, 0, 0), key = (seed low,
+ * seed high)); in the segment holding P, the base is `letter` when non-zero,
+ * else A if u < t_a, C if u < t_c, G if u < t_g, else T.  Segments (host) tile
+ * the collection in order: segment i covers [end of i-1 (0 for the first),
+ * end).  Patches (host, may be empty) then set out[pos - base0] = byte for
+ * every pos inside the range.  out (device): n bytes for positions
+ * [base0, base0 + n); base0 must be a multiple of 4, and the segments must
+ * reach base0 + n.  Waits for the work before returning.
+ * Errors: AH_ERR_ARG, AH_ERR_CUDA. */
+typedef struct {
+    uint64_t end;
+    uint32_t t_a, t_c, t_g;
+    uint32_t letter;
+} ah_gen_segment;
+ah_status ah_generate_bases(ah_ctx *ctx, uint64_t seed, const ah_gen_segment *segments, uint64_t n_segments,
+                            const uint64_t *patch_pos, const uint8_t *patch_bytes, uint64_t n_patches, uint64_t base0,
+                            uint64_t n, uint8_t *out, void *stream);
+
 /* Measurement: per-stage device time, host time and kernel launches.
  * ah_set_profiling clears the counters; enable = 1 then brackets each stage
  * of each call with CUDA events on the stream the stage runs on and times

@@ -32,7 +32,7 @@ AMPLICON_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("start", "<u4"
 EXPORTS = ["ah_create", "ah_destroy", "ah_last_error", "ah_device_bytes", "ah_load_genomes", "ah_unload_genomes",
            "ah_set_primers", "ah_set_nn_table", "ah_scan", "ah_tm", "ah_pair", "ah_fetch", "ah_set_profiling",
            "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan", "ah_run", "ah_run_begin", "ah_run_end",
-           "ah_load_genomes_ex", "ah_tm_sweep", "ah_amplitypes"]
+           "ah_load_genomes_ex", "ah_tm_sweep", "ah_amplitypes", "ah_generate_bases"]
 
 
 class AHError(RuntimeError):
@@ -113,6 +113,7 @@ def lib():
             "ah_run_begin": (I32, [P, U32, P, U32, ctypes.POINTER(RunOut), P, P]),
             "ah_tm_sweep": (I32, [P, U32, P, U32, P, U64, P, U64, P, U32, P, ctypes.POINTER(U64), P]),
             "ah_amplitypes": (I32, [P, U32, P, U64, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
+            "ah_generate_bases": (I32, [P, U64, P, U64, P, P, U64, U64, U64, P, P]),
             "ah_run_end": (I32, [P]),
             "ah_tune_scan": (I32, [P, U32, P, U32, U64, ctypes.POINTER(TuneResult), P]),
             "ah_pair_noalloc": (I32, [P, U32, P, P, U64, P, U64, ctypes.POINTER(U64), P]),
@@ -288,6 +289,17 @@ class Context:
                                             _ptr(rows), nr.value, ctypes.byref(nr), ctypes.byref(nv),
                                             ctypes.byref(nt), _stream(stream)))
         return variant[:n], rows[:nr.value], nv.value, nt.value
+
+    def generate_bases(self, coll, base0: int, n: int, out, stream=None):
+        """Bases [base0, base0 + n) of a countergen collection into device memory `out` (torch uint8)."""
+        segs = np.ascontiguousarray(coll.segments)
+        pp = np.ascontiguousarray(coll.patch_pos, dtype=np.uint64)
+        pb = np.ascontiguousarray(coll.patch_bytes, dtype=np.uint8)
+        lo, hi = np.searchsorted(pp, base0), np.searchsorted(pp, base0 + n)  # the patches in range
+        pp, pb = np.ascontiguousarray(pp[lo:hi]), np.ascontiguousarray(pb[lo:hi])
+        self._check(self._lib.ah_generate_bases(self.h, coll.seed, _ptr(segs), len(segs), _ptr(pp) if len(pp) else None,
+                                                _ptr(pb) if len(pb) else None, len(pp), base0, n, _ptr(out),
+                                                _stream(stream)))
 
     def ah_run_end(self, out: RunOut) -> RunOut:
         self._check(self._lib.ah_run_end(self.h), out.n_sites)

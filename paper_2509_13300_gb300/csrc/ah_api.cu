@@ -1708,6 +1708,46 @@ ah_status ah_amplitypes(ah_ctx *c, uint32_t set_id, const ah_amplicon *amplicons
     });
 }
 
+ah_status ah_generate_bases(ah_ctx *c, uint64_t seed, const ah_gen_segment *segments, uint64_t n_segments,
+                            const uint64_t *patch_pos, const uint8_t *patch_bytes, uint64_t n_patches, uint64_t base0,
+                            uint64_t n, uint8_t *out, void *stream)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require_idle(c);
+        require(segments && n_segments >= 1 && (n_patches == 0 || (patch_pos && patch_bytes)), AH_ERR_ARG,
+                "ah_generate_bases: null argument");
+        require(base0 % 4 == 0, AH_ERR_ARG, "ah_generate_bases: base0 must be a multiple of 4");
+        if (n == 0)
+            return;
+        require(out && is_device_ptr(c, out), AH_ERR_ARG, "ah_generate_bases: out must be device memory");
+        require(!is_device_ptr(c, segments) && (n_patches == 0 || !is_device_ptr(c, patch_pos)), AH_ERR_ARG,
+                "ah_generate_bases: segments and patches are host arrays");
+        for (uint64_t i = 0; i < n_segments; ++i)
+            require(i == 0 || segments[i].end >= segments[i - 1].end, AH_ERR_ARG,
+                    "ah_generate_bases: segment ends must not decrease");
+        require(segments[n_segments - 1].end >= base0 + n, AH_ERR_ARG,
+                "ah_generate_bases: the segments end before the range does");
+        cudaStream_t st = stream_of(c, stream);
+        auto *segs = (ah_gen_segment *)scratch(c, "gen_segs", n_segments * sizeof(ah_gen_segment));
+        AH_CUDA(cudaMemcpyAsync(segs, segments, n_segments * sizeof(ah_gen_segment), cudaMemcpyHostToDevice, st));
+        uint64_t *pp = nullptr;
+        uint8_t *pb = nullptr;
+        if (n_patches) {
+            pp = (uint64_t *)scratch(c, "gen_patch_pos", n_patches * sizeof(uint64_t));
+            pb = (uint8_t *)scratch(c, "gen_patch_bytes", n_patches);
+            AH_CUDA(cudaMemcpyAsync(pp, patch_pos, n_patches * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+            AH_CUDA(cudaMemcpyAsync(pb, patch_bytes, n_patches, cudaMemcpyHostToDevice, st));
+        }
+        {
+            Stage sg(c, "generate", st, n_patches ? 2 : 1);
+            launch_generate_bases(segs, n_segments, seed, pp, pb, n_patches, base0, n, out, st);
+        }
+        AH_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
 ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs, const ah_site *sites,
                 uint64_t n, float *tm_out, uint8_t *pass_out, void *stream)
 {

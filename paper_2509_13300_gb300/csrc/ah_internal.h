@@ -296,6 +296,11 @@ void launch_genome_compact(const unsigned int *gamp, uint64_t n_ids, uint64_t *h
 void launch_amplitype_rows(const uint32_t *gid, const uint32_t *type, uint64_t m, const unsigned int *gamp,
                            const unsigned int *gvar, ah_genome_amplitype *rows, cudaStream_t s);
 
+// gen.cu: counter-based synthetic bases (device segments and patches)
+void launch_generate_bases(const ah_gen_segment *segs, uint64_t n_segs, uint64_t seed, const uint64_t *patch_pos,
+                           const uint8_t *patch_bytes, uint64_t n_patches, uint64_t base0, uint64_t n, uint8_t *out,
+                           cudaStream_t s);
+
 // fetch.cu
 // lengths of the amplicons; a record outside its contig sets *err = kDevBounds (length 0)
 // With n_dev the kernel also writes len[count] = 0 (the scan's closing entry).

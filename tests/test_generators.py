@@ -1,0 +1,33 @@
+"""The counter-based input generator (large and served workloads): Philox4x32-10
+against the published known-answer vectors, and chunk independence of the
+collection bases (any range is a function of its positions alone)."""
+import numpy as np
+
+from paper_2509_13300_gb300 import countergen
+
+
+def test_philox_known_answer_vectors():
+    """Philox4x32-10 known-answer vectors (Salmon et al., SC 2011; the Random123
+    distribution's test vectors): zero counter and key, all-ones, and the pi digits."""
+    ctr = np.array([[0, 0, 0, 0], [0xFFFFFFFF] * 4, [0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344]], dtype=np.uint32)
+    keys = [(0, 0), (0xFFFFFFFF, 0xFFFFFFFF), (0xA4093822, 0x299F31D0)]
+    want = [[0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8], [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD],
+            [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]]
+    for c, k, w in zip(ctr, keys, want):
+        assert countergen.philox4x32(c[None, :], k)[0].tolist() == w
+
+
+def test_collection_bases_are_chunk_independent():
+    c = countergen.collection(seed=11, n_genomes=4, len_lo=5e4, len_hi=2e5)
+    full = c.bases()
+    assert len(full) == c.n_bases
+    cuts = [0, 4, 1000, 12345, 77777, c.n_bases]
+    parts = np.concatenate([c.bases(a, b) for a, b in zip(cuts[:-1], cuts[1:])])
+    assert np.array_equal(parts, full)
+    # composition follows the thresholds: no letter outside ACGTN, N only in N segments
+    assert set(np.unique(full).tolist()) <= set(b"ACGTN")
+    n_seg = c.segments[c.segments["letter"] != 0]
+    n_total = int(np.sum(np.diff(np.concatenate([[0], c.segments["end"]]))[c.segments["letter"] != 0]))
+    assert int((full == ord("N")).sum()) <= n_total and len(n_seg) > 0
+    # the planted patches are present
+    assert np.array_equal(full[c.patch_pos.astype(np.int64)], c.patch_bytes)

@@ -630,3 +630,58 @@ def test_amplicon_variants_and_amplitypes(ctx, case):
     assert (nv, nt) == (want_nv, want_nt)
     if case == "repeats":
         assert nt < len(want_rows)  # some genomes share an amplitype
+
+
+def test_device_generator_matches_cpu_twin(ctx):
+    """ah_generate_bases writes, on the device, the same bytes as the CPU twin,
+    for the whole collection and for ranges at other offsets."""
+    import torch
+    from paper_2509_13300_gb300 import countergen
+    c = countergen.collection(seed=7, n_genomes=6, len_lo=2e5, len_hi=8e5)
+    want = c.bases()
+    out = torch.zeros(c.n_bases, dtype=torch.uint8, device="cuda")
+    ctx.generate_bases(c, 0, c.n_bases, out)
+    assert out.cpu().numpy().tobytes() == want.tobytes()
+    for a, n in ((4, 1), (8, 4099), (40000, 123457), (c.n_bases - 1001 - (c.n_bases - 1001) % 4, 1001)):
+        part = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        ctx.generate_bases(c, a, n, part)
+        assert part.cpu().numpy().tobytes() == want[a:a + n].tobytes()
+    with pytest.raises(ah.AHError):  # base0 not a multiple of 4
+        ctx.generate_bases(c, 3, 10, out)
+
+
+def test_large_workload_shape_on_device_generated_genomes(ctx):
+    """The large workload's shape (counter-generated genomes, k = 4, window
+    100-3000, pairs of 960, 64 and 256 oligos scanned in one pass) on a small
+    seed-7 collection generated on the device: sites, Tm and amplicons equal the
+    oracle's on the CPU twin's bytes."""
+    import torch
+    from paper_2509_13300_gb300 import countergen
+    rng = np.random.default_rng(7)
+    p960 = synth.pcr_params("AGRRTTYGATYHTDGYTYAG", "YCNTTCCYTYDYRGTACT", k=4, min_len=100, max_len=3000,
+                            tm_min=45.0)
+    # oligo totals as the sum of the two primers' degeneracies: 32 + 32 and 128 + 128
+    p64 = synth.pcr_params(synth.random_primer(rng, 19, "RYSWK"), synth.random_primer(rng, 21, "WKMRY"), k=4,
+                           min_len=100, max_len=3000, tm_min=45.0)
+    p256 = synth.pcr_params(synth.random_primer(rng, 22, "RYSWKMR"), synth.random_primer(rng, 24, "KMRYSWK"), k=4,
+                            min_len=100, max_len=3000, tm_min=45.0)
+    pairs = [p960, p64, p256]
+    c = countergen.collection(seed=7, n_genomes=8, len_lo=2e5, len_hi=1e6, pairs=pairs)
+    w = c.workload()
+    o_sites = oracle.scan(w.seq, w.contig_off, w.contig_genome, pairs)
+    o_tm, o_ps = oracle.tm(w.seq, w.contig_off, o_sites, pairs)
+    o_amps = oracle.pair(o_sites, pairs, o_ps)
+    assert len(o_amps) > 0
+    dev = torch.zeros(c.n_bases, dtype=torch.uint8, device="cuda")
+    ctx.generate_bases(c, 0, c.n_bases, dev)
+    sid = ctx.ah_load_genomes(dev, c.n_bases, c.contig_off, c.contig_genome)
+    try:
+        pids = [ctx.ah_set_primers(p["fwd"], p["rev"], p) for p in pairs]
+        r = ctx.run(sid, pids, tm_filter=True)
+    finally:
+        ctx.ah_unload_genomes(sid)
+    assert r["sites"].tobytes() == o_sites.tobytes()
+    assert np.array_equal(r["pass_"], o_ps)
+    ok = ~np.isnan(o_tm)
+    assert np.abs(r["tm"][ok] - o_tm[ok]).max() <= TM_TOL
+    assert r["amps"].tobytes() == o_amps.tobytes()
