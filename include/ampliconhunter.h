@@ -462,6 +462,63 @@ ah_status ah_get_profile(const ah_ctx *ctx, const char *stage, double *ms, uint6
 ah_status ah_pair_noalloc(const int32_t *pair_windows, uint32_t n_pairs, const ah_site *sites, const uint8_t *pass,
                           uint64_t n, ah_amplicon *out, uint64_t cap, uint64_t *n_out, void *stream);
 
+/* Serving: continuous batching of requests over one resident genome set (a
+ * deployment form with no counterpart in the paper; each request is the
+ * paper's in-silico PCR of Sec. 2.1 restricted to some genomes of the set).
+ * A request names genomes of the set (ids as in the load's contig_genome),
+ * one primer pair (from ah_set_primers), a mismatch limit k (0..10, in place
+ * of the pair's own) and whether the Tm filter applies.  Its result is what
+ * the path gives for those genomes alone: the sites of the pair on their
+ * contigs with mm <= k, in canonical order, and the amplicons among them
+ * (both ends passing the Tm threshold when tm_filter is set), with `left`
+ * and `right` indexing the request's own site list; contig ids are those of
+ * the set.  A result does not depend on the other requests batched with it.
+ *
+ * ah_serve_start hands the context to a worker thread, which runs batches
+ * back to back: each time the GPU is free it admits queued requests in
+ * arrival order while their estimated device memory (sites and amplicons
+ * scale with the request's bases) stays within cfg->mem_budget bytes, at
+ * most cfg->max_batch of them and always at least one, and runs them
+ * together (one scan per primer pair over the union of their genomes' tiles).
+ * Until ah_serve_stop no other call may use the context.
+ * ah_serve_submit (any thread) queues a copy of the request and returns a
+ * ticket.  ah_serve_wait (any thread) blocks until the ticket's request is
+ * done, fills *info and copies its sites and amplicons to the host arrays:
+ * if either capacity is too small it returns AH_ERR_OVERFLOW with the counts
+ * in *info and keeps the result for another wait; otherwise (or on an
+ * error status) the ticket is released.  Times are milliseconds since
+ * ah_serve_start on a steady clock: submit, start of the batch that ran the
+ * request, and completion.  ah_serve_stop finishes the queued requests, joins
+ * the worker and frees the server (unreleased results are dropped).
+ * Errors: AH_ERR_ARG (bad argument, unknown pair, stopped server, unknown
+ * ticket), AH_ERR_OVERFLOW, and any status of the underlying path. */
+typedef struct ah_server ah_server;
+typedef struct {
+    size_t mem_budget;  /* bytes of device scratch one batch may plan for */
+    uint32_t max_batch; /* requests per batch, >= 1 */
+    uint32_t reserved;
+} ah_serve_config;
+typedef struct {
+    const uint32_t *genomes; /* host: genome ids (duplicates and unknown ids are ignored) */
+    uint32_t n_genomes;
+    uint32_t pair_id;
+    int32_t k;
+    int32_t tm_filter;
+} ah_request;
+typedef struct {
+    ah_status status;
+    uint32_t batch;       /* 1-based number of the batch that ran the request */
+    uint32_t batch_size;  /* requests in that batch */
+    uint32_t reserved;
+    uint64_t n_sites, n_amplicons, bases;
+    double submit_ms, start_ms, done_ms;
+} ah_request_info;
+ah_status ah_serve_start(ah_ctx *ctx, uint32_t set_id, const ah_serve_config *cfg, ah_server **out);
+ah_status ah_serve_submit(ah_server *srv, const ah_request *req, uint64_t *ticket_out);
+ah_status ah_serve_wait(ah_server *srv, uint64_t ticket, ah_request_info *info, ah_site *sites_out, uint64_t sites_cap,
+                        ah_amplicon *amps_out, uint64_t amps_cap);
+ah_status ah_serve_stop(ah_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

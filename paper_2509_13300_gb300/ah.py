@@ -32,7 +32,8 @@ AMPLICON_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("start", "<u4"
 EXPORTS = ["ah_create", "ah_destroy", "ah_last_error", "ah_device_bytes", "ah_load_genomes", "ah_unload_genomes",
            "ah_set_primers", "ah_set_nn_table", "ah_scan", "ah_tm", "ah_pair", "ah_fetch", "ah_set_profiling",
            "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan", "ah_run", "ah_run_begin", "ah_run_end",
-           "ah_load_genomes_ex", "ah_tm_sweep", "ah_amplitypes", "ah_generate_bases"]
+           "ah_load_genomes_ex", "ah_tm_sweep", "ah_amplitypes", "ah_generate_bases", "ah_serve_start",
+           "ah_serve_submit", "ah_serve_wait", "ah_serve_stop"]
 
 
 class AHError(RuntimeError):
@@ -67,6 +68,25 @@ class RunOut(ctypes.Structure):
                 ("amplicons", ctypes.c_void_p), ("amplicons_cap", ctypes.c_uint64), ("n_amplicons", ctypes.c_uint64),
                 ("seq", ctypes.c_void_p), ("seq_cap", ctypes.c_uint64), ("n_seq", ctypes.c_uint64),
                 ("seq_offsets", ctypes.c_void_p), ("tm_filter", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_size_t), ("max_batch", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("genomes", ctypes.c_void_p), ("n_genomes", ctypes.c_uint32), ("pair_id", ctypes.c_uint32),
+                ("k", ctypes.c_int32), ("tm_filter", ctypes.c_int32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("batch", ctypes.c_uint32), ("batch_size", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("n_sites", ctypes.c_uint64), ("n_amplicons", ctypes.c_uint64),
+                ("bases", ctypes.c_uint64), ("submit_ms", ctypes.c_double), ("start_ms", ctypes.c_double),
+                ("done_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 class NNTable(ctypes.Structure):
@@ -115,6 +135,10 @@ def lib():
             "ah_amplitypes": (I32, [P, U32, P, U64, P, P, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64), P]),
             "ah_generate_bases": (I32, [P, U64, P, U64, P, P, U64, U64, U64, P, P]),
             "ah_run_end": (I32, [P]),
+            "ah_serve_start": (I32, [P, U32, ctypes.POINTER(ServeConfig), ctypes.POINTER(P)]),
+            "ah_serve_submit": (I32, [P, ctypes.POINTER(Request), ctypes.POINTER(U64)]),
+            "ah_serve_wait": (I32, [P, U64, ctypes.POINTER(RequestInfo), P, U64, P, U64]),
+            "ah_serve_stop": (I32, [P]),
             "ah_tune_scan": (I32, [P, U32, P, U32, U64, ctypes.POINTER(TuneResult), P]),
             "ah_pair_noalloc": (I32, [P, U32, P, P, U64, P, U64, ctypes.POINTER(U64), P]),
             "ah_debug_compile_scan": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
@@ -172,6 +196,8 @@ class Context:
         self.h = h
 
     def close(self):
+        for srv in list(getattr(self, "_servers", ())):
+            srv.stop()
         if getattr(self, "h", None):
             self._lib.ah_destroy(self.h)
             self.h = None
@@ -402,6 +428,57 @@ class Context:
         out = np.zeros(max(total, 1), dtype=np.uint8)
         self.ah_fetch(set_id, amplicons, len(amplicons), out, total, offs)
         return out[:total].tobytes(), offs
+
+
+class Server:
+    """ah_serve_*: continuous batching of requests over one resident genome set.
+    The context belongs to the server's worker thread until stop()."""
+
+    def __init__(self, ctx: Context, set_id: int, mem_budget: int = 1 << 30, max_batch: int = 64):
+        self._lib = ctx._lib
+        self.ctx = ctx
+        cfg = ServeConfig(int(mem_budget), int(max_batch), 0)
+        h = ctypes.c_void_p()
+        ctx._check(self._lib.ah_serve_start(ctx.h, set_id, ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+        ctx.__dict__.setdefault("_servers", set()).add(self)
+
+    def submit(self, genomes, pair_id: int, k: int, tm_filter: bool = True) -> int:
+        g = np.ascontiguousarray(genomes, dtype=np.uint32)
+        req = Request(g.ctypes.data if len(g) else None, len(g), int(pair_id), int(k), int(bool(tm_filter)))
+        t = ctypes.c_uint64()
+        st = self._lib.ah_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if st != AH_OK:
+            raise AHError(st, "ah_serve_submit rejected the request")
+        return t.value
+
+    def wait(self, ticket: int):
+        """(sites, amplicons, info dict) of a submitted request."""
+        info = RequestInfo()
+        st = self._lib.ah_serve_wait(self.h, ticket, ctypes.byref(info), None, 0, None, 0)
+        if st == AH_OK:
+            return np.zeros(0, SITE_DTYPE), np.zeros(0, AMPLICON_DTYPE), info.as_dict()
+        if st != AH_ERR_OVERFLOW:
+            raise AHError(st, f"request {ticket} failed ({STATUS_NAMES.get(info.status, info.status)})")
+        sites = np.zeros(info.n_sites, SITE_DTYPE)
+        amps = np.zeros(info.n_amplicons, AMPLICON_DTYPE)
+        st = self._lib.ah_serve_wait(self.h, ticket, ctypes.byref(info), _ptr(sites), len(sites), _ptr(amps),
+                                     len(amps))
+        if st != AH_OK:
+            raise AHError(st, f"request {ticket}: results could not be read")
+        return sites, amps, info.as_dict()
+
+    def stop(self):
+        if getattr(self, "h", None):
+            self._lib.ah_serve_stop(self.h)
+            self.h = None
+            self.ctx.__dict__.get("_servers", set()).discard(self)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.stop()
 
 
 def debug_compile_scan(fwd: str, rev: str, k: int, R: int = 4, arith_pct: int = 0, order: int = 0):

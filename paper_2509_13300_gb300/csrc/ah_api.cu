@@ -7,8 +7,11 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <condition_variable>
+#include <deque>
 #include <mutex>
 #include <new>
+#include <thread>
 
 #include "ah_internal.h"
 
@@ -74,6 +77,7 @@ struct ah_ctx {
         FastRun fr;
     } pend;
     cudaEvent_t ev_run = nullptr; // recorded after the flag copy of a queued run
+    bool serving = false;         // a server's worker thread owns the context
     // caching allocator: large blocks released by the library are kept for reuse
     std::map<void *, size_t> live;             // block -> bytes
     std::multimap<size_t, void *> cached;      // bytes -> block
@@ -586,8 +590,9 @@ const ScanTuning &tuning_for(ah_ctx *c, const std::vector<ScanPattern> &pats)
 }
 
 // Launch the generated scan kernel over tiles [0, n_tiles) of a set.
+// Scan n_tiles tiles: the first n_tiles of the set, or tile_list[0 .. n_tiles) (device) when given.
 void launch_scan(ah_ctx *c, ScanKernel *k, const GenomeSet &gs, uint64_t n_tiles, uint64_t *keys, uint64_t cap,
-                 int pbits, cudaStream_t st)
+                 int pbits, cudaStream_t st, const uint64_t *tile_list = nullptr)
 {
     const uint64_t grid = std::min<uint64_t>(n_tiles, (uint64_t)c->sms * k->blocks_per_sm);
     const uint32_t *planes = gs.planes;
@@ -595,11 +600,12 @@ void launch_scan(ah_ctx *c, ScanKernel *k, const GenomeSet &gs, uint64_t n_tiles
     uint32_t nc = gs.n_contigs;
     uint64_t *work = c->d_flags + kFlagWork;
     AH_CUDA(cudaMemsetAsync(work, 0, sizeof(uint64_t), st));
-    void *args[] = {&planes, &n_tiles, &coff, &nc, &keys, &cap, &c->d_counter, &pbits, &c->d_err, &work};
+    void *args[] = {&planes, &n_tiles, &coff, &nc, &keys, &cap, &c->d_counter, &pbits, &c->d_err, &work, &tile_list};
     AH_CUDA(cudaLaunchKernel((const void *)k->fn, dim3((unsigned)grid), dim3(k->threads), args, k->smem, st));
 }
 
-std::vector<ScanPattern> patterns_of(ah_ctx *c, const uint32_t *pair_ids, uint32_t n_pairs)
+// The scan patterns of the listed pairs (k_override >= 0: that k for every pair).
+std::vector<ScanPattern> patterns_of(ah_ctx *c, const uint32_t *pair_ids, uint32_t n_pairs, int k_override = -1)
 {
     std::vector<ScanPattern> pats;
     for (uint32_t j = 0; j < n_pairs; ++j) {
@@ -608,7 +614,7 @@ std::vector<ScanPattern> patterns_of(ah_ctx *c, const uint32_t *pair_ids, uint32
             for (int strand = 0; strand < 2; ++strand) {
                 ScanPattern p;
                 p.L = pp.L[primer];
-                p.k = pp.params.k;
+                p.k = k_override >= 0 ? k_override : pp.params.k;
                 p.clamp = std::min(pp.params.clamp, p.L);
                 p.pair = (int)j;
                 p.primer = primer;
@@ -630,13 +636,15 @@ namespace {
 // Scan kernel over the whole set; keys land in the "scan_keys" scratch.
 // Returns the number of sites (one synchronisation; rerun once with a
 // larger key buffer if it overflowed).
+// tile_list (device, n_list entries): scan only those tiles.
 uint64_t scan_keys(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPattern> &pats, uint64_t **keys_out,
-                   cudaStream_t st)
+                   cudaStream_t st, const uint64_t *tile_list = nullptr, uint64_t n_list = 0)
 {
     const int pbits = std::max(1, bit_length(gs.n_bases));
     uint64_t count = 0;
     *keys_out = nullptr;
-    if (!gs.n_tiles)
+    const uint64_t n_tiles = tile_list ? n_list : gs.n_tiles;
+    if (!n_tiles)
         return 0;
     ScanKernel *k = scan_kernel(pats, tuning_for(c, pats), c->device);
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -644,7 +652,7 @@ uint64_t scan_keys(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPattern
         reset_flags(c, st);
         {
             Stage sg(c, "scan", st, 1);
-            launch_scan(c, k, gs, gs.n_tiles, keys, c->key_cap, pbits, st);
+            launch_scan(c, k, gs, n_tiles, keys, c->key_cap, pbits, st, tile_list);
         }
         check_flags(c, st);
         count = c->h_flags[0];
@@ -835,6 +843,7 @@ FastResult fast_end(ah_ctx *c, ah_run_out *o, cudaStream_t st, const ah_ctx::Fas
 void require_idle(ah_ctx *c)
 {
     require(!c->pend.active, AH_ERR_ARG, "a run is pending: complete it with ah_run_end first");
+    require(!c->serving, AH_ERR_ARG, "a server owns the context: stop it first");
 }
 
 void run_steps(ah_ctx *c, const GenomeSet &gs, const PairDev *pd, uint32_t n_pairs, uint64_t *keys, uint64_t ns,
@@ -923,6 +932,235 @@ void run_steps(ah_ctx *c, const GenomeSet &gs, const PairDev *pd, uint32_t n_pai
         throw Error(AH_ERR_OVERFLOW, "ah_run: an output buffer is too small (counts are in the out struct)");
 }
 
+
+// ---------------------------------------------------------------------------
+// Serving (continuous batching over one resident genome set).
+//
+// A worker thread owns the context while the server runs.  Requests wait in a
+// FIFO queue; each time the GPU is free the worker admits the queued requests
+// whose estimated device memory fits the budget (at least one), and runs them
+// as one batch: per primer pair, one scan over the union of their genomes'
+// tiles at the largest k among them, then sort, Tm and all-pairs amplicon
+// calling on those sites.  A request's result is then filtered exactly: its
+// genomes, its k (mm <= k) and, with its Tm filter, both sites passing.  A
+// site and an amplicon depend only on their own windows, so a request's result
+// does not depend on what it was batched with.
+// ---------------------------------------------------------------------------
+struct ServeReq {
+    std::vector<uint32_t> genomes;
+    uint32_t pair_id = 0;
+    int k = 0, tm_filter = 0;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    bool done = false;
+    ah_status status = AH_OK;
+    std::string msg;
+    uint32_t batch = 0, batch_size = 0;
+    uint64_t n_sites = 0, bases = 0;
+    std::vector<ah_site> sites;
+    std::vector<ah_amplicon> amps;
+};
+
+} // namespace
+
+struct ah_server {
+    ah_ctx *c = nullptr;
+    uint32_t set_id = 0;
+    ah_serve_config cfg{};
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::map<uint64_t, ServeReq> reqs;
+    std::deque<uint64_t> queue;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    std::vector<uint64_t> genome_bases; // bases per genome id
+    std::vector<std::vector<uint32_t>> genome_contigs;
+    double now_ms() const
+    {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+// device bytes a request's share of a batch may need (sites and amplicons grow with bases)
+size_t serve_request_bytes(const ServeReq &r) { return 4096 + (size_t)(r.bases / 1000) * 64; }
+
+// One batch: fills every request's result fields.
+void serve_batch(ah_server *S, std::vector<ServeReq *> &batch)
+{
+    ah_ctx *c = S->c;
+    GenomeSet &gs = get_set(c, S->set_id);
+    cudaStream_t st = c->stream;
+    std::map<uint32_t, std::vector<ServeReq *>> groups;
+    for (ServeReq *r : batch)
+        groups[r->pair_id].push_back(r);
+    for (auto &kv : groups) {
+        const uint32_t pid = kv.first;
+        std::vector<ServeReq *> &rs = kv.second;
+        int kmax = 0;
+        std::vector<char> in_union(gs.max_genome + 1, 0);
+        for (ServeReq *r : rs) {
+            kmax = std::max(kmax, r->k);
+            for (uint32_t g : r->genomes)
+                if (g <= gs.max_genome)
+                    in_union[g] = 1;
+        }
+        // tiles holding a start of a union genome's contig
+        std::vector<char> tflag(gs.n_tiles, 0);
+        for (uint32_t ci = 0; ci < gs.n_contigs; ++ci) {
+            const uint64_t a = gs.contig_off_h[ci], b = gs.contig_off_h[ci + 1];
+            if (b > a && in_union[gs.contig_genome_h[ci]])
+                for (uint64_t t = a / kTileBases; t <= (b - 1) / kTileBases; ++t)
+                    tflag[t] = 1;
+        }
+        std::vector<uint64_t> tiles;
+        for (uint64_t t = 0; t < gs.n_tiles; ++t)
+            if (tflag[t])
+                tiles.push_back(t);
+        std::vector<ah_site> sites_h;
+        std::vector<uint8_t> pass_h;
+        std::vector<ah_amplicon> amps_h;
+        if (!tiles.empty()) {
+            uint64_t *tl = (uint64_t *)scratch(c, "serve_tiles", tiles.size() * sizeof(uint64_t));
+            AH_CUDA(cudaMemcpyAsync(tl, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+            std::vector<ScanPattern> pats = patterns_of(c, &pid, 1, kmax);
+            const PairDev *pd = upload_pairs(c, &pid, 1, st);
+            uint64_t *keys = nullptr;
+            const uint64_t ns = scan_keys(c, gs, pats, &keys, st, tl, tiles.size());
+            if (ns) {
+                ah_site *sites = (ah_site *)scratch(c, "serve_sites", ns * sizeof(ah_site));
+                sort_decode(c, gs, 1, keys, ns, sites, st);
+                float *tm = (float *)scratch(c, "serve_tm", ns * sizeof(float));
+                uint8_t *pass = (uint8_t *)scratch(c, "serve_pass", ns);
+                uint32_t *q = (uint32_t *)scratch(c, "tm_queue", ns * sizeof(uint32_t));
+                {
+                    Stage sg(c, "tm", st, 2);
+                    launch_tm(sites, ns, nullptr, pd, 1, gs.planes, gs.contig_off, tm, pass, q,
+                              (uint32_t *)(c->d_flags + kFlagTmQueue), tm_seg_max(c), tm_few_exact(c), c->d_err, st);
+                }
+                uint64_t *counts = (uint64_t *)scratch(c, "pair_counts", ns * sizeof(uint64_t));
+                uint64_t *offs = (uint64_t *)scratch(c, "pair_offsets", ns * sizeof(uint64_t));
+                size_t tb = scan_u64_temp_bytes(ns);
+                void *temp = scratch(c, "scan_temp", tb);
+                {
+                    Stage sg(c, "pair", st, 2 + scan_u64_launches(ns));
+                    launch_pair_count(sites, ns, nullptr, nullptr, pd, counts, st);
+                    exclusive_scan_u64(temp, tb, counts, offs, ns, st);
+                    launch_total(offs, counts, ns, nullptr, 0, c->d_aux, 0, nullptr, nullptr, 0, st);
+                }
+                check_flags(c, st);
+                const uint64_t na = c->h_flags[kFlagAux];
+                ah_amplicon *amps = (ah_amplicon *)scratch(c, "serve_amps", std::max<uint64_t>(na, 1) * sizeof(ah_amplicon));
+                if (na) {
+                    Stage sg(c, "pair", st, 1);
+                    launch_pair_write(sites, ns, nullptr, nullptr, pd, offs, amps, na, nullptr, 0, st);
+                }
+                sites_h.resize(ns);
+                pass_h.resize(ns);
+                amps_h.resize(na);
+                AH_CUDA(cudaMemcpyAsync(sites_h.data(), sites, ns * sizeof(ah_site), cudaMemcpyDeviceToHost, st));
+                AH_CUDA(cudaMemcpyAsync(pass_h.data(), pass, ns, cudaMemcpyDeviceToHost, st));
+                if (na)
+                    AH_CUDA(cudaMemcpyAsync(amps_h.data(), amps, na * sizeof(ah_amplicon), cudaMemcpyDeviceToHost, st));
+                check_flags(c, st);
+            }
+        }
+        // per request: its genomes, its k, its Tm filter
+        std::vector<char> mine(gs.max_genome + 1, 0);
+        std::vector<int64_t> new_index(sites_h.size());
+        for (ServeReq *r : rs) {
+            for (uint32_t g : r->genomes)
+                if (g <= gs.max_genome)
+                    mine[g] = 1;
+            r->sites.clear();
+            for (size_t i = 0; i < sites_h.size(); ++i) {
+                const ah_site &x = sites_h[i];
+                const bool ok = x.genome <= gs.max_genome && mine[x.genome] && x.mm <= r->k;
+                new_index[i] = ok ? (int64_t)r->sites.size() : -1;
+                if (ok)
+                    r->sites.push_back(x);
+            }
+            r->n_sites = r->sites.size();
+            r->amps.clear();
+            for (const ah_amplicon &a : amps_h) {
+                if (new_index[a.left] < 0 || new_index[a.right] < 0)
+                    continue;
+                if (r->tm_filter && !(pass_h[a.left] && pass_h[a.right]))
+                    continue;
+                ah_amplicon b = a;
+                b.left = (uint32_t)new_index[a.left]; // indices into the request's own site list
+                b.right = (uint32_t)new_index[a.right];
+                r->amps.push_back(b);
+            }
+            for (uint32_t g : r->genomes)
+                if (g <= gs.max_genome)
+                    mine[g] = 0;
+        }
+    }
+}
+
+void serve_loop(ah_server *S)
+{
+    cudaSetDevice(S->c->device);
+    uint32_t batch_no = 0;
+    for (;;) {
+        std::vector<uint64_t> tickets;
+        std::vector<ServeReq> work;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+            if (S->queue.empty())
+                return; // stopped with nothing pending
+            size_t mem = 0;
+            const double t = S->now_ms();
+            while (!S->queue.empty() && tickets.size() < S->cfg.max_batch) {
+                ServeReq &r = S->reqs[S->queue.front()];
+                const size_t need = serve_request_bytes(r);
+                if (!tickets.empty() && mem + need > S->cfg.mem_budget)
+                    break; // admitted later, when the running work has left
+                mem += need;
+                r.t_start = t;
+                tickets.push_back(S->queue.front());
+                work.push_back(r); // a copy: the map may grow while the batch runs
+                S->queue.pop_front();
+            }
+        }
+        ++batch_no;
+        std::vector<ServeReq *> ptrs;
+        for (ServeReq &r : work)
+            ptrs.push_back(&r);
+        ah_status status = AH_OK;
+        std::string msg;
+        try {
+            serve_batch(S, ptrs);
+        } catch (const Error &e) {
+            status = e.status;
+            msg = e.msg;
+        } catch (const std::exception &e) {
+            status = AH_ERR_ARG;
+            msg = e.what();
+        }
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            const double t = S->now_ms();
+            for (size_t i = 0; i < tickets.size(); ++i) {
+                ServeReq &r = S->reqs[tickets[i]];
+                r.amps = std::move(work[i].amps);
+                r.sites = std::move(work[i].sites);
+                r.n_sites = work[i].n_sites;
+                r.batch_size = (uint32_t)tickets.size();
+                r.status = status;
+                r.msg = msg;
+                r.batch = batch_no;
+                r.t_done = t;
+                r.done = true;
+            }
+        }
+        S->cv_done.notify_all();
+    }
+}
 } // namespace
 
 // ===========================================================================
@@ -1131,6 +1369,8 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
         gs->n_bases = n_bases;
         gs->n_contigs = n_contigs;
         gs->n_tiles = (n_bases + kTileBases - 1) / kTileBases;
+        gs->contig_off_h.assign(contig_off, contig_off + n_contigs + 1);
+        gs->contig_genome_h.assign(contig_genome, contig_genome + n_contigs);
         {
             std::vector<uint32_t> ids(contig_genome, contig_genome + n_contigs);
             std::sort(ids.begin(), ids.end());
@@ -1879,6 +2119,114 @@ ah_status ah_fetch(ah_ctx *c, uint32_t set_id, const ah_amplicon *amplicons, uin
         out_finish(seq_out, dst, total, st);
         AH_CUDA(cudaStreamSynchronize(st));
     });
+}
+
+
+ah_status ah_serve_start(ah_ctx *c, uint32_t set_id, const ah_serve_config *cfg, ah_server **out)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require_idle(c);
+        require(out && cfg && cfg->max_batch >= 1 && cfg->mem_budget > 0, AH_ERR_ARG, "ah_serve_start: bad argument");
+        *out = nullptr;
+        GenomeSet &gs = get_set(c, set_id);
+        AH_CUDA(cudaStreamSynchronize(c->stream));
+        auto S = std::make_unique<ah_server>();
+        S->c = c;
+        S->set_id = set_id;
+        S->cfg = *cfg;
+        S->genome_bases.assign((size_t)gs.max_genome + 1, 0);
+        for (uint32_t ci = 0; ci < gs.n_contigs; ++ci)
+            S->genome_bases[gs.contig_genome_h[ci]] += gs.contig_off_h[ci + 1] - gs.contig_off_h[ci];
+        c->serving = true;
+        S->worker = std::thread(serve_loop, S.get());
+        *out = S.release();
+    });
+}
+
+ah_status ah_serve_submit(ah_server *S, const ah_request *req, uint64_t *ticket_out)
+{
+    if (!S || !req || !ticket_out || (req->n_genomes && !req->genomes))
+        return AH_ERR_ARG;
+    if (req->k < 0 || req->k > AH_MAX_MISMATCHES)
+        return AH_ERR_ARG;
+    ServeReq r;
+    r.genomes.assign(req->genomes, req->genomes + req->n_genomes);
+    std::sort(r.genomes.begin(), r.genomes.end());
+    r.genomes.erase(std::unique(r.genomes.begin(), r.genomes.end()), r.genomes.end());
+    r.pair_id = req->pair_id;
+    r.k = req->k;
+    r.tm_filter = req->tm_filter;
+    for (uint32_t g : r.genomes)
+        if (g < S->genome_bases.size())
+            r.bases += S->genome_bases[g];
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop || !S->c->pairs.count(req->pair_id))
+            return AH_ERR_ARG;
+        r.t_submit = S->now_ms();
+        const uint64_t t = S->next_ticket++;
+        S->reqs.emplace(t, std::move(r));
+        S->queue.push_back(t);
+        *ticket_out = t;
+    }
+    S->cv_work.notify_one();
+    return AH_OK;
+}
+
+ah_status ah_serve_wait(ah_server *S, uint64_t ticket, ah_request_info *info, ah_site *sites_out, uint64_t sites_cap,
+                        ah_amplicon *amps_out, uint64_t amps_cap)
+{
+    if (!S || !info)
+        return AH_ERR_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end())
+        return AH_ERR_ARG;
+    S->cv_done.wait(lk, [&] { return it->second.done; });
+    ServeReq &r = it->second;
+    info->status = r.status;
+    info->batch = r.batch;
+    info->batch_size = r.batch_size;
+    info->reserved = 0;
+    info->n_sites = r.sites.size();
+    info->n_amplicons = r.amps.size();
+    info->bases = r.bases;
+    info->submit_ms = r.t_submit;
+    info->start_ms = r.t_start;
+    info->done_ms = r.t_done;
+    if (r.status != AH_OK) {
+        const ah_status st = r.status;
+        S->reqs.erase(it);
+        return st;
+    }
+    if (r.sites.size() > sites_cap || r.amps.size() > amps_cap)
+        return AH_ERR_OVERFLOW; // kept: ask again with room
+    if ((!r.sites.empty() && !sites_out) || (!r.amps.empty() && !amps_out))
+        return AH_ERR_ARG;
+    if (!r.sites.empty())
+        memcpy(sites_out, r.sites.data(), r.sites.size() * sizeof(ah_site));
+    if (!r.amps.empty())
+        memcpy(amps_out, r.amps.data(), r.amps.size() * sizeof(ah_amplicon));
+    S->reqs.erase(it);
+    return AH_OK;
+}
+
+ah_status ah_serve_stop(ah_server *S)
+{
+    if (!S)
+        return AH_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable())
+        S->worker.join();
+    S->c->serving = false;
+    delete S;
+    return AH_OK;
 }
 
 } // extern "C"

@@ -47,6 +47,8 @@ struct GenomeSet {
     cudaEvent_t ready = nullptr;
     uint32_t max_genome = 0; // largest genome id
     uint64_t n_genomes = 0;  // distinct genome ids
+    std::vector<uint64_t> contig_off_h;    // host copies (request planning of the server)
+    std::vector<uint32_t> contig_genome_h;
 };
 
 // One registered primer pair.  mask[i] is the 4-bit IUPAC set of primer

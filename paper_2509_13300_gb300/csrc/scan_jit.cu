@@ -352,13 +352,14 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
     os << "extern \"C\" __global__ void __launch_bounds__(NT, " << t.min_blocks << ")\n"
        << "ah_scan_kernel(const u32 *__restrict__ planes, u64 n_tiles, const u64 *__restrict__ contig_off,\n"
        << "               u32 n_contigs, u64 *__restrict__ keys, u64 cap, u64 *__restrict__ counter, int pbits,\n"
-       << "               int *__restrict__ err, u64 *__restrict__ work)\n{\n"
+       << "               int *__restrict__ err, u64 *__restrict__ work, const u64 *__restrict__ tile_list)\n{\n"
        << "  // Every warp claims slices of tiles (32*R words of each plane plus a 32-word\n"
        << "  // overhang) from the shared counter `work` (zeroed before the launch), so SMs\n"
        << "  // that run faster take more, and runs its own S-stage pipeline: lane 0 claims\n"
        << "  // and starts bulk async copies (TMA) into the warp's buffers, one mbarrier\n"
        << "  // per stage; no CTA-wide barrier is ever taken.  A warp's claims only grow,\n"
        << "  // so the first claim past the end means that none of its stages holds work.\n"
+       << "  // With tile_list, the n_tiles tiles scanned are tile_list[0 .. n_tiles).\n"
        << "  extern __shared__ __align__(128) u32 smbuf[];\n"
        << "  __shared__ __align__(8) u64 bars[WPC * S];\n"
        << "  __shared__ u64 claims[WPC * S];\n"
@@ -373,7 +374,7 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "  }\n"
        << "  __syncwarp();\n"
        << "  auto issue = [&](u64 wi, int stg) {\n"
-       << "    const u64 tl = wi / SLICES;\n"
+       << "    const u64 tl = tile_list ? tile_list[wi / SLICES] : wi / SLICES;\n"
        << "    const int sl = (int)(wi % SLICES);\n"
        << "    asm volatile(\"mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\" ::\"r\"(smem_addr(&wbar[stg])),\n"
        << "                 \"r\"((u32)(4 * SLW * 4)) : \"memory\");\n"
@@ -402,7 +403,7 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "      }\n"
        << "      break;\n"
        << "    }\n"
-       << "    const u64 tile = wi / SLICES;\n"
+       << "    const u64 tile = tile_list ? tile_list[wi / SLICES] : wi / SLICES;\n"
        << "    const int wbase = (int)(wi % SLICES) * 32 * R;\n"
        << "    const u32 *sm = wbuf + stg * 4 * SLW;\n"
        << "    const int j0 = lane * R;\n"

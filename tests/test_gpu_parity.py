@@ -685,3 +685,70 @@ def test_large_workload_shape_on_device_generated_genomes(ctx):
     ok = ~np.isnan(o_tm)
     assert np.abs(r["tm"][ok] - o_tm[ok]).max() <= TM_TOL
     assert r["amps"].tobytes() == o_amps.tobytes()
+
+
+def _served_oracle(w, pair, genomes, k, tm_filter):
+    """A request's result by the plain definition: the pair scanned at the
+    request's k over the pool, sites of the named genomes kept, Tm and
+    amplicon calling on those sites alone."""
+    p = dict(pair, k=k)
+    sites = oracle.scan(w.seq, w.contig_off, w.contig_genome, [p])
+    sites = sites[np.isin(sites["genome"], np.asarray(genomes, dtype=np.uint32))]
+    passed = None
+    if tm_filter and len(sites):
+        _, passed = oracle.tm(w.seq, w.contig_off, sites, [p])
+    return sites, oracle.pair(sites, [p], passed)
+
+
+def test_served_requests_alone_and_in_the_mix(ctx):
+    """ah_serve_*: every request's result is the same whether it runs alone
+    (one request per batch), in large mixed batches, or in batches cut short
+    by the memory budget, and equals the plain definition on the pool."""
+    pairs = [synth.pcr_params(*synth.PAPER_PAIRS["Titan"], k=3, min_len=100, max_len=3000, tm_min=45.0),
+             synth.pcr_params(*synth.PAPER_PAIRS["V3V4"], k=2, min_len=100, max_len=3000, tm_min=50.0)]
+    w = synth.collection(seed=12, n_genomes=10, len_lo=1.5e5, len_hi=5e5, pairs=pairs, max_subs=3)
+    n_g = int(w.contig_genome.max()) + 1
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(24):
+        g = rng.choice(n_g, size=int(rng.integers(1, n_g + 1)), replace=False)
+        reqs.append((g.astype(np.uint32), int(rng.integers(len(pairs))), int(rng.integers(0, 4)),
+                     bool(rng.integers(2))))
+    reqs.append((np.zeros(0, np.uint32), 0, 2, True))                      # no genomes
+    reqs.append((np.array([n_g + 5, 1, 1], np.uint32), 1, 1, False))       # unknown id and a duplicate
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    pids = [ctx.ah_set_primers(p["fwd"], p["rev"], p) for p in pairs]
+    try:
+        def serve(max_batch, mem_budget, one_at_a_time):
+            out = []
+            with ah.Server(ctx, sid, mem_budget=mem_budget, max_batch=max_batch) as srv:
+                if one_at_a_time:
+                    for g, j, k, f in reqs:
+                        out.append(srv.wait(srv.submit(g, pids[j], k, f)))
+                else:
+                    tickets = [srv.submit(g, pids[j], k, f) for g, j, k, f in reqs]
+                    out = [srv.wait(t) for t in tickets]
+            return out
+
+        alone = serve(1, 1 << 30, True)
+        mixed = serve(64, 1 << 30, False)
+        budget = serve(64, 200_000, False)
+        # the context is usable again after the servers stopped
+        assert len(ctx.scan(sid, [pids[0]])) > 0
+    finally:
+        ctx.ah_unload_genomes(sid)
+    assert max(i["batch_size"] for _, _, i in mixed) > 8
+    assert max(i["batch_size"] for _, _, i in budget) < max(i["batch_size"] for _, _, i in mixed)
+    assert all(i["batch_size"] == 1 for _, _, i in alone)
+    total_amps = 0
+    for n, ((g, j, k, f), a, m, b) in enumerate(zip(reqs, alone, mixed, budget)):
+        for x in (m, b):
+            assert x[0].tobytes() == a[0].tobytes(), n
+            assert x[1].tobytes() == a[1].tobytes(), n
+        info = a[2]
+        assert info["status"] == 0 and info["submit_ms"] <= info["start_ms"] <= info["done_ms"]
+        want_s, want_a = _served_oracle(w, pairs[j], [x for x in g if x < n_g], k, f)
+        assert a[0].tobytes() == want_s.tobytes(), n
+        assert a[1].tobytes() == want_a.tobytes(), n
+        total_amps += len(want_a)
+    assert total_amps > 10
