@@ -239,9 +239,30 @@ def main():
     ap.add_argument("--n-genomes", type=int, default=100, help="smaller collections for profiling runs")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="one set at a time (default: the next set packs on a second stream after the current scan)")
+    ap.add_argument("--form", default="plain", choices=["plain", "batched", "served", "large"],
+                    help="plain: the genome-collection line (default); batched / served: those forms' lines")
+    ap.add_argument("--chunk-bases", type=int, default=2_000_000_000, help="batched: bases per set (whole genomes)")
+    ap.add_argument("--plain-genomes", type=int, default=400, help="batched: genomes timed in the plain form")
+    ap.add_argument("--requests", type=int, default=200, help="served: requests")
+    ap.add_argument("--rate", type=float, default=20.0, help="served: Poisson arrivals per second")
+    ap.add_argument("--max-batch", type=int, default=64, help="served: requests per batch")
+    ap.add_argument("--mem-budget", type=int, default=4 << 30, help="served: bytes one batch may plan for")
+    ap.add_argument("--large-chunk", type=int, default=16_000_000_000, help="large: bases per chunk (whole genomes)")
+    ap.add_argument("--check-genomes", type=int, default=6, help="large: sampled genomes checked by the oracle here")
+    ap.add_argument("--dump-genomes", type=int, default=0, help="large: sampled genomes whose GPU results are saved")
+    ap.add_argument("--dump-path", default="gpurun_out/large_sample.npz")
+    ap.add_argument("--check-dump", default=None, help="oracle check of a large-form dump (CPU only)")
     args = ap.parse_args()
+    if args.check_dump:
+        sys.exit(check_large_dump(args.check_dump))
     if args.impl == "reference":
         return run_reference(args)
+    if args.form == "batched":
+        return bench_batched(args)
+    if args.form == "served":
+        return bench_served(args)
+    if args.form == "large":
+        return bench_large(args)
 
     rank, world, local = dist_info()
     import torch
@@ -436,6 +457,584 @@ def ctx_scan_lop_count(pair: dict, tune: dict) -> int:
     from paper_2509_13300_gb300 import ah
     return ah.scan_lop3_per_word(pair["fwd"], pair["rev"], int(pair["k"]), tune["R"], tune["arith_pct"])
 
+
+
+# ---------------------------------------------------------------------------
+# Batched and served forms (bench.py --form batched | served): one JSON line
+# each, beside the plain form's.  Genomes come from the counter-based
+# generator, made on the device (ah_generate_bases).
+# ---------------------------------------------------------------------------
+def form_pairs(n: int, seed: int, ks):
+    """n degenerate pairs: the paper's four (Sec. 2.3), then random IUPAC pairs of 17-25 nt."""
+    from paper_2509_13300_gb300 import synth
+    rng = np.random.default_rng(seed)
+    fr = list(synth.PAPER_PAIRS.values())
+    while len(fr) < n:
+        fr.append((synth.random_primer(rng, int(rng.integers(17, 26)), "RYSWKM"),
+                   synth.random_primer(rng, int(rng.integers(17, 26)), "RYSWKM")))
+    return [synth.pcr_params(f, r, k=int(ks[i % len(ks)]), min_len=100, max_len=3000, tm_min=45.0)
+            for i, (f, r) in enumerate(fr[:n])]
+
+
+def device_collection(ctx, coll, torch, chunk: int = 1 << 31):
+    """The collection's ASCII bases in device memory, generated on the device."""
+    dev = torch.empty(coll.n_bases, dtype=torch.uint8, device="cuda")
+    for b0 in range(0, coll.n_bases, chunk):
+        ctx.generate_bases(coll, b0, min(chunk, coll.n_bases - b0), dev[b0:])
+    torch.cuda.synchronize()
+    return dev
+
+
+def genome_chunks(coll, max_bases: int):
+    """Consecutive genome ranges [g0, g1) of at most max_bases bases (one genome at least)."""
+    goff = coll.genome_off
+    out, g0 = [], 0
+    G = len(goff) - 1
+    while g0 < G:
+        g1 = int(np.searchsorted(goff, goff[g0] + max_bases, side="right")) - 1
+        g1 = min(G, max(g1, g0 + 1))
+        out.append((g0, g1))
+        g0 = g1
+    return out
+
+
+def sub_tables(coll, g0: int, g1: int):
+    """Base range and rebased contig tables of genomes [g0, g1)."""
+    b0, b1 = int(coll.genome_off[g0]), int(coll.genome_off[g1])
+    c0 = int(np.searchsorted(coll.contig_off, b0, side="left"))
+    c1 = int(np.searchsorted(coll.contig_off, b1, side="left"))
+    off = np.ascontiguousarray(coll.contig_off[c0:c1 + 1] - np.uint64(b0))
+    gen = np.ascontiguousarray(coll.contig_genome[c0:c1])
+    return b0, b1, off, gen
+
+
+class HostOut:
+    """Pinned host output buffers of one ah_run (grown on overflow)."""
+
+    def __init__(self, torch, ah, caps=(1 << 16, 1 << 14, 1 << 24)):
+        self.torch, self.ah = torch, ah
+        self.alloc(caps)
+
+    def alloc(self, caps):
+        t = self.torch
+        s, a, q = (max(int(x), 1) for x in caps)
+        self.caps = (s, a, q)
+        self.b = [t.empty(n, dtype=t.uint8).pin_memory() for n in (16 * s, 4 * s, s, 28 * a, q, 8 * (a + 1))]
+        self.o = self.ah.RunOut(self.b[0].data_ptr(), s, 0, self.b[1].data_ptr(), self.b[2].data_ptr(),
+                                self.b[3].data_ptr(), a, 0, self.b[4].data_ptr(), q, 0, self.b[5].data_ptr(), 1, 0)
+
+    def run(self, ctx, sid, pids, stream):
+        for _ in range(3):
+            try:
+                return ctx.ah_run(sid, pids, self.o, stream)
+            except self.ah.AHError as e:
+                if e.status != self.ah.AH_ERR_OVERFLOW:
+                    raise
+                o = self.o
+                self.alloc((o.n_sites * 5 // 4 + 1, o.n_amplicons * 5 // 4 + 1, o.n_seq * 5 // 4 + 1))
+        raise RuntimeError("ah_run kept overflowing")
+
+    def d2h_bytes(self):
+        o = self.o
+        return 21 * o.n_sites + 28 * o.n_amplicons + o.n_seq + 8 * (o.n_amplicons + 1)
+
+
+def bench_batched(args):
+    """Batched form: thousands of genomes of uneven length per set, streamed
+    from pinned host memory in double-buffered chunks, several pairs in one
+    scan launch; against the plain form (one genome per load and run)."""
+    import torch
+    from paper_2509_13300_gb300 import ah, build, countergen
+    build.build()
+    torch.cuda.set_device(0)
+    n_g = args.n_genomes if args.n_genomes != 100 else 10_000
+    pairs = form_pairs(4, 11, (3, 4, 4, 2))
+    t0 = time.perf_counter()
+    coll = countergen.collection(seed=11, n_genomes=n_g, len_lo=0.5e6, len_hi=8e6, pairs=pairs)
+    t_layout = time.perf_counter() - t0
+    ctx = ah.Context(0)
+    pids = [ctx.ah_set_primers(p["fwd"], p["rev"], p) for p in pairs]
+    N = coll.n_bases
+    # the collection in pinned host memory (generated on the device, copied down once)
+    host = torch.empty(N, dtype=torch.uint8, pin_memory=True)
+    gen = torch.empty(min(N, 1 << 31), dtype=torch.uint8, device="cuda")
+    for b0 in range(0, N, len(gen)):
+        n = min(len(gen), N - b0)
+        ctx.generate_bases(coll, b0, n, gen)
+        host[b0:b0 + n].copy_(gen[:n])
+    del gen
+    chunks = genome_chunks(coll, args.chunk_bases)
+    tabs = [sub_tables(coll, g0, g1) for g0, g1 in chunks]
+    cmax = max(b1 - b0 for b0, b1, _, _ in tabs)
+    dbuf = [torch.empty(cmax, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    cs = torch.cuda.Stream()                              # host-to-device copies
+    st = [torch.cuda.Stream(), torch.cuda.Stream()]       # two sets in flight
+    copied = [torch.cuda.Event() for _ in range(2)]
+    packed = [torch.cuda.Event() for _ in range(2)]
+    scan_done = torch.cuda.Event()
+    outs = HostOut(torch, ah)
+    totals = {}
+
+    def copy(i):
+        b0, b1, _, _ = tabs[i]
+        with torch.cuda.stream(cs):
+            if i >= 2:
+                cs.wait_event(packed[i % 2])            # buffer free once chunk i-2 is packed
+            dbuf[i % 2][:b1 - b0].copy_(host[b0:b1], non_blocking=True)
+            copied[i % 2].record(cs)
+
+    def load(i):
+        b0, b1, off, gen_ = tabs[i]
+        s = st[i % 2]
+        s.wait_event(copied[i % 2])
+        sid = ctx.ah_load_genomes(dbuf[i % 2], b1 - b0, off, gen_, s)
+        packed[i % 2].record(s)
+        return sid
+
+    def one_pass():
+        """Every chunk once: set i+1 packs on the other stream while set i runs,
+        and chunk i+2 crosses the link meanwhile."""
+        n_s = n_a = n_q = d2h = 0
+        for i in range(min(2, len(tabs))):
+            copy(i)
+        sid = load(0)
+        for i in range(len(tabs)):
+            nxt = load(i + 1) if i + 1 < len(tabs) else None
+            if i + 2 < len(tabs):
+                copy(i + 2)
+            outs.run(ctx, sid, pids, st[i % 2])
+            n_s, n_a, n_q = n_s + outs.o.n_sites, n_a + outs.o.n_amplicons, n_q + outs.o.n_seq
+            d2h += outs.d2h_bytes()
+            ctx.ah_unload_genomes(sid)
+            sid = nxt
+        totals.update(sites=n_s, amplicons=n_a, seq=n_q, d2h_bytes=d2h)
+
+    copy(0)
+    sid0 = load(0)
+    tune = None if args.no_tune else ctx.ah_tune_scan(sid0, pids, 0, st[0])
+    ctx.ah_unload_genomes(sid0)
+    torch.cuda.synchronize()
+    for _ in range(max(1, args.warmup)):
+        one_pass()
+    torch.cuda.synchronize()
+    ctx.ah_set_profiling(0)
+    ctx.ah_get_profile(None)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        clk.wait_first()
+        clk.mark(True)
+        e0.record(st[0])
+        for _ in range(args.steps):
+            one_pass()
+        st[0].wait_stream(st[1])
+        st[0].wait_stream(cs)
+        e1.record(st[0])
+        torch.cuda.synchronize()
+        clk.mark(False)
+    _, launches, _ = ctx.ah_get_profile(None)
+    t_batched = e0.elapsed_time(e1) / 1e3
+    # stage split: one more pass with events around every stage (untimed)
+    ctx.ah_set_profiling(1)
+    one_pass()
+    stages = {}
+    for name in ("pack", "scan", "sort", "decode", "tm", "pair", "fetch", "host.run", "host.run.wait", "host.load"):
+        ms, l, calls = ctx.ah_get_profile(name)
+        stages[name] = {"ms": ms, "launches": l}
+    ctx.ah_set_profiling(0)
+    gbps = N * len(pairs) * args.steps / t_batched / 1e9
+    # plain form: one genome per load and per run (host input, host outputs), on a sample
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(n_g, size=min(n_g, args.plain_genomes), replace=False))
+    plain_out = HostOut(torch, ah)
+    hs = torch.cuda.current_stream()
+
+    def plain(g):
+        b0, b1, off, gen_ = sub_tables(coll, int(g), int(g) + 1)
+        sid = ctx.ah_load_genomes(host[b0:b1], b1 - b0, off, gen_, hs)
+        plain_out.run(ctx, sid, pids, hs)
+        ctx.ah_unload_genomes(sid)
+        return b1 - b0
+
+    for g in sample[:5]:
+        plain(g)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nb = sum(plain(g) for g in sample)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    gbps_plain = nb * len(pairs) / t_plain / 1e9
+    line = {
+        "form": "batched", "metric": "Gbp/s scanned per primer pair (both strands, k mm)", "value": gbps,
+        "unit": "Gbp/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "s_per_pass": t_batched / args.steps, "higher_is_better": True, "data": "synthetic (counter-based, seed 11)",
+        "config": {"workload": f"batched-{n_g}genomes-{N / 1e9:.1f}Gbp-{len(pairs)}pairs",
+                   "n_genomes": n_g, "n_bases": N, "n_contigs": len(coll.contig_genome),
+                   "pairs": [(p["fwd"], p["rev"], p["k"]) for p in pairs], "chunks": len(tabs),
+                   "chunk_bases_max": cmax, "input": "pinned host memory, H2D copy of chunk i+2 overlapping "
+                   "set i's run and set i+1's packing", "outputs": "pinned host (sites, Tm, pass, amplicons, "
+                   "sequences)", "scan_tuning": tune, "layout_s": t_layout},
+        "results_per_pass": totals, "gpu_launches_per_pass": launches / max(1, args.steps),
+        "plain": {"value": gbps_plain, "unit": "Gbp/s", "genomes": len(sample), "bases": int(nb),
+                  "form": "one genome per ah_load_genomes (host input) and per ah_run (4 pairs, host outputs)",
+                  "s": t_plain},
+        "batched_over_plain": gbps / gbps_plain, "clocks": clk.summary(), "stages_ms_one_pass": stages,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def bench_served(args):
+    """Served form: a request loop over a resident pool; Poisson arrivals, then
+    a saturated burst, against sequential plain solves of the same requests."""
+    import torch
+    from paper_2509_13300_gb300 import ah, build, countergen
+    build.build()
+    torch.cuda.set_device(0)
+    n_g = args.n_genomes if args.n_genomes != 100 else 5_000
+    pairs = form_pairs(8, 13, (4,))
+    t0 = time.perf_counter()
+    coll = countergen.collection(seed=13, n_genomes=n_g, len_lo=2e6, len_hi=7e6, pairs=pairs)
+    t_layout = time.perf_counter() - t0
+    ctx = ah.Context(0)
+    pid = [ctx.ah_set_primers(p["fwd"], p["rev"], p) for p in pairs]
+    dev = device_collection(ctx, coll, torch)
+    N = coll.n_bases
+    sid = ctx.ah_load_genomes(dev, N, coll.contig_off, coll.contig_genome)
+    # requests: Zipf subset size over 1..n_g (P(s) ~ 1/s), a contiguous run of genomes
+    rng = np.random.default_rng(17)
+    R = args.requests
+    w = 1.0 / np.arange(1, n_g + 1)
+    sizes = rng.choice(np.arange(1, n_g + 1), size=R, p=w / w.sum())
+    starts = np.array([rng.integers(0, n_g - s + 1) for s in sizes])
+    req = [(int(a), int(a + s), int(rng.integers(len(pairs))), int(rng.integers(0, 5))) for a, s in zip(starts, sizes)]
+    gbases = np.diff(coll.genome_off.astype(np.int64))
+    req_bases = [int(gbases[a:b].sum()) for a, b, _, _ in req]
+
+    def serve(arrivals, max_batch, budget):
+        import threading as th
+        res = [None] * R
+        with ah.Server(ctx, sid, mem_budget=budget, max_batch=max_batch) as srv:
+            tickets = [None] * R
+            ready = [th.Event() for _ in range(R)]
+
+            def submitter():
+                t_start = time.perf_counter()
+                for i, (a, b, j, k) in enumerate(req):
+                    dt = arrivals[i] - (time.perf_counter() - t_start)
+                    if dt > 0:
+                        time.sleep(dt)
+                    tickets[i] = srv.submit(np.arange(a, b, dtype=np.uint32), pid[j], k, True)
+                    ready[i].set()
+
+            thr = th.Thread(target=submitter)
+            thr.start()
+            for i in range(R):
+                ready[i].wait()
+                res[i] = srv.wait(tickets[i])
+            thr.join()
+        info = [r[4] for r in res]
+        lat = np.array([x["done_ms"] - x["submit_ms"] for x in info])
+        span = (max(x["done_ms"] for x in info) - min(x["submit_ms"] for x in info)) / 1e3
+        return res, {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "mean_ms": float(lat.mean()), "makespan_s": span,
+                     "gbps": sum(req_bases) / span / 1e9,
+                     "batches": len({x["batch"] for x in info}),
+                     "mean_batch": float(np.mean([x["batch_size"] for x in info]))}
+
+    # warm-up: the scan variant of every (pair, k) compiles on first use
+    with ah.Server(ctx, sid, mem_budget=args.mem_budget, max_batch=1) as srv:
+        for j in range(len(pairs)):
+            for k in range(5):
+                srv.wait(srv.submit(np.arange(0, 2, dtype=np.uint32), pid[j], k, True))
+    serve(np.zeros(R), args.max_batch, args.mem_budget)
+    arr = np.cumsum(rng.exponential(1.0 / args.rate, size=R))
+    res_p, poisson = serve(arr, args.max_batch, args.mem_budget)
+    res_s, saturated = serve(np.zeros(R), args.max_batch, args.mem_budget)
+    for x, y in zip(res_p, res_s):   # the same results whatever they were batched with
+        assert x[0].tobytes() == y[0].tobytes() and x[1].tobytes() == y[1].tobytes() and x[2] == y[2]
+    # sequential plain solves: each request's genomes loaded as their own set, one ah_run
+    ctx_pids = {}
+    out = HostOut(torch, ah)
+    hs = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat = []
+    for (a, b, j, k), rr in zip(req, res_s):
+        t1 = time.perf_counter()
+        if (j, k) not in ctx_pids:
+            p = dict(pairs[j], k=k)
+            ctx_pids[(j, k)] = ctx.ah_set_primers(p["fwd"], p["rev"], p)
+        b0, b1, off, gen_ = sub_tables(coll, a, b)
+        s2 = ctx.ah_load_genomes(dev[b0:], b1 - b0, off, gen_, hs)
+        out.run(ctx, s2, [ctx_pids[(j, k)]], hs)
+        ctx.ah_unload_genomes(s2)
+        assert out.o.n_amplicons == len(rr[1]) and out.o.n_sites == len(rr[0])
+        lat.append((time.perf_counter() - t1) * 1e3)
+    t_seq = time.perf_counter() - t0
+    seq_plain = {"gbps": sum(req_bases) / t_seq / 1e9, "s": t_seq, "p50_ms": float(np.percentile(lat, 50)),
+                 "p99_ms": float(np.percentile(lat, 99)),
+                 "form": "each request alone: its genomes packed as their own set from device memory, one ah_run"}
+    ctx.ah_unload_genomes(sid)
+    line = {
+        "form": "served", "metric": "p50/p99 request latency; aggregate Gbp/s scanned per primer pair",
+        "value": saturated["gbps"], "unit": "Gbp/s", "n_gpus": 1, "higher_is_better": True,
+        "data": "synthetic (counter-based, seed 13)",
+        "config": {"workload": f"served-pool{n_g}genomes-{N / 1e9:.1f}Gbp-8pairs", "n_genomes": n_g, "n_bases": N,
+                   "requests": R, "rate_per_s": args.rate, "subset": "Zipf size over 1..n (P ~ 1/s), contiguous ids",
+                   "k": "uniform 0..4", "pairs": [(p["fwd"], p["rev"]) for p in pairs], "tm_filter": True,
+                   "max_batch": args.max_batch, "mem_budget": args.mem_budget, "layout_s": t_layout,
+                   "request_gbp_total": sum(req_bases) / 1e9},
+        "poisson": poisson, "saturated": saturated, "sequential_plain": seq_plain,
+        "saturated_over_sequential": saturated["gbps"] / seq_plain["gbps"],
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def large_pairs():
+    """The 960-oligo pair and two further pairs of 64 and 256 oligos (sum of the
+    two primers' degeneracies), k = 4, window 100-3000 bp, Tm threshold 50 C."""
+    from paper_2509_13300_gb300 import synth
+    rng = np.random.default_rng(7)
+    mk = lambda f, r: synth.pcr_params(f, r, k=4, min_len=100, max_len=3000, tm_min=50.0)
+    p960 = mk("AGRRTTYGATYHTDGYTYAG", "YCNTTCCYTYDYRGTACT")
+    p64 = mk(synth.random_primer(rng, 19, "RYSWK"), synth.random_primer(rng, 21, "WKMRY"))
+    p256 = mk(synth.random_primer(rng, 22, "RYSWKMR"), synth.random_primer(rng, 24, "KMRYSWK"))
+    return [p960, p64, p256]
+
+
+class DevOut:
+    """Device output buffers of one ah_run (grown on overflow)."""
+
+    def __init__(self, torch, ah, caps):
+        self.torch, self.ah = torch, ah
+        self.alloc(caps)
+
+    def alloc(self, caps):
+        t = self.torch
+        s, a, q = (max(int(x), 1) for x in caps)
+        self.b = None
+        t.cuda.empty_cache()
+        self.b = [t.empty(n, dtype=t.uint8, device="cuda") for n in (16 * s, 4 * s, s, 28 * a, q, 8 * (a + 1))]
+        self.o = self.ah.RunOut(self.b[0].data_ptr(), s, 0, self.b[1].data_ptr(), self.b[2].data_ptr(),
+                                self.b[3].data_ptr(), a, 0, self.b[4].data_ptr(), q, 0, self.b[5].data_ptr(), 1, 0)
+
+    def run(self, ctx, sid, pids, stream):
+        for _ in range(3):
+            try:
+                return ctx.ah_run(sid, pids, self.o, stream)
+            except self.ah.AHError as e:
+                if e.status != self.ah.AH_ERR_OVERFLOW:
+                    raise
+                o = self.o
+                self.alloc((o.n_sites * 5 // 4 + 1, o.n_amplicons * 5 // 4 + 1, o.n_seq * 5 // 4 + 1))
+        raise RuntimeError("ah_run kept overflowing")
+
+    def host(self, n, m):
+        """Sites, Tm, pass and amplicons of the last run, as numpy arrays."""
+        from paper_2509_13300_gb300 import ah
+        b = [x.cpu().numpy() for x in self.b[:4]]
+        return (b[0][:16 * n].view(ah.SITE_DTYPE), b[1][:4 * n].view(np.float32), b[2][:n],
+                b[3][:28 * m].view(ah.AMPLICON_DTYPE))
+
+
+def genome_slice(coll, chunk_tab, res, g):
+    """Results of genome g out of its chunk's run, re-indexed as the genome alone:
+    contigs from 0, amplicon ends indexing the genome's own site list."""
+    from paper_2509_13300_gb300 import ah
+    b0, b1, off, gen_ = chunk_tab
+    sites, tm, ps, amps = res
+    sel = np.nonzero(sites["genome"] == g)[0]
+    c0 = int(np.nonzero(gen_ == g)[0][0])
+    sg = sites[sel].copy()
+    sg["contig"] -= c0
+    remap = np.full(len(sites), -1, np.int64)
+    remap[sel] = np.arange(len(sel))
+    am = amps[amps["genome"] == g].copy()
+    am["contig"] -= c0
+    am["left"] = remap[am["left"]]
+    am["right"] = remap[am["right"]]
+    return sg, tm[sel].copy(), ps[sel].copy(), am
+
+
+def check_genome_against_oracle(coll, pairs, g, got, cores):
+    """The oracle on genome g alone (bases from the CPU twin); exact sites,
+    pass flags and amplicons, Tm within 0.01 C."""
+    import oracle
+    a, b = int(coll.genome_off[g]), int(coll.genome_off[g + 1])
+    seq = coll.bases(a, b)
+    c0 = int(np.searchsorted(coll.contig_off, a, side="left"))
+    c1 = int(np.searchsorted(coll.contig_off, b, side="left"))
+    off = (coll.contig_off[c0:c1 + 1] - np.uint64(a)).astype(np.uint64)
+    gen_ = np.full(c1 - c0, g, dtype=np.uint32)
+    s = oracle.scan(seq, off, gen_, pairs, n_threads=cores)
+    tm, ps = oracle.tm(seq, off, s, pairs, n_threads=cores)
+    am = oracle.pair(s, pairs, ps)
+    sg, tg, pg, ag = got
+    ok = ~np.isnan(tm)
+    return {"genome": int(g), "bases": b - a, "sites": len(s), "amplicons": len(am),
+            "sites_equal": sg.tobytes() == s.tobytes(), "pass_equal": bool(np.array_equal(pg, ps)),
+            "tm_nan_equal": bool(np.array_equal(np.isnan(tg), ~ok)),
+            "tm_max_err": float(np.abs(tg[ok].astype(np.float64) - tm[ok]).max()) if ok.any() else 0.0,
+            "amplicons_equal": ag.tobytes() == am.tobytes()}
+
+
+def bench_large(args):
+    """Large-scale form: a counter-generated collection (50,000 genomes of 1-8 Mbp,
+    seed 7) generated on the device chunk by chunk (whole genomes, up to 16 Gbp
+    per chunk) and streamed through the path with three pairs scanned in one
+    launch; a seeded sample of genomes is checked against the oracle."""
+    import torch
+    from paper_2509_13300_gb300 import ah, build, countergen
+    build.build()
+    torch.cuda.set_device(0)
+    n_g = args.n_genomes if args.n_genomes != 100 else 50_000
+    pairs = large_pairs()
+    t0 = time.perf_counter()
+    coll = countergen.collection(seed=7, n_genomes=n_g, len_lo=1e6, len_hi=8e6, pairs=pairs)
+    t_layout = time.perf_counter() - t0
+    ctx = ah.Context(0)
+    pids = [ctx.ah_set_primers(p["fwd"], p["rev"], p) for p in pairs]
+    N = coll.n_bases
+    tabs = [sub_tables(coll, g0, g1) for g0, g1 in genome_chunks(coll, args.large_chunk)]
+    cmax = max(b1 - b0 for b0, b1, _, _ in tabs)
+    abuf = [torch.empty(cmax + 3, dtype=torch.uint8, device="cuda") for _ in range(min(2, len(tabs)))]
+    st = [torch.cuda.Stream(), torch.cuda.Stream()]
+    out = DevOut(torch, ah, (cmax * 1.2e-3, 1 << 18, 1 << 28))
+    gen_ev = []
+
+    def gen_load(i):
+        b0, b1, off, gen_ = tabs[i]
+        s = st[i % 2]
+        e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        a0 = b0 - b0 % 4  # generated ranges start on a multiple of 4
+        e[0].record(s)
+        ctx.generate_bases(coll, a0, b1 - a0, abuf[i % 2], stream=s)
+        e[1].record(s)
+        gen_ev.append(e)
+        return ctx.ah_load_genomes(abuf[i % 2][b0 - a0:], b1 - b0, off, gen_, s)
+
+    totals = {}
+
+    def one_pass(keep=None):
+        n_s = n_a = n_q = 0
+        kept = {}
+        sid = gen_load(0)
+        for i in range(len(tabs)):
+            nxt = gen_load(i + 1) if i + 1 < len(tabs) else None   # packs beside run i
+            out.run(ctx, sid, pids, st[i % 2])
+            o = out.o
+            n_s, n_a, n_q = n_s + o.n_sites, n_a + o.n_amplicons, n_q + o.n_seq
+            if keep is not None and keep.get(i):
+                res = out.host(o.n_sites, o.n_amplicons)
+                for g in keep[i]:
+                    kept[g] = genome_slice(coll, tabs[i], res, g)
+            ctx.ah_unload_genomes(sid)
+            sid = nxt
+        totals.update(sites=n_s, amplicons=n_a, seq_bytes=n_q)
+        return kept
+
+    sid0 = gen_load(0)
+    tune = None if args.no_tune else ctx.ah_tune_scan(sid0, pids, 0, st[0])
+    ctx.ah_unload_genomes(sid0)
+    torch.cuda.synchronize()
+    one_pass()                    # warm-up: sizes the outputs
+    torch.cuda.synchronize()
+    gen_ev.clear()
+    ctx.ah_set_profiling(0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        clk.wait_first()
+        clk.mark(True)
+        e0.record(st[0])
+        one_pass()
+        st[0].wait_stream(st[1])
+        e1.record(st[0])
+        torch.cuda.synchronize()
+        clk.mark(False)
+    _, launches, _ = ctx.ah_get_profile(None)
+    t_all = e0.elapsed_time(e1) / 1e3
+    t_gen = sum(a.elapsed_time(b) for a, b in gen_ev) / 1e3
+    # stage split: one more pass with events around every stage (untimed)
+    ctx.ah_set_profiling(1)
+    one_pass()
+    stages = {}
+    for name in ("pack", "scan", "sort", "decode", "tm", "pair", "fetch"):
+        ms, l, calls = ctx.ah_get_profile(name)
+        stages[name] = {"ms": ms, "launches": l}
+    ctx.ah_set_profiling(0)
+    scan_s = stages["scan"]["ms"] / 1e3
+    hbm_peak, peak_kind, _ = load_peaks()
+    # the oracle on a seeded sample of genomes
+    rng = np.random.default_rng(7)
+    sample = np.sort(rng.choice(n_g, size=min(n_g, max(args.check_genomes, args.dump_genomes)), replace=False))
+    chunk_of = np.searchsorted(np.array([b1 for _, b1, _, _ in tabs]), coll.genome_off[sample], side="right")
+    keep = {}
+    for g, ci in zip(sample.tolist(), chunk_of.tolist()):
+        keep.setdefault(ci, []).append(g)
+    kept = one_pass(keep)
+    checks = []
+    cores = os.cpu_count() or 1
+    for g in sample[:args.check_genomes].tolist():
+        checks.append(check_genome_against_oracle(coll, pairs, g, kept[g], cores))
+    if args.dump_genomes:
+        os.makedirs(os.path.dirname(os.path.abspath(args.dump_path)), exist_ok=True)
+        arrs = {}
+        for g in sample.tolist():
+            sg, tg, pg, ag = kept[g]
+            arrs.update({f"s{g}": sg, f"t{g}": tg, f"p{g}": pg, f"a{g}": ag})
+        np.savez_compressed(args.dump_path, sample=sample, n_genomes=n_g, **arrs)
+    all_ok = all(c["sites_equal"] and c["pass_equal"] and c["tm_nan_equal"] and c["amplicons_equal"]
+                 and c["tm_max_err"] <= 0.01 for c in checks)
+    line = {
+        "form": "large", "metric": "Gbp/s scanned per primer pair (both strands, k mm)",
+        "value": N / t_all / 1e9, "unit": "Gbp/s", "n_gpus": 1, "higher_is_better": True,
+        "data": "synthetic (counter-based Philox4x32-10, seed 7, generated on the device)",
+        "config": {"workload": f"large-{n_g}genomes-{N / 1e9:.1f}Gbp-3pairs-k4", "n_genomes": n_g, "n_bases": N,
+                   "n_contigs": len(coll.contig_genome), "chunks": len(tabs), "chunk_bases_max": cmax,
+                   "pairs": [(p["fwd"], p["rev"]) for p in pairs], "k": 4, "window": [100, 3000],
+                   "tm_min_C": 50.0, "scan_tuning": tune, "layout_s": t_layout,
+                   "timed": "one pass: generation + pack + scan + sort + Tm + pair + fetch, outputs on the device"},
+        "seconds": t_all, "generation_s": t_gen, "path_gbps_excluding_generation": N / (t_all - t_gen) / 1e9,
+        "amplicons_per_s": totals["amplicons"] / t_all, "results": dict(totals),
+        "stages_ms": stages, "scan": {"hbm_gbs": 0.5 * N / scan_s / 1e9, "hbm_peak_gbs": hbm_peak,
+                                      "hbm_frac": 0.5 * N / scan_s / 1e9 / hbm_peak, "peak_kind": peak_kind,
+                                      "pattern_gbps": N * len(pairs) / scan_s / 1e9},
+        "gpu_launches": launches, "clocks": clk.summary(),
+        "oracle_check": {"genomes": len(checks), "all_equal": all_ok, "cores": cores,
+                         "bases": int(sum(c["bases"] for c in checks)),
+                         "sites": int(sum(c["sites"] for c in checks)),
+                         "amplicons": int(sum(c["amplicons"] for c in checks)),
+                         "tm_max_err": max([c["tm_max_err"] for c in checks] or [0.0]),
+                         "dumped": int(args.dump_genomes)},
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def check_large_dump(path: str):
+    """The oracle, on this machine, against the GPU results a large-form run
+    dumped for its sampled genomes (the genomes are regenerated by the CPU twin)."""
+    from paper_2509_13300_gb300 import countergen
+    d = np.load(path)
+    n_g = int(d["n_genomes"])
+    pairs = large_pairs()
+    coll = countergen.collection(seed=7, n_genomes=n_g, len_lo=1e6, len_hi=8e6, pairs=pairs)
+    cores = os.cpu_count() or 1
+    res = []
+    t0 = time.perf_counter()
+    for g in d["sample"].tolist():
+        got = (d[f"s{g}"], d[f"t{g}"], d[f"p{g}"], d[f"a{g}"])
+        r = check_genome_against_oracle(coll, pairs, g, got, cores)
+        res.append(r)
+        print(json.dumps(r), flush=True)
+    ok = all(r["sites_equal"] and r["pass_equal"] and r["tm_nan_equal"] and r["amplicons_equal"]
+             and r["tm_max_err"] <= 0.01 for r in res)
+    print(json.dumps({"genomes": len(res), "all_equal": ok, "bases": sum(r["bases"] for r in res),
+                      "sites": sum(r["sites"] for r in res), "amplicons": sum(r["amplicons"] for r in res),
+                      "tm_max_err": max(r["tm_max_err"] for r in res), "cores": cores,
+                      "seconds": time.perf_counter() - t0}), flush=True)
+    return 0 if ok else 1
 
 if __name__ == "__main__":
     main()

@@ -483,10 +483,12 @@ ah_status ah_pair_noalloc(const int32_t *pair_windows, uint32_t n_pairs, const a
  * Until ah_serve_stop no other call may use the context.
  * ah_serve_submit (any thread) queues a copy of the request and returns a
  * ticket.  ah_serve_wait (any thread) blocks until the ticket's request is
- * done, fills *info and copies its sites and amplicons to the host arrays:
- * if either capacity is too small it returns AH_ERR_OVERFLOW with the counts
- * in *info and keeps the result for another wait; otherwise (or on an
- * error status) the ticket is released.  Times are milliseconds since
+ * done, fills *info and copies its sites, amplicons and (when
+ * seq_offsets_out is not NULL) the amplicon sequences, as ah_fetch gives
+ * them, to the host arrays: seq_offsets_out takes n_amplicons + 1 offsets
+ * into seq_out.  If a capacity is too small it returns AH_ERR_OVERFLOW with
+ * the counts in *info and keeps the result for another wait; otherwise (or
+ * on an error status) the ticket is released.  Times are milliseconds since
  * ah_serve_start on a steady clock: submit, start of the batch that ran the
  * request, and completion.  ah_serve_stop finishes the queued requests, joins
  * the worker and frees the server (unreleased results are dropped).
@@ -510,13 +512,14 @@ typedef struct {
     uint32_t batch;       /* 1-based number of the batch that ran the request */
     uint32_t batch_size;  /* requests in that batch */
     uint32_t reserved;
-    uint64_t n_sites, n_amplicons, bases;
+    uint64_t n_sites, n_amplicons, n_seq, bases; /* n_seq: sequence bytes */
     double submit_ms, start_ms, done_ms;
 } ah_request_info;
 ah_status ah_serve_start(ah_ctx *ctx, uint32_t set_id, const ah_serve_config *cfg, ah_server **out);
 ah_status ah_serve_submit(ah_server *srv, const ah_request *req, uint64_t *ticket_out);
 ah_status ah_serve_wait(ah_server *srv, uint64_t ticket, ah_request_info *info, ah_site *sites_out, uint64_t sites_cap,
-                        ah_amplicon *amps_out, uint64_t amps_cap);
+                        ah_amplicon *amps_out, uint64_t amps_cap, char *seq_out, uint64_t seq_cap,
+                        uint64_t *seq_offsets_out);
 ah_status ah_serve_stop(ah_server *srv);
 
 #ifdef __cplusplus

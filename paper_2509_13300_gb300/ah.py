@@ -82,7 +82,7 @@ class Request(ctypes.Structure):
 class RequestInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("batch", ctypes.c_uint32), ("batch_size", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("n_sites", ctypes.c_uint64), ("n_amplicons", ctypes.c_uint64),
-                ("bases", ctypes.c_uint64), ("submit_ms", ctypes.c_double), ("start_ms", ctypes.c_double),
+                ("n_seq", ctypes.c_uint64), ("bases", ctypes.c_uint64), ("submit_ms", ctypes.c_double), ("start_ms", ctypes.c_double),
                 ("done_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
@@ -137,7 +137,7 @@ def lib():
             "ah_run_end": (I32, [P]),
             "ah_serve_start": (I32, [P, U32, ctypes.POINTER(ServeConfig), ctypes.POINTER(P)]),
             "ah_serve_submit": (I32, [P, ctypes.POINTER(Request), ctypes.POINTER(U64)]),
-            "ah_serve_wait": (I32, [P, U64, ctypes.POINTER(RequestInfo), P, U64, P, U64]),
+            "ah_serve_wait": (I32, [P, U64, ctypes.POINTER(RequestInfo), P, U64, P, U64, P, U64, P]),
             "ah_serve_stop": (I32, [P]),
             "ah_tune_scan": (I32, [P, U32, P, U32, U64, ctypes.POINTER(TuneResult), P]),
             "ah_pair_noalloc": (I32, [P, U32, P, P, U64, P, U64, ctypes.POINTER(U64), P]),
@@ -318,7 +318,10 @@ class Context:
 
     def generate_bases(self, coll, base0: int, n: int, out, stream=None):
         """Bases [base0, base0 + n) of a countergen collection into device memory `out` (torch uint8)."""
-        segs = np.ascontiguousarray(coll.segments)
+        ends = coll.segments["end"]
+        s0 = int(np.searchsorted(ends, base0, side="right"))  # the segments that hold the range
+        s1 = min(len(ends), int(np.searchsorted(ends, base0 + max(n, 1) - 1, side="right")) + 1)
+        segs = np.ascontiguousarray(coll.segments[s0:s1])
         pp = np.ascontiguousarray(coll.patch_pos, dtype=np.uint64)
         pb = np.ascontiguousarray(coll.patch_bytes, dtype=np.uint8)
         lo, hi = np.searchsorted(pp, base0), np.searchsorted(pp, base0 + n)  # the patches in range
@@ -452,21 +455,27 @@ class Server:
             raise AHError(st, "ah_serve_submit rejected the request")
         return t.value
 
-    def wait(self, ticket: int):
-        """(sites, amplicons, info dict) of a submitted request."""
+    def wait(self, ticket: int, sequences: bool = True):
+        """(sites, amplicons, sequences, offsets, info dict) of a submitted request
+        (sequences and offsets are None when not asked for)."""
         info = RequestInfo()
-        st = self._lib.ah_serve_wait(self.h, ticket, ctypes.byref(info), None, 0, None, 0)
+        z = np.zeros(1, np.uint64)
+        st = self._lib.ah_serve_wait(self.h, ticket, ctypes.byref(info), None, 0, None, 0, None, 0,
+                                     _ptr(z) if sequences else None)
         if st == AH_OK:
-            return np.zeros(0, SITE_DTYPE), np.zeros(0, AMPLICON_DTYPE), info.as_dict()
+            return (np.zeros(0, SITE_DTYPE), np.zeros(0, AMPLICON_DTYPE), b"" if sequences else None,
+                    z if sequences else None, info.as_dict())
         if st != AH_ERR_OVERFLOW:
             raise AHError(st, f"request {ticket} failed ({STATUS_NAMES.get(info.status, info.status)})")
         sites = np.zeros(info.n_sites, SITE_DTYPE)
         amps = np.zeros(info.n_amplicons, AMPLICON_DTYPE)
+        seq = np.zeros(max(info.n_seq, 1), np.uint8) if sequences else None
+        offs = np.zeros(info.n_amplicons + 1, np.uint64) if sequences else None
         st = self._lib.ah_serve_wait(self.h, ticket, ctypes.byref(info), _ptr(sites), len(sites), _ptr(amps),
-                                     len(amps))
+                                     len(amps), _ptr(seq), info.n_seq, _ptr(offs))
         if st != AH_OK:
             raise AHError(st, f"request {ticket}: results could not be read")
-        return sites, amps, info.as_dict()
+        return sites, amps, (seq[:info.n_seq].tobytes() if sequences else None), offs, info.as_dict()
 
     def stop(self):
         if getattr(self, "h", None):

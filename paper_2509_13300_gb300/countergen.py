@@ -123,70 +123,121 @@ class CounterCollection:
                               planted=np.zeros(0, dtype=synth.PLANT_DTYPE))
 
 
+def _draw_oligos(rng, primer: str, n_subs: np.ndarray) -> np.ndarray:
+    """len(n_subs) oligos of `primer` (uint8 rows): each position drawn from its
+    IUPAC set, then n_subs[i] distinct non-N positions replaced by a base outside
+    their set."""
+    n, L = len(n_subs), len(primer)
+    sets = [synth._IUPAC_BASES[ch] for ch in primer]
+    out = np.empty((n, L), dtype=np.uint8)
+    for j, st in enumerate(sets):
+        alpha = np.frombuffer("".join(sorted(st)).encode(), dtype=np.uint8)
+        out[:, j] = alpha[rng.integers(len(alpha), size=n)]
+    cand = np.array([j for j, ch in enumerate(primer) if ch != "N"], dtype=np.int64)
+    if len(cand) and n:
+        order = np.argsort(rng.random((n, len(cand))), axis=1)  # a random permutation per row
+        k = np.minimum(n_subs, len(cand))
+        for r in range(int(k.max()) if len(k) else 0):
+            rows = np.nonzero(k > r)[0]
+            cols = cand[order[rows, r]]
+            for j in np.unique(cols):
+                outside = np.frombuffer("".join(b for b in "ACGT" if b not in sets[j]).encode(), dtype=np.uint8)
+                sel = rows[cols == j]
+                out[sel, j] = outside[rng.integers(len(outside), size=len(sel))]
+    return out
+
+
+_COMP = np.zeros(256, dtype=np.uint8)
+for _a, _b in zip(b"ACGT", b"TGCA"):
+    _COMP[_a] = _b
+
+
 def collection(seed: int = 7, n_genomes: int = 50_000, len_lo: float = 1e6, len_hi: float = 8e6, pairs=None,
                k: int = 4, min_len: int = 100, max_len: int = 3000, plants=(1, 15)) -> CounterCollection:
     """Layout of a counter-generated collection (the large workload: 50,000 genomes of
-    1-8 Mbp, seed 7).  pairs: list of pcr_params dicts (default: one pair of 960 oligos)."""
+    1-8 Mbp, seed 7).  pairs: list of pcr_params dicts (default: one pair of 960 oligos).
+    Every draw is vectorised over genomes, so 50,000 genomes lay out in seconds."""
     rng = np.random.default_rng(seed)  # primer and patch content only
     if pairs is None:
         pairs = [synth.pcr_params("AGRRTTYGATYHTDGYTYAG", "YCNTTCCYTYDYRGTACT", k=k, min_len=min_len,
                                   max_len=max_len)]
-    g = np.arange(n_genomes, dtype=np.uint64)
+    G = n_genomes
+    g = np.arange(G, dtype=np.uint64)
     u = _uniform(seed, 1, g)
     lengths = np.round(len_lo * (len_hi / len_lo) ** u[:, 0]).astype(np.int64)
     gcs = 0.3 + 0.4 * u[:, 1]
     n_contigs = np.minimum(200, 1 + np.floor(np.log1p(-u[:, 2]) / np.log(0.95))).astype(np.int64)
-    contig_off, contig_genome, genome_off = [0], [], [0]
-    seg_end, seg_t, seg_letter = [], [], []
-    patch_pos, patch_bytes = [], []
-    base = 0
-    for i in range(n_genomes):
-        L = int(lengths[i])
-        cuts = np.sort((_uniform(seed, 2, np.arange(max(1, n_contigs[i] - 1)) + (i << 8))[:, 0] * L)
-                       .astype(np.int64))[: n_contigs[i] - 1]
-        bounds = np.concatenate([[0], cuts, [L]])
-        for c in range(len(bounds) - 1):
-            contig_off.append(base + int(bounds[c + 1]))
-            contig_genome.append(i)
-        # N runs: about 0.1 % of the bases, runs of 1..100
-        n_runs = max(0, int(round(L * 0.001 / 50.5)))
-        ur = _uniform(seed, 3, np.arange(max(n_runs, 1)) + (i << 20))[:n_runs]
-        runs = sorted((int(x[0] * L), 1 + int(x[1] * 100)) for x in ur)
-        t = gc_thresholds(float(gcs[i]))
-        pos = 0
-        for s, ln in runs:
-            s = max(s, pos)
-            e = min(L, s + ln)
-            if s >= e:
-                continue
-            if s > pos:
-                seg_end.append(base + s); seg_t.append(t); seg_letter.append(0)
-            seg_end.append(base + e); seg_t.append((0, 0, 0)); seg_letter.append(ord("N"))
-            pos = e
-        seg_end.append(base + L); seg_t.append(t); seg_letter.append(0)
-        # planted operon-like regions: forward oligo ... reverse-complemented reverse oligo
-        for _ in range(int(rng.integers(plants[0], plants[1] + 1)) if L > 4000 else 0):
-            pair = pairs[int(rng.integers(len(pairs)))]
-            span = int(rng.integers(max(pair["min_len"], 300), min(pair["max_len"], 1500) + 1))
-            s = int(rng.integers(0, L - span))
-            kk = pair["k"]
-            f = synth._draw_oligo(rng, pair["fwd"], int(rng.integers(0, kk + 1)))
-            r = synth._revcomp(synth._draw_oligo(rng, pair["rev"], int(rng.integers(0, kk + 1))))
-            for off, text in ((s, f), (s + span - len(r), r)):
-                patch_pos.extend(range(base + off, base + off + len(text)))
-                patch_bytes.extend(text.encode())
-        genome_off.append(base + L)
-        base += L
+    base = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    # contigs: n_c - 1 sorted cuts per genome (counter (genome << 8) + j)
+    nc1 = n_contigs - 1
+    owner = np.repeat(np.arange(G), nc1)
+    j = np.arange(len(owner)) - np.repeat(np.cumsum(nc1) - nc1, nc1)
+    cu = _uniform(seed, 2, (owner.astype(np.uint64) << np.uint64(8)) + j.astype(np.uint64))[:, 0]
+    cuts = (cu * lengths[owner]).astype(np.int64)
+    o = np.lexsort((cuts, owner))
+    cuts, owner_s = cuts[o], owner[o]
+    # contig starts: genome start, then the genome's cuts
+    starts = np.concatenate([base[:-1], base[owner_s] + cuts])
+    sg = np.concatenate([np.arange(G), owner_s])
+    o = np.lexsort((starts, sg))
+    contig_off = np.append(starts[o], base[-1]).astype(np.uint64)
+    contig_genome = sg[o].astype(np.uint32)
+    # N runs, about 0.1 % of the bases: runs of 1..100 at sorted starts, each cut
+    # short at the next run's start (counter (genome << 20) + j)
+    n_runs = np.round(lengths * 0.001 / 50.5).astype(np.int64)
+    rown = np.repeat(np.arange(G), n_runs)
+    j = np.arange(len(rown)) - np.repeat(np.cumsum(n_runs) - n_runs, n_runs)
+    ur = _uniform(seed, 3, (rown.astype(np.uint64) << np.uint64(20)) + j.astype(np.uint64))
+    rs = (ur[:, 0] * lengths[rown]).astype(np.int64)
+    rl = 1 + (ur[:, 1] * 100).astype(np.int64)
+    o = np.lexsort((rs, rown))
+    rs, rl, rown = rs[o], rl[o], rown[o]
+    nxt = np.append(rs[1:], 0)
+    last = np.append(rown[1:] != rown[:-1], True)
+    re = np.minimum(rs + rl, np.where(last, lengths[rown], nxt))
+    keep = re > rs
+    rs, re, rown = rs[keep], re[keep], rown[keep]
+    # segments: per genome, base stretches between the N runs, the N runs, the tail
+    at, cg = ((1.0 - gcs) / 2.0 * 4294967296.0).astype(np.int64), (gcs / 2.0 * 4294967296.0).astype(np.int64)
+    thr = np.stack([at, at + cg, at + 2 * cg], axis=1)
+    prev_end = np.where(np.append(True, rown[1:] != rown[:-1]), 0, np.append(0, re[:-1]))
+    gap = rs > prev_end
+    seg_end = np.concatenate([base[rown[gap]] + rs[gap], base[rown] + re, base[1:]])
+    seg_g = np.concatenate([rown[gap], rown, np.arange(G)])
+    seg_n = np.concatenate([np.zeros(gap.sum(), bool), np.ones(len(rown), bool), np.zeros(G, bool)])
+    o = np.argsort(seg_end, kind="stable")
     seg = np.zeros(len(seg_end), dtype=SEGMENT_DTYPE)
-    seg["end"] = seg_end
-    seg["t_a"], seg["t_c"], seg["t_g"] = (np.array([t[j] for t in seg_t], dtype=np.uint64) for j in range(3))
-    seg["letter"] = seg_letter
-    pp = np.array(patch_pos, dtype=np.uint64)
-    pb = np.frombuffer(bytes(patch_bytes), dtype=np.uint8).copy()
-    if len(pp):  # later patches win where two overlap; keep one write per position
+    seg["end"] = seg_end[o]
+    for f, col in zip(("t_a", "t_c", "t_g"), range(3)):
+        seg[f] = np.where(seg_n[o], 0, thr[seg_g[o], col])
+    seg["letter"] = np.where(seg_n[o], ord("N"), 0)
+    # planted operon-like regions: forward oligo ... reverse-complemented reverse oligo
+    npl = np.where(lengths > 4000, rng.integers(plants[0], plants[1] + 1, size=G), 0)
+    pg = np.repeat(np.arange(G), npl)
+    P = len(pg)
+    which = rng.integers(len(pairs), size=P)
+    lo = np.array([max(p["min_len"], 300) for p in pairs])[which]
+    hi = np.array([min(p["max_len"], 1500) for p in pairs])[which]
+    span = lo + (rng.random(P) * (hi - lo + 1)).astype(np.int64)
+    ps = (rng.random(P) * (lengths[pg] - span)).astype(np.int64)
+    kk = np.array([p["k"] for p in pairs])[which]
+    pos_l, byt_l = [], []
+    for i, p in enumerate(pairs):
+        sel = np.nonzero(which == i)[0]
+        if not len(sel):
+            continue
+        f = _draw_oligos(rng, p["fwd"], (rng.random(len(sel)) * (kk[sel] + 1)).astype(np.int64))
+        r = _draw_oligos(rng, p["rev"], (rng.random(len(sel)) * (kk[sel] + 1)).astype(np.int64))
+        r = _COMP[r[:, ::-1]]  # reverse complement
+        s0 = base[pg[sel]] + ps[sel]
+        s1 = s0 + span[sel] - r.shape[1]
+        pos_l += [(s0[:, None] + np.arange(f.shape[1])).ravel(), (s1[:, None] + np.arange(r.shape[1])).ravel()]
+        byt_l += [f.ravel(), r.ravel()]
+    pp = np.concatenate(pos_l).astype(np.uint64) if pos_l else np.zeros(0, np.uint64)
+    pb = np.concatenate(byt_l).astype(np.uint8) if byt_l else np.zeros(0, np.uint8)
+    if len(pp):  # where two plants overlap, the later one wins; one write per position
         order = np.argsort(pp, kind="stable")
         pp, pb = pp[order], pb[order]
         keep = np.append(pp[1:] != pp[:-1], True)
         pp, pb = pp[keep], pb[keep]
-    return CounterCollection(seed, np.array(contig_off, dtype=np.uint64), np.array(contig_genome, dtype=np.uint32),
-                             np.array(genome_off, dtype=np.uint64), seg, pp, pb, pairs)
+    return CounterCollection(seed, contig_off, contig_genome, base.astype(np.uint64), seg, pp, pb, pairs)

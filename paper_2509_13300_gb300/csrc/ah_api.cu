@@ -9,6 +9,7 @@
 #include <cstring>
 #include <condition_variable>
 #include <deque>
+#include <future>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -600,7 +601,9 @@ void launch_scan(ah_ctx *c, ScanKernel *k, const GenomeSet &gs, uint64_t n_tiles
     uint32_t nc = gs.n_contigs;
     uint64_t *work = c->d_flags + kFlagWork;
     AH_CUDA(cudaMemsetAsync(work, 0, sizeof(uint64_t), st));
-    void *args[] = {&planes, &n_tiles, &coff, &nc, &keys, &cap, &c->d_counter, &pbits, &c->d_err, &work, &tile_list};
+    const uint32_t *tcont = gs.tile_contig;
+    void *args[] = {&planes,       &n_tiles, &coff, &nc,   &keys,      &cap,  &c->d_counter,
+                    &pbits,        &c->d_err, &work, &tile_list, &tcont};
     AH_CUDA(cudaLaunchKernel((const void *)k->fn, dim3((unsigned)grid), dim3(k->threads), args, k->smem, st));
 }
 
@@ -958,6 +961,8 @@ struct ServeReq {
     uint64_t n_sites = 0, bases = 0;
     std::vector<ah_site> sites;
     std::vector<ah_amplicon> amps;
+    std::vector<char> seq;          // amplicon sequences, concatenated
+    std::vector<uint64_t> seq_off;  // n_amplicons + 1 offsets into seq
 };
 
 } // namespace
@@ -988,6 +993,151 @@ namespace {
 size_t serve_request_bytes(const ServeReq &r) { return 4096 + (size_t)(r.bases / 1000) * 64; }
 
 // One batch: fills every request's result fields.
+// Device results of one primer pair's group of requests.
+struct GroupData {
+    std::vector<ah_site> sites;
+    std::vector<uint8_t> pass;
+    std::vector<ah_amplicon> amps;
+};
+
+// Scan of the union of the group's genomes at the largest k among them, then
+// sort, Tm and amplicon calling without a Tm filter; results to the host.
+void group_device(ah_ctx *c, const GenomeSet &gs, uint32_t pid, const std::vector<ServeReq *> &rs, GroupData &d)
+{
+    cudaStream_t st = c->stream;
+    int kmax = 0;
+    std::vector<char> in_union(gs.max_genome + 1, 0);
+    for (ServeReq *r : rs) {
+        kmax = std::max(kmax, r->k);
+        for (uint32_t g : r->genomes)
+            if (g <= gs.max_genome)
+                in_union[g] = 1;
+    }
+    // tiles holding a start of a union genome's contig
+    std::vector<char> tflag(gs.n_tiles, 0);
+    for (uint32_t ci = 0; ci < gs.n_contigs; ++ci) {
+        const uint64_t a = gs.contig_off_h[ci], b = gs.contig_off_h[ci + 1];
+        if (b > a && in_union[gs.contig_genome_h[ci]])
+            for (uint64_t t = a / kTileBases; t <= (b - 1) / kTileBases; ++t)
+                tflag[t] = 1;
+    }
+    std::vector<uint64_t> tiles;
+    for (uint64_t t = 0; t < gs.n_tiles; ++t)
+        if (tflag[t])
+            tiles.push_back(t);
+    if (tiles.empty())
+        return;
+    uint64_t *tl = (uint64_t *)scratch(c, "serve_tiles", tiles.size() * sizeof(uint64_t));
+    AH_CUDA(cudaMemcpyAsync(tl, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    std::vector<ScanPattern> pats = patterns_of(c, &pid, 1, kmax);
+    const PairDev *pd = upload_pairs(c, &pid, 1, st);
+    uint64_t *keys = nullptr;
+    const uint64_t ns = scan_keys(c, gs, pats, &keys, st, tl, tiles.size());
+    if (!ns)
+        return;
+    ah_site *sites = (ah_site *)scratch(c, "serve_sites", ns * sizeof(ah_site));
+    sort_decode(c, gs, 1, keys, ns, sites, st);
+    float *tm = (float *)scratch(c, "serve_tm", ns * sizeof(float));
+    uint8_t *pass = (uint8_t *)scratch(c, "serve_pass", ns);
+    uint32_t *q = (uint32_t *)scratch(c, "tm_queue", ns * sizeof(uint32_t));
+    {
+        Stage sg(c, "tm", st, 2);
+        launch_tm(sites, ns, nullptr, pd, 1, gs.planes, gs.contig_off, tm, pass, q,
+                  (uint32_t *)(c->d_flags + kFlagTmQueue), tm_seg_max(c), tm_few_exact(c), c->d_err, st);
+    }
+    uint64_t *counts = (uint64_t *)scratch(c, "pair_counts", ns * sizeof(uint64_t));
+    uint64_t *offs = (uint64_t *)scratch(c, "pair_offsets", ns * sizeof(uint64_t));
+    size_t tb = scan_u64_temp_bytes(ns);
+    void *temp = scratch(c, "scan_temp", tb);
+    {
+        Stage sg(c, "pair", st, 2 + scan_u64_launches(ns));
+        launch_pair_count(sites, ns, nullptr, nullptr, pd, counts, st);
+        exclusive_scan_u64(temp, tb, counts, offs, ns, st);
+        launch_total(offs, counts, ns, nullptr, 0, c->d_aux, 0, nullptr, nullptr, 0, st);
+    }
+    d.sites.resize(ns);
+    d.pass.resize(ns);
+    AH_CUDA(cudaMemcpyAsync(d.sites.data(), sites, ns * sizeof(ah_site), cudaMemcpyDeviceToHost, st));
+    AH_CUDA(cudaMemcpyAsync(d.pass.data(), pass, ns, cudaMemcpyDeviceToHost, st));
+    check_flags(c, st);
+    const uint64_t na = c->h_flags[kFlagAux];
+    if (na) {
+        ah_amplicon *amps = (ah_amplicon *)scratch(c, "serve_amps", na * sizeof(ah_amplicon));
+        {
+            Stage sg(c, "pair", st, 1);
+            launch_pair_write(sites, ns, nullptr, nullptr, pd, offs, amps, na, nullptr, 0, st);
+        }
+        d.amps.resize(na);
+        AH_CUDA(cudaMemcpyAsync(d.amps.data(), amps, na * sizeof(ah_amplicon), cudaMemcpyDeviceToHost, st));
+        check_flags(c, st);
+    }
+}
+
+// Per request: its genomes, its k, its Tm filter.  Sites and amplicons are
+// bucketed by genome once; a request visits only its genomes' buckets.
+// Host work only (runs beside the next group's device work).
+void group_filter(uint64_t G, const GroupData &d, const std::vector<ServeReq *> &rs)
+{
+    std::vector<uint64_t> s_off(G + 1, 0), a_off(G + 1, 0);
+    for (const ah_site &x : d.sites)
+        ++s_off[x.genome + 1];
+    for (const ah_amplicon &x : d.amps)
+        ++a_off[x.genome + 1];
+    for (uint64_t g = 0; g < G; ++g) {
+        s_off[g + 1] += s_off[g];
+        a_off[g + 1] += a_off[g];
+    }
+    std::vector<uint64_t> s_idx(d.sites.size()), a_idx(d.amps.size());
+    {
+        std::vector<uint64_t> fs(s_off.begin(), s_off.end() - 1), fa(a_off.begin(), a_off.end() - 1);
+        for (uint64_t i = 0; i < d.sites.size(); ++i)
+            s_idx[fs[d.sites[i].genome]++] = i;
+        for (uint64_t i = 0; i < d.amps.size(); ++i)
+            a_idx[fa[d.amps[i].genome]++] = i;
+    }
+    std::vector<int64_t> new_index(d.sites.size(), -1);
+    for (ServeReq *r : rs) {
+        std::vector<uint64_t> mine;
+        for (uint32_t g : r->genomes)
+            if (g < G)
+                for (uint64_t q = s_off[g]; q < s_off[g + 1]; ++q)
+                    if (d.sites[s_idx[q]].mm <= r->k)
+                        mine.push_back(s_idx[q]);
+        std::sort(mine.begin(), mine.end()); // canonical order is the group's order
+        r->sites.resize(mine.size());
+        for (size_t j = 0; j < mine.size(); ++j) {
+            new_index[mine[j]] = (int64_t)j;
+            r->sites[j] = d.sites[mine[j]];
+        }
+        r->n_sites = mine.size();
+        std::vector<uint64_t> ka;
+        for (uint32_t g : r->genomes)
+            if (g < G)
+                for (uint64_t q = a_off[g]; q < a_off[g + 1]; ++q) {
+                    const ah_amplicon &x = d.amps[a_idx[q]];
+                    if (new_index[x.left] < 0 || new_index[x.right] < 0)
+                        continue;
+                    if (r->tm_filter && !(d.pass[x.left] && d.pass[x.right]))
+                        continue;
+                    ka.push_back(a_idx[q]);
+                }
+        std::sort(ka.begin(), ka.end());
+        r->amps.resize(ka.size());
+        for (size_t j = 0; j < ka.size(); ++j) {
+            ah_amplicon b = d.amps[ka[j]];
+            b.left = (uint32_t)new_index[b.left]; // indices into the request's own site list
+            b.right = (uint32_t)new_index[b.right];
+            r->amps[j] = b;
+        }
+        for (uint64_t i : mine)
+            new_index[i] = -1;
+    }
+}
+
+// One batch: fills every request's result fields.  Pair groups run one after
+// another on the device; each group's host filtering overlaps the next
+// group's device work; one fetch at the end decodes every distinct amplicon
+// some request keeps.
 void serve_batch(ah_server *S, std::vector<ServeReq *> &batch)
 {
     ah_ctx *c = S->c;
@@ -996,107 +1146,76 @@ void serve_batch(ah_server *S, std::vector<ServeReq *> &batch)
     std::map<uint32_t, std::vector<ServeReq *>> groups;
     for (ServeReq *r : batch)
         groups[r->pair_id].push_back(r);
-    for (auto &kv : groups) {
-        const uint32_t pid = kv.first;
-        std::vector<ServeReq *> &rs = kv.second;
-        int kmax = 0;
-        std::vector<char> in_union(gs.max_genome + 1, 0);
-        for (ServeReq *r : rs) {
-            kmax = std::max(kmax, r->k);
-            for (uint32_t g : r->genomes)
-                if (g <= gs.max_genome)
-                    in_union[g] = 1;
+    const uint64_t G = (uint64_t)gs.max_genome + 1;
+    std::deque<GroupData> data;
+    std::vector<std::future<void>> filters;
+    try {
+        for (auto &kv : groups) {
+            data.emplace_back();
+            group_device(c, gs, kv.first, kv.second, data.back());
+            const GroupData *d = &data.back();
+            const std::vector<ServeReq *> *rs = &kv.second;
+            filters.push_back(std::async(std::launch::async, [G, d, rs] { group_filter(G, *d, *rs); }));
         }
-        // tiles holding a start of a union genome's contig
-        std::vector<char> tflag(gs.n_tiles, 0);
-        for (uint32_t ci = 0; ci < gs.n_contigs; ++ci) {
-            const uint64_t a = gs.contig_off_h[ci], b = gs.contig_off_h[ci + 1];
-            if (b > a && in_union[gs.contig_genome_h[ci]])
-                for (uint64_t t = a / kTileBases; t <= (b - 1) / kTileBases; ++t)
-                    tflag[t] = 1;
+    } catch (...) {
+        for (auto &f : filters)
+            f.wait();
+        throw;
+    }
+    for (auto &f : filters)
+        f.get();
+    // distinct amplicons of the batch (a sequence depends on contig, start, end, orient)
+    struct Ref {
+        uint64_t k0, k1;
+        ServeReq *r;
+        uint32_t j;
+    };
+    std::vector<Ref> refs;
+    for (ServeReq *r : batch)
+        for (uint32_t j = 0; j < r->amps.size(); ++j) {
+            const ah_amplicon &x = r->amps[j];
+            refs.push_back({(uint64_t)x.contig << 32 | x.start, (uint64_t)x.end << 8 | x.orient, r, j});
         }
-        std::vector<uint64_t> tiles;
-        for (uint64_t t = 0; t < gs.n_tiles; ++t)
-            if (tflag[t])
-                tiles.push_back(t);
-        std::vector<ah_site> sites_h;
-        std::vector<uint8_t> pass_h;
-        std::vector<ah_amplicon> amps_h;
-        if (!tiles.empty()) {
-            uint64_t *tl = (uint64_t *)scratch(c, "serve_tiles", tiles.size() * sizeof(uint64_t));
-            AH_CUDA(cudaMemcpyAsync(tl, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-            std::vector<ScanPattern> pats = patterns_of(c, &pid, 1, kmax);
-            const PairDev *pd = upload_pairs(c, &pid, 1, st);
-            uint64_t *keys = nullptr;
-            const uint64_t ns = scan_keys(c, gs, pats, &keys, st, tl, tiles.size());
-            if (ns) {
-                ah_site *sites = (ah_site *)scratch(c, "serve_sites", ns * sizeof(ah_site));
-                sort_decode(c, gs, 1, keys, ns, sites, st);
-                float *tm = (float *)scratch(c, "serve_tm", ns * sizeof(float));
-                uint8_t *pass = (uint8_t *)scratch(c, "serve_pass", ns);
-                uint32_t *q = (uint32_t *)scratch(c, "tm_queue", ns * sizeof(uint32_t));
-                {
-                    Stage sg(c, "tm", st, 2);
-                    launch_tm(sites, ns, nullptr, pd, 1, gs.planes, gs.contig_off, tm, pass, q,
-                              (uint32_t *)(c->d_flags + kFlagTmQueue), tm_seg_max(c), tm_few_exact(c), c->d_err, st);
-                }
-                uint64_t *counts = (uint64_t *)scratch(c, "pair_counts", ns * sizeof(uint64_t));
-                uint64_t *offs = (uint64_t *)scratch(c, "pair_offsets", ns * sizeof(uint64_t));
-                size_t tb = scan_u64_temp_bytes(ns);
-                void *temp = scratch(c, "scan_temp", tb);
-                {
-                    Stage sg(c, "pair", st, 2 + scan_u64_launches(ns));
-                    launch_pair_count(sites, ns, nullptr, nullptr, pd, counts, st);
-                    exclusive_scan_u64(temp, tb, counts, offs, ns, st);
-                    launch_total(offs, counts, ns, nullptr, 0, c->d_aux, 0, nullptr, nullptr, 0, st);
-                }
-                check_flags(c, st);
-                const uint64_t na = c->h_flags[kFlagAux];
-                ah_amplicon *amps = (ah_amplicon *)scratch(c, "serve_amps", std::max<uint64_t>(na, 1) * sizeof(ah_amplicon));
-                if (na) {
-                    Stage sg(c, "pair", st, 1);
-                    launch_pair_write(sites, ns, nullptr, nullptr, pd, offs, amps, na, nullptr, 0, st);
-                }
-                sites_h.resize(ns);
-                pass_h.resize(ns);
-                amps_h.resize(na);
-                AH_CUDA(cudaMemcpyAsync(sites_h.data(), sites, ns * sizeof(ah_site), cudaMemcpyDeviceToHost, st));
-                AH_CUDA(cudaMemcpyAsync(pass_h.data(), pass, ns, cudaMemcpyDeviceToHost, st));
-                if (na)
-                    AH_CUDA(cudaMemcpyAsync(amps_h.data(), amps, na * sizeof(ah_amplicon), cudaMemcpyDeviceToHost, st));
-                check_flags(c, st);
-            }
+    std::sort(refs.begin(), refs.end(),
+              [](const Ref &a, const Ref &b) { return a.k0 != b.k0 ? a.k0 < b.k0 : a.k1 < b.k1; });
+    std::vector<ah_amplicon> recs;
+    std::vector<uint64_t> slot(refs.size());
+    for (size_t i = 0; i < refs.size(); ++i) {
+        if (i == 0 || refs[i].k0 != refs[i - 1].k0 || refs[i].k1 != refs[i - 1].k1)
+            recs.push_back(refs[i].r->amps[refs[i].j]);
+        slot[i] = recs.size() - 1;
+    }
+    const uint64_t nf = recs.size();
+    std::vector<uint64_t> f_off(nf + 1, 0);
+    for (uint64_t j = 0; j < nf; ++j)
+        f_off[j + 1] = f_off[j] + (recs[j].end - recs[j].start);
+    std::vector<char> seq_h(f_off.back());
+    if (nf) {
+        ah_amplicon *ra = (ah_amplicon *)scratch(c, "serve_fetch_amps", nf * sizeof(ah_amplicon));
+        uint64_t *ro = (uint64_t *)scratch(c, "serve_fetch_offs", (nf + 1) * sizeof(uint64_t));
+        char *rq = (char *)scratch(c, "serve_fetch_seq", std::max<uint64_t>(f_off.back(), 1));
+        AH_CUDA(cudaMemcpyAsync(ra, recs.data(), nf * sizeof(ah_amplicon), cudaMemcpyHostToDevice, st));
+        AH_CUDA(cudaMemcpyAsync(ro, f_off.data(), (nf + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+        {
+            Stage sg(c, "fetch", st, 1);
+            launch_fetch(ra, nf, nullptr, ro, gs.planes, gs.contig_off, rq, nullptr, 0, st);
         }
-        // per request: its genomes, its k, its Tm filter
-        std::vector<char> mine(gs.max_genome + 1, 0);
-        std::vector<int64_t> new_index(sites_h.size());
-        for (ServeReq *r : rs) {
-            for (uint32_t g : r->genomes)
-                if (g <= gs.max_genome)
-                    mine[g] = 1;
-            r->sites.clear();
-            for (size_t i = 0; i < sites_h.size(); ++i) {
-                const ah_site &x = sites_h[i];
-                const bool ok = x.genome <= gs.max_genome && mine[x.genome] && x.mm <= r->k;
-                new_index[i] = ok ? (int64_t)r->sites.size() : -1;
-                if (ok)
-                    r->sites.push_back(x);
-            }
-            r->n_sites = r->sites.size();
-            r->amps.clear();
-            for (const ah_amplicon &a : amps_h) {
-                if (new_index[a.left] < 0 || new_index[a.right] < 0)
-                    continue;
-                if (r->tm_filter && !(pass_h[a.left] && pass_h[a.right]))
-                    continue;
-                ah_amplicon b = a;
-                b.left = (uint32_t)new_index[a.left]; // indices into the request's own site list
-                b.right = (uint32_t)new_index[a.right];
-                r->amps.push_back(b);
-            }
-            for (uint32_t g : r->genomes)
-                if (g <= gs.max_genome)
-                    mine[g] = 0;
+        if (f_off.back())
+            AH_CUDA(cudaMemcpyAsync(seq_h.data(), rq, f_off.back(), cudaMemcpyDeviceToHost, st));
+        check_flags(c, st);
+    }
+    // per request, sequences in the order of its amplicons
+    std::map<ServeReq *, std::vector<uint64_t>> per;
+    for (ServeReq *r : batch)
+        per[r].assign(r->amps.size(), 0);
+    for (size_t i = 0; i < refs.size(); ++i)
+        per[refs[i].r][refs[i].j] = slot[i];
+    for (ServeReq *r : batch) {
+        r->seq_off.assign(1, 0);
+        r->seq.clear();
+        for (uint64_t j : per[r]) {
+            r->seq.insert(r->seq.end(), seq_h.begin() + f_off[j], seq_h.begin() + f_off[j + 1]);
+            r->seq_off.push_back(r->seq.size());
         }
     }
 }
@@ -1149,6 +1268,8 @@ void serve_loop(ah_server *S)
                 ServeReq &r = S->reqs[tickets[i]];
                 r.amps = std::move(work[i].amps);
                 r.sites = std::move(work[i].sites);
+                r.seq = std::move(work[i].seq);
+                r.seq_off = std::move(work[i].seq_off);
                 r.n_sites = work[i].n_sites;
                 r.batch_size = (uint32_t)tickets.size();
                 r.status = status;
@@ -1383,13 +1504,16 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
             gs->planes = (uint32_t *)dev_alloc(c, plane_bytes);
             gs->contig_off = (uint64_t *)dev_alloc(c, (n_contigs + 1) * sizeof(uint64_t));
             gs->contig_genome = (uint32_t *)dev_alloc(c, n_contigs * sizeof(uint32_t));
+            gs->tile_contig = (uint32_t *)dev_alloc(c, (gs->n_tiles + 1) * sizeof(uint32_t));
         } catch (...) {
             dev_free(c, gs->planes, plane_bytes);
             dev_free(c, gs->contig_off, (n_contigs + 1) * sizeof(uint64_t));
             dev_free(c, gs->contig_genome, n_contigs * sizeof(uint32_t));
+            dev_free(c, gs->tile_contig, (gs->n_tiles + 1) * sizeof(uint32_t));
             throw;
         }
-        gs->bytes = plane_bytes + (n_contigs + 1) * sizeof(uint64_t) + n_contigs * sizeof(uint32_t);
+        gs->bytes = plane_bytes + (n_contigs + 1) * sizeof(uint64_t) + n_contigs * sizeof(uint32_t) +
+                    (gs->n_tiles + 1) * sizeof(uint32_t);
         const bool dev_seq = n_bases && is_device_ptr(c, seq);
         // a queued run leaves the flag block and the staging scratch alone only for device input
         require((dev_seq && !reversed) || !c->pend.active, AH_ERR_ARG,
@@ -1480,6 +1604,8 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
             AH_CUDA(cudaMemcpyAsync(gs->contig_off, c->pin, ob, cudaMemcpyHostToDevice, st));
             AH_CUDA(cudaMemcpyAsync(gs->contig_genome, c->pin + ob, gb, cudaMemcpyHostToDevice, st));
             AH_CUDA(cudaEventRecord(c->pin_ev, st));
+            if (gs->n_tiles)
+                launch_tile_contigs(gs->contig_off, n_contigs, gs->n_tiles, gs->tile_contig, st);
         }
         if (c->set_events.empty()) {
             cudaEvent_t e;
@@ -1524,6 +1650,7 @@ ah_status ah_unload_genomes(ah_ctx *c, uint32_t set_id)
         dev_free(c, gs.planes, gs.n_tiles * kTileBytes);
         dev_free(c, gs.contig_off, (gs.n_contigs + 1) * sizeof(uint64_t));
         dev_free(c, gs.contig_genome, gs.n_contigs * sizeof(uint32_t));
+        dev_free(c, gs.tile_contig, (gs.n_tiles + 1) * sizeof(uint32_t));
         if (gs.ready)
             c->set_events.push_back(gs.ready);
         c->sets.erase(set_id);
@@ -2176,7 +2303,8 @@ ah_status ah_serve_submit(ah_server *S, const ah_request *req, uint64_t *ticket_
 }
 
 ah_status ah_serve_wait(ah_server *S, uint64_t ticket, ah_request_info *info, ah_site *sites_out, uint64_t sites_cap,
-                        ah_amplicon *amps_out, uint64_t amps_cap)
+                        ah_amplicon *amps_out, uint64_t amps_cap, char *seq_out, uint64_t seq_cap,
+                        uint64_t *seq_offsets_out)
 {
     if (!S || !info)
         return AH_ERR_ARG;
@@ -2192,6 +2320,7 @@ ah_status ah_serve_wait(ah_server *S, uint64_t ticket, ah_request_info *info, ah
     info->reserved = 0;
     info->n_sites = r.sites.size();
     info->n_amplicons = r.amps.size();
+    info->n_seq = r.seq.size();
     info->bases = r.bases;
     info->submit_ms = r.t_submit;
     info->start_ms = r.t_start;
@@ -2201,14 +2330,19 @@ ah_status ah_serve_wait(ah_server *S, uint64_t ticket, ah_request_info *info, ah
         S->reqs.erase(it);
         return st;
     }
-    if (r.sites.size() > sites_cap || r.amps.size() > amps_cap)
+    if (r.sites.size() > sites_cap || r.amps.size() > amps_cap || (seq_offsets_out && r.seq.size() > seq_cap))
         return AH_ERR_OVERFLOW; // kept: ask again with room
-    if ((!r.sites.empty() && !sites_out) || (!r.amps.empty() && !amps_out))
+    if ((!r.sites.empty() && !sites_out) || (!r.amps.empty() && !amps_out) || (seq_offsets_out && !r.seq.empty() && !seq_out))
         return AH_ERR_ARG;
     if (!r.sites.empty())
         memcpy(sites_out, r.sites.data(), r.sites.size() * sizeof(ah_site));
     if (!r.amps.empty())
         memcpy(amps_out, r.amps.data(), r.amps.size() * sizeof(ah_amplicon));
+    if (seq_offsets_out) {
+        memcpy(seq_offsets_out, r.seq_off.data(), r.seq_off.size() * sizeof(uint64_t));
+        if (!r.seq.empty())
+            memcpy(seq_out, r.seq.data(), r.seq.size());
+    }
     S->reqs.erase(it);
     return AH_OK;
 }

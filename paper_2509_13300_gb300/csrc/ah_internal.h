@@ -41,6 +41,9 @@ struct GenomeSet {
     uint32_t *planes = nullptr;        // device, n_tiles * kTileBytes
     uint64_t *contig_off = nullptr;    // device, n_contigs + 1
     uint32_t *contig_genome = nullptr; // device, n_contigs
+    // device, n_tiles + 1: tile_contig[t] = the last contig starting at or before
+    // position t * kTileBases (the contigs a tile's starts can fall in begin there)
+    uint32_t *tile_contig = nullptr;
     size_t bytes = 0;
     // recorded after the work that fills the set (the packing); every call that
     // reads the set waits for it on its own stream, and unloading waits for it
@@ -134,6 +137,9 @@ ScanKernel *scan_kernel(const std::vector<ScanPattern> &pats, const ScanTuning &
 // [seq_base, seq_base + seq_len) of a set of n_bases bases.
 void launch_pack(const uint8_t *seq, uint64_t seq_base, uint64_t seq_len, uint64_t n_bases, uint32_t *planes,
                  uint64_t t0, uint64_t t1, int *err, cudaStream_t s);
+// pack.cu: the per-tile contig table of a set (n_tiles + 1 entries)
+void launch_tile_contigs(const uint64_t *contig_off, uint32_t n_contigs, uint64_t n_tiles, uint32_t *out,
+                         cudaStream_t s);
 // One stretch of a contig-wise reversal: dst[k] = src[mirror - k] for k in
 // [start, start + len) (mirror = 2 * contig start + contig length - 1).
 struct RevChunk {

@@ -20,6 +20,8 @@
 // split between the logic and the multiply pipes (right shifts and nibble
 // placement are multiplies by run-time powers of two) so that the kernel is
 // bound by HBM: 1 byte read and 0.516 bytes written per base.
+#include <algorithm>
+
 #include "ah_internal.h"
 
 namespace ah {
@@ -249,6 +251,35 @@ __global__ void unpack_kernel(const uint32_t *__restrict__ planes, uint8_t *__re
 }
 
 } // namespace
+
+namespace {
+// tile_contig[t] = largest c < n_contigs with contig_off[c] <= t * kTileBases
+__global__ void tile_contigs_kernel(const uint64_t *__restrict__ contig_off, uint32_t n_contigs, uint64_t n_tiles,
+                                    uint32_t *__restrict__ out)
+{
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= n_tiles;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t P = t * kTileBases;
+        uint32_t lo = 0, hi = n_contigs;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (contig_off[mid] <= P)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        out[t] = lo;
+    }
+}
+} // namespace
+
+void launch_tile_contigs(const uint64_t *contig_off, uint32_t n_contigs, uint64_t n_tiles, uint32_t *out,
+                         cudaStream_t s)
+{
+    const uint64_t blocks = std::min<uint64_t>((n_tiles + 256) / 256, 4096);
+    tile_contigs_kernel<<<(unsigned)blocks, 256, 0, s>>>(contig_off, n_contigs, n_tiles, out);
+    AH_CUDA(cudaGetLastError());
+}
 
 void launch_pack(const uint8_t *seq, uint64_t seq_base, uint64_t seq_len, uint64_t n_bases, uint32_t *planes,
                  uint64_t t0, uint64_t t1, int *err, cudaStream_t s)

@@ -25,12 +25,14 @@
 // majority LOP3 plus integer adds for the sum (s = a + b + c - 2 maj), a mix
 // chosen by the tuner to balance the logic and integer pipes.
 //
-// Hits are rare; a warp that has any runs a slow path that rechecks each hit
-// bit against the contig table (windows never cross a contig end), recounts
-// its mismatches exactly from shared memory (a device check that the network
-// agrees), applies the 3' clamp, and appends 64-bit keys with one atomic per
-// warp.  Key = ((pair << pbits | flat position) << 10) | primer << 9 |
-// strand << 8 | mm, so sorting keys gives the canonical site order.
+// A warp with any hit runs a slower path in rounds, one hit per lane per
+// round: each lane checks its hit against the contig table (windows never
+// cross a contig end; the search is confined to the contigs of the tile by a
+// per-tile table), recounts its mismatches exactly from shared memory (a
+// device check that the network agrees) and applies the 3' clamp; the warp
+// appends the surviving 64-bit keys with one atomic per round.  Key =
+// ((pair << pbits | flat position) << 10) | primer << 9 | strand << 8 | mm,
+// so sorting keys gives the canonical site order.
 #include <nvrtc.h>
 
 #include <algorithm>
@@ -101,39 +103,36 @@ __device__ __forceinline__ bool mbar_wait(u64 *bar, u32 parity)
 // pattern tables.
 const char *kEmit = R"CUDA(
     if (__any_sync(0xffffffffu, any != 0u)) {
+        // Hits, one per lane per round: every lane takes its next hit bit, all
+        // check theirs at once (contig end, exact recount, clamp), and the warp
+        // appends the survivors with one atomic per round.
         u32 hl[NPAT * R];
 #pragma unroll
         for (int i = 0; i < NPAT * R; ++i) hl[i] = h[i];
-        u32 nv = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            u64 idx = 0;
-            if (pass == 1) {
-                u32 incl = nv;
-                for (int d = 1; d < 32; d <<= 1) {
-                    u32 y = __shfl_up_sync(0xffffffffu, incl, d);
-                    if (lane >= d) incl += y;
-                }
-                u32 total = __shfl_sync(0xffffffffu, incl, 31);
-                u64 base = 0;
-                if (lane == 31 && total) base = atomicAdd(counter, (u64)total);
-                base = __shfl_sync(0xffffffffu, base, 31);
-                idx = base + incl - nv;
-            }
-            for (int qr = 0; qr < NPAT * R; ++qr) {
-                u32 m = hl[qr];
+        // the contigs this tile's starts can fall in: [clo, chi)
+        const u32 clo = tile_contig[tile];
+        const u32 chi = min(n_contigs, tile_contig[tile + 1] + 1u);
+        int qr = 0;
+        u32 m = hl[0];
+        for (;;) {
+            while (m == 0u && qr + 1 < NPAT * R) m = hl[++qr];
+            const bool have = m != 0u;
+            if (!__any_sync(0xffffffffu, have)) break;
+            bool valid = false;
+            u64 key = 0;
+            if (have) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
                 const int q = qr / R, r = qr % R;
-                while (m) {
-                    const int b = __ffs(m) - 1;
-                    m &= m - 1;
-                    const int jr = j0 + r;
-                    const u64 P = tile * TB + (u64)b * W + wbase + jr;
-                    const int L = c_L[q];
-                    u32 lo = 0, hi = n_contigs;
-                    while (hi - lo > 1) {
-                        u32 mid = (lo + hi) >> 1;
-                        if (contig_off[mid] <= P) lo = mid; else hi = mid;
-                    }
-                    if (P + L > contig_off[lo + 1]) continue;
+                const int jr = j0 + r;
+                const u64 P = tile * TB + (u64)b * W + wbase + jr;
+                const int L = c_L[q];
+                u32 lo = clo, hi = chi;
+                while (hi - lo > 1) {
+                    u32 mid = (lo + hi) >> 1;
+                    if (contig_off[mid] <= P) lo = mid; else hi = mid;
+                }
+                if (P + L <= contig_off[lo + 1]) {
                     int mm = 0, clamp_bad = 0;
                     const int c = c_clamp[q];
                     for (int i = 0; i < L; ++i) {
@@ -145,14 +144,21 @@ const char *kEmit = R"CUDA(
                         const int in_clamp = c_strand[q] == 0 ? (i >= L - c) : (i < c);
                         clamp_bad |= mis & in_clamp;
                     }
-                    if (mm > c_k[q]) { atomicExch(err, 3); continue; } // network disagrees with the recount
-                    if (clamp_bad) continue;
-                    if (pass == 0) { ++nv; continue; }
-                    if (idx < cap)
-                        keys[idx] = ((((u64)c_pair[q] << pbits) | P) << 10) | ((u64)c_primer[q] << 9) |
-                                    ((u64)c_strand[q] << 8) | (u64)mm;
-                    ++idx;
+                    if (mm > c_k[q]) atomicExch(err, 3); // the network disagrees with the recount
+                    else if (!clamp_bad) {
+                        valid = true;
+                        key = ((((u64)c_pair[q] << pbits) | P) << 10) | ((u64)c_primer[q] << 9) |
+                              ((u64)c_strand[q] << 8) | (u64)mm;
+                    }
                 }
+            }
+            const u32 vb = __ballot_sync(0xffffffffu, valid);
+            if (vb) {
+                u64 base = 0;
+                if (lane == 0) base = atomicAdd(counter, (u64)__popc(vb));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                const u64 idx = base + __popc(vb & ((1u << lane) - 1u));
+                if (valid && idx < cap) keys[idx] = key;
             }
         }
     }
@@ -352,7 +358,8 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
     os << "extern \"C\" __global__ void __launch_bounds__(NT, " << t.min_blocks << ")\n"
        << "ah_scan_kernel(const u32 *__restrict__ planes, u64 n_tiles, const u64 *__restrict__ contig_off,\n"
        << "               u32 n_contigs, u64 *__restrict__ keys, u64 cap, u64 *__restrict__ counter, int pbits,\n"
-       << "               int *__restrict__ err, u64 *__restrict__ work, const u64 *__restrict__ tile_list)\n{\n"
+       << "               int *__restrict__ err, u64 *__restrict__ work, const u64 *__restrict__ tile_list,\n"
+       << "               const u32 *__restrict__ tile_contig)\n{\n"
        << "  // Every warp claims slices of tiles (32*R words of each plane plus a 32-word\n"
        << "  // overhang) from the shared counter `work` (zeroed before the launch), so SMs\n"
        << "  // that run faster take more, and runs its own S-stage pipeline: lane 0 claims\n"

@@ -697,7 +697,9 @@ def _served_oracle(w, pair, genomes, k, tm_filter):
     passed = None
     if tm_filter and len(sites):
         _, passed = oracle.tm(w.seq, w.contig_off, sites, [p])
-    return sites, oracle.pair(sites, [p], passed)
+    amps = oracle.pair(sites, [p], passed)
+    seqs, offs = oracle.fetch(w.seq, w.contig_off, amps)
+    return sites, amps, seqs, offs
 
 
 def test_served_requests_alone_and_in_the_mix(ctx):
@@ -737,18 +739,20 @@ def test_served_requests_alone_and_in_the_mix(ctx):
         assert len(ctx.scan(sid, [pids[0]])) > 0
     finally:
         ctx.ah_unload_genomes(sid)
-    assert max(i["batch_size"] for _, _, i in mixed) > 8
-    assert max(i["batch_size"] for _, _, i in budget) < max(i["batch_size"] for _, _, i in mixed)
-    assert all(i["batch_size"] == 1 for _, _, i in alone)
+    assert max(x[4]["batch_size"] for x in mixed) > 8
+    assert max(x[4]["batch_size"] for x in budget) < max(x[4]["batch_size"] for x in mixed)
+    assert all(x[4]["batch_size"] == 1 for x in alone)
     total_amps = 0
     for n, ((g, j, k, f), a, m, b) in enumerate(zip(reqs, alone, mixed, budget)):
         for x in (m, b):
             assert x[0].tobytes() == a[0].tobytes(), n
             assert x[1].tobytes() == a[1].tobytes(), n
-        info = a[2]
+            assert x[2] == a[2] and np.array_equal(x[3], a[3]), n
+        info = a[4]
         assert info["status"] == 0 and info["submit_ms"] <= info["start_ms"] <= info["done_ms"]
-        want_s, want_a = _served_oracle(w, pairs[j], [x for x in g if x < n_g], k, f)
+        want_s, want_a, want_q, want_o = _served_oracle(w, pairs[j], [x for x in g if x < n_g], k, f)
         assert a[0].tobytes() == want_s.tobytes(), n
         assert a[1].tobytes() == want_a.tobytes(), n
+        assert a[2] == want_q and np.array_equal(a[3], want_o), n
         total_amps += len(want_a)
     assert total_amps > 10
