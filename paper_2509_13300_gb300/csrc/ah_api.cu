@@ -36,6 +36,11 @@ struct ah_ctx {
     uint64_t *d_aux = nullptr;
     int *d_err = nullptr;
     cudaStream_t copy_stream = nullptr; // host->device copies that overlap packing
+    // ah_run's kernels go on this stream, created with the highest priority and
+    // joined to the caller's stream by events: when the next set's packing runs
+    // beside a run's later stages, the block scheduler prefers the run's blocks
+    cudaStream_t run_stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_packed[2] = {nullptr, nullptr};
     uint64_t *h_flags = nullptr;     // pinned host mirror of the flag block
     bool flags_dirty = false;        // work was queued that may set the error word, not read since
@@ -73,7 +78,8 @@ struct ah_ctx {
         uint32_t set_id = 0;
         std::vector<uint32_t> pair_ids;
         ah_run_out *o = nullptr;
-        cudaStream_t st = nullptr;
+        cudaStream_t st = nullptr;     // the run stream
+        cudaStream_t caller = nullptr; // the caller's stream
         const PairDev *pd = nullptr;
         FastRun fr;
     } pend;
@@ -849,6 +855,21 @@ void require_idle(ah_ctx *c)
     require(!c->serving, AH_ERR_ARG, "a server owns the context: stop it first");
 }
 
+// A run's work goes on the run stream, after the caller's earlier work; the
+// caller's stream then waits for everything the run queued.
+cudaStream_t enter_run_stream(ah_ctx *c, cudaStream_t caller)
+{
+    AH_CUDA(cudaEventRecord(c->ev_in, caller));
+    AH_CUDA(cudaStreamWaitEvent(c->run_stream, c->ev_in, 0));
+    return c->run_stream;
+}
+
+void leave_run_stream(ah_ctx *c, cudaStream_t caller)
+{
+    AH_CUDA(cudaEventRecord(c->ev_out, c->run_stream));
+    AH_CUDA(cudaStreamWaitEvent(caller, c->ev_out, 0));
+}
+
 void run_steps(ah_ctx *c, const GenomeSet &gs, const PairDev *pd, uint32_t n_pairs, uint64_t *keys, uint64_t ns,
                ah_run_out *o, cudaStream_t st)
 {
@@ -1310,13 +1331,14 @@ ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
     c->budget = mem_budget_bytes;
     ah_status st = guarded(c, [&] {
         AH_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device));
-        // default scan variant; AH_SCAN_TUNING="R,arith_pct,order,stages,warps[,min_blocks]" overrides
+        // default scan variant; AH_SCAN_TUNING="R,arith_pct,order,stages,warps[,min_blocks[,resident]]" overrides
         // it (profiling aid)
         if (const char *e = getenv("AH_SCAN_TUNING")) {
-            int R = 8, ap = 0, order = 1, S = 3, wpc = 4, mb = 1;
-            if (sscanf(e, "%d,%d,%d,%d,%d,%d", &R, &ap, &order, &S, &wpc, &mb) >= 1 && (R == 4 || R == 8) && ap >= 0 &&
-                ap <= 100 && (order == 0 || order == 1) && S >= 2 && S <= 4 && wpc >= 1 && wpc <= 16 && mb >= 1 &&
-                mb <= 8) {
+            int R = 8, ap = 0, order = 1, S = 3, wpc = 4, mb = 1, res = 0;
+            if (sscanf(e, "%d,%d,%d,%d,%d,%d,%d", &R, &ap, &order, &S, &wpc, &mb, &res) >= 1 && (R == 4 || R == 8) &&
+                ap >= 0 && ap <= 100 && (order == 0 || order == 1) && S >= 2 && S <= 4 && wpc >= 1 && wpc <= 16 &&
+                mb >= 1 && mb <= 8 && res >= 0 && res <= 8) {
+                c->tuning.resident = res;
                 c->tuning.R = R;
                 c->tuning.arith_pct = ap;
                 c->tuning.order = order;
@@ -1334,6 +1356,13 @@ ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
         AH_CUDA(cudaStreamSynchronize(c->stream));
         AH_CUDA(cudaMallocHost(&c->h_flags, kFlagWords * sizeof(uint64_t)));
         AH_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        {
+            int least = 0, greatest = 0;
+            AH_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+            AH_CUDA(cudaStreamCreateWithPriority(&c->run_stream, cudaStreamNonBlocking, greatest));
+        }
+        AH_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+        AH_CUDA(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
         AH_CUDA(cudaEventCreateWithFlags(&c->pin_ev, cudaEventDisableTiming));
         AH_CUDA(cudaEventCreateWithFlags(&c->ev_run, cudaEventDisableTiming));
         for (int b = 0; b < 2; ++b) {
@@ -1384,6 +1413,14 @@ void ah_destroy(ah_ctx *c)
         cudaStreamSynchronize(c->copy_stream);
         cudaStreamDestroy(c->copy_stream);
     }
+    if (c->run_stream) {
+        cudaStreamSynchronize(c->run_stream);
+        cudaStreamDestroy(c->run_stream);
+    }
+    if (c->ev_in)
+        cudaEventDestroy(c->ev_in);
+    if (c->ev_out)
+        cudaEventDestroy(c->ev_out);
     for (int b = 0; b < 2; ++b) {
         if (c->ev_copied[b])
             cudaEventDestroy(c->ev_copied[b]);
@@ -1859,7 +1896,8 @@ ah_status ah_run_begin(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
         o->n_sites = o->n_amplicons = o->n_seq = 0;
         HostSpan hs(c, "host.run");
         GenomeSet &gs = get_set(c, set_id);
-        cudaStream_t st = stream_of(c, stream);
+        const cudaStream_t caller = stream_of(c, stream);
+        cudaStream_t st = enter_run_stream(c, caller);
         wait_ready(gs, st);
         std::vector<ScanPattern> pats = patterns_of(c, pair_ids, n_pairs);
         const PairDev *pd = upload_pairs(c, pair_ids, n_pairs, st);
@@ -1869,9 +1907,11 @@ ah_status ah_run_begin(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
         P.pair_ids.assign(pair_ids, pair_ids + n_pairs);
         P.o = o;
         P.st = st;
+        P.caller = caller;
         P.pd = pd;
         if (gs.n_tiles && c->last_sites <= kSmallSort) {
             fast_begin(c, gs, pats, pd, n_pairs, o, st, (cudaEvent_t)scan_done, &P.fr);
+            leave_run_stream(c, caller);
             P.active = true;
             return;
         }
@@ -1888,6 +1928,7 @@ ah_status ah_run_begin(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
             P.status = e.status; // reported by ah_run_end, like the counts
             P.msg = e.msg;
         }
+        leave_run_stream(c, caller);
         P.active = P.done = true;
     });
 }
@@ -1911,13 +1952,16 @@ ah_status ah_run_end(ah_ctx *c)
         uint64_t *keys = nullptr;
         uint64_t ns = 0;
         const FastResult r = fast_end(c, P.o, P.st, P.fr, &keys, &ns);
-        if (r == kFastDone)
+        if (r == kFastDone) {
+            leave_run_stream(c, P.caller); // delivery copies may have been queued
             return;
+        }
         if (r == kFastRescan) {
             std::vector<ScanPattern> pats = patterns_of(c, P.pair_ids.data(), n_pairs);
             ns = scan_keys(c, gs, pats, &keys, P.st);
         }
         run_steps(c, gs, P.pd, n_pairs, keys, ns, P.o, P.st);
+        leave_run_stream(c, P.caller);
     });
 }
 

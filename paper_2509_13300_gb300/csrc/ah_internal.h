@@ -84,6 +84,8 @@ struct ScanTuning {
     int order = 0;        // 0: word-major, 1: pattern-major code order
     int stages = 4;       // TMA stages per warp (2..4)
     int warps = 16;       // warps per CTA (1..16); 16 warps = a 128-register cap
+    int resident = 0;     // CTAs launched per SM (0: as many as fit); fewer leave room for a
+                          // kernel that runs beside the scan (the next set's packing)
 };
 
 struct ScanKernel {

@@ -21,6 +21,7 @@
 // placement are multiplies by run-time powers of two) so that the kernel is
 // bound by HBM: 1 byte read and 0.516 bytes written per base.
 #include <algorithm>
+#include <cstdlib>
 
 #include "ah_internal.h"
 
@@ -296,6 +297,11 @@ void launch_pack(const uint8_t *seq, uint64_t seq_base, uint64_t seq_len, uint64
         AH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         AH_CUDA(cudaFuncSetAttribute(pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_kernel, kPackThreads, smem));
+        // one block per tile: blocks end as tiles are done, so kernels that run
+        // beside the packing (a run's later stages) get SMs as they free up;
+        // AH_PACK_BLOCKS=n keeps n persistent blocks per SM instead (profiling aid)
+        const char *e = getenv("AH_PACK_BLOCKS");
+        per_sm = (e && atoi(e) > 0) ? std::max(1, std::min(per_sm, atoi(e))) : (1 << 20);
         cached_dev = dev;
     }
     uint64_t blocks = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);

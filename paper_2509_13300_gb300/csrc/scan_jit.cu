@@ -500,7 +500,7 @@ ScanKernel *scan_kernel(const std::vector<ScanPattern> &pats, const ScanTuning &
     // cache key: device, tuning and the patterns (cheap; the source is only generated on a miss)
     std::string key = std::to_string(device) + "|" + std::to_string(t.R) + "," + std::to_string(t.arith_pct) + "," +
                       std::to_string(t.min_blocks) + "," + std::to_string(t.order) + "," + std::to_string(t.stages) +
-                      "," + std::to_string(t.warps) + "|";
+                      "," + std::to_string(t.warps) + "," + std::to_string(t.resident) + "|";
     for (auto &p : pats) {
         key += std::to_string(p.L) + "," + std::to_string(p.k) + "," + std::to_string(p.clamp) + "," +
                std::to_string(p.pair) + "," + std::to_string(p.primer) + "," + std::to_string(p.strand) + ":";
@@ -534,6 +534,8 @@ ScanKernel *scan_kernel(const std::vector<ScanPattern> &pats, const ScanTuning &
     int bps = 0;
     AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void *)k->fn, k->threads, k->smem));
     k->blocks_per_sm = std::max(1, bps);
+    if (t.resident > 0)
+        k->blocks_per_sm = std::min(k->blocks_per_sm, t.resident);
     ScanKernel *raw = k.get();
     g_cache[key] = std::move(k);
     return raw;
