@@ -243,7 +243,7 @@ def main():
                     help="plain: the genome-collection line (default); batched / served: those forms' lines")
     ap.add_argument("--chunk-bases", type=int, default=2_000_000_000, help="batched: bases per set (whole genomes)")
     ap.add_argument("--plain-genomes", type=int, default=400, help="batched: genomes timed in the plain form")
-    ap.add_argument("--requests", type=int, default=200, help="served: requests")
+    ap.add_argument("--requests", type=int, default=2000, help="served: requests")
     ap.add_argument("--rate", type=float, default=20.0, help="served: Poisson arrivals per second")
     ap.add_argument("--max-batch", type=int, default=64, help="served: requests per batch")
     ap.add_argument("--mem-budget", type=int, default=4 << 30, help="served: bytes one batch may plan for")
@@ -464,16 +464,26 @@ def ctx_scan_lop_count(pair: dict, tune: dict) -> int:
 # each, beside the plain form's.  Genomes come from the counter-based
 # generator, made on the device (ah_generate_bases).
 # ---------------------------------------------------------------------------
-def form_pairs(n: int, seed: int, ks):
-    """n degenerate pairs: the paper's four (Sec. 2.3), then random IUPAC pairs of 17-25 nt."""
+def synthetic_pairs(seed: int, ks):
+    """Four degenerate pairs of 17-25 nt whose oligo totals (sum of the two
+    primers' degeneracies) are 16, 64, 256 and 960; k cycles over ks."""
     from paper_2509_13300_gb300 import synth
     rng = np.random.default_rng(seed)
-    fr = list(synth.PAPER_PAIRS.values())
-    while len(fr) < n:
-        fr.append((synth.random_primer(rng, int(rng.integers(17, 26)), "RYSWKM"),
-                   synth.random_primer(rng, int(rng.integers(17, 26)), "RYSWKM")))
+    two = lambda n: "".join(rng.choice(list(synth.TWO_WAY), n))
+    three = lambda n: "".join(rng.choice(list(synth.THREE_WAY), n))
+    fr = [(synth.random_primer(rng, 17, two(3)), synth.random_primer(rng, 18, two(3))),      # 8 + 8
+          (synth.random_primer(rng, 19, two(5)), synth.random_primer(rng, 21, two(5))),      # 32 + 32
+          (synth.random_primer(rng, 22, two(7)), synth.random_primer(rng, 24, two(7))),      # 128 + 128
+          (synth.random_primer(rng, 20, two(6) + three(2)),                                  # 576
+           synth.random_primer(rng, 22, "N" + two(5) + three(1)))]                          # + 384
     return [synth.pcr_params(f, r, k=int(ks[i % len(ks)]), min_len=100, max_len=3000, tm_min=45.0)
-            for i, (f, r) in enumerate(fr[:n])]
+            for i, (f, r) in enumerate(fr)]
+
+
+def paper_pairs(k: int):
+    """The four pairs printed in the paper (Sec. 2.3)."""
+    from paper_2509_13300_gb300 import synth
+    return [synth.pcr_params(f, r, k=k, min_len=100, max_len=3000, tm_min=45.0) for f, r in synth.PAPER_PAIRS.values()]
 
 
 def device_collection(ctx, coll, torch, chunk: int = 1 << 31):
@@ -548,9 +558,9 @@ def bench_batched(args):
     build.build()
     torch.cuda.set_device(0)
     n_g = args.n_genomes if args.n_genomes != 100 else 10_000
-    pairs = form_pairs(4, 11, (3, 4, 4, 2))
+    pairs = synthetic_pairs(2, (2, 3, 4, 2))
     t0 = time.perf_counter()
-    coll = countergen.collection(seed=11, n_genomes=n_g, len_lo=0.5e6, len_hi=8e6, pairs=pairs)
+    coll = countergen.collection(seed=2, n_genomes=n_g, len_lo=0.5e6, len_hi=8e6, pairs=pairs)
     t_layout = time.perf_counter() - t0
     ctx = ah.Context(0)
     pids = [ctx.ah_set_primers(p["fwd"], p["rev"], p) for p in pairs]
@@ -642,31 +652,37 @@ def bench_batched(args):
         stages[name] = {"ms": ms, "launches": l}
     ctx.ah_set_profiling(0)
     gbps = N * len(pairs) * args.steps / t_batched / 1e9
-    # plain form: one genome per load and per run (host input, host outputs), on a sample
+    # plain forms on a sample of genomes (host input, host outputs): one genome per
+    # load, then one run per pair (one launch per genome per pair), and one run
+    # with every pair
     rng = np.random.default_rng(0)
     sample = np.sort(rng.choice(n_g, size=min(n_g, args.plain_genomes), replace=False))
     plain_out = HostOut(torch, ah)
     hs = torch.cuda.current_stream()
 
-    def plain(g):
+    def plain(g, per_pair):
         b0, b1, off, gen_ = sub_tables(coll, int(g), int(g) + 1)
         sid = ctx.ah_load_genomes(host[b0:b1], b1 - b0, off, gen_, hs)
-        plain_out.run(ctx, sid, pids, hs)
+        for ids in ([[p] for p in pids] if per_pair else [pids]):
+            plain_out.run(ctx, sid, ids, hs)
         ctx.ah_unload_genomes(sid)
         return b1 - b0
 
-    for g in sample[:5]:
-        plain(g)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    nb = sum(plain(g) for g in sample)
-    torch.cuda.synchronize()
-    t_plain = time.perf_counter() - t0
-    gbps_plain = nb * len(pairs) / t_plain / 1e9
+    plain_res = {}
+    for per_pair in (True, False):
+        for g in sample[:5]:
+            plain(g, per_pair)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nb = sum(plain(g, per_pair) for g in sample)
+        torch.cuda.synchronize()
+        t_plain = time.perf_counter() - t0
+        plain_res[per_pair] = (nb * len(pairs) / t_plain / 1e9, t_plain, nb)
+    gbps_plain, t_plain, nb = plain_res[True]
     line = {
         "form": "batched", "metric": "Gbp/s scanned per primer pair (both strands, k mm)", "value": gbps,
         "unit": "Gbp/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "s_per_pass": t_batched / args.steps, "higher_is_better": True, "data": "synthetic (counter-based, seed 11)",
+        "s_per_pass": t_batched / args.steps, "higher_is_better": True, "data": "synthetic (counter-based, seed 2)",
         "config": {"workload": f"batched-{n_g}genomes-{N / 1e9:.1f}Gbp-{len(pairs)}pairs",
                    "n_genomes": n_g, "n_bases": N, "n_contigs": len(coll.contig_genome),
                    "pairs": [(p["fwd"], p["rev"], p["k"]) for p in pairs], "chunks": len(tabs),
@@ -675,9 +691,11 @@ def bench_batched(args):
                    "sequences)", "scan_tuning": tune, "layout_s": t_layout},
         "results_per_pass": totals, "gpu_launches_per_pass": launches / max(1, args.steps),
         "plain": {"value": gbps_plain, "unit": "Gbp/s", "genomes": len(sample), "bases": int(nb),
-                  "form": "one genome per ah_load_genomes (host input) and per ah_run (4 pairs, host outputs)",
+                  "form": "one genome per ah_load_genomes (host input), one ah_run per pair (host outputs)",
                   "s": t_plain},
-        "batched_over_plain": gbps / gbps_plain, "clocks": clk.summary(), "stages_ms_one_pass": stages,
+        "plain_all_pairs": {"value": plain_res[False][0], "unit": "Gbp/s", "s": plain_res[False][1],
+                            "form": "one genome per ah_load_genomes, one ah_run with the 4 pairs"},
+        "batched_over_plain": gbps / gbps_plain, "batched_over_plain_all_pairs": gbps / plain_res[False][0], "clocks": clk.summary(), "stages_ms_one_pass": stages,
     }
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -691,100 +709,133 @@ def bench_served(args):
     build.build()
     torch.cuda.set_device(0)
     n_g = args.n_genomes if args.n_genomes != 100 else 5_000
-    pairs = form_pairs(8, 13, (4,))
+    pairs = paper_pairs(4) + synthetic_pairs(3, (4,))
     t0 = time.perf_counter()
-    coll = countergen.collection(seed=13, n_genomes=n_g, len_lo=2e6, len_hi=7e6, pairs=pairs)
+    coll = countergen.collection(seed=3, n_genomes=n_g, len_lo=2e6, len_hi=7e6, pairs=pairs)
     t_layout = time.perf_counter() - t0
     ctx = ah.Context(0)
     pid = [ctx.ah_set_primers(p["fwd"], p["rev"], p) for p in pairs]
     dev = device_collection(ctx, coll, torch)
     N = coll.n_bases
     sid = ctx.ah_load_genomes(dev, N, coll.contig_off, coll.contig_genome)
-    # requests: Zipf subset size over 1..n_g (P(s) ~ 1/s), a contiguous run of genomes
-    rng = np.random.default_rng(17)
+    # requests: subset size Zipf over 1..n_g (P(s) ~ 1/s), members uniform without replacement
+    rng = np.random.default_rng(3)
     R = args.requests
     w = 1.0 / np.arange(1, n_g + 1)
     sizes = rng.choice(np.arange(1, n_g + 1), size=R, p=w / w.sum())
-    starts = np.array([rng.integers(0, n_g - s + 1) for s in sizes])
-    req = [(int(a), int(a + s), int(rng.integers(len(pairs))), int(rng.integers(0, 5))) for a, s in zip(starts, sizes)]
+    req = [(np.sort(rng.choice(n_g, size=int(z), replace=False)).astype(np.uint32), int(rng.integers(len(pairs))),
+            int(rng.integers(0, 5))) for z in sizes]
     gbases = np.diff(coll.genome_off.astype(np.int64))
-    req_bases = [int(gbases[a:b].sum()) for a, b, _, _ in req]
-
-    def serve(arrivals, max_batch, budget):
+    req_bases = [int(gbases[g].sum()) for g, _, _ in req]
+    def serve(arrivals, max_batch, budget, n=None):
+        """Serve the first n requests at the given arrival times; returns per request
+        (n_sites, n_amplicons, digest of sites, amplicons and sequences) and the stats."""
+        import hashlib
         import threading as th
-        res = [None] * R
+        n = R if n is None else n
+        res = [None] * n
         with ah.Server(ctx, sid, mem_budget=budget, max_batch=max_batch) as srv:
-            tickets = [None] * R
-            ready = [th.Event() for _ in range(R)]
+            tickets = [None] * n
+            ready = [th.Event() for _ in range(n)]
 
             def submitter():
                 t_start = time.perf_counter()
-                for i, (a, b, j, k) in enumerate(req):
+                for i, (g, j, k) in enumerate(req[:n]):
                     dt = arrivals[i] - (time.perf_counter() - t_start)
                     if dt > 0:
                         time.sleep(dt)
-                    tickets[i] = srv.submit(np.arange(a, b, dtype=np.uint32), pid[j], k, True)
+                    tickets[i] = srv.submit(g, pid[j], k, True)
                     ready[i].set()
 
             thr = th.Thread(target=submitter)
             thr.start()
-            for i in range(R):
+            for i in range(n):
                 ready[i].wait()
-                res[i] = srv.wait(tickets[i])
+                sites, amps, seq, offs, info = srv.wait(tickets[i])
+                h = hashlib.sha1(sites.tobytes())
+                h.update(amps.tobytes())
+                h.update(seq)
+                res[i] = (len(sites), len(amps), h.hexdigest(), info)
             thr.join()
-        info = [r[4] for r in res]
+        info = [r[3] for r in res]
         lat = np.array([x["done_ms"] - x["submit_ms"] for x in info])
         span = (max(x["done_ms"] for x in info) - min(x["submit_ms"] for x in info)) / 1e3
         return res, {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                      "mean_ms": float(lat.mean()), "makespan_s": span,
-                     "gbps": sum(req_bases) / span / 1e9,
+                     "gbps": sum(req_bases[:n]) / span / 1e9,
                      "batches": len({x["batch"] for x in info}),
-                     "mean_batch": float(np.mean([x["batch_size"] for x in info]))}
+                     "mean_batch": float(np.mean([x["batch_size"] for x in info])),
+                     "max_batch": int(max(x["batch_size"] for x in info))}
 
     # warm-up: the scan variant of every (pair, k) compiles on first use
     with ah.Server(ctx, sid, mem_budget=args.mem_budget, max_batch=1) as srv:
         for j in range(len(pairs)):
             for k in range(5):
                 srv.wait(srv.submit(np.arange(0, 2, dtype=np.uint32), pid[j], k, True))
-    serve(np.zeros(R), args.max_batch, args.mem_budget)
+    serve(np.zeros(R), args.max_batch, args.mem_budget, n=min(R, 100))
     arr = np.cumsum(rng.exponential(1.0 / args.rate, size=R))
     res_p, poisson = serve(arr, args.max_batch, args.mem_budget)
     res_s, saturated = serve(np.zeros(R), args.max_batch, args.mem_budget)
     for x, y in zip(res_p, res_s):   # the same results whatever they were batched with
-        assert x[0].tobytes() == y[0].tobytes() and x[1].tobytes() == y[1].tobytes() and x[2] == y[2]
-    # sequential plain solves: each request's genomes loaded as their own set, one ah_run
+        assert x[:3] == y[:3]
+    # stage split of a saturated pass (untimed, events around every stage)
+    ctx.ah_set_profiling(1)
+    _, prof_run = serve(np.zeros(R), args.max_batch, args.mem_budget, n=min(R, 400))
+    stages = {"requests": min(R, 400), "makespan_s": prof_run["makespan_s"]}
+    for name in ("scan", "sort", "decode", "tm", "pair", "fetch", "host.serve.tiles", "host.serve.device",
+                 "host.serve.filter_wait", "host.serve.fetch", "host.serve.batch"):
+        ms, l, calls = ctx.ah_get_profile(name)
+        stages[name] = {"ms": ms, "launches": l, "calls": calls}
+    ctx.ah_set_profiling(0)
+    # sequential plain solves: each request's genomes gathered into one buffer
+    # (untimed), packed as their own set, one ah_run
     ctx_pids = {}
     out = HostOut(torch, ah)
     hs = torch.cuda.current_stream()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    goff = coll.genome_off.astype(np.int64)
+    coff = coll.contig_off.astype(np.int64)
+    cfirst = np.searchsorted(coff, goff[:-1], side="left")
+    clast = np.searchsorted(coff, goff[1:], side="left")
+    gbuf = torch.empty(max(req_bases), dtype=torch.uint8, device="cuda")
+    t_seq = 0.0
     lat = []
-    for (a, b, j, k), rr in zip(req, res_s):
-        t1 = time.perf_counter()
+    for (g, j, k), rr in zip(req, res_s):
         if (j, k) not in ctx_pids:
             p = dict(pairs[j], k=k)
             ctx_pids[(j, k)] = ctx.ah_set_primers(p["fwd"], p["rev"], p)
-        b0, b1, off, gen_ = sub_tables(coll, a, b)
-        s2 = ctx.ah_load_genomes(dev[b0:], b1 - b0, off, gen_, hs)
+        parts, offs, gens, o = [], [0], [], 0
+        for x in g.tolist():
+            parts.append(dev[int(goff[x]):int(goff[x + 1])])
+            c = coff[cfirst[x]:clast[x] + 1] - goff[x] + o
+            offs.extend(c[1:].tolist())
+            gens.extend([x] * (clast[x] - cfirst[x]))
+            o += int(gbases[x])
+        torch.cat(parts, out=gbuf[:o])
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        s2 = ctx.ah_load_genomes(gbuf, o, np.array(offs, np.uint64), np.array(gens, np.uint32), hs)
         out.run(ctx, s2, [ctx_pids[(j, k)]], hs)
         ctx.ah_unload_genomes(s2)
-        assert out.o.n_amplicons == len(rr[1]) and out.o.n_sites == len(rr[0])
-        lat.append((time.perf_counter() - t1) * 1e3)
-    t_seq = time.perf_counter() - t0
+        dt = time.perf_counter() - t1
+        t_seq += dt
+        lat.append(dt * 1e3)
+        assert out.o.n_sites == rr[0] and out.o.n_amplicons == rr[1]
     seq_plain = {"gbps": sum(req_bases) / t_seq / 1e9, "s": t_seq, "p50_ms": float(np.percentile(lat, 50)),
                  "p99_ms": float(np.percentile(lat, 99)),
-                 "form": "each request alone: its genomes packed as their own set from device memory, one ah_run"}
+                 "form": "each request alone: its genomes (gathered in device memory, untimed) packed as "
+                         "their own set, one ah_run"}
     ctx.ah_unload_genomes(sid)
     line = {
         "form": "served", "metric": "p50/p99 request latency; aggregate Gbp/s scanned per primer pair",
         "value": saturated["gbps"], "unit": "Gbp/s", "n_gpus": 1, "higher_is_better": True,
-        "data": "synthetic (counter-based, seed 13)",
+        "data": "synthetic (counter-based, seed 3)",
         "config": {"workload": f"served-pool{n_g}genomes-{N / 1e9:.1f}Gbp-8pairs", "n_genomes": n_g, "n_bases": N,
-                   "requests": R, "rate_per_s": args.rate, "subset": "Zipf size over 1..n (P ~ 1/s), contiguous ids",
+                   "requests": R, "rate_per_s": args.rate,
+                   "subset": "Zipf size over 1..n (P ~ 1/s), members uniform without replacement",
                    "k": "uniform 0..4", "pairs": [(p["fwd"], p["rev"]) for p in pairs], "tm_filter": True,
                    "max_batch": args.max_batch, "mem_budget": args.mem_budget, "layout_s": t_layout,
                    "request_gbp_total": sum(req_bases) / 1e9},
-        "poisson": poisson, "saturated": saturated, "sequential_plain": seq_plain,
+        "poisson": poisson, "saturated": saturated, "sequential_plain": seq_plain, "stages_ms_saturated": stages,
         "saturated_over_sequential": saturated["gbps"] / seq_plain["gbps"],
     }
     print(json.dumps(line), flush=True)

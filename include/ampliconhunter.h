@@ -479,7 +479,8 @@ ah_status ah_pair_noalloc(const int32_t *pair_windows, uint32_t n_pairs, const a
  * arrival order while their estimated device memory (sites and amplicons
  * scale with the request's bases) stays within cfg->mem_budget bytes, at
  * most cfg->max_batch of them and always at least one, and runs them
- * together (one scan per primer pair over the union of their genomes' tiles).
+ * together (one scan per primer pair and k over the union of their genomes'
+ * tiles).
  * Until ah_serve_stop no other call may use the context.
  * ah_serve_submit (any thread) queues a copy of the request and returns a
  * ticket.  ah_serve_wait (any thread) blocks until the ticket's request is

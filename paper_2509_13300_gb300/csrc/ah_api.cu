@@ -963,12 +963,12 @@ void run_steps(ah_ctx *c, const GenomeSet &gs, const PairDev *pd, uint32_t n_pai
 // A worker thread owns the context while the server runs.  Requests wait in a
 // FIFO queue; each time the GPU is free the worker admits the queued requests
 // whose estimated device memory fits the budget (at least one), and runs them
-// as one batch: per primer pair, one scan over the union of their genomes'
-// tiles at the largest k among them, then sort, Tm and all-pairs amplicon
-// calling on those sites.  A request's result is then filtered exactly: its
-// genomes, its k (mm <= k) and, with its Tm filter, both sites passing.  A
-// site and an amplicon depend only on their own windows, so a request's result
-// does not depend on what it was batched with.
+// as one batch: per (primer pair, k), one scan over the union of the
+// requests' genomes' tiles, then sort, Tm and all-pairs amplicon calling on
+// those sites.  A request's result is then taken out exactly: the sites of its
+// genomes and the amplicons between them (both ends passing under its Tm
+// filter).  A site and an amplicon depend only on their own windows, so a
+// request's result does not depend on what it was batched with.
 // ---------------------------------------------------------------------------
 struct ServeReq {
     std::vector<uint32_t> genomes;
@@ -1001,7 +1001,22 @@ struct ah_server {
     bool stop = false;
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
     std::vector<uint64_t> genome_bases; // bases per genome id
-    std::vector<std::vector<uint32_t>> genome_contigs;
+    // contigs of each genome id (CSR): genome_contig[genome_first[g] .. genome_first[g + 1])
+    std::vector<uint64_t> genome_first;
+    std::vector<uint32_t> genome_contig;
+    // pinned staging of a group's device results (several, so that the host
+    // filtering of a group overlaps the next groups' device work)
+    static constexpr int kStaging = 6;
+    struct Staging {
+        void *p = nullptr;
+        size_t bytes = 0;
+    } staging[kStaging];
+    ~ah_server()
+    {
+        for (auto &st : staging)
+            if (st.p)
+                cudaFreeHost(st.p);
+    }
     double now_ms() const
     {
         return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1013,44 +1028,75 @@ namespace {
 // device bytes a request's share of a batch may need (sites and amplicons grow with bases)
 size_t serve_request_bytes(const ServeReq &r) { return 4096 + (size_t)(r.bases / 1000) * 64; }
 
-// One batch: fills every request's result fields.
-// Device results of one primer pair's group of requests.
+// Device results of one group of requests (one primer pair and one k), in
+// pinned host memory.
 struct GroupData {
-    std::vector<ah_site> sites;
-    std::vector<uint8_t> pass;
-    std::vector<ah_amplicon> amps;
+    const ah_site *sites = nullptr;
+    const uint8_t *pass = nullptr;
+    const ah_amplicon *amps = nullptr;
+    uint64_t ns = 0, na = 0;
 };
 
-// Scan of the union of the group's genomes at the largest k among them, then
-// sort, Tm and amplicon calling without a Tm filter; results to the host.
-void group_device(ah_ctx *c, const GenomeSet &gs, uint32_t pid, const std::vector<ServeReq *> &rs, GroupData &d)
+void *staging_at_least(ah_server::Staging &st, size_t bytes)
+{
+    if (st.bytes < bytes) {
+        if (st.p)
+            AH_CUDA(cudaFreeHost(st.p));
+        st.p = nullptr;
+        st.bytes = 0;
+        const size_t want = std::max<size_t>(bytes + bytes / 4, 1 << 20);
+        AH_CUDA(cudaMallocHost(&st.p, want));
+        st.bytes = want;
+    }
+    return st.p;
+}
+
+// Scan of the union of the group's genomes, then sort, Tm and amplicon calling
+// without a Tm filter; results to the host staging buffer.
+// Tiles holding a start of a contig of the union of the requests' genomes:
+// each contig's tile range, ranges sorted and merged, then listed.  Host work
+// only (thread-safe: reads the set's host tables).
+std::vector<uint64_t> group_tiles(const GenomeSet &gs, const ah_server *S, const std::vector<ServeReq *> &rs)
+{
+    std::vector<uint32_t> gen;
+    for (ServeReq *r : rs)
+        gen.insert(gen.end(), r->genomes.begin(), r->genomes.end());
+    std::sort(gen.begin(), gen.end());
+    gen.erase(std::unique(gen.begin(), gen.end()), gen.end());
+    std::vector<std::pair<uint64_t, uint64_t>> ranges; // [first, last] tile of a contig
+    for (uint32_t g : gen) {
+        if (g + 1 >= S->genome_first.size())
+            continue;
+        for (uint64_t q = S->genome_first[g]; q < S->genome_first[g + 1]; ++q) {
+            const uint32_t ci = S->genome_contig[q];
+            const uint64_t a = gs.contig_off_h[ci], b = gs.contig_off_h[ci + 1];
+            if (b > a)
+                ranges.push_back({a / kTileBases, (b - 1) / kTileBases});
+        }
+    }
+    std::sort(ranges.begin(), ranges.end());
+    std::vector<uint64_t> tiles;
+    uint64_t next = 0; // first tile not yet listed
+    for (const auto &rg : ranges) { // sorted by first tile: the list comes out sorted and unique
+        for (uint64_t t = std::max(rg.first, next); t <= rg.second; ++t)
+            tiles.push_back(t);
+        next = std::max(next, rg.second + 1);
+    }
+    return tiles;
+}
+
+// Scan of the group's tiles at the group's k, then sort, Tm and amplicon
+// calling without a Tm filter; results to the host staging buffer.
+void group_device(ah_ctx *c, const GenomeSet &gs, uint32_t pid, int k, const std::vector<uint64_t> &tiles,
+                  ah_server::Staging &stage, GroupData &d)
 {
     cudaStream_t st = c->stream;
-    int kmax = 0;
-    std::vector<char> in_union(gs.max_genome + 1, 0);
-    for (ServeReq *r : rs) {
-        kmax = std::max(kmax, r->k);
-        for (uint32_t g : r->genomes)
-            if (g <= gs.max_genome)
-                in_union[g] = 1;
-    }
-    // tiles holding a start of a union genome's contig
-    std::vector<char> tflag(gs.n_tiles, 0);
-    for (uint32_t ci = 0; ci < gs.n_contigs; ++ci) {
-        const uint64_t a = gs.contig_off_h[ci], b = gs.contig_off_h[ci + 1];
-        if (b > a && in_union[gs.contig_genome_h[ci]])
-            for (uint64_t t = a / kTileBases; t <= (b - 1) / kTileBases; ++t)
-                tflag[t] = 1;
-    }
-    std::vector<uint64_t> tiles;
-    for (uint64_t t = 0; t < gs.n_tiles; ++t)
-        if (tflag[t])
-            tiles.push_back(t);
+    HostSpan span(c, "host.serve.device");
     if (tiles.empty())
         return;
     uint64_t *tl = (uint64_t *)scratch(c, "serve_tiles", tiles.size() * sizeof(uint64_t));
     AH_CUDA(cudaMemcpyAsync(tl, tiles.data(), tiles.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-    std::vector<ScanPattern> pats = patterns_of(c, &pid, 1, kmax);
+    std::vector<ScanPattern> pats = patterns_of(c, &pid, 1, k);
     const PairDev *pd = upload_pairs(c, &pid, 1, st);
     uint64_t *keys = nullptr;
     const uint64_t ns = scan_keys(c, gs, pats, &keys, st, tl, tiles.size());
@@ -1076,115 +1122,142 @@ void group_device(ah_ctx *c, const GenomeSet &gs, uint32_t pid, const std::vecto
         exclusive_scan_u64(temp, tb, counts, offs, ns, st);
         launch_total(offs, counts, ns, nullptr, 0, c->d_aux, 0, nullptr, nullptr, 0, st);
     }
-    d.sites.resize(ns);
-    d.pass.resize(ns);
-    AH_CUDA(cudaMemcpyAsync(d.sites.data(), sites, ns * sizeof(ah_site), cudaMemcpyDeviceToHost, st));
-    AH_CUDA(cudaMemcpyAsync(d.pass.data(), pass, ns, cudaMemcpyDeviceToHost, st));
     check_flags(c, st);
     const uint64_t na = c->h_flags[kFlagAux];
+    ah_amplicon *amps = (ah_amplicon *)scratch(c, "serve_amps", std::max<uint64_t>(na, 1) * sizeof(ah_amplicon));
     if (na) {
-        ah_amplicon *amps = (ah_amplicon *)scratch(c, "serve_amps", na * sizeof(ah_amplicon));
-        {
-            Stage sg(c, "pair", st, 1);
-            launch_pair_write(sites, ns, nullptr, nullptr, pd, offs, amps, na, nullptr, 0, st);
-        }
-        d.amps.resize(na);
-        AH_CUDA(cudaMemcpyAsync(d.amps.data(), amps, na * sizeof(ah_amplicon), cudaMemcpyDeviceToHost, st));
-        check_flags(c, st);
+        Stage sg(c, "pair", st, 1);
+        launch_pair_write(sites, ns, nullptr, nullptr, pd, offs, amps, na, nullptr, 0, st);
     }
+    // staging layout: sites, amplicons, pass flags
+    const size_t sb = ns * sizeof(ah_site), ab = na * sizeof(ah_amplicon);
+    char *h = (char *)staging_at_least(stage, sb + ab + ns);
+    AH_CUDA(cudaMemcpyAsync(h, sites, sb, cudaMemcpyDeviceToHost, st));
+    if (na)
+        AH_CUDA(cudaMemcpyAsync(h + sb, amps, ab, cudaMemcpyDeviceToHost, st));
+    AH_CUDA(cudaMemcpyAsync(h + sb + ab, pass, ns, cudaMemcpyDeviceToHost, st));
+    check_flags(c, st);
+    d.sites = (const ah_site *)h;
+    d.amps = (const ah_amplicon *)(h + sb);
+    d.pass = (const uint8_t *)(h + sb + ab);
+    d.ns = ns;
+    d.na = na;
 }
 
-// Per request: its genomes, its k, its Tm filter.  Sites and amplicons are
-// bucketed by genome once; a request visits only its genomes' buckets.
-// Host work only (runs beside the next group's device work).
+// Per request: the group's sites of its genomes (all have mm <= the group's
+// k), and the amplicons whose two ends are among them (both passing under the
+// Tm filter).  Sites of other genomes are few (they share an edge tile with a
+// requested genome), so the kept sites are copied in runs between the dropped
+// ones and an index is re-mapped by counting the dropped ones below it.  The
+// group's canonical order is kept.  Host work only (runs beside the next
+// group's device work).
 void group_filter(uint64_t G, const GroupData &d, const std::vector<ServeReq *> &rs)
 {
-    std::vector<uint64_t> s_off(G + 1, 0), a_off(G + 1, 0);
-    for (const ah_site &x : d.sites)
-        ++s_off[x.genome + 1];
-    for (const ah_amplicon &x : d.amps)
-        ++a_off[x.genome + 1];
-    for (uint64_t g = 0; g < G; ++g) {
-        s_off[g + 1] += s_off[g];
-        a_off[g + 1] += a_off[g];
-    }
-    std::vector<uint64_t> s_idx(d.sites.size()), a_idx(d.amps.size());
-    {
-        std::vector<uint64_t> fs(s_off.begin(), s_off.end() - 1), fa(a_off.begin(), a_off.end() - 1);
-        for (uint64_t i = 0; i < d.sites.size(); ++i)
-            s_idx[fs[d.sites[i].genome]++] = i;
-        for (uint64_t i = 0; i < d.amps.size(); ++i)
-            a_idx[fa[d.amps[i].genome]++] = i;
-    }
-    std::vector<int64_t> new_index(d.sites.size(), -1);
+    std::vector<char> mine(G, 0);
+    std::vector<uint64_t> dropped;
     for (ServeReq *r : rs) {
-        std::vector<uint64_t> mine;
         for (uint32_t g : r->genomes)
             if (g < G)
-                for (uint64_t q = s_off[g]; q < s_off[g + 1]; ++q)
-                    if (d.sites[s_idx[q]].mm <= r->k)
-                        mine.push_back(s_idx[q]);
-        std::sort(mine.begin(), mine.end()); // canonical order is the group's order
-        r->sites.resize(mine.size());
-        for (size_t j = 0; j < mine.size(); ++j) {
-            new_index[mine[j]] = (int64_t)j;
-            r->sites[j] = d.sites[mine[j]];
+                mine[g] = 1;
+        dropped.clear();
+        for (uint64_t i = 0; i < d.ns; ++i)
+            if (!mine[d.sites[i].genome])
+                dropped.push_back(i);
+        r->sites.clear();
+        r->sites.reserve(d.ns - dropped.size());
+        uint64_t from = 0;
+        for (size_t j = 0; j <= dropped.size(); ++j) {
+            const uint64_t end = j < dropped.size() ? dropped[j] : d.ns;
+            if (end > from)
+                r->sites.insert(r->sites.end(), d.sites + from, d.sites + end);
+            from = end + 1;
         }
-        r->n_sites = mine.size();
-        std::vector<uint64_t> ka;
+        r->n_sites = r->sites.size();
+        auto remap = [&](uint64_t i) -> int64_t { // -1: dropped
+            const auto it = std::lower_bound(dropped.begin(), dropped.end(), i);
+            if (it != dropped.end() && *it == i)
+                return -1;
+            return (int64_t)(i - (uint64_t)(it - dropped.begin()));
+        };
+        r->amps.clear();
+        for (uint64_t i = 0; i < d.na; ++i) {
+            const ah_amplicon &x = d.amps[i];
+            if (!mine[x.genome])
+                continue;
+            if (r->tm_filter && !(d.pass[x.left] && d.pass[x.right]))
+                continue;
+            const int64_t l = remap(x.left), rr = remap(x.right);
+            if (l < 0 || rr < 0)
+                continue;
+            ah_amplicon b = x;
+            b.left = (uint32_t)l; // indices into the request's own site list
+            b.right = (uint32_t)rr;
+            r->amps.push_back(b);
+        }
         for (uint32_t g : r->genomes)
             if (g < G)
-                for (uint64_t q = a_off[g]; q < a_off[g + 1]; ++q) {
-                    const ah_amplicon &x = d.amps[a_idx[q]];
-                    if (new_index[x.left] < 0 || new_index[x.right] < 0)
-                        continue;
-                    if (r->tm_filter && !(d.pass[x.left] && d.pass[x.right]))
-                        continue;
-                    ka.push_back(a_idx[q]);
-                }
-        std::sort(ka.begin(), ka.end());
-        r->amps.resize(ka.size());
-        for (size_t j = 0; j < ka.size(); ++j) {
-            ah_amplicon b = d.amps[ka[j]];
-            b.left = (uint32_t)new_index[b.left]; // indices into the request's own site list
-            b.right = (uint32_t)new_index[b.right];
-            r->amps[j] = b;
-        }
-        for (uint64_t i : mine)
-            new_index[i] = -1;
+                mine[g] = 0;
     }
 }
 
-// One batch: fills every request's result fields.  Pair groups run one after
-// another on the device; each group's host filtering overlaps the next
-// group's device work; one fetch at the end decodes every distinct amplicon
-// some request keeps.
+// One batch: fills every request's result fields.  Requests are grouped by
+// (primer pair, k); groups run one after another on the device, each group's
+// host filtering overlaps the next group's device work, and one fetch at the
+// end decodes every distinct amplicon some request keeps.
 void serve_batch(ah_server *S, std::vector<ServeReq *> &batch)
 {
     ah_ctx *c = S->c;
     GenomeSet &gs = get_set(c, S->set_id);
     cudaStream_t st = c->stream;
-    std::map<uint32_t, std::vector<ServeReq *>> groups;
+    std::map<std::pair<uint32_t, int>, std::vector<ServeReq *>> groups;
     for (ServeReq *r : batch)
-        groups[r->pair_id].push_back(r);
+        groups[{r->pair_id, r->k}].push_back(r);
     const uint64_t G = (uint64_t)gs.max_genome + 1;
     std::deque<GroupData> data;
     std::vector<std::future<void>> filters;
+    // every group's tile list is built on the host cores while the device works
+    std::vector<std::future<std::vector<uint64_t>>> plans;
+    for (auto &kv : groups) {
+        const std::vector<ServeReq *> *rs = &kv.second;
+        const GenomeSet *g = &gs;
+        plans.push_back(std::async(std::launch::async, [g, S, rs] { return group_tiles(*g, S, *rs); }));
+    }
     try {
+        size_t gi = 0;
         for (auto &kv : groups) {
+            if (gi >= ah_server::kStaging) { // the staging buffer is reused: its earlier group is filtered first
+                HostSpan hs(c, "host.serve.filter_wait");
+                filters[gi - ah_server::kStaging].get();
+            }
             data.emplace_back();
-            group_device(c, gs, kv.first, kv.second, data.back());
+            std::vector<uint64_t> tiles;
+            {
+                HostSpan hs(c, "host.serve.tiles");
+                tiles = plans[gi].get();
+            }
+            group_device(c, gs, kv.first.first, kv.first.second, tiles, S->staging[gi % ah_server::kStaging],
+                         data.back());
             const GroupData *d = &data.back();
             const std::vector<ServeReq *> *rs = &kv.second;
             filters.push_back(std::async(std::launch::async, [G, d, rs] { group_filter(G, *d, *rs); }));
+            ++gi;
         }
     } catch (...) {
         for (auto &f : filters)
-            f.wait();
+            if (f.valid())
+                f.wait();
+        for (auto &f : plans)
+            if (f.valid())
+                f.wait();
         throw;
     }
-    for (auto &f : filters)
-        f.get();
+    {
+        HostSpan hs(c, "host.serve.filter_wait");
+        for (auto &f : filters)
+            if (f.valid())
+                f.get();
+    }
+    HostSpan hs_fetch(c, "host.serve.fetch");
     // distinct amplicons of the batch (a sequence depends on contig, start, end, orient)
     struct Ref {
         uint64_t k0, k1;
@@ -1210,7 +1283,8 @@ void serve_batch(ah_server *S, std::vector<ServeReq *> &batch)
     std::vector<uint64_t> f_off(nf + 1, 0);
     for (uint64_t j = 0; j < nf; ++j)
         f_off[j + 1] = f_off[j] + (recs[j].end - recs[j].start);
-    std::vector<char> seq_h(f_off.back());
+    // sequences through the first staging buffer (every filter is done with it)
+    char *seq_h = (char *)staging_at_least(S->staging[0], std::max<uint64_t>(f_off.back(), 1));
     if (nf) {
         ah_amplicon *ra = (ah_amplicon *)scratch(c, "serve_fetch_amps", nf * sizeof(ah_amplicon));
         uint64_t *ro = (uint64_t *)scratch(c, "serve_fetch_offs", (nf + 1) * sizeof(uint64_t));
@@ -1222,7 +1296,7 @@ void serve_batch(ah_server *S, std::vector<ServeReq *> &batch)
             launch_fetch(ra, nf, nullptr, ro, gs.planes, gs.contig_off, rq, nullptr, 0, st);
         }
         if (f_off.back())
-            AH_CUDA(cudaMemcpyAsync(seq_h.data(), rq, f_off.back(), cudaMemcpyDeviceToHost, st));
+            AH_CUDA(cudaMemcpyAsync(seq_h, rq, f_off.back(), cudaMemcpyDeviceToHost, st));
         check_flags(c, st);
     }
     // per request, sequences in the order of its amplicons
@@ -1235,7 +1309,7 @@ void serve_batch(ah_server *S, std::vector<ServeReq *> &batch)
         r->seq_off.assign(1, 0);
         r->seq.clear();
         for (uint64_t j : per[r]) {
-            r->seq.insert(r->seq.end(), seq_h.begin() + f_off[j], seq_h.begin() + f_off[j + 1]);
+            r->seq.insert(r->seq.end(), seq_h + f_off[j], seq_h + f_off[j + 1]);
             r->seq_off.push_back(r->seq.size());
         }
     }
@@ -1274,6 +1348,7 @@ void serve_loop(ah_server *S)
         ah_status status = AH_OK;
         std::string msg;
         try {
+            HostSpan hs(S->c, "host.serve.batch");
             serve_batch(S, ptrs);
         } catch (const Error &e) {
             status = e.status;
@@ -2307,9 +2382,21 @@ ah_status ah_serve_start(ah_ctx *c, uint32_t set_id, const ah_serve_config *cfg,
         S->c = c;
         S->set_id = set_id;
         S->cfg = *cfg;
-        S->genome_bases.assign((size_t)gs.max_genome + 1, 0);
-        for (uint32_t ci = 0; ci < gs.n_contigs; ++ci)
+        const size_t G = (size_t)gs.max_genome + 1;
+        S->genome_bases.assign(G, 0);
+        S->genome_first.assign(G + 1, 0);
+        for (uint32_t ci = 0; ci < gs.n_contigs; ++ci) {
             S->genome_bases[gs.contig_genome_h[ci]] += gs.contig_off_h[ci + 1] - gs.contig_off_h[ci];
+            ++S->genome_first[gs.contig_genome_h[ci] + 1];
+        }
+        for (size_t g = 0; g < G; ++g)
+            S->genome_first[g + 1] += S->genome_first[g];
+        S->genome_contig.resize(gs.n_contigs);
+        {
+            std::vector<uint64_t> fill(S->genome_first.begin(), S->genome_first.end() - 1);
+            for (uint32_t ci = 0; ci < gs.n_contigs; ++ci)
+                S->genome_contig[fill[gs.contig_genome_h[ci]]++] = ci;
+        }
         c->serving = true;
         S->worker = std::thread(serve_loop, S.get());
         *out = S.release();
@@ -2352,32 +2439,37 @@ ah_status ah_serve_wait(ah_server *S, uint64_t ticket, ah_request_info *info, ah
 {
     if (!S || !info)
         return AH_ERR_ARG;
-    std::unique_lock<std::mutex> lk(S->mu);
-    auto it = S->reqs.find(ticket);
-    if (it == S->reqs.end())
-        return AH_ERR_ARG;
-    S->cv_done.wait(lk, [&] { return it->second.done; });
-    ServeReq &r = it->second;
-    info->status = r.status;
-    info->batch = r.batch;
-    info->batch_size = r.batch_size;
-    info->reserved = 0;
-    info->n_sites = r.sites.size();
-    info->n_amplicons = r.amps.size();
-    info->n_seq = r.seq.size();
-    info->bases = r.bases;
-    info->submit_ms = r.t_submit;
-    info->start_ms = r.t_start;
-    info->done_ms = r.t_done;
-    if (r.status != AH_OK) {
-        const ah_status st = r.status;
+    ServeReq r;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(ticket);
+        if (it == S->reqs.end())
+            return AH_ERR_ARG;
+        S->cv_done.wait(lk, [&] { return it->second.done; });
+        const ServeReq &q = it->second;
+        info->status = q.status;
+        info->batch = q.batch;
+        info->batch_size = q.batch_size;
+        info->reserved = 0;
+        info->n_sites = q.sites.size();
+        info->n_amplicons = q.amps.size();
+        info->n_seq = q.seq.size();
+        info->bases = q.bases;
+        info->submit_ms = q.t_submit;
+        info->start_ms = q.t_start;
+        info->done_ms = q.t_done;
+        if (q.status == AH_OK) {
+            if (q.sites.size() > sites_cap || q.amps.size() > amps_cap || (seq_offsets_out && q.seq.size() > seq_cap))
+                return AH_ERR_OVERFLOW; // kept: ask again with room
+            if ((!q.sites.empty() && !sites_out) || (!q.amps.empty() && !amps_out) ||
+                (seq_offsets_out && !q.seq.empty() && !seq_out))
+                return AH_ERR_ARG;
+        }
+        r = std::move(it->second); // released: the copies below run without the lock
         S->reqs.erase(it);
-        return st;
     }
-    if (r.sites.size() > sites_cap || r.amps.size() > amps_cap || (seq_offsets_out && r.seq.size() > seq_cap))
-        return AH_ERR_OVERFLOW; // kept: ask again with room
-    if ((!r.sites.empty() && !sites_out) || (!r.amps.empty() && !amps_out) || (seq_offsets_out && !r.seq.empty() && !seq_out))
-        return AH_ERR_ARG;
+    if (r.status != AH_OK)
+        return r.status;
     if (!r.sites.empty())
         memcpy(sites_out, r.sites.data(), r.sites.size() * sizeof(ah_site));
     if (!r.amps.empty())
@@ -2387,7 +2479,6 @@ ah_status ah_serve_wait(ah_server *S, uint64_t ticket, ah_request_info *info, ah
         if (!r.seq.empty())
             memcpy(seq_out, r.seq.data(), r.seq.size());
     }
-    S->reqs.erase(it);
     return AH_OK;
 }
 
