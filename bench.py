@@ -619,6 +619,17 @@ def bench_batched(args):
             sid = nxt
         totals.update(sites=n_s, amplicons=n_a, seq=n_q, d2h_bytes=d2h)
 
+    # the host link alone: every chunk's pinned host -> device copy, back to back
+    h2d_chunk = []
+    for i, (b0, b1, _, _) in enumerate(tabs):
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(cs)
+        with torch.cuda.stream(cs):
+            dbuf[i % 2][:b1 - b0].copy_(host[b0:b1], non_blocking=True)
+        h1.record(cs)
+        torch.cuda.synchronize()
+        h2d_chunk.append((b1 - b0) / (h0.elapsed_time(h1) / 1e3) / 1e9)
+    h2d_gbs = N / sum((b1 - b0) / (g * 1e9) for (b0, b1, _, _), g in zip(tabs, h2d_chunk)) / 1e9
     copy(0)
     sid0 = load(0)
     tune = None if args.no_tune else ctx.ah_tune_scan(sid0, pids, 0, st[0])
@@ -690,6 +701,8 @@ def bench_batched(args):
                    "set i's run and set i+1's packing", "outputs": "pinned host (sites, Tm, pass, amplicons, "
                    "sequences)", "scan_tuning": tune, "layout_s": t_layout},
         "results_per_pass": totals, "gpu_launches_per_pass": launches / max(1, args.steps),
+        "h2d_gbs": h2d_gbs, "h2d_gbs_per_chunk": [round(g, 1) for g in h2d_chunk],
+        "h2d_bound_s_per_pass": N / h2d_gbs / 1e9,
         "plain": {"value": gbps_plain, "unit": "Gbp/s", "genomes": len(sample), "bases": int(nb),
                   "form": "one genome per ah_load_genomes (host input), one ah_run per pair (host outputs)",
                   "s": t_plain},

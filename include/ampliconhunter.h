@@ -425,7 +425,7 @@ ah_status ah_generate_bases(ah_ctx *ctx, uint64_t seed, const ah_gen_segment *se
  * host sections, enable = 2 times host sections only, enable = 3 brackets
  * only the "pack" and "scan" stages (the streaming kernels; fewer events in
  * the stream) and times host sections, 0 stops.  Device
- * stages: "pack" (ah_load_genomes), "scan", "sort", "decode" (ah_scan),
+ * stages: "pack", "tables" (ah_load_genomes), "scan", "sort", "decode" (ah_scan),
  * "validate" (record checks of ah_tm / ah_pair), "tm", "pair", "fetch",
  * "sweep" (ah_tm_sweep), "amplitype" (ah_amplitypes).  Host
  * sections (wall time inside the library): "host.load", "host.load.alloc",

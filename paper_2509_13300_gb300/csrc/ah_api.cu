@@ -45,9 +45,18 @@ struct ah_ctx {
     uint64_t *h_flags = nullptr;     // pinned host mirror of the flag block
     bool flags_dirty = false;        // work was queued that may set the error word, not read since
     std::vector<cudaEvent_t> set_events; // free "ready" events of genome sets
-    uint8_t *pin = nullptr;          // pinned staging of small host->device copies (contig tables)
-    size_t pin_bytes = 0;
-    cudaEvent_t pin_ev = nullptr;    // recorded after the last copy out of pin
+    // mapped pinned staging of the contig tables, read on the device by a copy
+    // kernel (a copy-engine transfer would queue behind large host->device
+    // copies of the caller's); a ring of slots, so that a load waits only for
+    // the reads of the load four before it
+    static constexpr int kPinSlots = 4;
+    struct PinSlot {
+        uint8_t *p = nullptr;  // host address
+        uint8_t *dp = nullptr; // device address of the same memory
+        size_t bytes = 0;
+        cudaEvent_t ev = nullptr; // recorded after the reads out of the slot
+    } pin[kPinSlots];
+    int pin_next = 0;
     std::vector<PairDev> pairdev_h;  // host source of the last per-pair upload
     std::vector<uint32_t> pairdev_ids; // pair ids of that upload
     uint64_t pairdev_version = 0;      // pairs_version at that upload
@@ -1438,7 +1447,8 @@ ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
         }
         AH_CUDA(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
         AH_CUDA(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
-        AH_CUDA(cudaEventCreateWithFlags(&c->pin_ev, cudaEventDisableTiming));
+        for (auto &sl : c->pin)
+            AH_CUDA(cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming));
         AH_CUDA(cudaEventCreateWithFlags(&c->ev_run, cudaEventDisableTiming));
         for (int b = 0; b < 2; ++b) {
             AH_CUDA(cudaEventCreateWithFlags(&c->ev_copied[b], cudaEventDisableTiming));
@@ -1473,10 +1483,14 @@ void ah_destroy(ah_ctx *c)
         cudaEventDestroy(e);
     if (c->h_flags)
         cudaFreeHost(c->h_flags);
-    if (c->pin)
-        cudaFreeHost(c->pin);
-    if (c->pin_ev)
-        cudaEventDestroy(c->pin_ev);
+    for (auto &sl : c->pin) {
+        if (sl.ev)
+            cudaEventSynchronize(sl.ev);
+        if (sl.p)
+            cudaFreeHost(sl.p);
+        if (sl.ev)
+            cudaEventDestroy(sl.ev);
+    }
     if (c->ev_run)
         cudaEventDestroy(c->ev_run);
     for (auto &kv : c->sets)
@@ -1655,8 +1669,8 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
             RevChunk *ch_d = (RevChunk *)dev_alloc(c, std::max<size_t>(ch.size(), 1) * sizeof(RevChunk));
             temp.push_back(ch_d);
             AH_CUDA(cudaMemcpyAsync(ch_d, ch.data(), ch.size() * sizeof(RevChunk), cudaMemcpyHostToDevice, st));
+            Stage sg(c, "pack", st, 2);
             launch_reverse_contigs(src, dst, ch_d, ch.size(), st);
-            Stage sg(c, "pack", st, 1);
             launch_pack(dst, 0, n_bases, n_bases, gs->planes, 0, gs->n_tiles, c->d_err, st);
         } else if (gs->n_tiles) {
             HostSpan hs_pack(c, "host.load.pack");
@@ -1701,21 +1715,26 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
             // contig tables through pinned staging: asynchronous copies (a pageable
             // source would make the driver stage and wait)
             const size_t ob = (n_contigs + 1) * sizeof(uint64_t), gb = n_contigs * sizeof(uint32_t);
-            AH_CUDA(cudaEventSynchronize(c->pin_ev)); // the last copies out of the staging buffer are done
-            if (c->pin_bytes < ob + gb) {
-                if (c->pin)
-                    AH_CUDA(cudaFreeHost(c->pin));
-                c->pin = nullptr;
-                c->pin_bytes = 0;
+            ah_ctx::PinSlot &sl = c->pin[c->pin_next];
+            c->pin_next = (c->pin_next + 1) % ah_ctx::kPinSlots;
+            AH_CUDA(cudaEventSynchronize(sl.ev)); // the slot's earlier reads are done
+            if (sl.bytes < ob + gb) {
+                if (sl.p)
+                    AH_CUDA(cudaFreeHost(sl.p));
+                sl.p = sl.dp = nullptr;
+                sl.bytes = 0;
                 const size_t want = std::max<size_t>(ob + gb + (ob + gb) / 4, 1 << 16);
-                AH_CUDA(cudaMallocHost(&c->pin, want));
-                c->pin_bytes = want;
+                AH_CUDA(cudaHostAlloc((void **)&sl.p, want, cudaHostAllocMapped));
+                sl.bytes = want;
+                AH_CUDA(cudaHostGetDevicePointer((void **)&sl.dp, sl.p, 0));
             }
-            memcpy(c->pin, contig_off, ob);
-            memcpy(c->pin + ob, contig_genome, gb);
-            AH_CUDA(cudaMemcpyAsync(gs->contig_off, c->pin, ob, cudaMemcpyHostToDevice, st));
-            AH_CUDA(cudaMemcpyAsync(gs->contig_genome, c->pin + ob, gb, cudaMemcpyHostToDevice, st));
-            AH_CUDA(cudaEventRecord(c->pin_ev, st));
+            memcpy(sl.p, contig_off, ob);
+            memcpy(sl.p + ob, contig_genome, gb);
+            Stage sg(c, "tables", st, gs->n_tiles ? 3 : 2);
+            // ob and gb are multiples of 4 bytes; the slot and the tables are aligned
+            launch_copy_words((const uint32_t *)sl.dp, (uint32_t *)gs->contig_off, ob / 4, st);
+            launch_copy_words((const uint32_t *)(sl.dp + ob), gs->contig_genome, gb / 4, st);
+            AH_CUDA(cudaEventRecord(sl.ev, st));
             if (gs->n_tiles)
                 launch_tile_contigs(gs->contig_off, n_contigs, gs->n_tiles, gs->tile_contig, st);
         }

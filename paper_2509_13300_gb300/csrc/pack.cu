@@ -274,6 +274,23 @@ __global__ void tile_contigs_kernel(const uint64_t *__restrict__ contig_off, uin
 }
 } // namespace
 
+namespace {
+__global__ void copy_words_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, uint64_t n)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+} // namespace
+
+void launch_copy_words(const uint32_t *src, uint32_t *dst, uint64_t n_words, cudaStream_t s)
+{
+    if (!n_words)
+        return;
+    const uint64_t blocks = std::min<uint64_t>((n_words + 255) / 256, 1024);
+    copy_words_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, dst, n_words);
+    AH_CUDA(cudaGetLastError());
+}
+
 void launch_tile_contigs(const uint64_t *contig_off, uint32_t n_contigs, uint64_t n_tiles, uint32_t *out,
                          cudaStream_t s)
 {
