@@ -1626,20 +1626,22 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
         }
         const size_t plane_bytes = gs->n_tiles * kTileBytes;
         HostSpan hs_alloc(c, "host.load.alloc");
+        // the three tables in one block (one copy fills them): contig offsets,
+        // genome ids, per-tile contigs
+        const size_t ob = (n_contigs + 1) * sizeof(uint64_t), gb = n_contigs * sizeof(uint32_t),
+                     tb = (gs->n_tiles + 1) * sizeof(uint32_t);
+        const size_t table_bytes = ob + gb + tb; // a multiple of 4; ob keeps the rest 4-byte aligned
         try {
             gs->planes = (uint32_t *)dev_alloc(c, plane_bytes);
-            gs->contig_off = (uint64_t *)dev_alloc(c, (n_contigs + 1) * sizeof(uint64_t));
-            gs->contig_genome = (uint32_t *)dev_alloc(c, n_contigs * sizeof(uint32_t));
-            gs->tile_contig = (uint32_t *)dev_alloc(c, (gs->n_tiles + 1) * sizeof(uint32_t));
+            gs->contig_off = (uint64_t *)dev_alloc(c, table_bytes);
         } catch (...) {
             dev_free(c, gs->planes, plane_bytes);
-            dev_free(c, gs->contig_off, (n_contigs + 1) * sizeof(uint64_t));
-            dev_free(c, gs->contig_genome, n_contigs * sizeof(uint32_t));
-            dev_free(c, gs->tile_contig, (gs->n_tiles + 1) * sizeof(uint32_t));
+            dev_free(c, gs->contig_off, table_bytes);
             throw;
         }
-        gs->bytes = plane_bytes + (n_contigs + 1) * sizeof(uint64_t) + n_contigs * sizeof(uint32_t) +
-                    (gs->n_tiles + 1) * sizeof(uint32_t);
+        gs->contig_genome = (uint32_t *)((char *)gs->contig_off + ob);
+        gs->tile_contig = (uint32_t *)((char *)gs->contig_off + ob + gb);
+        gs->bytes = plane_bytes + table_bytes;
         const bool dev_seq = n_bases && is_device_ptr(c, seq);
         // a queued run leaves the flag block and the staging scratch alone only for device input
         require((dev_seq && !reversed) || !c->pend.active, AH_ERR_ARG,
@@ -1712,31 +1714,37 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
         }
         {
             HostSpan hs_tables(c, "host.load.tables");
-            // contig tables through pinned staging: asynchronous copies (a pageable
-            // source would make the driver stage and wait)
-            const size_t ob = (n_contigs + 1) * sizeof(uint64_t), gb = n_contigs * sizeof(uint32_t);
+            // the tables through a mapped pinned slot, read by one copy kernel; the
+            // per-tile contig table is built here by a merge walk over tiles and contigs
             ah_ctx::PinSlot &sl = c->pin[c->pin_next];
             c->pin_next = (c->pin_next + 1) % ah_ctx::kPinSlots;
             AH_CUDA(cudaEventSynchronize(sl.ev)); // the slot's earlier reads are done
-            if (sl.bytes < ob + gb) {
+            if (sl.bytes < table_bytes) {
                 if (sl.p)
                     AH_CUDA(cudaFreeHost(sl.p));
                 sl.p = sl.dp = nullptr;
                 sl.bytes = 0;
-                const size_t want = std::max<size_t>(ob + gb + (ob + gb) / 4, 1 << 16);
+                const size_t want = std::max<size_t>(table_bytes + table_bytes / 4, 1 << 16);
                 AH_CUDA(cudaHostAlloc((void **)&sl.p, want, cudaHostAllocMapped));
                 sl.bytes = want;
                 AH_CUDA(cudaHostGetDevicePointer((void **)&sl.dp, sl.p, 0));
             }
             memcpy(sl.p, contig_off, ob);
             memcpy(sl.p + ob, contig_genome, gb);
-            Stage sg(c, "tables", st, gs->n_tiles ? 3 : 2);
-            // ob and gb are multiples of 4 bytes; the slot and the tables are aligned
-            launch_copy_words((const uint32_t *)sl.dp, (uint32_t *)gs->contig_off, ob / 4, st);
-            launch_copy_words((const uint32_t *)(sl.dp + ob), gs->contig_genome, gb / 4, st);
+            {
+                // tile t: the last contig starting at or before t * kTileBases
+                uint32_t *tc = (uint32_t *)(sl.p + ob + gb);
+                uint32_t ci = 0;
+                for (uint64_t t = 0; t <= gs->n_tiles; ++t) {
+                    const uint64_t P = t * kTileBases;
+                    while (ci + 1 < n_contigs && contig_off[ci + 1] <= P)
+                        ++ci;
+                    tc[t] = ci;
+                }
+            }
+            Stage sg(c, "tables", st, 1);
+            launch_copy_words((const uint32_t *)sl.dp, (uint32_t *)gs->contig_off, table_bytes / 4, st);
             AH_CUDA(cudaEventRecord(sl.ev, st));
-            if (gs->n_tiles)
-                launch_tile_contigs(gs->contig_off, n_contigs, gs->n_tiles, gs->tile_contig, st);
         }
         if (c->set_events.empty()) {
             cudaEvent_t e;
@@ -1779,9 +1787,7 @@ ah_status ah_unload_genomes(ah_ctx *c, uint32_t set_id)
         // a failure of a packing nothing else synchronised on is reported here
         const int e = c->flags_dirty ? read_flags(c, c->stream) : 0;
         dev_free(c, gs.planes, gs.n_tiles * kTileBytes);
-        dev_free(c, gs.contig_off, (gs.n_contigs + 1) * sizeof(uint64_t));
-        dev_free(c, gs.contig_genome, gs.n_contigs * sizeof(uint32_t));
-        dev_free(c, gs.tile_contig, (gs.n_tiles + 1) * sizeof(uint32_t));
+        dev_free(c, gs.contig_off, 0); // the block of the three tables
         if (gs.ready)
             c->set_events.push_back(gs.ready);
         c->sets.erase(set_id);

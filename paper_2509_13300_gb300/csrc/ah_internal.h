@@ -141,9 +141,6 @@ void launch_pack(const uint8_t *seq, uint64_t seq_base, uint64_t seq_len, uint64
                  uint64_t t0, uint64_t t1, int *err, cudaStream_t s);
 // pack.cu: word copy by a kernel (src may be mapped host memory: no copy engine involved)
 void launch_copy_words(const uint32_t *src, uint32_t *dst, uint64_t n_words, cudaStream_t s);
-// pack.cu: the per-tile contig table of a set (n_tiles + 1 entries)
-void launch_tile_contigs(const uint64_t *contig_off, uint32_t n_contigs, uint64_t n_tiles, uint32_t *out,
-                         cudaStream_t s);
 // One stretch of a contig-wise reversal: dst[k] = src[mirror - k] for k in
 // [start, start + len) (mirror = 2 * contig start + contig length - 1).
 struct RevChunk {

@@ -253,26 +253,6 @@ __global__ void unpack_kernel(const uint32_t *__restrict__ planes, uint8_t *__re
 
 } // namespace
 
-namespace {
-// tile_contig[t] = largest c < n_contigs with contig_off[c] <= t * kTileBases
-__global__ void tile_contigs_kernel(const uint64_t *__restrict__ contig_off, uint32_t n_contigs, uint64_t n_tiles,
-                                    uint32_t *__restrict__ out)
-{
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= n_tiles;
-         t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t P = t * kTileBases;
-        uint32_t lo = 0, hi = n_contigs;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (contig_off[mid] <= P)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        out[t] = lo;
-    }
-}
-} // namespace
 
 namespace {
 __global__ void copy_words_kernel(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, uint64_t n)
@@ -288,14 +268,6 @@ void launch_copy_words(const uint32_t *src, uint32_t *dst, uint64_t n_words, cud
         return;
     const uint64_t blocks = std::min<uint64_t>((n_words + 255) / 256, 1024);
     copy_words_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, dst, n_words);
-    AH_CUDA(cudaGetLastError());
-}
-
-void launch_tile_contigs(const uint64_t *contig_off, uint32_t n_contigs, uint64_t n_tiles, uint32_t *out,
-                         cudaStream_t s)
-{
-    const uint64_t blocks = std::min<uint64_t>((n_tiles + 256) / 256, 4096);
-    tile_contigs_kernel<<<(unsigned)blocks, 256, 0, s>>>(contig_off, n_contigs, n_tiles, out);
     AH_CUDA(cudaGetLastError());
 }
 
@@ -324,9 +296,17 @@ void launch_pack(const uint8_t *seq, uint64_t seq_base, uint64_t seq_len, uint64
     uint64_t blocks = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
     if (blocks > t1 - t0)
         blocks = t1 - t0;
+    // A block that packs one tile uses one staging buffer, but it reserves two:
+    // three blocks per SM leave shared memory for a run's kernels beside the
+    // packing (measured: 6 blocks per SM pack faster alone, 128 vs 138 us for
+    // 0.4 Gbp, but the pipelined step is slower, 316 vs 306 us).
+    // AH_PACK_SMEM_KB sets the reservation (profiling aid; at least one buffer).
+    size_t smem_launch = smem;
+    if (const char *e = getenv("AH_PACK_SMEM_KB"))
+        smem_launch = std::min(smem, std::max(blocks >= t1 - t0 ? smem / 2 : smem, (size_t)atoi(e) * 1024));
     const int tma_ok = ((reinterpret_cast<uintptr_t>(seq) - seq_base) % 16 == 0) ? 1 : 0;
-    pack_kernel<<<(unsigned)blocks, kPackThreads, smem, s>>>(seq, seq_base, seq_len, n_bases, planes, t0, t1, tma_ok,
-                                                             1u, err);
+    pack_kernel<<<(unsigned)blocks, kPackThreads, smem_launch, s>>>(seq, seq_base, seq_len, n_bases, planes, t0, t1,
+                                                                    tma_ok, 1u, err);
     AH_CUDA(cudaGetLastError());
 }
 
