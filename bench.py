@@ -171,7 +171,7 @@ def cpu_baseline(w, target_s: float = 15.0):
     oracle.fetch(seq, off, a)
     dt = time.perf_counter() - t0
     return {"value": nb / dt / 1e9, "unit": "Gbp/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {g} of 100 genomes ({nb / 1e6:.1f} Mbp, {nc} contigs), scan+Tm+pair+fetch, "
+            "sample": f"first {g} of {len(goff) - 1} genomes ({nb / 1e6:.1f} Mbp, {nc} contigs), scan+Tm+pair+fetch, "
                       f"{dt:.1f} s"}
 
 
@@ -183,7 +183,7 @@ def run_reference(args):
         if rank != 0:
             dist.barrier()
             return
-    w = workload(1)
+    w = workload(1, args.n_genomes)
     steps = []
     for i in range(args.warmup + args.steps):
         r = cpu_baseline(w, target_s=args.ref_seconds)
