@@ -23,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "hmm.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -54,12 +55,12 @@ class NNTable(ctypes.Structure):
 def build(force: bool = False) -> str:
     """Compile oracle.c into _build/liboracle.so (gcc, -O2, OpenMP)."""
     with _lock:
-        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        if not force and os.path.exists(_LIB) and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS):
             return _LIB
         os.makedirs(_BUILD, exist_ok=True)
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp] + _SRCS + ["-lm"])
         os.replace(tmp, _LIB)
         return _LIB
 
@@ -85,6 +86,12 @@ def _load():
         lib.or_default_table.argtypes = [P]
         lib.or_degeneracy.restype = I64
         lib.or_degeneracy.argtypes = [ctypes.c_char_p]
+        lib.or_edit_distance.restype = I64
+        lib.or_edit_distance.argtypes = [ctypes.c_char_p, I64, ctypes.c_char_p, I64]
+        lib.or_hmm_build.restype = I64
+        lib.or_hmm_build.argtypes = [P, P, I64, P, P, P]
+        lib.or_hmm_viterbi.restype = ctypes.c_double
+        lib.or_hmm_viterbi.argtypes = [P, P, I64, ctypes.c_char_p, I64]
         _lib = lib
     return _lib
 
@@ -216,3 +223,35 @@ def default_table() -> NNTable:
 
 def degeneracy(primer: str) -> int:
     return int(_load().or_degeneracy(primer.encode()))
+
+
+# ---------------------------------------------------------------- profile HMM (hmm.c)
+def edit_distance(s: str, r: str) -> int:
+    """Unit-cost global alignment distance (0 only for equal A/C/G/T letters)."""
+    return int(_load().or_edit_distance(s.encode(), len(s), r.encode(), len(r)))
+
+
+def hmm_build(seqs):
+    """Profile from training sequences (list of str): (reference index, t, e) with
+    t[j, X, Y] the transition scores (X, Y in M, I, D; Y = M is the next move, E
+    at j = m) and e[j, x] the match emission scores (j = 1..m), in bits."""
+    lib = _load()
+    data = "".join(seqs).encode()
+    off = np.zeros(len(seqs) + 1, dtype=np.uint64)
+    off[1:] = np.cumsum([len(x) for x in seqs])
+    buf = np.frombuffer(data, dtype=np.uint8).copy() if data else np.zeros(1, np.uint8)
+    m = ctypes.c_int64()
+    ref = lib.or_hmm_build(_ptr(buf), _ptr(off), len(seqs), ctypes.byref(m), None, None)
+    if ref < 0:
+        raise ValueError("no training sequence")
+    t = np.zeros((m.value + 1, 3, 3), dtype=np.float64)
+    e = np.zeros((m.value + 1, 4), dtype=np.float64)
+    lib.or_hmm_build(_ptr(buf), _ptr(off), len(seqs), ctypes.byref(m), _ptr(t), _ptr(e))
+    return int(ref), t, e
+
+
+def hmm_viterbi(t: np.ndarray, e: np.ndarray, seq: str) -> float:
+    """Glocal Viterbi log-odds score (bits) of seq against the profile (t, e)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    return float(_load().or_hmm_viterbi(_ptr(t), _ptr(e), t.shape[0] - 1, seq.encode(), len(seq)))
