@@ -523,6 +523,39 @@ ah_status ah_serve_wait(ah_server *srv, uint64_t ticket, ah_request_info *info, 
                         uint64_t *seq_offsets_out);
 ah_status ah_serve_stop(ah_server *srv);
 
+/* Profile-HMM homology scores (Sec. 2.1, Amplicon analysis, item 2: a profile
+ * HMM trained on amplicons whose primers match exactly scores every predicted
+ * amplicon).  The paper names no aligner, topology or score; this library
+ * takes the following reading.  Profile: the most frequent training sequence
+ * is the reference (the first on ties), m = its length (1..3071); each
+ * training sequence is aligned to it globally with unit costs (0 for equal
+ * A/C/G/T letters, 1 for any other pair and per gap), the traceback
+ * preferring a diagonal step, then an insertion, then a deletion; the
+ * alignments' state paths (begin B = M_0, match M_j, insert I_j after column
+ * j, delete D_j, end E) give move counts from each state to the next
+ * column's M (E after column m), to I_j and to the next column's D, and
+ * letter counts per match column; probabilities are counts + 1 over the
+ * allowed moves and over A/C/G/T; insert states emit the background.  Score:
+ * the glocal Viterbi log-odds score (bits, uniform background; unknown
+ * letters score 0) of an amplicon's sequence as ah_fetch returns it (RF
+ * reverse-complemented), fp32.
+ * ah_hmm_build: training sequences (host, concatenated; offsets host, n + 1,
+ *   from 0) -> a profile id; the profile lives on the device until
+ *   ah_hmm_free or ah_destroy.  Errors: AH_ERR_ARG, AH_ERR_OOM.
+ * ah_hmm_tables: m, the reference's index, and (when not NULL) the move
+ *   scores t[(m + 1) * 9] = t[j][from][to] (from, to in M, I, D; -inf for a
+ *   move that does not exist) and match emissions e[(m + 1) * 4] (row 0 is
+ *   0), host arrays.
+ * ah_hmm_score: one score per amplicon of the set (host or device records and
+ *   scores); amplicons of up to 65,536 letters.  Errors: AH_ERR_ARG (unknown
+ *   id, a record outside its contig, too long), AH_ERR_CUDA. */
+ah_status ah_hmm_build(ah_ctx *ctx, const char *seqs, const uint64_t *offsets, uint64_t n, uint32_t *hmm_id_out);
+ah_status ah_hmm_tables(ah_ctx *ctx, uint32_t hmm_id, uint64_t *m_out, uint64_t *reference_out, float *t_out,
+                        float *e_out);
+ah_status ah_hmm_score(ah_ctx *ctx, uint32_t set_id, uint32_t hmm_id, const ah_amplicon *amplicons, uint64_t n,
+                       float *score_out, void *stream);
+ah_status ah_hmm_free(ah_ctx *ctx, uint32_t hmm_id);
+
 #ifdef __cplusplus
 }
 #endif

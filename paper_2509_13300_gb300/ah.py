@@ -33,7 +33,8 @@ EXPORTS = ["ah_create", "ah_destroy", "ah_last_error", "ah_device_bytes", "ah_lo
            "ah_set_primers", "ah_set_nn_table", "ah_scan", "ah_tm", "ah_pair", "ah_fetch", "ah_set_profiling",
            "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan", "ah_run", "ah_run_begin", "ah_run_end",
            "ah_load_genomes_ex", "ah_tm_sweep", "ah_amplitypes", "ah_generate_bases", "ah_serve_start",
-           "ah_serve_submit", "ah_serve_wait", "ah_serve_stop"]
+           "ah_serve_submit", "ah_serve_wait", "ah_serve_stop", "ah_hmm_build", "ah_hmm_tables", "ah_hmm_score",
+           "ah_hmm_free"]
 
 
 class AHError(RuntimeError):
@@ -139,6 +140,10 @@ def lib():
             "ah_serve_submit": (I32, [P, ctypes.POINTER(Request), ctypes.POINTER(U64)]),
             "ah_serve_wait": (I32, [P, U64, ctypes.POINTER(RequestInfo), P, U64, P, U64, P, U64, P]),
             "ah_serve_stop": (I32, [P]),
+            "ah_hmm_build": (I32, [P, P, P, U64, ctypes.POINTER(U32)]),
+            "ah_hmm_tables": (I32, [P, U32, ctypes.POINTER(U64), ctypes.POINTER(U64), P, P]),
+            "ah_hmm_score": (I32, [P, U32, U32, P, U64, P, P]),
+            "ah_hmm_free": (I32, [P, U32]),
             "ah_tune_scan": (I32, [P, U32, P, U32, U64, ctypes.POINTER(TuneResult), P]),
             "ah_pair_noalloc": (I32, [P, U32, P, P, U64, P, U64, ctypes.POINTER(U64), P]),
             "ah_debug_compile_scan": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
@@ -381,6 +386,41 @@ class Context:
     def ah_fetch(self, set_id: int, amplicons, n: int, seq_out, cap: int, offsets_out, stream=None):
         self._check(self._lib.ah_fetch(self.h, set_id, _ptr(amplicons), n, _ptr(seq_out), cap, _ptr(offsets_out),
                                        _stream(stream)))
+
+    # ------------------------------------------------ profile HMM
+    def hmm_build(self, seqs) -> int:
+        """Profile from training sequences (list of str or bytes) -> profile id."""
+        data = b"".join(x.encode() if isinstance(x, str) else bytes(x) for x in seqs)
+        off = np.zeros(len(seqs) + 1, dtype=np.uint64)
+        off[1:] = np.cumsum([len(x) for x in seqs])
+        buf = np.frombuffer(data, dtype=np.uint8).copy() if data else np.zeros(1, np.uint8)
+        hid = ctypes.c_uint32()
+        self._check(self._lib.ah_hmm_build(self.h, _ptr(buf), _ptr(off), len(seqs), ctypes.byref(hid)))
+        return hid.value
+
+    def hmm_tables(self, hmm_id: int):
+        """(m, reference index, t[(m + 1), 3, 3], e[(m + 1), 4]) as float32 arrays."""
+        m, ref = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self._lib.ah_hmm_tables(self.h, hmm_id, ctypes.byref(m), ctypes.byref(ref), None, None))
+        t = np.zeros((m.value + 1, 3, 3), dtype=np.float32)
+        e = np.zeros((m.value + 1, 4), dtype=np.float32)
+        self._check(self._lib.ah_hmm_tables(self.h, hmm_id, None, None, _ptr(t), _ptr(e)))
+        return m.value, ref.value, t, e
+
+    def hmm_score(self, set_id: int, hmm_id: int, amplicons, n: int | None = None, out=None, stream=None):
+        """Viterbi log-odds score (bits) of each amplicon; numpy float32 unless `out` is given."""
+        n = len(amplicons) if n is None else n
+        res = np.zeros(n, dtype=np.float32) if out is None else out
+        if not isinstance(amplicons, np.ndarray) or amplicons.flags["C_CONTIGUOUS"]:
+            a = amplicons
+        else:
+            a = np.ascontiguousarray(amplicons)
+        self._check(self._lib.ah_hmm_score(self.h, set_id, hmm_id, _ptr(a) if n else None, n,
+                                           _ptr(res) if n else None, _stream(stream)))
+        return res
+
+    def hmm_free(self, hmm_id: int):
+        self._check(self._lib.ah_hmm_free(self.h, hmm_id))
 
     # ------------------------------------------------ numpy conveniences (host buffers)
     def load(self, seq: np.ndarray, contig_off, contig_genome, stream=None, reversed: bool = False) -> int:

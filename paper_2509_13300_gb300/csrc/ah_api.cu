@@ -28,6 +28,8 @@ struct ah_ctx {
     std::map<uint32_t, std::unique_ptr<GenomeSet>> sets;
     uint32_t next_set = 1;
     std::map<uint32_t, PrimerPair> pairs;
+    std::map<uint32_t, HmmProfile> hmms;
+    uint32_t next_hmm = 1;
     uint32_t next_pair = 1;
     std::map<std::string, Scratch> scratch;
     // device flag block (FlagWord layout)
@@ -2521,6 +2523,116 @@ ah_status ah_serve_stop(ah_server *S)
     S->c->serving = false;
     delete S;
     return AH_OK;
+}
+
+
+ah_status ah_hmm_build(ah_ctx *c, const char *seqs, const uint64_t *offsets, uint64_t n, uint32_t *hmm_id_out)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require_idle(c);
+        require(hmm_id_out && offsets && n >= 1, AH_ERR_ARG, "ah_hmm_build: null argument or no sequence");
+        require(!is_device_ptr(c, offsets) && (offsets[n] == 0 || (seqs && !is_device_ptr(c, seqs))), AH_ERR_ARG,
+                "ah_hmm_build: sequences and offsets are host arrays");
+        require(offsets[0] == 0, AH_ERR_ARG, "ah_hmm_build: offsets must start at 0");
+        for (uint64_t q = 0; q < n; ++q)
+            require(offsets[q] <= offsets[q + 1], AH_ERR_ARG, "ah_hmm_build: offsets not monotone");
+        HmmProfile p;
+        build_profile(seqs, offsets, n, p);
+        require(p.m >= 1 && p.m + 1 <= kHmmMaxColumns, AH_ERR_ARG,
+                "ah_hmm_build: the reference must hold 1.." + std::to_string(kHmmMaxColumns - 1) + " letters");
+        p.d_t = (float *)dev_alloc(c, p.t.size() * sizeof(float));
+        p.d_e = (float *)dev_alloc(c, p.e.size() * sizeof(float));
+        AH_CUDA(cudaMemcpyAsync(p.d_t, p.t.data(), p.t.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        AH_CUDA(cudaMemcpyAsync(p.d_e, p.e.data(), p.e.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        AH_CUDA(cudaStreamSynchronize(c->stream));
+        const uint32_t id = c->next_hmm++;
+        c->hmms[id] = std::move(p);
+        *hmm_id_out = id;
+    });
+}
+
+ah_status ah_hmm_tables(ah_ctx *c, uint32_t hmm_id, uint64_t *m_out, uint64_t *reference_out, float *t_out,
+                        float *e_out)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        auto it = c->hmms.find(hmm_id);
+        require(it != c->hmms.end(), AH_ERR_ARG, "ah_hmm_tables: unknown profile id");
+        const HmmProfile &p = it->second;
+        if (m_out)
+            *m_out = (uint64_t)p.m;
+        if (reference_out)
+            *reference_out = p.reference;
+        if (t_out)
+            memcpy(t_out, p.t.data(), p.t.size() * sizeof(float));
+        if (e_out)
+            memcpy(e_out, p.e.data(), p.e.size() * sizeof(float));
+    });
+}
+
+ah_status ah_hmm_score(ah_ctx *c, uint32_t set_id, uint32_t hmm_id, const ah_amplicon *amplicons, uint64_t n,
+                       float *score_out, void *stream)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require_idle(c);
+        require(n == 0 || (amplicons && score_out), AH_ERR_ARG, "ah_hmm_score: null argument");
+        auto it = c->hmms.find(hmm_id);
+        require(it != c->hmms.end(), AH_ERR_ARG, "ah_hmm_score: unknown profile id");
+        const HmmProfile &p = it->second;
+        GenomeSet &gs = get_set(c, set_id);
+        if (n == 0)
+            return;
+        cudaStream_t st = stream_of(c, stream);
+        wait_ready(gs, st);
+        // the records on the host: bounds and the longest amplicon (shared memory of the kernel)
+        std::vector<ah_amplicon> h(n);
+        if (is_device_ptr(c, amplicons)) {
+            AH_CUDA(cudaMemcpyAsync(h.data(), amplicons, n * sizeof(ah_amplicon), cudaMemcpyDeviceToHost, st));
+            AH_CUDA(cudaStreamSynchronize(st));
+        } else {
+            memcpy(h.data(), amplicons, n * sizeof(ah_amplicon));
+        }
+        uint32_t max_len = 1;
+        for (const ah_amplicon &a : h) {
+            require(a.contig < gs.n_contigs && a.start <= a.end &&
+                        (uint64_t)a.end <= gs.contig_off_h[a.contig + 1] - gs.contig_off_h[a.contig],
+                    AH_ERR_ARG, "ah_hmm_score: an amplicon lies outside its contig");
+            max_len = std::max(max_len, a.end - a.start);
+        }
+        require(max_len <= kHmmMaxLetters, AH_ERR_ARG,
+                "ah_hmm_score: amplicons longer than " + std::to_string(kHmmMaxLetters) + " letters");
+        reset_flags(c, st);
+        const ah_amplicon *a = stage_in(c, "hmm_in", amplicons, n, st);
+        float *out = out_buf(c, "hmm_out", score_out, n);
+        {
+            Stage sg(c, "hmm", st, 1);
+            launch_hmm_viterbi(a, n, gs.planes, gs.contig_off, gs.n_contigs, p.d_t, p.d_e, p.m, (int)max_len, out,
+                               c->d_err, c->sms, st);
+        }
+        check_flags(c, st);
+        out_finish(score_out, out, n, st);
+        AH_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+ah_status ah_hmm_free(ah_ctx *c, uint32_t hmm_id)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    return guarded(c, [&] {
+        require_idle(c);
+        auto it = c->hmms.find(hmm_id);
+        require(it != c->hmms.end(), AH_ERR_ARG, "ah_hmm_free: unknown profile id");
+        AH_CUDA(cudaStreamSynchronize(c->stream));
+        dev_free(c, it->second.d_t, 0);
+        dev_free(c, it->second.d_e, 0);
+        c->hmms.erase(it);
+    });
 }
 
 } // extern "C"

@@ -76,6 +76,23 @@ struct ScanPattern {
     uint8_t mask[AH_MAX_PRIMER_LEN] = {};
 };
 
+// A profile HMM (hmm.cu): m match columns; t[(m + 1) * 9] move scores
+// t[j][from][to] (from, to in M, I, D; "to M" at j = m is the end state),
+// -inf where a move does not exist; e[(m + 1) * 4] match emission scores
+// (row 0 unused); bits against the uniform background.
+constexpr int kHmmMaxColumns = 6 * 512; // m + 1 at most
+constexpr uint32_t kHmmMaxLetters = 65536; // longest scored amplicon (shared memory of the kernel)
+struct HmmProfile {
+    int m = 0;
+    uint64_t reference = 0; // index of the training sequence used as the reference
+    std::vector<float> t, e;
+    float *d_t = nullptr, *d_e = nullptr;
+};
+void build_profile(const char *seqs, const uint64_t *off, uint64_t n, HmmProfile &p);
+void launch_hmm_viterbi(const ah_amplicon *amps, uint64_t n, const uint32_t *planes, const uint64_t *contig_off,
+                        uint32_t n_contigs, const float *t, const float *e, int m, int max_len, float *score_out,
+                        int *err, int sms, cudaStream_t s);
+
 // Tunables of the generated scan kernel (autotuned per pattern set).
 struct ScanTuning {
     int R = 4;            // 32-start words per thread (4 or 8: the loader reads 16-byte vectors at lane * R)

@@ -1,0 +1,387 @@
+// Profile-HMM homology scores of amplicons (Sec. 2.1, Amplicon analysis,
+// item 2: a profile HMM trained on amplicons whose primers match exactly
+// scores every predicted amplicon).
+//
+// Profile (built on the host, build_profile): the most frequent training
+// sequence is the reference (first occurrence on ties); every training
+// sequence is aligned to it globally with unit costs (equal A/C/G/T letters
+// cost 0, any other pair 1, a gap 1), the traceback preferring a diagonal
+// step, then a step that consumes a letter of the sequence (an insertion
+// after the current column), then a step that consumes a column (a
+// deletion); the state path of each alignment (B = M_0, M_j, I_j, D_j, E)
+// gives transition counts from every state to the next column's M (E after
+// column m), to I_j and to the next column's D, and letter counts for each
+// match column; probabilities are counts + 1 normalised over the allowed
+// moves (and over A/C/G/T); insert states emit the background.  Scores are
+// bits against the uniform background: log2(p / (1/4)) for match emissions
+// (0 for an unknown letter), 0 for insert emissions, log2 p for moves.
+//
+// Score (hmm_viterbi_kernel): the glocal Viterbi log-odds score of each
+// amplicon's sequence (as ah_fetch returns it) against the profile, fp32.
+// One block per amplicon, rows = sequence letters: each thread owns K
+// consecutive profile columns with their 13 scores in registers; M and I of
+// a row depend only on the previous row (the left neighbour's values come by
+// shuffle, or through shared memory across warps); the delete chain
+// D_j = max(E_j, D_{j-1} + t_DD) is a block-wide scan in the (max, +)
+// semiring over (t_DD, E_j) pairs.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ah_internal.h"
+
+namespace ah {
+namespace {
+
+int letter_code(char c)
+{
+    switch (c) {
+    case 'A': case 'a': return 0;
+    case 'C': case 'c': return 1;
+    case 'G': case 'g': return 2;
+    case 'T': case 't': return 3;
+    default: return 4;
+    }
+}
+
+enum { kM = 0, kI = 1, kD = 2 };
+
+} // namespace
+
+void build_profile(const char *seqs, const uint64_t *off, uint64_t n, HmmProfile &p)
+{
+    // the reference: most frequent sequence, first occurrence on ties (by hashing)
+    std::map<std::string, std::pair<uint64_t, uint64_t>> freq; // sequence -> (count, first index)
+    for (uint64_t q = 0; q < n; ++q) {
+        std::string s(seqs + off[q], seqs + off[q + 1]);
+        auto it = freq.find(s);
+        if (it == freq.end())
+            freq.emplace(std::move(s), std::make_pair(1ull, q));
+        else
+            ++it->second.first;
+    }
+    uint64_t best_q = 0, best_n = 0;
+    for (const auto &kv : freq)
+        if (kv.second.first > best_n || (kv.second.first == best_n && kv.second.second < best_q)) {
+            best_n = kv.second.first;
+            best_q = kv.second.second;
+        }
+    const char *R = seqs + off[best_q];
+    const int64_t m = (int64_t)(off[best_q + 1] - off[best_q]);
+    p.m = (int)m;
+    p.reference = best_q;
+    std::vector<double> ct((size_t)(m + 1) * 9, 0.0), ce((size_t)(m + 1) * 4, 0.0);
+    std::vector<int> rc(m);
+    for (int64_t j = 0; j < m; ++j)
+        rc[j] = letter_code(R[j]);
+    std::vector<uint32_t> dist; // (len + 1) x (m + 1) alignment costs
+    std::vector<uint8_t> moves;
+    for (uint64_t q = 0; q < n; ++q) {
+        const char *S = seqs + off[q];
+        const int64_t ls = (int64_t)(off[q + 1] - off[q]);
+        const int64_t W = m + 1;
+        dist.assign((size_t)(ls + 1) * W, 0);
+        for (int64_t j = 0; j <= m; ++j)
+            dist[j] = (uint32_t)j;
+        for (int64_t i = 1; i <= ls; ++i) {
+            const int si = letter_code(S[i - 1]);
+            uint32_t *row = &dist[i * W];
+            const uint32_t *up = &dist[(i - 1) * W];
+            row[0] = (uint32_t)i;
+            for (int64_t j = 1; j <= m; ++j) {
+                const uint32_t sub = up[j - 1] + ((si < 4 && si == rc[j - 1]) ? 0u : 1u);
+                row[j] = std::min(sub, std::min(up[j], row[j - 1]) + 1u);
+            }
+        }
+        moves.clear();
+        int64_t i = ls, j = m;
+        while (i > 0 || j > 0) {
+            const uint32_t here = dist[i * W + j];
+            if (i > 0 && j > 0) {
+                const int si = letter_code(S[i - 1]);
+                const uint32_t sub = dist[(i - 1) * W + j - 1] + ((si < 4 && si == rc[j - 1]) ? 0u : 1u);
+                if (here == sub) {
+                    moves.push_back(kM);
+                    --i;
+                    --j;
+                    continue;
+                }
+            }
+            if (i > 0 && here == dist[(i - 1) * W + j] + 1u) {
+                moves.push_back(kI);
+                --i;
+            } else {
+                moves.push_back(kD);
+                --j;
+            }
+        }
+        int from = kM; // B = M_0
+        int64_t col = 0, pos = 0;
+        for (auto it = moves.rbegin(); it != moves.rend(); ++it) {
+            const int to = *it;
+            ct[(size_t)col * 9 + from * 3 + to] += 1.0;
+            if (to == kM) {
+                ++col;
+                const int l = letter_code(S[pos]);
+                if (l < 4)
+                    ce[(size_t)col * 4 + l] += 1.0;
+                ++pos;
+            } else if (to == kI) {
+                ++pos;
+            } else {
+                ++col;
+            }
+            from = to;
+        }
+        ct[(size_t)col * 9 + from * 3 + kM] += 1.0; // to E
+    }
+    p.t.assign((size_t)(m + 1) * 9, -INFINITY);
+    p.e.assign((size_t)(m + 1) * 4, 0.0f);
+    for (int64_t j = 0; j <= m; ++j) {
+        for (int x = 0; x < 3; ++x) {
+            if (j == 0 && x == kD)
+                continue; // D_0 does not exist
+            const bool has_d = j < m;
+            double tot = 0.0;
+            for (int y = 0; y < 3; ++y)
+                if (y != kD || has_d)
+                    tot += ct[(size_t)j * 9 + x * 3 + y] + 1.0;
+            for (int y = 0; y < 3; ++y)
+                if (y != kD || has_d)
+                    p.t[(size_t)j * 9 + x * 3 + y] = (float)std::log2((ct[(size_t)j * 9 + x * 3 + y] + 1.0) / tot);
+        }
+        if (j > 0) {
+            const double tot = ce[j * 4] + ce[j * 4 + 1] + ce[j * 4 + 2] + ce[j * 4 + 3] + 4.0;
+            for (int l = 0; l < 4; ++l)
+                p.e[(size_t)j * 4 + l] = (float)std::log2((ce[(size_t)j * 4 + l] + 1.0) / tot * 4.0);
+        }
+    }
+}
+
+namespace {
+
+constexpr int kHmmThreads = 512;
+constexpr float kNeg = -INFINITY;
+
+struct MaxPlus { // D_out = max(b, D_in + a)
+    float a, b;
+};
+__device__ __forceinline__ MaxPlus mp_then(MaxPlus first, MaxPlus second)
+{
+    return {first.a + second.a, fmaxf(second.b, first.b + second.a)};
+}
+
+// Letter codes of amplicon `am` (as fetched: RF reverse-complemented) into seq.
+__device__ void decode_letters(const ah_amplicon &am, const uint32_t *__restrict__ planes,
+                               const uint64_t *__restrict__ contig_off, uint8_t *seq, int len)
+{
+    const uint64_t base = contig_off[am.contig] + am.start;
+    const bool rc = am.orient == 1;
+    for (int q = threadIdx.x; q < len; q += blockDim.x) {
+        const uint64_t P = base + (rc ? (uint64_t)(len - 1 - q) : (uint64_t)q);
+        const uint64_t t = P / kTileBases, r = P % kTileBases;
+        const int b = (int)(r / kTileW), j = (int)(r % kTileW);
+        const uint32_t *w = planes + t * 4 * kTileWX + j;
+        int code = 4;
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+            if ((__ldg(w + x * kTileWX) >> b) & 1u)
+                code = x;
+        if (code < 4 && rc)
+            code = 3 - code;
+        seq[q] = (uint8_t)code;
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kHmmThreads) hmm_viterbi_kernel(const ah_amplicon *__restrict__ amps, uint64_t n_amps,
+                                                                  const uint32_t *__restrict__ planes,
+                                                                  const uint64_t *__restrict__ contig_off,
+                                                                  uint32_t n_contigs, const float *__restrict__ t,
+                                                                  const float *__restrict__ e, int m, int max_len,
+                                                                  float *__restrict__ score_out, int *__restrict__ err)
+{
+    extern __shared__ uint8_t seq[];                 // max_len letter codes
+    __shared__ float edge_prev[3][kHmmThreads / 32]; // M, I, D of each warp's last column, previous row
+    __shared__ float edge_cur[2][kHmmThreads / 32];  // M, I of each warp's last column, current row
+    __shared__ MaxPlus wtot[kHmmThreads / 32];
+    __shared__ MaxPlus wpre[kHmmThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int c0 = threadIdx.x * K;
+    // this thread's columns: scores of the moves into M_j (from j-1), into D_j
+    // (from j-1) and into I_j (from j), and M_j's emissions
+    float toM[K][3], toD[K][3], toI[K][3], em[K][4];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int j = c0 + k;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+            toM[k][x] = (j >= 1 && j <= m) ? t[(j - 1) * 9 + x * 3 + 0] : kNeg;
+            toD[k][x] = (j >= 1 && j <= m) ? t[(j - 1) * 9 + x * 3 + 2] : kNeg;
+            toI[k][x] = (j <= m) ? t[j * 9 + x * 3 + 1] : kNeg;
+        }
+#pragma unroll
+        for (int l = 0; l < 4; ++l)
+            em[k][l] = (j >= 1 && j <= m) ? e[j * 4 + l] : 0.0f;
+    }
+    for (uint64_t ai = blockIdx.x; ai < n_amps; ai += gridDim.x) {
+        const ah_amplicon am = amps[ai];
+        bool ok = am.contig < n_contigs && am.start <= am.end;
+        if (ok)
+            ok = (uint64_t)am.end <= contig_off[am.contig + 1] - contig_off[am.contig] &&
+                 am.end - am.start <= (uint32_t)max_len;
+        if (!ok) { // checked on the host; a record that fails here is reported, not read
+            if (threadIdx.x == 0) {
+                atomicExch(err, kDevBounds);
+                score_out[ai] = kNeg;
+            }
+            continue;
+        }
+        const int n = (int)(am.end - am.start);
+        __syncthreads(); // the previous amplicon's letters are no longer read
+        decode_letters(am, planes, contig_off, seq, n);
+        // row 0: B = M_0; D_j reached from B through deletions
+        float pM[K], pI[K], pD[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            pM[k] = (c0 + k == 0) ? 0.0f : kNeg;
+            pI[k] = kNeg;
+            pD[k] = kNeg;
+        }
+        // the delete chain of a row from its M and I values (cur*: this row's)
+        auto delete_chain = [&](const float (&cM)[K], const float (&cI)[K], float (&cD)[K]) {
+            // left neighbour's M, I of this row
+            float lM = __shfl_up_sync(0xffffffffu, cM[K - 1], 1), lI = __shfl_up_sync(0xffffffffu, cI[K - 1], 1);
+            if (lane == 31) {
+                edge_cur[0][warp] = cM[K - 1];
+                edge_cur[1][warp] = cI[K - 1];
+            }
+            __syncthreads();
+            if (lane == 0) {
+                lM = warp > 0 ? edge_cur[0][warp - 1] : kNeg;
+                lI = warp > 0 ? edge_cur[1][warp - 1] : kNeg;
+            }
+            MaxPlus el[K], agg = {0.0f, kNeg};
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float pm = k ? cM[k - 1] : lM, pi = k ? cI[k - 1] : lI;
+                el[k] = {toD[k][kD], fmaxf(pm + toD[k][kM], pi + toD[k][kI])};
+                agg = mp_then(agg, el[k]);
+            }
+            // inclusive warp scan of the thread aggregates, then across warps
+            MaxPlus inc = agg;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                MaxPlus o{__shfl_up_sync(0xffffffffu, inc.a, d), __shfl_up_sync(0xffffffffu, inc.b, d)};
+                if (lane >= d)
+                    inc = mp_then(o, inc);
+            }
+            if (lane == 31)
+                wtot[warp] = inc;
+            __syncthreads();
+            if (warp == 0) {
+                MaxPlus w = lane < nwarps ? wtot[lane] : MaxPlus{0.0f, kNeg};
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    MaxPlus o{__shfl_up_sync(0xffffffffu, w.a, d), __shfl_up_sync(0xffffffffu, w.b, d)};
+                    if (lane >= d)
+                        w = mp_then(o, w);
+                }
+                // exclusive prefix of the warps
+                MaxPlus ex{__shfl_up_sync(0xffffffffu, w.a, 1), __shfl_up_sync(0xffffffffu, w.b, 1)};
+                if (lane < nwarps)
+                    wpre[lane] = lane ? ex : MaxPlus{0.0f, kNeg};
+            }
+            __syncthreads();
+            MaxPlus ex{__shfl_up_sync(0xffffffffu, inc.a, 1), __shfl_up_sync(0xffffffffu, inc.b, 1)};
+            if (lane == 0)
+                ex = {0.0f, kNeg};
+            const MaxPlus pre = mp_then(wpre[warp], ex);
+            float d = pre.b; // D at column c0 - 1 (from D = -inf before column 0)
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                d = fmaxf(el[k].b, d + el[k].a);
+                cD[k] = d;
+            }
+        };
+        delete_chain(pM, pI, pD);
+        for (int i = 1; i <= n; ++i) {
+            const int x = seq[i - 1];
+            // previous row at column c0 - 1
+            float lM = __shfl_up_sync(0xffffffffu, pM[K - 1], 1), lI = __shfl_up_sync(0xffffffffu, pI[K - 1], 1),
+                  lD = __shfl_up_sync(0xffffffffu, pD[K - 1], 1);
+            if (lane == 31) {
+                edge_prev[0][warp] = pM[K - 1];
+                edge_prev[1][warp] = pI[K - 1];
+                edge_prev[2][warp] = pD[K - 1];
+            }
+            __syncthreads();
+            if (lane == 0) {
+                lM = warp > 0 ? edge_prev[0][warp - 1] : kNeg;
+                lI = warp > 0 ? edge_prev[1][warp - 1] : kNeg;
+                lD = warp > 0 ? edge_prev[2][warp - 1] : kNeg;
+            }
+            float cM[K], cI[K], cD[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float qm = k ? pM[k - 1] : lM, qi = k ? pI[k - 1] : lI, qd = k ? pD[k - 1] : lD;
+                const float ex = x < 4 ? em[k][x] : 0.0f;
+                cM[k] = ex + fmaxf(fmaxf(qm + toM[k][kM], qi + toM[k][kI]), qd + toM[k][kD]);
+                cI[k] = fmaxf(fmaxf(pM[k] + toI[k][kM], pI[k] + toI[k][kI]), pD[k] + toI[k][kD]);
+            }
+            delete_chain(cM, cI, cD);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                pM[k] = cM[k];
+                pI[k] = cI[k];
+                pD[k] = cD[k];
+            }
+        }
+        // the thread holding column m ends the path
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (c0 + k == m)
+                score_out[ai] = fmaxf(fmaxf(pM[k] + t[m * 9 + kM * 3], pI[k] + t[m * 9 + kI * 3]),
+                                      pD[k] + t[m * 9 + kD * 3]);
+    }
+}
+
+template <int K>
+void launch_k(const ah_amplicon *amps, uint64_t n, const uint32_t *planes, const uint64_t *contig_off,
+              uint32_t n_contigs, const float *t, const float *e, int m, int max_len, float *out, int *err, int sms,
+              cudaStream_t s)
+{
+    const int threads = std::min(kHmmThreads, 32 * (((m + 1) + 32 * K - 1) / (32 * K)));
+    const size_t smem = (size_t)max_len;
+    if (smem > 48 * 1024)
+        AH_CUDA(cudaFuncSetAttribute(hmm_viterbi_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 1;
+    AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hmm_viterbi_kernel<K>, threads, smem));
+    const uint64_t blocks = std::min<uint64_t>(n, (uint64_t)sms * (uint64_t)std::max(1, per_sm));
+    hmm_viterbi_kernel<K><<<(unsigned)blocks, threads, smem, s>>>(amps, n, planes, contig_off, n_contigs, t, e, m,
+                                                                   max_len, out, err);
+    AH_CUDA(cudaGetLastError());
+}
+
+} // namespace
+
+void launch_hmm_viterbi(const ah_amplicon *amps, uint64_t n, const uint32_t *planes, const uint64_t *contig_off,
+                        uint32_t n_contigs, const float *t, const float *e, int m, int max_len, float *score_out,
+                        int *err, int sms, cudaStream_t s)
+{
+    if (n == 0)
+        return;
+    const int cols = m + 1;
+    if (cols <= kHmmThreads)
+        launch_k<1>(amps, n, planes, contig_off, n_contigs, t, e, m, max_len, score_out, err, sms, s);
+    else if (cols <= 2 * kHmmThreads)
+        launch_k<2>(amps, n, planes, contig_off, n_contigs, t, e, m, max_len, score_out, err, sms, s);
+    else if (cols <= 4 * kHmmThreads)
+        launch_k<4>(amps, n, planes, contig_off, n_contigs, t, e, m, max_len, score_out, err, sms, s);
+    else if (cols <= 6 * kHmmThreads)
+        launch_k<6>(amps, n, planes, contig_off, n_contigs, t, e, m, max_len, score_out, err, sms, s);
+    else
+        throw Error(AH_ERR_ARG, "ah_hmm_score: profile longer than " + std::to_string(kHmmMaxColumns) + " columns");
+}
+
+} // namespace ah

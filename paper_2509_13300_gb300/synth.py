@@ -258,3 +258,49 @@ def random_small(seed: int, n_bases: int = 2000, n_contigs: int = 3, L_f: int = 
         g[m] += ord("a") - ord("A")
     lens = _contig_lengths(rng, n_bases, n_contigs)
     return _assemble("random_small", [(g, lens)], [pair], [])
+
+
+def _mutate(rng, s: str, sub: float, indel: float) -> str:
+    """Copy of s with per-letter substitutions (rate sub) and single-letter
+    insertions and deletions (rate indel each)."""
+    out = []
+    for c in s:
+        u = rng.random()
+        if u < indel:  # deletion
+            continue
+        if u < 2 * indel:  # insertion before the letter
+            out.append("ACGT"[int(rng.integers(4))])
+        if rng.random() < sub:
+            c = "ACGT".replace(c, "")[int(rng.integers(3))] if c in "ACGT" else c
+        out.append(c)
+    return "".join(out)
+
+
+def operon_family(seed: int = 21, n_genomes: int = 12, genome_len: int = 150_000, template_len: int = 600,
+                  copies=(1, 4), sub: float = 0.02, indel: float = 0.005, k: int = 2) -> Workload:
+    """Genomes carrying copies of one operon-like template (a gene family): each
+    copy is the forward primer (an oligo with 0-2 substitutions, 70 % exact),
+    the template with per-copy substitutions and small indels, and the reverse
+    complement of the reverse primer, inserted in either orientation into a
+    random genome of one contig.  Amplicons whose two sites match exactly are
+    the training set of a profile HMM; the others are scored against it."""
+    rng = np.random.default_rng(seed)
+    fwd = random_primer(rng, 20, "".join(rng.choice(list(TWO_WAY), 2)))
+    rev = random_primer(rng, 20, "".join(rng.choice(list(TWO_WAY), 2)))
+    pair = pcr_params(fwd, rev, k=k, min_len=100, max_len=template_len + 400)
+    template = random_bases(rng, template_len, 0.5).tobytes().decode()
+    genomes = []
+    for gi in range(n_genomes):
+        g = random_bases(rng, genome_len, float(rng.uniform(0.4, 0.6)))
+        n_cp = int(rng.integers(copies[0], copies[1] + 1))
+        slots = np.sort(rng.choice(genome_len // (template_len + 500) - 1, size=n_cp, replace=False))
+        for sl in slots:
+            nf = 0 if rng.random() < 0.7 else int(rng.integers(1, 3))
+            nr = 0 if rng.random() < 0.7 else int(rng.integers(1, 3))
+            body = _draw_oligo(rng, fwd, nf) + _mutate(rng, template, sub, indel) + _revcomp(_draw_oligo(rng, rev, nr))
+            if rng.random() < 0.5:
+                body = _revcomp(body)
+            p0 = int(sl) * (template_len + 500) + int(rng.integers(0, 100))
+            g[p0:p0 + len(body)] = np.frombuffer(body.encode(), dtype=np.uint8)
+        genomes.append((g, [genome_len]))
+    return _assemble("operon_family", genomes, [pair], [])

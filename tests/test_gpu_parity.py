@@ -756,3 +756,69 @@ def test_served_requests_alone_and_in_the_mix(ctx):
         assert a[2] == want_q and np.array_equal(a[3], want_o), n
         total_amps += len(want_a)
     assert total_amps > 10
+
+
+def test_profile_hmm_build_and_scores(ctx):
+    """ah_hmm_build / ah_hmm_score: the profile trained on the exact-match
+    amplicons of an operon family (training set taken end to end: a k = 0 run
+    and its fetched sequences) equals the oracle's (fp32 of its fp64 scores),
+    and the fp32 Viterbi score of every k = 2 amplicon and of random regions is
+    within the fp32 accumulation bound of the oracle's fp64 score."""
+    import torch
+    w = synth.operon_family(seed=21, n_genomes=16)
+    p = w.pairs[0]
+    p0 = dict(p, k=0)
+    s0 = oracle.scan(w.seq, w.contig_off, w.contig_genome, [p0])
+    a0 = oracle.pair(s0, [p0])
+    q0, o0 = oracle.fetch(w.seq, w.contig_off, a0)
+    train = [q0[int(o0[i]):int(o0[i + 1])].decode() for i in range(len(a0))]
+    assert len(train) >= 8
+    ref, T, E = oracle.hmm_build(train)
+    s2 = oracle.scan(w.seq, w.contig_off, w.contig_genome, [p])
+    a2 = oracle.pair(s2, [p])
+    rng = np.random.default_rng(3)  # unrelated regions in either orientation
+    extra = np.zeros(40, dtype=oracle.AMPLICON_DTYPE)
+    lens = np.diff(w.contig_off.astype(np.int64))
+    for r in extra:
+        c = int(rng.integers(len(lens)))
+        L = int(rng.integers(200, 900))
+        s = int(rng.integers(0, lens[c] - L))
+        r["genome"], r["contig"], r["start"], r["end"], r["orient"] = w.contig_genome[c], c, s, s + L, rng.integers(2)
+    amps = np.concatenate([a2, extra])
+    q2, o2 = oracle.fetch(w.seq, w.contig_off, amps)
+    seqs = [q2[int(o2[i]):int(o2[i + 1])].decode() for i in range(len(amps))]
+    want = np.array([oracle.hmm_viterbi(T, E, x) for x in seqs])
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    try:
+        pid0 = ctx.ah_set_primers(p0["fwd"], p0["rev"], p0)
+        r0 = ctx.run(sid, [pid0], tm_filter=False)
+        gtrain = [r0["seqs"][int(r0["offs"][i]):int(r0["offs"][i + 1])].decode() for i in range(len(r0["amps"]))]
+        assert gtrain == train
+        hid = ctx.hmm_build(gtrain)
+        m, gref, gt, ge = ctx.hmm_tables(hid)
+        assert (m, gref) == (T.shape[0] - 1, ref)
+        assert np.array_equal(np.isinf(gt), np.isinf(T))
+        fin = ~np.isinf(T)
+        assert np.abs(gt[fin] - T[fin]).max() <= 1e-5
+        assert np.abs(ge - E).max() <= 1e-5
+        got = ctx.hmm_score(sid, hid, amps)
+        # device records and scores give the same
+        dev_amps = torch.from_numpy(amps.view(np.uint8).copy()).cuda()
+        dev_out = torch.zeros(len(amps), dtype=torch.float32, device="cuda")
+        ctx.hmm_score(sid, hid, dev_amps, n=len(amps), out=dev_out)
+        assert np.array_equal(dev_out.cpu().numpy(), got)
+        with pytest.raises(ah.AHError):
+            ctx.hmm_score(sid, hid + 99, amps)
+        bad = amps[:1].copy()
+        bad["end"] = lens[bad["contig"][0]] + 5
+        with pytest.raises(ah.AHError):
+            ctx.hmm_score(sid, hid, bad)
+        ctx.hmm_free(hid)
+    finally:
+        ctx.ah_unload_genomes(sid)
+    pmax = float(max(np.abs(T[fin]).max(), np.abs(E).max()))
+    n_all = np.array([len(x) for x in seqs])
+    tol = (n_all + m) ** 2 * pmax * 2.0 ** -24 + 1e-3  # fp32 accumulation along one path
+    err = np.abs(got.astype(np.float64) - want)
+    assert (err <= tol).all(), (err.max(), tol.min())
+    assert want[:len(a2)].min() > want[len(a2):].max()  # family members above unrelated regions

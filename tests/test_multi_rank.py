@@ -44,10 +44,12 @@ def test_timing_reductions_over_two_gloo_ranks(tmp_path):
         mx = bench.max_over_ranks(1.0 + rank, world)
         sm = bench.sum_over_ranks(10.0 * (rank + 1), world)
         bench.barrier(world)
-        print(json.dumps({{"rank": rank, "world": world, "max": mx, "sum": sm}}), flush=True)
+        with open({str(tmp_path)!r} + f"/rank{{rank}}.json", "w") as f:  # one file per rank: no interleaving
+            json.dump({{"rank": rank, "world": world, "max": mx, "sum": sm}}, f)
         dist.destroy_process_group()
     """))
-    out = sorted(_torchrun([str(script)]), key=lambda d: d["rank"])
+    _torchrun([str(script)])
+    out = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(2)]
     assert [d["rank"] for d in out] == [0, 1]
     assert all(d["world"] == 2 and d["max"] == 2.0 and d["sum"] == 30.0 for d in out)
 
