@@ -239,7 +239,7 @@ def main():
     ap.add_argument("--n-genomes", type=int, default=100, help="smaller collections for profiling runs")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="one set at a time (default: the next set packs on a second stream after the current scan)")
-    ap.add_argument("--form", default="plain", choices=["plain", "batched", "served", "large"],
+    ap.add_argument("--form", default="plain", choices=["plain", "batched", "served", "large", "hmm"],
                     help="plain: the genome-collection line (default); batched / served: those forms' lines")
     ap.add_argument("--chunk-bases", type=int, default=2_000_000_000, help="batched: bases per set (whole genomes)")
     ap.add_argument("--plain-genomes", type=int, default=400, help="batched: genomes timed in the plain form")
@@ -263,6 +263,8 @@ def main():
         return bench_served(args)
     if args.form == "large":
         return bench_large(args)
+    if args.form == "hmm":
+        return bench_hmm(args)
 
     rank, world, local = dist_info()
     import torch
@@ -1075,6 +1077,92 @@ def bench_large(args):
     print(json.dumps(line), flush=True)
     ctx.close()
 
+
+
+def bench_hmm(args):
+    """Profile-HMM form: a profile trained on the exact-match amplicons of an
+    operon family scores every k = 2 amplicon of the collection (glocal Viterbi,
+    fp32); throughput in cell updates per second, a sample checked by the oracle."""
+    import torch
+    from paper_2509_13300_gb300 import ah, build, synth
+    build.build()
+    torch.cuda.set_device(0)
+    n_g = args.n_genomes if args.n_genomes != 100 else 2000
+    t0 = time.perf_counter()
+    w = synth.operon_family(seed=21, n_genomes=n_g)
+    t_gen = time.perf_counter() - t0
+    p = w.pairs[0]
+    p0 = dict(p, k=0)
+    ctx = ah.Context(0)
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    pid0 = ctx.ah_set_primers(p0["fwd"], p0["rev"], p0)
+    pid2 = ctx.ah_set_primers(p["fwd"], p["rev"], p)
+    r0 = ctx.run(sid, [pid0], tm_filter=False)
+    train = [r0["seqs"][int(r0["offs"][i]):int(r0["offs"][i + 1])] for i in range(len(r0["amps"]))]
+    t0 = time.perf_counter()
+    hid = ctx.hmm_build(train)
+    t_build = time.perf_counter() - t0
+    m, ref, T, E = ctx.hmm_tables(hid)
+    r2 = ctx.run(sid, [pid2], tm_filter=False)
+    amps = r2["amps"]
+    lens = (amps["end"] - amps["start"]).astype(np.int64)
+    cells = float(lens.sum()) * m
+    dev_amps = torch.from_numpy(amps.view(np.uint8).copy()).cuda()
+    out = torch.zeros(len(amps), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    for _ in range(max(1, args.warmup)):
+        ctx.hmm_score(sid, hid, dev_amps, n=len(amps), out=out, stream=stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        clk.wait_first()
+        clk.mark(True)
+        ev[0].record(stream)
+        for _ in range(args.steps):
+            ctx.hmm_score(sid, hid, dev_amps, n=len(amps), out=out, stream=stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        clk.mark(False)
+    dt = ev[0].elapsed_time(ev[1]) / 1e3 / args.steps
+    got = out.cpu().numpy()
+    # the oracle on a sample: its own profile from the same training sequences
+    import oracle
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(len(amps), size=min(len(amps), args.check_genomes * 4), replace=False))
+    oref, oT, oE = oracle.hmm_build([x.decode() for x in train])
+    qs, qo = oracle.fetch(w.seq, w.contig_off, amps[sample])
+    t0 = time.perf_counter()
+    want = np.array([oracle.hmm_viterbi(oT, oE, qs[int(qo[i]):int(qo[i + 1])].decode()) for i in range(len(sample))])
+    t_cpu = time.perf_counter() - t0
+    cpu_cells = float(lens[sample].sum()) * m
+    pmax = float(max(np.abs(oT[~np.isinf(oT)]).max(), np.abs(oE).max()))
+    tol = (lens[sample] + m) ** 2 * pmax * 2.0 ** -24 + 1e-3
+    err = np.abs(got[sample].astype(np.float64) - want)
+    clocks = clk.summary()
+    fp_ops_per_cell = 19  # FADD + FMNMX per cell, counted in the kernel source (M 6, I 5, delete chain 8)
+    fp32_peak = 152 * 128 * (clocks["sm_mhz"] or 2070.0) * 1e6
+    achieved = cells / dt * fp_ops_per_cell
+    line = {
+        "form": "hmm", "metric": "cell updates per second (glocal Viterbi, profile x amplicon)",
+        "value": cells / dt / 1e9, "unit": "GCUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "data": "synthetic (operon family, seed 21)",
+        "config": {"workload": f"hmm-operonfamily-{n_g}genomes", "n_bases": w.n_bases, "profile_columns": m,
+                   "training_amplicons": len(train), "reference_index": ref, "scored_amplicons": len(amps),
+                   "letters_scored": int(lens.sum()), "generation_s": t_gen, "profile_build_s": t_build},
+        "amplicons_per_s": len(amps) / dt,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s (fp32 add/max)",
+                     "frac": achieved / fp32_peak, "ops_per_cell": fp_ops_per_cell,
+                     "peak_note": "152 SMs x 128 fp32 lanes x median SM clock"},
+        "oracle_check": {"amplicons": len(sample), "max_abs_err_bits": float(err.max()) if len(err) else 0.0,
+                         "within_fp32_bound": bool((err <= tol).all()), "min_bound_bits": float(tol.min()) if len(tol) else 0.0},
+        "cpu_baseline": {"value": cpu_cells / t_cpu / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(sample)} amplicons, fp64 Viterbi, {t_cpu:.1f} s"},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.hmm_free(hid)
+    ctx.ah_unload_genomes(sid)
+    ctx.close()
 
 def check_large_dump(path: str):
     """The oracle, on this machine, against the GPU results a large-form run
