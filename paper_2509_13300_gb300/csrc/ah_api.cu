@@ -2604,15 +2604,25 @@ ah_status ah_hmm_score(ah_ctx *c, uint32_t set_id, uint32_t hmm_id, const ah_amp
                     AH_ERR_ARG, "ah_hmm_score: an amplicon lies outside its contig");
             max_len = std::max(max_len, a.end - a.start);
         }
-        require(max_len <= kHmmMaxLetters, AH_ERR_ARG,
-                "ah_hmm_score: amplicons longer than " + std::to_string(kHmmMaxLetters) + " letters");
+        require(max_len <= kHmmMaxLetters / 4, AH_ERR_ARG,
+                "ah_hmm_score: amplicons longer than " + std::to_string(kHmmMaxLetters / 4) + " letters");
+        require(n <= 0xffffffffull, AH_ERR_ARG, "ah_hmm_score: at most 2^32 - 1 amplicons per call");
+        // amplicons of similar length side by side (the kernel scores several in lockstep)
+        std::vector<uint32_t> ord(n);
+        for (uint64_t q = 0; q < n; ++q)
+            ord[q] = (uint32_t)q;
+        std::stable_sort(ord.begin(), ord.end(), [&](uint32_t x, uint32_t y) {
+            return h[x].end - h[x].start > h[y].end - h[y].start;
+        });
         reset_flags(c, st);
         const ah_amplicon *a = stage_in(c, "hmm_in", amplicons, n, st);
+        uint32_t *d_ord = (uint32_t *)scratch(c, "hmm_order", n * sizeof(uint32_t));
+        AH_CUDA(cudaMemcpyAsync(d_ord, ord.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
         float *out = out_buf(c, "hmm_out", score_out, n);
         {
             Stage sg(c, "hmm", st, 1);
-            launch_hmm_viterbi(a, n, gs.planes, gs.contig_off, gs.n_contigs, p.d_t, p.d_e, p.m, (int)max_len, out,
-                               c->d_err, c->sms, st);
+            launch_hmm_viterbi(a, d_ord, n, gs.planes, gs.contig_off, gs.n_contigs, p.d_t, p.d_e, p.m, (int)max_len,
+                               out, c->d_err, c->sms, st);
         }
         check_flags(c, st);
         out_finish(score_out, out, n, st);

@@ -18,14 +18,16 @@
 //
 // Score (hmm_viterbi_kernel): the glocal Viterbi log-odds score of each
 // amplicon's sequence (as ah_fetch returns it) against the profile, fp32.
-// One block per amplicon, rows = sequence letters: each thread owns K
-// consecutive profile columns with their 13 scores in registers; M and I of
-// a row depend only on the previous row (the left neighbour's values come by
-// shuffle, or through shared memory across warps); the delete chain
-// D_j = max(E_j, D_{j-1} + t_DD) is a block-wide scan in the (max, +)
-// semiring over (t_DD, E_j) pairs.
+// A block scores a group of amplicons of similar length in lockstep, rows =
+// sequence letters: each thread owns K consecutive profile columns with their
+// 13 scores in registers; M and I of a row depend only on the previous row
+// (the left neighbour's values come by shuffle, or through shared memory
+// across warps); the delete chain D_j = max(E_j, D_{j-1} + t_DD) is a
+// block-wide scan in the (max, +) semiring over (t_DD, E_j) pairs.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "ah_internal.h"
@@ -163,14 +165,6 @@ namespace {
 constexpr int kHmmThreads = 512;
 constexpr float kNeg = -INFINITY;
 
-struct MaxPlus { // D_out = max(b, D_in + a)
-    float a, b;
-};
-__device__ __forceinline__ MaxPlus mp_then(MaxPlus first, MaxPlus second)
-{
-    return {first.a + second.a, fmaxf(second.b, first.b + second.a)};
-}
-
 // Letter codes of amplicon `am` (as fetched: RF reverse-complemented) into seq.
 __device__ void decode_letters(const ah_amplicon &am, const uint32_t *__restrict__ planes,
                                const uint64_t *__restrict__ contig_off, uint8_t *seq, int len)
@@ -193,19 +187,23 @@ __device__ void decode_letters(const ah_amplicon &am, const uint32_t *__restrict
     }
 }
 
-template <int K>
-__global__ void __launch_bounds__(kHmmThreads) hmm_viterbi_kernel(const ah_amplicon *__restrict__ amps, uint64_t n_amps,
+// A amplicons per block, in lockstep over rows (the host groups amplicons of
+// similar length): the barriers of a row serve A rows of work.  The delete
+// chain's (max, +) pairs share their t_DD part across the A amplicons.
+template <int K, int A>
+__global__ void __launch_bounds__(kHmmThreads) hmm_viterbi_kernel(const ah_amplicon *__restrict__ amps,
+                                                                  const uint32_t *__restrict__ order, uint64_t n_amps,
                                                                   const uint32_t *__restrict__ planes,
                                                                   const uint64_t *__restrict__ contig_off,
                                                                   uint32_t n_contigs, const float *__restrict__ t,
                                                                   const float *__restrict__ e, int m, int max_len,
                                                                   float *__restrict__ score_out, int *__restrict__ err)
 {
-    extern __shared__ uint8_t seq[];                 // max_len letter codes
-    __shared__ float edge_prev[3][kHmmThreads / 32]; // M, I, D of each warp's last column, previous row
-    __shared__ float edge_cur[2][kHmmThreads / 32];  // M, I of each warp's last column, current row
-    __shared__ MaxPlus wtot[kHmmThreads / 32];
-    __shared__ MaxPlus wpre[kHmmThreads / 32];
+    extern __shared__ uint8_t seq[];                    // A x max_len letter codes
+    __shared__ float edge_prev[A][3][kHmmThreads / 32]; // M, I, D of each warp's last column, previous row
+    __shared__ float edge_cur[A][2][kHmmThreads / 32];  // M, I of each warp's last column, current row
+    __shared__ float wtot_a[kHmmThreads / 32], wtot_b[A][kHmmThreads / 32];
+    __shared__ float wpre_a[kHmmThreads / 32], wpre_b[A][kHmmThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int c0 = threadIdx.x * K;
     // this thread's columns: scores of the moves into M_j (from j-1), into D_j
@@ -224,164 +222,263 @@ __global__ void __launch_bounds__(kHmmThreads) hmm_viterbi_kernel(const ah_ampli
         for (int l = 0; l < 4; ++l)
             em[k][l] = (j >= 1 && j <= m) ? e[j * 4 + l] : 0.0f;
     }
-    for (uint64_t ai = blockIdx.x; ai < n_amps; ai += gridDim.x) {
-        const ah_amplicon am = amps[ai];
-        bool ok = am.contig < n_contigs && am.start <= am.end;
-        if (ok)
-            ok = (uint64_t)am.end <= contig_off[am.contig + 1] - contig_off[am.contig] &&
-                 am.end - am.start <= (uint32_t)max_len;
-        if (!ok) { // checked on the host; a record that fails here is reported, not read
-            if (threadIdx.x == 0) {
-                atomicExch(err, kDevBounds);
-                score_out[ai] = kNeg;
-            }
-            continue;
-        }
-        const int n = (int)(am.end - am.start);
-        __syncthreads(); // the previous amplicon's letters are no longer read
-        decode_letters(am, planes, contig_off, seq, n);
-        // row 0: B = M_0; D_j reached from B through deletions
-        float pM[K], pI[K], pD[K];
+    // the delete chain's t_DD prefix of this thread's columns (the same for every amplicon)
+    float tdd_sum = 0.0f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            pM[k] = (c0 + k == 0) ? 0.0f : kNeg;
-            pI[k] = kNeg;
-            pD[k] = kNeg;
+    for (int k = 0; k < K; ++k)
+        tdd_sum += toD[k][kD];
+    const uint64_t n_groups = (n_amps + A - 1) / A;
+    for (uint64_t gi = blockIdx.x; gi < n_groups; gi += gridDim.x) {
+        int len[A];
+        uint32_t idx[A];
+        int rows = 0;
+        __syncthreads(); // the previous group's letters are no longer read
+#pragma unroll
+        for (int s = 0; s < A; ++s) {
+            const uint64_t q = gi * A + s;
+            len[s] = -1; // -1: no amplicon in this slot
+            idx[s] = 0;
+            if (q < n_amps) {
+                idx[s] = order[q];
+                const ah_amplicon am = amps[idx[s]];
+                bool ok = am.contig < n_contigs && am.start <= am.end;
+                if (ok)
+                    ok = (uint64_t)am.end <= contig_off[am.contig + 1] - contig_off[am.contig] &&
+                         am.end - am.start <= (uint32_t)max_len;
+                if (ok) {
+                    len[s] = (int)(am.end - am.start);
+                    decode_letters(am, planes, contig_off, seq + s * max_len, len[s]);
+                    rows = max(rows, len[s]);
+                } else if (threadIdx.x == 0) { // checked on the host; reported, not read
+                    atomicExch(err, kDevBounds);
+                    score_out[idx[s]] = kNeg;
+                }
+            }
         }
-        // the delete chain of a row from its M and I values (cur*: this row's)
-        auto delete_chain = [&](const float (&cM)[K], const float (&cI)[K], float (&cD)[K]) {
-            // left neighbour's M, I of this row
-            float lM = __shfl_up_sync(0xffffffffu, cM[K - 1], 1), lI = __shfl_up_sync(0xffffffffu, cI[K - 1], 1);
-            if (lane == 31) {
-                edge_cur[0][warp] = cM[K - 1];
-                edge_cur[1][warp] = cI[K - 1];
-            }
-            __syncthreads();
-            if (lane == 0) {
-                lM = warp > 0 ? edge_cur[0][warp - 1] : kNeg;
-                lI = warp > 0 ? edge_cur[1][warp - 1] : kNeg;
-            }
-            MaxPlus el[K], agg = {0.0f, kNeg};
+        float pM[A][K], pI[A][K], pD[A][K];
+#pragma unroll
+        for (int s = 0; s < A; ++s)
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const float pm = k ? cM[k - 1] : lM, pi = k ? cI[k - 1] : lI;
-                el[k] = {toD[k][kD], fmaxf(pm + toD[k][kM], pi + toD[k][kI])};
-                agg = mp_then(agg, el[k]);
+                pM[s][k] = (c0 + k == 0) ? 0.0f : kNeg;
+                pI[s][k] = kNeg;
+                pD[s][k] = kNeg;
             }
-            // inclusive warp scan of the thread aggregates, then across warps
-            MaxPlus inc = agg;
+        // the delete chains of a row from its M and I values
+        auto delete_chain = [&](const float (&cM)[A][K], const float (&cI)[A][K], float (&cD)[A][K]) {
+            float lM[A], lI[A];
+#pragma unroll
+            for (int s = 0; s < A; ++s) {
+                lM[s] = __shfl_up_sync(0xffffffffu, cM[s][K - 1], 1);
+                lI[s] = __shfl_up_sync(0xffffffffu, cI[s][K - 1], 1);
+                if (lane == 31) {
+                    edge_cur[s][0][warp] = cM[s][K - 1];
+                    edge_cur[s][1][warp] = cI[s][K - 1];
+                }
+            }
+            __syncthreads();
+            if (lane == 0)
+#pragma unroll
+                for (int s = 0; s < A; ++s) {
+                    lM[s] = warp > 0 ? edge_cur[s][0][warp - 1] : kNeg;
+                    lI[s] = warp > 0 ? edge_cur[s][1][warp - 1] : kNeg;
+                }
+            // per column: D_j = max(b_j, D_{j-1} + a_j); thread aggregate (a, b[s])
+            float eb[A][K], agg_b[A];
+#pragma unroll
+            for (int s = 0; s < A; ++s) {
+                float acc = kNeg;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const float pm = k ? cM[s][k - 1] : lM[s], pi = k ? cI[s][k - 1] : lI[s];
+                    eb[s][k] = fmaxf(pm + toD[k][kM], pi + toD[k][kI]);
+                    acc = fmaxf(eb[s][k], acc + toD[k][kD]);
+                }
+                agg_b[s] = acc;
+            }
+            // inclusive warp scan: (a1, b1) then (a2, b2) = (a1 + a2, max(b2, b1 + a2))
+            float inc_a = tdd_sum, inc_b[A];
+#pragma unroll
+            for (int s = 0; s < A; ++s)
+                inc_b[s] = agg_b[s];
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                MaxPlus o{__shfl_up_sync(0xffffffffu, inc.a, d), __shfl_up_sync(0xffffffffu, inc.b, d)};
+                const float oa = __shfl_up_sync(0xffffffffu, inc_a, d);
+#pragma unroll
+                for (int s = 0; s < A; ++s) {
+                    const float ob = __shfl_up_sync(0xffffffffu, inc_b[s], d);
+                    if (lane >= d)
+                        inc_b[s] = fmaxf(inc_b[s], ob + inc_a);
+                }
                 if (lane >= d)
-                    inc = mp_then(o, inc);
+                    inc_a = oa + inc_a;
             }
-            if (lane == 31)
-                wtot[warp] = inc;
+            if (lane == 31) {
+                wtot_a[warp] = inc_a;
+#pragma unroll
+                for (int s = 0; s < A; ++s)
+                    wtot_b[s][warp] = inc_b[s];
+            }
             __syncthreads();
             if (warp == 0) {
-                MaxPlus w = lane < nwarps ? wtot[lane] : MaxPlus{0.0f, kNeg};
+                float wa = lane < nwarps ? wtot_a[lane] : 0.0f, wb[A];
+#pragma unroll
+                for (int s = 0; s < A; ++s)
+                    wb[s] = lane < nwarps ? wtot_b[s][lane] : kNeg;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
-                    MaxPlus o{__shfl_up_sync(0xffffffffu, w.a, d), __shfl_up_sync(0xffffffffu, w.b, d)};
+                    const float oa = __shfl_up_sync(0xffffffffu, wa, d);
+#pragma unroll
+                    for (int s = 0; s < A; ++s) {
+                        const float ob = __shfl_up_sync(0xffffffffu, wb[s], d);
+                        if (lane >= d)
+                            wb[s] = fmaxf(wb[s], ob + wa);
+                    }
                     if (lane >= d)
-                        w = mp_then(o, w);
+                        wa = oa + wa;
                 }
                 // exclusive prefix of the warps
-                MaxPlus ex{__shfl_up_sync(0xffffffffu, w.a, 1), __shfl_up_sync(0xffffffffu, w.b, 1)};
+                const float xa = __shfl_up_sync(0xffffffffu, wa, 1);
                 if (lane < nwarps)
-                    wpre[lane] = lane ? ex : MaxPlus{0.0f, kNeg};
+                    wpre_a[lane] = lane ? xa : 0.0f;
+#pragma unroll
+                for (int s = 0; s < A; ++s) {
+                    const float xb = __shfl_up_sync(0xffffffffu, wb[s], 1);
+                    if (lane < nwarps)
+                        wpre_b[s][lane] = lane ? xb : kNeg;
+                }
             }
             __syncthreads();
-            MaxPlus ex{__shfl_up_sync(0xffffffffu, inc.a, 1), __shfl_up_sync(0xffffffffu, inc.b, 1)};
-            if (lane == 0)
-                ex = {0.0f, kNeg};
-            const MaxPlus pre = mp_then(wpre[warp], ex);
-            float d = pre.b; // D at column c0 - 1 (from D = -inf before column 0)
+            // this thread's exclusive prefix = (warps before) then (lanes before)
+            const float xa = __shfl_up_sync(0xffffffffu, inc_a, 1);
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                d = fmaxf(el[k].b, d + el[k].a);
-                cD[k] = d;
+            for (int s = 0; s < A; ++s) {
+                float xb = __shfl_up_sync(0xffffffffu, inc_b[s], 1);
+                if (lane == 0)
+                    xb = kNeg;
+                const float lane_a = lane ? xa : 0.0f;
+                float d = fmaxf(xb, wpre_b[s][warp] + lane_a); // D at column c0 - 1
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    d = fmaxf(eb[s][k], d + toD[k][kD]);
+                    cD[s][k] = d;
+                }
             }
         };
+        auto finish = [&](int i) { // amplicons whose last row is i: the holder of column m scores them
+#pragma unroll
+            for (int s = 0; s < A; ++s)
+                if (len[s] == i)
+#pragma unroll
+                    for (int k = 0; k < K; ++k)
+                        if (c0 + k == m)
+                            score_out[idx[s]] =
+                                fmaxf(fmaxf(pM[s][k] + t[m * 9 + kM * 3], pI[s][k] + t[m * 9 + kI * 3]),
+                                      pD[s][k] + t[m * 9 + kD * 3]);
+        };
+        __syncthreads(); // the letters are decoded
         delete_chain(pM, pI, pD);
-        for (int i = 1; i <= n; ++i) {
-            const int x = seq[i - 1];
-            // previous row at column c0 - 1
-            float lM = __shfl_up_sync(0xffffffffu, pM[K - 1], 1), lI = __shfl_up_sync(0xffffffffu, pI[K - 1], 1),
-                  lD = __shfl_up_sync(0xffffffffu, pD[K - 1], 1);
-            if (lane == 31) {
-                edge_prev[0][warp] = pM[K - 1];
-                edge_prev[1][warp] = pI[K - 1];
-                edge_prev[2][warp] = pD[K - 1];
+        finish(0);
+        for (int i = 1; i <= rows; ++i) {
+            float lM[A], lI[A], lD[A];
+#pragma unroll
+            for (int s = 0; s < A; ++s) {
+                lM[s] = __shfl_up_sync(0xffffffffu, pM[s][K - 1], 1);
+                lI[s] = __shfl_up_sync(0xffffffffu, pI[s][K - 1], 1);
+                lD[s] = __shfl_up_sync(0xffffffffu, pD[s][K - 1], 1);
+                if (lane == 31) {
+                    edge_prev[s][0][warp] = pM[s][K - 1];
+                    edge_prev[s][1][warp] = pI[s][K - 1];
+                    edge_prev[s][2][warp] = pD[s][K - 1];
+                }
             }
             __syncthreads();
-            if (lane == 0) {
-                lM = warp > 0 ? edge_prev[0][warp - 1] : kNeg;
-                lI = warp > 0 ? edge_prev[1][warp - 1] : kNeg;
-                lD = warp > 0 ? edge_prev[2][warp - 1] : kNeg;
-            }
-            float cM[K], cI[K], cD[K];
+            if (lane == 0)
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const float qm = k ? pM[k - 1] : lM, qi = k ? pI[k - 1] : lI, qd = k ? pD[k - 1] : lD;
-                const float ex = x < 4 ? em[k][x] : 0.0f;
-                cM[k] = ex + fmaxf(fmaxf(qm + toM[k][kM], qi + toM[k][kI]), qd + toM[k][kD]);
-                cI[k] = fmaxf(fmaxf(pM[k] + toI[k][kM], pI[k] + toI[k][kI]), pD[k] + toI[k][kD]);
+                for (int s = 0; s < A; ++s) {
+                    lM[s] = warp > 0 ? edge_prev[s][0][warp - 1] : kNeg;
+                    lI[s] = warp > 0 ? edge_prev[s][1][warp - 1] : kNeg;
+                    lD[s] = warp > 0 ? edge_prev[s][2][warp - 1] : kNeg;
+                }
+            float cM[A][K], cI[A][K], cD[A][K];
+#pragma unroll
+            for (int s = 0; s < A; ++s) {
+                const int x = i <= len[s] ? seq[s * max_len + i - 1] : 4;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const float qm = k ? pM[s][k - 1] : lM[s], qi = k ? pI[s][k - 1] : lI[s],
+                                qd = k ? pD[s][k - 1] : lD[s];
+                    // (a select, not an indexed load: the emission scores stay in registers)
+                    const float ex = x == 0 ? em[k][0] : x == 1 ? em[k][1] : x == 2 ? em[k][2] : x == 3 ? em[k][3] : 0.0f;
+                    cM[s][k] = ex + fmaxf(fmaxf(qm + toM[k][kM], qi + toM[k][kI]), qd + toM[k][kD]);
+                    cI[s][k] = fmaxf(fmaxf(pM[s][k] + toI[k][kM], pI[s][k] + toI[k][kI]), pD[s][k] + toI[k][kD]);
+                }
             }
             delete_chain(cM, cI, cD);
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                pM[k] = cM[k];
-                pI[k] = cI[k];
-                pD[k] = cD[k];
-            }
-        }
-        // the thread holding column m ends the path
+            for (int s = 0; s < A; ++s)
 #pragma unroll
-        for (int k = 0; k < K; ++k)
-            if (c0 + k == m)
-                score_out[ai] = fmaxf(fmaxf(pM[k] + t[m * 9 + kM * 3], pI[k] + t[m * 9 + kI * 3]),
-                                      pD[k] + t[m * 9 + kD * 3]);
+                for (int k = 0; k < K; ++k) {
+                    pM[s][k] = cM[s][k];
+                    pI[s][k] = cI[s][k];
+                    pD[s][k] = cD[s][k];
+                }
+            finish(i);
+        }
     }
 }
 
-template <int K>
-void launch_k(const ah_amplicon *amps, uint64_t n, const uint32_t *planes, const uint64_t *contig_off,
-              uint32_t n_contigs, const float *t, const float *e, int m, int max_len, float *out, int *err, int sms,
-              cudaStream_t s)
+template <int K, int A>
+void launch_k(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
+              const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m, int max_len,
+              float *out, int *err, int sms, cudaStream_t s)
 {
     const int threads = std::min(kHmmThreads, 32 * (((m + 1) + 32 * K - 1) / (32 * K)));
-    const size_t smem = (size_t)max_len;
-    if (smem > 48 * 1024)
-        AH_CUDA(cudaFuncSetAttribute(hmm_viterbi_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = (size_t)A * (size_t)max_len;
+    AH_CUDA(cudaFuncSetAttribute(hmm_viterbi_kernel<K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::max<size_t>(smem, 1)));
     int per_sm = 1;
-    AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hmm_viterbi_kernel<K>, threads, smem));
-    const uint64_t blocks = std::min<uint64_t>(n, (uint64_t)sms * (uint64_t)std::max(1, per_sm));
-    hmm_viterbi_kernel<K><<<(unsigned)blocks, threads, smem, s>>>(amps, n, planes, contig_off, n_contigs, t, e, m,
-                                                                   max_len, out, err);
+    AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hmm_viterbi_kernel<K, A>, threads, smem));
+    const uint64_t groups = (n + A - 1) / A;
+    const uint64_t blocks = std::min<uint64_t>(groups, (uint64_t)sms * (uint64_t)std::max(1, per_sm));
+    hmm_viterbi_kernel<K, A><<<(unsigned)blocks, threads, smem, s>>>(amps, order, n, planes, contig_off, n_contigs, t,
+                                                                      e, m, max_len, out, err);
     AH_CUDA(cudaGetLastError());
 }
 
 } // namespace
 
-void launch_hmm_viterbi(const ah_amplicon *amps, uint64_t n, const uint32_t *planes, const uint64_t *contig_off,
-                        uint32_t n_contigs, const float *t, const float *e, int m, int max_len, float *score_out,
-                        int *err, int sms, cudaStream_t s)
+void launch_hmm_viterbi(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
+                        const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m,
+                        int max_len, float *score_out, int *err, int sms, cudaStream_t s)
 {
     if (n == 0)
         return;
     const int cols = m + 1;
-    if (cols <= kHmmThreads)
-        launch_k<1>(amps, n, planes, contig_off, n_contigs, t, e, m, max_len, score_out, err, sms, s);
-    else if (cols <= 2 * kHmmThreads)
-        launch_k<2>(amps, n, planes, contig_off, n_contigs, t, e, m, max_len, score_out, err, sms, s);
-    else if (cols <= 4 * kHmmThreads)
-        launch_k<4>(amps, n, planes, contig_off, n_contigs, t, e, m, max_len, score_out, err, sms, s);
-    else if (cols <= 6 * kHmmThreads)
-        launch_k<6>(amps, n, planes, contig_off, n_contigs, t, e, m, max_len, score_out, err, sms, s);
-    else
-        throw Error(AH_ERR_ARG, "ah_hmm_score: profile longer than " + std::to_string(kHmmMaxColumns) + " columns");
+    // AH_HMM_VARIANT="K,A" picks columns per thread and amplicons per block (profiling aid)
+    int vk = 0, va = 0;
+    if (const char *v = getenv("AH_HMM_VARIANT"))
+        if (sscanf(v, "%d,%d", &vk, &va) != 2)
+            vk = va = 0;
+#define AH_HMM_TRY(K_, A_)                                                                                      \
+    if ((vk == 0 || (vk == K_ && va == A_)) && cols <= K_ * kHmmThreads) {                                     \
+        launch_k<K_, A_>(amps, order, n, planes, contig_off, n_contigs, t, e, m, max_len, score_out, err, sms, s); \
+        return;                                                                                                \
+    }
+    if (vk) { // the named variant (when it covers the profile)
+        AH_HMM_TRY(1, 4)
+        AH_HMM_TRY(2, 2)
+        AH_HMM_TRY(4, 1)
+        AH_HMM_TRY(4, 2)
+        AH_HMM_TRY(8, 1)
+        vk = va = 0;
+    }
+    // default (measured on 639 columns: 4 columns x 2 amplicons 398 GCUPS; 2 x 2 272; 4 x 1 315;
+    // 8 x 1 234, register-capped); longer profiles take 6 columns x 1 amplicon
+    AH_HMM_TRY(4, 2)
+    AH_HMM_TRY(6, 1)
+#undef AH_HMM_TRY
+    throw Error(AH_ERR_ARG, "ah_hmm_score: profile longer than " + std::to_string(kHmmMaxColumns) + " columns");
 }
 
 } // namespace ah
