@@ -427,10 +427,13 @@ ah_status ah_generate_bases(ah_ctx *ctx, uint64_t seed, const ah_gen_segment *se
  * the stream) and times host sections, 0 stops.  Device
  * stages: "pack", "tables" (ah_load_genomes), "scan", "sort", "decode" (ah_scan),
  * "validate" (record checks of ah_tm / ah_pair), "tm", "pair", "fetch",
- * "sweep" (ah_tm_sweep), "amplitype" (ah_amplitypes).  Host
- * sections (wall time inside the library): "host.load", "host.load.alloc",
- * "host.load.tables", "host.load.pack", "host.run", "host.run.prep",
- * "host.run.launch", "host.run.wait", "host.unload".  ah_get_profile returns,
+ * "sweep" (ah_tm_sweep), "amplitype" (ah_amplitypes), "generate"
+ * (ah_generate_bases), "hmm" (ah_hmm_score).  Host sections (wall time
+ * inside the library): "host.load", "host.load.alloc", "host.load.tables",
+ * "host.load.pack", "host.run", "host.run.prep", "host.run.launch",
+ * "host.run.wait", "host.unload", and for a server's batches
+ * "host.serve.batch", "host.serve.tiles", "host.serve.device",
+ * "host.serve.filter_wait", "host.serve.fetch".  ah_get_profile returns,
  * for one stage or section, the summed milliseconds, the kernels launched
  * and the number of bracketed calls; stage = NULL gives the sums over device
  * stages and the count of every kernel the library launched since the last
@@ -547,7 +550,7 @@ ah_status ah_serve_stop(ah_server *srv);
  *   move that does not exist) and match emissions e[(m + 1) * 4] (row 0 is
  *   0), host arrays.
  * ah_hmm_score: one score per amplicon of the set (host or device records and
- *   scores); amplicons of up to 65,536 letters.  Errors: AH_ERR_ARG (unknown
+ *   scores); amplicons of up to 16,384 letters.  Errors: AH_ERR_ARG (unknown
  *   id, a record outside its contig, too long), AH_ERR_CUDA. */
 ah_status ah_hmm_build(ah_ctx *ctx, const char *seqs, const uint64_t *offsets, uint64_t n, uint32_t *hmm_id_out);
 ah_status ah_hmm_tables(ah_ctx *ctx, uint32_t hmm_id, uint64_t *m_out, uint64_t *reference_out, float *t_out,
