@@ -609,6 +609,7 @@ const ScanTuning &tuning_for(ah_ctx *c, const std::vector<ScanPattern> &pats)
 
 // Launch the generated scan kernel over tiles [0, n_tiles) of a set.
 // Scan n_tiles tiles: the first n_tiles of the set, or tile_list[0 .. n_tiles) (device) when given.
+// The caller resets the flag block (the work counter included) on the same stream first.
 void launch_scan(ah_ctx *c, ScanKernel *k, const GenomeSet &gs, uint64_t n_tiles, uint64_t *keys, uint64_t cap,
                  int pbits, cudaStream_t st, const uint64_t *tile_list = nullptr)
 {
@@ -616,8 +617,7 @@ void launch_scan(ah_ctx *c, ScanKernel *k, const GenomeSet &gs, uint64_t n_tiles
     const uint32_t *planes = gs.planes;
     const uint64_t *coff = gs.contig_off;
     uint32_t nc = gs.n_contigs;
-    uint64_t *work = c->d_flags + kFlagWork;
-    AH_CUDA(cudaMemsetAsync(work, 0, sizeof(uint64_t), st));
+    uint64_t *work = c->d_flags + kFlagWork; // zeroed with the flag block by the caller's reset_flags
     const uint32_t *tcont = gs.tile_contig;
     void *args[] = {&planes,       &n_tiles, &coff, &nc,   &keys,      &cap,  &c->d_counter,
                     &pbits,        &c->d_err, &work, &tile_list, &tcont};
