@@ -229,7 +229,8 @@ def traffic_record(kernel: str):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 1000 plain, 2 batched passes, 10 HMM passes)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
@@ -253,6 +254,8 @@ def main():
     ap.add_argument("--dump-path", default="gpurun_out/large_sample.npz")
     ap.add_argument("--check-dump", default=None, help="oracle check of a large-form dump (CPU only)")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = {"batched": 2, "hmm": 10}.get(args.form, 1000)
     if args.check_dump:
         sys.exit(check_large_dump(args.check_dump))
     if args.impl == "reference":
