@@ -255,7 +255,7 @@ def main():
     ap.add_argument("--check-dump", default=None, help="oracle check of a large-form dump (CPU only)")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = {"batched": 2, "hmm": 10}.get(args.form, 1000)
+        args.steps = 2 if args.impl == "reference" else {"batched": 2, "hmm": 10}.get(args.form, 1000)
     if args.check_dump:
         sys.exit(check_large_dump(args.check_dump))
     if args.impl == "reference":
