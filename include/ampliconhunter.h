@@ -175,8 +175,10 @@ size_t ah_device_bytes(const ah_ctx *ctx);
  * last n_bases.  contig_genome (host): genome id of each contig.
  * The library packs the sequence on the device into its own layout (4 one-hot
  * bitplanes A/C/G/T) and returns an id in *set_id_out.  Host arrays are not
- * referenced after the call.  A device seq is read by work queued on
- * `stream` (stream-ordered, like any CUDA call): it must stay valid until
+ * referenced after the call: a host seq is copied in chunks through staging
+ * buffers on the device (the copies overlap the packing) and the call waits
+ * for the copies, not for the packing.  A device seq is read by work queued
+ * on `stream` (stream-ordered, like any CUDA call): it must stay valid until
  * that work has run; the call returns without waiting for it.  Every later
  * call that reads the set orders itself after the packing, whatever stream
  * it is given.  A device-side failure of the packing is reported by the next
@@ -338,7 +340,7 @@ ah_status ah_run(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32_
  * exactly as ah_run does (same results, counts and errors, including
  * AH_ERR_OVERFLOW).  `out` and its buffers, the set and the pairs must stay
  * as they are until ah_run_end returns.  While a run is pending the only
- * calls accepted on the context are ah_load_genomes with a device sequence,
+ * calls accepted on the context are ah_load_genomes (not reversed),
  * ah_run_end, ah_get_profile, ah_last_error, ah_device_bytes and ah_destroy;
  * every other call returns AH_ERR_ARG.  When the last run needed the
  * step-by-step form, ah_run_begin already does the whole run and

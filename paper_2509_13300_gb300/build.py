@@ -51,6 +51,24 @@ def source_digest() -> str:
     return h.hexdigest()[:16]
 
 
+# the source files that define each profiled kernel (with the internal header)
+KERNEL_SOURCES = {"ah_scan_kernel": ["scan_jit.cu"], "pack_kernel": ["pack.cu"], "tm_kernel": ["tm.cu"],
+                  "rank_sort_decode_kernel": ["sites.cu"], "hmm_viterbi_kernel": ["hmm.cu"]}
+
+
+def kernel_digest(kernel: str) -> str | None:
+    """Hash of one kernel's sources: a profile of the kernel stays valid while it matches."""
+    import hashlib
+    files = KERNEL_SOURCES.get(kernel)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for f in files + ["ah_internal.h"]:
+        h.update(f.encode())
+        h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     """Compile what changed and link the library; returns its path."""
     extra = extra or []

@@ -44,6 +44,8 @@ struct ah_ctx {
     cudaStream_t run_stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_packed[2] = {nullptr, nullptr};
+    cudaEvent_t ev_load_start = nullptr; // a host load's copies start after the caller's earlier work
+    cudaEvent_t ev_last_copy = nullptr;  // recorded after a host load's last copy
     uint64_t *h_flags = nullptr;     // pinned host mirror of the flag block
     bool flags_dirty = false;        // work was queued that may set the error word, not read since
     std::vector<cudaEvent_t> set_events; // free "ready" events of genome sets
@@ -1456,6 +1458,8 @@ ah_status ah_create(int device, size_t mem_budget_bytes, ah_ctx **out)
             AH_CUDA(cudaEventCreateWithFlags(&c->ev_copied[b], cudaEventDisableTiming));
             AH_CUDA(cudaEventCreateWithFlags(&c->ev_packed[b], cudaEventDisableTiming));
         }
+        AH_CUDA(cudaEventCreateWithFlags(&c->ev_load_start, cudaEventDisableTiming));
+        AH_CUDA(cudaEventCreateWithFlags(&c->ev_last_copy, cudaEventDisableTiming));
     });
     if (st != AH_OK) {
         g_create_err = c->err;
@@ -1518,6 +1522,10 @@ void ah_destroy(ah_ctx *c)
         if (c->ev_packed[b])
             cudaEventDestroy(c->ev_packed[b]);
     }
+    if (c->ev_load_start)
+        cudaEventDestroy(c->ev_load_start);
+    if (c->ev_last_copy)
+        cudaEventDestroy(c->ev_last_copy);
     if (c->stream)
         cudaStreamDestroy(c->stream);
     delete c;
@@ -1645,9 +1653,8 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
         gs->tile_contig = (uint32_t *)((char *)gs->contig_off + ob + gb);
         gs->bytes = plane_bytes + table_bytes;
         const bool dev_seq = n_bases && is_device_ptr(c, seq);
-        // a queued run leaves the flag block and the staging scratch alone only for device input
-        require((dev_seq && !reversed) || !c->pend.active, AH_ERR_ARG,
-                "a run is pending: host input and reversed sets are loaded after ah_run_end");
+        // a queued run leaves the flag block alone for plain loads (host or device input)
+        require(!reversed || !c->pend.active, AH_ERR_ARG, "a run is pending: reversed sets are loaded after ah_run_end");
         // the packing first (it reads no contig table), then the tables' copies
         std::vector<void *> temp; // freed once the packing is done (reversed loads)
         if (gs->n_tiles && reversed) {
@@ -1692,9 +1699,12 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
                 const uint64_t stage_bytes = chunk_tiles * kTileBases + kTileBases;
                 uint8_t *stage[2] = {(uint8_t *)scratch(c, "load_stage0", stage_bytes),
                                      (uint8_t *)scratch(c, "load_stage1", stage_bytes)};
-                // the copy stream starts after everything queued so far on st
-                AH_CUDA(cudaEventRecord(c->ev_packed[0], st));
+                // the copy stream starts after everything queued so far on st, and after
+                // the packing of an earlier load from these staging buffers
                 AH_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[0], 0));
+                AH_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[1], 0));
+                AH_CUDA(cudaEventRecord(c->ev_load_start, st));
+                AH_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_load_start, 0));
                 uint64_t i = 0;
                 for (uint64_t t0 = 0; t0 < gs->n_tiles; t0 += chunk_tiles, ++i) {
                     const int b = (int)(i & 1);
@@ -1712,6 +1722,7 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
                     }
                     AH_CUDA(cudaEventRecord(c->ev_packed[b], st));
                 }
+                AH_CUDA(cudaEventRecord(c->ev_last_copy, c->copy_stream));
             }
         }
         {
@@ -1756,7 +1767,15 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
         gs->ready = c->set_events.back();
         c->set_events.pop_back();
         AH_CUDA(cudaEventRecord(gs->ready, st));
-        if (!dev_seq || reversed) { // the caller's host buffer may be reused once this call returns
+        if (!dev_seq && !reversed) {
+            // the caller's host buffer may be reused once this call returns: wait for
+            // the copies only; the packing stays queued (like a device-input load, a
+            // failure reaches the next call that synchronises), so a host load may
+            // also overlap a pending run
+            if (gs->n_tiles)
+                AH_CUDA(cudaEventSynchronize(c->ev_last_copy));
+            c->flags_dirty = true;
+        } else if (reversed) { // the temporaries are freed once the packing is done
             try {
                 check_flags(c, st);
             } catch (...) {

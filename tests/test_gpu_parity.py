@@ -454,10 +454,12 @@ def test_run_past_the_one_synchronisation_sizes(ctx, case):
     ctx.ah_unload_genomes(sid)
 
 
-def test_run_begin_end_pipeline(ctx):
+@pytest.mark.parametrize("source", ["device", "host"])
+def test_run_begin_end_pipeline(ctx, source):
     """ah_run_begin / ah_run_end give ah_run's records; while a run is pending
     other calls are refused; three sets run as a pipeline (the next set packs on
-    a second stream after the current scan) each match the oracle."""
+    a second stream after the current scan, or, from host memory, is copied
+    and packed while the run computes) each match the oracle."""
     import torch
     ws = [synth.collection(seed=s, n_genomes=2, len_lo=3e5, len_hi=6e5) for s in (4, 5, 6)]
     pair = dict(ws[0].pairs[0], tm_min=50.0)  # one pair for every set (the generator draws one per seed)
@@ -472,7 +474,7 @@ def test_run_begin_end_pipeline(ctx):
         want.append((o, seqs, offs))
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     scan_done = torch.cuda.Event()
-    dev = [torch.from_numpy(w.seq).cuda() for w in ws]
+    dev = [torch.from_numpy(w.seq).cuda() for w in ws] if source == "device" else [w.seq for w in ws]
     torch.cuda.synchronize()
     cap = 20000
     u8 = dict(dtype=torch.uint8, device="cuda")
@@ -490,7 +492,8 @@ def test_run_begin_end_pipeline(ctx):
         assert e.value.status == ah.AH_ERR_ARG
         nxt = None
         if i + 1 < len(ws):
-            streams[(i + 1) % 2].wait_event(scan_done)
+            if source == "device":
+                streams[(i + 1) % 2].wait_event(scan_done)
             nxt = ctx.ah_load_genomes(dev[i + 1], len(ws[i + 1].seq), ws[i + 1].contig_off,
                                       ws[i + 1].contig_genome, streams[(i + 1) % 2])
         ctx.ah_run_end(out)
