@@ -407,11 +407,15 @@ ah_status ah_amplitypes(ah_ctx *ctx, uint32_t set_id, const ah_amplicon *amplico
  * seed high)); in the segment holding P, the base is `letter` when non-zero,
  * else A if u < t_a, C if u < t_c, G if u < t_g, else T.  Segments (host) tile
  * the collection in order: segment i covers [end of i-1 (0 for the first),
- * end).  Patches (host, may be empty) then set out[pos - base0] = byte for
- * every pos inside the range.  out (device): n bytes for positions
+ * end).  Patches (may be empty) then set out[pos - base0] = byte for every
+ * pos inside the range.  out (device): n bytes for positions
  * [base0, base0 + n); base0 must be a multiple of 4, and the segments must
- * reach base0 + n.  Waits for the work before returning.
- * Errors: AH_ERR_ARG, AH_ERR_CUDA. */
+ * reach base0 + n.  Segments and patches are either host arrays (checked,
+ * copied, and the call waits for the work) or device arrays of the whole
+ * collection (stream-ordered: the call returns without waiting; a range the
+ * segments do not cover is written as N and reported as AH_ERR_DEVICE_CHECK
+ * by the next call that synchronises).
+ * Errors: AH_ERR_ARG, AH_ERR_CUDA, AH_ERR_DEVICE_CHECK. */
 typedef struct {
     uint64_t end;
     uint32_t t_a, t_c, t_g;

@@ -321,8 +321,16 @@ class Context:
                                             ctypes.byref(nt), _stream(stream)))
         return variant[:n], rows[:nr.value], nv.value, nt.value
 
-    def generate_bases(self, coll, base0: int, n: int, out, stream=None):
-        """Bases [base0, base0 + n) of a countergen collection into device memory `out` (torch uint8)."""
+    def generate_bases(self, coll, base0: int, n: int, out, stream=None, tables=None):
+        """Bases [base0, base0 + n) of a countergen collection into device memory `out` (torch uint8).
+        tables: the collection's segments and patches already on the device (device_tables());
+        the call is then stream-ordered, else host slices are passed and the call waits."""
+        if tables is not None:
+            segs, ns, pp, pb, npch = tables
+            self._check(self._lib.ah_generate_bases(self.h, coll.seed, _ptr(segs), ns, _ptr(pp) if npch else None,
+                                                    _ptr(pb) if npch else None, npch, base0, n, _ptr(out),
+                                                    _stream(stream)))
+            return
         ends = coll.segments["end"]
         s0 = int(np.searchsorted(ends, base0, side="right"))  # the segments that hold the range
         s1 = min(len(ends), int(np.searchsorted(ends, base0 + max(n, 1) - 1, side="right")) + 1)
@@ -334,6 +342,15 @@ class Context:
         self._check(self._lib.ah_generate_bases(self.h, coll.seed, _ptr(segs), len(segs), _ptr(pp) if len(pp) else None,
                                                 _ptr(pb) if len(pb) else None, len(pp), base0, n, _ptr(out),
                                                 _stream(stream)))
+
+    @staticmethod
+    def device_tables(coll):
+        """A collection's segments and patches as device tensors (for generate_bases)."""
+        import torch
+        segs = torch.from_numpy(np.ascontiguousarray(coll.segments).view(np.uint8).copy()).cuda()
+        pp = torch.from_numpy(np.ascontiguousarray(coll.patch_pos, dtype=np.uint64).view(np.uint8).copy()).cuda()
+        pb = torch.from_numpy(np.ascontiguousarray(coll.patch_bytes, dtype=np.uint8).copy()).cuda()
+        return segs, len(coll.segments), pp, pb, len(coll.patch_pos)
 
     def ah_run_end(self, out: RunOut) -> RunOut:
         self._check(self._lib.ah_run_end(self.h), out.n_sites)

@@ -2254,14 +2254,29 @@ ah_status ah_generate_bases(ah_ctx *c, uint64_t seed, const ah_gen_segment *segm
         if (n == 0)
             return;
         require(out && is_device_ptr(c, out), AH_ERR_ARG, "ah_generate_bases: out must be device memory");
-        require(!is_device_ptr(c, segments) && (n_patches == 0 || !is_device_ptr(c, patch_pos)), AH_ERR_ARG,
-                "ah_generate_bases: segments and patches are host arrays");
+        cudaStream_t st = stream_of(c, stream);
+        const bool dev_tables = is_device_ptr(c, segments);
+        if (dev_tables) {
+            // device tables: stream-ordered, no host pass over them; a range the
+            // segments do not cover is written as N and reported by the next call
+            // that synchronises
+            require(n_patches == 0 || (is_device_ptr(c, patch_pos) && is_device_ptr(c, patch_bytes)), AH_ERR_ARG,
+                    "ah_generate_bases: device segments take device patches");
+            {
+                Stage sg(c, "generate", st, n_patches ? 2 : 1);
+                launch_generate_bases(segments, n_segments, seed, patch_pos, patch_bytes, n_patches, base0, n, out,
+                                      c->d_err, st);
+            }
+            c->flags_dirty = true;
+            return;
+        }
+        require(n_patches == 0 || (!is_device_ptr(c, patch_pos) && !is_device_ptr(c, patch_bytes)), AH_ERR_ARG,
+                "ah_generate_bases: host segments take host patches");
         for (uint64_t i = 0; i < n_segments; ++i)
             require(i == 0 || segments[i].end >= segments[i - 1].end, AH_ERR_ARG,
                     "ah_generate_bases: segment ends must not decrease");
         require(segments[n_segments - 1].end >= base0 + n, AH_ERR_ARG,
                 "ah_generate_bases: the segments end before the range does");
-        cudaStream_t st = stream_of(c, stream);
         auto *segs = (ah_gen_segment *)scratch(c, "gen_segs", n_segments * sizeof(ah_gen_segment));
         AH_CUDA(cudaMemcpyAsync(segs, segments, n_segments * sizeof(ah_gen_segment), cudaMemcpyHostToDevice, st));
         uint64_t *pp = nullptr;
@@ -2272,10 +2287,12 @@ ah_status ah_generate_bases(ah_ctx *c, uint64_t seed, const ah_gen_segment *segm
             AH_CUDA(cudaMemcpyAsync(pp, patch_pos, n_patches * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
             AH_CUDA(cudaMemcpyAsync(pb, patch_bytes, n_patches, cudaMemcpyHostToDevice, st));
         }
+        reset_flags(c, st);
         {
             Stage sg(c, "generate", st, n_patches ? 2 : 1);
-            launch_generate_bases(segs, n_segments, seed, pp, pb, n_patches, base0, n, out, st);
+            launch_generate_bases(segs, n_segments, seed, pp, pb, n_patches, base0, n, out, c->d_err, st);
         }
+        check_flags(c, st);
         AH_CUDA(cudaStreamSynchronize(st));
     });
 }

@@ -326,7 +326,7 @@ void launch_amplitype_rows(const uint32_t *gid, const uint32_t *type, uint64_t m
 // gen.cu: counter-based synthetic bases (device segments and patches)
 void launch_generate_bases(const ah_gen_segment *segs, uint64_t n_segs, uint64_t seed, const uint64_t *patch_pos,
                            const uint8_t *patch_bytes, uint64_t n_patches, uint64_t base0, uint64_t n, uint8_t *out,
-                           cudaStream_t s);
+                           int *err, cudaStream_t s);
 
 // fetch.cu
 // lengths of the amplicons; a record outside its contig sets *err = kDevBounds (length 0)

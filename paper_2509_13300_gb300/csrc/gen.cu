@@ -31,14 +31,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 
 constexpr int kGenThreads = 256;
-constexpr uint64_t kGenBlock = 4096; // positions per block (4 per Philox call, 4 calls per thread)
-
-__device__ __forceinline__ uint8_t gen_letter(const ah_gen_segment &s, uint32_t u)
-{
-    if (s.letter)
-        return (uint8_t)s.letter;
-    return u < s.t_a ? 'A' : (u < s.t_c ? 'C' : (u < s.t_g ? 'G' : 'T'));
-}
+constexpr int kGenQuads = 16;                                        // consecutive Philox calls per thread
+constexpr uint64_t kGenBlock = 4ull * kGenQuads * kGenThreads;      // 16,384 positions per block
+constexpr int kGenStage = 128;                                       // segments staged in shared memory
 
 // first segment whose end is above P, searched in [lo, hi)
 __device__ __forceinline__ uint64_t seg_of(const ah_gen_segment *__restrict__ segs, uint64_t lo, uint64_t hi, uint64_t P)
@@ -53,11 +48,17 @@ __device__ __forceinline__ uint64_t seg_of(const ah_gen_segment *__restrict__ se
     return lo;
 }
 
-__global__ void __launch_bounds__(kGenThreads) gen_bases_kernel(const ah_gen_segment *__restrict__ segs,
+// Each thread draws kGenQuads consecutive quads (64 consecutive positions):
+// its segment is found once and advanced as positions pass segment ends; the
+// block's segments are staged in shared memory when they fit; four quads
+// leave as one 16-byte store when aligned.
+__global__ void __launch_bounds__(kGenThreads, 1) gen_bases_kernel(const ah_gen_segment *__restrict__ segs,
                                                                  uint64_t n_segs, uint32_t k0, uint32_t k1,
-                                                                 uint64_t base0, uint64_t n, uint8_t *__restrict__ out)
+                                                                 uint64_t base0, uint64_t n, uint8_t *__restrict__ out,
+                                                                 int *__restrict__ err)
 {
     __shared__ uint64_t bracket[2];
+    __shared__ ah_gen_segment st[kGenStage];
     const uint64_t p0 = base0 + (uint64_t)blockIdx.x * kGenBlock; // multiple of 4 (base0 is)
     const uint64_t p1 = min(base0 + n, p0 + kGenBlock);
     if (threadIdx.x == 0) {
@@ -66,25 +67,70 @@ __global__ void __launch_bounds__(kGenThreads) gen_bases_kernel(const ah_gen_seg
     }
     __syncthreads();
     const uint64_t s_lo = bracket[0], s_hi = bracket[1];
-    for (uint64_t q = p0 / 4 + threadIdx.x; q * 4 < p1; q += kGenThreads) {
+    if (s_lo >= n_segs || segs[s_hi - 1].end < p1) { // the segments end before this block's range
+        for (uint64_t P = p0 + threadIdx.x; P < p1; P += kGenThreads)
+            out[P - base0] = 'N';
+        if (threadIdx.x == 0)
+            atomicExch(err, kDevBounds);
+        return;
+    }
+    const bool staged = s_hi - s_lo <= (uint64_t)kGenStage;
+    if (staged)
+        for (uint64_t i = threadIdx.x; i < s_hi - s_lo; i += kGenThreads)
+            st[i] = segs[s_lo + i];
+    __syncthreads();
+    const ah_gen_segment *sg = staged ? st : segs + s_lo; // index relative to s_lo
+    const uint64_t nsg = s_hi - s_lo;
+    const uint64_t q0 = p0 / 4 + (uint64_t)threadIdx.x * kGenQuads;
+    if (q0 * 4 >= p1)
+        return;
+    uint64_t s = seg_of(sg, 0, nsg, q0 * 4);
+    // the current segment's fields in registers, reloaded only when a position passes its end;
+    // positions counted from the thread's first one (32-bit)
+    const uint64_t pbase = q0 * 4;
+    auto rel_end = [&](uint64_t i) -> uint32_t { // segment end relative to pbase, saturated
+        const uint64_t e = sg[i].end;
+        return e <= pbase ? 0u : (e - pbase >= 0xffffffffull ? 0xffffffffu : (uint32_t)(e - pbase));
+    };
+    uint32_t send = rel_end(s), ta = sg[s].t_a, tc = sg[s].t_c, tg = sg[s].t_g, lt = sg[s].letter;
+    uint32_t words[kGenQuads];
+#pragma unroll
+    for (int j = 0; j < kGenQuads; ++j) {
+        const uint64_t q = q0 + j;
         const uint4 r = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), 0u, 0u), k0, k1);
         const uint32_t u[4] = {r.x, r.y, r.z, r.w};
-        uint8_t b[4];
-        uint64_t s = seg_of(segs, s_lo, s_hi, q * 4);
+        uint32_t w = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint64_t P = q * 4 + j;
-            while (s + 1 < s_hi && segs[s].end <= P)
+        for (int x = 0; x < 4; ++x) {
+            const uint32_t rp = 4u * j + x; // position - pbase
+            while (rp >= send && s + 1 < nsg) {
                 ++s;
-            b[j] = gen_letter(segs[s], u[j]);
+                send = rel_end(s);
+                ta = sg[s].t_a;
+                tc = sg[s].t_c;
+                tg = sg[s].t_g;
+                lt = sg[s].letter;
+            }
+            const uint32_t v = u[x];
+            const uint32_t letter = lt ? lt : (v < ta ? 'A' : (v < tc ? 'C' : (v < tg ? 'G' : 'T')));
+            w |= letter << (8 * x);
         }
-        const uint64_t o = q * 4 - base0;
-        if (q * 4 + 4 <= p1 && ((reinterpret_cast<uintptr_t>(out) + o) & 3) == 0) {
-            *reinterpret_cast<uint32_t *>(out + o) = b[0] | (uint32_t)b[1] << 8 | (uint32_t)b[2] << 16 | (uint32_t)b[3] << 24;
-        } else {
-            for (int j = 0; j < 4 && q * 4 + j < p1; ++j)
-                out[o + j] = b[j];
-        }
+        words[j] = w;
+    }
+    const uint64_t o = q0 * 4 - base0;
+    const bool full = q0 * 4 + 4 * kGenQuads <= p1;
+    if (full && ((reinterpret_cast<uintptr_t>(out) + o) & 15) == 0) {
+#pragma unroll
+        for (int j = 0; j < kGenQuads; j += 4)
+            *reinterpret_cast<uint4 *>(out + o + 4 * j) = make_uint4(words[j], words[j + 1], words[j + 2], words[j + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kGenQuads; ++j)
+            for (int x = 0; x < 4; ++x) {
+                const uint64_t P = (q0 + j) * 4 + x;
+                if (P < p1)
+                    out[P - base0] = (uint8_t)(words[j] >> (8 * x));
+            }
     }
 }
 
@@ -102,7 +148,7 @@ __global__ void gen_patch_kernel(const uint64_t *__restrict__ pos, const uint8_t
 
 void launch_generate_bases(const ah_gen_segment *segs, uint64_t n_segs, uint64_t seed, const uint64_t *patch_pos,
                            const uint8_t *patch_bytes, uint64_t n_patches, uint64_t base0, uint64_t n, uint8_t *out,
-                           cudaStream_t s)
+                           int *err, cudaStream_t s)
 {
     if (n == 0)
         return;
@@ -110,7 +156,7 @@ void launch_generate_bases(const ah_gen_segment *segs, uint64_t n_segs, uint64_t
     if (blocks > 0x7fffffffull)
         throw Error(AH_ERR_ARG, "ah_generate_bases: range too large for one call");
     gen_bases_kernel<<<(unsigned)blocks, kGenThreads, 0, s>>>(segs, n_segs, (uint32_t)seed, (uint32_t)(seed >> 32),
-                                                               base0, n, out);
+                                                               base0, n, out, err);
     AH_CUDA(cudaGetLastError());
     if (n_patches) {
         const uint64_t pb = std::min<uint64_t>((n_patches + 255) / 256, 8192);

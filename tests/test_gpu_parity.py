@@ -651,6 +651,17 @@ def test_device_generator_matches_cpu_twin(ctx):
         assert part.cpu().numpy().tobytes() == want[a:a + n].tobytes()
     with pytest.raises(ah.AHError):  # base0 not a multiple of 4
         ctx.generate_bases(c, 3, 10, out)
+    # the same from the collection's tables on the device (stream-ordered calls)
+    tables = ctx.device_tables(c)
+    out.zero_()
+    ctx.generate_bases(c, 0, c.n_bases, out, tables=tables)
+    torch.cuda.synchronize()
+    assert out.cpu().numpy().tobytes() == want.tobytes()
+    for a, n in ((8, 4099), (40000, 123457)):
+        part = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        ctx.generate_bases(c, a, n, part, tables=tables)
+        torch.cuda.synchronize()
+        assert part.cpu().numpy().tobytes() == want[a:a + n].tobytes()
 
 
 def test_large_workload_shape_on_device_generated_genomes(ctx):
