@@ -294,8 +294,13 @@ void launch_pack(const uint8_t *seq, uint64_t seq_base, uint64_t seq_len, uint64
         cached_dev = dev;
     }
     uint64_t blocks = (uint64_t)sms * (uint64_t)(per_sm > 0 ? per_sm : 1);
-    if (blocks > t1 - t0)
-        blocks = t1 - t0;
+    // AH_PACK_TILES=n: n tiles per block (the second staged while the first is packed)
+    static int tiles_per_block = -1;
+    if (tiles_per_block < 0) {
+        const char *e = getenv("AH_PACK_TILES");
+        tiles_per_block = (e && atoi(e) > 0) ? atoi(e) : 1;
+    }
+    blocks = std::min<uint64_t>(blocks, (t1 - t0 + tiles_per_block - 1) / tiles_per_block);
     // A block that packs one tile uses one staging buffer, but it reserves two:
     // three blocks per SM leave shared memory for a run's kernels beside the
     // packing (measured: 6 blocks per SM pack faster alone, 128 vs 138 us for
