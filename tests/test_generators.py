@@ -31,3 +31,34 @@ def test_collection_bases_are_chunk_independent():
     assert int((full == ord("N")).sum()) <= n_total and len(n_seg) > 0
     # the planted patches are present
     assert np.array_equal(full[c.patch_pos.astype(np.int64)], c.patch_bytes)
+
+
+def test_collection_layout_invariants():
+    """The vectorised layout: genome lengths in range, contigs inside their
+    genomes and in order, segments tiling the collection, about 0.1 % N."""
+    c = countergen.collection(seed=7, n_genomes=300, len_lo=1e5, len_hi=8e5)
+    goff = c.genome_off.astype(np.int64)
+    lens = np.diff(goff)
+    assert goff[0] == 0 and goff[-1] == c.n_bases
+    assert lens.min() >= 1e5 - 1 and lens.max() <= 8e5 + 1
+    coff = c.contig_off.astype(np.int64)
+    assert np.all(np.diff(coff) >= 0) and coff[0] == 0 and coff[-1] == c.n_bases
+    owner = np.searchsorted(goff, coff[:-1], side="right") - 1
+    assert np.array_equal(owner, c.contig_genome)
+    assert np.all(np.diff(c.contig_genome.astype(np.int64)) >= 0)
+    ends = c.segments["end"].astype(np.int64)
+    assert np.all(np.diff(ends) >= 0) and ends[-1] == c.n_bases
+    seg_len = np.diff(np.concatenate([[0], ends]))
+    n_frac = seg_len[c.segments["letter"] != 0].sum() / c.n_bases
+    assert 0.0005 < n_frac < 0.0015
+    # patches lie inside the collection, sorted and unique
+    pp = c.patch_pos.astype(np.int64)
+    assert len(pp) > 0 and np.all(np.diff(pp) > 0) and pp[-1] < c.n_bases
+
+
+def test_operon_family_plants_homologous_amplicons():
+    from paper_2509_13300_gb300 import synth
+    w = synth.operon_family(seed=5, n_genomes=4, genome_len=60_000, template_len=400)
+    assert len(w.contig_genome) == 4 and w.n_bases == 240_000
+    p = w.pairs[0]
+    assert len(p["fwd"]) == 20 and len(p["rev"]) == 20 and p["max_len"] == 800
