@@ -251,7 +251,7 @@ def main():
     ap.add_argument("--large-chunk", type=int, default=16_000_000_000, help="large: bases per chunk (whole genomes)")
     ap.add_argument("--check-genomes", type=int, default=6, help="large: sampled genomes checked by the oracle here")
     ap.add_argument("--dump-genomes", type=int, default=0, help="large: sampled genomes whose GPU results are saved")
-    ap.add_argument("--dump-path", default="gpurun_out/large_sample.npz")
+    ap.add_argument("--dump-path", default="large_sample.npz")
     ap.add_argument("--check-dump", default=None, help="oracle check of a large-form dump (CPU only)")
     args = ap.parse_args()
     if args.steps is None:
