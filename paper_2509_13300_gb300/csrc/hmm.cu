@@ -190,8 +190,8 @@ __device__ void decode_letters(const ah_amplicon &am, const uint32_t *__restrict
 // A amplicons per block, in lockstep over rows (the host groups amplicons of
 // similar length): the barriers of a row serve A rows of work.  The delete
 // chain's (max, +) pairs share their t_DD part across the A amplicons.
-template <int K, int A>
-__global__ void __launch_bounds__(kHmmThreads) hmm_viterbi_kernel(const ah_amplicon *__restrict__ amps,
+template <int K, int A, int NT>
+__global__ void __launch_bounds__(NT) hmm_viterbi_kernel(const ah_amplicon *__restrict__ amps,
                                                                   const uint32_t *__restrict__ order, uint64_t n_amps,
                                                                   const uint32_t *__restrict__ planes,
                                                                   const uint64_t *__restrict__ contig_off,
@@ -200,10 +200,10 @@ __global__ void __launch_bounds__(kHmmThreads) hmm_viterbi_kernel(const ah_ampli
                                                                   float *__restrict__ score_out, int *__restrict__ err)
 {
     extern __shared__ uint8_t seq[];                    // A x max_len letter codes
-    __shared__ float edge_prev[A][3][kHmmThreads / 32]; // M, I, D of each warp's last column, previous row
-    __shared__ float edge_cur[A][2][kHmmThreads / 32];  // M, I of each warp's last column, current row
-    __shared__ float wtot_a[kHmmThreads / 32], wtot_b[A][kHmmThreads / 32];
-    __shared__ float wpre_a[kHmmThreads / 32], wpre_b[A][kHmmThreads / 32];
+    __shared__ float edge_prev[A][3][NT / 32]; // M, I, D of each warp's last column, previous row
+    __shared__ float edge_cur[A][2][NT / 32];  // M, I of each warp's last column, current row
+    __shared__ float wtot_a[NT / 32], wtot_b[A][NT / 32];
+    __shared__ float wpre_a[NT / 32], wpre_b[A][NT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int c0 = threadIdx.x * K;
     // this thread's columns: scores of the moves into M_j (from j-1), into D_j
@@ -428,22 +428,26 @@ __global__ void __launch_bounds__(kHmmThreads) hmm_viterbi_kernel(const ah_ampli
     }
 }
 
-template <int K, int A>
-void launch_k(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
+// NT: the most threads a block may have (the register budget per thread follows from it)
+template <int K, int A, int NT>
+bool launch_k(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
               const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m, int max_len,
               float *out, int *err, int sms, cudaStream_t s)
 {
-    const int threads = std::min(kHmmThreads, 32 * (((m + 1) + 32 * K - 1) / (32 * K)));
+    const int threads = 32 * (((m + 1) + 32 * K - 1) / (32 * K));
+    if (threads > NT)
+        return false; // the profile needs more columns than this variant holds
     const size_t smem = (size_t)A * (size_t)max_len;
-    AH_CUDA(cudaFuncSetAttribute(hmm_viterbi_kernel<K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    AH_CUDA(cudaFuncSetAttribute(hmm_viterbi_kernel<K, A, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)std::max<size_t>(smem, 1)));
     int per_sm = 1;
-    AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hmm_viterbi_kernel<K, A>, threads, smem));
+    AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hmm_viterbi_kernel<K, A, NT>, threads, smem));
     const uint64_t groups = (n + A - 1) / A;
     const uint64_t blocks = std::min<uint64_t>(groups, (uint64_t)sms * (uint64_t)std::max(1, per_sm));
-    hmm_viterbi_kernel<K, A><<<(unsigned)blocks, threads, smem, s>>>(amps, order, n, planes, contig_off, n_contigs, t,
-                                                                      e, m, max_len, out, err);
+    hmm_viterbi_kernel<K, A, NT><<<(unsigned)blocks, threads, smem, s>>>(amps, order, n, planes, contig_off,
+                                                                          n_contigs, t, e, m, max_len, out, err);
     AH_CUDA(cudaGetLastError());
+    return true;
 }
 
 } // namespace
@@ -460,23 +464,24 @@ void launch_hmm_viterbi(const ah_amplicon *amps, const uint32_t *order, uint64_t
     if (const char *v = getenv("AH_HMM_VARIANT"))
         if (sscanf(v, "%d,%d", &vk, &va) != 2)
             vk = va = 0;
-#define AH_HMM_TRY(K_, A_)                                                                                      \
-    if ((vk == 0 || (vk == K_ && va == A_)) && cols <= K_ * kHmmThreads) {                                     \
-        launch_k<K_, A_>(amps, order, n, planes, contig_off, n_contigs, t, e, m, max_len, score_out, err, sms, s); \
-        return;                                                                                                \
-    }
+#define AH_HMM_TRY(K_, A_, NT_)                                                                                  \
+    if ((vk == 0 || (vk == K_ && va == A_)) &&                                                                   \
+        launch_k<K_, A_, NT_>(amps, order, n, planes, contig_off, n_contigs, t, e, m, max_len, score_out, err, sms, \
+                              s))                                                                                \
+        return;
     if (vk) { // the named variant (when it covers the profile)
-        AH_HMM_TRY(1, 4)
-        AH_HMM_TRY(2, 2)
-        AH_HMM_TRY(4, 1)
-        AH_HMM_TRY(4, 2)
-        AH_HMM_TRY(8, 1)
+        AH_HMM_TRY(2, 2, 512)
+        AH_HMM_TRY(4, 1, 512)
+        AH_HMM_TRY(4, 2, 512)
+        AH_HMM_TRY(4, 4, 256)
+        AH_HMM_TRY(8, 2, 256)
+        AH_HMM_TRY(8, 1, 256)
         vk = va = 0;
     }
     // default (measured on 639 columns: 4 columns x 2 amplicons 398 GCUPS; 2 x 2 272; 4 x 1 315;
     // 8 x 1 234, register-capped); longer profiles take 6 columns x 1 amplicon
-    AH_HMM_TRY(4, 2)
-    AH_HMM_TRY(6, 1)
+    AH_HMM_TRY(4, 2, 512)
+    AH_HMM_TRY(6, 1, 512)
 #undef AH_HMM_TRY
     throw Error(AH_ERR_ARG, "ah_hmm_score: profile longer than " + std::to_string(kHmmMaxColumns) + " columns");
 }
