@@ -147,6 +147,7 @@ def lib():
             "ah_tune_scan": (I32, [P, U32, P, U32, U64, ctypes.POINTER(TuneResult), P]),
             "ah_pair_noalloc": (I32, [P, U32, P, P, U64, P, U64, ctypes.POINTER(U64), P]),
             "ah_debug_compile_scan": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
+            "ah_debug_hmm_profile": (I32, [P, P, U64, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P, P]),
             "ah_debug_scan_source": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
         }
         for name, (res, args) in sig.items():
@@ -545,6 +546,25 @@ class Server:
 
     def __exit__(self, *a):
         self.stop()
+
+
+def debug_hmm_profile(seqs):
+    """The library's profile of training sequences, built on the host without a
+    context (no GPU needed): (m, reference index, t[(m + 1), 3, 3], e[(m + 1), 4])."""
+    data = b"".join(x.encode() if isinstance(x, str) else bytes(x) for x in seqs)
+    off = np.zeros(len(seqs) + 1, dtype=np.uint64)
+    off[1:] = np.cumsum([len(x) for x in seqs])
+    buf = np.frombuffer(data, dtype=np.uint8).copy() if data else np.zeros(1, np.uint8)
+    m, ref = ctypes.c_uint64(), ctypes.c_uint64()
+    rc = lib().ah_debug_hmm_profile(_ptr(buf), _ptr(off), len(seqs), 0, ctypes.byref(m), ctypes.byref(ref), None, None)
+    if rc:
+        raise ValueError("no training sequence")
+    t = np.zeros((m.value + 1, 3, 3), dtype=np.float32)
+    e = np.zeros((m.value + 1, 4), dtype=np.float32)
+    rc = lib().ah_debug_hmm_profile(_ptr(buf), _ptr(off), len(seqs), m.value, ctypes.byref(m), ctypes.byref(ref),
+                                    _ptr(t), _ptr(e))
+    assert rc == 0
+    return m.value, ref.value, t, e
 
 
 def debug_compile_scan(fwd: str, rev: str, k: int, R: int = 4, arith_pct: int = 0, order: int = 0):

@@ -487,3 +487,29 @@ void launch_hmm_viterbi(const ah_amplicon *amps, const uint32_t *order, uint64_t
 }
 
 } // namespace ah
+
+// The profile of a training set without a context or a GPU (development aid:
+// lets the host-side builder be compared with an independent implementation on
+// machines without a GPU).  Returns 0 and writes m and the reference index;
+// when t and e are not NULL they receive (m + 1) * 9 and (m + 1) * 4 scores.
+// Returns 1 for no training sequence, 2 when t or e is given and m exceeds
+// m_cap.
+extern "C" int ah_debug_hmm_profile(const char *seqs, const uint64_t *offsets, uint64_t n, uint64_t m_cap,
+                                    uint64_t *m_out, uint64_t *reference_out, float *t, float *e)
+{
+    if (n == 0 || !offsets || !m_out || !reference_out)
+        return 1;
+    ah::HmmProfile p;
+    ah::build_profile(seqs, offsets, n, p);
+    *m_out = (uint64_t)p.m;
+    *reference_out = p.reference;
+    if (t || e) {
+        if ((uint64_t)p.m > m_cap)
+            return 2;
+        if (t)
+            memcpy(t, p.t.data(), p.t.size() * sizeof(float));
+        if (e)
+            memcpy(e, p.e.data(), p.e.size() * sizeof(float));
+    }
+    return 0;
+}

@@ -1,7 +1,8 @@
 """Pins of the profile-HMM oracle (oracle/hmm.c) against brute force and closed
 forms: alignment distance by enumerating every alignment, the Viterbi score by
 enumerating every state path, the profile of identical training sequences in
-closed form, and the counts of single insertions and deletions."""
+closed form, and the counts of single insertions and deletions.  Then the
+library's host-side profile builder against the pinned oracle (no GPU)."""
 import math
 
 import numpy as np
@@ -139,3 +140,32 @@ def test_unknown_letters_score_as_background():
     # the N column emits log-odds 0; the best path still matches it
     want = e[1, 0] + e[2, 1] + 0.0 + e[4, 3] + sum(t[j, 0, 0] for j in range(5))
     assert a == pytest.approx(want)
+
+
+def test_library_profile_builder_equals_the_oracle():
+    """The library's host-side profile builder (no GPU needed) against the
+    oracle's, on random training sets with repeats (reference ties), unknown
+    letters, substitutions and indels: same reference, same move and emission
+    scores (fp32 of the oracle's fp64)."""
+    from paper_2509_13300_gb300 import ah, build, synth
+    build.build()
+    rng = np.random.default_rng(11)
+    for trial in range(40):
+        L = int(rng.integers(5, 120))
+        base = "".join(rng.choice(list(LET), size=L))
+        n = int(rng.integers(1, 12))
+        train = []
+        for _ in range(n):
+            x = synth._mutate(rng, base, float(rng.uniform(0, 0.1)), float(rng.uniform(0, 0.05)))
+            if rng.random() < 0.2 and x:
+                i = int(rng.integers(len(x)))
+                x = x[:i] + "N" + x[i + 1:]
+            train.append(x if x else "A")
+        if rng.random() < 0.3:
+            train += [train[int(rng.integers(len(train)))]] * int(rng.integers(1, 3))  # repeats
+        m, ref, t, e = ah.debug_hmm_profile(train)
+        oref, T, E = oracle.hmm_build(train)
+        assert (m, ref) == (T.shape[0] - 1, oref), trial
+        assert np.array_equal(np.isinf(t), np.isinf(T)), trial
+        fin = ~np.isinf(T)
+        assert np.abs(t[fin] - T[fin]).max() <= 1e-5 and np.abs(e - E).max() <= 1e-5, trial
