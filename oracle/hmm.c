@@ -2,9 +2,9 @@
  * Oracle for profile-HMM scoring of amplicons (test infrastructure only; see
  * oracle.c for the rules on who may use it).
  *
- * The paper (Sec. 2.1, Amplicon analysis, item 2) trains a profile HMM on
- * high-confidence amplicons -- those whose primers match exactly -- and uses
- * it to score every predicted amplicon for homology.  It names no aligner,
+ * The paper (Sec. 2.1, Amplicon analysis, item 2) builds a profile HMM from
+ * the amplicons whose primers match exactly and scores every predicted
+ * amplicon against it for homology.  It names no aligner,
  * model topology or scoring mode; the reading taken here, in plain steps:
  *
  *   Profile (or_hmm_build):
