@@ -374,8 +374,8 @@ ah_status ah_tm_sweep(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, ui
                       uint32_t n_thresholds, ah_sweep_row *rows, uint64_t *n_genomes_out, void *stream);
 
 /* Amplicon sequence variants and amplitypes (Sec. 3.3, Amplicon Pattern
- * Visualization: an amplitype is a genome's combination of copy numbers and
- * sequence variants).  amplicons (host or device): n records of the set (as
+ * Visualization: the amplitype of a genome is which variants it carries and
+ * how many copies of each).  amplicons (host or device): n records of the set (as
  * ah_pair returns them); the sequence of each is the one ah_fetch returns (RF
  * reverse-complemented, N for non-ACGT), hashed on the device (two
  * polynomial hashes modulo 2^61 - 1: 122 bits).  variant_out (host or device,

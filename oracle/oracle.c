@@ -472,9 +472,9 @@ double or_duplex_tm(const char *oligo, const char *bottom, const or_nn_table *ta
     return duplex_tm(oligo, bottom, (int)strlen(oligo), tab, p);
 }
 
-/* Max Tm over every oligo of degenerate primer X at one site (Sec. 2.1: the
- * threshold is applied to the maximum over all oligonucleotides represented
- * by the primer, each checked individually). */
+/* Max Tm over every oligo of degenerate primer X at one site (Sec. 2.1: a
+ * site passes when its best oligo reaches the threshold; every oligo of the
+ * primer is evaluated on its own). */
 static double site_max_tm(const uint8_t *window, int strand, const char *primer, const or_nn_table *tab,
                           const or_tm_params *p)
 {
