@@ -82,9 +82,9 @@ typedef struct ah_ctx ah_ctx;
  * Na_mM, K_mM, Tris_mM, Mg_mM, dNTPs_mM
  *           ion concentrations (mM); [Na_eq] = Na + K + Tris/2
  *           + 120 sqrt(Mg - dNTPs) when Mg > dNTPs (von Ahsen 2001)
- * saltcorr  0 none; 1 Tm += 16.6 log10[Na_eq]; 2 Tm += 16.6 log10([Na_eq]/(1 +
- *           0.7 [Na_eq])) + 3.85; 3 Tm += 12.5 log10[Na_eq]; 4 Tm += 11.7
- *           log10[Na_eq]; 5 dS += 0.368 (L - 1) ln[Na_eq] ([Na_eq] in mol/L) */
+ * saltcorr  0 none; 1 Tm += 16.6 log10[Na_eq] (Schildkraut-Lifson 1965);
+ *           5 dS += 0.368 (L - 1) ln[Na_eq] (SantaLucia 1998); [Na_eq] in
+ *           mol/L.  Other methods are rejected (AH_ERR_ARG). */
 typedef struct ah_pcr_params {
     int32_t k;
     int32_t clamp;
@@ -212,8 +212,8 @@ ah_status ah_unload_genomes(ah_ctx *ctx, uint32_t set_id);
  * at least 5 letters and degeneracy at most 10000, k at most 10; this library
  * also requires at most 32 letters.  Errors: AH_ERR_PRIMER for a primer or k
  * outside the limits, AH_ERR_ARG for other bad parameters (clamp < 0,
- * min_len > max_len, x <= 0, salt method outside 0..5, [Na_eq] <= 0 with a
- * salt method). */
+ * min_len > max_len, x <= 0, salt method other than 0, 1 or 5, [Na_eq] <= 0
+ * with a salt method). */
 ah_status ah_set_primers(ah_ctx *ctx, const char *fwd, const char *rev, const ah_pcr_params *params,
                          uint32_t *pair_id_out);
 

@@ -443,10 +443,9 @@ static double na_equivalent_mM(const or_tm_params *p)
 
 /* Tm in deg C of one duplex of length L (Sec. 2.1: dnac1, dnac2, Na, K, Tris,
  * Mg, dNTPs and the salt correction method are parameters).  Salt methods:
- * 0 none; 1-4 Tm shifts 16.6 log10[Na] (Schildkraut-Lifson 1965),
- * 16.6 log10([Na]/(1+0.7[Na])) + 3.85 (Wetmur 1991), 12.5 log10[Na]
- * (SantaLucia 1996), 11.7 log10[Na] (SantaLucia 1998); 5 entropy term
- * 0.368 (L-1) ln[Na] (SantaLucia 1998).  [Na] in mol/L. */
+ * 0 none; 1 Tm shift 16.6 log10[Na] (Schildkraut-Lifson 1965); 5 entropy
+ * term 0.368 (L-1) ln[Na] (SantaLucia 1998).  [Na] in mol/L.  Other method
+ * numbers give NaN (the library rejects them). */
 static double duplex_tm(const char *o, const char *b, int L, const or_nn_table *tab, const or_tm_params *p)
 {
     double H, S;
@@ -456,13 +455,10 @@ static double duplex_tm(const char *o, const char *b, int L, const or_nn_table *
         S += 0.368 * (double)(L - 1) * log(na);
     double x = (p->dnac1_nM - p->dnac2_nM / 2.0) * 1e-9;
     double tm = 1000.0 * H / (S + GAS_R * log(x)) - 273.15;
-    switch (p->saltcorr) {
-    case 1: tm += 16.6 * log10(na); break;
-    case 2: tm += 16.6 * log10(na / (1.0 + 0.7 * na)) + 3.85; break;
-    case 3: tm += 12.5 * log10(na); break;
-    case 4: tm += 11.7 * log10(na); break;
-    default: break;
-    }
+    if (p->saltcorr == 1)
+        tm += 16.6 * log10(na);
+    else if (p->saltcorr != 0 && p->saltcorr != 5)
+        tm = NAN;
     return tm;
 }
 

@@ -504,15 +504,8 @@ PairDev make_pair_dev(const PrimerPair &pp)
     const double na = na_eq_mM(pp.params) / 1000.0;
     d.saltcorr = pp.params.saltcorr;
     d.log_na = pp.params.saltcorr == 5 ? std::log(na) : 0.0;
-    d.tm_shift = 0.0;
-    switch (pp.params.saltcorr) {
-    case 1: d.tm_shift = 16.6 * std::log10(na); break;
-    case 2: d.tm_shift = 16.6 * std::log10(na / (1.0 + 0.7 * na)) + 3.85; break;
-    case 3: d.tm_shift = 12.5 * std::log10(na); break;
-    case 4: d.tm_shift = 11.7 * std::log10(na); break;
-    default: break;
-    }
-    d.thr = d.tm_min + 273.15 - ((d.saltcorr >= 1 && d.saltcorr <= 4) ? d.tm_shift : 0.0);
+    d.tm_shift = pp.params.saltcorr == 1 ? 16.6 * std::log10(na) : 0.0; // Schildkraut-Lifson (1965)
+    d.thr = d.tm_min + 273.15 - d.tm_shift;
     for (int i = 0; i < 256; ++i) {
         d.stack_dH[i] = (float)pp.table.stack_dH[i];
         d.stack_dS[i] = (float)pp.table.stack_dS[i];
@@ -1844,7 +1837,7 @@ ah_status ah_set_primers(ah_ctx *c, const char *fwd, const char *rev, const ah_p
         require(p->k >= 0 && p->k <= AH_MAX_MISMATCHES, AH_ERR_PRIMER, "k must be 0..10");
         require(p->clamp >= 0, AH_ERR_ARG, "clamp must be >= 0");
         require(p->min_len >= 0 && p->min_len <= p->max_len, AH_ERR_ARG, "need 0 <= min_len <= max_len");
-        require(p->saltcorr >= 0 && p->saltcorr <= 5, AH_ERR_ARG, "saltcorr must be 0..5");
+        require(p->saltcorr == 0 || p->saltcorr == 1 || p->saltcorr == 5, AH_ERR_ARG, "saltcorr must be 0, 1 or 5");
         require(!std::isnan(p->tm_min) && p->tm_min < INFINITY, AH_ERR_ARG, "tm_min must be a number or -inf");
         const double vals[] = {p->dnac1_nM, p->dnac2_nM, p->Na_mM, p->K_mM, p->Tris_mM, p->Mg_mM, p->dNTPs_mM};
         for (double v : vals)

@@ -77,7 +77,7 @@ __device__ double exact_tm(const PairDev &pd, const int8_t *bt, int L, uint64_t 
     if (pd.saltcorr == 5)
         S = __dadd_rn(S, __dmul_rn(__dmul_rn(0.368, (double)(L - 1)), pd.log_na));
     double tm = __dsub_rn(__ddiv_rn(__dmul_rn(1000.0, H), __dadd_rn(S, pd.sconst)), 273.15);
-    if (pd.saltcorr >= 1 && pd.saltcorr <= 4)
+    if (pd.saltcorr == 1)
         tm = __dadd_rn(tm, pd.tm_shift);
     return tm;
 }
@@ -594,7 +594,7 @@ __global__ void sweep_weights_kernel(const PairDev *__restrict__ pairs, int n_pa
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const int e = i % 272, pj = i / 272, j = pj % n_thr, p = pj / n_thr;
         const PairDev &pd = pairs[p];
-        const double thr = thr_c[j] + 273.15 - ((pd.saltcorr >= 1 && pd.saltcorr <= 4) ? pd.tm_shift : 0.0);
+        const double thr = thr_c[j] + 273.15 - pd.tm_shift;
         W[i] = e < 256 ? fix_weight(pd.stack_dH_d[e], pd.stack_dS_d[e], thr)
                        : fix_weight(pd.term_dH_d[e - 256], pd.term_dS_d[e - 256], thr);
     }
@@ -659,7 +659,7 @@ __global__ void sweep_pass_kernel(const ah_site *__restrict__ sites, uint64_t n,
                             const long long v = c[y] + Wp[256 + y * 4 + bt[L - 1]];
                             fin = v < fin ? v : fin;
                         }
-                    const double thr = T + 273.15 - ((pd.saltcorr >= 1 && pd.saltcorr <= 4) ? pd.tm_shift : 0.0);
+                    const double thr = T + 273.15 - pd.tm_shift;
                     const double Cp = pd.sconst + (pd.saltcorr == 5 ? 0.368 * (double)(L - 1) * pd.log_na : 0.0);
                     const long long F = fin - __double2ll_rn(thr * Cp * kFix);
                     dec = F < -kFixMargin ? 1 : (F > kFixMargin ? 0 : -1);

@@ -127,12 +127,21 @@ def test_paper_primer_pairs(ctx):
     assert_parity(gpu_run(ctx, w), oracle_run(w))
 
 
-@pytest.mark.parametrize("salt", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("salt", [0, 1, 5])
 def test_salt_methods_and_ions(ctx, salt):
     w = synth.tiny(0)
     w.pairs = [dict(w.pairs[0], saltcorr=salt, K_mM=10.0, Tris_mM=20.0, Mg_mM=1.5, dNTPs_mM=0.2,
                     dnac1_nM=400.0, dnac2_nM=100.0, tm_min=45.0)]
     assert_parity(gpu_run(ctx, w), oracle_run(w))
+
+
+@pytest.mark.parametrize("salt", [2, 3, 4, 6, 7, -1])
+def test_salt_methods_not_offered_are_rejected(ctx, salt):
+    """Only the salt methods the oracle pins to published values (0, 1, 5) are offered."""
+    p = dict(synth.tiny(0).pairs[0], saltcorr=salt)
+    with pytest.raises(ah.AHError) as e:
+        ctx.ah_set_primers(p["fwd"], p["rev"], p)
+    assert e.value.status == ah.AH_ERR_ARG
 
 
 def test_custom_nn_table_with_mismatch_terms(ctx):

@@ -439,6 +439,54 @@ def test_salt_equivalent_concentration():
     assert abs(a - c) < 1e-9
 
 
+def _read_published():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "tm_biopython.txt")):
+        line = line.split("#")[0].strip()
+        if line:
+            rows.append(line.split())
+    return rows
+
+
+def test_tm_published_values_of_the_named_model():
+    """Sec. 2.1 names Biopython's NN model; its documentation prints Tm_NN of one
+    28-mer under the defaults (dnac1 = dnac2 = 25 nM, 50 mM Na+, entropy salt
+    term) and with Tris and Mg2+, to two decimals.  These fix the gas constant,
+    the 273.15 offset, the x = dnac1 - dnac2/2 term, the 0.368 (N-1) ln[Na]
+    entropy term and the von Ahsen Tris/2 and 120 sqrt(Mg) terms: a change to
+    any of them moves at least one value by more than the printed rounding."""
+    rows = [r for r in _read_published() if r[0] == "tm"]
+    assert len(rows) == 3
+    for r in rows:
+        seq = r[1]
+        d1, d2, na, k, tris, mg, dntp = (float(x) for x in r[2:9])
+        p = dict(dnac1_nM=d1, dnac2_nM=d2, Na_mM=na, K_mM=k, Tris_mM=tris, Mg_mM=mg, dNTPs_mM=dntp,
+                 saltcorr=int(r[9]))
+        got = oracle.duplex_tm(seq, "".join(COMP[b] for b in seq), p)
+        assert abs(got - float(r[10])) <= 0.005 + 1e-9, (r, got)
+
+
+def test_tm_salt_shift_methods():
+    """Method 1 (Schildkraut-Lifson 1965) shifts Tm by the published correction
+    (salt_correction(Na=50, method=1) = -21.60); at [Na_eq] = 1 M every salt
+    term vanishes (log 1 = 0), so methods 0, 1 and 5 then agree; methods the
+    library does not offer give NaN."""
+    seq = "CGTTCCAAAGATGTGGGCATGAGCTTAC"
+    bot = "".join(COMP[b] for b in seq)
+    for r in (r for r in _read_published() if r[0] == "salt"):
+        na, k, tris, mg, dntp = (float(x) for x in r[1:6])
+        ions = dict(dnac1_nM=25.0, dnac2_nM=25.0, Na_mM=na, K_mM=k, Tris_mM=tris, Mg_mM=mg, dNTPs_mM=dntp)
+        shift = oracle.duplex_tm(seq, bot, dict(ions, saltcorr=int(r[6]))) - \
+            oracle.duplex_tm(seq, bot, dict(ions, saltcorr=0))
+        assert abs(shift - float(r[7])) <= 0.005 + 1e-9, (r, shift)
+    one_molar = dict(P0, Na_mM=1000.0)
+    t0 = oracle.duplex_tm(seq, bot, dict(one_molar, saltcorr=0))
+    for m in (1, 5):
+        assert abs(oracle.duplex_tm(seq, bot, dict(one_molar, saltcorr=m)) - t0) < 1e-9
+    for m in (2, 3, 4, 6, 7):
+        assert math.isnan(oracle.duplex_tm(seq, bot, dict(P0, saltcorr=m)))
+
+
 def test_degeneracy_of_paper_primers():
     """Sec. 1: the two Titan primers together hold 960 oligonucleotides."""
     f, r = synth.PAPER_PAIRS["Titan"]
