@@ -243,7 +243,7 @@ typedef struct ah_tune_result {
     int32_t warps_per_cta; /* warps per thread block */
     int32_t regs;          /* registers per thread of the chosen variant */
     int32_t reserved;
-    double us_per_tile;    /* measured time per 32768-base tile */
+    double us_per_tile;    /* measured time per 32768-base tile (all launches of the scan) */
     uint64_t tiles;        /* tiles in the timed sample */
 } ah_tune_result;
 
@@ -251,7 +251,10 @@ typedef struct ah_tune_result {
  * compiles the candidate variants of the scan kernel specialised to these
  * pairs, times each on the first sample_tiles tiles of the set (0 = 4096),
  * and keeps the fastest for every later ah_scan of the same pattern set on
- * this context.  best_out (host, may be null) receives the choice.
+ * this context.  A scan of several pairs whose networks are large runs as
+ * one launch per group of pairs; each group is tuned on its own, and
+ * best_out (host, may be null) receives the slowest group's variant with
+ * the groups' summed time.
  * Errors: AH_ERR_ARG, AH_ERR_JIT, AH_ERR_CUDA. */
 ah_status ah_tune_scan(ah_ctx *ctx, uint32_t set_id, const uint32_t *pair_ids, uint32_t n_pairs,
                        uint64_t sample_tiles, ah_tune_result *best_out, void *stream);

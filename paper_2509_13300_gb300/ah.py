@@ -588,5 +588,5 @@ def scan_lop3_per_word(fwd: str, rev: str, k: int, R: int = 4, arith_pct: int = 
     """Logic-pipe (LOP3) operations the generated hot loop issues per 32-start
     word for one pair, counted in its generated source."""
     src = debug_scan_source(fwd, rev, k, R, arith_pct)
-    hot = src[src.index("u32 h[NPAT * R];"):src.index("__any_sync")]
+    hot = src[src.index("u32 hg[NGRP * R];"):src.index("__any_sync")]
     return round(hot.count("lop3<") / R)

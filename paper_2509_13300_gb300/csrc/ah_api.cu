@@ -605,17 +605,17 @@ const ScanTuning &tuning_for(ah_ctx *c, const std::vector<ScanPattern> &pats)
 // Launch the generated scan kernel over tiles [0, n_tiles) of a set.
 // Scan n_tiles tiles: the first n_tiles of the set, or tile_list[0 .. n_tiles) (device) when given.
 // The caller resets the flag block (the work counter included) on the same stream first.
+// work: the launch's slice counter (a flag word zeroed by the caller's reset_flags).
 void launch_scan(ah_ctx *c, ScanKernel *k, const GenomeSet &gs, uint64_t n_tiles, uint64_t *keys, uint64_t cap,
-                 int pbits, cudaStream_t st, const uint64_t *tile_list = nullptr)
+                 int pbits, cudaStream_t st, const uint64_t *tile_list, uint64_t *work)
 {
     const uint64_t grid = std::min<uint64_t>(n_tiles, (uint64_t)c->sms * k->blocks_per_sm);
     const uint32_t *planes = gs.planes;
     const uint64_t *coff = gs.contig_off;
     uint32_t nc = gs.n_contigs;
-    uint64_t *work = c->d_flags + kFlagWork; // zeroed with the flag block by the caller's reset_flags
-    const uint32_t *tcont = gs.tile_contig;
-    void *args[] = {&planes,       &n_tiles, &coff, &nc,   &keys,      &cap,  &c->d_counter,
-                    &pbits,        &c->d_err, &work, &tile_list, &tcont};
+    const uint32_t *tcont = gs.tile_contig, *troom = gs.tile_room;
+    void *args[] = {&planes, &n_tiles,  &coff, &nc,        &keys,  &cap,  &c->d_counter,
+                    &pbits,  &c->d_err, &work, &tile_list, &tcont, &troom};
     AH_CUDA(cudaLaunchKernel((const void *)k->fn, dim3((unsigned)grid), dim3(k->threads), args, k->smem, st));
 }
 
@@ -642,6 +642,29 @@ std::vector<ScanPattern> patterns_of(ah_ctx *c, const uint32_t *pair_ids, uint32
     return pats;
 }
 
+// The patterns of each launch group (scan_launch_groups).
+std::vector<std::vector<ScanPattern>> split_launches(const std::vector<ScanPattern> &pats)
+{
+    std::vector<std::vector<ScanPattern>> out;
+    for (const auto &g : scan_launch_groups(pats))
+        out.emplace_back(pats.begin() + g.first, pats.begin() + g.second);
+    return out;
+}
+
+// Scan kernels over n_tiles tiles of a set (or tile_list), one launch per
+// launch group, all appending to keys; returns the number of launches.  The
+// caller resets the flag block (the groups' work counters included) first.
+int launch_scans(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPattern> &pats, uint64_t n_tiles,
+                 uint64_t *keys, uint64_t cap, int pbits, cudaStream_t st, const uint64_t *tile_list = nullptr)
+{
+    const auto parts = split_launches(pats);
+    for (size_t i = 0; i < parts.size(); ++i) {
+        ScanKernel *k = scan_kernel(parts[i], tuning_for(c, parts[i]), c->device);
+        launch_scan(c, k, gs, n_tiles, keys, cap, pbits, st, tile_list, c->d_flags + kFlagWork + i);
+    }
+    return (int)parts.size();
+}
+
 } // namespace
 
 namespace {
@@ -661,13 +684,12 @@ uint64_t scan_keys(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPattern
     const uint64_t n_tiles = tile_list ? n_list : gs.n_tiles;
     if (!n_tiles)
         return 0;
-    ScanKernel *k = scan_kernel(pats, tuning_for(c, pats), c->device);
     for (int attempt = 0; attempt < 2; ++attempt) {
         uint64_t *keys = (uint64_t *)scratch(c, "scan_keys", c->key_cap * sizeof(uint64_t));
         reset_flags(c, st);
         {
-            Stage sg(c, "scan", st, 1);
-            launch_scan(c, k, gs, n_tiles, keys, c->key_cap, pbits, st, tile_list);
+            Stage sg(c, "scan", st, (int)scan_launch_groups(pats).size());
+            launch_scans(c, gs, pats, n_tiles, keys, c->key_cap, pbits, st, tile_list);
         }
         check_flags(c, st);
         count = c->h_flags[0];
@@ -773,12 +795,12 @@ void fast_begin(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPattern> &
     char *seq = seq_direct ? o->seq : (char *)scratch(c, "run_seq", nq_max);
     const uint8_t *filt = o->tm_filter ? pass : nullptr;
 
-    ScanKernel *k = scan_kernel(pats, tuning_for(c, pats), c->device);
+    const int n_launch = (int)scan_launch_groups(pats).size();
     span.reset(new HostSpan(c, "host.run.launch"));
     reset_flags(c, st);
     {
-        Stage sg(c, "scan", st, 1);
-        launch_scan(c, k, gs, gs.n_tiles, keys, c->key_cap, pbits, st);
+        Stage sg(c, "scan", st, n_launch);
+        launch_scans(c, gs, pats, gs.n_tiles, keys, c->key_cap, pbits, st);
     }
     if (scan_done)
         AH_CUDA(cudaEventRecord(scan_done, st));
@@ -1632,7 +1654,7 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
         // the three tables in one block (one copy fills them): contig offsets,
         // genome ids, per-tile contigs
         const size_t ob = (n_contigs + 1) * sizeof(uint64_t), gb = n_contigs * sizeof(uint32_t),
-                     tb = (gs->n_tiles + 1) * sizeof(uint32_t);
+                     tb = 2 * (gs->n_tiles + 1) * sizeof(uint32_t);
         const size_t table_bytes = ob + gb + tb; // a multiple of 4; ob keeps the rest 4-byte aligned
         try {
             gs->planes = (uint32_t *)dev_alloc(c, plane_bytes);
@@ -1644,6 +1666,7 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
         }
         gs->contig_genome = (uint32_t *)((char *)gs->contig_off + ob);
         gs->tile_contig = (uint32_t *)((char *)gs->contig_off + ob + gb);
+        gs->tile_room = gs->tile_contig + (gs->n_tiles + 1);
         gs->bytes = plane_bytes + table_bytes;
         const bool dev_seq = n_bases && is_device_ptr(c, seq);
         // a queued run leaves the flag block alone for plain loads (host or device input)
@@ -1738,14 +1761,18 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
             memcpy(sl.p, contig_off, ob);
             memcpy(sl.p + ob, contig_genome, gb);
             {
-                // tile t: the last contig starting at or before t * kTileBases
+                // tile t: the last contig starting at or before t * kTileBases, and
+                // the room from the tile's first position to that contig's end
                 uint32_t *tc = (uint32_t *)(sl.p + ob + gb);
+                uint32_t *room = tc + (gs->n_tiles + 1);
                 uint32_t ci = 0;
                 for (uint64_t t = 0; t <= gs->n_tiles; ++t) {
                     const uint64_t P = t * kTileBases;
                     while (ci + 1 < n_contigs && contig_off[ci + 1] <= P)
                         ++ci;
                     tc[t] = ci;
+                    const uint64_t end = n_contigs ? contig_off[ci + 1] : 0;
+                    room[t] = end > P ? (uint32_t)std::min<uint64_t>(end - P, 0xffffffffull) : 0u;
                 }
             }
             Stage sg(c, "tables", st, 1);
@@ -1944,52 +1971,67 @@ ah_status ah_tune_scan(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
             cand.push_back(t);
         }
         cudaEvent_t e0 = get_event(c), e1 = get_event(c);
-        double best_us = 1e30;
-        ScanTuning best = c->tuning;
-        int best_regs = -1;
-        for (const ScanTuning &t : cand) {
-            ScanKernel *k = nullptr;
-            try {
-                k = scan_kernel(pats, t, c->device);
-            } catch (const Error &) {
-                continue; // a variant that does not compile is skipped
+        // each launch group is tuned on its own (its kernel is compiled and run alone);
+        // the result reports the slowest group's variant and the groups' summed time
+        double total_us = 0, worst_us = -1;
+        ScanTuning worst = c->tuning;
+        int worst_regs = -1;
+        for (const std::vector<ScanPattern> &gp : split_launches(pats)) {
+            double best_us = 1e30;
+            ScanTuning best = c->tuning;
+            int best_regs = -1;
+            for (const ScanTuning &t : cand) {
+                ScanKernel *k = nullptr;
+                try {
+                    k = scan_kernel(gp, t, c->device);
+                } catch (const Error &) {
+                    continue; // a variant that does not compile is skipped
+                }
+                uint64_t *keys = (uint64_t *)scratch(c, "scan_keys", c->key_cap * sizeof(uint64_t));
+                float ms_min = 1e30f;
+                for (int rep = 0; rep < 4; ++rep) {
+                    reset_flags(c, st);
+                    AH_CUDA(cudaEventRecord(e0, st));
+                    launch_scan(c, k, gs, tiles, keys, c->key_cap, pbits, st, nullptr, c->d_flags + kFlagWork);
+                    AH_CUDA(cudaEventRecord(e1, st));
+                    AH_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0;
+                    AH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (rep > 0)
+                        ms_min = std::min(ms_min, ms);
+                }
+                check_flags(c, st);
+                const double us = ms_min * 1e3 / (double)tiles;
+                if (getenv("AH_TUNE_VERBOSE"))
+                    fprintf(stderr,
+                            "ah_tune_scan: patterns=%zu R=%d arith=%d order=%d stages=%d warps=%d regs=%d bps=%d  "
+                            "%.4f us/tile\n",
+                            gp.size(), t.R, t.arith_pct, t.order, t.stages, t.warps, k->regs, k->blocks_per_sm, us);
+                if (us < best_us) {
+                    best_us = us;
+                    best = t;
+                    best_regs = k->regs;
+                }
             }
-            uint64_t *keys = (uint64_t *)scratch(c, "scan_keys", c->key_cap * sizeof(uint64_t));
-            float ms_min = 1e30f;
-            for (int rep = 0; rep < 4; ++rep) {
-                reset_flags(c, st);
-                AH_CUDA(cudaEventRecord(e0, st));
-                launch_scan(c, k, gs, tiles, keys, c->key_cap, pbits, st);
-                AH_CUDA(cudaEventRecord(e1, st));
-                AH_CUDA(cudaEventSynchronize(e1));
-                float ms = 0;
-                AH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                if (rep > 0)
-                    ms_min = std::min(ms_min, ms);
-            }
-            check_flags(c, st);
-            const double us = ms_min * 1e3 / (double)tiles;
-            if (getenv("AH_TUNE_VERBOSE"))
-                fprintf(stderr, "ah_tune_scan: R=%d arith=%d order=%d stages=%d warps=%d regs=%d bps=%d  %.4f us/tile\n",
-                        t.R, t.arith_pct, t.order, t.stages, t.warps, k->regs, k->blocks_per_sm, us);
-            if (us < best_us) {
-                best_us = us;
-                best = t;
-                best_regs = k->regs;
+            c->tuned[signature(gp)] = best;
+            total_us += best_us;
+            if (best_us > worst_us) {
+                worst_us = best_us;
+                worst = best;
+                worst_regs = best_regs;
             }
         }
         c->events.push_back(e0);
         c->events.push_back(e1);
-        c->tuned[signature(pats)] = best;
         if (best_out) {
-            best_out->R = best.R;
-            best_out->arith_pct = best.arith_pct;
-            best_out->min_blocks = best.min_blocks;
-            best_out->order = best.order;
-            best_out->stages = best.stages;
-            best_out->warps_per_cta = best.warps;
-            best_out->regs = best_regs;
-            best_out->us_per_tile = best_us;
+            best_out->R = worst.R;
+            best_out->arith_pct = worst.arith_pct;
+            best_out->min_blocks = worst.min_blocks;
+            best_out->order = worst.order;
+            best_out->stages = worst.stages;
+            best_out->warps_per_cta = worst.warps;
+            best_out->regs = worst_regs;
+            best_out->us_per_tile = total_us;
             best_out->tiles = tiles;
         }
     });

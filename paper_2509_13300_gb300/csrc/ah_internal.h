@@ -44,6 +44,9 @@ struct GenomeSet {
     // device, n_tiles + 1: tile_contig[t] = the last contig starting at or before
     // position t * kTileBases (the contigs a tile's starts can fall in begin there)
     uint32_t *tile_contig = nullptr;
+    // device, n_tiles + 1: bases from position t * kTileBases to the end of
+    // contig tile_contig[t] (0 past the last base, capped at 2^32 - 1)
+    uint32_t *tile_room = nullptr;
     size_t bytes = 0;
     // recorded after the work that fills the set (the packing); every call that
     // reads the set waits for it on its own stream, and unloading waits for it
@@ -151,6 +154,11 @@ int comp_mask(int m);
 std::string scan_compile_only(const std::vector<ScanPattern> &pats, const ScanTuning &t, bool *ok);
 std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &t);
 ScanKernel *scan_kernel(const std::vector<ScanPattern> &pats, const ScanTuning &t, int device);
+// Launch groups of a pattern list, as [first, end) pattern index ranges:
+// consecutive pairs share a launch while their generated network stays small
+// (a larger one spills registers and misses in the instruction cache); a pair
+// is never split.  At most AH_MAX_PAIRS_PER_SCAN groups.
+std::vector<std::pair<int, int>> scan_launch_groups(const std::vector<ScanPattern> &pats);
 
 // ---- kernel launchers ----
 // pack.cu: pack tiles [t0, t1) from seq, which holds flat positions
@@ -199,9 +207,9 @@ enum FlagWord : int {
     kFlagAmps = 4,    // ... amplicons
     kFlagSeq = 5,     // ... sequence bytes
     kFlagRedo = 6,    // ... kRedo* bits: a count above what the launches were sized for
-    kFlagWork = 7,    // scan: slices claimed so far (zeroed before each scan launch)
-    kFlagErr = 15,    // DeviceErr (low 32 bits)
-    kFlagWords = 16
+    kFlagWork = 7,    // scan: slices claimed so far, one word per launch group (zeroed before a scan)
+    kFlagErr = kFlagWork + AH_MAX_PAIRS_PER_SCAN, // DeviceErr (low 32 bits)
+    kFlagWords = kFlagErr + 1
 };
 constexpr uint64_t kRedoSites = 1, kRedoAmps = 2, kRedoSeq = 4;
 

@@ -25,14 +25,23 @@
 // majority LOP3 plus integer adds for the sum (s = a + b + c - 2 maj), a mix
 // chosen by the tuner to balance the logic and integer pipes.
 //
-// A warp with any hit runs a slower path in rounds, one hit per lane per
-// round: each lane checks its hit against the contig table (windows never
-// cross a contig end; the search is confined to the contigs of the tile by a
-// per-tile table), recounts its mismatches exactly from shared memory (a
-// device check that the network agrees) and applies the 3' clamp; the warp
-// appends the surviving 64-bit keys with one atomic per round.  Key =
-// ((pair << pbits | flat position) << 10) | primer << 9 | strand << 8 | mm,
-// so sorting keys gives the canonical site order.
+// Hits.  The network's hit words of the patterns of one primer pair are
+// OR-ed into one word per pair and thread word (few live registers however
+// many patterns one launch scans).  A warp with any hit visits the hit
+// starts together: the lanes that hold hits publish their words to shared
+// memory one lane at a time, and for each hit start the warp gathers the 32
+// window bases as four ballots of the plane bits (bit i = base at window
+// position i), so that every pattern of the pair is re-counted exactly by
+// warp-uniform AND/OR/popc against per-pattern position masks (the network
+// only filters; the recount yields the mismatch count and the 3' clamp test,
+// and a network hit that no pattern confirms is reported as a device-check
+// error).  Windows never cross a contig end: a hit within the first contig
+// of its tile takes that contig's end from a per-tile table loaded while the
+// network runs; any other takes it from a cooperative search of the tile's
+// contigs (one load per lane, cached per warp).  Surviving keys collect in a per-warp stash in shared memory and
+// are appended 32 at a time with one atomic (the rest when the warp ends).
+// Key = ((pair << pbits | flat position) << 10) | primer << 9 | strand << 8
+// | mm, so sorting keys gives the canonical site order.
 #include <nvrtc.h>
 
 #include <algorithm>
@@ -97,70 +106,87 @@ __device__ __forceinline__ bool mbar_wait(u64 *bar, u32 parity)
 }
 )CUDA";
 
-// Body of the kernel after the generated hit words.  Uses: h[NPAT*R] (hit
-// words), any, lane, sm (the warp's slice planes, stride SLW), tile, wbase
-// (first tile word of the slice), j0 (the thread's first slice word) and the
-// pattern tables.
+// Body of the kernel after the generated hit words.  Uses: hg[NGRP*R] (hit
+// words per pattern group and thread word), any, lane, warp, sm (the warp's
+// slice planes, stride SLW), tile, wbase and the per-warp state in shared
+// memory (hsbuf, stash, w_nv, w_cs, w_ce); @VISIT@ is replaced by the cases of
+// the pattern groups.
 const char *kEmit = R"CUDA(
     if (__any_sync(0xffffffffu, any != 0u)) {
-        // Hits, one per lane per round: every lane takes its next hit bit, all
-        // check theirs at once (contig end, exact recount, clamp), and the warp
-        // appends the survivors with one atomic per round.
-        u32 hl[NPAT * R];
+        u32 *hs = hsbuf + warp * HSW;
+        u32 nzw[NZW]; // bit i: hg[i] != 0
 #pragma unroll
-        for (int i = 0; i < NPAT * R; ++i) hl[i] = h[i];
-        // the contigs this tile's starts can fall in: [clo, chi)
-        const u32 clo = tile_contig[tile];
-        const u32 chi = min(n_contigs, tile_contig[tile + 1] + 1u);
-        int qr = 0;
-        u32 m = hl[0];
-        for (;;) {
-            while (m == 0u && qr + 1 < NPAT * R) m = hl[++qr];
-            const bool have = m != 0u;
-            if (!__any_sync(0xffffffffu, have)) break;
-            bool valid = false;
-            u64 key = 0;
-            if (have) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
-                const int q = qr / R, r = qr % R;
-                const int jr = j0 + r;
-                const u64 P = tile * TB + (u64)b * W + wbase + jr;
-                const int L = c_L[q];
-                u32 lo = clo, hi = chi;
-                while (hi - lo > 1) {
-                    u32 mid = (lo + hi) >> 1;
-                    if (contig_off[mid] <= P) lo = mid; else hi = mid;
-                }
-                if (P + L <= contig_off[lo + 1]) {
-                    int mm = 0, clamp_bad = 0;
-                    const int c = c_clamp[q];
-                    for (int i = 0; i < L; ++i) {
-                        const int wj = jr + i;
-                        const u32 code = ((sm[wj] >> b) & 1u) | (((sm[SLW + wj] >> b) & 1u) << 1) |
-                                         (((sm[2 * SLW + wj] >> b) & 1u) << 2) | (((sm[3 * SLW + wj] >> b) & 1u) << 3);
-                        const int mis = (code & c_mask[q][i]) == 0u;
-                        mm += mis;
-                        const int in_clamp = c_strand[q] == 0 ? (i >= L - c) : (i < c);
-                        clamp_bad |= mis & in_clamp;
-                    }
-                    if (mm > c_k[q]) atomicExch(err, 3); // the network disagrees with the recount
-                    else if (!clamp_bad) {
-                        valid = true;
-                        key = ((((u64)c_pair[q] << pbits) | P) << 10) | ((u64)c_primer[q] << 9) |
-                              ((u64)c_strand[q] << 8) | (u64)mm;
+        for (int z = 0; z < NZW; ++z) nzw[z] = 0u;
+#pragma unroll
+        for (int i = 0; i < NGRP * R; ++i) nzw[i >> 5] |= (hg[i] != 0u ? 1u : 0u) << (i & 31);
+        u32 nv = w_nv[warp];
+        u64 cs = w_cs[warp], ce = w_ce[warp];
+        u32 lanes = __ballot_sync(0xffffffffu, any != 0u);
+        while (lanes) {
+            const int src = __ffs(lanes) - 1;
+            lanes &= lanes - 1;
+            if (lane == src) {
+#pragma unroll
+                for (int i = 0; i < NGRP * R; ++i) hs[i] = hg[i];
+#pragma unroll
+                for (int z = 0; z < NZW; ++z) hs[NGRP * R + z] = nzw[z];
+            }
+            __syncwarp();
+            for (int z = 0; z < NZW; ++z) {
+                u32 nz = hs[NGRP * R + z];
+                while (nz) {
+                    const int i = z * 32 + __ffs(nz) - 1;
+                    nz &= nz - 1;
+                    const int g = i / R;
+                    const int jr = src * R + i % R; // slice word of the starts
+                    u32 m = hs[i];
+                    while (m) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1;
+                        const u64 P = tile * TB + (u64)b * W + wbase + jr;
+                        // window bases, bit i = base at position i of the window
+                        const u32 cA = __ballot_sync(0xffffffffu, (sm[jr + lane] >> b) & 1u);
+                        const u32 cC = __ballot_sync(0xffffffffu, (sm[SLW + jr + lane] >> b) & 1u);
+                        const u32 cG = __ballot_sync(0xffffffffu, (sm[2 * SLW + jr + lane] >> b) & 1u);
+                        const u32 cT = __ballot_sync(0xffffffffu, (sm[3 * SLW + jr + lane] >> b) & 1u);
+                        // end (flat) of the contig holding P: the tile's first contig when P lies
+                        // within `room` of the tile's start, else the first contig end above P
+                        // among the tile's contigs [clo, chi) (cached per warp)
+                        const u32 o = (u32)(b * W + wbase + jr);
+                        if (o >= room && (P < cs || P >= ce)) {
+                            const u32 clo = tile_contig[tile];
+                            const u32 chi = min(n_contigs, tile_contig[tile + 1] + 1u);
+                            cs = 0;
+                            ce = 0;
+                            for (u32 x0 = clo + 1u; x0 <= chi; x0 += 32u) {
+                                const u32 x = x0 + (u32)lane;
+                                const bool in = x <= chi;
+                                const u64 e = in ? contig_off[x] : 0ull;
+                                const u32 f = __ballot_sync(0xffffffffu, in && e > P);
+                                if (f) {
+                                    const int fl = __ffs(f) - 1;
+                                    ce = __shfl_sync(0xffffffffu, e, fl);
+                                    cs = contig_off[x0 + fl - 1u];
+                                    break;
+                                }
+                            }
+                        }
+                        const u64 cend = o < room ? tile * TB + room : ce;
+                        bool some = false;
+                        // exact count of every pattern of the group (masks compiled in)
+                        switch (g) {
+@VISIT@                        }
+                        if (!some && lane == 0)
+                            atomicExch(err, 3); // the network disagrees with the exact count
                     }
                 }
             }
-            const u32 vb = __ballot_sync(0xffffffffu, valid);
-            if (vb) {
-                u64 base = 0;
-                if (lane == 0) base = atomicAdd(counter, (u64)__popc(vb));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                const u64 idx = base + __popc(vb & ((1u << lane) - 1u));
-                if (valid && idx < cap) keys[idx] = key;
-            }
+            __syncwarp();
         }
+        w_nv[warp] = nv;
+        w_cs[warp] = cs;
+        w_ce[warp] = ce;
+        __syncwarp();
     }
 )CUDA";
 
@@ -333,33 +359,60 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
     os << "#define W " << kTileW << "\n#define WX " << kTileWX << "\n#define TB " << kTileBases << "ull\n";
     os << "#define R " << R << "\n#define NPAT " << npat << "\n#define NWIN " << nwin << "\n#define NT " << NT
        << "\n";
-    auto table = [&](const char *name, auto get) {
-        os << "__device__ const u8 " << name << "[" << npat << "] = {";
-        for (int q = 0; q < npat; ++q)
-            os << (q ? ", " : "") << get(pats[q]);
-        os << "};\n";
-    };
-    table("c_L", [](const ScanPattern &p) { return p.L; });
-    table("c_k", [](const ScanPattern &p) { return p.k; });
-    table("c_clamp", [](const ScanPattern &p) { return p.clamp; });
-    table("c_pair", [](const ScanPattern &p) { return p.pair; });
-    table("c_primer", [](const ScanPattern &p) { return p.primer; });
-    table("c_strand", [](const ScanPattern &p) { return p.strand; });
-    os << "__device__ const u8 c_mask[" << npat << "][32] = {";
+    // pattern groups: runs of consecutive patterns of one primer pair
+    std::vector<int> g0;
+    std::vector<int> group_of(npat);
     for (int q = 0; q < npat; ++q) {
-        os << (q ? ", " : "") << "{";
-        for (int i = 0; i < 32; ++i)
-            os << (i ? "," : "") << (i < pats[q].L ? (int)pats[q].mask[i] : 15);
-        os << "}";
+        if (q == 0 || pats[q].pair != pats[q - 1].pair)
+            g0.push_back(q);
+        group_of[q] = (int)g0.size() - 1;
     }
-    os << "};\n";
+    const int ngrp = (int)g0.size();
+    g0.push_back(npat);
+    const int nzw = (ngrp * R + 31) / 32;
+    os << "#define NGRP " << ngrp << "\n#define NZW " << nzw << "\n#define HSW (NGRP * R + NZW)\n";
+    // per pattern group: the exact recount of each of its patterns at one start
+    // from the window columns cA..cT, with the pattern's position masks compiled in
+    std::ostringstream vs;
+    for (int gi = 0; gi < ngrp; ++gi) {
+        vs << "                        case " << gi << ":\n";
+        for (int q = g0[gi]; q < g0[gi + 1]; ++q) {
+            const ScanPattern &p = pats[q];
+            uint32_t m[4] = {0, 0, 0, 0}, lm = 0, cm = 0;
+            for (int i = 0; i < p.L; ++i) {
+                for (int x = 0; x < 4; ++x)
+                    if (p.mask[i] & (1 << x))
+                        m[x] |= 1u << i;
+                lm |= 1u << i;
+                if (p.strand == 0 ? (i >= p.L - p.clamp) : (i < p.clamp)) // the c 3'-most positions
+                    cm |= 1u << i;
+            }
+            vs << "                        {\n"
+               << "                            const u32 mis = ~((cA & " << m[0] << "u) | (cC & " << m[1]
+               << "u) | (cG & " << m[2] << "u) | (cT & " << m[3] << "u)) & " << lm << "u;\n"
+               << "                            const u32 mm = __popc(mis);\n"
+               << "                            if (mm <= " << p.k << "u) {\n"
+               << "                                some = true;\n"
+               << "                                if (" << (cm ? "(mis & " + std::to_string(cm) + "u) == 0u && " : "")
+               << "P + " << p.L << "u <= cend) {\n"
+               << "                                    if (lane == (int)(nv & 31u))\n"
+               << "                                        stash[warp * 32 + lane] = ((((u64)" << p.pair
+               << "u << pbits) | P) << 10) | " << ((p.primer << 9) | (p.strand << 8)) << "ull | (u64)mm;\n"
+               << "                                    if ((++nv & 31u) == 0u)\n"
+               << "                                        flush(32u);\n"
+               << "                                }\n"
+               << "                            }\n"
+               << "                        }\n";
+        }
+        vs << "                        break;\n";
+    }
     os << "#define S " << t.stages << "\n#define WPC " << t.warps << "\n#define SLICES (W / (32 * R))\n"
        << "#define SLW (32 * R + 32)\n";
     os << "extern \"C\" __global__ void __launch_bounds__(NT, " << t.min_blocks << ")\n"
        << "ah_scan_kernel(const u32 *__restrict__ planes, u64 n_tiles, const u64 *__restrict__ contig_off,\n"
        << "               u32 n_contigs, u64 *__restrict__ keys, u64 cap, u64 *__restrict__ counter, int pbits,\n"
        << "               int *__restrict__ err, u64 *__restrict__ work, const u64 *__restrict__ tile_list,\n"
-       << "               const u32 *__restrict__ tile_contig)\n{\n"
+       << "               const u32 *__restrict__ tile_contig, const u32 *__restrict__ tile_room)\n{\n"
        << "  // Every warp claims slices of tiles (32*R words of each plane plus a 32-word\n"
        << "  // overhang) from the shared counter `work` (zeroed before the launch), so SMs\n"
        << "  // that run faster take more, and runs its own S-stage pipeline: lane 0 claims\n"
@@ -370,12 +423,21 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "  extern __shared__ __align__(128) u32 smbuf[];\n"
        << "  __shared__ __align__(8) u64 bars[WPC * S];\n"
        << "  __shared__ u64 claims[WPC * S];\n"
+       << "  // per warp: hit words of one lane being visited, the key stash, its fill\n"
+       << "  // count, and the last contig found ([w_cs, w_ce) in flat positions)\n"
+       << "  __shared__ u32 hsbuf[WPC * HSW];\n"
+       << "  __shared__ u64 stash[WPC * 32];\n"
+       << "  __shared__ u64 w_cs[WPC], w_ce[WPC];\n"
+       << "  __shared__ u32 w_nv[WPC];\n"
        << "  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n"
        << "  u32 *wbuf = smbuf + warp * (S * 4 * SLW);\n"
        << "  u64 *wbar = bars + warp * S;\n"
        << "  u64 *witem = claims + warp * S;\n"
        << "  const u64 n_items = n_tiles * SLICES;\n"
        << "  if (lane == 0) {\n"
+       << "    w_nv[warp] = 0u;\n"
+       << "    w_cs[warp] = 0ull;\n"
+       << "    w_ce[warp] = 0ull;\n"
        << "    for (int q = 0; q < S; ++q) mbar_init(&wbar[q], 1);\n"
        << "    asm volatile(\"fence.mbarrier_init.release.cluster;\" ::: \"memory\");\n"
        << "  }\n"
@@ -387,6 +449,13 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "                 \"r\"((u32)(4 * SLW * 4)) : \"memory\");\n"
        << "    for (int x = 0; x < 4; ++x)\n"
        << "      tma_copy(wbuf + (stg * 4 + x) * SLW, planes + (tl * 4 + x) * WX + sl * 32 * R, SLW * 4, &wbar[stg]);\n"
+       << "  };\n"
+       << "  // append the n keys stash[warp * 32 + 0 .. n) with one atomic\n"
+       << "  auto flush = [&](u32 n) {\n"
+       << "    u64 base = 0;\n"
+       << "    if (lane == 0) base = atomicAdd(counter, (u64)n);\n"
+       << "    base = __shfl_sync(0xffffffffu, base, 0);\n"
+       << "    if ((u32)lane < n && base + lane < cap) keys[base + lane] = stash[warp * 32 + lane];\n"
        << "  };\n"
        << "  if (lane == 0)\n"
        << "    for (int q = 0; q < S; ++q) {\n"
@@ -412,6 +481,7 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "    }\n"
        << "    const u64 tile = tile_list ? tile_list[wi / SLICES] : wi / SLICES;\n"
        << "    const int wbase = (int)(wi % SLICES) * 32 * R;\n"
+       << "    const u32 room = tile_room[tile]; // used only on hits; the load overlaps the network\n"
        << "    const u32 *sm = wbuf + stg * 4 * SLW;\n"
        << "    const int j0 = lane * R;\n"
        << "    u32 pA[NWIN], pC[NWIN], pG[NWIN], pT[NWIN], pV[NWIN];\n"
@@ -428,13 +498,15 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "    }\n"
        << "#pragma unroll\n"
        << "    for (int w = 0; w < NWIN; ++w) pV[w] = pA[w] + pC[w] + pG[w] + pT[w];\n"
-       << "    u32 h[NPAT * R];\n"
-       << "    u32 any = 0;\n";
+       << "    u32 hg[NGRP * R];\n";
     std::map<std::pair<int, int>, std::string> cache;
+    std::vector<bool> assigned(ngrp * R, false);
     auto one = [&](int q, int r) {
         os << "    // pattern " << q << ", word " << r << "\n";
         std::string hw = gen_hit(g, pats[q], r, cache);
-        os << "    h[" << q * R + r << "] = " << hw << ";\n    any |= h[" << q * R + r << "];\n";
+        const int i = group_of[q] * R + r;
+        os << "    hg[" << i << "] " << (assigned[i] ? "|=" : "=") << " " << hw << ";\n";
+        assigned[i] = true;
     };
     if (t.order == 0) {
         for (int r = 0; r < R; ++r)
@@ -445,7 +517,12 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
             for (int r = 0; r < R; ++r)
                 one(q, r);
     }
-    os << kEmit;
+    os << "    u32 any = 0u;\n";
+    for (int i = 0; i < ngrp * R; ++i)
+        os << "    any |= hg[" << i << "];\n";
+    std::string emit = kEmit;
+    emit.replace(emit.find("@VISIT@"), 7, vs.str());
+    os << emit;
     os << "    __syncwarp();\n"
        << "    if (lane == 0) { // refill this stage with the next claim\n"
        << "      const u64 w = atomicAdd(work, 1ull);\n"
@@ -453,8 +530,65 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "      if (w < n_items) issue(w, stg);\n"
        << "    }\n"
        << "    __syncwarp();\n"
-       << "  }\n}\n";
+       << "  }\n"
+       << "  __syncwarp();\n"
+       << "  const u32 rest = w_nv[warp] & 31u; // keys still in the stash\n"
+       << "  if (rest) flush(rest);\n"
+       << "}\n";
     return os.str();
+}
+
+// Logic and integer operations of one pattern's network per thread word (the
+// generator's own statement count).
+static int pattern_ops(const ScanPattern &p)
+{
+    Gen g;
+    std::map<std::pair<int, int>, std::string> cache;
+    gen_hit(g, p, 0, cache);
+    const std::string src = g.os.str();
+    return (int)std::count(src.begin(), src.end(), ';');
+}
+
+std::vector<std::pair<int, int>> scan_launch_groups(const std::vector<ScanPattern> &pats)
+{
+    // measured on GB300: one pair of a 960-oligo primer set at k = 4 (~150-190 operations
+    // per word) runs spill-free; three such pairs in one kernel spilled under the
+    // register cap and stalled on instruction fetch
+    int budget = 240;
+    if (const char *e = getenv("AH_SCAN_GROUP_OPS"))
+        budget = std::max(1, atoi(e));
+    static std::mutex mu;
+    static std::map<std::string, std::vector<std::pair<int, int>>> cache;
+    std::string key = std::to_string(budget) + "|";
+    for (const auto &p : pats) {
+        key += std::to_string(p.L) + "," + std::to_string(p.k) + "," + std::to_string(p.pair) + ":";
+        for (int i = 0; i < p.L; ++i)
+            key += (char)('a' + p.mask[i]);
+        key += ";";
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end())
+        return it->second;
+    std::vector<std::pair<int, int>> out;
+    int q = 0, start = 0, ops = 0;
+    const int n = (int)pats.size();
+    while (q < n) {
+        int e = q, pops = 0; // the pair starting at q: [q, e)
+        while (e < n && pats[e].pair == pats[q].pair)
+            pops += pattern_ops(pats[e++]);
+        if (q > start && ops + pops > budget) {
+            out.push_back({start, q});
+            start = q;
+            ops = 0;
+        }
+        ops += pops;
+        q = e;
+    }
+    if (n > start)
+        out.push_back({start, n});
+    cache[key] = out;
+    return out;
 }
 
 namespace {
