@@ -1,19 +1,20 @@
 #!/usr/bin/env python3
 """Benchmark of the in-silico PCR hot path on one GB300 (or N, one process per GPU).
 
-Workload (N = 1): the genome-collection configuration -- 100 synthetic
-genomes, lengths log-uniform in 2-7 Mbp (~0.4 Gbp), 1-200 contigs each, GC
-U(0.3, 0.7), 0.1% N runs, planted operon-like regions; one degenerate pair of
-20 and 22 nt with 960 oligos in total; k = 3; window 100-2500 bp; Tm with
-50 mM Na+, 0.25 uM primer, threshold 50 C.
+Default workload (N = 1): the large collection -- 50,000 synthetic genomes of
+1-8 Mbp (169 Gbp, counter-based generator, seed 7), 1-200 contigs each, GC
+U(0.3, 0.7), 0.1% N runs, planted operon-like regions; three degenerate pairs
+of 960, 64 and 256 oligos at k = 4; window 100-3000 bp; Tm threshold 50 C.
 
-One step = the whole hot path on that batch through the C ABI: load/pack the
-resident ASCII genomes, scan both strands, Tm of every site, pair, fetch the
-amplicon sequences.  `value` is Gbp scanned per primer pair per second with
-the inputs already in HBM; `e2e` is the same with host (pinned) input and
-output buffers, the copies inside the timed region.  Under torchrun every
-rank scans its own seeded collection (weak scaling, no data-path collective);
-value = all ranks' bases / max rank time.
+One step = the whole hot path over the collection through the C ABI, in
+chunks of whole genomes: load/pack the resident ASCII bases, scan both
+strands for the three pairs, Tm of every site, pair, fetch the amplicon
+sequences.  `value` is bases x pairs scanned per second with the inputs
+already in HBM; `e2e` is the same with host (pinned) input and output
+buffers on the first chunk(s), the copies inside the timed region; the
+`collection` key is the 100-genome (0.4 Gbp, one pair, k = 3) workload.
+Under torchrun every rank scans its own seeded collection (weak scaling, no
+data-path collective); value = all ranks' bases x pairs / max rank time.
 
 --impl reference times the CPU oracle on a bounded sample of the same
 workload (the reference arm of this benchmark).
@@ -176,6 +177,9 @@ def cpu_baseline(w, target_s: float = 15.0):
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands, on the host cores, on a
+    bounded sample of the large workload (genomes drawn with seed 7), for the
+    same metric and unit as the default line."""
     rank, world, _ = dist_info()
     if world > 1:
         import torch.distributed as dist
@@ -183,19 +187,24 @@ def run_reference(args):
         if rank != 0:
             dist.barrier()
             return
-    w = workload(1, args.n_genomes)
-    steps = []
+    pairs = large_pairs()
+    coll = large_collection(7, args.n_genomes)
+    cores = os.cpu_count() or 1
+    sample = oracle_sample(coll, args.ref_seconds, cores)
+    nb = int(sum(coll.genome_off[g + 1] - coll.genome_off[g] for g in sample.tolist()))
+    vals = []
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(w, target_s=args.ref_seconds)
+        _, t = oracle_on_genomes(coll, pairs, sample, cores)
         if i >= args.warmup:
-            steps.append(r)
-    v = float(np.mean([r["value"] for r in steps]))
+            vals.append(nb * len(pairs) / t / 1e9)
+    v = float(np.mean(vals))
+    desc = (f"{len(sample)} of {len(coll.genome_off) - 1} genomes drawn with seed 7 ({nb / 1e6:.1f} Mbp), "
+            f"3 pairs, scan+Tm+pair+fetch per step")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gbp/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": steps[0]["sample"]},
-            "cpu_baseline": {"value": v, "unit": "Gbp/s", "cores": steps[0]["cores"], "kind": "oracle",
-                             "sample": steps[0]["sample"]},
+            "config": {"workload": LARGE_WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": v, "unit": "Gbp/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": "Gbp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -237,11 +246,14 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default (or AH_SCAN_TUNING) scan variant")
-    ap.add_argument("--n-genomes", type=int, default=100, help="smaller collections for profiling runs")
+    ap.add_argument("--n-genomes", type=int, default=None, help="smaller collections for profiling runs")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="one set at a time (default: the next set packs on a second stream after the current scan)")
-    ap.add_argument("--form", default="plain", choices=["plain", "batched", "served", "large", "hmm"],
-                    help="plain: the genome-collection line (default); batched / served: those forms' lines")
+    ap.add_argument("--form", default="large", choices=["large", "collection", "plain", "batched", "served", "hmm"],
+                    help="large: the 50,000-genome line (default); collection (alias plain): the 100-genome "
+                         "line; batched / served / hmm: those forms' lines")
+    ap.add_argument("--e2e-chunks", type=int, default=1, help="large: chunks timed end to end from host input")
+    ap.add_argument("--no-collection", action="store_true", help="large: skip the collection workload's key")
     ap.add_argument("--chunk-bases", type=int, default=2_000_000_000, help="batched: bases per set (whole genomes)")
     ap.add_argument("--plain-genomes", type=int, default=400, help="batched: genomes timed in the plain form")
     ap.add_argument("--requests", type=int, default=2000, help="served: requests")
@@ -255,7 +267,7 @@ def main():
     ap.add_argument("--check-dump", default=None, help="oracle check of a large-form dump (CPU only)")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = 2 if args.impl == "reference" else {"batched": 2, "hmm": 10}.get(args.form, 1000)
+        args.steps = 2 if args.impl == "reference" else {"batched": 2, "hmm": 10, "large": 10}.get(args.form, 1000)
     if args.check_dump:
         sys.exit(check_large_dump(args.check_dump))
     if args.impl == "reference":
@@ -264,11 +276,16 @@ def main():
         return bench_batched(args)
     if args.form == "served":
         return bench_served(args)
-    if args.form == "large":
-        return bench_large(args)
     if args.form == "hmm":
         return bench_hmm(args)
+    if args.form in ("collection", "plain"):
+        return bench_collection(args)
+    return bench_large_main(args)
 
+
+def bench_collection(args, emit: bool = True):
+    """The genome-collection workload (100 genomes, 0.4 Gbp, one 960-oligo pair,
+    k = 3): one step = load/pack + run of the whole collection."""
     rank, world, local = dist_info()
     import torch
     if world > 1:
@@ -278,7 +295,7 @@ def main():
     from paper_2509_13300_gb300 import ah, build
     build.build()
 
-    w = workload(1 + rank, args.n_genomes)
+    w = workload(1 + rank, args.n_genomes or 100)
     p = w.pairs[0]
     n_bases = w.n_bases
     # one stream carries the library's work and the timing events
@@ -455,7 +472,7 @@ def main():
 
     if rank != 0:
         ctx.close()
-        return
+        return None
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(w)
     line = {
         "metric": METRIC, "value": value, "unit": "Gbp/s", "n_gpus": world, "steps": args.steps,
@@ -473,8 +490,10 @@ def main():
         "gpu_launches": int(total_launches), "clocks": clocks,
         "timed_region_kernel_us": {st: live[st]["avg_launch_us"] for st in live},
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
     ctx.close()
+    return line
 
 
 def ctx_scan_lop_count(pair: dict, tune: dict) -> int:
@@ -583,7 +602,7 @@ def bench_batched(args):
     from paper_2509_13300_gb300 import ah, build, countergen
     build.build()
     torch.cuda.set_device(0)
-    n_g = args.n_genomes if args.n_genomes != 100 else 10_000
+    n_g = args.n_genomes or 10_000
     pairs = synthetic_pairs(2, (2, 3, 4, 2))
     t0 = time.perf_counter()
     coll = countergen.collection(seed=2, n_genomes=n_g, len_lo=0.5e6, len_hi=8e6, pairs=pairs)
@@ -747,7 +766,7 @@ def bench_served(args):
     from paper_2509_13300_gb300 import ah, build, countergen
     build.build()
     torch.cuda.set_device(0)
-    n_g = args.n_genomes if args.n_genomes != 100 else 5_000
+    n_g = args.n_genomes or 5_000
     pairs = paper_pairs(4) + synthetic_pairs(3, (4,))
     t0 = time.perf_counter()
     coll = countergen.collection(seed=3, n_genomes=n_g, len_lo=2e6, len_hi=7e6, pairs=pairs)
@@ -920,6 +939,10 @@ class DevOut:
                 self.alloc((o.n_sites * 5 // 4 + 1, o.n_amplicons * 5 // 4 + 1, o.n_seq * 5 // 4 + 1))
         raise RuntimeError("ah_run kept overflowing")
 
+    def host_seq(self, m, q):
+        """Sequence bytes and offsets of the last run's m amplicons."""
+        return (self.b[4][:q].cpu().numpy().tobytes(), self.b[5][:8 * (m + 1)].cpu().numpy().view(np.uint64))
+
     def host(self, n, m):
         """Sites, Tm, pass and amplicons of the last run, as numpy arrays."""
         from paper_2509_13300_gb300 import ah
@@ -969,135 +992,340 @@ def check_genome_against_oracle(coll, pairs, g, got, cores):
             "amplicons_equal": ag.tobytes() == am.tobytes()}
 
 
-def bench_large(args):
-    """Large-scale form: a counter-generated collection (50,000 genomes of 1-8 Mbp,
-    seed 7) generated on the device chunk by chunk (whole genomes, up to 16 Gbp
-    per chunk) and streamed through the path with three pairs scanned in one
-    launch; a seeded sample of genomes is checked against the oracle."""
+LARGE_WORKLOAD = "large-50000genomes-169Gbp-3pairs-k4"
+
+
+def large_collection(seed: int = 7, n_genomes: int | None = None):
+    """The large workload's layout: 50,000 counter-generated genomes of 1-8 Mbp
+    (seed 7), the three pairs of large_pairs()."""
+    from paper_2509_13300_gb300 import countergen
+    return countergen.collection(seed=seed, n_genomes=n_genomes or 50_000, len_lo=1e6, len_hi=8e6,
+                                 pairs=large_pairs())
+
+
+def oracle_sample(coll, target_s: float, cores: int, seed: int = 7):
+    """Genomes drawn in a seeded random order until about target_s of oracle
+    work (the oracle scans ~0.12 Mbp/s per core with these three pairs at k = 4)."""
+    order = np.random.default_rng(seed).permutation(len(coll.genome_off) - 1)
+    gl = np.diff(coll.genome_off.astype(np.int64))
+    want = max(1.0e6, 0.12e6 * cores * target_s)
+    n = int(np.searchsorted(np.cumsum(gl[order]), want)) + 1
+    return np.sort(order[:max(1, min(n, len(order)))])
+
+
+def oracle_on_genomes(coll, pairs, genomes, cores):
+    """The oracle (scan, Tm, pair, fetch) on each genome alone; bases from the
+    CPU twin of the counter-based generator.  Returns per genome (sites, Tm,
+    pass, amplicons, sequences, sequence offsets) and the oracle's seconds."""
+    import oracle
+    out, t = {}, 0.0
+    for g in genomes.tolist():
+        a, b = int(coll.genome_off[g]), int(coll.genome_off[g + 1])
+        seq = coll.bases(a, b)
+        c0 = int(np.searchsorted(coll.contig_off, a, side="left"))
+        c1 = int(np.searchsorted(coll.contig_off, b, side="left"))
+        off = (coll.contig_off[c0:c1 + 1] - np.uint64(a)).astype(np.uint64)
+        gen_ = np.full(c1 - c0, g, dtype=np.uint32)
+        t0 = time.perf_counter()
+        s_ = oracle.scan(seq, off, gen_, pairs, n_threads=cores)
+        tm, ps = oracle.tm(seq, off, s_, pairs, n_threads=cores)
+        am = oracle.pair(s_, pairs, ps)
+        qs, qo = oracle.fetch(seq, off, am)
+        t += time.perf_counter() - t0
+        out[g] = (s_, tm, ps, am, qs, qo)
+    return out, t
+
+
+def parity_summary(coll, got, want):
+    """Compare the GPU's records of each sampled genome with the oracle's:
+    bit-exact sites, pass flags, amplicons and sequences; Tm within 0.01 C."""
+    res = {"genomes": 0, "bases": 0, "sites": 0, "amplicons": 0, "sites_equal": True, "pass_equal": True,
+           "tm_nan_equal": True, "amplicons_equal": True, "sequences_equal": True, "max_dtm_C": 0.0}
+    for g, (s_, tm, ps, am, qs, qo) in want.items():
+        sg, tg, pg, ag, gq, go = got[g]
+        ok = ~np.isnan(tm)
+        res["genomes"] += 1
+        res["bases"] += int(coll.genome_off[g + 1] - coll.genome_off[g])
+        res["sites"] += len(s_)
+        res["amplicons"] += len(am)
+        res["sites_equal"] &= sg.tobytes() == s_.tobytes()
+        res["pass_equal"] &= bool(np.array_equal(pg, ps))
+        res["tm_nan_equal"] &= bool(np.array_equal(np.isnan(tg), ~ok))
+        if ok.any() and len(tg) == len(tm):
+            res["max_dtm_C"] = max(res["max_dtm_C"], float(np.abs(tg[ok].astype(np.float64) - tm[ok]).max()))
+        res["amplicons_equal"] &= ag.tobytes() == am.tobytes()
+        res["sequences_equal"] &= gq == qs and np.array_equal(go.astype(np.uint64), qo.astype(np.uint64))
+    res["all_equal"] = bool(res["sites_equal"] and res["pass_equal"] and res["tm_nan_equal"] and
+                            res["amplicons_equal"] and res["sequences_equal"] and res["max_dtm_C"] <= 0.01)
+    return res
+
+
+def genome_records(coll, chunk_tab, res, g):
+    """Records of genome g out of its chunk's run outputs, re-indexed as the
+    genome alone (contigs from 0, amplicon ends into the genome's own sites),
+    with its amplicons' sequences and offsets."""
+    sites, tm, ps, amps, seq, offs = res
+    sg, tg, pg, am = genome_slice(coll, chunk_tab, (sites, tm, ps, amps), g)
+    sel = np.nonzero(amps["genome"] == g)[0]
+    parts = [seq[int(offs[i]):int(offs[i + 1])] for i in sel]
+    q = b"".join(parts)
+    qo = np.concatenate([[0], np.cumsum([len(x) for x in parts])]).astype(np.uint64)
+    return sg, tg, pg, am, q, qo
+
+
+def bench_large_main(args):
+    """Default line: the large workload (50,000 genomes, 169 Gbp, three pairs of
+    960, 64 and 256 oligos at k = 4, window 100-3000 bp, Tm threshold 50 C).
+
+    The ASCII bases are generated on the device once, before the timed region
+    (counter-based Philox4x32-10, seed 7 + rank), and stay resident in HBM.
+    One step = one pass over the collection in chunks of whole genomes
+    (<= 16 Gbp): pack (ah_load_genomes from the resident bases), scan of the
+    three pairs, canonical sort, Tm, Tm-filtered pairing and fetch
+    (ah_run_begin / ah_run_end) into device buffers; chunk i+1 packs on a
+    second stream once chunk i's scan is done.  value = bases x pairs x steps /
+    time.  Under torchrun every rank runs its own collection (weak scaling)."""
+    rank, world, local = dist_info()
     import torch
-    from paper_2509_13300_gb300 import ah, build, countergen
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_2509_13300_gb300 import ah, build
     build.build()
-    torch.cuda.set_device(0)
-    n_g = args.n_genomes if args.n_genomes != 100 else 50_000
     pairs = large_pairs()
     t0 = time.perf_counter()
-    coll = countergen.collection(seed=7, n_genomes=n_g, len_lo=1e6, len_hi=8e6, pairs=pairs)
+    coll = large_collection(7 + rank, args.n_genomes)
     t_layout = time.perf_counter() - t0
-    ctx = ah.Context(0)
+    n_g = len(coll.genome_off) - 1
+    N, npair = coll.n_bases, len(pairs)
+    ctx = ah.Context(local)
     pids = [ctx.ah_set_primers(p["fwd"], p["rev"], p) for p in pairs]
-    N = coll.n_bases
+    t0 = time.perf_counter()
+    seq_d = device_collection(ctx, coll, torch)  # resident ASCII, generated outside the timed region
+    t_gen = time.perf_counter() - t0
     tabs = [sub_tables(coll, g0, g1) for g0, g1 in genome_chunks(coll, args.large_chunk)]
     cmax = max(b1 - b0 for b0, b1, _, _ in tabs)
-    abuf = [torch.empty(cmax + 3, dtype=torch.uint8, device="cuda") for _ in range(min(2, len(tabs)))]
-    tables = ctx.device_tables(coll)  # segments and patches of the whole collection, on the device once
-    st = [torch.cuda.Stream(), torch.cuda.Stream()]
-    out = DevOut(torch, ah, (cmax * 1.2e-3, 1 << 18, 1 << 28))
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    scan_done = torch.cuda.Event()
 
-    def gen_load(i):
+    def load(i, s):
         b0, b1, off, gen_ = tabs[i]
-        s = st[i % 2]
-        a0 = b0 - b0 % 4  # generated ranges start on a multiple of 4
-        # stream-ordered: chunk i+1 is generated and packed beside chunk i's run
-        ctx.generate_bases(coll, a0, b1 - a0, abuf[i % 2], stream=s, tables=tables)
-        return ctx.ah_load_genomes(abuf[i % 2][b0 - a0:], b1 - b0, off, gen_, s)
+        return ctx.ah_load_genomes(seq_d[b0:b1], b1 - b0, off, gen_, s)
 
+    # tuning on the first chunk; output capacities from one pass of ah_run
+    sid = load(0, streams[0])
+    tune = None if args.no_tune else ctx.ah_tune_scan(sid, pids, 0, streams[0])
+    ctx.ah_unload_genomes(sid)
+    out = DevOut(torch, ah, (cmax * 1.2e-3 * npair / 3, 1 << 16, 1 << 26))
+    caps = [0, 0, 0]
+    for i in range(len(tabs)):
+        sid = load(i, streams[0])
+        out.run(ctx, sid, pids, streams[0])
+        o = out.o
+        caps = [max(caps[0], o.n_sites), max(caps[1], o.n_amplicons), max(caps[2], o.n_seq)]
+        ctx.ah_unload_genomes(sid)
+    out.alloc((caps[0] * 9 // 8 + 1024, caps[1] * 9 // 8 + 64, caps[2] * 9 // 8 + 4096))
     totals = {}
 
     def one_pass(keep=None):
+        """Every chunk once, two sets in flight: chunk i+1 is packed on the other
+        stream once chunk i's scan has finished (ah_run_begin records scan_done)."""
         n_s = n_a = n_q = 0
         kept = {}
-        sid = gen_load(0)
+        prev = load(0, streams[0])
         for i in range(len(tabs)):
-            nxt = gen_load(i + 1) if i + 1 < len(tabs) else None   # packs beside run i
-            out.run(ctx, sid, pids, st[i % 2])
+            ctx.ah_run_begin(prev, pids, out.o, streams[i % 2], scan_done)
+            nxt = None
+            if i + 1 < len(tabs):
+                streams[(i + 1) % 2].wait_event(scan_done)
+                nxt = load(i + 1, streams[(i + 1) % 2])
+            ctx.ah_run_end(out.o)
             o = out.o
             n_s, n_a, n_q = n_s + o.n_sites, n_a + o.n_amplicons, n_q + o.n_seq
             if keep is not None and keep.get(i):
-                res = out.host(o.n_sites, o.n_amplicons)
+                torch.cuda.synchronize()
+                res = out.host(o.n_sites, o.n_amplicons) + out.host_seq(o.n_amplicons, o.n_seq)
                 for g in keep[i]:
-                    kept[g] = genome_slice(coll, tabs[i], res, g)
-            ctx.ah_unload_genomes(sid)
-            sid = nxt
+                    kept[g] = genome_records(coll, tabs[i], res, g)
+            ctx.ah_unload_genomes(prev)
+            prev = nxt
         totals.update(sites=n_s, amplicons=n_a, seq_bytes=n_q)
         return kept
 
-    sid0 = gen_load(0)
-    tune = None if args.no_tune else ctx.ah_tune_scan(sid0, pids, 0, st[0])
-    ctx.ah_unload_genomes(sid0)
+    for _ in range(max(3, args.warmup)):
+        one_pass()
     torch.cuda.synchronize()
-    one_pass()                    # warm-up: sizes the outputs
+    # timed region: CUDA events on the launching streams; pack and scan stages timed live
+    ctx.ah_set_profiling(3)
+    barrier(world)
     torch.cuda.synchronize()
-    ctx.ah_set_profiling(0)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clk:
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with ClockSampler(local) as clk:
         clk.wait_first()
         clk.mark(True)
-        e0.record(st[0])
-        one_pass()
-        st[0].wait_stream(st[1])
-        e1.record(st[0])
+        ev[0].record(streams[0])
+        for _ in range(args.steps):
+            one_pass()
+        streams[0].wait_stream(streams[1])
+        ev[1].record(streams[0])
         torch.cuda.synchronize()
         clk.mark(False)
-    _, launches, _ = ctx.ah_get_profile(None)
-    t_all = e0.elapsed_time(e1) / 1e3
-    # stage split: one more pass with events around every stage (untimed)
+    barrier(world)
+    t_ms = ev[0].elapsed_time(ev[1])
+    t_max = max_over_ranks(t_ms, world)
+    bases_all = sum_over_ranks(float(N), world)
+    value = bases_all * npair * args.steps / (t_max / 1e3) / 1e9
+    live = {}
+    for st in ("pack", "scan"):
+        ms, launches, calls = ctx.ah_get_profile(st)
+        live[st] = {"ms_per_step": ms / args.steps, "launches_per_step": launches / args.steps}
+    _, total_launches, _ = ctx.ah_get_profile(None)
+    # stage breakdown: one more pass with events around every stage (untimed)
     ctx.ah_set_profiling(1)
     one_pass()
-    stages = {}
-    for name in ("generate", "pack", "tables", "scan", "sort", "decode", "tm", "pair", "fetch"):
-        ms, l, calls = ctx.ah_get_profile(name)
-        stages[name] = {"ms": ms, "launches": l}
+    stages = {"note": "untimed pass, CUDA events around every stage; chunk i+1's packing overlaps chunk i's run"}
+    for st in ("pack", "tables", "scan", "sort", "decode", "tm", "pair", "fetch"):
+        ms, launches, calls = ctx.ah_get_profile(st)
+        stages[st] = {"ms_per_step": ms, "launches_per_step": launches}
     ctx.ah_set_profiling(0)
-    scan_s = stages["scan"]["ms"] / 1e3
+
+    # ---- roofline of the dominant kernel (live CUDA-event durations of the timed region) ----
     hbm_peak, peak_kind, _ = load_peaks()
-    # the oracle on a seeded sample of genomes
-    rng = np.random.default_rng(7)
-    sample = np.sort(rng.choice(n_g, size=min(n_g, max(args.check_genomes, args.dump_genomes)), replace=False))
-    chunk_of = np.searchsorted(np.array([b1 for _, b1, _, _ in tabs]), coll.genome_off[sample], side="right")
-    keep = {}
-    for g, ci in zip(sample.tolist(), chunk_of.tolist()):
-        keep.setdefault(ci, []).append(g)
-    kept = one_pass(keep)
-    checks = []
-    cores = os.cpu_count() or 1
-    for g in sample[:args.check_genomes].tolist():
-        checks.append(check_genome_against_oracle(coll, pairs, g, kept[g], cores))
-    if args.dump_genomes:
-        os.makedirs(os.path.dirname(os.path.abspath(args.dump_path)), exist_ok=True)
-        arrs = {}
-        for g in sample.tolist():
-            sg, tg, pg, ag = kept[g]
-            arrs.update({f"s{g}": sg, f"t{g}": tg, f"p{g}": pg, f"a{g}": ag})
-        np.savez_compressed(args.dump_path, sample=sample, n_genomes=n_g, **arrs)
-    all_ok = all(c["sites_equal"] and c["pass_equal"] and c["tm_nan_equal"] and c["amplicons_equal"]
-                 and c["tm_max_err"] <= 0.01 for c in checks)
+    clocks = clk.summary()
+    clk_mhz = clocks["sm_mhz"] or 2070.0
+    scan_s = live["scan"]["ms_per_step"] / 1e3
+    pack_s = live["pack"]["ms_per_step"] / 1e3
+    words = N / 32.0
+    lop = sum(ah.scan_lop3_per_word(p["fwd"], p["rev"], int(p["k"]), (tune or {}).get("R", 4), 0) for p in pairs)
+    alu_peak = SMS * LOP_LANES_PER_CLK * clk_mhz * 1e6 / 1e12
+    scan_tops = lop * words / scan_s / 1e12
+    scan_hbm = 0.5 * N * live["scan"]["launches_per_step"] / scan_s / 1e9  # each launch reads the planes once
+    pack_hbm = 1.5 * N / pack_s / 1e9
+    # the scan dominates the serialised launch list; the packing's live time is
+    # stretched by the run it overlaps, so it is reported beside (pack_roofline)
+    tr_pack = traffic_record("pack_kernel")
+    pack_roof = {"bound": "hbm", "achieved": pack_hbm, "peak": hbm_peak, "unit": "GB/s", "frac": pack_hbm / hbm_peak,
+                 "traffic": tr_pack["dram_bytes_per_launch"] if tr_pack else None, "kernel": "pack_kernel",
+                 "peak_kind": peak_kind, "algorithmic": "1.5 B/base (1 B ASCII read + 0.5 B planes written)",
+                 "note": "live duration includes the sort/Tm/pair/fetch kernels of the previous chunk it runs beside"}
+    tr = traffic_record("ah_scan_kernel")
+    roof = {"bound": "alu", "achieved": scan_tops, "peak": alu_peak, "unit": "Tops/s",
+            "frac": scan_tops / alu_peak, "traffic": tr["dram_bytes_per_launch"] if tr else None,
+            "kernel": "ah_scan_kernel",
+            "peak_note": f"logic pipe: {SMS} SMs x {LOP_LANES_PER_CLK} LOP3 lanes/clk (measured) x {clk_mhz:.0f} "
+                         f"MHz (median SM clock under load)",
+            "algorithmic": f"{lop} LOP3 per 32 starts for the three pairs ({len(tabs)} chunks x "
+                           f"{live['scan']['launches_per_step'] / len(tabs):.0f} launches per chunk)",
+            "hbm_achieved_gbs": scan_hbm, "hbm_peak_gbs": hbm_peak, "hbm_frac": scan_hbm / hbm_peak,
+            "hbm_peak_kind": peak_kind, "hbm_algorithmic": "0.5 B/base of planes per launch"}
+    roof["scope"] = "all launches of the kernel in one step, summed; per-launch traffic from the ncu capture"
+
+    # ---- end to end through the C ABI: host (pinned) input and outputs, the first chunks ----
+    e2e = None
+    ne = min(max(0, args.e2e_chunks), len(tabs))
+    if ne > 0:
+        hb0, hb1 = tabs[0][0], tabs[ne - 1][1]
+        host = torch.empty(hb1 - hb0, dtype=torch.uint8, pin_memory=True)
+        host.copy_(seq_d[hb0:hb1])
+        hout = HostOut(torch, ah, (caps[0] * 9 // 8 + 1024, caps[1] * 9 // 8 + 64, caps[2] * 9 // 8 + 4096))
+
+        def host_pass():
+            h2d = d2h = 0
+            b0, b1, off, gen_ = tabs[0]
+            prev = ctx.ah_load_genomes(host[b0 - hb0:b1 - hb0], b1 - b0, off, gen_, streams[0])
+            h2d += b1 - b0 + off.nbytes + gen_.nbytes
+            for i in range(ne):
+                ctx.ah_run_begin(prev, pids, hout.o, streams[i % 2], None)
+                nxt = None
+                if i + 1 < ne:
+                    b0, b1, off, gen_ = tabs[i + 1]
+                    nxt = ctx.ah_load_genomes(host[b0 - hb0:b1 - hb0], b1 - b0, off, gen_, streams[(i + 1) % 2])
+                    h2d += b1 - b0 + off.nbytes + gen_.nbytes
+                ctx.ah_run_end(hout.o)
+                d2h += hout.d2h_bytes()
+                ctx.ah_unload_genomes(prev)
+                prev = nxt
+            return h2d, d2h
+
+        host_pass()
+        reps = max(1, args.e2e_steps // 5)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(streams[0])
+        for _ in range(reps):
+            h2d, d2h = host_pass()
+        streams[0].wait_stream(streams[1])
+        e1.record(streams[0])
+        torch.cuda.synchronize()
+        e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+        sub = sum_over_ranks(float(hb1 - hb0), world)
+        e2e = {"value": sub * npair * reps / (e_ms / 1e3) / 1e9, "unit": "Gbp/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": reps,
+               "subset": f"first {ne} of {len(tabs)} chunks ({(hb1 - hb0) / 1e9:.1f} Gbp of {N / 1e9:.1f}) per step",
+               "pipeline": "the next chunk's host load (copy + packing) is issued while the current run computes"}
+        del host
+
+    # ---- oracle sample: the CPU baseline and parity with the GPU's records of the same genomes ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        sample = oracle_sample(coll, 15.0, cores)
+        chunk_of = np.searchsorted(np.array([b1 for _, b1, _, _ in tabs]), coll.genome_off[sample], side="right")
+        keep = {}
+        for g, ci in zip(sample.tolist(), chunk_of.tolist()):
+            keep.setdefault(ci, []).append(g)
+        got = one_pass(keep)
+        want, t_cpu = oracle_on_genomes(coll, pairs, sample, cores)
+        nb = int(sum(coll.genome_off[g + 1] - coll.genome_off[g] for g in sample.tolist()))
+        cpu = {"value": nb * npair / t_cpu / 1e9, "unit": "Gbp/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(sample)} of {n_g} genomes drawn with seed 7 ({nb / 1e6:.1f} Mbp), 3 pairs, "
+                         f"scan+Tm+pair+fetch, {t_cpu:.1f} s",
+               "parity": parity_summary(coll, got, want)}
+        if args.dump_genomes:
+            arrs = {}
+            for g in sample.tolist():
+                sg, tg, pg, ag, _, _ = got[g]
+                arrs.update({f"s{g}": sg, f"t{g}": tg, f"p{g}": pg, f"a{g}": ag})
+            np.savez_compressed(args.dump_path, sample=sample, n_genomes=n_g, **arrs)
+    del seq_d
+    ctx.close()
+    torch.cuda.empty_cache()
+
+    # ---- the collection workload's key (100 genomes, 0.4 Gbp, one pair, k = 3) ----
+    coll_key = None
+    if not args.no_collection and world == 1:
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.warmup, sub.e2e_steps, sub.no_cpu_baseline, sub.n_genomes = 400, 5, 0, True, None
+        c = bench_collection(sub, emit=False)
+        if c:
+            coll_key = {"workload": c["config"]["workload"], "value": c["value"], "unit": c["unit"],
+                        "ms_per_step": c["ms_per_step"], "steps": sub.steps,
+                        "timed_region_kernel_us": c["timed_region_kernel_us"], "roofline": c["roofline"]}
+    if rank != 0:
+        return None
     line = {
-        "form": "large", "metric": "Gbp/s scanned per primer pair (both strands, k mm)",
-        "value": N / t_all / 1e9, "unit": "Gbp/s", "n_gpus": 1, "higher_is_better": True,
-        "data": "synthetic (counter-based Philox4x32-10, seed 7, generated on the device)",
-        "config": {"workload": f"large-{n_g}genomes-{N / 1e9:.1f}Gbp-3pairs-k4", "n_genomes": n_g, "n_bases": N,
-                   "n_contigs": len(coll.contig_genome), "chunks": len(tabs), "chunk_bases_max": cmax,
-                   "pairs": [(p["fwd"], p["rev"]) for p in pairs], "k": 4, "window": [100, 3000],
-                   "tm_min_C": 50.0, "scan_tuning": tune, "layout_s": t_layout,
-                   "timed": "one pass: generation + pack + scan + sort + Tm + pair + fetch, outputs on the device; "
-                            "chunk i+1 generated and packed beside chunk i's run"},
-        "seconds": t_all,
-        "stage_note": "stages of an untimed pass; generation and packing of chunk i+1 run beside chunk i's run",
-        "amplicons_per_s": totals["amplicons"] / t_all, "results": dict(totals),
-        "stages_ms": stages, "scan": {"hbm_gbs": 0.5 * N / scan_s / 1e9, "hbm_peak_gbs": hbm_peak,
-                                      "hbm_frac": 0.5 * N / scan_s / 1e9 / hbm_peak, "peak_kind": peak_kind,
-                                      "pattern_gbps": N * len(pairs) / scan_s / 1e9},
-        "gpu_launches": launches, "clocks": clk.summary(),
-        "oracle_check": {"genomes": len(checks), "all_equal": all_ok, "cores": cores,
-                         "bases": int(sum(c["bases"] for c in checks)),
-                         "sites": int(sum(c["sites"] for c in checks)),
-                         "amplicons": int(sum(c["amplicons"] for c in checks)),
-                         "tm_max_err": max([c["tm_max_err"] for c in checks] or [0.0]),
-                         "dumped": int(args.dump_genomes)},
+        "metric": METRIC, "value": value, "unit": "Gbp/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32",
+        "data": "synthetic (counter-based Philox4x32-10 bases, seed 7 + rank, generated on the device)",
+        "config": {"workload": LARGE_WORKLOAD, "n_genomes": n_g, "n_bases_per_gpu": N,
+                   "n_contigs": len(coll.contig_genome), "pairs": npair, "oligos": [960, 64, 256], "k": 4,
+                   "window": [100, 3000], "tm_min_C": 50.0, "tm_dtype": "f32", "chunks": len(tabs),
+                   "chunk_bases_max": cmax, "parallelism": f"replicas x{world}", "scan_tuning": tune,
+                   "value_counts": "bases x primer pairs per second (each base once per pair scanned)",
+                   "input": "ASCII bases resident in HBM (generated before the timed region)",
+                   "l2": "inputs larger than L2 (169 GB resident ASCII; up to 8 GB of planes per chunk)",
+                   "layout_s": t_layout, "generation_s": t_gen},
+        "results_per_pass": dict(totals), "amplicons_per_s": totals["amplicons"] * args.steps / (t_max / 1e3),
+        "stages": stages, "roofline": roof, "pack_roofline": pack_roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": int(total_launches), "clocks": clocks,
+        "timed_region_ms_per_step": {st: live[st]["ms_per_step"] for st in live},
+        "collection": coll_key,
     }
     print(json.dumps(line), flush=True)
-    ctx.close()
-
+    return line
 
 
 def bench_hmm(args):
@@ -1108,7 +1336,7 @@ def bench_hmm(args):
     from paper_2509_13300_gb300 import ah, build, synth
     build.build()
     torch.cuda.set_device(0)
-    n_g = args.n_genomes if args.n_genomes != 100 else 2000
+    n_g = args.n_genomes or 2000
     t0 = time.perf_counter()
     w = synth.operon_family(seed=21, n_genomes=n_g)
     t_gen = time.perf_counter() - t0

@@ -39,3 +39,70 @@ def test_form_pairs():
     assert len(paper) == 4 and all(p["k"] == 4 for p in paper)
     large = bench.large_pairs()
     assert [oracle.degeneracy(p["fwd"]) + oracle.degeneracy(p["rev"]) for p in large] == [960, 64, 256]
+
+
+def _small_large_like():
+    """A few short genomes with the large workload's three pairs (CPU-sized)."""
+    return countergen.collection(seed=5, n_genomes=3, len_lo=6e4, len_hi=1.2e5, pairs=bench.large_pairs())
+
+
+def test_oracle_sample_is_seeded_whole_genomes_and_bounded():
+    c = countergen.collection(seed=7, n_genomes=300, len_lo=1e5, len_hi=8e5)
+    a = bench.oracle_sample(c, 1.0, 4)
+    assert np.array_equal(a, bench.oracle_sample(c, 1.0, 4))       # seeded
+    assert np.all(np.diff(a) > 0) and a[0] >= 0 and a[-1] < 300     # sorted genome ids
+    gl = np.diff(c.genome_off.astype(np.int64))
+    want = max(1.0e6, 0.12e6 * 4 * 1.0)
+    assert gl[a].sum() >= want and gl[a].sum() - gl[a].max() < want  # just enough bases
+    assert len(bench.oracle_sample(c, 4.0, 4)) > len(a)
+
+
+def test_genome_records_of_a_chunk_equal_each_genome_alone():
+    """Slicing one run over several genomes into per-genome records (contigs
+    rebased, amplicon ends re-indexed, sequences cut out) gives exactly the
+    oracle's records of each genome run alone."""
+    c = _small_large_like()
+    pairs = bench.large_pairs()
+    b0, b1, off, gen = bench.sub_tables(c, 0, 3)
+    seq = c.bases(b0, b1)
+    s = oracle.scan(seq, off, gen, pairs)
+    tm, ps = oracle.tm(seq, off, s, pairs)
+    am = oracle.pair(s, pairs, ps)
+    qs, qo = oracle.fetch(seq, off, am)
+    res = (s, tm.astype(np.float32), ps, am, qs, qo)
+    want, _ = bench.oracle_on_genomes(c, pairs, np.arange(3), 1)
+    got = {g: bench.genome_records(c, (b0, b1, off, gen), res, g) for g in range(3)}
+    summ = bench.parity_summary(c, got, want)
+    assert summ["all_equal"] and summ["genomes"] == 3 and summ["sites"] == len(s)
+
+
+def test_parity_summary_flags_each_kind_of_difference():
+    c = _small_large_like()
+    pairs = bench.large_pairs()
+    want, _ = bench.oracle_on_genomes(c, pairs, np.array([1]), 1)
+    s_, tm, ps, am, qs, qo = want[1]
+    assert len(s_) > 0
+
+    def got(**kw):
+        d = dict(s=s_.copy(), tm=tm.astype(np.float32), ps=ps.copy(), am=am.copy(), qs=qs, qo=qo.copy())
+        d.update(kw)
+        return {1: (d["s"], d["tm"], d["ps"], d["am"], d["qs"], d["qo"])}
+
+    assert bench.parity_summary(c, got(), want)["all_equal"]
+    s2 = s_.copy()
+    s2["mm"][0] ^= 1
+    assert not bench.parity_summary(c, got(s=s2), want)["sites_equal"]
+    p2 = ps.copy()
+    p2[0] ^= 1
+    assert not bench.parity_summary(c, got(ps=p2), want)["pass_equal"]
+    t2 = tm.astype(np.float32)
+    i = int(np.nonzero(~np.isnan(t2))[0][0])
+    t2[i] += 0.02
+    r = bench.parity_summary(c, got(tm=t2), want)
+    assert not r["all_equal"] and 0.015 < r["max_dtm_C"] < 0.025
+    if len(am):
+        a2 = am.copy()
+        a2["end"][0] += 1
+        assert not bench.parity_summary(c, got(am=a2), want)["amplicons_equal"]
+        q2 = bytes([qs[0] ^ 1]) + qs[1:]
+        assert not bench.parity_summary(c, got(qs=q2), want)["sequences_equal"]

@@ -56,8 +56,10 @@ def test_timing_reductions_over_two_gloo_ranks(tmp_path):
 
 def test_ranks_scan_their_own_collections():
     import bench
-    a, b = bench.workload(1, 2), bench.workload(2, 2)  # ranks 0 and 1 of a 2-rank run (seed 1 + rank)
+    a, b = bench.workload(1, 2), bench.workload(2, 2)  # collection workload: seed 1 + rank
     assert a.n_bases != b.n_bases or not np.array_equal(a.seq[:1000], b.seq[:1000])
+    c, d = bench.large_collection(7, 3), bench.large_collection(8, 3)  # large workload: seed 7 + rank
+    assert c.n_bases != d.n_bases or not np.array_equal(c.bases(0, 1000), d.bases(0, 1000))
 
 
 def test_reference_arm_runs_on_rank_zero_alone():
