@@ -179,7 +179,9 @@ size_t ah_device_bytes(const ah_ctx *ctx);
  * buffers on the device (the copies overlap the packing) and the call waits
  * for the copies, not for the packing.  A device seq is read by work queued
  * on `stream` (stream-ordered, like any CUDA call): it must stay valid until
- * that work has run; the call returns without waiting for it.  Every later
+ * that work has run; the call returns without waiting for it.  A device seq
+ * at a 16-byte aligned address is staged by bulk copies; at any other address
+ * the packing reads it byte by byte, several times slower.  Every later
  * call that reads the set orders itself after the packing, whatever stream
  * it is given.  A device-side failure of the packing is reported by the next
  * call on the context that synchronises (ah_unload_genomes at the latest).

@@ -785,7 +785,7 @@ void fast_begin(ah_ctx *c, const GenomeSet &gs, const std::vector<ScanPattern> &
     ah_site *sites = sites_direct ? o->sites : (ah_site *)scratch(c, "run_sites", ns_max * sizeof(ah_site));
     float *tm = sites_direct && o->tm ? o->tm : (float *)scratch(c, "run_tm", ns_max * sizeof(float));
     uint8_t *pass = sites_direct && o->pass ? o->pass : (uint8_t *)scratch(c, "run_pass", ns_max);
-    uint32_t *queue = (uint32_t *)scratch(c, "tm_queue", ns_max * sizeof(uint32_t));
+    uint32_t *queue = (uint32_t *)scratch(c, "tm_queue", 2 * ns_max * sizeof(uint32_t));
     uint64_t *counts = (uint64_t *)scratch(c, "pair_counts", ns_max * sizeof(uint64_t));
     uint64_t *offs = (uint64_t *)scratch(c, "pair_offsets", ns_max * sizeof(uint64_t));
     ah_amplicon *amps = amps_direct ? o->amplicons : (ah_amplicon *)scratch(c, "run_amps", na_max * sizeof(ah_amplicon));
@@ -916,7 +916,7 @@ void run_steps(ah_ctx *c, const GenomeSet &gs, const PairDev *pd, uint32_t n_pai
         sort_decode(c, gs, n_pairs, keys, ns, sites, st);
         {
             Stage sg(c, "tm", st, 2);
-            uint32_t *q = (uint32_t *)scratch(c, "tm_queue", ns * sizeof(uint32_t));
+            uint32_t *q = (uint32_t *)scratch(c, "tm_queue", 2 * ns * sizeof(uint32_t));
             launch_tm(sites, ns, nullptr, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, pass, q,
                       (uint32_t *)(c->d_flags + kFlagTmQueue), tm_seg_max(c), tm_few_exact(c), c->d_err, st);
         }
@@ -1134,7 +1134,7 @@ void group_device(ah_ctx *c, const GenomeSet &gs, uint32_t pid, int k, const std
     sort_decode(c, gs, 1, keys, ns, sites, st);
     float *tm = (float *)scratch(c, "serve_tm", ns * sizeof(float));
     uint8_t *pass = (uint8_t *)scratch(c, "serve_pass", ns);
-    uint32_t *q = (uint32_t *)scratch(c, "tm_queue", ns * sizeof(uint32_t));
+    uint32_t *q = (uint32_t *)scratch(c, "tm_queue", 2 * ns * sizeof(uint32_t));
     {
         Stage sg(c, "tm", st, 2);
         launch_tm(sites, ns, nullptr, pd, 1, gs.planes, gs.contig_off, tm, pass, q,
@@ -2159,7 +2159,7 @@ ah_status ah_tm_sweep(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint
         float *tm = (float *)scratch(c, "sweep_tm", std::max<uint64_t>(n_sites, 1) * sizeof(float));
         if (n_sites) {
             Stage sg(c, "tm", st, 2);
-            uint32_t *q = (uint32_t *)scratch(c, "tm_queue", n_sites * sizeof(uint32_t));
+            uint32_t *q = (uint32_t *)scratch(c, "tm_queue", 2 * n_sites * sizeof(uint32_t));
             launch_tm(s, n_sites, nullptr, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, nullptr, q,
                       (uint32_t *)(c->d_flags + kFlagTmQueue), tm_seg_max(c), tm_few_exact(c), c->d_err, st);
         }
@@ -2357,7 +2357,7 @@ ah_status ah_tm(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uint32_t n
         uint8_t *ps = pass_out ? out_buf(c, "pass_out", pass_out, n) : nullptr;
         {
             Stage sg(c, "tm", st, 2);
-            uint32_t *q = (uint32_t *)scratch(c, "tm_queue", n * sizeof(uint32_t));
+            uint32_t *q = (uint32_t *)scratch(c, "tm_queue", 2 * n * sizeof(uint32_t));
             launch_tm(s, n, nullptr, pd, (int)n_pairs, gs.planes, gs.contig_off, tm, ps, q,
                       (uint32_t *)(c->d_flags + kFlagTmQueue), tm_seg_max(c),
                       tm_few_exact(c), c->d_err, st);

@@ -202,12 +202,13 @@ void launch_rank_sort_decode(const uint64_t *keys, uint64_t n, const uint64_t *n
 enum FlagWord : int {
     kFlagCounter = 0, // scan hits appended
     kFlagAux = 1,     // a total computed on the device
-    kFlagTmQueue = 2, // sites queued for the exhaustive fp64 Tm
-    kFlagSites = 3,   // one-synchronisation path: sites sorted
-    kFlagAmps = 4,    // ... amplicons
-    kFlagSeq = 5,     // ... sequence bytes
-    kFlagRedo = 6,    // ... kRedo* bits: a count above what the launches were sized for
-    kFlagWork = 7,    // scan: slices claimed so far, one word per launch group (zeroed before a scan)
+    kFlagTmQueue = 2, // two words: sites queued for the exhaustive fp64 Tm and finished
+                      // blocks (two u32), then sites deferred by the fast Tm kernel (u64)
+    kFlagSites = 4,   // one-synchronisation path: sites sorted
+    kFlagAmps = 5,    // ... amplicons
+    kFlagSeq = 6,     // ... sequence bytes
+    kFlagRedo = 7,    // ... kRedo* bits: a count above what the launches were sized for
+    kFlagWork = 8,    // scan: slices claimed so far, one word per launch group (zeroed before a scan)
     kFlagErr = kFlagWork + AH_MAX_PAIRS_PER_SCAN, // DeviceErr (low 32 bits)
     kFlagWords = kFlagErr + 1
 };
@@ -252,10 +253,14 @@ struct PairDev {
 
 // tm.cu
 // queue: n entries of scratch for the sites decided by exhaustive fp64
-// enumeration; queue_n: two device words (queue length, finished blocks;
-// zeroed here).  seg_max: the largest nkey - 1 over the pairs' primers.
-// few_exact (all pairs' few_exact): the Tm kernel's last block evaluates the
-// queue; else a second kernel does, a block per site.
+// enumeration; queue_n: four device u32 words (queue length, finished
+// blocks, then a u64 count of deferred sites; zeroed here).  queue holds 2 n
+// entries: the exhaustive queue, then the list of deferred sites.  seg_max:
+// the largest nkey - 1 over the pairs' primers.  few_exact (all pairs'
+// few_exact): a thread-per-site kernel computes every site and defers those
+// within 0.01 C of tm_min to the four-lane kernel, whose last block evaluates
+// the exhaustive queue; else the four-lane kernel takes every site and a
+// second kernel works off the queue, a block per site.
 // n_dev: optional device count (min(*n_dev, n) sites).
 void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const PairDev *pairs_d, int n_pairs, const uint32_t *planes,
                const uint64_t *contig_off, float *tm_out, uint8_t *pass_out, uint32_t *queue, uint32_t *queue_n,

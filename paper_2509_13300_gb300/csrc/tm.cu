@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
                                                            const uint64_t *__restrict__ contig_off,
                                                            float *__restrict__ tm_out, uint8_t *__restrict__ pass_out,
                                                            uint32_t *__restrict__ queue, uint32_t *__restrict__ queue_n,
-                                                           int seg_max, int last_block_exact, int *__restrict__ err)
+                                                           int seg_max, int last_block_exact, int *__restrict__ err,
+                                                           const uint32_t *__restrict__ idx_list)
 {
     static_assert(32 * kTmWarps == kExactThreads, "the last block evaluates queued sites with exact_site");
     __shared__ int8_t bts[kTmWarps][8][AH_MAX_PRIMER_LEN];
@@ -241,7 +242,9 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
     TmPairD *pdd = reinterpret_cast<TmPairD *>(tm_smem + (size_t)n_pairs * sizeof(TmPairS));
     float2 *seg_smem =
         reinterpret_cast<float2 *>(tm_smem + (size_t)n_pairs * sizeof(TmPairS) + (size_t)nd * sizeof(TmPairD));
-    for (int j = 0; j < n_pairs; ++j) {
+    // a block with no site of the list skips the tables (it still counts itself below)
+    const bool has_work = (uint64_t)blockIdx.x * kTmWarps * 8 < dev_count(n_arg, n_dev);
+    for (int j = 0; has_work && j < n_pairs; ++j) {
         const PairDev &P = pairs[j];
         for (int t = threadIdx.x; t < 256; t += blockDim.x)
             ps[j].st[t] = make_float2(P.stack_dH[t], P.stack_dS[t]);
@@ -270,8 +273,9 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
     const float INF = INFINITY;
     const uint64_t groups = (uint64_t)gridDim.x * kTmWarps * 8;
     for (uint64_t base = ((uint64_t)blockIdx.x * kTmWarps + warp) * 8; base < n; base += groups) {
-        const uint64_t i = base + g;
-        const bool live = i < n;
+        const bool live = base + g < n;
+        // with idx_list, the sites taken are sites[idx_list[0 .. n)]
+        const uint64_t i = live && idx_list ? (uint64_t)idx_list[base + g] : base + g;
         ah_site s{};
         if (live)
             s = sites[i];
@@ -577,6 +581,262 @@ __global__ void __launch_bounds__(32 * kTmWarps) tm_kernel(const ah_site *__rest
 }
 
 // ---------------------------------------------------------------------------
+// Thread-per-site Tm (the path taken when every pair has few_exact).  The same
+// maximum as tm_kernel -- Dinkelbach iteration on the key-position shortest
+// path, fp32 -- but one thread carries all four states of one site: each
+// state keeps its path cost and the path's dH and dS sums, so the argmin
+// oligo's terms come out of the forward pass without a backtrack.  Between
+// two keys that are not adjacent the segment's table is separable (the stack
+// out of key k0 depends only on the base at k0, the stack into key k1 only on
+// the base at k1, the fixed stretch between them on neither), so one argmin
+// over the four predecessors serves all four successors.  A warp gathers its
+// 32 sites' windows together: per site, four coalesced 32-word loads (one per
+// plane) and four ballots give the window's bases as 32-bit columns.  Sites
+// whose maximum lies within 0.01 deg C of tm_min are deferred to tm_kernel
+// (which decides them exactly); everything else is written here.
+// ---------------------------------------------------------------------------
+constexpr int kFastThreads = 128;
+
+// Per pair in shared memory: stacks as (1000 dH, dS) indexed [template bases
+// (t0, t1)][oligo bases (o0, o1)], so the 16 entries of one template pair are
+// contiguous; terminal pairs [oligo base][template base]; per primer its keys,
+// masks, length and C + salt entropy.
+struct TmFastPair {
+    float2 st[256];
+    float2 tm[16];
+    uint8_t mask[2][AH_MAX_PRIMER_LEN];
+    uint8_t key[2][AH_MAX_PRIMER_LEN];
+    int L[2], nkey[2];
+    float cst[2];
+    float tm_min_f, tm_shift_f;
+};
+static_assert(sizeof(TmFastPair) % 8 == 0, "TmFastPair keeps 8-byte alignment");
+
+__global__ void __launch_bounds__(kFastThreads) tm_fast_kernel(const ah_site *__restrict__ sites, uint64_t n_arg,
+                                                               const uint64_t *__restrict__ n_dev,
+                                                               const PairDev *__restrict__ pairs, int n_pairs,
+                                                               const uint32_t *__restrict__ planes,
+                                                               const uint64_t *__restrict__ contig_off,
+                                                               float *__restrict__ tm_out,
+                                                               uint8_t *__restrict__ pass_out,
+                                                               uint32_t *__restrict__ defer,
+                                                               unsigned long long *__restrict__ defer_n,
+                                                               int *__restrict__ err)
+{
+    extern __shared__ __align__(16) unsigned char fast_smem[];
+    TmFastPair *fp = reinterpret_cast<TmFastPair *>(fast_smem);
+    const uint64_t n = dev_count(n_arg, n_dev);
+    if ((uint64_t)blockIdx.x * blockDim.x >= n)
+        return; // the whole block: no site for it
+    for (int j = 0; j < n_pairs; ++j) {
+        const PairDev &P = pairs[j];
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+            const int o0 = t >> 6, o1 = (t >> 4) & 3, t0 = (t >> 2) & 3, t1 = t & 3; // PairDev index order
+            fp[j].st[((t0 * 4 + t1) * 4 + o0) * 4 + o1] = make_float2(1000.f * P.stack_dH[t], P.stack_dS[t]);
+        }
+        if (threadIdx.x < 16)
+            fp[j].tm[threadIdx.x] = make_float2(1000.f * P.term_dH[threadIdx.x], P.term_dS[threadIdx.x]);
+        if (threadIdx.x < 2 * AH_MAX_PRIMER_LEN) {
+            (&fp[j].mask[0][0])[threadIdx.x] = (&P.mask[0][0])[threadIdx.x];
+            (&fp[j].key[0][0])[threadIdx.x] = (&P.key[0][0])[threadIdx.x];
+        }
+        if (threadIdx.x < 2) {
+            const int x = threadIdx.x;
+            fp[j].L[x] = P.L[x];
+            fp[j].nkey[x] = P.nkey[x];
+            fp[j].cst[x] = (float)(P.sconst + (P.saltcorr == 5 ? 0.368 * (double)(P.L[x] - 1) * P.log_na : 0.0));
+        }
+        if (threadIdx.x == 0) {
+            fp[j].tm_min_f = P.tm_min_f;
+            fp[j].tm_shift_f = (float)P.tm_shift;
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const float INF = INFINITY;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    // whole warps take 32 consecutive sites, so the window gather below is uniform
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+        const uint64_t i = i0 + lane;
+        const bool live = i < n;
+        ah_site s{};
+        if (live)
+            s = sites[i];
+        const bool bad_rec = live && (s.pair >= n_pairs || s.primer > 1 || s.strand > 1);
+        if (bad_rec)
+            atomicExch(err, kDevBounds);
+        const bool act = live && !bad_rec;
+        const TmFastPair &sp = fp[act ? s.pair : 0];
+        const int pr = act ? s.primer : 0;
+        const int L = sp.L[pr];
+        // window of the site: tile word offset and bit row of its first position
+        uint64_t wofs = 0;
+        int brow = 0;
+        if (act) {
+            const uint64_t P = contig_off[s.contig] + s.pos;
+            const uint64_t t = P / kTileBases, r = P % kTileBases;
+            brow = (int)(r / kTileW);
+            wofs = t * 4 * kTileWX + (r % kTileW);
+        }
+        // columns of the window's bases (bit q = base at position P + q is A / C / G / T)
+        uint32_t cA = 0, cC = 0, cG = 0, cT = 0;
+        for (uint32_t todo = __ballot_sync(0xffffffffu, act); todo; todo &= todo - 1) {
+            const int k = __ffs(todo) - 1;
+            const uint64_t wk = __shfl_sync(0xffffffffu, wofs, k);
+            const int bk = __shfl_sync(0xffffffffu, brow, k);
+            const uint32_t *w = planes + wk + lane; // position P_k + lane (the tile's extension covers 32 more)
+            const uint32_t a = __ballot_sync(0xffffffffu, (__ldg(w) >> bk) & 1u);
+            const uint32_t c = __ballot_sync(0xffffffffu, (__ldg(w + kTileWX) >> bk) & 1u);
+            const uint32_t g = __ballot_sync(0xffffffffu, (__ldg(w + 2 * kTileWX) >> bk) & 1u);
+            const uint32_t tt = __ballot_sync(0xffffffffu, (__ldg(w + 3 * kTileWX) >> bk) & 1u);
+            if (lane == k) {
+                cA = a;
+                cC = c;
+                cG = g;
+                cT = tt;
+            }
+        }
+        if (!act) {
+            if (bad_rec) {
+                tm_out[i] = NAN;
+                if (pass_out)
+                    pass_out[i] = 0;
+            }
+            continue;
+        }
+        const uint32_t lm = L >= 32 ? 0xffffffffu : ((1u << L) - 1u);
+        const bool bad = (~(cA | cC | cG | cT) & lm) != 0u; // a letter other than A, C, G, T
+        // template base opposite primer position q, 2 bits as (hi << 1) | lo with
+        // A 0, C 1, G 2, T 3: '+' the complement of the window base at q, '-' the
+        // window base at L - 1 - q
+        uint32_t blo, bhi;
+        if (s.strand == 0) {
+            blo = ~(cC | cT) & lm;
+            bhi = ~(cG | cT) & lm;
+        } else {
+            blo = __brev(cC | cT) >> (32 - L);
+            bhi = __brev(cG | cT) >> (32 - L);
+        }
+        if (bad) {
+            tm_out[i] = NAN;
+            if (pass_out)
+                pass_out[i] = 0;
+            continue;
+        }
+        auto bt = [&](int q) { return (int)(((blo >> q) & 1u) | (((bhi >> q) & 1u) << 1)); };
+        const uint8_t *key = sp.key[pr];
+        const uint8_t *mask = sp.mask[pr];
+        const int nk = sp.nkey[pr];
+        const int b0 = bt(0), bL = bt(L - 1);
+        const float cst = sp.cst[pr];
+        float lam = 0.f;
+        for (int it = 0; it < 64; ++it) {
+            // forward pass at lam: per state y (oligo base at the current key) the
+            // cheapest path cost 1000 dH - lam dS and that path's 1000 dH and dS
+            float c[4], h[4], e[4];
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                const float2 t = sp.tm[y * 4 + b0];
+                const bool ok = (mask[0] >> y) & 1;
+                c[y] = ok ? fmaf(-lam, t.y, t.x) : INF;
+                h[y] = t.x;
+                e[y] = t.y;
+            }
+            for (int si = 0; si + 1 < nk; ++si) {
+                const int k0 = key[si], k1 = key[si + 1];
+                const int m1 = mask[k1];
+                float nc[4], nh[4], ne[4];
+                if (k1 == k0 + 1) {
+                    const float2 *E = &sp.st[(bt(k0) * 4 + bt(k1)) * 16]; // E[o0 * 4 + o1]
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) {
+                        float best = INF, bh = 0.f, be = 0.f;
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) {
+                            const float2 v2 = E[x * 4 + y];
+                            const float v = c[x] + fmaf(-lam, v2.y, v2.x);
+                            if (v < best) {
+                                best = v;
+                                bh = h[x] + v2.x;
+                                be = e[x] + v2.y;
+                            }
+                        }
+                        const bool ok = (m1 >> y) & 1;
+                        nc[y] = ok ? best : INF;
+                        nh[y] = bh;
+                        ne[y] = be;
+                    }
+                } else {
+                    // fixed bases next to the keys, the stretch between them, then one
+                    // argmin over the bases at k0 (the stack out of k0), shared by every y
+                    const int fa = __ffs(mask[k0 + 1]) - 1, fb = __ffs(mask[k1 - 1]) - 1;
+                    float sh = 0.f, se = 0.f;
+                    for (int q = k0 + 2; q < k1; ++q) {
+                        const float2 v2 = sp.st[(bt(q - 1) * 4 + bt(q)) * 16 + (__ffs(mask[q - 1]) - 1) * 4 +
+                                                (__ffs(mask[q]) - 1)];
+                        sh += v2.x;
+                        se += v2.y;
+                    }
+                    const float2 *EA = &sp.st[(bt(k0) * 4 + bt(k0 + 1)) * 16 + fa]; // EA[o0 * 4]
+                    float best = INF, bh = 0.f, be = 0.f;
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) {
+                        const float2 v2 = EA[x * 4];
+                        const float v = c[x] + fmaf(-lam, v2.y, v2.x);
+                        if (v < best) {
+                            best = v;
+                            bh = h[x] + v2.x;
+                            be = e[x] + v2.y;
+                        }
+                    }
+                    const float2 *EB = &sp.st[(bt(k1 - 1) * 4 + bt(k1)) * 16 + fb * 4]; // EB[o1]
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) {
+                        const float2 v2 = EB[y];
+                        const float qh = sh + v2.x, qe = se + v2.y;
+                        const bool ok = ((m1 >> y) & 1) && best < INF;
+                        nc[y] = ok ? best + fmaf(-lam, qe, qh) : INF;
+                        nh[y] = bh + qh;
+                        ne[y] = be + qe;
+                    }
+                }
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    c[y] = nc[y];
+                    h[y] = nh[y];
+                    e[y] = ne[y];
+                }
+            }
+            // the 3' terminal pair, then the argmin end state (ties: the lowest base)
+            float best = INF, H = 0.f, S = 0.f;
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+                const float2 t = sp.tm[y * 4 + bL];
+                const float v = c[y] < INF ? c[y] + fmaf(-lam, t.y, t.x) : INF;
+                if (v < best) {
+                    best = v;
+                    H = h[y] + t.x;
+                    S = e[y] + t.y;
+                }
+            }
+            const float r = H / (S + cst);
+            // stop when the ratio no longer improves by more than 1e-4 K (as tm_kernel)
+            if (it > 0 && !(r > lam + 1e-4f))
+                break;
+            lam = r;
+        }
+        const float tm32 = lam - 273.15f + sp.tm_shift_f;
+        if (pass_out && fabsf(tm32 - sp.tm_min_f) < 0.01f) {
+            defer[atomicAdd(defer_n, 1ull)] = (uint32_t)i; // decided exactly by tm_kernel
+            continue;
+        }
+        tm_out[i] = tm32;
+        if (pass_out)
+            pass_out[i] = tm32 >= sp.tm_min_f;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Tm-threshold sweep (Sec. 3.3, Annealing Temperature Optimization: amplicon
 // counts, genomes amplified and off-target patterns as the threshold moves).
 // Per site a bit per threshold (passes or not, decided as the fp64 definition
@@ -752,29 +1012,52 @@ void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const Pa
         return;
     if (seg_max < 1 || seg_max > AH_MAX_PRIMER_LEN - 1)
         throw Error(AH_ERR_ARG, "Tm: segment count outside 1..31");
-    static int cached_dev = -1, sms = 148;
+    static int cached_dev = -1, sms = 148, fast_bps = 1, tm_bps = 1;
     int dev = 0;
     AH_CUDA(cudaGetDevice(&dev));
+    const size_t smem = (size_t)n_pairs * sizeof(TmPairS) + (size_t)(n_pairs <= kTmStageD ? n_pairs : 0) * sizeof(TmPairD) +
+                        (size_t)kTmWarps * 8 * seg_max * 16 * sizeof(float2);
+    const size_t fast_smem = (size_t)n_pairs * sizeof(TmFastPair);
     if (dev != cached_dev) {
         AH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         const int most = AH_MAX_PAIRS_PER_SCAN * (int)sizeof(TmPairS) + kTmStageD * (int)sizeof(TmPairD) +
                          kTmWarps * 8 * (AH_MAX_PRIMER_LEN - 1) * 16 * (int)sizeof(float2);
         AH_CUDA(cudaFuncSetAttribute(tm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most));
+        const int most_fast = AH_MAX_PAIRS_PER_SCAN * (int)sizeof(TmFastPair);
+        AH_CUDA(cudaFuncSetAttribute(tm_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast));
+        AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fast_bps, tm_fast_kernel, kFastThreads, most_fast));
+        AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tm_bps, tm_kernel, 32 * kTmWarps, most));
+        fast_bps = std::max(1, fast_bps);
+        tm_bps = std::max(1, tm_bps);
         cached_dev = dev;
     }
-    AH_CUDA(cudaMemsetAsync(queue_n, 0, 2 * sizeof(uint32_t), s)); // queue length, finished blocks
+    // queue length, finished blocks, deferred sites
+    AH_CUDA(cudaMemsetAsync(queue_n, 0, 2 * sizeof(uint64_t), s));
+    if (few_exact) {
+        // every site in one thread; those near tm_min go to the four-lane kernel below
+        uint32_t *defer = queue + n;
+        unsigned long long *defer_n = reinterpret_cast<unsigned long long *>(queue_n) + 1;
+        const uint64_t fb = std::min<uint64_t>((n + kFastThreads - 1) / kFastThreads, (uint64_t)sms * fast_bps);
+        tm_fast_kernel<<<(unsigned)fb, kFastThreads, fast_smem, s>>>(sites, n, n_dev, pairs_d, n_pairs, planes,
+                                                                      contig_off, tm_out, pass_out, defer, defer_n,
+                                                                      err);
+        AH_CUDA(cudaGetLastError());
+        // deferred sites (few; their count stays on the device): a persistent grid
+        const uint64_t tb = std::min<uint64_t>((n + 8 * kTmWarps - 1) / (8 * kTmWarps), (uint64_t)sms * tm_bps);
+        tm_kernel<<<(unsigned)tb, 32 * kTmWarps, smem, s>>>(sites, n, reinterpret_cast<const uint64_t *>(defer_n),
+                                                            pairs_d, n_pairs, planes, contig_off, tm_out, pass_out,
+                                                            queue, queue_n, seg_max, 1, err, defer);
+        AH_CUDA(cudaGetLastError());
+        return;
+    }
     const uint64_t per_block = 8ull * kTmWarps; // sites per block per pass
     uint64_t blocks = (n + per_block - 1) / per_block;
     if (blocks > 65535)
         blocks = 65535;
-    const size_t smem = (size_t)n_pairs * sizeof(TmPairS) + (size_t)(n_pairs <= kTmStageD ? n_pairs : 0) * sizeof(TmPairD) +
-                        (size_t)kTmWarps * 8 * seg_max * 16 * sizeof(float2);
     tm_kernel<<<(unsigned)blocks, 32 * kTmWarps, smem, s>>>(sites, n, n_dev, pairs_d, n_pairs, planes, contig_off,
-                                                            tm_out, pass_out, queue, queue_n, seg_max,
-                                                            few_exact ? 1 : 0, err);
+                                                            tm_out, pass_out, queue, queue_n, seg_max, 0, err,
+                                                            nullptr);
     AH_CUDA(cudaGetLastError());
-    if (few_exact)
-        return;
     tm_exact_kernel<<<(unsigned)sms, kExactThreads, 0, s>>>(sites, pairs_d, planes, contig_off, queue, queue_n,
                                                               tm_out, pass_out);
     AH_CUDA(cudaGetLastError());
