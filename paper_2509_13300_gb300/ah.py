@@ -149,6 +149,7 @@ def lib():
             "ah_debug_compile_scan": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
             "ah_debug_hmm_profile": (I32, [P, P, U64, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P, P]),
             "ah_debug_scan_source": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
+            "ah_debug_scan_stall": (I32, [P, I32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -229,6 +230,11 @@ class Context:
 
     def device_bytes(self) -> int:
         return int(self._lib.ah_device_bytes(self.h))
+
+    def debug_scan_stall(self, on: bool):
+        """Test aid: make later scans take their timeout path (each warp's first
+        slice waits on a barrier that nothing completes; 20 us limit)."""
+        self._check(self._lib.ah_debug_scan_stall(self.h, 1 if on else 0))
 
     def ah_set_profiling(self, enable):
         """0/False off, 1/True stage events and host sections, 2 host sections only,

@@ -47,6 +47,9 @@ struct ah_ctx {
     cudaEvent_t ev_load_start = nullptr; // a host load's copies start after the caller's earlier work
     cudaEvent_t ev_last_copy = nullptr;  // recorded after a host load's last copy
     uint64_t *h_flags = nullptr;     // pinned host mirror of the flag block
+    // test of the timeout path (ah_debug_scan_stall): each warp's first slice
+    // is armed without a copy and the per-slice wait limit drops to 20 us
+    bool scan_stall_first = false;
     bool flags_dirty = false;        // work was queued that may set the error word, not read since
     std::vector<cudaEvent_t> set_events; // free "ready" events of genome sets
     // mapped pinned staging of the contig tables, read on the device by a copy
@@ -614,8 +617,10 @@ void launch_scan(ah_ctx *c, ScanKernel *k, const GenomeSet &gs, uint64_t n_tiles
     const uint64_t *coff = gs.contig_off;
     uint32_t nc = gs.n_contigs;
     const uint32_t *tcont = gs.tile_contig, *troom = gs.tile_room;
-    void *args[] = {&planes, &n_tiles,  &coff, &nc,        &keys,  &cap,  &c->d_counter,
-                    &pbits,  &c->d_err, &work, &tile_list, &tcont, &troom};
+    uint64_t wait_ns = c->scan_stall_first ? 20000ull : 2000000000ull;
+    int stall = c->scan_stall_first ? 1 : 0;
+    void *args[] = {&planes, &n_tiles,  &coff, &nc,        &keys,  &cap,   &c->d_counter,
+                    &pbits,  &c->d_err, &work, &tile_list, &tcont, &troom, &wait_ns, &stall};
     AH_CUDA(cudaLaunchKernel((const void *)k->fn, dim3((unsigned)grid), dim3(k->threads), args, k->smem, st));
 }
 
@@ -2699,6 +2704,20 @@ ah_status ah_hmm_score(ah_ctx *c, uint32_t set_id, uint32_t hmm_id, const ah_amp
         out_finish(score_out, out, n, st);
         AH_CUDA(cudaStreamSynchronize(st));
     });
+}
+
+// Test aid (not in the public header).  on != 0: in later scans the first
+// slice of every warp is armed on its barrier with no copy behind it (a wait
+// that nothing will end) and the per-slice wait limit is 20 us, so the scan
+// takes its timeout path -- error word, bounded wait for the warp's copies
+// still in flight, exit -- and the call returns AH_ERR_TIMEOUT.  Nothing
+// faults or hangs.  on == 0 restores normal scans.
+ah_status ah_debug_scan_stall(ah_ctx *c, int on)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    c->scan_stall_first = on != 0;
+    return AH_OK;
 }
 
 ah_status ah_hmm_free(ah_ctx *c, uint32_t hmm_id)

@@ -93,15 +93,31 @@ __device__ __forceinline__ u64 global_ns()
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
 }
-// bounded wait for a barrier phase: gives up after ~2 s instead of hanging
-__device__ __forceinline__ bool mbar_wait(u64 *bar, u32 parity)
+__device__ __forceinline__ bool mbar_test(u64 *bar, u32 parity)
 {
-    if (mbar_try(bar, parity))
+    u32 ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// bounded wait for a barrier phase: gives up after limit_ns instead of hanging.
+// Limits of a millisecond and more poll with try_wait (the thread may be
+// suspended between tests); shorter ones poll with the non-blocking test, so
+// that the limit itself decides.
+__device__ __forceinline__ bool mbar_wait(u64 *bar, u32 parity, u64 limit_ns)
+{
+    if (mbar_test(bar, parity))
         return true;
     const u64 t0 = global_ns();
-    while (!mbar_try(bar, parity))
-        if (global_ns() - t0 > 2000000000ull)
-            return false;
+    if (limit_ns >= 1000000ull) {
+        while (!mbar_try(bar, parity))
+            if (global_ns() - t0 > limit_ns)
+                return false;
+    } else {
+        while (!mbar_test(bar, parity))
+            if (global_ns() - t0 > limit_ns)
+                return false;
+    }
     return true;
 }
 )CUDA";
@@ -412,7 +428,8 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "ah_scan_kernel(const u32 *__restrict__ planes, u64 n_tiles, const u64 *__restrict__ contig_off,\n"
        << "               u32 n_contigs, u64 *__restrict__ keys, u64 cap, u64 *__restrict__ counter, int pbits,\n"
        << "               int *__restrict__ err, u64 *__restrict__ work, const u64 *__restrict__ tile_list,\n"
-       << "               const u32 *__restrict__ tile_contig, const u32 *__restrict__ tile_room)\n{\n"
+       << "               const u32 *__restrict__ tile_contig, const u32 *__restrict__ tile_room, u64 wait_ns,\n"
+       << "               int stall_first)\n{\n"
        << "  // Every warp claims slices of tiles (32*R words of each plane plus a 32-word\n"
        << "  // overhang) from the shared counter `work` (zeroed before the launch), so SMs\n"
        << "  // that run faster take more, and runs its own S-stage pipeline: lane 0 claims\n"
@@ -442,13 +459,16 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "    asm volatile(\"fence.mbarrier_init.release.cluster;\" ::: \"memory\");\n"
        << "  }\n"
        << "  __syncwarp();\n"
-       << "  auto issue = [&](u64 wi, int stg) {\n"
+       << "  // stall_first (a test of the timeout path): the first slice of each warp is\n"
+       << "  // armed on its barrier without a copy, so its wait can only run out\n"
+       << "  auto issue = [&](u64 wi, int stg, bool copy) {\n"
        << "    const u64 tl = tile_list ? tile_list[wi / SLICES] : wi / SLICES;\n"
        << "    const int sl = (int)(wi % SLICES);\n"
        << "    asm volatile(\"mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\" ::\"r\"(smem_addr(&wbar[stg])),\n"
        << "                 \"r\"((u32)(4 * SLW * 4)) : \"memory\");\n"
-       << "    for (int x = 0; x < 4; ++x)\n"
-       << "      tma_copy(wbuf + (stg * 4 + x) * SLW, planes + (tl * 4 + x) * WX + sl * 32 * R, SLW * 4, &wbar[stg]);\n"
+       << "    if (copy)\n"
+       << "      for (int x = 0; x < 4; ++x)\n"
+       << "        tma_copy(wbuf + (stg * 4 + x) * SLW, planes + (tl * 4 + x) * WX + sl * 32 * R, SLW * 4, &wbar[stg]);\n"
        << "  };\n"
        << "  // append the n keys stash[warp * 32 + 0 .. n) with one atomic\n"
        << "  auto flush = [&](u32 n) {\n"
@@ -461,7 +481,7 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "    for (int q = 0; q < S; ++q) {\n"
        << "      const u64 w = atomicAdd(work, 1ull);\n"
        << "      witem[q] = w;\n"
-       << "      if (w < n_items) issue(w, q);\n"
+       << "      if (w < n_items) issue(w, q, !(stall_first && q == 0));\n"
        << "    }\n"
        << "  __syncwarp();\n"
        << "  for (int k = 0;; ++k) {\n"
@@ -469,13 +489,15 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "    const u64 wi = witem[stg];\n"
        << "    if (wi >= n_items)\n"
        << "      break;\n"
-       << "    const bool ok = mbar_wait(&wbar[stg], (u32)((k / S) & 1));\n"
+       << "    const bool ok = mbar_wait(&wbar[stg], (u32)((k / S) & 1), wait_ns);\n"
        << "    if (!__all_sync(0xffffffffu, ok)) {\n"
-       << "      // a copy never landed: report, wait (bounded) for the copies still in flight, leave\n"
+       << "      // a copy did not land in time: report, wait (bounded, ~2 s) for every copy\n"
+       << "      // of this warp still in flight, this stage's included, then leave\n"
        << "      if (lane == 0) {\n"
        << "        atomicExch(err, 1);\n"
-       << "        for (int d = 1; d < S; ++d)\n"
-       << "          if (witem[(k + d) % S] < n_items) mbar_wait(&wbar[(k + d) % S], (u32)(((k + d) / S) & 1));\n"
+       << "        for (int d = 0; d < S; ++d)\n"
+       << "          if (witem[(k + d) % S] < n_items && !(stall_first && k + d == 0)) // no copy was issued there\n"
+       << "            mbar_wait(&wbar[(k + d) % S], (u32)(((k + d) / S) & 1), 2000000000ull);\n"
        << "      }\n"
        << "      break;\n"
        << "    }\n"
@@ -527,7 +549,7 @@ std::string scan_source(const std::vector<ScanPattern> &pats, const ScanTuning &
        << "    if (lane == 0) { // refill this stage with the next claim\n"
        << "      const u64 w = atomicAdd(work, 1ull);\n"
        << "      witem[stg] = w;\n"
-       << "      if (w < n_items) issue(w, stg);\n"
+       << "      if (w < n_items) issue(w, stg, true);\n"
        << "    }\n"
        << "    __syncwarp();\n"
        << "  }\n"

@@ -110,6 +110,77 @@ def test_several_pairs_in_one_pass(ctx):
     assert_parity(gpu_run(ctx, w), oracle_run(w))
 
 
+def test_many_sites_take_the_thread_per_site_tm_path(ctx):
+    """Over 32,768 sites, so ah_tm runs the one-thread-per-site kernel; its
+    maximum is within 0.01 C of the oracle's, and with the threshold put
+    exactly on an oracle site value (such sites are deferred to the exact
+    decision) every pass flag is still the fp64 one."""
+    w = synth.random_small(41, n_bases=300_000, n_contigs=4, L_f=11, L_r=10, k=4, codes_f="RYN", codes_r="SWK",
+                           min_len=30, max_len=300)
+    o = oracle_run(w)
+    assert len(o["sites"]) >= 40_000
+    ok = ~np.isnan(o["tm"])
+    med = float(np.median(o["tm"][ok]))
+    at_site = float(o["tm"][ok][np.argmin(np.abs(o["tm"][ok] - med))])
+    for thr in (med + 0.003, at_site):
+        w.pairs = [dict(w.pairs[0], tm_min=thr)]
+        o = oracle_run(w)
+        assert 0 < o["pass_"].sum() < len(o["pass_"])
+        assert_parity(gpu_run(ctx, w), o)
+
+
+def test_scan_wait_limit_reports_timeout_and_the_context_stays_usable(ctx):
+    """Failure detection without a fault: each warp's first slice waits on a
+    barrier that no copy will complete (20 us limit); the scan gives up, waits
+    for its warps' real copies still in flight and ah_scan returns
+    AH_ERR_TIMEOUT; the next scan on the same context is exact."""
+    w = synth.random_small(51, n_bases=3_000_000, n_contigs=3, L_f=16, L_r=15, k=2, min_len=30, max_len=900)
+    p = w.pairs[0]
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    try:
+        pid = ctx.ah_set_primers(p["fwd"], p["rev"], p)
+        ctx.debug_scan_stall(True)
+        try:
+            with pytest.raises(ah.AHError) as e:
+                ctx.scan(sid, [pid])
+            assert e.value.status == ah.AH_ERR_TIMEOUT
+        finally:
+            ctx.debug_scan_stall(False)
+        sites = ctx.scan(sid, [pid])
+    finally:
+        ctx.ah_unload_genomes(sid)
+    assert sites.tobytes() == oracle.scan(w.seq, w.contig_off, w.contig_genome, w.pairs).tobytes()
+
+
+def test_full_collection_workload_against_the_oracle(ctx):
+    """The whole 100-genome collection workload (0.41 Gbp, 1,777 contigs, the
+    960-oligo pair, k = 3, Tm threshold 50 C) through ah_run, against the oracle
+    on every genome: sites, pass flags, Tm-filtered amplicons and sequences."""
+    import os
+    import bench
+    w = bench.workload(1, 100)
+    p = w.pairs[0]
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    try:
+        pid = ctx.ah_set_primers(p["fwd"], p["rev"], p)
+        g = ctx.run(sid, [pid], tm_filter=True)
+    finally:
+        ctx.ah_unload_genomes(sid)
+    cores = os.cpu_count() or 1
+    s = oracle.scan(w.seq, w.contig_off, w.contig_genome, w.pairs, n_threads=cores)
+    tm, ps = oracle.tm(w.seq, w.contig_off, s, w.pairs, n_threads=cores)
+    a = oracle.pair(s, w.pairs, ps)
+    q, qo = oracle.fetch(w.seq, w.contig_off, a)
+    assert len(s) > 5000 and len(a) > 100
+    assert g["sites"].tobytes() == s.tobytes()
+    ok = ~np.isnan(tm)
+    assert np.array_equal(np.isnan(g["tm"]), ~ok)
+    assert np.abs(g["tm"][ok].astype(np.float64) - tm[ok]).max() <= TM_TOL
+    assert np.array_equal(g["pass_"], ps)
+    assert g["amps"].tobytes() == a.tobytes()
+    assert g["seqs"] == q and np.array_equal(g["offs"].astype(np.uint64), qo.astype(np.uint64))
+
+
 def test_collection_spanning_many_tiles(ctx):
     """Genome-collection generator at reduced size: ~5 Mbp, 6 genomes, many
     contigs, N runs, planted operons with 0-4 substitutions, the 960-oligo pair."""
