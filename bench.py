@@ -38,8 +38,19 @@ METRIC = "Gbp/s scanned per primer pair (both strands, k mm)"
 WORKLOAD = "collection-100genomes-0.4Gbp-pair960-k3"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
-# logic-pipe issue roof of a GB300: 152 SMs x 64 lane-ops/clk (LOP3 is half rate) x clock
-SMS, LOP_LANES_PER_CLK = 152, 64
+# logic-pipe issue roof of a GB300: 152 SMs x LOP3 lane-ops/clk x clock; the lane rate
+# is measured at the start of every run (ah_debug_pipe_rates: 61 measured on GB300,
+# half of the 128-lane integer-add rate); this value is only the fallback
+SMS, LOP_LANES_PER_CLK = 152, 61.0
+
+
+def logic_lanes(ah):
+    """(LOP3 lanes/clk/SM, its source): measured on this GPU, else the fallback."""
+    try:
+        lop, iadd = ah.debug_pipe_rates()
+        return lop, f"measured on this GPU (ah_debug_pipe_rates: LOP3 {lop:.1f}, IADD {iadd:.1f} lanes/clk/SM)"
+    except Exception as e:  # noqa: BLE001 -- the probe is an aid; the roofline still gets a denominator
+        return LOP_LANES_PER_CLK, f"fallback {LOP_LANES_PER_CLK} (probe failed: {e})"
 
 
 def workload(seed: int, n_genomes: int = 100):
@@ -402,14 +413,15 @@ def bench_collection(args, emit: bool = True):
     words = n_bases / 32.0
     scan_tops = lop_per_word * words / (scan_us * 1e-6) / 1e12
     clk_mhz = clocks["sm_mhz"] or 2070.0
-    alu_peak = SMS * LOP_LANES_PER_CLK * clk_mhz * 1e6 / 1e12
+    lanes, lanes_src = logic_lanes(ah)
+    alu_peak = SMS * lanes * clk_mhz * 1e6 / 1e12
     if dominant == "scan":
         tr = traffic_record("ah_scan_kernel")
         roof = {"bound": "alu", "achieved": scan_tops, "peak": alu_peak, "unit": "Tops/s",
                 "frac": scan_tops / alu_peak, "traffic": tr["dram_bytes_per_launch"] if tr else None,
                 "kernel": "ah_scan_kernel",
-                "peak_note": f"logic pipe: {SMS} SMs x {LOP_LANES_PER_CLK} LOP3 lanes/clk x {clk_mhz:.0f} MHz "
-                             f"(median SM clock under load)",
+                "peak_note": f"logic pipe: {SMS} SMs x {lanes:.1f} LOP3 lanes/clk x {clk_mhz:.0f} MHz "
+                             f"(median SM clock under load); lanes {lanes_src}",
                 "algorithmic": f"{lop_per_word} LOP3 per 32 starts per pass over the planes",
                 "hbm_achieved_gbs": scan_hbm, "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": scan_hbm / hbm_peak, "hbm_peak_kind": peak_kind,
@@ -1219,7 +1231,8 @@ def bench_large_main(args):
     pack_s = live["pack"]["ms_per_step"] / 1e3
     words = N / 32.0
     lop = sum(ah.scan_lop3_per_word(p["fwd"], p["rev"], int(p["k"]), (tune or {}).get("R", 4), 0) for p in pairs)
-    alu_peak = SMS * LOP_LANES_PER_CLK * clk_mhz * 1e6 / 1e12
+    lanes, lanes_src = logic_lanes(ah)
+    alu_peak = SMS * lanes * clk_mhz * 1e6 / 1e12
     scan_tops = lop * words / scan_s / 1e12
     # each launch group reads its chunk's planes once
     scan_hbm = 0.5 * N * (live["scan"]["launches_per_step"] / len(tabs)) / scan_s / 1e9
@@ -1235,8 +1248,8 @@ def bench_large_main(args):
     roof = {"bound": "alu", "achieved": scan_tops, "peak": alu_peak, "unit": "Tops/s",
             "frac": scan_tops / alu_peak, "traffic": tr["dram_bytes_per_launch"] if tr else None,
             "kernel": "ah_scan_kernel",
-            "peak_note": f"logic pipe: {SMS} SMs x {LOP_LANES_PER_CLK} LOP3 lanes/clk (measured) x {clk_mhz:.0f} "
-                         f"MHz (median SM clock under load)",
+            "peak_note": f"logic pipe: {SMS} SMs x {lanes:.1f} LOP3 lanes/clk x {clk_mhz:.0f} MHz (median SM clock "
+                         f"under load); lanes {lanes_src}",
             "algorithmic": f"{lop} LOP3 per 32 starts for the three pairs ({len(tabs)} chunks x "
                            f"{live['scan']['launches_per_step'] / len(tabs):.0f} launches per chunk)",
             "hbm_achieved_gbs": scan_hbm, "hbm_peak_gbs": hbm_peak, "hbm_frac": scan_hbm / hbm_peak,

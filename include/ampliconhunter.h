@@ -455,22 +455,25 @@ ah_status ah_get_profile(const ah_ctx *ctx, const char *stage, double *ms, uint6
 
 /* Amplicon calling that allocates nothing (the paper has no counterpart: this
  * is a deployment variant of ah_pair).  For callers that must not allocate
- * device memory during the call -- for example while a stream is being
- * captured into a CUDA graph, inside an application whose allocator owns all
- * of device memory, or in a latency-bound loop that must stay off the
- * driver's allocator.  It runs the same pairing as ah_pair on the current
- * CUDA device and takes no context: its scratch lives in one fixed device
- * array of about 4.4 MB compiled into the library, which every GPU that loads
- * the library holds until the process exits.
+ * device memory during the call -- an application whose own allocator owns
+ * all of device memory, or a latency-bound loop that must stay off the
+ * driver's allocator (cudaMalloc/cudaFree are slow and cudaFree synchronises
+ * the device).  It runs the same pairing as ah_pair on the current CUDA
+ * device and takes no context: its scratch lives in one fixed device array of
+ * about 4.4 MB compiled into the library, which every GPU that loads the
+ * library holds until the process exits.  The call waits on `stream` (it
+ * reads the error word and the amplicon count back to the host).
  * pair_windows (host): n_pairs x 4 int32 {L_fwd, L_rev, min_len, max_len},
- *   indexed by ah_site.pair; 1 <= n_pairs <= 16, 1 <= L <= 32.
+ *   indexed by ah_site.pair; 1 <= n_pairs <= 16, 1 <= L <= 32; checked on
+ *   every call, also when n = 0.
  * sites, pass (may be null), out: device memory of the current device; sites
  *   in canonical order as ah_scan returns them.  n <= 262144 (1 << 18);
- *   larger n returns AH_ERR_ARG, as do host pointers and records whose
- *   pair, primer or strand is out of range.
+ *   larger n returns AH_ERR_ARG, as do host pointers, records whose pair,
+ *   primer or strand is out of range, and lists out of canonical order.
  * Overflow contract as for every call (cap = 0 is a size query); *n_out host.
- * The first call on each device looks up the array's device address; make
- * it before any stream capture.  All calls share the one array: calls that
+ * The first call on each device looks up the array's device address and
+ * keeps it for the life of the process (the device's primary context must
+ * not be reset in between).  All calls share the one array: calls that
  * overlap on the GPU (two streams or two threads) race and must not be made.
  * Errors: AH_ERR_ARG, AH_ERR_OVERFLOW, AH_ERR_CUDA (no message string). */
 ah_status ah_pair_noalloc(const int32_t *pair_windows, uint32_t n_pairs, const ah_site *sites, const uint8_t *pass,

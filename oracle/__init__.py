@@ -193,6 +193,30 @@ def fetch(seq, contig_off, amplicons: np.ndarray):
     return out[:total].tobytes(), offsets
 
 
+def amplitypes(seq, contig_off, amplicons: np.ndarray):
+    """Amplicon sequence variants and amplitypes (Sec. 3.3, Amplicon Pattern
+    Visualization): a variant is an exact amplicon sequence as fetch() gives it
+    (RF reverse-complemented, non-ACGT as N), numbered 0, 1, ... by first
+    occurrence in `amplicons`; a genome's amplitype is its multiset of
+    (variant, copy number), numbered by first occurrence over the genomes with
+    amplicons in ascending id.  Returns (variant id per amplicon, rows
+    (genome, amplitype, amplicons, variants) in ascending genome, number of
+    variants, number of amplitypes)."""
+    seqs, offs = fetch(seq, contig_off, amplicons)
+    var = {}
+    vid = [var.setdefault(seqs[int(offs[i]):int(offs[i + 1])], len(var)) for i in range(len(amplicons))]
+    per = {}
+    for g, v in zip(amplicons["genome"].tolist(), vid):
+        per.setdefault(g, {}).setdefault(v, 0)
+        per[g][v] += 1
+    types = {}
+    rows = []
+    for g in sorted(per):
+        pattern = frozenset(per[g].items())
+        rows.append((g, types.setdefault(pattern, len(types)), sum(per[g].values()), len(per[g])))
+    return np.array(vid, dtype=np.uint32), rows, len(var), len(types)
+
+
 def reverse_contigs(seq: np.ndarray, contig_off: np.ndarray) -> np.ndarray:
     """The decoy collection (Sec. 2.1, Amplicon analysis): every contig reversed,
     not complemented, in place of the original; contig offsets unchanged."""

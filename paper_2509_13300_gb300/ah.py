@@ -150,6 +150,7 @@ def lib():
             "ah_debug_hmm_profile": (I32, [P, P, U64, U64, ctypes.POINTER(U64), ctypes.POINTER(U64), P, P]),
             "ah_debug_scan_source": (I32, [ctypes.c_char_p, ctypes.c_char_p, I32, I32, I32, I32, ctypes.c_char_p, S]),
             "ah_debug_scan_stall": (I32, [P, I32]),
+            "ah_debug_pipe_rates": (I32, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -571,6 +572,16 @@ def debug_hmm_profile(seqs):
                                     _ptr(t), _ptr(e))
     assert rc == 0
     return m.value, ref.value, t, e
+
+
+def debug_pipe_rates():
+    """Measured issue rates of the current GPU: (LOP3, 32-bit integer add)
+    lane-operations per clock per SM, from the SMs' own cycle counters."""
+    out = (ctypes.c_double * 2)()
+    rc = lib().ah_debug_pipe_rates(out)
+    if rc != 0:
+        raise AHError(AH_ERR_CUDA, f"pipe-rate probe failed ({rc})")
+    return float(out[0]), float(out[1])
 
 
 def debug_compile_scan(fwd: str, rev: str, k: int, R: int = 4, arith_pct: int = 0, order: int = 0):

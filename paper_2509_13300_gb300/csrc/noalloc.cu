@@ -1,21 +1,24 @@
 // ah_pair_noalloc: amplicon calling that allocates no memory at all.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA stream is
-// being captured into a graph, allocators that own all of device memory and
-// forbid side allocations, or real-time loops that must not hit the driver's
-// allocator.  This entry point runs the same pairing kernels as ah_pair but
-// keeps every piece of scratch (per-site counts and offsets, the prefix-sum
-// temporary, the per-pair lengths and windows, the error word and the
-// result count) in one file-scope device array of fixed size, so it neither
-// allocates nor frees anything, on the device or through any library.
+// Some callers cannot call cudaMalloc during a call: an application whose
+// own allocator owns all of device memory and forbids side allocations, or a
+// latency-bound loop that must stay off the driver's allocator (cudaMalloc
+// and cudaFree can take milliseconds and cudaFree synchronises the device).
+// This entry point runs the same pairing kernels as ah_pair but keeps every
+// piece of scratch (per-site counts and offsets, the prefix-sum temporary,
+// the per-pair lengths and windows, the error word and the result count) in
+// one file-scope device array of fixed size, so it neither allocates nor
+// frees anything, on the device or through any library.  It does wait on its
+// stream (it reads the error word and the amplicon count back to the host).
 //
 // The array is kScratchBytes (about 4.4 MB); every GPU that loads this
 // library holds it until the process exits.  Host code cannot use the
 // array's name as a device address, so the first call on each device looks
 // its address up with cudaGetSymbolAddress (with that device current) and
-// caches it; that first call should therefore come before any stream
-// capture.  All calls share the array: calls that overlap on the GPU (on two
-// streams, or from two threads) race and must not be issued.
+// caches it for the life of the process: the cache assumes the device's
+// primary context is never reset (no cudaDeviceReset in between).  All calls
+// share the array: calls that overlap on the GPU (on two streams, or from two
+// threads) race and must not be issued.
 #include <cub/device/device_scan.cuh>
 
 #include <algorithm>
@@ -39,12 +42,25 @@ std::mutex g_mu;
 unsigned char *g_addr[kMaxDevices] = {};
 
 // Reject records whose pair, primer or strand would index outside the
-// per-pair table (the only memory the pairing kernels index with them).
+// per-pair table (the only memory the pairing kernels index with them), and
+// lists out of canonical order (pair, contig, pos, primer, strand), which the
+// pairing's searches assume.
 __global__ void check_records(const ah_site *__restrict__ s, uint64_t n, int n_pairs, int *__restrict__ err)
 {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        if (s[i].pair >= n_pairs || s[i].primer > 1 || s[i].strand > 1)
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const ah_site b = s[i];
+        bool bad = b.pair >= n_pairs || b.primer > 1 || b.strand > 1;
+        if (i > 0) {
+            const ah_site a = s[i - 1];
+            const unsigned long long ka = ((unsigned long long)a.pair << 32) | a.contig,
+                                     kb = ((unsigned long long)b.pair << 32) | b.contig;
+            const unsigned long long ta = ((unsigned long long)a.pos << 2) | ((a.primer & 1u) << 1) | (a.strand & 1u),
+                                     tb = ((unsigned long long)b.pos << 2) | ((b.primer & 1u) << 1) | (b.strand & 1u);
+            bad |= ka > kb || (ka == kb && ta > tb);
+        }
+        if (bad)
             atomicExch(err, 1);
+    }
 }
 
 struct Windows {
@@ -100,15 +116,15 @@ extern "C" ah_status ah_pair_noalloc(const int32_t *pair_windows, uint32_t n_pai
         }
         base = g_addr[dev];
     }
-    if (n == 0)
-        return AH_OK;
-    if (!sites || !on_device(sites, dev) || (pass && !on_device(pass, dev)) || (cap && (!out || !on_device(out, dev))))
-        return AH_ERR_ARG;
-    for (uint32_t j = 0; j < n_pairs; ++j) {
+    for (uint32_t j = 0; j < n_pairs; ++j) { // the windows are checked whatever n is
         const int32_t *w = pair_windows + 4 * j;
         if (w[0] < 1 || w[0] > AH_MAX_PRIMER_LEN || w[1] < 1 || w[1] > AH_MAX_PRIMER_LEN || w[2] < 0 || w[2] > w[3])
             return AH_ERR_ARG;
     }
+    if (n == 0)
+        return AH_OK;
+    if (!sites || !on_device(sites, dev) || (pass && !on_device(pass, dev)) || (cap && (!out || !on_device(out, dev))))
+        return AH_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     uint64_t *counts = (uint64_t *)base;
     uint64_t *offs = (uint64_t *)(base + kCountsBytes);

@@ -515,3 +515,40 @@ def test_decoy_reversal_is_per_contig_reversal():
     mir = sorted((int(s["contig"]), int(lens[s["contig"]] - 6 - s["pos"]), int(s["primer"]), int(s["strand"])) for s in fw)
     got = sorted((int(s["contig"]), int(s["pos"]), int(s["primer"]), int(s["strand"])) for s in rv)
     assert mir == got
+
+
+# ----------------------------------------------------------------------------- amplitypes
+
+def test_amplitypes_of_a_hand_built_collection():
+    """Four genomes whose amplicons are cut from known sequences: X (twice in
+    genome 0, once as the reverse complement read RF), Y and Z.  Variants are
+    numbered by first occurrence (X 0, Y 1, Z 2); genomes 0 and 1 carry the
+    same multiset {X: 2, Y: 1} in different orders and share amplitype 0;
+    genome 2 carries {X: 1, Y: 1} (another copy number: amplitype 1); genome 3
+    carries {Z: 1} (amplitype 2); genome 4 has no amplicon (no row)."""
+    X, Y, Z = "ACGTTGCAAGGCTT", "ACGTTGCAAGGCTA", "ACGTNGCAAGGCTT"   # Y, Z differ from X in one letter
+    rc = lambda q: "".join({"A": "T", "C": "G", "G": "C", "T": "A", "N": "N"}[c] for c in reversed(q))
+    spacer = "GGGGG"
+    genomes = [[X, Y, rc(X)], [Y, X, X], [X, Y], [Z], ["CCCC"]]
+    orients = [[0, 0, 1], [0, 0, 0], [0, 0], [0], [0]]      # the third amplicon of genome 0 is RF
+    seq, off, gen, amps = "", [0], [], []
+    for g, parts in enumerate(genomes):
+        start = len(seq)
+        body = spacer.join(parts) + spacer
+        seq += body
+        off.append(len(seq))
+        gen.append(g)
+        if g == 4:
+            continue
+        pos = 0
+        for q, o in zip(parts, orients[g]):
+            amps.append((g, g, pos, pos + len(q), o))
+            pos += len(q) + len(spacer)
+    a = np.zeros(len(amps), dtype=oracle.AMPLICON_DTYPE)
+    for i, (g, c, s0, e0, o) in enumerate(amps):
+        a[i]["genome"], a[i]["contig"], a[i]["start"], a[i]["end"], a[i]["orient"] = g, c, s0, e0, o
+    seq_u8 = np.frombuffer(seq.encode(), dtype=np.uint8).copy()
+    vid, rows, nv, nt = oracle.amplitypes(seq_u8, np.array(off, dtype=np.uint64), a)
+    assert vid.tolist() == [0, 1, 0, 1, 0, 0, 0, 1, 2]
+    assert rows == [(0, 0, 3, 2), (1, 0, 3, 2), (2, 1, 2, 2), (3, 2, 1, 1)]
+    assert (nv, nt) == (3, 3)
