@@ -89,6 +89,7 @@ struct ah_ctx {
     };
     struct RunPending {
         bool active = false, done = false; // done: completed already by ah_run_begin
+        bool scan_only = false;            // only the scan was queued: ah_run_end finishes step by step
         ah_status status = AH_OK;
         std::string msg;
         uint32_t set_id = 0;
@@ -2076,21 +2077,41 @@ ah_status ah_run_begin(ah_ctx *c, uint32_t set_id, const uint32_t *pair_ids, uin
             P.active = true;
             return;
         }
-        // counts above the one-synchronisation sizes (seen in the last run): step by step, now
-        uint64_t *keys = nullptr;
-        const uint64_t ns = scan_keys(c, gs, pats, &keys, st);
+        // counts above the one-synchronisation sizes (seen in the last run): queue the
+        // scan and its count's copy only; ah_run_end reads the count and finishes step
+        // by step, so the caller's next packing (after scan_done) runs beside that
+        if (!gs.n_tiles) {
+            uint64_t *keys = nullptr;
+            const uint64_t ns = scan_keys(c, gs, pats, &keys, st);
+            try {
+                run_steps(c, gs, pd, n_pairs, keys, ns, o, st);
+            } catch (const Error &e) {
+                if (e.status != AH_ERR_OVERFLOW)
+                    throw;
+                P.status = e.status; // reported by ah_run_end, like the counts
+                P.msg = e.msg;
+            }
+            if (scan_done)
+                AH_CUDA(cudaEventRecord((cudaEvent_t)scan_done, st));
+            leave_run_stream(c, caller);
+            P.active = P.done = true;
+            return;
+        }
+        const int pbits = std::max(1, bit_length(gs.n_bases));
+        uint64_t *keys = (uint64_t *)scratch(c, "scan_keys", c->key_cap * sizeof(uint64_t));
+        reset_flags(c, st);
+        {
+            Stage sg(c, "scan", st, (int)scan_launch_groups(pats).size());
+            launch_scans(c, gs, pats, gs.n_tiles, keys, c->key_cap, pbits, st);
+        }
         if (scan_done)
             AH_CUDA(cudaEventRecord((cudaEvent_t)scan_done, st));
-        try {
-            run_steps(c, gs, pd, n_pairs, keys, ns, o, st);
-        } catch (const Error &e) {
-            if (e.status != AH_ERR_OVERFLOW)
-                throw;
-            P.status = e.status; // reported by ah_run_end, like the counts
-            P.msg = e.msg;
-        }
+        AH_CUDA(cudaMemcpyAsync(c->h_flags, c->d_flags, kFlagWords * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        AH_CUDA(cudaEventRecord(c->ev_run, st));
+        P.fr.keys = keys;
+        P.scan_only = true;
         leave_run_stream(c, caller);
-        P.active = P.done = true;
+        P.active = true;
     });
 }
 
@@ -2112,6 +2133,28 @@ ah_status ah_run_end(ah_ctx *c)
         const uint32_t n_pairs = (uint32_t)P.pair_ids.size();
         uint64_t *keys = nullptr;
         uint64_t ns = 0;
+        if (P.scan_only) { // the scan ran alone: its count, then step by step
+            {
+                HostSpan span(c, "host.run.wait");
+                AH_CUDA(cudaEventSynchronize(c->ev_run));
+            }
+            c->flags_dirty = false;
+            const int e = (int)(c->h_flags[kFlagErr] & 0xffffffffu);
+            if (e != 0) {
+                AH_CUDA(cudaMemsetAsync(c->d_flags + kFlagErr, 0, sizeof(uint64_t), P.st));
+                raise_device_error(e);
+            }
+            ns = c->h_flags[kFlagCounter];
+            keys = P.fr.keys;
+            if (ns > c->key_cap) { // the key buffer was too small: grow it and scan again
+                c->key_cap = ns;
+                std::vector<ScanPattern> pats = patterns_of(c, P.pair_ids.data(), n_pairs);
+                ns = scan_keys(c, gs, pats, &keys, P.st);
+            }
+            run_steps(c, gs, P.pd, n_pairs, keys, ns, P.o, P.st);
+            leave_run_stream(c, P.caller);
+            return;
+        }
         const FastResult r = fast_end(c, P.o, P.st, P.fr, &keys, &ns);
         if (r == kFastDone) {
             leave_run_stream(c, P.caller); // delivery copies may have been queued

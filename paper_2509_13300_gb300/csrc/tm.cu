@@ -678,22 +678,37 @@ __global__ void __launch_bounds__(kFastThreads) tm_fast_kernel(const ah_site *__
             brow = (int)(r / kTileW);
             wofs = t * 4 * kTileWX + (r % kTileW);
         }
-        // columns of the window's bases (bit q = base at position P + q is A / C / G / T)
+        // columns of the window's bases (bit q = base at position P + q is A / C / G / T),
+        // eight sites at a time: their 32 loads are all in flight before the ballots
         uint32_t cA = 0, cC = 0, cG = 0, cT = 0;
-        for (uint32_t todo = __ballot_sync(0xffffffffu, act); todo; todo &= todo - 1) {
-            const int k = __ffs(todo) - 1;
-            const uint64_t wk = __shfl_sync(0xffffffffu, wofs, k);
-            const int bk = __shfl_sync(0xffffffffu, brow, k);
-            const uint32_t *w = planes + wk + lane; // position P_k + lane (the tile's extension covers 32 more)
-            const uint32_t a = __ballot_sync(0xffffffffu, (__ldg(w) >> bk) & 1u);
-            const uint32_t c = __ballot_sync(0xffffffffu, (__ldg(w + kTileWX) >> bk) & 1u);
-            const uint32_t g = __ballot_sync(0xffffffffu, (__ldg(w + 2 * kTileWX) >> bk) & 1u);
-            const uint32_t tt = __ballot_sync(0xffffffffu, (__ldg(w + 3 * kTileWX) >> bk) & 1u);
-            if (lane == k) {
-                cA = a;
-                cC = c;
-                cG = g;
-                cT = tt;
+        const uint32_t actm = __ballot_sync(0xffffffffu, act);
+        for (int k0 = 0; k0 < 32; k0 += 8) {
+            if (!((actm >> k0) & 0xffu))
+                continue;
+            uint32_t wv[8][4];
+            int bk[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint64_t wk = __shfl_sync(0xffffffffu, wofs, k0 + j);
+                bk[j] = __shfl_sync(0xffffffffu, brow, k0 + j);
+                const bool on = (actm >> (k0 + j)) & 1u;
+                const uint32_t *w = planes + wk + lane; // position P_k + lane (the tile's extension covers 32 more)
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+                    wv[j][x] = on ? __ldg(w + x * kTileWX) : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t a = __ballot_sync(0xffffffffu, (wv[j][0] >> bk[j]) & 1u);
+                const uint32_t c = __ballot_sync(0xffffffffu, (wv[j][1] >> bk[j]) & 1u);
+                const uint32_t g = __ballot_sync(0xffffffffu, (wv[j][2] >> bk[j]) & 1u);
+                const uint32_t tt = __ballot_sync(0xffffffffu, (wv[j][3] >> bk[j]) & 1u);
+                if (lane == k0 + j) {
+                    cA = a;
+                    cC = c;
+                    cG = g;
+                    cT = tt;
+                }
             }
         }
         if (!act) {

@@ -127,6 +127,24 @@ def test_many_sites_take_the_thread_per_site_tm_path(ctx):
         o = oracle_run(w)
         assert 0 < o["pass_"].sum() < len(o["pass_"])
         assert_parity(gpu_run(ctx, w), o)
+    # ah_run, twice: the first run overflows the one-synchronisation sizes and
+    # finishes step by step; the second (the last count was large) queues only
+    # the scan in ah_run_begin and finishes in ah_run_end
+    p = w.pairs[0]
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    try:
+        pid = ctx.ah_set_primers(p["fwd"], p["rev"], p)
+        runs = [ctx.run(sid, [pid], tm_filter=True) for _ in range(2)]
+    finally:
+        ctx.ah_unload_genomes(sid)
+    o_amps = oracle.pair(o["sites"], w.pairs, o["pass_"])
+    o_seqs, o_offs = oracle.fetch(w.seq, w.contig_off, o_amps)
+    for r in runs:
+        assert r["sites"].tobytes() == o["sites"].tobytes()
+        assert np.array_equal(r["pass_"], o["pass_"])
+        ok = ~np.isnan(o["tm"])
+        assert np.abs(r["tm"][ok].astype(np.float64) - o["tm"][ok]).max() <= TM_TOL
+        assert r["amps"].tobytes() == o_amps.tobytes() and r["seqs"] == o_seqs
 
 
 def test_scan_wait_limit_reports_timeout_and_the_context_stays_usable(ctx):
