@@ -263,7 +263,7 @@ def main():
     ap.add_argument("--form", default="large", choices=["large", "collection", "plain", "batched", "served", "hmm"],
                     help="large: the 50,000-genome line (default); collection (alias plain): the 100-genome "
                          "line; batched / served / hmm: those forms' lines")
-    ap.add_argument("--e2e-chunks", type=int, default=1, help="large: chunks timed end to end from host input")
+    ap.add_argument("--e2e-chunks", type=int, default=2, help="large: chunks timed end to end from host input")
     ap.add_argument("--no-collection", action="store_true", help="large: skip the collection workload's key")
     ap.add_argument("--chunk-bases", type=int, default=2_000_000_000, help="batched: bases per set (whole genomes)")
     ap.add_argument("--plain-genomes", type=int, default=400, help="batched: genomes timed in the plain form")
@@ -434,53 +434,65 @@ def bench_collection(args, emit: bool = True):
                 "algorithmic": "1.5 B/base (1 B ASCII read + 0.5 B planes written)"}
 
     # ---- end to end through the public API with host (pinned) buffers ----
+    # the input as 2-bit codes and no-base runs (ah_load_genomes_2bit), and as ASCII
     seq_h = torch.from_numpy(w.seq).pin_memory()
+    codes, gaps = ah.encode_2bit(w.seq)
+    codes_h = torch.from_numpy(codes).pin_memory()
     out_h, bufs_h = run_out("cpu", True)
+    inputs = {"2bit": (lambda st_: ctx.ah_load_genomes_2bit(codes_h, n_bases, gaps, w.contig_off, w.contig_genome,
+                                                            st_), codes.nbytes + gaps.nbytes),
+              "ascii": (lambda st_: ctx.ah_load_genomes(seq_h, n_bases, w.contig_off, w.contig_genome, st_),
+                        n_bases)}
 
-    def counts_host():
+    def counts_host(kind):
         n, m, q = out_h.n_sites, out_h.n_amplicons, out_h.n_seq
-        h2d = n_bases + w.contig_off.nbytes + w.contig_genome.nbytes
+        h2d = inputs[kind][1] + w.contig_off.nbytes + w.contig_genome.nbytes
         d2h = 16 * n + 4 * n + n + 28 * m + q + 8 * (m + 1)
         return h2d, d2h
 
-    def steps_host(K):
+    def steps_host(K, kind):
         """K steps through the C ABI with host (pinned) input and outputs.  Pipelined
         (default): the next set's host load -- its copies and packing -- is issued
         right after this run is queued, so the host link stays busy while the run
         computes; the load returns once its copies are done."""
+        load = inputs[kind][0]
         if args.no_pipeline:
             for _ in range(K):
-                sid = ctx.ah_load_genomes(seq_h, n_bases, w.contig_off, w.contig_genome, stream)
+                sid = load(stream)
                 ctx.ah_run(sid, [pid], out_h, stream)
                 ctx.ah_unload_genomes(sid)
-            return counts_host()
-        prev = ctx.ah_load_genomes(seq_h, n_bases, w.contig_off, w.contig_genome, streams[0])
+            return counts_host(kind)
+        prev = load(streams[0])
         for i in range(K):
             ctx.ah_run_begin(prev, [pid], out_h, streams[i % 2], None)
             nxt = None
             if i + 1 < K:
-                nxt = ctx.ah_load_genomes(seq_h, n_bases, w.contig_off, w.contig_genome, streams[(i + 1) % 2])
+                nxt = load(streams[(i + 1) % 2])
             ctx.ah_run_end(out_h)
             ctx.ah_unload_genomes(prev)
             prev = nxt
-        return counts_host()
+        return counts_host(kind)
 
     e2e = None
     if args.e2e_steps > 0:
-        steps_host(2)
-        barrier(world)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(streams[0])
-        h2d, d2h = steps_host(args.e2e_steps)
-        for s_ in streams:
-            streams[0].wait_stream(s_)
-        e1.record(streams[0])
-        torch.cuda.synchronize()
-        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
-        e2e = {"value": bases_all * args.e2e_steps / (e2e_ms / 1e3) / 1e9, "unit": "Gbp/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
-               "pipeline": not args.no_pipeline}
+        res = {}
+        for kind in ("2bit", "ascii"):
+            steps_host(2, kind)
+            barrier(world)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(streams[0])
+            h2d, d2h = steps_host(args.e2e_steps, kind)
+            for s_ in streams:
+                streams[0].wait_stream(s_)
+            e1.record(streams[0])
+            torch.cuda.synchronize()
+            e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+            res[kind] = {"value": bases_all * args.e2e_steps / (e2e_ms / 1e3) / 1e9, "unit": "Gbp/s",
+                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "steps": args.e2e_steps,
+                         "pipeline": not args.no_pipeline}
+        e2e = dict(res["2bit"], input="2-bit base codes + no-base runs (ah_load_genomes_2bit) from pinned host memory",
+                   ascii_input=res["ascii"])
 
     if rank != 0:
         ctx.close()
@@ -570,6 +582,39 @@ def aligned_chunks(ctx, coll, tabs, torch):
             ctx.generate_bases(coll, g0, n, dev[a + (c0 - b0) - (c0 - g0):])
     torch.cuda.synchronize()
     return dev, starts
+
+
+def device_encode_2bit(torch, ascii_d, step: int = 1 << 28):
+    """The 2-bit codes and no-base runs of ah_load_genomes_2bit for ASCII bases in
+    device memory (torch ops, before any timed region): codes on the device,
+    runs as an (n, 2) uint64 numpy array."""
+    n = ascii_d.numel()
+    lut = torch.full((256,), 255, dtype=torch.uint8, device=ascii_d.device)
+    for i, ch in enumerate(b"ACGT"):
+        lut[ch] = i
+        lut[ch + 32] = i
+    codes = torch.empty((n + 3) // 4, dtype=torch.uint8, device=ascii_d.device)
+    starts, ends = [], []
+    prev = torch.zeros(1, dtype=torch.int8, device=ascii_d.device)
+    for a in range(0, n, step):  # step is a multiple of 4
+        b = min(n, a + step)
+        c = lut.index_select(0, ascii_d[a:b].int())
+        bad = c == 255
+        c = torch.where(bad, torch.zeros_like(c), c)
+        if (b - a) % 4:
+            c = torch.cat([c, torch.zeros(4 - (b - a) % 4, dtype=torch.uint8, device=c.device)])
+        q = c.view(-1, 4)
+        codes[a // 4:a // 4 + q.shape[0]] = q[:, 0] | (q[:, 1] << 2) | (q[:, 2] << 4) | (q[:, 3] << 6)
+        bi = bad.to(torch.int8)
+        d = torch.diff(bi, prepend=prev)
+        starts.append(torch.nonzero(d == 1).flatten() + a)
+        ends.append(torch.nonzero(d == -1).flatten() + a)
+        prev = bi[-1:]
+    st_ = torch.cat(starts).cpu().numpy().astype(np.uint64)
+    en = torch.cat(ends).cpu().numpy().astype(np.uint64)
+    if len(en) < len(st_):  # a run reaching the end
+        en = np.append(en, np.uint64(n))
+    return codes, np.stack([st_, en - st_], axis=1) if len(st_) else np.zeros((0, 2), np.uint64)
 
 
 def genome_chunks(coll, max_bases: int):
@@ -1260,49 +1305,76 @@ def bench_large_main(args):
     e2e = None
     ne = min(max(0, args.e2e_chunks), len(tabs))
     if ne > 0:
-        hb0, hb1 = tabs[0][0], tabs[ne - 1][1]
-        host = torch.empty(hb1 - hb0, dtype=torch.uint8, pin_memory=True)
+        torch.cuda.empty_cache()
+        hout = HostOut(torch, ah, (caps[0] * 9 // 8 + 1024, caps[1] * 9 // 8 + 64, caps[2] * 9 // 8 + 4096))
+        reps = max(1, args.e2e_steps // 5)
+
+        def measure(n_chunks, load, in_bytes):
+            """reps steps over the first n_chunks chunks from host input; the next
+            chunk's host load (copies + packing) is issued while the current run computes."""
+            def host_pass():
+                h2d = d2h = 0
+                prev = load(0, streams[0])
+                h2d += in_bytes[0]
+                for i in range(n_chunks):
+                    ctx.ah_run_begin(prev, pids, hout.o, streams[i % 2], None)
+                    nxt = None
+                    if i + 1 < n_chunks:
+                        nxt = load(i + 1, streams[(i + 1) % 2])
+                        h2d += in_bytes[i + 1]
+                    ctx.ah_run_end(hout.o)
+                    d2h += hout.d2h_bytes()
+                    ctx.ah_unload_genomes(prev)
+                    prev = nxt
+                return h2d, d2h
+
+            host_pass()
+            barrier(world)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(streams[0])
+            for _ in range(reps):
+                h2d, d2h = host_pass()
+            streams[0].wait_stream(streams[1])
+            e1.record(streams[0])
+            torch.cuda.synchronize()
+            e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+            sub = sum_over_ranks(float(sum(tabs[i][1] - tabs[i][0] for i in range(n_chunks))), world)
+            return sub * npair * reps / (e_ms / 1e3) / 1e9, int(h2d), int(d2h)
+
+        # 2-bit codes and no-base runs in pinned host memory (encoded before the timed region)
+        codes_h, gaps_h = [], []
         for i in range(ne):
             b0, b1 = tabs[i][0], tabs[i][1]
-            host[b0 - hb0:b1 - hb0].copy_(seq_d[at[i]:at[i] + b1 - b0])
-        hout = HostOut(torch, ah, (caps[0] * 9 // 8 + 1024, caps[1] * 9 // 8 + 64, caps[2] * 9 // 8 + 4096))
+            cd, gp = device_encode_2bit(torch, seq_d[at[i]:at[i] + b1 - b0])
+            ch = torch.empty(cd.numel(), dtype=torch.uint8, pin_memory=True)
+            ch.copy_(cd)
+            del cd
+            codes_h.append(ch)
+            gaps_h.append(gp)
 
-        def host_pass():
-            h2d = d2h = 0
-            b0, b1, off, gen_ = tabs[0]
-            prev = ctx.ah_load_genomes(host[b0 - hb0:b1 - hb0], b1 - b0, off, gen_, streams[0])
-            h2d += b1 - b0 + off.nbytes + gen_.nbytes
-            for i in range(ne):
-                ctx.ah_run_begin(prev, pids, hout.o, streams[i % 2], None)
-                nxt = None
-                if i + 1 < ne:
-                    b0, b1, off, gen_ = tabs[i + 1]
-                    nxt = ctx.ah_load_genomes(host[b0 - hb0:b1 - hb0], b1 - b0, off, gen_, streams[(i + 1) % 2])
-                    h2d += b1 - b0 + off.nbytes + gen_.nbytes
-                ctx.ah_run_end(hout.o)
-                d2h += hout.d2h_bytes()
-                ctx.ah_unload_genomes(prev)
-                prev = nxt
-            return h2d, d2h
+        def load2(i, st_):
+            b0, b1, off, gen_ = tabs[i]
+            return ctx.ah_load_genomes_2bit(codes_h[i], b1 - b0, gaps_h[i], off, gen_, st_)
 
-        host_pass()
-        reps = max(1, args.e2e_steps // 5)
-        barrier(world)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(streams[0])
-        for _ in range(reps):
-            h2d, d2h = host_pass()
-        streams[0].wait_stream(streams[1])
-        e1.record(streams[0])
-        torch.cuda.synchronize()
-        e_ms = max_over_ranks(e0.elapsed_time(e1), world)
-        sub = sum_over_ranks(float(hb1 - hb0), world)
-        e2e = {"value": sub * npair * reps / (e_ms / 1e3) / 1e9, "unit": "Gbp/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "steps": reps,
-               "subset": f"first {ne} of {len(tabs)} chunks ({(hb1 - hb0) / 1e9:.1f} Gbp of {N / 1e9:.1f}) per step",
-               "pipeline": "the next chunk's host load (copy + packing) is issued while the current run computes"}
+        in2 = [codes_h[i].numel() + gaps_h[i].nbytes + tabs[i][2].nbytes + tabs[i][3].nbytes for i in range(ne)]
+        v2, h2d2, d2h2 = measure(ne, load2, in2)
+        del codes_h
+        # the same from ASCII host input, first chunk (the link carries 4x the bytes)
+        b0, b1, off0, gen0 = tabs[0]
+        host = torch.empty(b1 - b0, dtype=torch.uint8, pin_memory=True)
+        host.copy_(seq_d[at[0]:at[0] + b1 - b0])
+        va, h2da, d2ha = measure(1, lambda i, st_: ctx.ah_load_genomes(host, b1 - b0, off0, gen0, st_),
+                                 [b1 - b0 + off0.nbytes + gen0.nbytes])
         del host
+        sub_gbp = sum(tabs[i][1] - tabs[i][0] for i in range(ne)) / 1e9
+        e2e = {"value": v2, "unit": "Gbp/s", "h2d_bytes_per_step": h2d2, "d2h_bytes_per_step": d2h2, "steps": reps,
+               "input": "2-bit base codes + no-base runs from pinned host memory (ah_load_genomes_2bit); outputs "
+                        "(sites, Tm, pass flags, amplicons, sequences) to pinned host memory",
+               "subset": f"first {ne} of {len(tabs)} chunks ({sub_gbp:.1f} Gbp of {N / 1e9:.1f}) per step",
+               "pipeline": "the next chunk's host load (copy + packing) is issued while the current run computes",
+               "ascii_input": {"value": va, "unit": "Gbp/s", "h2d_bytes_per_step": h2da, "d2h_bytes_per_step": d2ha,
+                               "subset": f"first chunk ({(b1 - b0) / 1e9:.1f} Gbp) from ASCII (ah_load_genomes)"}}
 
     # ---- oracle sample: the CPU baseline and parity with the GPU's records of the same genomes ----
     cpu = None
@@ -1334,12 +1406,13 @@ def bench_large_main(args):
     coll_key = None
     if not args.no_collection and world == 1:
         sub = argparse.Namespace(**vars(args))
-        sub.steps, sub.warmup, sub.e2e_steps, sub.no_cpu_baseline, sub.n_genomes = 400, 5, 0, True, None
+        sub.steps, sub.warmup, sub.e2e_steps, sub.no_cpu_baseline, sub.n_genomes = 400, 5, 20, True, None
         c = bench_collection(sub, emit=False)
         if c:
             coll_key = {"workload": c["config"]["workload"], "value": c["value"], "unit": c["unit"],
                         "ms_per_step": c["ms_per_step"], "steps": sub.steps,
-                        "timed_region_kernel_us": c["timed_region_kernel_us"], "roofline": c["roofline"]}
+                        "timed_region_kernel_us": c["timed_region_kernel_us"], "roofline": c["roofline"],
+                        "e2e": c["e2e"]}
     if rank != 0:
         return None
     line = {

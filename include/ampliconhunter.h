@@ -203,6 +203,23 @@ ah_status ah_load_genomes_ex(ah_ctx *ctx, const uint8_t *seq, uint64_t n_bases, 
                              uint32_t n_contigs, const uint32_t *contig_genome, uint32_t flags, uint32_t *set_id_out,
                              void *stream);
 
+/* ah_load_genomes from 2-bit base codes (the loaded set is the same as from
+ * the ASCII letters they encode): a quarter of the bytes over the host link.
+ * The idea is that of 2-bit genome files: two bits per base and a list of the
+ * runs that are no base (N, IUPAC codes, gaps).
+ * codes (host or device): ceil(n_bases / 4) bytes; base p is bits
+ * 2 (p % 4) .. 2 (p % 4) + 1 of byte p / 4, A 0, C 1, G 2, T 3.  Device
+ * codes must be 16-byte aligned (else AH_ERR_ARG).
+ * gaps (host): n_gaps (start, length) pairs of uint64, sorted by start,
+ * disjoint, length >= 1, inside [0, n_bases): the positions that are no
+ * base, whatever their codes hold.
+ * contig_off, contig_genome, set_id_out, stream, ownership, the waiting
+ * rules and errors: as ah_load_genomes (the call also returns AH_ERR_ARG for
+ * gaps that are unsorted, overlapping, empty or outside the set). */
+ah_status ah_load_genomes_2bit(ah_ctx *ctx, const uint8_t *codes, uint64_t n_bases, const uint64_t *gaps,
+                               uint64_t n_gaps, const uint64_t *contig_off, uint32_t n_contigs,
+                               const uint32_t *contig_genome, uint32_t *set_id_out, void *stream);
+
 /* Free a loaded genome set (after its packing has run).  AH_ERR_ARG for an
  * unknown id; AH_ERR_TIMEOUT for a packing that failed on the device and was
  * not reported before (the set is freed either way). */

@@ -119,6 +119,7 @@ def lib():
             "ah_device_bytes": (S, [P]),
             "ah_load_genomes": (I32, [P, P, U64, P, U32, P, ctypes.POINTER(U32), P]),
             "ah_load_genomes_ex": (I32, [P, P, U64, P, U32, P, U32, ctypes.POINTER(U32), P]),
+            "ah_load_genomes_2bit": (I32, [P, P, U64, P, U64, P, U32, P, ctypes.POINTER(U32), P]),
             "ah_unload_genomes": (I32, [P, U32]),
             "ah_set_primers": (I32, [P, ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(PcrParams),
                                      ctypes.POINTER(U32)]),
@@ -258,6 +259,18 @@ class Context:
         self._check(self._lib.ah_load_genomes_ex(self.h, _ptr(seq), n_bases, _ptr(contig_off), len(contig_off) - 1,
                                                  _ptr(contig_genome), AH_LOAD_REVERSED if reversed else 0,
                                                  ctypes.byref(sid), _stream(stream)))
+        return sid.value
+
+    def ah_load_genomes_2bit(self, codes, n_bases: int, gaps: np.ndarray, contig_off: np.ndarray,
+                             contig_genome: np.ndarray, stream=None) -> int:
+        """Load from 2-bit codes (encode_2bit) and the no-base runs (gaps: (n, 2) uint64)."""
+        gaps = np.ascontiguousarray(gaps, dtype=np.uint64).reshape(-1, 2)
+        contig_off = np.ascontiguousarray(contig_off, dtype=np.uint64)
+        contig_genome = np.ascontiguousarray(contig_genome, dtype=np.uint32)
+        sid = ctypes.c_uint32()
+        self._check(self._lib.ah_load_genomes_2bit(self.h, _ptr(codes), n_bases, _ptr(gaps) if len(gaps) else None,
+                                                   len(gaps), _ptr(contig_off), len(contig_off) - 1,
+                                                   _ptr(contig_genome), ctypes.byref(sid), _stream(stream)))
         return sid.value
 
     def ah_unload_genomes(self, set_id: int):
@@ -572,6 +585,29 @@ def debug_hmm_profile(seqs):
                                     _ptr(t), _ptr(e))
     assert rc == 0
     return m.value, ref.value, t, e
+
+
+def encode_2bit(seq: np.ndarray):
+    """ASCII bases -> (2-bit codes, no-base runs) for ah_load_genomes_2bit: base p
+    in bits 2 (p % 4) of byte p / 4 (A 0, C 1, G 2, T 3, either case); every
+    other letter is no base, listed as (start, length) runs (its code bits 0)."""
+    seq = np.ascontiguousarray(seq, dtype=np.uint8)
+    lut = np.full(256, 255, dtype=np.uint8)
+    for i, ch in enumerate(b"ACGT"):
+        lut[ch] = i
+        lut[ch + 32] = i
+    c = lut[seq]
+    bad = c == 255
+    c = np.where(bad, 0, c).astype(np.uint8)
+    n = len(c)
+    pad = np.zeros((-n) % 4, dtype=np.uint8)
+    q = np.concatenate([c, pad]).reshape(-1, 4)
+    codes = (q[:, 0] | (q[:, 1] << 2) | (q[:, 2] << 4) | (q[:, 3] << 6)).astype(np.uint8)
+    edges = np.diff(np.concatenate([[0], bad.view(np.int8), [0]]))
+    starts = np.nonzero(edges == 1)[0]
+    ends = np.nonzero(edges == -1)[0]
+    gaps = np.stack([starts, ends - starts], axis=1).astype(np.uint64) if len(starts) else np.zeros((0, 2), np.uint64)
+    return codes, gaps
 
 
 def debug_pipe_rates():

@@ -1621,9 +1621,17 @@ ah_status ah_load_genomes(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const
     return ah_load_genomes_ex(c, seq, n_bases, contig_off, n_contigs, contig_genome, 0, set_id_out, stream);
 }
 
-ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const uint64_t *contig_off,
-                             uint32_t n_contigs, const uint32_t *contig_genome, uint32_t flags, uint32_t *set_id_out,
-                             void *stream)
+namespace {
+// 2-bit input of ah_load_genomes_2bit: codes (host or device), no-base runs (host)
+struct TwoBit {
+    const uint64_t *gaps = nullptr;
+    uint64_t n_gaps = 0;
+};
+} // namespace
+
+static ah_status load_impl(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const uint64_t *contig_off,
+                           uint32_t n_contigs, const uint32_t *contig_genome, uint32_t flags, uint32_t *set_id_out,
+                           void *stream, const TwoBit *two)
 {
     if (!c)
         return AH_ERR_ARG;
@@ -1677,6 +1685,9 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
         const bool dev_seq = n_bases && is_device_ptr(c, seq);
         // a queued run leaves the flag block alone for plain loads (host or device input)
         require(!reversed || !c->pend.active, AH_ERR_ARG, "a run is pending: reversed sets are loaded after ah_run_end");
+        require(!two || !reversed, AH_ERR_ARG, "ah_load_genomes_2bit: no reversed form");
+        require(!two || !dev_seq || reinterpret_cast<uintptr_t>(seq) % 16 == 0, AH_ERR_ARG,
+                "ah_load_genomes_2bit: device codes must be 16-byte aligned");
         // the packing first (it reads no contig table), then the tables' copies
         std::vector<void *> temp; // freed once the packing is done (reversed loads)
         if (gs->n_tiles && reversed) {
@@ -1705,6 +1716,47 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
             Stage sg(c, "pack", st, 2);
             launch_reverse_contigs(src, dst, ch_d, ch.size(), st);
             launch_pack(dst, 0, n_bases, n_bases, gs->planes, 0, gs->n_tiles, c->d_err, st);
+        } else if (gs->n_tiles && two) {
+            HostSpan hs_pack(c, "host.load.pack");
+            // the no-base runs on the device (small; the host array may go when the call returns)
+            uint64_t *gaps_d = (uint64_t *)scratch(c, "load_gaps", std::max<uint64_t>(two->n_gaps, 1) * 16);
+            if (two->n_gaps)
+                AH_CUDA(cudaMemcpyAsync(gaps_d, two->gaps, two->n_gaps * 16, cudaMemcpyHostToDevice, st));
+            if (dev_seq) {
+                Stage sg(c, "pack", st, 1);
+                launch_pack2(seq, 0, n_bases, n_bases, gaps_d, two->n_gaps, gs->planes, 0, gs->n_tiles, st);
+            } else {
+                // host codes: tile-aligned chunks through two staging buffers, copies on
+                // the copy stream beside the packing of the previous chunk; each chunk
+                // also carries the next 64 positions (the extension row)
+                const uint64_t chunk_tiles = 2048; // 64 Mbp, 16 MB of codes
+                const uint64_t stage_bytes = (chunk_tiles * kTileBases + 64) / 4;
+                uint8_t *stage[2] = {(uint8_t *)scratch(c, "load_stage0", stage_bytes),
+                                     (uint8_t *)scratch(c, "load_stage1", stage_bytes)};
+                AH_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[0], 0));
+                AH_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[1], 0));
+                AH_CUDA(cudaEventRecord(c->ev_load_start, st));
+                AH_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_load_start, 0));
+                uint64_t i = 0;
+                for (uint64_t t0 = 0; t0 < gs->n_tiles; t0 += chunk_tiles, ++i) {
+                    const int b = (int)(i & 1);
+                    const uint64_t t1 = std::min(gs->n_tiles, t0 + chunk_tiles);
+                    const uint64_t b0 = t0 * kTileBases;
+                    const uint64_t b1 = std::min(n_bases, t1 * kTileBases + 64);
+                    if (i >= 2)
+                        AH_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[b], 0));
+                    AH_CUDA(cudaMemcpyAsync(stage[b], seq + b0 / 4, (b1 - b0 + 3) / 4, cudaMemcpyHostToDevice,
+                                            c->copy_stream));
+                    AH_CUDA(cudaEventRecord(c->ev_copied[b], c->copy_stream));
+                    AH_CUDA(cudaStreamWaitEvent(st, c->ev_copied[b], 0));
+                    {
+                        Stage sg(c, "pack", st, 1);
+                        launch_pack2(stage[b], b0, b1 - b0, n_bases, gaps_d, two->n_gaps, gs->planes, t0, t1, st);
+                    }
+                    AH_CUDA(cudaEventRecord(c->ev_packed[b], st));
+                }
+                AH_CUDA(cudaEventRecord(c->ev_last_copy, c->copy_stream));
+            }
         } else if (gs->n_tiles) {
             HostSpan hs_pack(c, "host.load.pack");
             if (dev_seq) {
@@ -1818,6 +1870,36 @@ ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, co
         c->sets[id] = std::move(gs);
         *set_id_out = id;
     });
+}
+
+ah_status ah_load_genomes_ex(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, const uint64_t *contig_off,
+                             uint32_t n_contigs, const uint32_t *contig_genome, uint32_t flags, uint32_t *set_id_out,
+                             void *stream)
+{
+    return load_impl(c, seq, n_bases, contig_off, n_contigs, contig_genome, flags, set_id_out, stream, nullptr);
+}
+
+ah_status ah_load_genomes_2bit(ah_ctx *c, const uint8_t *codes, uint64_t n_bases, const uint64_t *gaps,
+                               uint64_t n_gaps, const uint64_t *contig_off, uint32_t n_contigs,
+                               const uint32_t *contig_genome, uint32_t *set_id_out, void *stream)
+{
+    if (!c)
+        return AH_ERR_ARG;
+    if ((n_gaps && !gaps) || (n_bases && !codes)) {
+        c->err = "ah_load_genomes_2bit: null codes or gaps";
+        return AH_ERR_ARG;
+    }
+    for (uint64_t g = 0; g < n_gaps; ++g) { // sorted, disjoint, inside the set
+        const uint64_t a = gaps[2 * g], len = gaps[2 * g + 1];
+        if (len == 0 || a + len > n_bases || a + len < a || (g && a < gaps[2 * g - 2] + gaps[2 * g - 1])) {
+            c->err = "ah_load_genomes_2bit: gaps must be sorted, disjoint, non-empty runs inside the set";
+            return AH_ERR_ARG;
+        }
+    }
+    TwoBit two;
+    two.gaps = gaps;
+    two.n_gaps = n_gaps;
+    return load_impl(c, codes, n_bases, contig_off, n_contigs, contig_genome, 0, set_id_out, stream, &two);
 }
 
 ah_status ah_unload_genomes(ah_ctx *c, uint32_t set_id)

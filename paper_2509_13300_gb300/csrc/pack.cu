@@ -232,6 +232,158 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const uint8_t *__res
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packer from 2-bit base codes (the load form whose host input is a quarter
+// of ASCII's size): base p is bits 2 (p % 4) .. 2 (p % 4) + 1 of byte p / 4,
+// A 0, C 1, G 2, T 3; positions listed in `gaps` (sorted, disjoint (start,
+// length) pairs) and positions at or past n_bases are no base (all four
+// planes 0).  One block per tile: the tile's 8 KB of codes and the next
+// tile's first 8 bytes (the extension row) are loaded into shared memory with
+// coalesced 16-byte loads; thread ci builds the plane words of columns
+// 4 ci .. 4 ci + 3, for which row b holds exactly byte ci of the row.  Four
+// rows at a time: the rows' bytes form one 32-bit word, and each column's low
+// and high code bits are gathered into a nibble by one carry-free multiply.
+// A tile that a gap or the end of the data touches marks its no-base
+// positions in a shared bitmap first.
+// ---------------------------------------------------------------------------
+constexpr int kCodeRowBytes = kTileW / 4;                  // 256 bytes of codes per row
+constexpr int kCodeWords = (32 * kCodeRowBytes + 16) / 4;  // the tile + the extension row (16 bytes read)
+constexpr int kInvWords = (kTileBases + 32) / 32;          // no-base bitmap of the tile + extension row
+
+// bits 0, 8, 16, 24 of v (each 0 or 1) -> bits 0..3
+__device__ __forceinline__ uint32_t gather4(uint32_t v) { return (v * 0x10204080u) >> 28; }
+
+__global__ void __launch_bounds__(kPackThreads) pack2_kernel(const uint8_t *__restrict__ codes, uint64_t base0,
+                                                             uint64_t n_avail, uint64_t n_bases,
+                                                             const uint64_t *__restrict__ gaps, uint64_t n_gaps,
+                                                             uint32_t *__restrict__ planes, uint64_t t0, uint64_t t1)
+{
+    __shared__ __align__(16) uint32_t cw[kCodeWords];
+    __shared__ uint32_t inv[kInvWords];
+    __shared__ uint64_t first_gap;
+    __shared__ int any_inv;
+    const int ci = threadIdx.x;
+    const uint64_t avail_end = base0 + n_avail < n_bases ? base0 + n_avail : n_bases; // bases present here
+    for (uint64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
+        const uint64_t p0 = t * kTileBases, pe = p0 + kTileBases + 32; // the tile and its extension row
+        // codes: bytes (p0 - base0) / 4 .. + 8208 of `codes`; zero past the available bytes
+        const uint64_t cb0 = (p0 - base0) / 4;
+        const uint64_t bytes_avail = (avail_end > p0 ? (avail_end - p0 + 3) / 4 : 0);
+        if (bytes_avail >= (uint64_t)kCodeWords * 4) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(codes + cb0);
+            for (int w = ci; w < kCodeWords / 4; w += blockDim.x)
+                reinterpret_cast<uint4 *>(cw)[w] = __ldg(src + w);
+        } else {
+            for (int w = ci; w < kCodeWords; w += blockDim.x) {
+                uint32_t v = 0;
+                for (int q = 0; q < 4; ++q)
+                    if ((uint64_t)(4 * w + q) < bytes_avail)
+                        v |= (uint32_t)codes[cb0 + 4 * w + q] << (8 * q);
+                cw[w] = v;
+            }
+        }
+        // no-base positions: gaps that meet [p0, pe), and everything at or past avail_end
+        if (ci == 0) {
+            uint64_t lo = 0, hi = n_gaps; // first gap ending after p0
+            while (lo < hi) {
+                const uint64_t mid = (lo + hi) / 2;
+                if (gaps[2 * mid] + gaps[2 * mid + 1] <= p0)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            first_gap = lo;
+            any_inv = (lo < n_gaps && gaps[2 * lo] < pe) || avail_end < pe;
+        }
+        __syncthreads();
+        const bool marked = any_inv != 0;
+        if (marked) {
+            for (int w = ci; w < kInvWords; w += blockDim.x)
+                inv[w] = 0u;
+            __syncthreads();
+            auto mark = [&](uint64_t a, uint64_t b) { // positions [a, b) of the tile, relative to p0
+                const uint64_t w0 = a >> 5, w1 = (b - 1) >> 5;
+                for (uint64_t w = w0 + ci; w <= w1; w += blockDim.x) {
+                    const uint64_t x0 = a > 32 * w ? a - 32 * w : 0, x1 = b < 32 * w + 32 ? b - 32 * w : 32;
+                    const uint32_t m = (x1 - x0 >= 32 ? 0xffffffffu : ((1u << (x1 - x0)) - 1u)) << x0;
+                    atomicOr(&inv[w], m);
+                }
+            };
+            for (uint64_t g = first_gap; g < n_gaps && gaps[2 * g] < pe; ++g) {
+                const uint64_t a = gaps[2 * g] > p0 ? gaps[2 * g] - p0 : 0;
+                const uint64_t e = gaps[2 * g] + gaps[2 * g + 1];
+                const uint64_t b = (e < pe ? e : pe) - p0;
+                if (b > a)
+                    mark(a, b);
+            }
+            if (avail_end < pe)
+                mark(avail_end > p0 ? avail_end - p0 : 0, pe - p0);
+        }
+        __syncthreads();
+        const uint8_t *cbytes = reinterpret_cast<const uint8_t *>(cw);
+        uint32_t lo[4] = {0, 0, 0, 0}, hi[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int rb = 0; rb < 8; ++rb) {
+            const uint32_t x = (uint32_t)cbytes[(4 * rb + 0) * kCodeRowBytes + ci] |
+                               ((uint32_t)cbytes[(4 * rb + 1) * kCodeRowBytes + ci] << 8) |
+                               ((uint32_t)cbytes[(4 * rb + 2) * kCodeRowBytes + ci] << 16) |
+                               ((uint32_t)cbytes[(4 * rb + 3) * kCodeRowBytes + ci] << 24);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                lo[k] |= gather4((x >> (2 * k)) & 0x01010101u) << (4 * rb);
+                hi[k] |= gather4((x >> (2 * k + 1)) & 0x01010101u) << (4 * rb);
+            }
+        }
+        uint32_t val[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
+        if (marked) {
+#pragma unroll 4
+            for (int b = 0; b < 32; ++b) {
+                const uint32_t nib = (inv[b * (kTileW / 32) + (ci >> 3)] >> (4 * (ci & 7))) & 0xFu;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    val[k] &= ~(((nib >> k) & 1u) << b);
+            }
+        }
+        uint4 pa, pc, pg, pt;
+        uint32_t *A = &pa.x, *C = &pc.x, *G = &pg.x, *T = &pt.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            A[k] = val[k] & ~hi[k] & ~lo[k];
+            C[k] = val[k] & ~hi[k] & lo[k];
+            G[k] = val[k] & hi[k] & ~lo[k];
+            T[k] = val[k] & hi[k] & lo[k];
+        }
+        uint32_t *dst = planes + t * 4 * kTileWX;
+        const int j0 = 4 * ci;
+        *reinterpret_cast<uint4 *>(dst + 0 * kTileWX + j0) = pa;
+        *reinterpret_cast<uint4 *>(dst + 1 * kTileWX + j0) = pc;
+        *reinterpret_cast<uint4 *>(dst + 2 * kTileWX + j0) = pg;
+        *reinterpret_cast<uint4 *>(dst + 3 * kTileWX + j0) = pt;
+        if (j0 < kTileExt) {
+            // extension words: row b + 1 of the same column, bit 31 from the next tile's head
+            const uint32_t hb = cbytes[32 * kCodeRowBytes + ci];
+            uint32_t hv = 0xFu;
+            if (marked)
+                hv = ~(inv[kTileBases / 32 + (ci >> 3)] >> (4 * (ci & 7))) & 0xFu;
+            uint4 ea, ec, eg, et;
+            uint32_t *EA = &ea.x, *EC = &ec.x, *EG = &eg.x, *ET = &et.x;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t code = (hb >> (2 * k)) & 3u, v = (hv >> k) & 1u;
+                EA[k] = (A[k] >> 1) | ((v & (code == 0)) << 31);
+                EC[k] = (C[k] >> 1) | ((v & (code == 1)) << 31);
+                EG[k] = (G[k] >> 1) | ((v & (code == 2)) << 31);
+                ET[k] = (T[k] >> 1) | ((v & (code == 3)) << 31);
+            }
+            *reinterpret_cast<uint4 *>(dst + 0 * kTileWX + kTileW + j0) = ea;
+            *reinterpret_cast<uint4 *>(dst + 1 * kTileWX + kTileW + j0) = ec;
+            *reinterpret_cast<uint4 *>(dst + 2 * kTileWX + kTileW + j0) = eg;
+            *reinterpret_cast<uint4 *>(dst + 3 * kTileWX + kTileW + j0) = et;
+        }
+        __syncthreads(); // the shared buffers are refilled for the next tile
+    }
+}
+
 // Decode the planes back to one byte per position (0 = no base, 1..4 = A C G T,
 // 5 = more than one plane set, which the packer never produces).  Test aid.
 __global__ void unpack_kernel(const uint32_t *__restrict__ planes, uint8_t *__restrict__ codes, uint64_t n_bases)
@@ -261,6 +413,26 @@ __global__ void copy_words_kernel(const uint32_t *__restrict__ src, uint32_t *__
         dst[i] = src[i];
 }
 } // namespace
+
+void launch_pack2(const uint8_t *codes, uint64_t base0, uint64_t n_avail, uint64_t n_bases, const uint64_t *gaps,
+                  uint64_t n_gaps, uint32_t *planes, uint64_t t0, uint64_t t1, cudaStream_t s)
+{
+    if (t1 <= t0)
+        return;
+    if (reinterpret_cast<uintptr_t>(codes) % 16 != 0 || base0 % kTileBases != 0)
+        throw Error(AH_ERR_ARG, "2-bit codes must start 16-byte aligned at a tile boundary");
+    static int cached_dev = -1, sms = 148;
+    int dev = 0;
+    AH_CUDA(cudaGetDevice(&dev));
+    if (dev != cached_dev) {
+        AH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        cached_dev = dev;
+    }
+    const uint64_t blocks = std::min<uint64_t>(t1 - t0, (uint64_t)sms * 8);
+    pack2_kernel<<<(unsigned)blocks, kPackThreads, 0, s>>>(codes, base0, n_avail, n_bases, gaps, n_gaps, planes, t0,
+                                                           t1);
+    AH_CUDA(cudaGetLastError());
+}
 
 void launch_copy_words(const uint32_t *src, uint32_t *dst, uint64_t n_words, cudaStream_t s)
 {

@@ -106,3 +106,18 @@ def test_parity_summary_flags_each_kind_of_difference():
         assert not bench.parity_summary(c, got(am=a2), want)["amplicons_equal"]
         q2 = bytes([qs[0] ^ 1]) + qs[1:]
         assert not bench.parity_summary(c, got(qs=q2), want)["sequences_equal"]
+
+
+def test_device_encode_2bit_equals_the_host_encoder():
+    """The bench's torch encoder (run here on CPU tensors) gives the codes and
+    runs of ah.encode_2bit, also across its internal steps and at the end."""
+    import torch
+    from paper_2509_13300_gb300 import ah
+    rng = np.random.default_rng(8)
+    letters = np.frombuffer(b"ACGTacgtNNNNRY-", dtype=np.uint8)
+    for n, step in ((1, 4), (37, 8), (1001, 16), (5000, 1 << 28)):
+        seq = letters[rng.integers(0, len(letters), n)]
+        seq[-1] = ord("N")  # a run reaching the end
+        codes, gaps = bench.device_encode_2bit(torch, torch.from_numpy(seq.copy()), step=step)
+        c2, g2 = ah.encode_2bit(seq)
+        assert codes.numpy().tobytes() == c2.tobytes() and np.array_equal(gaps, g2), (n, step)

@@ -62,3 +62,25 @@ def test_operon_family_plants_homologous_amplicons():
     assert len(w.contig_genome) == 4 and w.n_bases == 240_000
     p = w.pairs[0]
     assert len(p["fwd"]) == 20 and len(p["rev"]) == 20 and p["max_len"] == 800
+
+
+def test_encode_2bit_round_trip():
+    """The 2-bit host encoding of ah_load_genomes_2bit: decoding the codes and
+    the no-base runs gives the input upper-cased, every non-ACGT letter as N."""
+    from paper_2509_13300_gb300 import ah
+    rng = np.random.default_rng(4)
+    letters = np.frombuffer(b"ACGTacgtNnRYKM-.", dtype=np.uint8)
+    for n in (0, 1, 3, 4, 5, 1000, 4097):
+        seq = letters[rng.integers(0, len(letters), n)] if n else np.zeros(0, np.uint8)
+        codes, gaps = ah.encode_2bit(seq)
+        assert len(codes) == (n + 3) // 4 and gaps.shape[1] == 2
+        dec = np.array([b"ACGT"[(codes[p // 4] >> (2 * (p % 4))) & 3] for p in range(n)], dtype=np.uint8)
+        for a, ln in gaps.tolist():
+            dec[a:a + ln] = ord("N")
+        want = np.array([ch - 32 if 97 <= ch <= 122 else ch for ch in seq.tolist()], dtype=np.uint8)
+        want = np.where(np.isin(want, np.frombuffer(b"ACGT", np.uint8)), want, ord("N")).astype(np.uint8)
+        assert dec.tobytes() == want.tobytes()
+        # runs are sorted, disjoint, non-empty and maximal
+        if len(gaps) > 1:
+            assert np.all(gaps[1:, 0] > gaps[:-1, 0] + gaps[:-1, 1])
+        assert np.all(gaps[:, 1] >= 1) if len(gaps) else True

@@ -199,6 +199,72 @@ def test_full_collection_workload_against_the_oracle(ctx):
     assert g["seqs"] == q and np.array_equal(g["offs"].astype(np.uint64), qo.astype(np.uint64))
 
 
+@pytest.mark.parametrize("device_input", [False, True])
+def test_2bit_load_gives_the_letters(ctx, device_input):
+    """ah_load_genomes_2bit over 70 Mbp (two host staging chunks, a tiny
+    contig, a contig ending inside a tile, N runs, IUPAC letters, gaps and
+    lower case): fetching every contig whole gives the input upper-cased with
+    every non-ACGT letter as N, exactly as the ASCII load does."""
+    import torch
+    rng = np.random.default_rng(23)
+    n = 70_000_003
+    seq = np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, n)].copy()
+    lower = rng.random(n) < 0.01
+    seq[lower] += 32
+    for s0 in rng.integers(0, n - 200, 3000):  # runs of other letters
+        seq[s0:s0 + int(rng.integers(1, 120))] = np.frombuffer(b"NRY-", np.uint8)[int(rng.integers(0, 4))]
+    off = np.array([0, 5, 40_000_000, 40_032_781, 69_999_000, n], dtype=np.uint64)
+    gen = np.array([0, 0, 1, 1, 2], dtype=np.uint32)
+    codes, gaps = ah.encode_2bit(seq)
+    src = torch.from_numpy(codes).cuda() if device_input else codes
+    amps = np.zeros(len(off) - 1, dtype=ah.AMPLICON_DTYPE)
+    amps["genome"] = gen
+    amps["contig"] = np.arange(len(off) - 1)
+    amps["end"] = np.diff(off.astype(np.int64))
+    up = np.where((seq >= 97) & (seq <= 122), seq - 32, seq).astype(np.uint8)
+    want = np.where(np.isin(up, np.frombuffer(b"ACGT", np.uint8)), up, ord("N")).astype(np.uint8).tobytes()
+    for load in ("2bit", "ascii"):
+        if load == "2bit":
+            sid = ctx.ah_load_genomes_2bit(src, n, gaps, off, gen)
+        else:
+            sid = ctx.load(seq, off, gen)
+        try:
+            got, offs = ctx.fetch(sid, amps)
+        finally:
+            ctx.ah_unload_genomes(sid)
+        assert got == want, load
+        assert np.array_equal(offs.astype(np.int64), off.astype(np.int64))
+
+
+def test_2bit_load_scan_parity(ctx):
+    """The whole path on a set loaded from 2-bit codes equals the oracle on the
+    letters (short primers, lower case, IUPAC letters and gaps, tiny contigs)."""
+    w = synth.random_small(61, n_bases=90_000, n_contigs=7, L_f=9, L_r=8, k=2, codes_f="RN", codes_r="SB",
+                           lower_frac=0.05, iupac_frac=0.01, min_len=30, max_len=600)
+    codes, gaps = ah.encode_2bit(w.seq)
+    sid = ctx.ah_load_genomes_2bit(codes, len(w.seq), gaps, w.contig_off, w.contig_genome)
+    try:
+        pids = [ctx.ah_set_primers(p["fwd"], p["rev"], p) for p in w.pairs]
+        sites = ctx.scan(sid, pids)
+        tm, ps = ctx.tm(sid, pids, sites)
+        amps = ctx.pair(sid, pids, sites)
+        amps_tm = ctx.pair(sid, pids, sites, ps)
+        seqs, offs = ctx.fetch(sid, amps)
+    finally:
+        ctx.ah_unload_genomes(sid)
+    g = dict(sites=sites, tm=tm, pass_=ps, amps=amps, amps_tm=amps_tm, seqs=seqs, offs=offs)
+    assert_parity(g, oracle_run(w), min_sites=50)
+
+
+def test_2bit_load_rejects_bad_gaps(ctx):
+    codes = np.zeros(25, np.uint8)
+    off, gen = np.array([0, 100], np.uint64), np.zeros(1, np.uint32)
+    for bad in ([[10, 0]], [[10, 5], [12, 3]], [[90, 20]], [[50, 5], [10, 5]]):
+        with pytest.raises(ah.AHError) as e:
+            ctx.ah_load_genomes_2bit(codes, 100, np.array(bad, np.uint64), off, gen)
+        assert e.value.status == ah.AH_ERR_ARG
+
+
 def test_collection_spanning_many_tiles(ctx):
     """Genome-collection generator at reduced size: ~5 Mbp, 6 genomes, many
     contigs, N runs, planted operons with 0-4 substitutions, the 960-oligo pair."""
