@@ -232,7 +232,9 @@ def load_peaks():
 
 
 def traffic_record(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, if it still matches this build."""
+    """DRAM bytes per unit (base or site) of a kernel from a committed ncu
+    capture, if it still matches this build (a launch's traffic grows with the
+    bases it packs or scans: the bench scales it to the launches it times)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         rec = json.load(open(path)).get(kernel)
@@ -418,7 +420,7 @@ def bench_collection(args, emit: bool = True):
     if dominant == "scan":
         tr = traffic_record("ah_scan_kernel")
         roof = {"bound": "alu", "achieved": scan_tops, "peak": alu_peak, "unit": "Tops/s",
-                "frac": scan_tops / alu_peak, "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "frac": scan_tops / alu_peak, "traffic": tr["dram_bytes_per_base"] * n_bases if tr else None,
                 "kernel": "ah_scan_kernel",
                 "peak_note": f"logic pipe: {SMS} SMs x {lanes:.1f} LOP3 lanes/clk x {clk_mhz:.0f} MHz "
                              f"(median SM clock under load); lanes {lanes_src}",
@@ -429,7 +431,7 @@ def bench_collection(args, emit: bool = True):
     else:
         tr = traffic_record("pack_kernel")
         roof = {"bound": "hbm", "achieved": pack_hbm, "peak": hbm_peak, "unit": "GB/s",
-                "frac": pack_hbm / hbm_peak, "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "frac": pack_hbm / hbm_peak, "traffic": tr["dram_bytes_per_base"] * n_bases if tr else None,
                 "kernel": "pack_kernel", "peak_kind": peak_kind,
                 "algorithmic": "1.5 B/base (1 B ASCII read + 0.5 B planes written)"}
 
@@ -1285,13 +1287,14 @@ def bench_large_main(args):
     # the scan dominates the serialised launch list; the packing's live time is
     # stretched by the run it overlaps, so it is reported beside (pack_roofline)
     tr_pack = traffic_record("pack_kernel")
+    per_launch = N / len(tabs)  # bases per chunk: one packing and one launch per launch group
     pack_roof = {"bound": "hbm", "achieved": pack_hbm, "peak": hbm_peak, "unit": "GB/s", "frac": pack_hbm / hbm_peak,
-                 "traffic": tr_pack["dram_bytes_per_launch"] if tr_pack else None, "kernel": "pack_kernel",
+                 "traffic": tr_pack["dram_bytes_per_base"] * per_launch if tr_pack else None, "kernel": "pack_kernel",
                  "peak_kind": peak_kind, "algorithmic": "1.5 B/base (1 B ASCII read + 0.5 B planes written)",
                  "note": "live duration includes the sort/Tm/pair/fetch kernels of the previous chunk it runs beside"}
     tr = traffic_record("ah_scan_kernel")
     roof = {"bound": "alu", "achieved": scan_tops, "peak": alu_peak, "unit": "Tops/s",
-            "frac": scan_tops / alu_peak, "traffic": tr["dram_bytes_per_launch"] if tr else None,
+            "frac": scan_tops / alu_peak, "traffic": tr["dram_bytes_per_base"] * per_launch if tr else None,
             "kernel": "ah_scan_kernel",
             "peak_note": f"logic pipe: {SMS} SMs x {lanes:.1f} LOP3 lanes/clk x {clk_mhz:.0f} MHz (median SM clock "
                          f"under load); lanes {lanes_src}",
@@ -1299,7 +1302,8 @@ def bench_large_main(args):
                            f"{live['scan']['launches_per_step'] / len(tabs):.0f} launches per chunk)",
             "hbm_achieved_gbs": scan_hbm, "hbm_peak_gbs": hbm_peak, "hbm_frac": scan_hbm / hbm_peak,
             "hbm_peak_kind": peak_kind, "hbm_algorithmic": "0.5 B/base of planes per launch"}
-    roof["scope"] = "all launches of the kernel in one step, summed; per-launch traffic from the ncu capture"
+    roof["scope"] = ("achieved: all launches of the kernel in one step; traffic: DRAM bytes of one launch (one launch "
+                     "group over an average chunk), scaled by bases from an ncu capture of a 0.31 Gbp launch")
 
     # ---- end to end through the C ABI: host (pinned) input and outputs, the first chunks ----
     e2e = None
@@ -1420,7 +1424,8 @@ def bench_large_main(args):
         "warmup": max(3, args.warmup), "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32",
         "data": "synthetic (counter-based Philox4x32-10 bases, seed 7 + rank, generated on the device)",
-        "config": {"workload": LARGE_WORKLOAD, "n_genomes": n_g, "n_bases_per_gpu": N,
+        "config": {"workload": LARGE_WORKLOAD if n_g == 50_000 else f"large-{n_g}genomes-{N / 1e9:.1f}Gbp-3pairs-k4",
+                   "n_genomes": n_g, "n_bases_per_gpu": N,
                    "n_contigs": len(coll.contig_genome), "pairs": npair, "oligos": [960, 64, 256], "k": 4,
                    "window": [100, 3000], "tm_min_C": 50.0, "tm_dtype": "f32", "chunks": len(tabs),
                    "chunk_bases_max": cmax, "parallelism": f"replicas x{world}", "scan_tuning": tune,
