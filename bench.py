@@ -269,6 +269,7 @@ def main():
     ap.add_argument("--no-collection", action="store_true", help="large: skip the collection workload's key")
     ap.add_argument("--chunk-bases", type=int, default=2_000_000_000, help="batched: bases per set (whole genomes)")
     ap.add_argument("--plain-genomes", type=int, default=400, help="batched: genomes timed in the plain form")
+    ap.add_argument("--batched-input", default="2bit", choices=["2bit", "ascii"], help="batched: host input format")
     ap.add_argument("--requests", type=int, default=2000, help="served: requests")
     ap.add_argument("--rate", type=float, default=20.0, help="served: Poisson arrivals per second")
     ap.add_argument("--max-batch", type=int, default=64, help="served: requests per batch")
@@ -700,7 +701,18 @@ def bench_batched(args):
     chunks = genome_chunks(coll, args.chunk_bases)
     tabs = [sub_tables(coll, g0, g1) for g0, g1 in chunks]
     cmax = max(b1 - b0 for b0, b1, _, _ in tabs)
-    dbuf = [torch.empty(cmax, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    two = args.batched_input == "2bit"
+    codes_h, gaps_h = [], []
+    if two:  # every chunk as 2-bit codes and no-base runs in pinned host memory (encoded once)
+        for b0, b1, _, _ in tabs:
+            cd, gp = device_encode_2bit(torch, host[b0:b1].cuda())
+            ch = torch.empty(cd.numel(), dtype=torch.uint8, pin_memory=True)
+            ch.copy_(cd)
+            codes_h.append(ch)
+            gaps_h.append(gp)
+        del cd
+        torch.cuda.empty_cache()
+    dbuf = [torch.empty((cmax + 3) // 4 + 16 if two else cmax, dtype=torch.uint8, device="cuda") for _ in range(2)]
     cs = torch.cuda.Stream()                              # host-to-device copies
     st = [torch.cuda.Stream(), torch.cuda.Stream()]       # two sets in flight
     copied = [torch.cuda.Event() for _ in range(2)]
@@ -714,14 +726,20 @@ def bench_batched(args):
         with torch.cuda.stream(cs):
             if i >= 2:
                 cs.wait_event(packed[i % 2])            # buffer free once chunk i-2 is packed
-            dbuf[i % 2][:b1 - b0].copy_(host[b0:b1], non_blocking=True)
+            if two:
+                dbuf[i % 2][:codes_h[i].numel()].copy_(codes_h[i], non_blocking=True)
+            else:
+                dbuf[i % 2][:b1 - b0].copy_(host[b0:b1], non_blocking=True)
             copied[i % 2].record(cs)
 
     def load(i):
         b0, b1, off, gen_ = tabs[i]
         s = st[i % 2]
         s.wait_event(copied[i % 2])
-        sid = ctx.ah_load_genomes(dbuf[i % 2], b1 - b0, off, gen_, s)
+        if two:
+            sid = ctx.ah_load_genomes_2bit(dbuf[i % 2], b1 - b0, gaps_h[i], off, gen_, s)
+        else:
+            sid = ctx.ah_load_genomes(dbuf[i % 2], b1 - b0, off, gen_, s)
         packed[i % 2].record(s)
         return sid
 
@@ -744,16 +762,20 @@ def bench_batched(args):
         totals.update(sites=n_s, amplicons=n_a, seq=n_q, d2h_bytes=d2h)
 
     # the host link alone: every chunk's pinned host -> device copy, back to back
-    h2d_chunk = []
+    h2d_chunk, link_bytes = [], 0
     for i, (b0, b1, _, _) in enumerate(tabs):
+        nb = codes_h[i].numel() if two else b1 - b0
+        link_bytes += nb
         h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         h0.record(cs)
         with torch.cuda.stream(cs):
-            dbuf[i % 2][:b1 - b0].copy_(host[b0:b1], non_blocking=True)
+            dbuf[i % 2][:nb].copy_(codes_h[i] if two else host[b0:b1], non_blocking=True)
         h1.record(cs)
         torch.cuda.synchronize()
-        h2d_chunk.append((b1 - b0) / (h0.elapsed_time(h1) / 1e3) / 1e9)
-    h2d_gbs = N / sum((b1 - b0) / (g * 1e9) for (b0, b1, _, _), g in zip(tabs, h2d_chunk)) / 1e9
+        h2d_chunk.append(nb / (h0.elapsed_time(h1) / 1e3) / 1e9)
+    h2d_s = sum((codes_h[i].numel() if two else b1 - b0) / (g * 1e9)
+                for i, ((b0, b1, _, _), g) in enumerate(zip(tabs, h2d_chunk)))
+    h2d_gbs = link_bytes / h2d_s / 1e9
     copy(0)
     sid0 = load(0)
     tune = None if args.no_tune else ctx.ah_tune_scan(sid0, pids, 0, st[0])
@@ -795,9 +817,20 @@ def bench_batched(args):
     plain_out = HostOut(torch, ah)
     hs = torch.cuda.current_stream()
 
+    plain_codes = {}
+    if two:  # each sampled genome alone as 2-bit codes in pinned host memory
+        for g in np.sort(np.random.default_rng(0).choice(n_g, size=min(n_g, args.plain_genomes), replace=False)):
+            b0, b1, _, _ = sub_tables(coll, int(g), int(g) + 1)
+            cd, gp = ah.encode_2bit(host[b0:b1].numpy())
+            plain_codes[int(g)] = (torch.from_numpy(cd).pin_memory(), gp)
+
     def plain(g, per_pair):
         b0, b1, off, gen_ = sub_tables(coll, int(g), int(g) + 1)
-        sid = ctx.ah_load_genomes(host[b0:b1], b1 - b0, off, gen_, hs)
+        if two:
+            cd, gp = plain_codes[int(g)]
+            sid = ctx.ah_load_genomes_2bit(cd, b1 - b0, gp, off, gen_, hs)
+        else:
+            sid = ctx.ah_load_genomes(host[b0:b1], b1 - b0, off, gen_, hs)
         for ids in ([[p] for p in pids] if per_pair else [pids]):
             plain_out.run(ctx, sid, ids, hs)
         ctx.ah_unload_genomes(sid)
@@ -821,12 +854,14 @@ def bench_batched(args):
         "config": {"workload": f"batched-{n_g}genomes-{N / 1e9:.1f}Gbp-{len(pairs)}pairs",
                    "n_genomes": n_g, "n_bases": N, "n_contigs": len(coll.contig_genome),
                    "pairs": [(p["fwd"], p["rev"], p["k"]) for p in pairs], "chunks": len(tabs),
-                   "chunk_bases_max": cmax, "input": "pinned host memory, H2D copy of chunk i+2 overlapping "
-                   "set i's run and set i+1's packing", "outputs": "pinned host (sites, Tm, pass, amplicons, "
+                   "chunk_bases_max": cmax,
+                   "input": ("2-bit codes and no-base runs (ah_load_genomes_2bit)" if two else "ASCII") +
+                            " in pinned host memory, H2D copy of chunk i+2 overlapping set i's run and set i+1's "
+                            "packing; the plain forms load the same format", "outputs": "pinned host (sites, Tm, pass, amplicons, "
                    "sequences)", "scan_tuning": tune, "layout_s": t_layout},
         "results_per_pass": totals, "gpu_launches_per_pass": launches / max(1, args.steps),
         "h2d_gbs": h2d_gbs, "h2d_gbs_per_chunk": [round(g, 1) for g in h2d_chunk],
-        "h2d_bound_s_per_pass": N / h2d_gbs / 1e9,
+        "h2d_bound_s_per_pass": h2d_s, "h2d_bytes_per_pass": link_bytes,
         "plain": {"value": gbps_plain, "unit": "Gbp/s", "genomes": len(sample), "bases": int(nb),
                   "form": "one genome per ah_load_genomes (host input), one ah_run per pair (host outputs)",
                   "s": t_plain},

@@ -1718,8 +1718,11 @@ static ah_status load_impl(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, cons
             launch_pack(dst, 0, n_bases, n_bases, gs->planes, 0, gs->n_tiles, c->d_err, st);
         } else if (gs->n_tiles && two) {
             HostSpan hs_pack(c, "host.load.pack");
-            // the no-base runs on the device (small; the host array may go when the call returns)
-            uint64_t *gaps_d = (uint64_t *)scratch(c, "load_gaps", std::max<uint64_t>(two->n_gaps, 1) * 16);
+            // the no-base runs on the device, owned by the set (another load in flight on
+            // another stream must not overwrite them while this packing reads them)
+            gs->gaps_bytes = std::max<uint64_t>(two->n_gaps, 1) * 16;
+            gs->gaps = (uint64_t *)dev_alloc(c, gs->gaps_bytes);
+            uint64_t *gaps_d = gs->gaps;
             if (two->n_gaps)
                 AH_CUDA(cudaMemcpyAsync(gaps_d, two->gaps, two->n_gaps * 16, cudaMemcpyHostToDevice, st));
             if (dev_seq) {
@@ -1917,6 +1920,7 @@ ah_status ah_unload_genomes(ah_ctx *c, uint32_t set_id)
         const int e = c->flags_dirty ? read_flags(c, c->stream) : 0;
         dev_free(c, gs.planes, gs.n_tiles * kTileBytes);
         dev_free(c, gs.contig_off, 0); // the block of the three tables
+        dev_free(c, gs.gaps, gs.gaps_bytes);
         if (gs.ready)
             c->set_events.push_back(gs.ready);
         c->sets.erase(set_id);

@@ -47,6 +47,10 @@ struct GenomeSet {
     // device, n_tiles + 1: bases from position t * kTileBases to the end of
     // contig tile_contig[t] (0 past the last base, capped at 2^32 - 1)
     uint32_t *tile_room = nullptr;
+    // device, the no-base runs of a 2-bit load (read by its packing; the set owns
+    // them so that loads in flight on other streams never share them)
+    uint64_t *gaps = nullptr;
+    size_t gaps_bytes = 0;
     size_t bytes = 0;
     // recorded after the work that fills the set (the packing); every call that
     // reads the set waits for it on its own stream, and unloading waits for it

@@ -310,8 +310,10 @@ __global__ void __launch_bounds__(kPackThreads) pack2_kernel(const uint8_t *__re
                 }
             };
             for (uint64_t g = first_gap; g < n_gaps && gaps[2 * g] < pe; ++g) {
-                const uint64_t a = gaps[2 * g] > p0 ? gaps[2 * g] - p0 : 0;
                 const uint64_t e = gaps[2 * g] + gaps[2 * g + 1];
+                if (e <= p0) // (only out-of-order runs end before the tile: never index with them)
+                    continue;
+                const uint64_t a = gaps[2 * g] > p0 ? gaps[2 * g] - p0 : 0;
                 const uint64_t b = (e < pe ? e : pe) - p0;
                 if (b > a)
                     mark(a, b);

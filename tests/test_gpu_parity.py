@@ -256,6 +256,39 @@ def test_2bit_load_scan_parity(ctx):
     assert_parity(g, oracle_run(w), min_sites=50)
 
 
+def test_2bit_loads_in_flight_on_two_streams(ctx):
+    """Two 2-bit loads queued back to back on two streams, without waiting
+    (the batched form's pattern): each set keeps its own no-base runs, so both
+    give their letters."""
+    import torch
+    rng = np.random.default_rng(31)
+    seqs, srcs, gapss, offs = [], [], [], []
+    for j, n in enumerate((9_000_017, 7_500_001)):
+        seq = np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, n)].copy()
+        for s0 in rng.integers(0, n - 200, 4000 + 3000 * j):
+            seq[s0:s0 + int(rng.integers(1, 60))] = ord("N")
+        codes, gaps = ah.encode_2bit(seq)
+        seqs.append(seq)
+        srcs.append(torch.from_numpy(codes).cuda())
+        gapss.append(gaps)
+        offs.append(np.array([0, n // 3, n], dtype=np.uint64))
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    sids = [ctx.ah_load_genomes_2bit(srcs[j], len(seqs[j]), gapss[j], offs[j], np.zeros(2, np.uint32), streams[j])
+            for j in range(2)]
+    try:
+        for j in range(2):
+            amps = np.zeros(2, dtype=ah.AMPLICON_DTYPE)
+            amps["contig"] = [0, 1]
+            amps["end"] = np.diff(offs[j].astype(np.int64))
+            got, _ = ctx.fetch(sids[j], amps)
+            want = np.where(seqs[j] == ord("N"), ord("N"), seqs[j]).astype(np.uint8).tobytes()
+            assert got == want, j
+    finally:
+        for sid in sids:
+            ctx.ah_unload_genomes(sid)
+
+
 def test_2bit_load_rejects_bad_gaps(ctx):
     codes = np.zeros(25, np.uint8)
     off, gen = np.array([0, 100], np.uint64), np.zeros(1, np.uint32)
