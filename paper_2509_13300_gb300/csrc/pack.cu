@@ -6,20 +6,28 @@
 // async copies (TMA) bring them into shared memory, two tiles staged per CTA
 // so the next copy overlaps the current packing.  Word j of plane x takes bit
 // b from row b, column j, so thread i builds the four words of columns
-// 4i .. 4i+3 alone, with no cross-lane traffic:
-//   - per block of 4 rows it reads 4 row words (4 columns each) and
-//     transposes the 4x4 bytes with PRMT, giving one register per column;
+// 4i .. 4i+3 alone, with no cross-lane traffic.  Per block of 4 rows it reads
+// 4 row words (4 columns each) and transposes the 4x4 bytes with PRMT, giving
+// one register per column (4 rows), and then:
 //   - a letter's base is read from bits 1 and 2 of its byte (A 00, C 01,
-//     T 10, G 11); those bits of 4 bytes are gathered into 4 bits by one
-//     multiply whose partial products never overlap (no carries);
-//   - a byte is a base only if it is exactly A/C/G/T in either case: its low
-//     nibble (1, 3, 7, 4) indexes an 8-entry PRMT table holding that letter
-//     (other entries 0xFF; nibbles >= 8 select a sign byte, 0x00 or 0xFF),
-//     and an exact per-byte zero test compares the two.
+//     T 10, G 11).  Bit 2 is copied up to bit 5, and one multiply by a
+//     constant whose partial products never share a bit (so no carries)
+//     moves bit 1 of the 4 bytes to bits 0..3 and bit 5 to bits 4..7 of the
+//     product's high word; PRMT drops that byte into the column's even- or
+//     odd-block word, and two masks per plane turn these into the column's
+//     32-bit bit-1 and bit-2 words;
+//   - a byte is a base only if it is exactly A/C/G/T in either case.  The
+//     fast test: the byte must equal, up to case, the letter its low nibble
+//     names (1 A, 3 C, 4 T, 7 G; an 8-entry PRMT table).  The low nibbles of
+//     two rows interleave into a selector whose byte order is that of the
+//     transpose's first stage, so one PRMT and one XOR per 4 bytes give 0 or
+//     0x20 for every base byte; the thread ORs them over its 128 bytes.  Only
+//     when some byte fails does the thread run the exact per-byte test for its
+//     columns (a per-byte zero test and a gather by multiply).
 // Plane words then follow from (h, l, valid) with one LOP3 each.  The work is
-// split between the logic and the multiply pipes (right shifts and nibble
-// placement are multiplies by run-time powers of two) so that the kernel is
-// bound by HBM: 1 byte read and 0.516 bytes written per base.
+// split between the logic and the multiply pipes (shifts by constants are
+// multiplies by run-time powers of two) so that the kernel is bound by HBM:
+// 1 byte read and 0.516 bytes written per base.
 #include <algorithm>
 #include <cstdlib>
 
@@ -32,6 +40,13 @@ constexpr int kRowWords = kTileW / 4; // u32 words per ASCII row in shared memor
 constexpr int kPackThreads = kTileW / 4;
 constexpr int kRows = 33;                    // 32 rows + the next tile's head
 constexpr int kBufWords = kRows * kRowWords; // one staged tile
+
+// PRMT table: byte n is the (upper-case) letter whose low nibble is n, 0xFF
+// where no letter has that nibble
+constexpr uint32_t kLetterLo = 0x43FF41FFu, kLetterHi = 0x47FFFF54u;
+// bit 8k+1 -> bit 32+k and bit 8k+5 -> bit 36+k of the 64-bit product: byte k
+// moves by 31 - 7k; every partial product lands on its own bit
+constexpr uint32_t kGatherLH = (1u << 31) | (1u << 24) | (1u << 17) | (1u << 10);
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -72,6 +87,20 @@ __device__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     return true;
 }
 
+// Exact validity of 4 bytes (one column, 4 rows): bit k set iff byte k is
+// exactly one of A C G T in either case.
+__device__ __forceinline__ uint32_t valid4(uint32_t raw, uint32_t sixteen, uint32_t top4)
+{
+    const uint32_t n = raw & 0x0F0F0F0Fu;
+    const uint32_t x = n + __umulhi(n, top4);                       // nibbles n0 n1 | n2 n3 (n | n >> 4)
+    const uint32_t sel = __byte_perm(x, 0, 0x4420);                 // 4 selector nibbles
+    const uint32_t expect = __byte_perm(kLetterLo, kLetterHi, sel); // letter the nibble names
+    const uint32_t z = (raw & 0xDFDFDFDFu) ^ expect;                // upper-cased letter vs expected
+    const uint32_t s = (z & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;             // byte MSB: low 7 bits non-zero
+    const uint32_t valid = ~(s | z) & 0x80808080u;                  // byte MSB: z byte == 0
+    return __umulhi(valid * 0x00204081u, sixteen);                  // byte k MSB -> bit k
+}
+
 // Classify 4 bytes (one column, 4 rows) and add their bits at the nibble
 // given by pw (a run-time power of two) of the column's L (bit 1 of the
 // letter), H (bit 2) and V (exactly one of A C G T, either case) words.
@@ -80,17 +109,28 @@ __device__ __forceinline__ void classify4(uint32_t raw, uint32_t pw, uint32_t si
 {
     const uint32_t l4 = __umulhi((raw & 0x02020202u) * 0x08102040u, sixteen); // byte k bit 1 -> bit k
     const uint32_t h4 = __umulhi((raw & 0x04040404u) * 0x04081020u, sixteen); // byte k bit 2 -> bit k
-    const uint32_t n = raw & 0x0F0F0F0Fu;
-    const uint32_t x = n + __umulhi(n, top4);                           // nibbles n0 n1 | n2 n3 (n | n >> 4)
-    const uint32_t sel = __byte_perm(x, 0, 0x4420);                     // 4 selector nibbles
-    const uint32_t expect = __byte_perm(0x43FF41FFu, 0x47FFFF54u, sel); // letter the nibble names
-    const uint32_t z = (raw & 0xDFDFDFDFu) ^ expect;                    // upper-cased letter vs expected
-    const uint32_t s = (z & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;                 // byte MSB: low 7 bits non-zero
-    const uint32_t valid = ~(s | z) & 0x80808080u;                      // byte MSB: z byte == 0
-    const uint32_t v4 = __umulhi(valid * 0x00204081u, sixteen);         // byte k MSB -> bit k
     L = l4 * pw + L; // the nibbles are disjoint: add = or
     H = h4 * pw + H;
-    V = v4 * pw + V;
+    V = valid4(raw, sixteen, top4) * pw + V;
+}
+
+// 4x4 byte transpose of rows r .. r+3 (4 columns each): col[k] = byte k of
+// each row; t[] = the first stage, (a0 b0 a1 b1), (a2 b2 a3 b3), (c0 d0 c1 d1),
+// (c2 d2 c3 d3).
+__device__ __forceinline__ void load_block(const uint32_t *__restrict__ rows, int r, int ci, uint32_t (&row)[4],
+                                           uint32_t (&t)[4], uint32_t (&col)[4])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        row[q] = rows[(r + q) * kRowWords + ci];
+    t[0] = __byte_perm(row[0], row[1], 0x5140);
+    t[1] = __byte_perm(row[0], row[1], 0x7362);
+    t[2] = __byte_perm(row[2], row[3], 0x5140);
+    t[3] = __byte_perm(row[2], row[3], 0x7362);
+    col[0] = __byte_perm(t[0], t[2], 0x5410);
+    col[1] = __byte_perm(t[0], t[2], 0x7632);
+    col[2] = __byte_perm(t[1], t[3], 0x5410);
+    col[3] = __byte_perm(t[1], t[3], 0x7632);
 }
 
 // Build plane words for columns 4*ci .. 4*ci+3 from rows 0 .. 31 of the
@@ -102,34 +142,57 @@ __device__ __forceinline__ void classify4(uint32_t raw, uint32_t pw, uint32_t si
 __device__ __forceinline__ void pack_columns(const uint32_t *__restrict__ rows, int ci, uint32_t *__restrict__ dst,
                                              uint32_t one)
 {
-    const int r0 = 0, j0 = 4 * ci;
-    const uint32_t sixteen = one << 4, top4 = one << 28;
-    uint32_t L[4] = {0, 0, 0, 0}, H[4] = {0, 0, 0, 0}, V[4] = {0, 0, 0, 0};
+    const int j0 = 4 * ci;
+    const uint32_t eight = one << 3, sixteen = one << 4, top4 = one << 28;
+    // per column: byte m of ev / od = bits 1 (low nibble) and 2 (high nibble)
+    // of rows 8m .. 8m+3 / 8m+4 .. 8m+7
+    uint32_t ev[4] = {0, 0, 0, 0}, od[4] = {0, 0, 0, 0};
+    uint32_t bad = 0; // OR of (byte ^ letter its nibble names): only 0x20 bits if all are bases
 #pragma unroll
     for (int rb = 0; rb < 8; ++rb) {
-        const int r = r0 + 4 * rb;
-        const uint32_t a = rows[(r + 0) * kRowWords + ci];
-        const uint32_t b = rows[(r + 1) * kRowWords + ci];
-        const uint32_t c = rows[(r + 2) * kRowWords + ci];
-        const uint32_t d = rows[(r + 3) * kRowWords + ci];
-        // 4x4 byte transpose: col k = bytes k of a, b, c, d
-        const uint32_t t0 = __byte_perm(a, b, 0x5140), t1 = __byte_perm(a, b, 0x7362);
-        const uint32_t t2 = __byte_perm(c, d, 0x5140), t3 = __byte_perm(c, d, 0x7362);
-        const uint32_t col[4] = {__byte_perm(t0, t2, 0x5410), __byte_perm(t0, t2, 0x7632), __byte_perm(t1, t3, 0x5410),
-                                 __byte_perm(t1, t3, 0x7632)};
-        const uint32_t pw = one << (4 * rb);
+        uint32_t row[4], t[4], col[4];
+        load_block(rows, 4 * rb, ci, row, t, col);
+        const uint32_t s01 = (row[0] & 0x0F0F0F0Fu) | ((row[1] * sixteen) & 0xF0F0F0F0u);
+        const uint32_t s23 = (row[2] & 0x0F0F0F0Fu) | ((row[3] * sixteen) & 0xF0F0F0F0u);
+        bad |= (t[0] ^ __byte_perm(kLetterLo, kLetterHi, s01)) | (t[1] ^ __byte_perm(kLetterLo, kLetterHi, s01 >> 16));
+        bad |= (t[2] ^ __byte_perm(kLetterLo, kLetterHi, s23)) | (t[3] ^ __byte_perm(kLetterLo, kLetterHi, s23 >> 16));
+        // byte 0 of the gathered word goes to byte rb / 2
+        const uint32_t put = rb / 2 == 0 ? 0x3214u : rb / 2 == 1 ? 0x3240u : rb / 2 == 2 ? 0x3410u : 0x4210u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t w = (col[k] & 0x02020202u) | ((col[k] * eight) & 0x20202020u);
+            const uint32_t g = __umulhi(w, kGatherLH); // bits 0..3: bit 1 of rows 4rb.., bits 4..7: bit 2
+            if (rb & 1)
+                od[k] = __byte_perm(od[k], g, put);
+            else
+                ev[k] = __byte_perm(ev[k], g, put);
+        }
+    }
+    uint32_t V[4] = {~0u, ~0u, ~0u, ~0u};
+    if (bad & 0xDFDFDFDFu) { // some byte is not a base: exact per-byte test for these columns
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            classify4(col[k], pw, sixteen, top4, L[k], H[k], V[k]);
+            V[k] = 0;
+#pragma unroll
+        for (int rb = 0; rb < 8; ++rb) {
+            uint32_t row[4], t[4], col[4];
+            load_block(rows, 4 * rb, ci, row, t, col);
+            const uint32_t pw = one << (4 * rb);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                V[k] = valid4(col[k], sixteen, top4) * pw + V[k];
+        }
     }
     uint4 pa, pc, pg, pt;
     uint32_t *A = &pa.x, *C = &pc.x, *G = &pg.x, *T = &pt.x;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        A[k] = V[k] & ~H[k] & ~L[k];
-        C[k] = V[k] & ~H[k] & L[k];
-        T[k] = V[k] & H[k] & ~L[k];
-        G[k] = V[k] & H[k] & L[k];
+        const uint32_t L = (ev[k] & 0x0F0F0F0Fu) | ((od[k] * sixteen) & 0xF0F0F0F0u);
+        const uint32_t H = (__umulhi(ev[k], top4) & 0x0F0F0F0Fu) | (od[k] & 0xF0F0F0F0u);
+        A[k] = V[k] & ~H & ~L;
+        C[k] = V[k] & ~H & L;
+        T[k] = V[k] & H & ~L;
+        G[k] = V[k] & H & L;
     }
     *reinterpret_cast<uint4 *>(dst + 0 * kTileWX + j0) = pa;
     *reinterpret_cast<uint4 *>(dst + 1 * kTileWX + j0) = pc;

@@ -517,6 +517,27 @@ def test_pack_classifies_every_byte_value(ctx):
     assert np.array_equal(goff, woff) and got == want
 
 
+def test_pack_single_non_bases_in_base_tiles(ctx):
+    """Tiles of bases (either case) with single non-base bytes scattered through
+    them, at word, row and tile edges: the packer's fast all-bases test must
+    send every such column to the exact per-byte test."""
+    rng = np.random.default_rng(11)
+    n = 7 * 32768 + 1234
+    seq = rng.choice(np.frombuffer(b"ACGTacgt", np.uint8), n)
+    others = np.array([v for v in range(256) if v not in b"ACGTacgt"], np.uint8)
+    edges = [0, 3, 4, 1023, 1024, 31 * 1024, 32767, 32768, 32768 + 31 * 1024 + 1023, 3 * 32768 + 5 * 1024 + 511]
+    pos = np.unique(np.concatenate([edges, rng.integers(0, n, 60)]))
+    seq[pos] = rng.choice(others, len(pos))
+    off = np.array([0, n], np.uint64)
+    sid = ctx.ah_load_genomes(seq, n, off, np.array([0], np.uint32))
+    amps = np.zeros(1, dtype=ah.AMPLICON_DTYPE)
+    amps["end"] = [n]
+    got, goff = ctx.fetch(sid, amps)
+    want, woff = oracle.fetch(seq, off, amps)
+    ctx.ah_unload_genomes(sid)
+    assert np.array_equal(goff, woff) and got == want
+
+
 @pytest.mark.parametrize("tm_filter", [True, False])
 def test_run_equals_separate_calls_and_oracle(ctx, tm_filter):
     """ah_run (the fused path) gives the records of ah_scan/ah_tm/ah_pair/ah_fetch
