@@ -29,6 +29,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cstdlib>
+
 #include "ah_internal.h"
 
 namespace ah {
@@ -744,10 +746,46 @@ __global__ void __launch_bounds__(kFastThreads) tm_fast_kernel(const ah_site *__
         const int nk = sp.nkey[pr];
         const int b0 = bt(0), bL = bt(L - 1);
         const float cst = sp.cst[pr];
-        float lam = 0.f;
+        // What does not depend on lam, once per site.  The fixed stretches
+        // between keys that are not adjacent are the same for every oligo: they
+        // add one constant to every path, move no argmin, and join H and S at
+        // the end.  The start is an achieved ratio, that of one oligo: at each
+        // position the base pairing with the template where the mask allows it,
+        // else the mask's first base.  Each pass then either confirms the ratio
+        // (no oligo beats it by more than 1e-4 K) or moves to a better one.
+        float SH = 0.f, SE = 0.f;
+        for (int si = 0; si + 1 < nk; ++si) {
+            const int k0 = key[si], k1 = key[si + 1];
+            for (int q = k0 + 2; q < k1; ++q) {
+                const float2 v2 =
+                    sp.st[(bt(q - 1) * 4 + bt(q)) * 16 + (__ffs(mask[q - 1]) - 1) * 4 + (__ffs(mask[q]) - 1)];
+                SH += v2.x;
+                SE += v2.y;
+            }
+        }
+        float lam;
+        {
+            auto pick = [&](int q) {
+                const int pairing = 3 - bt(q);
+                return ((mask[q] >> pairing) & 1) ? pairing : __ffs(mask[q]) - 1;
+            };
+            int o0 = pick(0);
+            float2 t = sp.tm[o0 * 4 + b0];
+            float H0 = t.x, S0 = t.y;
+            for (int q = 1; q < L; ++q) {
+                const int o1 = pick(q);
+                const float2 v2 = sp.st[(bt(q - 1) * 4 + bt(q)) * 16 + o0 * 4 + o1];
+                H0 += v2.x;
+                S0 += v2.y;
+                o0 = o1;
+            }
+            t = sp.tm[o0 * 4 + bL];
+            lam = (H0 + t.x) / (S0 + t.y + cst);
+        }
         for (int it = 0; it < 64; ++it) {
             // forward pass at lam: per state y (oligo base at the current key) the
             // cheapest path cost 1000 dH - lam dS and that path's 1000 dH and dS
+            // (fixed stretches left out)
             float c[4], h[4], e[4];
 #pragma unroll
             for (int y = 0; y < 4; ++y) {
@@ -782,16 +820,9 @@ __global__ void __launch_bounds__(kFastThreads) tm_fast_kernel(const ah_site *__
                         ne[y] = be;
                     }
                 } else {
-                    // fixed bases next to the keys, the stretch between them, then one
-                    // argmin over the bases at k0 (the stack out of k0), shared by every y
+                    // the stack out of k0 into the fixed base after it: one argmin over
+                    // the bases at k0, shared by every y; then the stack into k1
                     const int fa = __ffs(mask[k0 + 1]) - 1, fb = __ffs(mask[k1 - 1]) - 1;
-                    float sh = 0.f, se = 0.f;
-                    for (int q = k0 + 2; q < k1; ++q) {
-                        const float2 v2 = sp.st[(bt(q - 1) * 4 + bt(q)) * 16 + (__ffs(mask[q - 1]) - 1) * 4 +
-                                                (__ffs(mask[q]) - 1)];
-                        sh += v2.x;
-                        se += v2.y;
-                    }
                     const float2 *EA = &sp.st[(bt(k0) * 4 + bt(k0 + 1)) * 16 + fa]; // EA[o0 * 4]
                     float best = INF, bh = 0.f, be = 0.f;
 #pragma unroll
@@ -808,11 +839,10 @@ __global__ void __launch_bounds__(kFastThreads) tm_fast_kernel(const ah_site *__
 #pragma unroll
                     for (int y = 0; y < 4; ++y) {
                         const float2 v2 = EB[y];
-                        const float qh = sh + v2.x, qe = se + v2.y;
                         const bool ok = ((m1 >> y) & 1) && best < INF;
-                        nc[y] = ok ? best + fmaf(-lam, qe, qh) : INF;
-                        nh[y] = bh + qh;
-                        ne[y] = be + qe;
+                        nc[y] = ok ? best + fmaf(-lam, v2.y, v2.x) : INF;
+                        nh[y] = bh + v2.x;
+                        ne[y] = be + v2.y;
                     }
                 }
 #pragma unroll
@@ -834,9 +864,9 @@ __global__ void __launch_bounds__(kFastThreads) tm_fast_kernel(const ah_site *__
                     S = e[y] + t.y;
                 }
             }
-            const float r = H / (S + cst);
+            const float r = (H + SH) / (S + SE + cst);
             // stop when the ratio no longer improves by more than 1e-4 K (as tm_kernel)
-            if (it > 0 && !(r > lam + 1e-4f))
+            if (!(r > lam + 1e-4f))
                 break;
             lam = r;
         }
@@ -1044,6 +1074,10 @@ void launch_tm(const ah_site *sites, uint64_t n, const uint64_t *n_dev, const Pa
         AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tm_bps, tm_kernel, 32 * kTmWarps, most));
         fast_bps = std::max(1, fast_bps);
         tm_bps = std::max(1, tm_bps);
+        // AH_TM_FAST_BLOCKS=n: at most n blocks of the thread-per-site kernel per SM (profiling aid)
+        if (const char *e = getenv("AH_TM_FAST_BLOCKS"))
+            if (atoi(e) > 0)
+                fast_bps = std::min(fast_bps, atoi(e));
         cached_dev = dev;
     }
     // queue length, finished blocks, deferred sites
