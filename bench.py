@@ -276,7 +276,8 @@ def main():
     ap.add_argument("--mem-budget", type=int, default=4 << 30, help="served: bytes one batch may plan for")
     ap.add_argument("--large-chunk", type=int, default=16_000_000_000, help="large: bases per chunk (whole genomes)")
     ap.add_argument("--check-genomes", type=int, default=6, help="large: sampled genomes checked by the oracle here")
-    ap.add_argument("--dump-genomes", type=int, default=0, help="large: sampled genomes whose GPU results are saved")
+    ap.add_argument("--dump-genomes", type=int, default=0,
+                    help="large: GPU results of this many seeded genomes saved for --check-dump")
     ap.add_argument("--dump-path", default="large_sample.npz")
     ap.add_argument("--check-dump", default=None, help="oracle check of a large-form dump (CPU only)")
     args = ap.parse_args()
@@ -1431,12 +1432,20 @@ def bench_large_main(args):
                "sample": f"{len(sample)} of {n_g} genomes drawn with seed 7 ({nb / 1e6:.1f} Mbp), 3 pairs, "
                          f"scan+Tm+pair+fetch, {t_cpu:.1f} s",
                "parity": parity_summary(coll, got, want)}
-        if args.dump_genomes:
-            arrs = {}
-            for g in sample.tolist():
-                sg, tg, pg, ag, _, _ = got[g]
-                arrs.update({f"s{g}": sg, f"t{g}": tg, f"p{g}": pg, f"a{g}": ag})
-            np.savez_compressed(args.dump_path, sample=sample, n_genomes=n_g, **arrs)
+    if rank == 0 and world == 1 and args.dump_genomes:
+        # GPU records of a seeded sample of genomes from one pass of the timed configuration,
+        # for the oracle to check on another machine (--check-dump regenerates the genomes)
+        dump = np.sort(np.random.default_rng(7).choice(n_g, size=min(args.dump_genomes, n_g), replace=False))
+        chunk_of = np.searchsorted(np.array([b1 for _, b1, _, _ in tabs]), coll.genome_off[dump], side="right")
+        keep = {}
+        for g, ci in zip(dump.tolist(), chunk_of.tolist()):
+            keep.setdefault(ci, []).append(g)
+        got = one_pass(keep)
+        arrs = {}
+        for g in dump.tolist():
+            sg, tg, pg, ag, _, _ = got[g]
+            arrs.update({f"s{g}": sg, f"t{g}": tg, f"p{g}": pg, f"a{g}": ag})
+        np.savez_compressed(args.dump_path, sample=dump, n_genomes=n_g, **arrs)
     del seq_d
     ctx.close()
     torch.cuda.empty_cache()
@@ -1482,7 +1491,8 @@ def bench_large_main(args):
 def bench_hmm(args):
     """Profile-HMM form: a profile trained on the exact-match amplicons of an
     operon family scores every k = 2 amplicon of the collection (glocal Viterbi,
-    fp32); throughput in cell updates per second, a sample checked by the oracle."""
+    fp32, and the Forward score beside it); throughput in cell updates per
+    second, a sample checked by the oracle."""
     import torch
     from paper_2509_13300_gb300 import ah, build, synth
     build.build()
@@ -1525,6 +1535,18 @@ def bench_hmm(args):
         clk.mark(False)
     dt = ev[0].elapsed_time(ev[1]) / 1e3 / args.steps
     got = out.cpu().numpy()
+    # the Forward score (log-sum over state paths) of the same amplicons, timed the same way
+    out_f = torch.zeros(len(amps), dtype=torch.float32, device="cuda")
+    for _ in range(max(1, args.warmup)):
+        ctx.hmm_forward(sid, hid, dev_amps, n=len(amps), out=out_f, stream=stream)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        ctx.hmm_forward(sid, hid, dev_amps, n=len(amps), out=out_f, stream=stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    dt_f = ev[0].elapsed_time(ev[1]) / 1e3 / args.steps
+    got_f = out_f.cpu().numpy()
     # the oracle on a sample: its own profile from the same training sequences
     import oracle
     rng = np.random.default_rng(0)
@@ -1534,10 +1556,17 @@ def bench_hmm(args):
     t0 = time.perf_counter()
     want = np.array([oracle.hmm_viterbi(oT, oE, qs[int(qo[i]):int(qo[i + 1])].decode()) for i in range(len(sample))])
     t_cpu = time.perf_counter() - t0
+    want_f = np.array([oracle.hmm_forward(oT, oE, qs[int(qo[i]):int(qo[i + 1])].decode())
+                       for i in range(len(sample))])
     cpu_cells = float(lens[sample].sum()) * m
-    pmax = float(max(np.abs(oT[~np.isinf(oT)]).max(), np.abs(oE).max()))
-    tol = (lens[sample] + m) ** 2 * pmax * 2.0 ** -24 + 1e-3
+    # fp32 accumulation along a path of N = n + m moves, ten standard deviations of
+    # a random walk of roundings (the bound of the parity tests)
+    pmean = float(np.concatenate([np.abs(oT[~np.isinf(oT)]), np.abs(oE[1:]).ravel()]).mean())
+    N = lens[sample] + m
+    tol = 10.0 * np.sqrt(N) * 2.0 ** -24 * (np.abs(want) + N * pmean) + 1e-4
+    tol_f = 10.0 * np.sqrt(N) * (2.0 ** -24 * (np.abs(want_f) + N * pmean) + 4 * 2.0 ** -23) + 1e-4
     err = np.abs(got[sample].astype(np.float64) - want)
+    err_f = np.abs(got_f[sample].astype(np.float64) - want_f)
     clocks = clk.summary()
     fp_ops_per_cell = 19  # FADD + FMNMX per cell, counted in the kernel source (M 6, I 5, delete chain 8)
     fp32_peak = 152 * 128 * (clocks["sm_mhz"] or 2070.0) * 1e6
@@ -1555,6 +1584,11 @@ def bench_hmm(args):
                      "peak_note": "152 SMs x 128 fp32 lanes x median SM clock"},
         "oracle_check": {"amplicons": len(sample), "max_abs_err_bits": float(err.max()) if len(err) else 0.0,
                          "within_fp32_bound": bool((err <= tol).all()), "min_bound_bits": float(tol.min()) if len(tol) else 0.0},
+        "forward": {"value": cells / dt_f / 1e9, "unit": "GCUPS", "ms_per_step": dt_f * 1e3,
+                    "score": "glocal Forward (log-sum over state paths), fp32",
+                    "oracle_check": {"amplicons": len(sample),
+                                     "max_abs_err_bits": float(err_f.max()) if len(err_f) else 0.0,
+                                     "within_fp32_bound": bool((err_f <= tol_f).all())}},
         "cpu_baseline": {"value": cpu_cells / t_cpu / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
                          "sample": f"{len(sample)} amplicons, fp64 Viterbi, {t_cpu:.1f} s"},
         "clocks": clocks,

@@ -572,7 +572,7 @@ ah_status ah_serve_stop(ah_server *srv);
  * allowed moves and over A/C/G/T; insert states emit the background.  Score:
  * the glocal Viterbi log-odds score (bits, uniform background; unknown
  * letters score 0) of an amplicon's sequence as ah_fetch returns it (RF
- * reverse-complemented), fp32.
+ * reverse-complemented), fp32; ah_hmm_forward gives the Forward score.
  * ah_hmm_build: training sequences (host, concatenated; offsets host, n + 1,
  *   from 0) -> a profile id; the profile lives on the device until
  *   ah_hmm_free or ah_destroy.  Errors: AH_ERR_ARG, AH_ERR_OOM.
@@ -588,6 +588,13 @@ ah_status ah_hmm_tables(ah_ctx *ctx, uint32_t hmm_id, uint64_t *m_out, uint64_t 
                         float *e_out);
 ah_status ah_hmm_score(ah_ctx *ctx, uint32_t set_id, uint32_t hmm_id, const ah_amplicon *amplicons, uint64_t n,
                        float *score_out, void *stream);
+/* ah_hmm_forward: as ah_hmm_score, with the glocal Forward log-odds score
+ * instead of Viterbi: log2 of the sum, over every state path from B to E that
+ * emits the amplicon's sequence, of 2 to the path's score (bits, fp32; the
+ * Viterbi recurrence with the maximum of the predecessors replaced by
+ * log2(2^a + 2^b)).  Same arguments, limits and errors. */
+ah_status ah_hmm_forward(ah_ctx *ctx, uint32_t set_id, uint32_t hmm_id, const ah_amplicon *amplicons, uint64_t n,
+                         float *score_out, void *stream);
 ah_status ah_hmm_free(ah_ctx *ctx, uint32_t hmm_id);
 
 #ifdef __cplusplus

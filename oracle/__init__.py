@@ -92,6 +92,8 @@ def _load():
         lib.or_hmm_build.argtypes = [P, P, I64, P, P, P]
         lib.or_hmm_viterbi.restype = ctypes.c_double
         lib.or_hmm_viterbi.argtypes = [P, P, I64, ctypes.c_char_p, I64]
+        lib.or_hmm_forward.restype = ctypes.c_double
+        lib.or_hmm_forward.argtypes = [P, P, I64, ctypes.c_char_p, I64]
         _lib = lib
     return _lib
 
@@ -279,3 +281,11 @@ def hmm_viterbi(t: np.ndarray, e: np.ndarray, seq: str) -> float:
     t = np.ascontiguousarray(t, dtype=np.float64)
     e = np.ascontiguousarray(e, dtype=np.float64)
     return float(_load().or_hmm_viterbi(_ptr(t), _ptr(e), t.shape[0] - 1, seq.encode(), len(seq)))
+
+
+def hmm_forward(t: np.ndarray, e: np.ndarray, seq: str) -> float:
+    """Glocal Forward log-odds score (bits) of seq against the profile (t, e):
+    log2 of the sum over every state path of 2^(path score)."""
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    return float(_load().or_hmm_forward(_ptr(t), _ptr(e), t.shape[0] - 1, seq.encode(), len(seq)))

@@ -34,6 +34,11 @@
  *   against the profile -- the best path from B through the states to E,
  *   every letter emitted by an M or I state -- in bits.
  *
+ *   Score (or_hmm_forward): the glocal Forward log-odds score -- log2 of the
+ *   sum, over every such path, of 2 to the path's score -- in bits: the same
+ *   recurrence with the maximum of the three predecessors replaced by
+ *   log2(2^a + 2^b + 2^c).
+ *
  * Table layout shared with the tests (not with the library): per position
  * j = 0..m, 9 transition scores t[j][X][Y] with X, Y in (M, I, D) (Y = M
  * meaning the next move, which is E at j = m), -INFINITY where a move does
@@ -266,5 +271,57 @@ double or_hmm_viterbi(const double *t, const double *e, int64_t m, const char *x
     free(VM);
     free(VI);
     free(VD);
+    return s;
+}
+
+/* log2(2^a + 2^b + 2^c), -INFINITY when all three are -INFINITY */
+static double lse3(double a, double b, double c)
+{
+    double m = max3(a, b, c);
+    if (m == -INFINITY)
+        return -INFINITY;
+    return m + log2(exp2(a - m) + exp2(b - m) + exp2(c - m));
+}
+
+/* Glocal Forward log-odds score (bits) of x[0..n) against the profile. */
+double or_hmm_forward(const double *t, const double *e, int64_t m, const char *x, int64_t n)
+{
+    const double NEG = -INFINITY;
+    int64_t W = m + 1;
+    double *FM = malloc((size_t)(n + 1) * (size_t)W * sizeof(double));
+    double *FI = malloc((size_t)(n + 1) * (size_t)W * sizeof(double));
+    double *FD = malloc((size_t)(n + 1) * (size_t)W * sizeof(double));
+#define T(j, X, Y) t[(j) * 9 + (X) * 3 + (Y)]
+    for (int64_t i = 0; i <= n; i++) {
+        for (int64_t j = 0; j <= m; j++) {
+            double fm = NEG, fi = NEG, fd = NEG;
+            if (i == 0 && j == 0) {
+                fm = 0.0; /* B: the empty path */
+            } else {
+                if (i > 0 && j > 0) {
+                    int l = letter(x[i - 1]);
+                    double em = l < 4 ? e[j * 4 + l] : 0.0;
+                    fm = em + lse3(FM[(i - 1) * W + j - 1] + T(j - 1, ST_M, ST_M),
+                                   FI[(i - 1) * W + j - 1] + T(j - 1, ST_I, ST_M),
+                                   FD[(i - 1) * W + j - 1] + T(j - 1, ST_D, ST_M));
+                }
+                if (i > 0)
+                    fi = lse3(FM[(i - 1) * W + j] + T(j, ST_M, ST_I), FI[(i - 1) * W + j] + T(j, ST_I, ST_I),
+                              FD[(i - 1) * W + j] + T(j, ST_D, ST_I));
+                if (j > 0)
+                    fd = lse3(FM[i * W + j - 1] + T(j - 1, ST_M, ST_D), FI[i * W + j - 1] + T(j - 1, ST_I, ST_D),
+                              FD[i * W + j - 1] + T(j - 1, ST_D, ST_D));
+            }
+            FM[i * W + j] = fm;
+            FI[i * W + j] = fi;
+            FD[i * W + j] = fd;
+        }
+    }
+    double s = lse3(FM[n * W + m] + T(m, ST_M, ST_M), FI[n * W + m] + T(m, ST_I, ST_M),
+                    FD[n * W + m] + T(m, ST_D, ST_M));
+#undef T
+    free(FM);
+    free(FI);
+    free(FD);
     return s;
 }

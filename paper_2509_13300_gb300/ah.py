@@ -34,7 +34,7 @@ EXPORTS = ["ah_create", "ah_destroy", "ah_last_error", "ah_device_bytes", "ah_lo
            "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan", "ah_run", "ah_run_begin", "ah_run_end",
            "ah_load_genomes_ex", "ah_tm_sweep", "ah_amplitypes", "ah_generate_bases", "ah_serve_start",
            "ah_serve_submit", "ah_serve_wait", "ah_serve_stop", "ah_hmm_build", "ah_hmm_tables", "ah_hmm_score",
-           "ah_hmm_free"]
+           "ah_hmm_forward", "ah_hmm_free"]
 
 
 class AHError(RuntimeError):
@@ -144,6 +144,7 @@ def lib():
             "ah_hmm_build": (I32, [P, P, P, U64, ctypes.POINTER(U32)]),
             "ah_hmm_tables": (I32, [P, U32, ctypes.POINTER(U64), ctypes.POINTER(U64), P, P]),
             "ah_hmm_score": (I32, [P, U32, U32, P, U64, P, P]),
+            "ah_hmm_forward": (I32, [P, U32, U32, P, U64, P, P]),
             "ah_hmm_free": (I32, [P, U32]),
             "ah_tune_scan": (I32, [P, U32, P, U32, U64, ctypes.POINTER(TuneResult), P]),
             "ah_pair_noalloc": (I32, [P, U32, P, P, U64, P, U64, ctypes.POINTER(U64), P]),
@@ -445,17 +446,24 @@ class Context:
         self._check(self._lib.ah_hmm_tables(self.h, hmm_id, None, None, _ptr(t), _ptr(e)))
         return m.value, ref.value, t, e
 
-    def hmm_score(self, set_id: int, hmm_id: int, amplicons, n: int | None = None, out=None, stream=None):
-        """Viterbi log-odds score (bits) of each amplicon; numpy float32 unless `out` is given."""
+    def hmm_score(self, set_id: int, hmm_id: int, amplicons, n: int | None = None, out=None, stream=None,
+                  forward: bool = False):
+        """Viterbi (or, with forward=True, Forward) log-odds score (bits) of each
+        amplicon; numpy float32 unless `out` is given."""
         n = len(amplicons) if n is None else n
         res = np.zeros(n, dtype=np.float32) if out is None else out
         if not isinstance(amplicons, np.ndarray) or amplicons.flags["C_CONTIGUOUS"]:
             a = amplicons
         else:
             a = np.ascontiguousarray(amplicons)
-        self._check(self._lib.ah_hmm_score(self.h, set_id, hmm_id, _ptr(a) if n else None, n,
-                                           _ptr(res) if n else None, _stream(stream)))
+        fn = self._lib.ah_hmm_forward if forward else self._lib.ah_hmm_score
+        self._check(fn(self.h, set_id, hmm_id, _ptr(a) if n else None, n, _ptr(res) if n else None,
+                       _stream(stream)))
         return res
+
+    def hmm_forward(self, set_id: int, hmm_id: int, amplicons, n: int | None = None, out=None, stream=None):
+        """Forward log-odds score (bits) of each amplicon: log2 of the sum over state paths."""
+        return self.hmm_score(set_id, hmm_id, amplicons, n, out, stream, forward=True)
 
     def hmm_free(self, hmm_id: int):
         self._check(self._lib.ah_hmm_free(self.h, hmm_id))

@@ -54,7 +54,7 @@ def source_digest() -> str:
 # the source files that define each profiled kernel (with the internal header)
 KERNEL_SOURCES = {"ah_scan_kernel": ["scan_jit.cu"], "pack_kernel": ["pack.cu"], "tm_kernel": ["tm.cu"],
                   "tm_fast_kernel": ["tm.cu"],
-                  "rank_sort_decode_kernel": ["sites.cu"], "hmm_viterbi_kernel": ["hmm.cu"]}
+                  "rank_sort_decode_kernel": ["sites.cu"], "hmm_score_kernel": ["hmm.cu"]}
 
 
 def kernel_digest(kernel: str) -> str | None:

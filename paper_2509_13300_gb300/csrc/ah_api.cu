@@ -2778,8 +2778,11 @@ ah_status ah_hmm_tables(ah_ctx *c, uint32_t hmm_id, uint64_t *m_out, uint64_t *r
     });
 }
 
-ah_status ah_hmm_score(ah_ctx *c, uint32_t set_id, uint32_t hmm_id, const ah_amplicon *amplicons, uint64_t n,
-                       float *score_out, void *stream)
+namespace {
+
+// ah_hmm_score (Viterbi) and ah_hmm_forward (Forward): the same checks, grouping and launch
+ah_status hmm_scores(ah_ctx *c, uint32_t set_id, uint32_t hmm_id, const ah_amplicon *amplicons, uint64_t n,
+                     float *score_out, void *stream, bool forward)
 {
     if (!c)
         return AH_ERR_ARG;
@@ -2826,13 +2829,27 @@ ah_status ah_hmm_score(ah_ctx *c, uint32_t set_id, uint32_t hmm_id, const ah_amp
         float *out = out_buf(c, "hmm_out", score_out, n);
         {
             Stage sg(c, "hmm", st, 1);
-            launch_hmm_viterbi(a, d_ord, n, gs.planes, gs.contig_off, gs.n_contigs, p.d_t, p.d_e, p.m, (int)max_len,
-                               out, c->d_err, c->sms, st);
+            launch_hmm_score(a, d_ord, n, gs.planes, gs.contig_off, gs.n_contigs, p.d_t, p.d_e, p.m, (int)max_len,
+                             forward, out, c->d_err, c->sms, st);
         }
         check_flags(c, st);
         out_finish(score_out, out, n, st);
         AH_CUDA(cudaStreamSynchronize(st));
     });
+}
+
+} // namespace
+
+ah_status ah_hmm_score(ah_ctx *c, uint32_t set_id, uint32_t hmm_id, const ah_amplicon *amplicons, uint64_t n,
+                       float *score_out, void *stream)
+{
+    return hmm_scores(c, set_id, hmm_id, amplicons, n, score_out, stream, false);
+}
+
+ah_status ah_hmm_forward(ah_ctx *c, uint32_t set_id, uint32_t hmm_id, const ah_amplicon *amplicons, uint64_t n,
+                         float *score_out, void *stream)
+{
+    return hmm_scores(c, set_id, hmm_id, amplicons, n, score_out, stream, true);
 }
 
 // Test aid (not in the public header).  on != 0: in later scans the first

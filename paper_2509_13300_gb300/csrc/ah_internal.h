@@ -96,10 +96,11 @@ struct HmmProfile {
     float *d_t = nullptr, *d_e = nullptr;
 };
 void build_profile(const char *seqs, const uint64_t *off, uint64_t n, HmmProfile &p);
-// order: n indices into amps, amplicons of similar length next to each other
-void launch_hmm_viterbi(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
-                        const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m,
-                        int max_len, float *score_out, int *err, int sms, cudaStream_t s);
+// order: n indices into amps, amplicons of similar length next to each other;
+// forward: the Forward (log-sum over paths) score instead of Viterbi
+void launch_hmm_score(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
+                      const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m,
+                      int max_len, bool forward, float *score_out, int *err, int sms, cudaStream_t s);
 
 // Tunables of the generated scan kernel (autotuned per pattern set).
 struct ScanTuning {

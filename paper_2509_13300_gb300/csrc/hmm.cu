@@ -16,14 +16,17 @@
 // bits against the uniform background: log2(p / (1/4)) for match emissions
 // (0 for an unknown letter), 0 for insert emissions, log2 p for moves.
 //
-// Score (hmm_viterbi_kernel): the glocal Viterbi log-odds score of each
-// amplicon's sequence (as ah_fetch returns it) against the profile, fp32.
+// Scores (hmm_score_kernel): the glocal Viterbi log-odds score of each
+// amplicon's sequence (as ah_fetch returns it) against the profile, fp32, or
+// the glocal Forward score: the same recurrence with the maximum of the
+// predecessors replaced by log2(2^a + 2^b) (the log-sum semiring).
 // A block scores a group of amplicons of similar length in lockstep, rows =
 // sequence letters: each thread owns K consecutive profile columns with their
 // 13 scores in registers; M and I of a row depend only on the previous row
 // (the left neighbour's values come by shuffle, or through shared memory
 // across warps); the delete chain D_j = max(E_j, D_{j-1} + t_DD) is a
-// block-wide scan in the (max, +) semiring over (t_DD, E_j) pairs.
+// block-wide scan in the (max, +) semiring over (t_DD, E_j) pairs (for the
+// Forward score, in (log-sum, +)).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -165,6 +168,21 @@ namespace {
 constexpr int kHmmThreads = 512;
 constexpr float kNeg = -INFINITY;
 
+// The semiring's "sum" of two log2 scores: Viterbi takes the larger, Forward
+// log2(2^a + 2^b) (exp2f and the __log2f intrinsic of CUDA's math library).
+struct MaxSum {
+    __device__ static __forceinline__ float add(float a, float b) { return fmaxf(a, b); }
+};
+struct LogSum {
+    __device__ static __forceinline__ float add(float a, float b)
+    {
+        const float hi = fmaxf(a, b), lo = fminf(a, b);
+        if (lo == kNeg) // also both -inf
+            return hi;
+        return hi + __log2f(1.0f + exp2f(lo - hi)); // 1 + 2^d in [1, 2]: absolute error ~2^-22
+    }
+};
+
 // Letter codes of amplicon `am` (as fetched: RF reverse-complemented) into seq.
 __device__ void decode_letters(const ah_amplicon &am, const uint32_t *__restrict__ planes,
                                const uint64_t *__restrict__ contig_off, uint8_t *seq, int len)
@@ -190,8 +208,8 @@ __device__ void decode_letters(const ah_amplicon &am, const uint32_t *__restrict
 // A amplicons per block, in lockstep over rows (the host groups amplicons of
 // similar length): the barriers of a row serve A rows of work.  The delete
 // chain's (max, +) pairs share their t_DD part across the A amplicons.
-template <int K, int A, int NT>
-__global__ void __launch_bounds__(NT) hmm_viterbi_kernel(const ah_amplicon *__restrict__ amps,
+template <class Op, int K, int A, int NT>
+__global__ void __launch_bounds__(NT) hmm_score_kernel(const ah_amplicon *__restrict__ amps,
                                                                   const uint32_t *__restrict__ order, uint64_t n_amps,
                                                                   const uint32_t *__restrict__ planes,
                                                                   const uint64_t *__restrict__ contig_off,
@@ -291,8 +309,8 @@ __global__ void __launch_bounds__(NT) hmm_viterbi_kernel(const ah_amplicon *__re
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     const float pm = k ? cM[s][k - 1] : lM[s], pi = k ? cI[s][k - 1] : lI[s];
-                    eb[s][k] = fmaxf(pm + toD[k][kM], pi + toD[k][kI]);
-                    acc = fmaxf(eb[s][k], acc + toD[k][kD]);
+                    eb[s][k] = Op::add(pm + toD[k][kM], pi + toD[k][kI]);
+                    acc = Op::add(eb[s][k], acc + toD[k][kD]);
                 }
                 agg_b[s] = acc;
             }
@@ -308,7 +326,7 @@ __global__ void __launch_bounds__(NT) hmm_viterbi_kernel(const ah_amplicon *__re
                 for (int s = 0; s < A; ++s) {
                     const float ob = __shfl_up_sync(0xffffffffu, inc_b[s], d);
                     if (lane >= d)
-                        inc_b[s] = fmaxf(inc_b[s], ob + inc_a);
+                        inc_b[s] = Op::add(inc_b[s], ob + inc_a);
                 }
                 if (lane >= d)
                     inc_a = oa + inc_a;
@@ -332,7 +350,7 @@ __global__ void __launch_bounds__(NT) hmm_viterbi_kernel(const ah_amplicon *__re
                     for (int s = 0; s < A; ++s) {
                         const float ob = __shfl_up_sync(0xffffffffu, wb[s], d);
                         if (lane >= d)
-                            wb[s] = fmaxf(wb[s], ob + wa);
+                            wb[s] = Op::add(wb[s], ob + wa);
                     }
                     if (lane >= d)
                         wa = oa + wa;
@@ -357,10 +375,10 @@ __global__ void __launch_bounds__(NT) hmm_viterbi_kernel(const ah_amplicon *__re
                 if (lane == 0)
                     xb = kNeg;
                 const float lane_a = lane ? xa : 0.0f;
-                float d = fmaxf(xb, wpre_b[s][warp] + lane_a); // D at column c0 - 1
+                float d = Op::add(xb, wpre_b[s][warp] + lane_a); // D at column c0 - 1
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
-                    d = fmaxf(eb[s][k], d + toD[k][kD]);
+                    d = Op::add(eb[s][k], d + toD[k][kD]);
                     cD[s][k] = d;
                 }
             }
@@ -373,7 +391,7 @@ __global__ void __launch_bounds__(NT) hmm_viterbi_kernel(const ah_amplicon *__re
                     for (int k = 0; k < K; ++k)
                         if (c0 + k == m)
                             score_out[idx[s]] =
-                                fmaxf(fmaxf(pM[s][k] + t[m * 9 + kM * 3], pI[s][k] + t[m * 9 + kI * 3]),
+                                Op::add(Op::add(pM[s][k] + t[m * 9 + kM * 3], pI[s][k] + t[m * 9 + kI * 3]),
                                       pD[s][k] + t[m * 9 + kD * 3]);
         };
         __syncthreads(); // the letters are decoded
@@ -410,8 +428,8 @@ __global__ void __launch_bounds__(NT) hmm_viterbi_kernel(const ah_amplicon *__re
                                 qd = k ? pD[s][k - 1] : lD[s];
                     // (a select, not an indexed load: the emission scores stay in registers)
                     const float ex = x == 0 ? em[k][0] : x == 1 ? em[k][1] : x == 2 ? em[k][2] : x == 3 ? em[k][3] : 0.0f;
-                    cM[s][k] = ex + fmaxf(fmaxf(qm + toM[k][kM], qi + toM[k][kI]), qd + toM[k][kD]);
-                    cI[s][k] = fmaxf(fmaxf(pM[s][k] + toI[k][kM], pI[s][k] + toI[k][kI]), pD[s][k] + toI[k][kD]);
+                    cM[s][k] = ex + Op::add(Op::add(qm + toM[k][kM], qi + toM[k][kI]), qd + toM[k][kD]);
+                    cI[s][k] = Op::add(Op::add(pM[s][k] + toI[k][kM], pI[s][k] + toI[k][kI]), pD[s][k] + toI[k][kD]);
                 }
             }
             delete_chain(cM, cI, cD);
@@ -429,7 +447,7 @@ __global__ void __launch_bounds__(NT) hmm_viterbi_kernel(const ah_amplicon *__re
 }
 
 // NT: the most threads a block may have (the register budget per thread follows from it)
-template <int K, int A, int NT>
+template <class Op, int K, int A, int NT>
 bool launch_k(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
               const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m, int max_len,
               float *out, int *err, int sms, cudaStream_t s)
@@ -438,13 +456,13 @@ bool launch_k(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const 
     if (threads > NT)
         return false; // the profile needs more columns than this variant holds
     const size_t smem = (size_t)A * (size_t)max_len;
-    AH_CUDA(cudaFuncSetAttribute(hmm_viterbi_kernel<K, A, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    AH_CUDA(cudaFuncSetAttribute(hmm_score_kernel<Op, K, A, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)std::max<size_t>(smem, 1)));
     int per_sm = 1;
-    AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hmm_viterbi_kernel<K, A, NT>, threads, smem));
+    AH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hmm_score_kernel<Op, K, A, NT>, threads, smem));
     const uint64_t groups = (n + A - 1) / A;
     const uint64_t blocks = std::min<uint64_t>(groups, (uint64_t)sms * (uint64_t)std::max(1, per_sm));
-    hmm_viterbi_kernel<K, A, NT><<<(unsigned)blocks, threads, smem, s>>>(amps, order, n, planes, contig_off,
+    hmm_score_kernel<Op, K, A, NT><<<(unsigned)blocks, threads, smem, s>>>(amps, order, n, planes, contig_off,
                                                                           n_contigs, t, e, m, max_len, out, err);
     AH_CUDA(cudaGetLastError());
     return true;
@@ -452,9 +470,9 @@ bool launch_k(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const 
 
 } // namespace
 
-void launch_hmm_viterbi(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
-                        const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m,
-                        int max_len, float *score_out, int *err, int sms, cudaStream_t s)
+void launch_hmm_score(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
+                      const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m,
+                      int max_len, bool forward, float *score_out, int *err, int sms, cudaStream_t s)
 {
     if (n == 0)
         return;
@@ -464,11 +482,18 @@ void launch_hmm_viterbi(const ah_amplicon *amps, const uint32_t *order, uint64_t
     if (const char *v = getenv("AH_HMM_VARIANT"))
         if (sscanf(v, "%d,%d", &vk, &va) != 2)
             vk = va = 0;
-#define AH_HMM_TRY(K_, A_, NT_)                                                                                  \
+#define AH_HMM_TRY_OP(OP_, K_, A_, NT_)                                                                          \
     if ((vk == 0 || (vk == K_ && va == A_)) &&                                                                   \
-        launch_k<K_, A_, NT_>(amps, order, n, planes, contig_off, n_contigs, t, e, m, max_len, score_out, err, sms, \
-                              s))                                                                                \
+        launch_k<OP_, K_, A_, NT_>(amps, order, n, planes, contig_off, n_contigs, t, e, m, max_len, score_out, err, \
+                                   sms, s))                                                                      \
         return;
+    if (forward) { // the default variants only
+        vk = va = 0;
+        AH_HMM_TRY_OP(LogSum, 4, 2, 512)
+        AH_HMM_TRY_OP(LogSum, 6, 1, 512)
+        throw Error(AH_ERR_ARG, "ah_hmm_forward: profile longer than " + std::to_string(kHmmMaxColumns) + " columns");
+    }
+#define AH_HMM_TRY(K_, A_, NT_) AH_HMM_TRY_OP(MaxSum, K_, A_, NT_)
     if (vk) { // the named variant (when it covers the profile)
         AH_HMM_TRY(2, 2, 512)
         AH_HMM_TRY(4, 1, 512)
@@ -483,6 +508,7 @@ void launch_hmm_viterbi(const ah_amplicon *amps, const uint32_t *order, uint64_t
     AH_HMM_TRY(4, 2, 512)
     AH_HMM_TRY(6, 1, 512)
 #undef AH_HMM_TRY
+#undef AH_HMM_TRY_OP
     throw Error(AH_ERR_ARG, "ah_hmm_score: profile longer than " + std::to_string(kHmmMaxColumns) + " columns");
 }
 

@@ -114,15 +114,16 @@ __device__ __forceinline__ void classify4(uint32_t raw, uint32_t pw, uint32_t si
     V = valid4(raw, sixteen, top4) * pw + V;
 }
 
-// 4x4 byte transpose of rows r .. r+3 (4 columns each): col[k] = byte k of
-// each row; t[] = the first stage, (a0 b0 a1 b1), (a2 b2 a3 b3), (c0 d0 c1 d1),
-// (c2 d2 c3 d3).
-__device__ __forceinline__ void load_block(const uint32_t *__restrict__ rows, int r, int ci, uint32_t (&row)[4],
-                                           uint32_t (&t)[4], uint32_t (&col)[4])
+// 4x4 byte transpose of rows r .. r+3 (row(q) = this thread's word of row q,
+// 4 columns): col[k] = byte k of each row; t[] = the first stage, (a0 b0 a1
+// b1), (a2 b2 a3 b3), (c0 d0 c1 d1), (c2 d2 c3 d3).
+template <class Row>
+__device__ __forceinline__ void load_block(const Row &rowf, int r, uint32_t (&row)[4], uint32_t (&t)[4],
+                                           uint32_t (&col)[4])
 {
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-        row[q] = rows[(r + q) * kRowWords + ci];
+        row[q] = rowf(r + q);
     t[0] = __byte_perm(row[0], row[1], 0x5140);
     t[1] = __byte_perm(row[0], row[1], 0x7362);
     t[2] = __byte_perm(row[2], row[3], 0x5140);
@@ -139,8 +140,8 @@ __device__ __forceinline__ void load_block(const uint32_t *__restrict__ rows, in
 // .. W + 4*ci + 3: bit b of extension word W + j is the base at row b + 1,
 // column j, i.e. the column's own word shifted right by one with bit 31 from
 // row 32 (the next tile's first row, staged with the tile).
-__device__ __forceinline__ void pack_columns(const uint32_t *__restrict__ rows, int ci, uint32_t *__restrict__ dst,
-                                             uint32_t one)
+template <class Row>
+__device__ __forceinline__ void pack_columns(const Row &rowf, int ci, uint32_t *__restrict__ dst, uint32_t one)
 {
     const int j0 = 4 * ci;
     const uint32_t eight = one << 3, sixteen = one << 4, top4 = one << 28;
@@ -151,7 +152,7 @@ __device__ __forceinline__ void pack_columns(const uint32_t *__restrict__ rows, 
 #pragma unroll
     for (int rb = 0; rb < 8; ++rb) {
         uint32_t row[4], t[4], col[4];
-        load_block(rows, 4 * rb, ci, row, t, col);
+        load_block(rowf, 4 * rb, row, t, col);
         const uint32_t s01 = (row[0] & 0x0F0F0F0Fu) | ((row[1] * sixteen) & 0xF0F0F0F0u);
         const uint32_t s23 = (row[2] & 0x0F0F0F0Fu) | ((row[3] * sixteen) & 0xF0F0F0F0u);
         bad |= (t[0] ^ __byte_perm(kLetterLo, kLetterHi, s01)) | (t[1] ^ __byte_perm(kLetterLo, kLetterHi, s01 >> 16));
@@ -176,7 +177,7 @@ __device__ __forceinline__ void pack_columns(const uint32_t *__restrict__ rows, 
 #pragma unroll
         for (int rb = 0; rb < 8; ++rb) {
             uint32_t row[4], t[4], col[4];
-            load_block(rows, 4 * rb, ci, row, t, col);
+            load_block(rowf, 4 * rb, row, t, col);
             const uint32_t pw = one << (4 * rb);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
@@ -201,7 +202,7 @@ __device__ __forceinline__ void pack_columns(const uint32_t *__restrict__ rows, 
     if (j0 < kTileExt) {
         // row 32 of these four columns: bit k of hl / hh / hv = byte k's letter bits and validity
         uint32_t hl = 0, hh = 0, hv = 0;
-        classify4(rows[32 * kRowWords + ci], one, one << 4, one << 28, hl, hh, hv);
+        classify4(rowf(32), one, one << 4, one << 28, hl, hh, hv);
         const uint32_t ha = hv & ~hh & ~hl, hc = hv & ~hh & hl, ht = hv & hh & ~hl, hg = hv & hh & hl;
         uint4 ea, ec, eg, et;
         uint32_t *EA = &ea.x, *EC = &ec.x, *EG = &eg.x, *ET = &et.x;
@@ -290,7 +291,8 @@ __global__ void __launch_bounds__(kPackThreads) pack_kernel(const uint8_t *__res
             }
             __syncthreads();
         }
-        pack_columns(rows, threadIdx.x, planes + t * 4 * kTileWX, one);
+        const int ci = threadIdx.x;
+        pack_columns([&](int r) { return rows[r * kRowWords + ci]; }, ci, planes + t * 4 * kTileWX, one);
         __syncthreads(); // this buffer is refilled two tiles from now
     }
 }

@@ -972,11 +972,12 @@ def test_served_requests_alone_and_in_the_mix(ctx):
 
 
 def test_profile_hmm_build_and_scores(ctx):
-    """ah_hmm_build / ah_hmm_score: the profile trained on the exact-match
-    amplicons of an operon family (training set taken end to end: a k = 0 run
-    and its fetched sequences) equals the oracle's (fp32 of its fp64 scores),
-    and the fp32 Viterbi score of every k = 2 amplicon and of random regions is
-    within the fp32 accumulation bound of the oracle's fp64 score."""
+    """ah_hmm_build / ah_hmm_score / ah_hmm_forward: the profile trained on the
+    exact-match amplicons of an operon family (training set taken end to end: a
+    k = 0 run and its fetched sequences) equals the oracle's (fp32 of its fp64
+    scores), and the fp32 Viterbi and Forward scores of every k = 2 amplicon and
+    of random regions are within the fp32 accumulation bound of the oracle's
+    fp64 scores."""
     import torch
     w = synth.operon_family(seed=21, n_genomes=16)
     p = w.pairs[0]
@@ -1015,6 +1016,7 @@ def test_profile_hmm_build_and_scores(ctx):
         assert np.abs(gt[fin] - T[fin]).max() <= 1e-5
         assert np.abs(ge - E).max() <= 1e-5
         got = ctx.hmm_score(sid, hid, amps)
+        got_f = ctx.hmm_forward(sid, hid, amps)
         # device records and scores give the same
         dev_amps = torch.from_numpy(amps.view(np.uint8).copy()).cuda()
         dev_out = torch.zeros(len(amps), dtype=torch.float32, device="cuda")
@@ -1040,3 +1042,10 @@ def test_profile_hmm_build_and_scores(ctx):
     err = np.abs(got.astype(np.float64) - want)
     assert (err <= tol).all(), (err.max(), tol.min())
     assert want[:len(a2)].min() > want[len(a2):].max()  # family members above unrelated regions
+    # Forward: the same walk, plus per log-sum step an absolute error of a few
+    # 2^-23 from log2(1 + 2^d) (exp2f / log2f within 2 ulp)
+    want_f = np.array([oracle.hmm_forward(T, E, x) for x in seqs])
+    tol_f = 10.0 * np.sqrt(N) * (2.0 ** -24 * (np.abs(want_f) + N * pmean) + 4 * 2.0 ** -23) + 1e-4
+    err_f = np.abs(got_f.astype(np.float64) - want_f)
+    assert (err_f <= tol_f).all(), (err_f.max(), tol_f.min())
+    assert (want_f >= want - 1e-9).all() and (got_f >= got - 1e-3).all()  # the sum is at least the best path

@@ -1,7 +1,8 @@
 """Pins of the profile-HMM oracle (oracle/hmm.c) against brute force and closed
-forms: alignment distance by enumerating every alignment, the Viterbi score by
-enumerating every state path, the profile of identical training sequences in
-closed form, and the counts of single insertions and deletions.  Then the
+forms: alignment distance by enumerating every alignment, the Viterbi and
+Forward scores by enumerating every state path, the profile of identical
+training sequences in closed form, and the counts of single insertions and
+deletions.  Then the
 library's host-side profile builder against the pinned oracle (no GPU)."""
 import math
 
@@ -86,6 +87,63 @@ def test_viterbi_is_the_best_of_all_state_paths():
             want = _brute_viterbi(t, e, x)
             got = oracle.hmm_viterbi(t, e, x)
             assert got == pytest.approx(want, abs=1e-9), (train, x)
+
+
+def _all_path_scores(t, e, x):
+    """The score of every state path from B = M_0 to E emitting exactly x."""
+    m = t.shape[0] - 1
+    n = len(x)
+    out = []
+
+    def em(j, i):
+        c = x[i]
+        return e[j, LET.index(c)] if c in LET else 0.0
+
+    def walk(state, j, i, score):
+        if score == -math.inf:
+            return
+        if j == m:
+            if i == n:
+                out.append(score + t[m, state, 0])
+            if i < n:
+                walk(1, m, i + 1, score + t[m, state, 1])
+            return
+        if i < n:
+            walk(0, j + 1, i + 1, score + t[j, state, 0] + em(j + 1, i))
+            walk(1, j, i + 1, score + t[j, state, 1])
+        walk(2, j + 1, i, score + t[j, state, 2])
+
+    walk(0, 0, 0, 0.0)
+    return [v for v in out if v > -math.inf]
+
+
+def test_forward_is_the_log_sum_over_all_state_paths():
+    """Forward = log2 of the sum of 2^score over every path (enumerated); it is
+    at least the Viterbi score and at most Viterbi + log2(number of paths)."""
+    rng = np.random.default_rng(4)
+    for trial in range(60):
+        m = int(rng.integers(1, 4))
+        train = ["".join(rng.choice(list(LET), size=max(1, m + int(rng.integers(-1, 2)))))
+                 for _ in range(int(rng.integers(1, 5)))]
+        _, t, e = oracle.hmm_build(train)
+        for _ in range(4):
+            x = "".join(rng.choice(list(LET + "N"), size=int(rng.integers(0, 5))))
+            scores = _all_path_scores(t, e, x)
+            top = max(scores)
+            want = top + math.log2(sum(2.0 ** (v - top) for v in scores))
+            got = oracle.hmm_forward(t, e, x)
+            assert got == pytest.approx(want, abs=1e-9), (train, x)
+            vit = oracle.hmm_viterbi(t, e, x)
+            assert vit - 1e-12 <= got <= vit + math.log2(len(scores)) + 1e-12
+
+
+def test_forward_of_the_empty_sequence_is_the_delete_path():
+    """With no letter to emit the only path is B, D_1 .. D_m, E."""
+    _, t, e = oracle.hmm_build(["ACGTA", "ACGTA", "ACTA"])
+    m = t.shape[0] - 1
+    want = t[0, 0, 2] + sum(t[j, 2, 2] for j in range(1, m)) + t[m, 2, 0]
+    assert oracle.hmm_forward(t, e, "") == pytest.approx(want, abs=1e-12)
+    assert oracle.hmm_viterbi(t, e, "") == pytest.approx(want, abs=1e-12)
 
 
 def test_profile_of_identical_sequences_in_closed_form():
