@@ -1347,7 +1347,7 @@ def bench_large_main(args):
     if ne > 0:
         torch.cuda.empty_cache()
         hout = HostOut(torch, ah, (caps[0] * 9 // 8 + 1024, caps[1] * 9 // 8 + 64, caps[2] * 9 // 8 + 4096))
-        reps = max(1, args.e2e_steps // 5)
+        reps = max(1, args.e2e_steps // 2)
 
         def measure(n_chunks, load, in_bytes):
             """reps steps over the first n_chunks chunks from host input; the next
@@ -1393,6 +1393,21 @@ def bench_large_main(args):
             codes_h.append(ch)
             gaps_h.append(gp)
 
+        # the host link alone on this machine: one pinned host -> device copy of the first chunk's codes
+        link_gbs = None
+        if codes_h:
+            dtmp = torch.empty(codes_h[0].numel(), dtype=torch.uint8, device="cuda")
+            l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for _ in range(2):
+                l0.record(streams[0])
+                with torch.cuda.stream(streams[0]):
+                    dtmp.copy_(codes_h[0], non_blocking=True)
+                l1.record(streams[0])
+                torch.cuda.synchronize()
+            link_gbs = codes_h[0].numel() / (l0.elapsed_time(l1) / 1e3) / 1e9
+            del dtmp
+            torch.cuda.empty_cache()
+
         def load2(i, st_):
             b0, b1, off, gen_ = tabs[i]
             return ctx.ah_load_genomes_2bit(codes_h[i], b1 - b0, gaps_h[i], off, gen_, st_)
@@ -1413,6 +1428,7 @@ def bench_large_main(args):
                         "(sites, Tm, pass flags, amplicons, sequences) to pinned host memory",
                "subset": f"first {ne} of {len(tabs)} chunks ({sub_gbp:.1f} Gbp of {N / 1e9:.1f}) per step",
                "pipeline": "the next chunk's host load (copy + packing) is issued while the current run computes",
+               "link_h2d_gbs": link_gbs,
                "ascii_input": {"value": va, "unit": "Gbp/s", "h2d_bytes_per_step": h2da, "d2h_bytes_per_step": d2ha,
                                "subset": f"first chunk ({(b1 - b0) / 1e9:.1f} Gbp) from ASCII (ah_load_genomes)"}}
 

@@ -175,9 +175,11 @@ size_t ah_device_bytes(const ah_ctx *ctx);
  * last n_bases.  contig_genome (host): genome id of each contig.
  * The library packs the sequence on the device into its own layout (4 one-hot
  * bitplanes A/C/G/T) and returns an id in *set_id_out.  Host arrays are not
- * referenced after the call: a host seq is copied in chunks through staging
- * buffers on the device (the copies overlap the packing) and the call waits
- * for the copies, not for the packing.  A device seq is read by work queued
+ * referenced after the call: a host seq is copied through a staging buffer
+ * on the device (the whole sequence when it fits in 4 GiB, else chunks of that
+ * size through two buffers, the copies overlapping the packing; at most 1/16
+ * of a memory budget; the context keeps the buffers for later loads) and the
+ * call waits for the copies, not for the packing.  A device seq is read by work queued
  * on `stream` (stream-ordered, like any CUDA call): it must stay valid until
  * that work has run; the call returns without waiting for it.  A device seq
  * at a 16-byte aligned address is staged by bulk copies; at any other address

@@ -322,6 +322,37 @@ void *scratch(ah_ctx *c, const std::string &name, size_t bytes)
     return s.p;
 }
 
+// The staging buffers of host loads: one holding a set's whole input when it
+// fits (at most kHostStageMax bytes, and 1/16 of a memory budget), so that its
+// copy runs beside the previous run's scan instead of waiting for the packing of
+// earlier pieces; else two of that size, used in turn.  Before a buffer is
+// replaced, every earlier copy into it and every packing from it has finished.
+// Returns the bytes each buffer in use holds (stage[1] is null for one buffer).
+constexpr uint64_t kHostStageMax = (4ull << 30) + (1ull << 20);
+uint64_t host_stage(ah_ctx *c, uint64_t want, uint8_t *stage[2])
+{
+    uint64_t cap = std::min<uint64_t>(want, kHostStageMax);
+    if (const char *e = getenv("AH_HOST_STAGE_MB")) // profiling aid: a smaller cap
+        if (atoll(e) > 0)
+            cap = std::min<uint64_t>(cap, (uint64_t)atoll(e) << 20);
+    if (c->budget)
+        cap = std::min<uint64_t>(cap, std::max<uint64_t>(c->budget / 16, 64ull << 20));
+    cap = std::max<uint64_t>(cap, 1ull << 20);
+    const bool two = want > cap;
+    Scratch &s0 = c->scratch["load_stage0"], &s1 = c->scratch["load_stage1"];
+    if (s0.bytes < cap || (two && s1.bytes < cap)) {
+        for (int b = 0; b < 2; ++b) {
+            AH_CUDA(cudaEventSynchronize(c->ev_copied[b]));
+            AH_CUDA(cudaEventSynchronize(c->ev_packed[b]));
+        }
+        AH_CUDA(cudaEventSynchronize(c->ev_last_copy));
+    }
+    stage[0] = (uint8_t *)scratch(c, "load_stage0", cap);
+    stage[1] = two ? (uint8_t *)scratch(c, "load_stage1", cap) : nullptr;
+    return two ? std::min(c->scratch["load_stage0"].bytes, c->scratch["load_stage1"].bytes)
+               : c->scratch["load_stage0"].bytes;
+}
+
 bool is_device_ptr(ah_ctx *c, const void *p)
 {
     if (!p)
@@ -1729,13 +1760,13 @@ static ah_status load_impl(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, cons
                 Stage sg(c, "pack", st, 1);
                 launch_pack2(seq, 0, n_bases, n_bases, gaps_d, two->n_gaps, gs->planes, 0, gs->n_tiles, st);
             } else {
-                // host codes: tile-aligned chunks through two staging buffers, copies on
-                // the copy stream beside the packing of the previous chunk; each chunk
-                // also carries the next 64 positions (the extension row)
-                const uint64_t chunk_tiles = 2048; // 64 Mbp, 16 MB of codes
-                const uint64_t stage_bytes = (chunk_tiles * kTileBases + 64) / 4;
-                uint8_t *stage[2] = {(uint8_t *)scratch(c, "load_stage0", stage_bytes),
-                                     (uint8_t *)scratch(c, "load_stage1", stage_bytes)};
+                // host codes: tile-aligned chunks through two staging buffers (the whole
+                // set in one when it fits), copies on the copy stream beside the packing
+                // of the previous chunk; each chunk also carries the next 64 positions
+                // (the extension row)
+                uint8_t *stage[2];
+                const uint64_t cap = host_stage(c, (gs->n_tiles * kTileBases + 64) / 4 + 16, stage);
+                const uint64_t chunk_tiles = std::max<uint64_t>(1, (cap * 4 - 128) / kTileBases);
                 AH_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[0], 0));
                 AH_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[1], 0));
                 AH_CUDA(cudaEventRecord(c->ev_load_start, st));
@@ -1772,10 +1803,9 @@ static ah_status load_impl(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, cons
                 // host sequence: tile-aligned chunks through two staging buffers; the
                 // copies run on a second stream so chunk i+1 crosses the link while chunk
                 // i is packed.  Each chunk also carries the next tile (extension words).
-                const uint64_t chunk_tiles = 1024; // 32 Mbp
-                const uint64_t stage_bytes = chunk_tiles * kTileBases + kTileBases;
-                uint8_t *stage[2] = {(uint8_t *)scratch(c, "load_stage0", stage_bytes),
-                                     (uint8_t *)scratch(c, "load_stage1", stage_bytes)};
+                uint8_t *stage[2];
+                const uint64_t cap = host_stage(c, gs->n_tiles * kTileBases + kTileBases, stage);
+                const uint64_t chunk_tiles = std::max<uint64_t>(1, (cap - kTileBases) / kTileBases);
                 // the copy stream starts after everything queued so far on st, and after
                 // the packing of an earlier load from these staging buffers
                 AH_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_packed[0], 0));
