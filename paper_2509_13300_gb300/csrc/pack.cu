@@ -540,12 +540,12 @@ void launch_pack(const uint8_t *seq, uint64_t seq_base, uint64_t seq_len, uint64
         tiles_per_block = (e && atoi(e) > 0) ? atoi(e) : 1;
     }
     blocks = std::min<uint64_t>(blocks, (t1 - t0 + tiles_per_block - 1) / tiles_per_block);
-    // A block that packs one tile uses one staging buffer, but it reserves two:
-    // three blocks per SM leave shared memory for a run's kernels beside the
-    // packing (measured: 6 blocks per SM pack faster alone, 128 vs 138 us for
-    // 0.4 Gbp, but the pipelined step is slower, 316 vs 306 us).
-    // AH_PACK_SMEM_KB sets the reservation (profiling aid; at least one buffer).
-    size_t smem_launch = smem;
+    // A block that packs one tile reserves the one staging buffer it uses: six
+    // blocks per SM (measured on the large workload: the packing alone at 0.97
+    // of the copy peak against 0.84 with two buffers reserved, and a pass 2.4 %
+    // shorter; the collection step unchanged).  AH_PACK_SMEM_KB sets the
+    // reservation (profiling aid; at least one buffer).
+    size_t smem_launch = blocks >= t1 - t0 ? smem / 2 : smem;
     if (const char *e = getenv("AH_PACK_SMEM_KB"))
         smem_launch = std::min(smem, std::max(blocks >= t1 - t0 ? smem / 2 : smem, (size_t)atoi(e) * 1024));
     const int tma_ok = ((reinterpret_cast<uintptr_t>(seq) - seq_base) % 16 == 0) ? 1 : 0;
