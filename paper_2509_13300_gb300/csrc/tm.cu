@@ -693,7 +693,9 @@ __global__ void __launch_bounds__(kFastThreads) tm_fast_kernel(const ah_site *__
             for (int j = 0; j < 8; ++j) {
                 const uint64_t wk = __shfl_sync(0xffffffffu, wofs, k0 + j);
                 bk[j] = __shfl_sync(0xffffffffu, brow, k0 + j);
-                const bool on = (actm >> (k0 + j)) & 1u;
+                const int Lk = __shfl_sync(0xffffffffu, L, k0 + j);
+                // the window's L positions only (the sectors past them are not read)
+                const bool on = ((actm >> (k0 + j)) & 1u) && lane < Lk;
                 const uint32_t *w = planes + wk + lane; // position P_k + lane (the tile's extension covers 32 more)
 #pragma unroll
                 for (int x = 0; x < 4; ++x)
