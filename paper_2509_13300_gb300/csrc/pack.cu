@@ -220,7 +220,7 @@ __device__ __forceinline__ void pack_columns(const Row &rowf, int ci, uint32_t *
     }
 }
 
-__global__ void __launch_bounds__(kPackThreads) pack_kernel(const uint8_t *__restrict__ seq, uint64_t seq_base,
+__global__ void __launch_bounds__(kPackThreads, 6) pack_kernel(const uint8_t *__restrict__ seq, uint64_t seq_base,
                                                             uint64_t seq_len, uint64_t n_bases,
                                                             uint32_t *__restrict__ planes, uint64_t t0, uint64_t t1,
                                                             int tma_ok, uint32_t one, int *__restrict__ err)
