@@ -201,6 +201,14 @@ ah_status ah_load_genomes(ah_ctx *ctx, const uint8_t *seq, uint64_t n_bases, con
  * for its packing before it returns.  Unknown flag bits: AH_ERR_ARG.
  * Other arguments, ownership and errors as ah_load_genomes. */
 #define AH_LOAD_REVERSED 1u
+/* flags: AH_LOAD_HOST_ASYNC (ah_load_genomes_ex, ah_load_genomes_2bit_ex): a
+ * host seq (or host codes and gaps) is read by copies the call queues and does
+ * not wait for, so a host load can overlap the caller's next calls (a run in
+ * flight).  The caller keeps those host arrays valid and unchanged until the
+ * set is ready: until a call that reads the set and synchronises (ah_scan,
+ * ah_run, ah_run_end, ...) or ah_unload_genomes of the set has returned.
+ * Ignored for device input and for reversed loads (which always wait). */
+#define AH_LOAD_HOST_ASYNC 2u
 ah_status ah_load_genomes_ex(ah_ctx *ctx, const uint8_t *seq, uint64_t n_bases, const uint64_t *contig_off,
                              uint32_t n_contigs, const uint32_t *contig_genome, uint32_t flags, uint32_t *set_id_out,
                              void *stream);
@@ -221,6 +229,11 @@ ah_status ah_load_genomes_ex(ah_ctx *ctx, const uint8_t *seq, uint64_t n_bases, 
 ah_status ah_load_genomes_2bit(ah_ctx *ctx, const uint8_t *codes, uint64_t n_bases, const uint64_t *gaps,
                                uint64_t n_gaps, const uint64_t *contig_off, uint32_t n_contigs,
                                const uint32_t *contig_genome, uint32_t *set_id_out, void *stream);
+/* ah_load_genomes_2bit with flags (AH_LOAD_HOST_ASYNC; other bits: AH_ERR_ARG). */
+ah_status ah_load_genomes_2bit_ex(ah_ctx *ctx, const uint8_t *codes, uint64_t n_bases, const uint64_t *gaps,
+                                  uint64_t n_gaps, const uint64_t *contig_off, uint32_t n_contigs,
+                                  const uint32_t *contig_genome, uint32_t flags, uint32_t *set_id_out,
+                                  void *stream);
 
 /* Free a loaded genome set (after its packing has run).  AH_ERR_ARG for an
  * unknown id; AH_ERR_TIMEOUT for a packing that failed on the device and was

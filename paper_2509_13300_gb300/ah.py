@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "AH_OK", 1: "AH_ERR_ARG", 2: "AH_ERR_PRIMER", 3: "AH_ERR_OOM"
                 5: "AH_ERR_OVERFLOW", 6: "AH_ERR_CUDA", 7: "AH_ERR_TIMEOUT", 8: "AH_ERR_JIT",
                 9: "AH_ERR_DEVICE_CHECK"}
 AH_LOAD_REVERSED = 1  # ah_load_genomes_ex flag: contigs packed reversed (decoy genomes)
+AH_LOAD_HOST_ASYNC = 2  # load flag: host input copies queued, not waited for (keep the input unchanged)
 
 SITE_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("pos", "<u4"), ("primer", "u1"),
                        ("strand", "u1"), ("mm", "u1"), ("pair", "u1")])
@@ -32,7 +33,8 @@ AMPLICON_DTYPE = np.dtype([("genome", "<u4"), ("contig", "<u4"), ("start", "<u4"
 EXPORTS = ["ah_create", "ah_destroy", "ah_last_error", "ah_device_bytes", "ah_load_genomes", "ah_unload_genomes",
            "ah_set_primers", "ah_set_nn_table", "ah_scan", "ah_tm", "ah_pair", "ah_fetch", "ah_set_profiling",
            "ah_get_profile", "ah_pair_noalloc", "ah_tune_scan", "ah_run", "ah_run_begin", "ah_run_end",
-           "ah_load_genomes_ex", "ah_tm_sweep", "ah_amplitypes", "ah_generate_bases", "ah_serve_start",
+           "ah_load_genomes_ex", "ah_load_genomes_2bit", "ah_load_genomes_2bit_ex", "ah_tm_sweep", "ah_amplitypes",
+           "ah_generate_bases", "ah_serve_start",
            "ah_serve_submit", "ah_serve_wait", "ah_serve_stop", "ah_hmm_build", "ah_hmm_tables", "ah_hmm_score",
            "ah_hmm_forward", "ah_hmm_free"]
 
@@ -120,6 +122,7 @@ def lib():
             "ah_load_genomes": (I32, [P, P, U64, P, U32, P, ctypes.POINTER(U32), P]),
             "ah_load_genomes_ex": (I32, [P, P, U64, P, U32, P, U32, ctypes.POINTER(U32), P]),
             "ah_load_genomes_2bit": (I32, [P, P, U64, P, U64, P, U32, P, ctypes.POINTER(U32), P]),
+            "ah_load_genomes_2bit_ex": (I32, [P, P, U64, P, U64, P, U32, P, U32, ctypes.POINTER(U32), P]),
             "ah_unload_genomes": (I32, [P, U32]),
             "ah_set_primers": (I32, [P, ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(PcrParams),
                                      ctypes.POINTER(U32)]),
@@ -252,26 +255,31 @@ class Context:
         return ms.value, l.value, k.value
 
     def ah_load_genomes(self, seq, n_bases: int, contig_off: np.ndarray, contig_genome: np.ndarray,
-                        stream=None, reversed: bool = False) -> int:
-        """reversed: pack every contig reversed (the decoy collection)."""
+                        stream=None, reversed: bool = False, host_async: bool = False) -> int:
+        """reversed: pack every contig reversed (the decoy collection).  host_async:
+        a host seq's copies are queued, not waited for (AH_LOAD_HOST_ASYNC): keep it
+        unchanged until a synchronising call on the set has returned."""
         contig_off = np.ascontiguousarray(contig_off, dtype=np.uint64)
         contig_genome = np.ascontiguousarray(contig_genome, dtype=np.uint32)
         sid = ctypes.c_uint32()
+        flags = (AH_LOAD_REVERSED if reversed else 0) | (AH_LOAD_HOST_ASYNC if host_async else 0)
         self._check(self._lib.ah_load_genomes_ex(self.h, _ptr(seq), n_bases, _ptr(contig_off), len(contig_off) - 1,
-                                                 _ptr(contig_genome), AH_LOAD_REVERSED if reversed else 0,
-                                                 ctypes.byref(sid), _stream(stream)))
+                                                 _ptr(contig_genome), flags, ctypes.byref(sid), _stream(stream)))
         return sid.value
 
     def ah_load_genomes_2bit(self, codes, n_bases: int, gaps: np.ndarray, contig_off: np.ndarray,
-                             contig_genome: np.ndarray, stream=None) -> int:
-        """Load from 2-bit codes (encode_2bit) and the no-base runs (gaps: (n, 2) uint64)."""
+                             contig_genome: np.ndarray, stream=None, host_async: bool = False) -> int:
+        """Load from 2-bit codes (encode_2bit) and the no-base runs (gaps: (n, 2) uint64);
+        host_async as ah_load_genomes (the codes and gaps stay unchanged meanwhile)."""
         gaps = np.ascontiguousarray(gaps, dtype=np.uint64).reshape(-1, 2)
         contig_off = np.ascontiguousarray(contig_off, dtype=np.uint64)
         contig_genome = np.ascontiguousarray(contig_genome, dtype=np.uint32)
         sid = ctypes.c_uint32()
-        self._check(self._lib.ah_load_genomes_2bit(self.h, _ptr(codes), n_bases, _ptr(gaps) if len(gaps) else None,
-                                                   len(gaps), _ptr(contig_off), len(contig_off) - 1,
-                                                   _ptr(contig_genome), ctypes.byref(sid), _stream(stream)))
+        self._check(self._lib.ah_load_genomes_2bit_ex(self.h, _ptr(codes), n_bases,
+                                                      _ptr(gaps) if len(gaps) else None, len(gaps),
+                                                      _ptr(contig_off), len(contig_off) - 1, _ptr(contig_genome),
+                                                      AH_LOAD_HOST_ASYNC if host_async else 0, ctypes.byref(sid),
+                                                      _stream(stream)))
         return sid.value
 
     def ah_unload_genomes(self, set_id: int):

@@ -322,6 +322,28 @@ void *scratch(ah_ctx *c, const std::string &name, size_t bytes)
     return s.p;
 }
 
+// The next mapped pinned slot of the ring, holding at least `bytes`: host data
+// that a copy kernel reads over the link (a copy-engine transfer would queue
+// behind a large host->device copy still in flight); waits only for the reads
+// of the slot's earlier use.
+ah_ctx::PinSlot &pin_slot(ah_ctx *c, size_t bytes)
+{
+    ah_ctx::PinSlot &sl = c->pin[c->pin_next];
+    c->pin_next = (c->pin_next + 1) % ah_ctx::kPinSlots;
+    AH_CUDA(cudaEventSynchronize(sl.ev)); // the slot's earlier reads are done
+    if (sl.bytes < bytes) {
+        if (sl.p)
+            AH_CUDA(cudaFreeHost(sl.p));
+        sl.p = sl.dp = nullptr;
+        sl.bytes = 0;
+        const size_t want = std::max<size_t>(bytes + bytes / 4, 1 << 16);
+        AH_CUDA(cudaHostAlloc((void **)&sl.p, want, cudaHostAllocMapped));
+        sl.bytes = want;
+        AH_CUDA(cudaHostGetDevicePointer((void **)&sl.dp, sl.p, 0));
+    }
+    return sl;
+}
+
 // The staging buffers of host loads: one holding a set's whole input when it
 // fits (at most kHostStageMax bytes, and 1/16 of a memory budget), so that its
 // copy runs beside the previous run's scan instead of waiting for the packing of
@@ -1668,8 +1690,10 @@ static ah_status load_impl(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, cons
         return AH_ERR_ARG;
     return guarded(c, [&] {
         HostSpan hs(c, "host.load");
-        require((flags & ~AH_LOAD_REVERSED) == 0, AH_ERR_ARG, "ah_load_genomes_ex: unknown flag bits");
+        require((flags & ~(AH_LOAD_REVERSED | AH_LOAD_HOST_ASYNC)) == 0, AH_ERR_ARG,
+                "ah_load_genomes_ex: unknown flag bits");
         const bool reversed = (flags & AH_LOAD_REVERSED) != 0;
+        const bool host_async = (flags & AH_LOAD_HOST_ASYNC) != 0;
         require(set_id_out && contig_off && contig_genome && n_contigs >= 1, AH_ERR_ARG,
                 "ah_load_genomes: null argument or no contigs");
         require(n_bases == 0 || seq, AH_ERR_ARG, "ah_load_genomes: seq is null");
@@ -1754,8 +1778,12 @@ static ah_status load_impl(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, cons
             gs->gaps_bytes = std::max<uint64_t>(two->n_gaps, 1) * 16;
             gs->gaps = (uint64_t *)dev_alloc(c, gs->gaps_bytes);
             uint64_t *gaps_d = gs->gaps;
-            if (two->n_gaps)
-                AH_CUDA(cudaMemcpyAsync(gaps_d, two->gaps, two->n_gaps * 16, cudaMemcpyHostToDevice, st));
+            if (two->n_gaps) { // through a pinned slot, like the contig tables
+                ah_ctx::PinSlot &gsl = pin_slot(c, two->n_gaps * 16);
+                memcpy(gsl.p, two->gaps, two->n_gaps * 16);
+                launch_copy_words((const uint32_t *)gsl.dp, (uint32_t *)gaps_d, two->n_gaps * 4, st);
+                AH_CUDA(cudaEventRecord(gsl.ev, st));
+            }
             if (dev_seq) {
                 Stage sg(c, "pack", st, 1);
                 launch_pack2(seq, 0, n_bases, n_bases, gaps_d, two->n_gaps, gs->planes, 0, gs->n_tiles, st);
@@ -1836,19 +1864,7 @@ static ah_status load_impl(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, cons
             HostSpan hs_tables(c, "host.load.tables");
             // the tables through a mapped pinned slot, read by one copy kernel; the
             // per-tile contig table is built here by a merge walk over tiles and contigs
-            ah_ctx::PinSlot &sl = c->pin[c->pin_next];
-            c->pin_next = (c->pin_next + 1) % ah_ctx::kPinSlots;
-            AH_CUDA(cudaEventSynchronize(sl.ev)); // the slot's earlier reads are done
-            if (sl.bytes < table_bytes) {
-                if (sl.p)
-                    AH_CUDA(cudaFreeHost(sl.p));
-                sl.p = sl.dp = nullptr;
-                sl.bytes = 0;
-                const size_t want = std::max<size_t>(table_bytes + table_bytes / 4, 1 << 16);
-                AH_CUDA(cudaHostAlloc((void **)&sl.p, want, cudaHostAllocMapped));
-                sl.bytes = want;
-                AH_CUDA(cudaHostGetDevicePointer((void **)&sl.dp, sl.p, 0));
-            }
+            ah_ctx::PinSlot &sl = pin_slot(c, table_bytes);
             memcpy(sl.p, contig_off, ob);
             memcpy(sl.p + ob, contig_genome, gb);
             {
@@ -1882,8 +1898,9 @@ static ah_status load_impl(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, cons
             // the caller's host buffer may be reused once this call returns: wait for
             // the copies only; the packing stays queued (like a device-input load, a
             // failure reaches the next call that synchronises), so a host load may
-            // also overlap a pending run
-            if (gs->n_tiles)
+            // also overlap a pending run.  AH_LOAD_HOST_ASYNC: the caller keeps the
+            // buffer unchanged until the set is ready, so the copies stay queued too
+            if (gs->n_tiles && !host_async)
                 AH_CUDA(cudaEventSynchronize(c->ev_last_copy));
             c->flags_dirty = true;
         } else if (reversed) { // the temporaries are freed once the packing is done
@@ -1916,8 +1933,20 @@ ah_status ah_load_genomes_2bit(ah_ctx *c, const uint8_t *codes, uint64_t n_bases
                                uint64_t n_gaps, const uint64_t *contig_off, uint32_t n_contigs,
                                const uint32_t *contig_genome, uint32_t *set_id_out, void *stream)
 {
+    return ah_load_genomes_2bit_ex(c, codes, n_bases, gaps, n_gaps, contig_off, n_contigs, contig_genome, 0,
+                                   set_id_out, stream);
+}
+
+ah_status ah_load_genomes_2bit_ex(ah_ctx *c, const uint8_t *codes, uint64_t n_bases, const uint64_t *gaps,
+                                  uint64_t n_gaps, const uint64_t *contig_off, uint32_t n_contigs,
+                                  const uint32_t *contig_genome, uint32_t flags, uint32_t *set_id_out, void *stream)
+{
     if (!c)
         return AH_ERR_ARG;
+    if (flags & ~AH_LOAD_HOST_ASYNC) {
+        c->err = "ah_load_genomes_2bit_ex: unknown flag bits (AH_LOAD_HOST_ASYNC only)";
+        return AH_ERR_ARG;
+    }
     if ((n_gaps && !gaps) || (n_bases && !codes)) {
         c->err = "ah_load_genomes_2bit: null codes or gaps";
         return AH_ERR_ARG;
@@ -1932,7 +1961,7 @@ ah_status ah_load_genomes_2bit(ah_ctx *c, const uint8_t *codes, uint64_t n_bases
     TwoBit two;
     two.gaps = gaps;
     two.n_gaps = n_gaps;
-    return load_impl(c, codes, n_bases, contig_off, n_contigs, contig_genome, 0, set_id_out, stream, &two);
+    return load_impl(c, codes, n_bases, contig_off, n_contigs, contig_genome, flags, set_id_out, stream, &two);
 }
 
 ah_status ah_unload_genomes(ah_ctx *c, uint32_t set_id)

@@ -26,7 +26,7 @@ def lib():
 def header_symbols():
     src = open(os.path.join(ROOT, "include", "ampliconhunter.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)  # drop comments
-    return sorted(set(re.findall(r"\b(ah_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(ah_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_binding_exports():

@@ -289,6 +289,62 @@ def test_2bit_loads_in_flight_on_two_streams(ctx):
             ctx.ah_unload_genomes(sid)
 
 
+def test_host_loads_queued_without_waiting(ctx):
+    """AH_LOAD_HOST_ASYNC: host loads (2-bit and ASCII, pinned buffers, several
+    sets queued back to back on two streams while a run is pending) return
+    before their copies finish; every set still gives its letters, and a run on
+    each equals the oracle's."""
+    import torch
+    rng = np.random.default_rng(47)
+    w = synth.random_small(62, n_bases=300_000, n_contigs=5, L_f=9, L_r=8, k=2, codes_f="RN", codes_r="SB",
+                           min_len=30, max_len=600)
+    p = w.pairs[0]
+    pid = ctx.ah_set_primers(p["fwd"], p["rev"], p)
+    o = oracle_run(w)
+    seqs, srcs = [], []
+    for j, n in enumerate((5_000_011, 3_200_003, 4_100_000)):
+        seq = np.frombuffer(b"ACGTacgt", np.uint8)[rng.integers(0, 8, n)].copy()
+        for s0 in rng.integers(0, n - 200, 2000):
+            seq[s0:s0 + int(rng.integers(1, 60))] = ord("N")
+        seqs.append(seq)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    # a run in flight on the small set while the big host loads are queued
+    sid0 = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    sids, keep = [], []
+    try:
+        for j, seq in enumerate(seqs):
+            off = np.array([0, len(seq) // 2, len(seq)], np.uint64)
+            if j % 2 == 0:
+                codes, gaps = ah.encode_2bit(seq)
+                host = torch.from_numpy(codes).pin_memory()
+                sids.append(ctx.ah_load_genomes_2bit(host, len(seq), gaps, off, np.zeros(2, np.uint32),
+                                                     streams[j % 2], host_async=True))
+            else:
+                host = torch.from_numpy(seq).pin_memory()
+                sids.append(ctx.ah_load_genomes(host, len(seq), off, np.zeros(2, np.uint32), streams[j % 2],
+                                                host_async=True))
+            keep.append(host)  # unchanged until the set is ready
+        r = ctx.run(sid0, [pid], tm_filter=True)
+        assert r["sites"].tobytes() == o["sites"].tobytes() and r["amps"].tobytes() == o["amps_tm"].tobytes()
+        for j, seq in enumerate(seqs):
+            amps = np.zeros(2, dtype=ah.AMPLICON_DTYPE)
+            amps["contig"] = [0, 1]
+            amps["end"] = [len(seq) // 2, len(seq) - len(seq) // 2]
+            got, _ = ctx.fetch(sids[j], amps)
+            up = np.where(seq == ord("N"), ord("N"), seq & 0xDF).astype(np.uint8).tobytes()
+            assert got == up, j
+    finally:
+        for sid in sids:
+            ctx.ah_unload_genomes(sid)
+        ctx.ah_unload_genomes(sid0)
+    with pytest.raises(ah.AHError) as e:
+        ctx._check(ctx._lib.ah_load_genomes_2bit_ex(ctx.h, ah._ptr(np.zeros(4, np.uint8)), 16, None, 0,
+                                                    ah._ptr(np.array([0, 16], np.uint64)), 1,
+                                                    ah._ptr(np.zeros(1, np.uint32)), 1, ah.ctypes.byref(
+                                                        ah.ctypes.c_uint32()), None))
+    assert e.value.status == ah.AH_ERR_ARG  # the reversed flag has no 2-bit form
+
+
 def test_2bit_load_rejects_bad_gaps(ctx):
     codes = np.zeros(25, np.uint8)
     off, gen = np.array([0, 100], np.uint64), np.zeros(1, np.uint32)
