@@ -1376,7 +1376,7 @@ def bench_large_main(args):
     if ne > 0:
         torch.cuda.empty_cache()
         hout = HostOut(torch, ah, (caps[0] * 9 // 8 + 1024, caps[1] * 9 // 8 + 64, caps[2] * 9 // 8 + 4096))
-        reps = max(1, args.e2e_steps // 2)
+        reps = max(1, args.e2e_steps)
 
         def measure(n_chunks, load, in_bytes):
             """reps steps over the first n_chunks chunks from host input; the next
