@@ -336,7 +336,10 @@ ah_ctx::PinSlot &pin_slot(ah_ctx *c, size_t bytes)
             AH_CUDA(cudaFreeHost(sl.p));
         sl.p = sl.dp = nullptr;
         sl.bytes = 0;
-        const size_t want = std::max<size_t>(bytes + bytes / 4, 1 << 16);
+        // a power of two: slots grow rarely (freeing pinned memory synchronises the device)
+        size_t want = (size_t)1 << 20;
+        while (want < bytes)
+            want <<= 1;
         AH_CUDA(cudaHostAlloc((void **)&sl.p, want, cudaHostAllocMapped));
         sl.bytes = want;
         AH_CUDA(cudaHostGetDevicePointer((void **)&sl.dp, sl.p, 0));
