@@ -266,8 +266,8 @@ def main():
     ap.add_argument("--form", default="large", choices=["large", "collection", "plain", "batched", "served", "hmm"],
                     help="large: the 50,000-genome line (default); collection (alias plain): the 100-genome "
                          "line; batched / served / hmm: those forms' lines")
-    ap.add_argument("--e2e-chunks", type=int, default=64,
-                    help="large: chunks timed end to end from host input (default: every chunk; 0: none)")
+    ap.add_argument("--e2e-chunks", type=int, default=4,
+                    help="large: chunks timed end to end from host input (0: none; 11 or more: every chunk)")
     ap.add_argument("--no-collection", action="store_true", help="large: skip the collection workload's key")
     ap.add_argument("--chunk-bases", type=int, default=2_000_000_000, help="batched: bases per set (whole genomes)")
     ap.add_argument("--plain-genomes", type=int, default=400, help="batched: genomes timed in the plain form")
