@@ -93,6 +93,37 @@ def test_random_small_with_edge_letters(ctx, seed, k, clamp):
     assert_parity(gpu_run(ctx, w), oracle_run(w))
 
 
+@pytest.mark.parametrize("clamp", [0, 3])
+def test_longest_primers_with_planted_sites(ctx, clamp):
+    """Primers of the longest supported length (32, the width of a window word)
+    and 31, planted on both strands with 0..6 substitutions at k = 4, some
+    across contig ends and next to no-base runs: the whole path equals the
+    oracle."""
+    rng = np.random.default_rng(77 + clamp)
+    fwd = synth.random_primer(rng, 32, "RYNSW")
+    rev = synth.random_primer(rng, 31, "KMY")
+    n = 400_000
+    g = synth.random_bases(rng, n, 0.5)
+    for s0 in rng.integers(0, n - 100, 60):
+        g[s0:s0 + int(rng.integers(1, 40))] = ord("N")
+    for j in range(80):
+        a = int(rng.integers(0, n - 2600))
+        f = synth._draw_oligo(rng, fwd, int(rng.integers(0, 7)))
+        r = synth._revcomp(synth._draw_oligo(rng, rev, int(rng.integers(0, 7))))
+        gap = int(rng.integers(100, 2400))
+        left, right = (f, r) if j % 2 == 0 else (r, f)  # FR and RF
+        g[a:a + len(left)] = np.frombuffer(left.encode(), np.uint8)
+        g[a + 32 + gap:a + 32 + gap + len(right)] = np.frombuffer(right.encode(), np.uint8)
+    cuts = np.sort(rng.choice(np.arange(1, n), 6, replace=False)).astype(np.uint64)
+    off = np.concatenate([[0], cuts, [n]]).astype(np.uint64)
+    w = synth.Workload("longest", g, off, np.zeros(len(off) - 1, np.uint32),
+                       [synth.pcr_params(fwd, rev, k=4, min_len=100, max_len=3000, clamp=clamp)],
+                       np.zeros(0, dtype=synth.PLANT_DTYPE))
+    o = oracle_run(w)
+    assert len(o["sites"]) >= 40 and len(o["amps"]) >= 10
+    assert_parity(gpu_run(ctx, w), o)
+
+
 def test_k_at_least_length_reports_every_window(ctx):
     w = synth.random_small(21, n_bases=5000, n_contigs=3, L_f=6, L_r=5, k=6, min_len=5, max_len=40)
     assert_parity(gpu_run(ctx, w), oracle_run(w), min_sites=19000)
