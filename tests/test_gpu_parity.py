@@ -124,6 +124,24 @@ def test_longest_primers_with_planted_sites(ctx, clamp):
     assert_parity(gpu_run(ctx, w), o)
 
 
+def test_thread_per_site_tm_at_high_degeneracy(ctx):
+    """Primers of 8,192 and 4,096 oligos (six N and an R; six N), enough chance
+    sites (above 32,768) for the thread-per-site Tm: every site's maximum over
+    all oligos within 0.01 C of the oracle's enumeration of every oligo, the
+    pass flags exact at a threshold near the median, and the whole path equal."""
+    rng = np.random.default_rng(5)
+    fwd, rev = "ANCNGNTNANCR", "CNNGNNTANNGC"
+    n = 3_200_000
+    g = synth.random_bases(rng, n, 0.5)
+    off = np.array([0, 400_000, 1_300_000, 2_500_000, n], np.uint64)
+    w = synth.Workload("degenerate", g, off, np.zeros(4, np.uint32),
+                       [synth.pcr_params(fwd, rev, k=1, min_len=30, max_len=60, tm_min=31.0)],
+                       np.zeros(0, dtype=synth.PLANT_DTYPE))
+    o = oracle_run(w)
+    assert len(o["sites"]) > 32768 and 0.2 < o["pass_"].mean() < 0.8
+    assert_parity(gpu_run(ctx, w), o)
+
+
 def test_k_at_least_length_reports_every_window(ctx):
     w = synth.random_small(21, n_bases=5000, n_contigs=3, L_f=6, L_r=5, k=6, min_len=5, max_len=40)
     assert_parity(gpu_run(ctx, w), oracle_run(w), min_sites=19000)
