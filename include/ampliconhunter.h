@@ -221,8 +221,8 @@ ah_status ah_load_genomes_ex(ah_ctx *ctx, const uint8_t *seq, uint64_t n_bases, 
  * 2 (p % 4) .. 2 (p % 4) + 1 of byte p / 4, A 0, C 1, G 2, T 3.  Device
  * codes must be 16-byte aligned (else AH_ERR_ARG).
  * gaps (host): n_gaps (start, length) pairs of uint64, sorted by start,
- * disjoint, length >= 1, inside [0, n_bases): the positions that are no
- * base, whatever their codes hold.
+ * disjoint, length >= 1, inside [0, n_bases), at most 2^32 - 1 of them: the
+ * positions that are no base, whatever their codes hold.
  * contig_off, contig_genome, set_id_out, stream, ownership, the waiting
  * rules and errors: as ah_load_genomes (the call also returns AH_ERR_ARG for
  * gaps that are unsorted, overlapping, empty or outside the set). */

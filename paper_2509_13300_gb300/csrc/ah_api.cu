@@ -1777,19 +1777,33 @@ static ah_status load_impl(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, cons
         } else if (gs->n_tiles && two) {
             HostSpan hs_pack(c, "host.load.pack");
             // the no-base runs on the device, owned by the set (another load in flight on
-            // another stream must not overwrite them while this packing reads them)
-            gs->gaps_bytes = std::max<uint64_t>(two->n_gaps, 1) * 16;
+            // another stream must not overwrite them while this packing reads them),
+            // followed by each tile's first run that ends after the tile's start (a
+            // merge walk here, so the packing searches nothing); through a pinned
+            // slot, like the contig tables
+            const uint64_t run_bytes = two->n_gaps * 16, tab_bytes = (gs->n_tiles + 1) * 4;
+            gs->gaps_bytes = std::max<uint64_t>(run_bytes + tab_bytes, 16);
             gs->gaps = (uint64_t *)dev_alloc(c, gs->gaps_bytes);
             uint64_t *gaps_d = gs->gaps;
-            if (two->n_gaps) { // through a pinned slot, like the contig tables
-                ah_ctx::PinSlot &gsl = pin_slot(c, two->n_gaps * 16);
-                memcpy(gsl.p, two->gaps, two->n_gaps * 16);
-                launch_copy_words((const uint32_t *)gsl.dp, (uint32_t *)gaps_d, two->n_gaps * 4, st);
+            const uint32_t *tile_gap_d = reinterpret_cast<const uint32_t *>(gs->gaps + 2 * two->n_gaps);
+            {
+                ah_ctx::PinSlot &gsl = pin_slot(c, run_bytes + tab_bytes);
+                memcpy(gsl.p, two->gaps, run_bytes);
+                uint32_t *tg = reinterpret_cast<uint32_t *>(gsl.p + run_bytes);
+                uint64_t gi = 0;
+                for (uint64_t t = 0; t <= gs->n_tiles; ++t) {
+                    const uint64_t p0 = t * kTileBases;
+                    while (gi < two->n_gaps && two->gaps[2 * gi] + two->gaps[2 * gi + 1] <= p0)
+                        ++gi;
+                    tg[t] = (uint32_t)gi;
+                }
+                launch_copy_words((const uint32_t *)gsl.dp, (uint32_t *)gaps_d, (run_bytes + tab_bytes) / 4, st);
                 AH_CUDA(cudaEventRecord(gsl.ev, st));
             }
             if (dev_seq) {
                 Stage sg(c, "pack", st, 1);
-                launch_pack2(seq, 0, n_bases, n_bases, gaps_d, two->n_gaps, gs->planes, 0, gs->n_tiles, st);
+                launch_pack2(seq, 0, n_bases, n_bases, gaps_d, two->n_gaps, tile_gap_d, gs->planes, 0, gs->n_tiles,
+                             st);
             } else {
                 // host codes: tile-aligned chunks through two staging buffers (the whole
                 // set in one when it fits), copies on the copy stream beside the packing
@@ -1816,7 +1830,8 @@ static ah_status load_impl(ah_ctx *c, const uint8_t *seq, uint64_t n_bases, cons
                     AH_CUDA(cudaStreamWaitEvent(st, c->ev_copied[b], 0));
                     {
                         Stage sg(c, "pack", st, 1);
-                        launch_pack2(stage[b], b0, b1 - b0, n_bases, gaps_d, two->n_gaps, gs->planes, t0, t1, st);
+                        launch_pack2(stage[b], b0, b1 - b0, n_bases, gaps_d, two->n_gaps, tile_gap_d, gs->planes, t0,
+                                     t1, st);
                     }
                     AH_CUDA(cudaEventRecord(c->ev_packed[b], st));
                 }
@@ -1952,6 +1967,10 @@ ah_status ah_load_genomes_2bit_ex(ah_ctx *c, const uint8_t *codes, uint64_t n_ba
     }
     if ((n_gaps && !gaps) || (n_bases && !codes)) {
         c->err = "ah_load_genomes_2bit: null codes or gaps";
+        return AH_ERR_ARG;
+    }
+    if (n_gaps > 0xffffffffull) {
+        c->err = "ah_load_genomes_2bit: more than 2^32 - 1 no-base runs";
         return AH_ERR_ARG;
     }
     for (uint64_t g = 0; g < n_gaps; ++g) { // sorted, disjoint, inside the set

@@ -175,10 +175,12 @@ void launch_copy_words(const uint32_t *src, uint32_t *dst, uint64_t n_words, cud
 // Pack tiles [t0, t1) from 2-bit codes (A 0, C 1, G 2, T 3; base p in bits
 // 2 (p % 4) of byte p / 4) whose first byte holds position base0 (a tile
 // boundary) and that hold n_avail positions; gaps (device, n_gaps (start,
-// length) pairs, sorted, disjoint) and positions >= n_bases are no base.
-// codes must be 16-byte aligned.
+// length) pairs, sorted, disjoint) and positions >= n_bases are no base;
+// tile_gap (device, one per tile + 1): the index of the first gap that ends
+// after the tile's first position.  codes must be 16-byte aligned.
 void launch_pack2(const uint8_t *codes, uint64_t base0, uint64_t n_avail, uint64_t n_bases, const uint64_t *gaps,
-                  uint64_t n_gaps, uint32_t *planes, uint64_t t0, uint64_t t1, cudaStream_t s);
+                  uint64_t n_gaps, const uint32_t *tile_gap, uint32_t *planes, uint64_t t0, uint64_t t1,
+                  cudaStream_t s);
 // One stretch of a contig-wise reversal: dst[k] = src[mirror - k] for k in
 // [start, start + len) (mirror = 2 * contig start + contig length - 1).
 struct RevChunk {

@@ -309,7 +309,8 @@ __global__ void __launch_bounds__(kPackThreads, 6) pack_kernel(const uint8_t *__
 // rows at a time: the rows' bytes form one 32-bit word, and each column's low
 // and high code bits are gathered into a nibble by one carry-free multiply.
 // A tile that a gap or the end of the data touches marks its no-base
-// positions in a shared bitmap first.
+// positions in a shared bitmap first; tile_gap[t] (built at load by a merge
+// walk) is the first gap that ends after tile t's start.
 // ---------------------------------------------------------------------------
 constexpr int kCodeRowBytes = kTileW / 4;                  // 256 bytes of codes per row
 constexpr int kCodeWords = (32 * kCodeRowBytes + 16) / 4;  // the tile + the extension row (16 bytes read)
@@ -321,12 +322,11 @@ __device__ __forceinline__ uint32_t gather4(uint32_t v) { return (v * 0x10204080
 __global__ void __launch_bounds__(kPackThreads) pack2_kernel(const uint8_t *__restrict__ codes, uint64_t base0,
                                                              uint64_t n_avail, uint64_t n_bases,
                                                              const uint64_t *__restrict__ gaps, uint64_t n_gaps,
+                                                             const uint32_t *__restrict__ tile_gap,
                                                              uint32_t *__restrict__ planes, uint64_t t0, uint64_t t1)
 {
     __shared__ __align__(16) uint32_t cw[kCodeWords];
     __shared__ uint32_t inv[kInvWords];
-    __shared__ uint64_t first_gap;
-    __shared__ int any_inv;
     const int ci = threadIdx.x;
     const uint64_t avail_end = base0 + n_avail < n_bases ? base0 + n_avail : n_bases; // bases present here
     for (uint64_t t = t0 + blockIdx.x; t < t1; t += gridDim.x) {
@@ -347,21 +347,11 @@ __global__ void __launch_bounds__(kPackThreads) pack2_kernel(const uint8_t *__re
                 cw[w] = v;
             }
         }
-        // no-base positions: gaps that meet [p0, pe), and everything at or past avail_end
-        if (ci == 0) {
-            uint64_t lo = 0, hi = n_gaps; // first gap ending after p0
-            while (lo < hi) {
-                const uint64_t mid = (lo + hi) / 2;
-                if (gaps[2 * mid] + gaps[2 * mid + 1] <= p0)
-                    lo = mid + 1;
-                else
-                    hi = mid;
-            }
-            first_gap = lo;
-            any_inv = (lo < n_gaps && gaps[2 * lo] < pe) || avail_end < pe;
-        }
+        // no-base positions: gaps that meet [p0, pe), and everything at or past avail_end;
+        // the tile's first gap ending after p0 comes from the table built at load
+        const uint64_t first_gap = tile_gap[t];
+        const bool marked = (first_gap < n_gaps && gaps[2 * first_gap] < pe) || avail_end < pe;
         __syncthreads();
-        const bool marked = any_inv != 0;
         if (marked) {
             for (int w = ci; w < kInvWords; w += blockDim.x)
                 inv[w] = 0u;
@@ -482,7 +472,8 @@ __global__ void copy_words_kernel(const uint32_t *__restrict__ src, uint32_t *__
 } // namespace
 
 void launch_pack2(const uint8_t *codes, uint64_t base0, uint64_t n_avail, uint64_t n_bases, const uint64_t *gaps,
-                  uint64_t n_gaps, uint32_t *planes, uint64_t t0, uint64_t t1, cudaStream_t s)
+                  uint64_t n_gaps, const uint32_t *tile_gap, uint32_t *planes, uint64_t t0, uint64_t t1,
+                  cudaStream_t s)
 {
     if (t1 <= t0)
         return;
@@ -496,8 +487,8 @@ void launch_pack2(const uint8_t *codes, uint64_t base0, uint64_t n_avail, uint64
         cached_dev = dev;
     }
     const uint64_t blocks = std::min<uint64_t>(t1 - t0, (uint64_t)sms * 8);
-    pack2_kernel<<<(unsigned)blocks, kPackThreads, 0, s>>>(codes, base0, n_avail, n_bases, gaps, n_gaps, planes, t0,
-                                                           t1);
+    pack2_kernel<<<(unsigned)blocks, kPackThreads, 0, s>>>(codes, base0, n_avail, n_bases, gaps, n_gaps, tile_gap,
+                                                           planes, t0, t1);
     AH_CUDA(cudaGetLastError());
 }
 
