@@ -1556,6 +1556,11 @@ void ah_destroy(ah_ctx *c)
         cudaEventSynchronize(c->ev_run); // a queued run still uses the context's memory
     if (c->stream)
         cudaStreamSynchronize(c->stream);
+    // host loads queued without waiting (AH_LOAD_HOST_ASYNC) may still copy into the staging buffers
+    if (c->copy_stream)
+        cudaStreamSynchronize(c->copy_stream);
+    if (c->run_stream)
+        cudaStreamSynchronize(c->run_stream);
     for (auto &kv : c->live)
         cudaFree(kv.first);
     for (auto &p : c->pending) {
