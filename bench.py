@@ -269,6 +269,8 @@ def main():
     ap.add_argument("--e2e-chunks", type=int, default=4,
                     help="large: chunks timed end to end from host input (0: none; 11 or more: every chunk)")
     ap.add_argument("--no-collection", action="store_true", help="large: skip the collection workload's key")
+    ap.add_argument("--no-forms", action="store_true", help="large: skip the batched and served forms' keys")
+    ap.add_argument("--forms-requests", type=int, default=400, help="large: requests of the served form's key")
     ap.add_argument("--chunk-bases", type=int, default=2_000_000_000, help="batched: bases per set (whole genomes)")
     ap.add_argument("--plain-genomes", type=int, default=400, help="batched: genomes timed in the plain form")
     ap.add_argument("--batched-input", default="2bit", choices=["2bit", "ascii"], help="batched: host input format")
@@ -694,7 +696,7 @@ class HostOut:
         return 21 * o.n_sites + 28 * o.n_amplicons + o.n_seq + 8 * (o.n_amplicons + 1)
 
 
-def bench_batched(args):
+def bench_batched(args, emit: bool = True):
     """Batched form: thousands of genomes of uneven length per set, streamed
     from pinned host memory in double-buffered chunks, several pairs in one
     scan launch; against the plain form (one genome per load and run)."""
@@ -889,11 +891,13 @@ def bench_batched(args):
                             "form": "one genome per ah_load_genomes, one ah_run with the 4 pairs"},
         "batched_over_plain": gbps / gbps_plain, "batched_over_plain_all_pairs": gbps / plain_res[False][0], "clocks": clk.summary(), "stages_ms_one_pass": stages,
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
     ctx.close()
+    return line
 
 
-def bench_served(args):
+def bench_served(args, emit: bool = True):
     """Served form: a request loop over a resident pool; Poisson arrivals, then
     a saturated burst, against sequential plain solves of the same requests."""
     import torch
@@ -1029,9 +1033,12 @@ def bench_served(args):
                    "request_gbp_total": sum(req_bases) / 1e9},
         "poisson": poisson, "saturated": saturated, "sequential_plain": seq_plain, "stages_ms_saturated": stages,
         "saturated_over_sequential": saturated["gbps"] / seq_plain["gbps"],
+        "same_results_poisson_and_saturated": True,   # per-request digests compared above
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
     ctx.close()
+    return line
 
 
 def large_pairs():
@@ -1509,6 +1516,9 @@ def bench_large_main(args):
                         "ms_per_step": c["ms_per_step"], "steps": sub.steps,
                         "timed_region_kernel_us": c["timed_region_kernel_us"], "roofline": c["roofline"],
                         "e2e": c["e2e"]}
+    forms = None
+    if not args.no_forms and world == 1:
+        forms = form_keys(args)
     if rank != 0:
         return None
     line = {
@@ -1530,10 +1540,57 @@ def bench_large_main(args):
         "stages": stages, "roofline": roof, "pack_roofline": pack_roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(total_launches), "clocks": clocks,
         "timed_region_ms_per_step": {st: live[st]["ms_per_step"] for st in live},
-        "collection": coll_key,
+        "collection": coll_key, "forms": forms,
     }
     print(json.dumps(line), flush=True)
     return line
+
+
+def form_keys(args):
+    """The batched and served forms on their own workloads (10,000 genomes
+    streamed from pinned host memory against one load and run per genome; a
+    resident 5,000-genome pool serving Poisson-arriving requests, then the
+    same requests all at once, against sequential plain solves), run after the
+    large workload's memory is released.  A form that fails is reported by its
+    error and does not stop the line."""
+    import torch
+    out = {}
+    for name, fn, over in (("batched", bench_batched, {"steps": 2, "warmup": 3}),
+                           ("served", bench_served, {"requests": args.forms_requests})):
+        sub = argparse.Namespace(**vars(args))
+        sub.n_genomes = None
+        for k, v in over.items():
+            setattr(sub, k, v)
+        t0 = time.perf_counter()
+        try:
+            r = fn(sub, emit=False)
+        except Exception as e:  # noqa: BLE001 - reported in the line
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+            continue
+        finally:
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+        if name == "batched":
+            out[name] = {"workload": r["config"]["workload"], "value": r["value"], "unit": r["unit"],
+                         "s_per_pass": r["s_per_pass"], "steps": r["steps"],
+                         "plain": {"value": r["plain"]["value"], "form": r["plain"]["form"],
+                                   "genomes": r["plain"]["genomes"]},
+                         "plain_all_pairs": {"value": r["plain_all_pairs"]["value"],
+                                             "form": r["plain_all_pairs"]["form"]},
+                         "batched_over_plain": r["batched_over_plain"],
+                         "batched_over_plain_all_pairs": r["batched_over_plain_all_pairs"],
+                         "input": r["config"]["input"], "h2d_gbs": r["h2d_gbs"],
+                         "results_per_pass": r["results_per_pass"], "clocks": r["clocks"]}
+        else:
+            out[name] = {"workload": r["config"]["workload"], "requests": r["config"]["requests"],
+                         "rate_per_s": r["config"]["rate_per_s"], "k": r["config"]["k"],
+                         "max_batch": r["config"]["max_batch"], "mem_budget": r["config"]["mem_budget"],
+                         "poisson": r["poisson"], "saturated": r["saturated"],
+                         "sequential_plain": r["sequential_plain"],
+                         "saturated_over_sequential": r["saturated_over_sequential"],
+                         "same_results_poisson_and_saturated": r["same_results_poisson_and_saturated"]}
+        out[name]["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 def bench_hmm(args):
