@@ -1652,6 +1652,24 @@ def bench_hmm(args):
     torch.cuda.synchronize()
     dt_f = ev[0].elapsed_time(ev[1]) / 1e3 / args.steps
     got_f = out_f.cpu().numpy()
+    # the other kernel of each score on the same amplicons (AH_HMM_KERNEL), for comparison
+    other = {}
+    try:
+        for name, kern, fn, o in (("viterbi", "wave", ctx.hmm_score, out), ("forward", "rows", ctx.hmm_forward, out_f)):
+            os.environ["AH_HMM_KERNEL"] = kern
+            fn(sid, hid, dev_amps, n=len(amps), out=o, stream=stream)
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            for _ in range(args.steps):
+                fn(sid, hid, dev_amps, n=len(amps), out=o, stream=stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            d = ev[0].elapsed_time(ev[1]) / 1e3 / args.steps
+            other[name] = {"kernel": kern, "value": cells / d / 1e9, "unit": "GCUPS", "ms_per_step": d * 1e3}
+        other["viterbi"]["max_abs_diff_bits"] = float(np.abs(out.cpu().numpy() - got).max())
+        other["forward"]["max_abs_diff_bits"] = float(np.abs(out_f.cpu().numpy() - got_f).max())
+    finally:
+        os.environ.pop("AH_HMM_KERNEL", None)
     # the oracle on a sample: its own profile from the same training sequences
     import oracle
     rng = np.random.default_rng(0)
@@ -1673,7 +1691,9 @@ def bench_hmm(args):
     err = np.abs(got[sample].astype(np.float64) - want)
     err_f = np.abs(got_f[sample].astype(np.float64) - want_f)
     clocks = clk.summary()
-    fp_ops_per_cell = 19  # FADD + FMNMX per cell, counted in the kernel source (M 6, I 5, delete chain 8)
+    # FADD + FMNMX per cell of the recurrence (M 6, I 5, D 5); the block-per-group kernel
+    # that scores Viterbi executes 19 (its delete-chain scan evaluates D's terms twice)
+    fp_ops_per_cell = 16
     fp32_peak = 152 * 128 * (clocks["sm_mhz"] or 2070.0) * 1e6
     achieved = cells / dt * fp_ops_per_cell
     line = {
@@ -1694,6 +1714,9 @@ def bench_hmm(args):
                     "oracle_check": {"amplicons": len(sample),
                                      "max_abs_err_bits": float(err_f.max()) if len(err_f) else 0.0,
                                      "within_fp32_bound": bool((err_f <= tol_f).all())}},
+        "kernels": {"viterbi": "hmm_score_kernel (a block per group of amplicons, rows in lockstep)",
+                    "forward": "hmm_wave_kernel (one warp per amplicon, anti-diagonal steps)"},
+        "other_kernel": other,
         "cpu_baseline": {"value": cpu_cells / t_cpu / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
                          "sample": f"{len(sample)} amplicons, fp64 Viterbi, {t_cpu:.1f} s"},
         "clocks": clocks,

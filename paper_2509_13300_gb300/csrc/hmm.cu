@@ -20,13 +20,32 @@
 // amplicon's sequence (as ah_fetch returns it) against the profile, fp32, or
 // the glocal Forward score: the same recurrence with the maximum of the
 // predecessors replaced by log2(2^a + 2^b) (the log-sum semiring).
-// A block scores a group of amplicons of similar length in lockstep, rows =
-// sequence letters: each thread owns K consecutive profile columns with their
-// 13 scores in registers; M and I of a row depend only on the previous row
-// (the left neighbour's values come by shuffle, or through shared memory
-// across warps); the delete chain D_j = max(E_j, D_{j-1} + t_DD) is a
-// block-wide scan in the (max, +) semiring over (t_DD, E_j) pairs (for the
-// Forward score, in (log-sum, +)).
+// Two kernels compute the same recurrence.
+//
+// hmm_wave_kernel (the Forward scores' default): one warp per amplicon, no
+// block barriers.  The
+// profile's columns are cut into stripes of 32 * K; within a stripe lane l
+// owns K consecutive columns with their 13 scores in registers and, at step
+// s, computes row i = s - l (an anti-diagonal wavefront): M and I of its
+// columns from its own previous row, the delete chain along its K columns.
+// The left neighbour's last column arrives by one shuffle per state (its row
+// i from the previous step; its row i - 1 is kept from the step before).
+// Lane 0 takes column (stripe start - 1) from the previous stripe, whose
+// lane 31 wrote it per row to a per-warp boundary buffer in global memory;
+// the warp loads it 32 rows at a time (one row per lane, two blocks ahead of
+// use) and hands row i to lane 0 by shuffle at step i (row i is overwritten
+// at step i + 31, after its block was loaded).  A stripe
+// costs len + 32 steps, so the wavefront's fill and drain are 31 steps per
+// stripe.
+//
+// hmm_score_kernel (the Viterbi scores' default; AH_HMM_KERNEL=rows or =wave
+// forces one kernel for both scores): a block scores a group of amplicons
+// of similar length in lockstep, rows = sequence letters: each thread owns K
+// consecutive profile columns with their 13 scores in registers; M and I of a
+// row depend only on the previous row (the left neighbour's values come by
+// shuffle, or through shared memory across warps); the delete chain
+// D_j = max(E_j, D_{j-1} + t_DD) is a block-wide scan in the (max, +)
+// semiring over (t_DD, E_j) pairs (for the Forward score, in (log-sum, +)).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -468,14 +487,242 @@ bool launch_k(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const 
     return true;
 }
 
+// Letter codes of amplicon `am` into seq, the warp's lanes in turn.
+__device__ void decode_letters_warp(const ah_amplicon &am, const uint32_t *__restrict__ planes,
+                                    const uint64_t *__restrict__ contig_off, uint8_t *seq, int len, int lane)
+{
+    const uint64_t base = contig_off[am.contig] + am.start;
+    const bool rc = am.orient == 1;
+    for (int q = lane; q < len; q += 32) {
+        const uint64_t P = base + (rc ? (uint64_t)(len - 1 - q) : (uint64_t)q);
+        const uint64_t tt = P / kTileBases, r = P % kTileBases;
+        const int b = (int)(r / kTileW), j = (int)(r % kTileW);
+        const uint32_t *w = planes + tt * 4 * kTileWX + j;
+        int code = 4;
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+            if ((__ldg(w + x * kTileWX) >> b) & 1u)
+                code = x;
+        if (code < 4 && rc)
+            code = 3 - code;
+        seq[q] = (uint8_t)code;
+    }
+}
+
+constexpr int kWaveWarps = 4;        // warps (amplicons in flight) per block
+constexpr int kWaveBlocksPerSm = 8;  // grid: at most this many blocks per SM
+constexpr uint64_t kWaveScratchMax = 256ull << 20;
+
+// One warp per amplicon; lanes over the columns of a stripe, steps over
+// anti-diagonals (see the head of this file).  bnd_all: 3 * (max_len + 1)
+// floats per warp of the grid (M, I, D of the column left of the stripe, per
+// row).
+template <class Op, int K>
+__global__ void __launch_bounds__(32 * kWaveWarps) hmm_wave_kernel(
+    const ah_amplicon *__restrict__ amps, const uint32_t *__restrict__ order, uint64_t n_amps,
+    const uint32_t *__restrict__ planes, const uint64_t *__restrict__ contig_off, uint32_t n_contigs,
+    const float *__restrict__ t, const float *__restrict__ e, int m, int max_len, float *__restrict__ bnd_all,
+    float *__restrict__ score_out, int *__restrict__ err)
+{
+    extern __shared__ uint8_t wave_seq[]; // kWaveWarps x seq_stride letter codes
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int seq_stride = (max_len + 15) & ~15;
+    uint8_t *seq = wave_seq + warp * seq_stride;
+    const uint64_t slot = (uint64_t)blockIdx.x * kWaveWarps + warp;
+    float *bnd = bnd_all + slot * 3ull * (uint64_t)(max_len + 1);
+    constexpr int span = 32 * K;
+    const int n_stripes = (m + 1 + span - 1) / span;
+    const float endM = t[m * 9 + kM * 3], endI = t[m * 9 + kI * 3], endD = t[m * 9 + kD * 3];
+    for (uint64_t q = slot; q < n_amps; q += (uint64_t)gridDim.x * kWaveWarps) {
+        const uint32_t idx = order[q];
+        const ah_amplicon am = amps[idx];
+        bool ok = am.contig < n_contigs && am.start <= am.end;
+        if (ok)
+            ok = (uint64_t)am.end <= contig_off[am.contig + 1] - contig_off[am.contig] &&
+                 am.end - am.start <= (uint32_t)max_len;
+        if (!ok) { // checked on the host; reported, not read
+            if (lane == 0) {
+                atomicExch(err, kDevBounds);
+                score_out[idx] = kNeg;
+            }
+            continue;
+        }
+        const int len = (int)(am.end - am.start);
+        __syncwarp(); // the previous amplicon's letters are no longer read
+        decode_letters_warp(am, planes, contig_off, seq, len, lane);
+        __syncwarp();
+        for (int s = 0; s < n_stripes; ++s) {
+            const int c0 = s * span + lane * K;
+            // scores of the moves into M_j (from j-1), into D_j (from j-1), into I_j (from j); M_j's emissions
+            float toM[K][3], toD[K][3], toI[K][3], em[K][4];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int j = c0 + k;
+#pragma unroll
+                for (int x = 0; x < 3; ++x) {
+                    toM[k][x] = (j >= 1 && j <= m) ? t[(j - 1) * 9 + x * 3 + 0] : kNeg;
+                    toD[k][x] = (j >= 1 && j <= m) ? t[(j - 1) * 9 + x * 3 + 2] : kNeg;
+                    toI[k][x] = (j <= m) ? t[j * 9 + x * 3 + 1] : kNeg;
+                }
+#pragma unroll
+                for (int l = 0; l < 4; ++l)
+                    em[k][l] = (j >= 1 && j <= m) ? e[j * 4 + l] : 0.0f;
+            }
+            float pM[K], pI[K], pD[K]; // this lane's columns at its previous row
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                pM[k] = pI[k] = pD[k] = kNeg;
+            float lpM = kNeg, lpI = kNeg, lpD = kNeg; // column c0 - 1 at the previous row
+            float oM = kNeg, oI = kNeg, oD = kNeg;    // this lane's last column at its latest row
+            const bool last_stripe = s + 1 == n_stripes;
+            // the previous stripe's boundary, 32 rows per block, row 32 b + lane in each lane:
+            // the block in use and the next one (loaded 32 steps before lane 0 needs it)
+            float bM, bI, bD, nM, nI, nD;
+            auto load_block = [&](int blk, float &M_, float &I_, float &D_) {
+                const int r = blk * 32 + lane;
+                M_ = I_ = D_ = kNeg;
+                if (s > 0 && r <= len) {
+                    M_ = bnd[3 * r];
+                    I_ = bnd[3 * r + 1];
+                    D_ = bnd[3 * r + 2];
+                }
+            };
+            load_block(0, bM, bI, bD);
+            load_block(1, nM, nI, nD);
+            for (int st = 0; st < len + 32; ++st) {
+                const int i = st - lane;
+                // column c0 - 1 at row i: the left lane's latest row, or the previous stripe's boundary
+                float rM = __shfl_up_sync(0xffffffffu, oM, 1);
+                float rI = __shfl_up_sync(0xffffffffu, oI, 1);
+                float rD = __shfl_up_sync(0xffffffffu, oD, 1);
+                if (s > 0) {
+                    const float gM = __shfl_sync(0xffffffffu, bM, st & 31);
+                    const float gI = __shfl_sync(0xffffffffu, bI, st & 31);
+                    const float gD = __shfl_sync(0xffffffffu, bD, st & 31);
+                    if (lane == 0) {
+                        rM = gM;
+                        rI = gI;
+                        rD = gD;
+                    }
+                    if ((st & 31) == 31) { // rows 32 b + 64 .. are not yet overwritten (row r at step r + 31)
+                        bM = nM;
+                        bI = nI;
+                        bD = nD;
+                        load_block((st >> 5) + 2, nM, nI, nD);
+                    }
+                } else if (lane == 0) {
+                    rM = rI = rD = kNeg;
+                }
+                if (i < 0 || i > len)
+                    continue;
+                float cM[K], cI[K], cD[K];
+                if (i == 0) { // B = M_0 at row 0; no letter consumed yet
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        cM[k] = (c0 + k == 0) ? 0.0f : kNeg;
+                        cI[k] = kNeg;
+                    }
+                } else {
+                    const int x = seq[i - 1];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const float qm = k ? pM[k - 1] : lpM, qi = k ? pI[k - 1] : lpI, qd = k ? pD[k - 1] : lpD;
+                        // (a select, not an indexed load: the emission scores stay in registers)
+                        const float ex =
+                            x == 0 ? em[k][0] : x == 1 ? em[k][1] : x == 2 ? em[k][2] : x == 3 ? em[k][3] : 0.0f;
+                        cM[k] = ex + Op::add(Op::add(qm + toM[k][kM], qi + toM[k][kI]), qd + toM[k][kD]);
+                        cI[k] = Op::add(Op::add(pM[k] + toI[k][kM], pI[k] + toI[k][kI]), pD[k] + toI[k][kD]);
+                    }
+                }
+                // the delete chain along the row
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const float lm = k ? cM[k - 1] : rM, li = k ? cI[k - 1] : rI, ld = k ? cD[k - 1] : rD;
+                    cD[k] = Op::add(Op::add(lm + toD[k][kM], li + toD[k][kI]), ld + toD[k][kD]);
+                }
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    pM[k] = cM[k];
+                    pI[k] = cI[k];
+                    pD[k] = cD[k];
+                }
+                lpM = rM;
+                lpI = rI;
+                lpD = rD;
+                oM = cM[K - 1];
+                oI = cI[K - 1];
+                oD = cD[K - 1];
+                if (lane == 31 && !last_stripe) {
+                    bnd[3 * i] = oM;
+                    bnd[3 * i + 1] = oI;
+                    bnd[3 * i + 2] = oD;
+                }
+                if (i == len && last_stripe)
+#pragma unroll
+                    for (int k = 0; k < K; ++k)
+                        if (c0 + k == m)
+                            score_out[idx] = Op::add(Op::add(cM[k] + endM, cI[k] + endI), cD[k] + endD);
+            }
+            __syncwarp(); // the stripe's boundary is written before the next stripe reads it
+        }
+    }
+}
+
+uint64_t wave_blocks(uint64_t n, int max_len, int sms)
+{
+    const uint64_t per_block = (uint64_t)kWaveWarps * 3ull * (uint64_t)(max_len + 1) * sizeof(float);
+    uint64_t b = std::min<uint64_t>((n + kWaveWarps - 1) / kWaveWarps, (uint64_t)sms * kWaveBlocksPerSm);
+    b = std::min<uint64_t>(b, std::max<uint64_t>((uint64_t)sms, kWaveScratchMax / per_block));
+    return std::max<uint64_t>(b, 1);
+}
+
+template <class Op, int K>
+void launch_wave(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
+                 const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m, int max_len,
+                 float *bnd, float *out, int *err, int sms, cudaStream_t s)
+{
+    const size_t smem = (size_t)kWaveWarps * (size_t)((max_len + 15) & ~15);
+    AH_CUDA(cudaFuncSetAttribute(hmm_wave_kernel<Op, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::max<size_t>(smem, 1)));
+    const uint64_t blocks = wave_blocks(n, max_len, sms);
+    hmm_wave_kernel<Op, K><<<(unsigned)blocks, 32 * kWaveWarps, smem, s>>>(amps, order, n, planes, contig_off,
+                                                                           n_contigs, t, e, m, max_len, bnd, out, err);
+    AH_CUDA(cudaGetLastError());
+}
+
 } // namespace
+
+size_t hmm_scratch_bytes(uint64_t n, int max_len, int sms)
+{
+    return wave_blocks(n, max_len, sms) * (uint64_t)kWaveWarps * 3ull * (uint64_t)(max_len + 1) * sizeof(float);
+}
 
 void launch_hmm_score(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
                       const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m,
-                      int max_len, bool forward, float *score_out, int *err, int sms, cudaStream_t s)
+                      int max_len, bool forward, float *bnd, float *score_out, int *err, int sms, cudaStream_t s)
 {
     if (n == 0)
         return;
+    // default: the warp wavefront for Forward scores (108 against 91 GCUPS on 639 columns x 5,023
+    // amplicons), the block-per-group kernel for Viterbi scores (457 against 310); AH_HMM_KERNEL=rows
+    // or =wave forces one of them (profiling aid)
+    const char *kern = getenv("AH_HMM_KERNEL");
+    bool wave = forward;
+    if (kern && strcmp(kern, "rows") == 0)
+        wave = false;
+    else if (kern && strcmp(kern, "wave") == 0)
+        wave = true;
+    if (wave) {
+        if (m + 1 > kHmmMaxColumns)
+            throw Error(AH_ERR_ARG, "ah_hmm_score: profile longer than " + std::to_string(kHmmMaxColumns) + " columns");
+        if (forward)
+            launch_wave<LogSum, 4>(amps, order, n, planes, contig_off, n_contigs, t, e, m, max_len, bnd, score_out,
+                                   err, sms, s);
+        else
+            launch_wave<MaxSum, 4>(amps, order, n, planes, contig_off, n_contigs, t, e, m, max_len, bnd, score_out,
+                                   err, sms, s);
+        return;
+    }
     const int cols = m + 1;
     // AH_HMM_VARIANT="K,A" picks columns per thread and amplicons per block (profiling aid)
     int vk = 0, va = 0;

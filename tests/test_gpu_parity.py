@@ -1154,3 +1154,61 @@ def test_profile_hmm_build_and_scores(ctx):
     err_f = np.abs(got_f.astype(np.float64) - want_f)
     assert (err_f <= tol_f).all(), (err_f.max(), tol_f.min())
     assert (want_f >= want - 1e-9).all() and (got_f >= got - 1e-3).all()  # the sum is at least the best path
+
+
+@pytest.mark.parametrize("kernel", ["wave", "rows"])
+def test_profile_hmm_kernels_on_profiles_of_several_lengths(ctx, kernel, monkeypatch):
+    """Both scoring kernels (the warp wavefront and the block-per-group kernel,
+    forced by AH_HMM_KERNEL for both scores) against the oracle's fp64 Viterbi
+    and Forward scores, on profiles of m + 1 = 40, 129, 255 and 640 columns
+    (the wavefront's stripes hold 128: a lone partial stripe, a last stripe of
+    one column, a nearly full one, five full ones) and on amplicons of 0, 1 and
+    2 letters up to 1,700."""
+    monkeypatch.setenv("AH_HMM_KERNEL", kernel)
+    w = synth.operon_family(seed=21, n_genomes=16)
+    p = w.pairs[0]
+    p0 = dict(p, k=0)
+    s0 = oracle.scan(w.seq, w.contig_off, w.contig_genome, [p0])
+    a0 = oracle.pair(s0, [p0])
+    q0, o0 = oracle.fetch(w.seq, w.contig_off, a0)
+    train = [q0[int(o0[i]):int(o0[i + 1])].decode() for i in range(len(a0))]
+    assert min(len(x) for x in train) >= 254
+    s2 = oracle.scan(w.seq, w.contig_off, w.contig_genome, [p])
+    amps = oracle.pair(s2, [p])[:24]
+    rng = np.random.default_rng(8)
+    lens = np.diff(w.contig_off.astype(np.int64))
+    extra = np.zeros(24, dtype=oracle.AMPLICON_DTYPE)
+    for q, r in enumerate(extra):
+        c = int(rng.integers(len(lens)))
+        L = [0, 1, 2][q] if q < 3 else int(rng.integers(3, 1700))
+        s = int(rng.integers(0, lens[c] - L))
+        r["genome"], r["contig"], r["start"], r["end"], r["orient"] = w.contig_genome[c], c, s, s + L, q % 2
+    amps = np.concatenate([amps, extra])
+    qa, oa = oracle.fetch(w.seq, w.contig_off, amps)
+    seqs = [qa[int(oa[i]):int(oa[i + 1])].decode() for i in range(len(amps))]
+    sid = ctx.load(w.seq, w.contig_off, w.contig_genome)
+    try:
+        for cut in (39, 128, 254, None):
+            tr = [x[:cut] for x in train] if cut else train
+            _, T, E = oracle.hmm_build(tr)
+            m = T.shape[0] - 1
+            assert m == (cut or m)
+            hid = ctx.hmm_build(tr)
+            got = ctx.hmm_score(sid, hid, amps).astype(np.float64)
+            got_f = ctx.hmm_forward(sid, hid, amps).astype(np.float64)
+            ctx.hmm_free(hid)
+            want = np.array([oracle.hmm_viterbi(T, E, x) for x in seqs])
+            want_f = np.array([oracle.hmm_forward(T, E, x) for x in seqs])
+            fin = ~np.isinf(T)
+            # the fp32 accumulation bound of the test above (a random walk of
+            # roundings along one path of N = n + m moves, ten standard deviations)
+            pmean = float(np.concatenate([np.abs(T[fin]), np.abs(E[1:]).ravel()]).mean())
+            N = np.array([len(x) for x in seqs]) + m
+            tol = 10.0 * np.sqrt(N) * 2.0 ** -24 * (np.abs(want) + N * pmean) + 1e-4
+            tol_f = 10.0 * np.sqrt(N) * (2.0 ** -24 * (np.abs(want_f) + N * pmean) + 4 * 2.0 ** -23) + 1e-4
+            assert np.isfinite(got).all() and np.isfinite(got_f).all(), (cut, kernel)
+            err, err_f = np.abs(got - want), np.abs(got_f - want_f)
+            assert (err <= tol).all(), (cut, kernel, err.max(), int(err.argmax()))
+            assert (err_f <= tol_f).all(), (cut, kernel, err_f.max(), int(err_f.argmax()))
+    finally:
+        ctx.ah_unload_genomes(sid)
