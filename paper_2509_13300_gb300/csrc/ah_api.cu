@@ -15,6 +15,7 @@
 #include <thread>
 
 #include "ah_internal.h"
+#include "hmm.h"
 
 using namespace ah;
 
@@ -2913,11 +2914,15 @@ ah_status hmm_scores(ah_ctx *c, uint32_t set_id, uint32_t hmm_id, const ah_ampli
         uint32_t *d_ord = (uint32_t *)scratch(c, "hmm_order", n * sizeof(uint32_t));
         AH_CUDA(cudaMemcpyAsync(d_ord, ord.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
         float *out = out_buf(c, "hmm_out", score_out, n);
-        float *bnd = (float *)scratch(c, "hmm_bnd", hmm_scratch_bytes(n, (int)max_len, c->sms));
-        {
+        if (hmm_use_wave(forward)) {
+            float *bnd = (float *)scratch(c, "hmm_bnd", hmm_scratch_bytes(n, (int)max_len, c->sms));
+            Stage sg(c, "hmm", st, 1);
+            launch_hmm_wave(a, d_ord, n, gs.planes, gs.contig_off, gs.n_contigs, p.d_t, p.d_e, p.m, (int)max_len,
+                            forward, bnd, out, c->d_err, c->sms, st);
+        } else {
             Stage sg(c, "hmm", st, 1);
             launch_hmm_score(a, d_ord, n, gs.planes, gs.contig_off, gs.n_contigs, p.d_t, p.d_e, p.m, (int)max_len,
-                             forward, bnd, out, c->d_err, c->sms, st);
+                             forward, out, c->d_err, c->sms, st);
         }
         check_flags(c, st);
         out_finish(score_out, out, n, st);

@@ -98,11 +98,9 @@ struct HmmProfile {
 void build_profile(const char *seqs, const uint64_t *off, uint64_t n, HmmProfile &p);
 // order: n indices into amps, amplicons of similar length next to each other;
 // forward: the Forward (log-sum over paths) score instead of Viterbi
-// bnd: hmm_scratch_bytes(n, max_len, sms) bytes of device scratch (the wavefront kernel's stripe boundaries)
 void launch_hmm_score(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
                       const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m,
-                      int max_len, bool forward, float *bnd, float *score_out, int *err, int sms, cudaStream_t s);
-size_t hmm_scratch_bytes(uint64_t n, int max_len, int sms);
+                      int max_len, bool forward, float *score_out, int *err, int sms, cudaStream_t s);
 
 // Tunables of the generated scan kernel (autotuned per pattern set).
 struct ScanTuning {

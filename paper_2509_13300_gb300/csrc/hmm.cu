@@ -53,6 +53,7 @@
 #include <cstring>
 
 #include "ah_internal.h"
+#include "hmm.h"
 
 namespace ah {
 namespace {
@@ -697,32 +698,40 @@ size_t hmm_scratch_bytes(uint64_t n, int max_len, int sms)
     return wave_blocks(n, max_len, sms) * (uint64_t)kWaveWarps * 3ull * (uint64_t)(max_len + 1) * sizeof(float);
 }
 
-void launch_hmm_score(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
-                      const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m,
-                      int max_len, bool forward, float *bnd, float *score_out, int *err, int sms, cudaStream_t s)
+bool hmm_use_wave(bool forward)
+{
+    // measured on 639 columns x 5,023 amplicons: Forward 108 GCUPS on the wavefront against 91 on
+    // the block kernel; Viterbi 310 against 457
+    const char *kern = getenv("AH_HMM_KERNEL");
+    if (kern && strcmp(kern, "rows") == 0)
+        return false;
+    if (kern && strcmp(kern, "wave") == 0)
+        return true;
+    return forward;
+}
+
+void launch_hmm_wave(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
+                     const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m,
+                     int max_len, bool forward, float *bnd, float *score_out, int *err, int sms, cudaStream_t s)
 {
     if (n == 0)
         return;
-    // default: the warp wavefront for Forward scores (108 against 91 GCUPS on 639 columns x 5,023
-    // amplicons), the block-per-group kernel for Viterbi scores (457 against 310); AH_HMM_KERNEL=rows
-    // or =wave forces one of them (profiling aid)
-    const char *kern = getenv("AH_HMM_KERNEL");
-    bool wave = forward;
-    if (kern && strcmp(kern, "rows") == 0)
-        wave = false;
-    else if (kern && strcmp(kern, "wave") == 0)
-        wave = true;
-    if (wave) {
-        if (m + 1 > kHmmMaxColumns)
-            throw Error(AH_ERR_ARG, "ah_hmm_score: profile longer than " + std::to_string(kHmmMaxColumns) + " columns");
-        if (forward)
-            launch_wave<LogSum, 4>(amps, order, n, planes, contig_off, n_contigs, t, e, m, max_len, bnd, score_out,
-                                   err, sms, s);
-        else
-            launch_wave<MaxSum, 4>(amps, order, n, planes, contig_off, n_contigs, t, e, m, max_len, bnd, score_out,
-                                   err, sms, s);
+    if (m + 1 > kHmmMaxColumns)
+        throw Error(AH_ERR_ARG, "ah_hmm_score: profile longer than " + std::to_string(kHmmMaxColumns) + " columns");
+    if (forward)
+        launch_wave<LogSum, 4>(amps, order, n, planes, contig_off, n_contigs, t, e, m, max_len, bnd, score_out, err,
+                               sms, s);
+    else
+        launch_wave<MaxSum, 4>(amps, order, n, planes, contig_off, n_contigs, t, e, m, max_len, bnd, score_out, err,
+                               sms, s);
+}
+
+void launch_hmm_score(const ah_amplicon *amps, const uint32_t *order, uint64_t n, const uint32_t *planes,
+                      const uint64_t *contig_off, uint32_t n_contigs, const float *t, const float *e, int m,
+                      int max_len, bool forward, float *score_out, int *err, int sms, cudaStream_t s)
+{
+    if (n == 0)
         return;
-    }
     const int cols = m + 1;
     // AH_HMM_VARIANT="K,A" picks columns per thread and amplicons per block (profiling aid)
     int vk = 0, va = 0;
