@@ -1562,14 +1562,18 @@ def form_keys(args):
         for k, v in over.items():
             setattr(sub, k, v)
         t0 = time.perf_counter()
+        r = None
         try:
             r = fn(sub, emit=False)
         except Exception as e:  # noqa: BLE001 - reported in the line
             out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
-            continue
-        finally:
+        try:  # the form's memory back before the next one (a failed form may leave the device unusable)
             torch.cuda.synchronize()
             torch.cuda.empty_cache()
+        except Exception:  # noqa: BLE001
+            pass
+        if r is None:
+            continue
         if name == "batched":
             out[name] = {"workload": r["config"]["workload"], "value": r["value"], "unit": r["unit"],
                          "s_per_pass": r["s_per_pass"], "steps": r["steps"],

@@ -121,3 +121,35 @@ def test_device_encode_2bit_equals_the_host_encoder():
         codes, gaps = bench.device_encode_2bit(torch, torch.from_numpy(seq.copy()), step=step)
         c2, g2 = ah.encode_2bit(seq)
         assert codes.numpy().tobytes() == c2.tobytes() and np.array_equal(gaps, g2), (n, step)
+
+
+def test_form_keys_summarise_each_form_and_report_a_failing_one(monkeypatch):
+    """The default line's `forms` key: each form runs on its own workload with the
+    overrides of the key (two batched passes after three, the served requests of
+    --forms-requests), a summary of its line is kept, and a form that raises is
+    reported by its error without stopping the others."""
+    import argparse
+    seen = {}
+
+    def batched(args, emit=True):
+        seen["batched"] = (args.steps, args.warmup, args.n_genomes, emit)
+        return {"config": {"workload": "batched-w", "input": "2-bit"}, "value": 2000.0, "unit": "Gbp/s",
+                "s_per_pass": 0.05, "steps": args.steps,
+                "plain": {"value": 14.0, "form": "one genome per load", "genomes": 400},
+                "plain_all_pairs": {"value": 27.0, "form": "one run of all pairs"},
+                "batched_over_plain": 2000.0 / 14.0, "batched_over_plain_all_pairs": 2000.0 / 27.0,
+                "h2d_gbs": 170.0, "results_per_pass": {"sites": 1}, "clocks": {"sm_mhz": 2070.0}}
+
+    def served(args, emit=True):
+        seen["served"] = (args.requests, args.n_genomes, emit)
+        raise RuntimeError("no device")
+
+    monkeypatch.setattr(bench, "bench_batched", batched)
+    monkeypatch.setattr(bench, "bench_served", served)
+    args = argparse.Namespace(steps=20, warmup=5, n_genomes=123, forms_requests=77, requests=2000)
+    out = bench.form_keys(args)
+    assert seen == {"batched": (2, 3, None, False), "served": (77, None, False)}
+    assert out["batched"]["workload"] == "batched-w" and out["batched"]["batched_over_plain"] == 2000.0 / 14.0
+    assert out["batched"]["plain"]["genomes"] == 400 and out["batched"]["wall_s"] >= 0.0
+    assert out["served"] == {"error": "RuntimeError: no device"}
+    assert args.steps == 20 and args.n_genomes == 123  # the caller's arguments are left alone
